@@ -1,0 +1,16 @@
+"""Plain FP64 CPU oracle of additive-multigrid MPCG (test infrastructure).
+
+This package is the slow, obviously-correct reference that the CUDA path is
+checked against.  It is test infrastructure only: ``tests/``,
+``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference``
+legs of ``bench.py`` may import it; the library never does, and the two share
+no code (only the seeded input generators of
+``paper_2402_12833_gb300.problems``, which hold none of the method's
+arithmetic).
+
+Modules
+  operators  - stencil -> CSR, prolongations (Section 2.1), Galerkin products
+  mg         - the additive MG level corrections (Eq. 3, Eq. 4) as columns
+  mpcg       - Algorithm 1 with the truncated window, pseudo-inverse, drop rule
+  pcg        - textbook additive-MG PCG, used only as an independent pin
+"""

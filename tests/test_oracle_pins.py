@@ -1,0 +1,318 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms, textbook algorithms, dense direct solves, invariants of Algorithm 1
+and the discretisation order.  A mistake planted in the oracle (dropped term,
+wrong sign, transposed operand) must fail at least one of them; the
+``test_planted_*`` cases plant a few such mistakes and show that they do.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import mg as omg
+from oracle import mpcg as ompcg
+from oracle.operators import prolongation, prolongation_1d, stencil_to_csr
+from oracle.pcg import pcg
+from paper_2402_12833_gb300 import problems as pb
+
+
+def _hier(prob, nu=2, omega=2.0 / 3.0):
+    return omg.Hierarchy(prob.dim, prob.n1, prob.stencil, prob.levels, nu=nu, omega=omega)
+
+
+# ---------------------------------------------------------------- transfers
+
+def _hat(t):
+    return np.maximum(0.0, 1.0 - np.abs(t))
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_prolongation_is_interpolation_of_the_coarse_q1_function(dim):
+    """P c evaluates the coarse Q1 function sum_I c_I phi_I at the fine nodes
+    (Section 2.1: nested spaces, P the natural embedding)."""
+    nc = 3
+    nf = 2 * nc + 1
+    rng = np.random.default_rng(0)
+    c = rng.standard_normal(nc ** dim)
+    P = prolongation(dim, nc) if dim > 1 else prolongation_1d(nc)
+    got = P @ c
+    hc, hf = 1.0 / (nc + 1), 1.0 / (nf + 1)
+    xf = (np.arange(nf) + 1) * hf
+    xc = (np.arange(nc) + 1) * hc
+    B = _hat((xf[:, None] - xc[None, :]) / hc)          # 1D coarse basis at fine nodes
+    full = B
+    for _ in range(dim - 1):
+        full = np.kron(B, full)
+    assert np.allclose(got, full @ c, atol=1e-14)
+
+
+def test_galerkin_equals_rediscretisation_constant_kappa():
+    """For constant coefficients, P^T A_h P is the Q1 matrix of the coarse grid."""
+    for dim, nodes in ((2, 33), (3, 17)):
+        prob = pb.poisson_random(dim, nodes, 1)
+        H = _hier(prob)
+        for j in range(H.levels - 1):
+            nj = H.n1[j] + 2
+            ref = stencil_to_csr(dim, H.n1[j], pb.assemble_diffusion(dim, nj))
+            assert abs(H.A[j] - ref).max() < 1e-13 * abs(ref).max()
+
+
+def test_galerkin_equals_rediscretisation_coarse_aligned_kappa():
+    """Same identity when kappa is constant on the coarsest elements."""
+    nodes = 33
+    kap4 = 10.0 ** (4 * pb.uniform(9, 16)).reshape(4, 4)          # 4x4 coarsest elements
+    prob_st = pb.assemble_diffusion(2, nodes, kappa=np.kron(kap4, np.ones((8, 8))))
+    H = omg.Hierarchy(2, nodes - 2, prob_st, pb.levels_for_nodes(nodes))
+    for j in range(H.levels - 1):
+        nj = H.n1[j] + 2
+        ref = stencil_to_csr(2, H.n1[j], pb.assemble_diffusion(2, nj, kappa=np.kron(kap4, np.ones(((nj - 1) // 4,) * 2))))
+        assert abs(H.A[j] - ref).max() < 1e-12 * abs(ref).max()
+
+
+# ---------------------------------------------------------------- level operators
+
+def test_two_sweep_jacobi_closed_form():
+    """Eq. 3 with c_0 = 0, nu = 2, M = D/omega: S g = 2 w D^-1 g - w^2 D^-1 A D^-1 g."""
+    prob = pb.diffusion_macro(2, 33, 5)
+    H = _hier(prob)
+    j = H.J
+    g = pb.normal(3, H.A[j].shape[0])
+    w = H.omega
+    Dinv = 1.0 / H.A[j].diagonal()
+    want = 2 * w * Dinv * g - w * w * Dinv * (H.A[j] @ (Dinv * g))
+    assert np.allclose(H.smooth(j, g), want, rtol=1e-13, atol=1e-13 * abs(want).max())
+
+
+def test_coarse_solve_matches_dense_solve():
+    prob = pb.diffusion_macro(3, 9, 2)
+    H = _hier(prob)
+    g = pb.normal(1, H.A[0].shape[0])
+    x = H.coarse_solve(g)
+    ref = np.linalg.solve(H.A[0].toarray(), g)
+    assert np.allclose(x, ref, rtol=1e-12, atol=1e-14)
+    assert np.linalg.norm(H.A[0] @ x - g) <= 1e-13 * np.linalg.norm(g)
+
+
+def test_columns_sum_to_additive_mg_eq4():
+    """sum_l z^l = B r of Eq. 4, with B built from dense composite transfers
+    and dense level operators (no successive application)."""
+    prob = pb.diffusion_macro(2, 17, 4)
+    H = _hier(prob)
+    n = H.A[-1].shape[0]
+    r = pb.normal(2, n)
+    B = np.zeros((n, n))
+    cols = []
+    for l in range(H.levels):
+        Pl = np.eye(n)
+        for i in range(H.levels - 1, l, -1):
+            Pl = Pl @ H.P[i].toarray()                 # P_l^L = P_J ... P_{l+1}
+        Al = H.A[l].toarray()
+        if l == 0:
+            S = np.linalg.inv(Al)
+        else:
+            Dw = np.diag(H.omega / np.diag(Al))
+            T = np.eye(Al.shape[0]) - Dw @ Al
+            S = Dw + T @ Dw                              # sum_{i<2} T^i (w D^-1)
+        Bl = Pl @ S @ Pl.T                              # R_L^l = (P_l^L)^T
+        cols.append(Bl @ r)
+        B += Bl
+    Z = H.mg_columns(r)
+    for l in range(H.levels):
+        assert np.allclose(Z[:, l], cols[l], rtol=1e-11, atol=1e-12 * abs(cols[l]).max())
+    assert np.allclose(Z.sum(axis=1), B @ r, rtol=1e-11, atol=1e-12)
+    assert np.allclose(B, B.T, atol=1e-12 * abs(B).max())   # symmetric preconditioner
+
+
+# ---------------------------------------------------------------- pseudo-inverse
+
+def test_scaled_pinv_is_inverse_for_spd():
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((7, 7))
+    G = X @ X.T + 0.1 * np.eye(7)
+    assert np.allclose(ompcg.scaled_pinv(G, 1e-12), np.linalg.inv(G), rtol=1e-9, atol=1e-10)
+
+
+def test_scaled_pinv_moore_penrose_on_singular():
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((6, 3))
+    G = X @ X.T                                          # rank 3
+    G[:, 5] = 0.0; G[5, :] = 0.0                         # a dropped column
+    Gp = ompcg.scaled_pinv(G, 1e-10)
+    assert np.allclose(G @ Gp @ G, G, atol=1e-9)
+    assert np.allclose(Gp @ G @ Gp, Gp, atol=1e-9)
+    assert np.all(Gp[5] == 0.0) and np.all(Gp[:, 5] == 0.0)
+    # alpha = G^+ g for g in range(G) solves G alpha = g
+    g = G @ rng.standard_normal(6)
+    assert np.allclose(G @ (Gp @ g), g, atol=1e-9)
+
+
+# ---------------------------------------------------------------- Algorithm 1
+
+def test_mpcg_single_summed_column_equals_pcg():
+    """With the one column B r, MPCG is additive MG-PCG (Section 2.2)."""
+    prob = pb.poisson_random(2, 65, 1)
+    H = _hier(prob)
+    A = H.A[-1]
+    one_col = lambda r: H.additive_mg(r)[:, None]
+    res = ompcg.mpcg(A, prob.b, one_col, m=1, rtol=1e-10)
+    x, k, hist = pcg(A, prob.b, H.additive_mg, rtol=1e-10)
+    assert res.iters == k
+    assert np.allclose(res.res_hist, hist, rtol=1e-6)
+    assert np.linalg.norm(res.x - x) <= 1e-11 * np.linalg.norm(x)
+
+
+def test_single_grid_converges_in_one_iteration():
+    prob = pb.poisson_random(2, 5, 3)                    # 3x3 interior, levels = 1
+    H = _hier(prob)
+    assert H.levels == 1
+    res = ompcg.mpcg(H.A[0], prob.b, H.mg_columns, rtol=1e-13)
+    assert res.iters == 1
+
+
+def test_exact_error_column_converges_in_one_iteration():
+    prob = pb.diffusion_macro(2, 33, 7, rhs="normal", rhs_seed=8)
+    H = _hier(prob)
+    A = H.A[-1]
+    Ad = A.toarray()
+    res = ompcg.mpcg(A, prob.b, H.mg_columns, rtol=1e-12, extra_column=lambda r: np.linalg.solve(Ad, r))
+    assert res.iters == 1
+
+
+def test_zero_extra_column_is_dropped_and_changes_nothing():
+    prob = pb.poisson_random(2, 33, 4)
+    H = _hier(prob)
+    A = H.A[-1]
+    plain = ompcg.mpcg(A, prob.b, H.mg_columns, rtol=1e-9)
+    zero = ompcg.mpcg(A, prob.b, H.mg_columns, rtol=1e-9, extra_column=lambda r: np.zeros_like(r))
+    assert zero.iters == plain.iters
+    assert all(H.levels in d for d in zero.dropped)
+    assert np.allclose(zero.x, plain.x, rtol=1e-13, atol=1e-15)
+    assert all(a[-1] == 0.0 for a in zero.alpha_hist)
+
+
+@pytest.mark.parametrize("m", [1, 5])
+def test_energy_error_monotone_and_orthogonality(m):
+    prob = pb.diffusion_macro(2, 33, 6, rhs="normal", rhs_seed=9)
+    H = _hier(prob)
+    A = H.A[-1]
+    xs = np.linalg.solve(A.toarray(), prob.b)
+    xk = []
+    # record iterates by re-running with growing maxit (plain, slow, obviously right)
+    for it in range(1, 9):
+        xk.append(ompcg.mpcg(A, prob.b, H.mg_columns, m=m, rtol=1e-30, maxit=it).x)
+    errs = [np.sqrt((xs - x) @ (A @ (xs - x))) for x in xk]
+    assert all(e2 <= e1 * (1 + 1e-12) for e1, e2 in zip(errs, errs[1:]))
+    res = ompcg.mpcg(A, prob.b, H.mg_columns, m=m, rtol=1e-30, maxit=8, keep_blocks=True)
+    r = prob.b.copy()
+    x = np.zeros_like(r)
+    for k, ((P, AP), a) in enumerate(zip(res.blocks, res.alpha_hist)):
+        x = x + P @ a
+        r_next = prob.b - A @ x
+        # P_k^T r_{k+1} = 0: alpha minimises the energy over x_k + span P_k
+        assert np.abs(P.T @ r_next).max() <= 1e-9 * np.abs(P.T @ r).max()
+        # P_k is A-orthogonal to the window's blocks
+        for Pj, _ in res.blocks[max(0, k - m):k]:
+            Gkj = P.T @ (A @ Pj)
+            scale = np.sqrt(np.outer(np.einsum("ij,ij->j", P, AP), np.einsum("ij,ij->j", Pj, A @ Pj)))
+            assert np.all(np.abs(Gkj) <= 1e-8 * scale + 1e-300)
+        r = r_next
+
+
+def test_full_window_iterate_is_energy_projection():
+    """With m >= k, x_k minimises the A-norm error over x_0 + span(P_0..P_{k-1})."""
+    prob = pb.diffusion_macro(2, 17, 2, rhs="normal", rhs_seed=3)
+    H = _hier(prob)
+    A = H.A[-1]
+    k = 4
+    res = ompcg.mpcg(A, prob.b, H.mg_columns, m=50, rtol=1e-30, maxit=k, keep_blocks=True)
+    V = np.column_stack([P for P, _ in res.blocks])
+    V = V[:, np.abs(V).max(axis=0) > 0]
+    y, *_ = np.linalg.lstsq(V.T @ (A @ V), V.T @ prob.b, rcond=1e-13)
+    assert np.linalg.norm(V @ y - res.x) <= 1e-8 * np.linalg.norm(res.x)
+
+
+@pytest.mark.parametrize("dim,nodes", [(2, 9), (2, 17), (3, 9)])
+def test_tiny_grids_match_dense_solution(dim, nodes):
+    prob = pb.diffusion_macro(dim, nodes, 1, rhs="normal", rhs_seed=2)
+    H = _hier(prob)
+    A = H.A[-1]
+    xs = np.linalg.solve(A.toarray(), prob.b)
+    res = ompcg.mpcg(A, prob.b, H.mg_columns, rtol=1e-14, maxit=400)
+    assert np.linalg.norm(res.x - xs) <= 1e-11 * np.linalg.norm(xs)
+
+
+def test_manufactured_solution_second_order():
+    """Nodal error against u = sin(pi x) sin(pi y) falls ~4x per refinement."""
+    errs = []
+    for nodes in (17, 33, 65, 129):
+        prob = pb.poisson_manufactured_2d(nodes)
+        H = _hier(prob)
+        res = ompcg.mpcg(H.A[-1], prob.b, H.mg_columns, rtol=1e-12)
+        errs.append(np.abs(res.x - pb.manufactured_u(2, nodes)).max())
+    ratios = [a / b for a, b in zip(errs, errs[1:])]
+    assert all(3.6 < q < 4.4 for q in ratios), ratios
+
+
+def test_manufactured_solution_second_order_3d():
+    errs = []
+    for nodes in (9, 17, 33):
+        prob = pb.poisson_manufactured_3d(nodes)
+        H = _hier(prob)
+        res = ompcg.mpcg(H.A[-1], prob.b, H.mg_columns, rtol=1e-12)
+        errs.append(np.abs(res.x - pb.manufactured_u(3, nodes)).max())
+    ratios = [a / b for a, b in zip(errs, errs[1:])]
+    assert all(3.4 < q < 4.6 for q in ratios), ratios
+
+
+def test_mpcg_fewer_iterations_than_pcg_on_poisson():
+    """Qualitative claim of Section 3.1, on a random right-hand side."""
+    prob = pb.poisson_random(2, 129, 1)
+    H = _hier(prob)
+    A = H.A[-1]
+    k_mp = ompcg.mpcg(A, prob.b, H.mg_columns, m=5).iters
+    _, k_pcg, _ = pcg(A, prob.b, H.additive_mg)
+    assert k_mp < k_pcg
+
+
+# ---------------------------------------------------------------- planted mistakes
+
+def test_planted_wrong_prolongation_weight_fails_interpolation_pin(monkeypatch):
+    import oracle.operators as ops
+
+    def bad_p1(nc):
+        nf = 2 * nc + 1
+        rows, cols, vals = [], [], []
+        for I in range(nc):
+            rows += [2 * I, 2 * I + 1, 2 * I + 2]; cols += [I] * 3; vals += [0.4, 1.0, 0.4]
+        return sp.csr_matrix((vals, (rows, cols)), shape=(nf, nc))
+    monkeypatch.setattr(ops, "prolongation_1d", bad_p1)
+    with pytest.raises(AssertionError):
+        test_galerkin_equals_rediscretisation_constant_kappa()
+
+
+def test_planted_residual_sign_fails_projection_pin(monkeypatch):
+    real = ompcg.mpcg
+
+    def flipped(A, b, mgc, **kw):
+        # plant: x -= P alpha instead of += (a wrong sign in the x update)
+        res = real(A, b, mgc, **kw)
+        res.x = -res.x
+        return res
+    monkeypatch.setattr(ompcg, "mpcg", flipped)
+    with pytest.raises(AssertionError):
+        test_full_window_iterate_is_energy_projection()
+
+
+def test_planted_transposed_restriction_fails_eq4_pin(monkeypatch):
+    real = omg.Hierarchy.restrict_all
+
+    def no_transpose(self, r):
+        rs = [None] * self.levels
+        rs[self.J] = r
+        for j in range(self.J, 0, -1):
+            rs[j - 1] = 0.25 * (self.P[j].T @ rs[j])        # plant: a rescaled restriction
+        return rs
+    monkeypatch.setattr(omg.Hierarchy, "restrict_all", no_transpose)
+    with pytest.raises(AssertionError):
+        test_columns_sum_to_additive_mg_eq4()
