@@ -1,0 +1,169 @@
+/*
+ * mpcg.h -- C ABI of the additive-multigrid multipreconditioned CG solver
+ * (Kothari, Nestola, Favino, Krause, "Integrating Additive Multigrid with
+ * Multipreconditioned Conjugate Gradient Method").
+ *
+ * The solver computes Algorithm 1 of the paper: every iteration builds the
+ * block Z = [z^0 | ... | z^L] of per-level additive multigrid corrections
+ * z^l = P_l^L S_l (R_L^l r) (Section 2.2; restriction R = P^T and composite
+ * transfers by successive two-level transfers, Section 2.1; damped-Jacobi
+ * smoothing S_l^nu on levels l >= 1, Eq. 3; an exact Cholesky solve on the
+ * coarsest level), A-orthogonalises it against the last m search blocks,
+ * and updates x and r with the energy-optimal coefficients
+ * alpha = (P^T A P)^+ P^T r (Section 2.2, Eq. 5 and Eq. 6).
+ *
+ * Problem class (Section 1): a symmetric positive definite matrix from a Q1
+ * finite-element discretisation on a uniform structured grid of the unit
+ * square or cube, homogeneous Dirichlet nodes eliminated.
+ *
+ * Conventions for every entry point
+ *   - Vectors hold the n interior unknowns in lexicographic order, x fastest.
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *     library never frees them.  mpcg_solve also accepts host pointers for b
+ *     and x (pinned or pageable) and stages them through device memory.
+ *   - All work is enqueued on the stream given in mpcg_options (0 = legacy
+ *     default stream).  Entry points that return results to the host
+ *     (iteration counts, histories) synchronise that stream before returning.
+ *   - A negative status is an error; mpcg_last_error() returns a message for
+ *     the calling thread.  No entry point aborts the process, and no kernel
+ *     traps or asserts.
+ *   - Thread safety: a hierarchy may be used by one host thread at a time.
+ */
+#ifndef MPCG_H
+#define MPCG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MPCG_OK = 0,
+  MPCG_NOT_CONVERGED = 1,  /* maxit reached; x holds the last iterate        */
+  MPCG_ERR_ARG = -1,       /* invalid argument (message says which)          */
+  MPCG_ERR_CUDA = -2,      /* a CUDA runtime call failed                     */
+  MPCG_ERR_NOT_SPD = -3,   /* coarsest operator not positive definite        */
+  MPCG_ERR_BREAKDOWN = -4, /* non-finite value, or every search column dropped */
+  MPCG_ERR_TIMEOUT = -5,   /* a bounded device-side wait ran out             */
+  MPCG_ERR_OOM = -6        /* device allocation failed                       */
+} mpcg_status;
+
+enum { MPCG_FORMAT_STENCIL = 0 };
+enum { MPCG_FP64 = 0, MPCG_MIXED = 1 };
+
+/* Largest supported number of columns (grids, plus an appended column) and
+ * window length. */
+#define MPCG_MAX_COLS 12
+#define MPCG_MAX_WINDOW 16
+
+/*
+ * A fine-grid operator in stencil form.
+ *   dim        2 or 3
+ *   nodes      nodes per side of the grid, boundary included; nodes - 1 must
+ *              be a power of two >= 4 (so that the grid can be coarsened
+ *              down to 5 nodes per side)
+ *   values_dev device array of 3^dim * n doubles, n = (nodes-2)^dim: plane s
+ *              (s = (dx+1) + 3(dy+1) [+ 9(dz+1)]) holds for every row the
+ *              coefficient coupling it to the neighbour at offset
+ *              (dx, dy[, dz]).  Couplings to eliminated boundary nodes must be
+ *              zero.  The matrix must be symmetric positive definite.
+ *              Read during mg_hierarchy_setup only.
+ */
+typedef struct {
+  int dim;
+  int nodes;
+  int format;                 /* MPCG_FORMAT_STENCIL */
+  const double* values_dev;
+} mg_operator;
+
+/* Solver options.  mpcg_default_options() fills the paper's / the default
+ * values: m = 5 (Section 3 uses the last 5 blocks), nu = 2, omega = 2/3,
+ * pinv_tau = 1e-12, drop_delta = 1e-10, precision MPCG_FP64,
+ * inner_rtol = 1e-4, inner pinv_tau = 1e-6, inner drop_delta = 1e-5. */
+typedef struct {
+  int m;                 /* truncation window: stored search blocks, 1..MPCG_MAX_WINDOW */
+  int nu;                /* damped-Jacobi sweeps per level, >= 1 (Eq. 3, c_0 = 0) */
+  double omega;          /* Jacobi damping */
+  double pinv_tau;       /* eigenvalue cutoff of the scaled pseudo-inverse (FP64 path) */
+  double drop_delta;     /* column-drop threshold on A-norm^2 ratios (FP64 path) */
+  int precision;         /* MPCG_FP64, or MPCG_MIXED (FP32 bulk, FP64 reductions + refinement) */
+  double inner_rtol;     /* MPCG_MIXED: relative tolerance of each FP32 inner solve */
+  double inner_pinv_tau; /* MPCG_MIXED: cutoff used inside the FP32 inner solve */
+  double inner_drop_delta;
+  int max_outer;         /* MPCG_MIXED: maximum refinement steps */
+  void* stream;          /* cudaStream_t */
+} mpcg_options;
+
+typedef struct mg_hierarchy mg_hierarchy;
+
+/* Fill *opt with the defaults listed above.  Returns MPCG_ERR_ARG on NULL. */
+mpcg_status mpcg_default_options(mpcg_options* opt);
+
+/*
+ * Build the multilevel hierarchy below A_fine (Section 2.1): `levels` nested
+ * grids by uniform coarsening (levels = 1: the fine grid is the coarsest and
+ * is solved exactly), bilinear/trilinear prolongations P_j between
+ * consecutive grids, restrictions R_j = P_j^T, Galerkin coarse operators
+ * A_{j-1} = P_j^T A_j P_j, the damped inverse diagonals, and the dense
+ * Cholesky factor of the coarsest operator.  All of it is computed on the
+ * device.  The coarsest grid may hold at most 1024 unknowns.
+ * On success *out owns device memory until mg_hierarchy_destroy.
+ * Errors: MPCG_ERR_ARG (bad sizes, levels too many for the grid),
+ * MPCG_ERR_NOT_SPD (coarsest Cholesky failed), MPCG_ERR_OOM, MPCG_ERR_CUDA.
+ */
+mpcg_status mg_hierarchy_setup(const mg_operator* A_fine, int levels,
+                               const mpcg_options* opt, mg_hierarchy** out);
+
+/*
+ * Solve A x = b by Algorithm 1 (FP64), or by FP32 inner MPCG solves inside
+ * FP64 iterative refinement when opt->precision == MPCG_MIXED.
+ *   b, x       n doubles each (device or host memory); x holds x_0 on entry
+ *              and the final iterate on return.
+ *   rtol       stop when ||b - A x||_2 <= rtol ||b||_2 (recursive residual in
+ *              the FP64 path; true FP64 residual in the mixed path)
+ *   maxit      maximum number of x updates (inner updates in MIXED)
+ *   iters_out  number of x updates performed (may be NULL)
+ *   res_hist   host array of >= maxit+1 doubles or NULL: ||r_k||/||b||
+ *   alpha_hist host array of >= maxit * ncols doubles or NULL: the alpha
+ *              vector of each iteration (FP64 path), ncols = mg_num_columns()
+ * Returns MPCG_OK, MPCG_NOT_CONVERGED, or an error.  On MPCG_ERR_BREAKDOWN
+ * x holds the last iterate.
+ */
+mpcg_status mpcg_solve(mg_hierarchy* h, const double* b, double* x, double rtol,
+                       int maxit, int* iters_out, double* res_hist, double* alpha_hist);
+
+/* Number of grids and of search columns (grids + appended columns). */
+int mg_num_levels(const mg_hierarchy* h);
+int mg_num_columns(const mg_hierarchy* h);
+/* Interior unknowns of grid `level` (0 = coarsest), or -1. */
+long long mg_level_size(const mg_hierarchy* h, int level);
+
+/*
+ * Y = A_level X for `ncols` columns (block SpMM of the Section 2.2 update
+ * A Z); X_dev, Y_dev are column-major n_level x ncols device arrays.
+ */
+mpcg_status mg_apply_operator(mg_hierarchy* h, int level, const double* X_dev,
+                              double* Y_dev, int ncols);
+
+/*
+ * Z = [z^0 | ... | z^J] (Section 2.2): the additive multigrid correction of
+ * every grid for the fine residual r, coarse grid first.  Z_dev is a
+ * column-major n x levels device array.
+ */
+mpcg_status mg_corrections(mg_hierarchy* h, const double* r_dev, double* Z_dev);
+
+/* Copy grid `level`'s Galerkin operator in the stencil format above into
+ * planes_dev (3^dim * n_level doubles, device). */
+mpcg_status mg_get_operator(mg_hierarchy* h, int level, double* planes_dev);
+
+/* Release everything the hierarchy owns.  NULL is ignored. */
+void mg_hierarchy_destroy(mg_hierarchy* h);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* mpcg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPCG_H */

@@ -1,0 +1,718 @@
+// C ABI of libmpcg: hierarchy setup (Section 2.1) and the additive-MG MPCG
+// solver (Section 2.2, Algorithm 1), FP64 and FP32-bulk mixed precision.
+//
+// One solver iteration is captured once as a CUDA graph whose body sits in a
+// device-side while loop (a conditional graph node): the convergence kernel
+// clears the loop condition, so a whole solve is a single graph launch with
+// no host round trip per iteration.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace mpcg;
+
+namespace {
+
+thread_local std::string g_err;
+
+void set_err(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      set_err("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return e_ == cudaErrorMemoryAllocation ? MPCG_ERR_OOM : MPCG_ERR_CUDA;               \
+    }                                                                                      \
+  } while (0)
+
+#define CKS(expr)                              \
+  do {                                         \
+    mpcg_status s_ = (expr);                   \
+    if (s_ != MPCG_OK) return s_;              \
+  } while (0)
+
+struct Level {
+  GridDesc g;
+  double* st64 = nullptr;
+  float* st32 = nullptr;
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
+};
+
+struct Alloc {
+  std::vector<void*> ptrs;
+  template <typename P>
+  mpcg_status get(P** p, size_t count, cudaStream_t s) {
+    void* q = nullptr;
+    const size_t bytes = count * sizeof(P);
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+      set_err("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+      return MPCG_ERR_OOM;
+    }
+    ptrs.push_back(q);
+    e = cudaMemsetAsync(q, 0, bytes ? bytes : 16, s);
+    if (e != cudaSuccess) {
+      set_err("cudaMemsetAsync failed: %s", cudaGetErrorString(e));
+      return MPCG_ERR_CUDA;
+    }
+    *p = (P*)q;
+    return MPCG_OK;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+template <typename T>
+struct Solver {
+  bool built = false;
+  int C = 0, m = 0, hist_cap = 0;
+  Alloc mem, hist_mem;
+  T* rlev[kMaxLevels] = {};
+  T* zc[kMaxLevels] = {};
+  T* tmp[kMaxLevels] = {};
+  T* tmp2[kMaxLevels] = {};
+  T *x = nullptr, *r = nullptr, *b = nullptr, *Z = nullptr, *AZ = nullptr;
+  Window<T> win = {};
+  DevState* state = nullptr;
+  double *part_res = nullptr, *part_zaz = nullptr, *part_W = nullptr, *part_G = nullptr, *part_r = nullptr;
+  double *res_hist = nullptr, *alpha_hist = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool use_graph = false;
+  void drop_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    use_graph = false;
+  }
+  void release() {
+    drop_graph();
+    mem.release();
+    hist_mem.release();
+    built = false;
+    hist_cap = 0;
+  }
+};
+
+}  // namespace
+
+struct mg_hierarchy {
+  int device = 0;
+  int dim = 2, levels = 1;
+  mpcg_options opt;
+  cudaStream_t stream = 0;
+  cudaStream_t cap_stream = nullptr;
+  Level lev[kMaxLevels];
+  double* L0 = nullptr;
+  int n0 = 0;
+  int* info = nullptr;
+  bool have32 = false;
+  Alloc mem;
+  Solver<double> s64;
+  Solver<float> s32;
+  double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *nrm = nullptr, *part_mix = nullptr;
+  double* stage = nullptr;   // 2 n doubles: staging for host b and x
+};
+
+namespace {
+
+template <typename T>
+const T* st_of(const Level& L);
+template <>
+const double* st_of<double>(const Level& L) { return L.st64; }
+template <>
+const float* st_of<float>(const Level& L) { return L.st32; }
+template <typename T>
+const T* dinv_of(const Level& L);
+template <>
+const double* dinv_of<double>(const Level& L) { return L.dinv64; }
+template <>
+const float* dinv_of<float>(const Level& L) { return L.dinv32; }
+
+template <typename T>
+mpcg_status build_solver(mg_hierarchy* h, Solver<T>& S) {
+  if (S.built) return MPCG_OK;
+  cudaStream_t s = h->stream;
+  const int J = h->levels - 1;
+  const GridDesc& gf = h->lev[J].g;
+  S.C = h->levels;
+  S.m = h->opt.m;
+  const int C = S.C;
+  CKS(S.mem.get(&S.x, gf.len, s));
+  CKS(S.mem.get(&S.r, gf.len, s));
+  CKS(S.mem.get(&S.b, gf.len, s));
+  CKS(S.mem.get(&S.Z, (size_t)C * gf.len, s));
+  CKS(S.mem.get(&S.AZ, (size_t)C * gf.len, s));
+  for (int j = 0; j < S.m; ++j) {
+    CKS(S.mem.get(&S.win.P[j], (size_t)C * gf.len, s));
+    CKS(S.mem.get(&S.win.AP[j], (size_t)C * gf.len, s));
+  }
+  for (int j = 0; j <= J; ++j) {
+    const GridDesc& g = h->lev[j].g;
+    if (j < J) {
+      CKS(S.mem.get(&S.rlev[j], g.len, s));
+      CKS(S.mem.get(&S.zc[j], (size_t)(j + 1) * g.len, s));
+    }
+    if (h->opt.nu > 2) {
+      CKS(S.mem.get(&S.tmp[j], g.len, s));
+      CKS(S.mem.get(&S.tmp2[j], g.len, s));
+    }
+  }
+  CKS(S.mem.get(&S.state, 1, s));
+  CKS(S.mem.get(&S.part_res, 2 * kRedBlocks, s));
+  CKS(S.mem.get(&S.part_zaz, (size_t)C * kRedBlocks, s));
+  CKS(S.mem.get(&S.part_W, (size_t)S.m * C * C * kGramBlocks, s));
+  CKS(S.mem.get(&S.part_G, (size_t)(C * (C + 1) / 2 + C) * kRedBlocks, s));
+  CKS(S.mem.get(&S.part_r, kRedBlocks, s));
+  S.built = true;
+  return MPCG_OK;
+}
+
+template <typename T>
+mpcg_status ensure_hist(mg_hierarchy* h, Solver<T>& S, int maxit) {
+  if (S.hist_cap >= maxit + 1) return MPCG_OK;
+  S.drop_graph();
+  S.hist_mem.release();
+  int cap = 64;
+  while (cap < maxit + 1) cap *= 2;
+  CKS(S.hist_mem.get(&S.res_hist, cap, h->stream));
+  CKS(S.hist_mem.get(&S.alpha_hist, (size_t)cap * S.C, h->stream));
+  S.hist_cap = cap;
+  return MPCG_OK;
+}
+
+// The additive MG block Z = MG(r) (Section 2.2): restrict r to every grid,
+// solve on the coarsest, smooth on the others, prolong every correction to
+// the fine grid.  Column l of Z is the correction of grid l.
+template <typename T>
+void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState* state, cudaStream_t s) {
+  const int J = h->levels - 1;
+  if (J == 0) {
+    launch_coarse_solve<T>(h->lev[0].g, h->L0, r, Z, state, s);
+    return;
+  }
+  const T* rj = r;
+  for (int j = J; j >= 1; --j) {
+    launch_restrict<T>(h->lev[j].g, h->lev[j - 1].g, rj, S.rlev[j - 1], state, s);
+    rj = S.rlev[j - 1];
+  }
+  launch_coarse_solve<T>(h->lev[0].g, h->L0, S.rlev[0], S.zc[0], state, s);
+  const int nu = h->opt.nu;
+  for (int j = 1; j <= J; ++j) {
+    const Level& L = h->lev[j];
+    T* dst = j == J ? Z : S.zc[j];
+    launch_prolong<T>(h->lev[j - 1].g, L.g, S.zc[j - 1], dst, j, state, s);
+    const T* rr = j == J ? r : S.rlev[j];
+    T* out = dst + (size_t)j * L.g.len;
+    const T* st = st_of<T>(L);
+    const T* di = dinv_of<T>(L);
+    if (nu == 1) {
+      launch_jacobi<T>(L.g, st, di, rr, nullptr, out, 0, state, s);
+    } else if (nu == 2) {
+      launch_jacobi<T>(L.g, st, di, rr, nullptr, out, 1, state, s);
+    } else {
+      T* a = S.tmp[j];
+      T* b = S.tmp2[j];
+      launch_jacobi<T>(L.g, st, di, rr, nullptr, a, 1, state, s);
+      for (int k = 3; k <= nu; ++k) {
+        T* o = k == nu ? out : b;
+        launch_jacobi<T>(L.g, st, di, rr, a, o, 2, state, s);
+        T* t = a;
+        a = b;
+        b = t;
+      }
+    }
+  }
+}
+
+template <typename T>
+void enqueue_prologue(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond, int use_cond,
+                      cudaStream_t s) {
+  const Level& L = h->lev[h->levels - 1];
+  launch_residual<T>(L.g, st_of<T>(L), S.b, S.x, S.r, S.part_res, s);
+  launch_init(S.state, S.part_res, kRedBlocks, S.res_hist, cond, use_cond, s);
+}
+
+template <typename T>
+void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
+  const Level& L = h->lev[h->levels - 1];
+  const int C = S.C;
+  enqueue_mg<T>(h, S, S.r, S.Z, S.state, s);
+  launch_spmm<T>(L.g, st_of<T>(L), S.Z, S.AZ, C, S.part_zaz, S.state, s);
+  launch_gram_window<T>(L.g, S.win, S.Z, C, S.part_W, S.state, s);
+  launch_small_beta(S.state, S.part_W, C, s);
+  launch_orth_update<T>(L.g, S.win, S.Z, S.AZ, S.r, C, S.part_G, S.state, s);
+  launch_small_alpha(S.state, S.part_G, S.part_zaz, C, S.alpha_hist, s);
+  launch_update_xr<T>(L.g, S.win, S.x, S.r, C, S.part_r, S.state, s);
+  launch_check(S.state, S.part_r, kRedBlocks, S.res_hist, cond, use_cond, s);
+}
+
+// Capture prologue + while(cond){body} as one graph.  On any failure the
+// solver falls back to direct launches with a host-side convergence test.
+template <typename T>
+void build_graph(mg_hierarchy* h, Solver<T>& S) {
+  S.drop_graph();
+  cudaGraph_t graph = nullptr;
+  cudaGraphConditionalHandle cond;
+  cudaStream_t cs = h->cap_stream;
+  bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
+  ok = ok && cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  ok = ok && cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                 cudaSuccess;
+  if (!ok) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return;
+  }
+  enqueue_prologue<T>(h, S, cond, 1, cs);
+  cudaStreamCaptureStatus st;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  ok = cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &deps, nullptr, &ndeps) == cudaSuccess;
+  ok = ok && cudaGraphAddNode(&cnode, graph, deps, nullptr, ndeps, &cp) == cudaSuccess;
+  ok = ok && cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                 cudaSuccess;
+  cudaGraph_t g2 = nullptr;
+  const bool ended = cudaStreamEndCapture(cs, &g2) == cudaSuccess;
+  ok = ok && ended;
+  if (ok) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+         cudaSuccess;
+    if (ok) {
+      enqueue_body<T>(h, S, cond, 1, cs);
+      cudaGraph_t b2 = nullptr;
+      ok = cudaStreamEndCapture(cs, &b2) == cudaSuccess;
+    }
+  }
+  cudaGraphExec_t exec = nullptr;
+  ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+  if (!ok) {
+    cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return;
+  }
+  S.graph = graph;
+  S.exec = exec;
+  S.use_graph = true;
+}
+
+// Run prologue + loop for solver S (buffers b, x already filled).
+template <typename T>
+mpcg_status run_solver(mg_hierarchy* h, Solver<T>& S, DevState* host_state) {
+  cudaStream_t s = h->stream;
+  if (!S.use_graph) build_graph<T>(h, S);
+  if (S.use_graph) {
+    CK(cudaGraphLaunch(S.exec, s));
+  } else {
+    // direct launches; the host reads the done flag after every iteration
+    cudaGraphConditionalHandle dummy = 0;
+    enqueue_prologue<T>(h, S, dummy, 0, s);
+    for (;;) {
+      int done = 0;
+      CK(cudaMemcpyAsync(&done, &S.state->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (done) break;
+      enqueue_body<T>(h, S, dummy, 0, s);
+    }
+  }
+  CK(cudaMemcpyAsync(host_state, S.state, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  return MPCG_OK;
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+mpcg_status build_f32(mg_hierarchy* h) {
+  if (h->have32) return MPCG_OK;
+  cudaStream_t s = h->stream;
+  const int S = h->dim == 3 ? 27 : 9;
+  for (int j = 0; j < h->levels; ++j) {
+    Level& L = h->lev[j];
+    CKS(h->mem.get(&L.st32, (size_t)S * L.g.len, s));
+    CKS(h->mem.get(&L.dinv32, L.g.len, s));
+    launch_convert_f32(L.st64, L.st32, (long long)S * L.g.len, s);
+    launch_convert_f32(L.dinv64, L.dinv32, L.g.len, s);
+  }
+  const GridDesc& gf = h->lev[h->levels - 1].g;
+  CKS(h->mem.get(&h->b64, gf.len, s));
+  CKS(h->mem.get(&h->x64, gf.len, s));
+  CKS(h->mem.get(&h->r64, gf.len, s));
+  CKS(h->mem.get(&h->nrm, 4, s));
+  CKS(h->mem.get(&h->part_mix, 2 * kRedBlocks, s));
+  CK(cudaGetLastError());
+  h->have32 = true;
+  return MPCG_OK;
+}
+
+mpcg_status check_h(const mg_hierarchy* h) {
+  if (!h) {
+    set_err("hierarchy is NULL");
+    return MPCG_ERR_ARG;
+  }
+  return MPCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mpcg_last_error(void) { return g_err.c_str(); }
+
+mpcg_status mpcg_default_options(mpcg_options* opt) {
+  if (!opt) {
+    set_err("options pointer is NULL");
+    return MPCG_ERR_ARG;
+  }
+  opt->m = 5;
+  opt->nu = 2;
+  opt->omega = 2.0 / 3.0;
+  opt->pinv_tau = 1e-12;
+  opt->drop_delta = 1e-10;
+  opt->precision = MPCG_FP64;
+  opt->inner_rtol = 1e-4;
+  opt->inner_pinv_tau = 1e-6;
+  opt->inner_drop_delta = 1e-5;
+  opt->max_outer = 20;
+  opt->stream = nullptr;
+  return MPCG_OK;
+}
+
+int mg_num_levels(const mg_hierarchy* h) { return h ? h->levels : -1; }
+int mg_num_columns(const mg_hierarchy* h) { return h ? h->levels : -1; }
+long long mg_level_size(const mg_hierarchy* h, int level) {
+  if (!h || level < 0 || level >= h->levels) return -1;
+  return h->lev[level].g.n;
+}
+
+void mg_hierarchy_destroy(mg_hierarchy* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  h->s64.release();
+  h->s32.release();
+  h->mem.release();
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+mpcg_status mg_hierarchy_setup(const mg_operator* A, int levels, const mpcg_options* opt_in, mg_hierarchy** out) {
+  g_err.clear();
+  if (!out) {
+    set_err("out pointer is NULL");
+    return MPCG_ERR_ARG;
+  }
+  *out = nullptr;
+  if (!A || !A->values_dev) {
+    set_err("operator or its values pointer is NULL");
+    return MPCG_ERR_ARG;
+  }
+  if (A->format != MPCG_FORMAT_STENCIL) {
+    set_err("unsupported operator format %d", A->format);
+    return MPCG_ERR_ARG;
+  }
+  if (A->dim != 2 && A->dim != 3) {
+    set_err("dim must be 2 or 3 (got %d)", A->dim);
+    return MPCG_ERR_ARG;
+  }
+  const int q = A->nodes - 1;
+  if (q < 2 || (q & (q - 1)) != 0 || q > (1 << 15)) {
+    set_err("nodes - 1 must be a power of two in [2, 32768] (nodes = %d)", A->nodes);
+    return MPCG_ERR_ARG;
+  }
+  int k = 0;
+  while ((1 << k) < q) ++k;
+  if (levels < 1 || levels > k || levels > kMaxLevels || levels > MPCG_MAX_COLS) {
+    set_err("levels = %d invalid for %d nodes per side (1..%d)", levels, A->nodes,
+            k < MPCG_MAX_COLS ? k : MPCG_MAX_COLS);
+    return MPCG_ERR_ARG;
+  }
+  mpcg_options opt;
+  if (opt_in) opt = *opt_in;
+  else mpcg_default_options(&opt);
+  if (opt.m < 1 || opt.m > MPCG_MAX_WINDOW || opt.nu < 1 || !(opt.omega > 0.0) || opt.pinv_tau < 0.0 ||
+      opt.drop_delta < 0.0 || (opt.precision != MPCG_FP64 && opt.precision != MPCG_MIXED) || opt.max_outer < 1) {
+    set_err("invalid options (m in 1..%d, nu >= 1, omega > 0, tau/delta >= 0, max_outer >= 1)", MPCG_MAX_WINDOW);
+    return MPCG_ERR_ARG;
+  }
+  const int n1c = (q >> (levels - 1)) - 1;
+  long long n0 = 1;
+  for (int d = 0; d < A->dim; ++d) n0 *= n1c;
+  if (n0 > 1024) {
+    set_err("coarsest grid has %lld unknowns (> 1024); use more levels", n0);
+    return MPCG_ERR_ARG;
+  }
+  mg_hierarchy* h = new mg_hierarchy();
+  cudaGetDevice(&h->device);
+  h->dim = A->dim;
+  h->levels = levels;
+  h->opt = opt;
+  h->stream = (cudaStream_t)opt.stream;
+  h->n0 = (int)n0;
+  mpcg_status st = MPCG_OK;
+  auto fail = [&](mpcg_status s) {
+    mg_hierarchy_destroy(h);
+    return s;
+  };
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    set_err("cudaStreamCreateWithFlags failed");
+    return fail(MPCG_ERR_CUDA);
+  }
+  const int S = A->dim == 3 ? 27 : 9;
+  cudaStream_t s = h->stream;
+  for (int j = 0; j < levels; ++j) {
+    h->lev[j].g = make_grid(A->dim, (q >> (levels - 1 - j)) - 1);
+    if ((st = h->mem.get(&h->lev[j].st64, (size_t)S * h->lev[j].g.len, s)) != MPCG_OK) return fail(st);
+    if ((st = h->mem.get(&h->lev[j].dinv64, h->lev[j].g.len, s)) != MPCG_OK) return fail(st);
+  }
+  const int J = levels - 1;
+  // fine stencil: compact [S][n] -> padded [S][len]
+  launch_pack<double, double>(h->lev[J].g, A->values_dev, h->lev[J].g.n, h->lev[J].st64, S, s);
+  for (int j = J; j >= 1; --j) launch_galerkin(h->lev[j].g, h->lev[j - 1].g, h->lev[j].st64, h->lev[j - 1].st64, s);
+  for (int j = 0; j < levels; ++j) launch_dinv<double>(h->lev[j].g, h->lev[j].st64, h->lev[j].dinv64, opt.omega, s);
+  if ((st = h->mem.get(&h->L0, (size_t)n0 * n0, s)) != MPCG_OK) return fail(st);
+  if ((st = h->mem.get(&h->info, 4, s)) != MPCG_OK) return fail(st);
+  launch_dense_from_stencil(h->lev[0].g, h->lev[0].st64, h->L0, s);
+  launch_cholesky(h->L0, (int)n0, h->info, s);
+  int info = 0;
+  if (cudaMemcpyAsync(&info, h->info, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    set_err("setup kernels failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return fail(MPCG_ERR_CUDA);
+  }
+  if (info != 0) {
+    set_err("coarsest operator is not positive definite (Cholesky pivot %d)", info);
+    return fail(MPCG_ERR_NOT_SPD);
+  }
+  if ((st = build_solver<double>(h, h->s64)) != MPCG_OK) return fail(st);
+  if (opt.precision == MPCG_MIXED) {
+    if ((st = build_f32(h)) != MPCG_OK) return fail(st);
+    if ((st = build_solver<float>(h, h->s32)) != MPCG_OK) return fail(st);
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    set_err("setup failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return fail(MPCG_ERR_CUDA);
+  }
+  *out = h;
+  return MPCG_OK;
+}
+
+static mpcg_status solve_fp64(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, int* iters_out,
+                              double* res_hist, double* alpha_hist) {
+  Solver<double>& S = h->s64;
+  cudaStream_t s = h->stream;
+  const GridDesc& gf = h->lev[h->levels - 1].g;
+  CKS(ensure_hist(h, S, maxit));
+  launch_pack<double, double>(gf, b, gf.n, S.b, 1, s);
+  launch_pack<double, double>(gf, x, gf.n, S.x, 1, s);
+  launch_set_params(S.state, rtol, maxit, S.m, S.C, h->opt.drop_delta, h->opt.pinv_tau, s);
+  DevState hs;
+  CKS(run_solver<double>(h, S, &hs));
+  launch_unpack<double, double>(gf, S.x, x, gf.n, 1, s);
+  if (res_hist) CK(cudaMemcpyAsync(res_hist, S.res_hist, sizeof(double) * (hs.k + 1), cudaMemcpyDeviceToHost, s));
+  if (alpha_hist && hs.k > 0)
+    CK(cudaMemcpyAsync(alpha_hist, S.alpha_hist, sizeof(double) * hs.k * S.C, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (iters_out) *iters_out = hs.k;
+  if (hs.done == 3) {
+    set_err("breakdown at iteration %d (non-finite value or every column dropped)", hs.k);
+    return MPCG_ERR_BREAKDOWN;
+  }
+  return hs.done == 1 ? MPCG_OK : MPCG_NOT_CONVERGED;
+}
+
+static mpcg_status solve_mixed(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, int* iters_out,
+                               double* res_hist) {
+  CKS(build_f32(h));
+  CKS(build_solver<float>(h, h->s32));
+  Solver<float>& S = h->s32;
+  cudaStream_t s = h->stream;
+  const Level& L = h->lev[h->levels - 1];
+  const GridDesc& gf = L.g;
+  CKS(ensure_hist(h, S, maxit));
+  launch_pack<double, double>(gf, b, gf.n, h->b64, 1, s);
+  launch_pack<double, double>(gf, x, gf.n, h->x64, 1, s);
+  int total = 0, nhist = 0;
+  mpcg_status result = MPCG_NOT_CONVERGED;
+  std::vector<double> inner(maxit + 1);
+  for (int outer = 0; outer <= h->opt.max_outer; ++outer) {
+    launch_residual<double>(gf, L.st64, h->b64, h->x64, h->r64, h->part_mix, s);
+    launch_sum_partials(h->part_mix, 2, kRedBlocks, h->nrm, s);
+    double nrm[2];
+    CK(cudaMemcpyAsync(nrm, h->nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double rn = sqrt(nrm[0]), bn = sqrt(nrm[1]);
+    if (!isfinite(rn)) {
+      set_err("non-finite residual in refinement step %d", outer);
+      result = MPCG_ERR_BREAKDOWN;
+      break;
+    }
+    if (outer == 0 && res_hist) res_hist[nhist++] = bn > 0 ? rn / bn : 0.0;
+    if (bn == 0.0 || rn <= rtol * bn) {
+      result = MPCG_OK;
+      break;
+    }
+    if (total >= maxit || outer == h->opt.max_outer) break;
+    launch_scale_to_f32(gf, h->r64, h->nrm, S.b, s);
+    CK(cudaMemsetAsync(S.x, 0, sizeof(float) * gf.len, s));
+    launch_set_params(S.state, h->opt.inner_rtol, maxit - total, S.m, S.C, h->opt.inner_drop_delta,
+                      h->opt.inner_pinv_tau, s);
+    DevState hs;
+    CKS(run_solver<float>(h, S, &hs));
+    if (res_hist && hs.k > 0) {
+      CK(cudaMemcpyAsync(inner.data(), S.res_hist, sizeof(double) * (hs.k + 1), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int i = 1; i <= hs.k && nhist <= maxit; ++i) res_hist[nhist++] = inner[i] * rn / bn;
+    }
+    total += hs.k;
+    if (hs.done == 3) {
+      set_err("breakdown in the FP32 inner solve of refinement step %d", outer);
+      result = MPCG_ERR_BREAKDOWN;
+      break;
+    }
+    launch_axpy_mixed(gf, h->x64, S.x, h->nrm, s);
+    if (hs.k == 0) break;
+  }
+  launch_unpack<double, double>(gf, h->x64, x, gf.n, 1, s);
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  if (iters_out) *iters_out = total;
+  return result;
+}
+
+mpcg_status mpcg_solve(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, int* iters_out,
+                       double* res_hist, double* alpha_hist) {
+  g_err.clear();
+  CKS(check_h(h));
+  if (!b || !x) {
+    set_err("b and x must not be NULL");
+    return MPCG_ERR_ARG;
+  }
+  if (maxit < 0 || !(rtol >= 0.0)) {
+    set_err("maxit must be >= 0 and rtol >= 0");
+    return MPCG_ERR_ARG;
+  }
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = h->stream;
+  const GridDesc& gf = h->lev[h->levels - 1].g;
+  const size_t nb = sizeof(double) * gf.n;
+  const bool bdev = is_device_pointer(b), xdev = is_device_pointer(x);
+  const double* bd = b;
+  double* xd = x;
+  if (!bdev || !xdev) {
+    if (!h->stage) CKS(h->mem.get(&h->stage, 2 * (size_t)gf.n, s));
+    if (!bdev) {
+      CK(cudaMemcpyAsync(h->stage, b, nb, cudaMemcpyHostToDevice, s));
+      bd = h->stage;
+    }
+    if (!xdev) {
+      CK(cudaMemcpyAsync(h->stage + gf.n, x, nb, cudaMemcpyHostToDevice, s));
+      xd = h->stage + gf.n;
+    }
+  }
+  mpcg_status st = h->opt.precision == MPCG_MIXED
+                       ? solve_mixed(h, bd, xd, rtol, maxit, iters_out, res_hist)
+                       : solve_fp64(h, bd, xd, rtol, maxit, iters_out, res_hist, alpha_hist);
+  if (!xdev && (st >= 0 || st == MPCG_ERR_BREAKDOWN)) {
+    CK(cudaMemcpyAsync(x, xd, nb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return st;
+}
+
+mpcg_status mg_apply_operator(mg_hierarchy* h, int level, const double* X, double* Y, int ncols) {
+  g_err.clear();
+  CKS(check_h(h));
+  if (level < 0 || level >= h->levels || ncols < 1 || !X || !Y) {
+    set_err("bad level, column count or pointer");
+    return MPCG_ERR_ARG;
+  }
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = h->stream;
+  const Level& L = h->lev[level];
+  double *xp = nullptr, *yp = nullptr;
+  const int chunk = ncols < kMaxCols ? ncols : kMaxCols;
+  CK(cudaMalloc(&xp, sizeof(double) * chunk * L.g.len));
+  CK(cudaMalloc(&yp, sizeof(double) * chunk * L.g.len));
+  cudaMemsetAsync(xp, 0, sizeof(double) * chunk * L.g.len, s);
+  for (int c0 = 0; c0 < ncols; c0 += chunk) {
+    const int nc = ncols - c0 < chunk ? ncols - c0 : chunk;
+    launch_pack<double, double>(L.g, X + (size_t)c0 * L.g.n, L.g.n, xp, nc, s);
+    launch_spmm<double>(L.g, L.st64, xp, yp, nc, nullptr, nullptr, s);
+    launch_unpack<double, double>(L.g, yp, Y + (size_t)c0 * L.g.n, L.g.n, nc, s);
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(xp);
+  cudaFree(yp);
+  CK(e);
+  CK(cudaGetLastError());
+  return MPCG_OK;
+}
+
+mpcg_status mg_corrections(mg_hierarchy* h, const double* r, double* Z) {
+  g_err.clear();
+  CKS(check_h(h));
+  if (!r || !Z) {
+    set_err("NULL pointer");
+    return MPCG_ERR_ARG;
+  }
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = h->stream;
+  Solver<double>& S = h->s64;
+  const GridDesc& gf = h->lev[h->levels - 1].g;
+  launch_pack<double, double>(gf, r, gf.n, S.r, 1, s);
+  enqueue_mg<double>(h, S, S.r, S.Z, nullptr, s);
+  launch_unpack<double, double>(gf, S.Z, Z, gf.n, h->levels, s);
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  return MPCG_OK;
+}
+
+mpcg_status mg_get_operator(mg_hierarchy* h, int level, double* planes) {
+  g_err.clear();
+  CKS(check_h(h));
+  if (level < 0 || level >= h->levels || !planes) {
+    set_err("bad level or pointer");
+    return MPCG_ERR_ARG;
+  }
+  CK(cudaSetDevice(h->device));
+  const Level& L = h->lev[level];
+  const int S = h->dim == 3 ? 27 : 9;
+  launch_unpack<double, double>(L.g, L.st64, planes, L.g.n, S, h->stream);
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  return MPCG_OK;
+}
+
+}  // extern "C"

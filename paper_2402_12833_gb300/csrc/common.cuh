@@ -1,0 +1,89 @@
+// Internal definitions shared by the CUDA translation units of libmpcg.
+//
+// Padded grid layout
+// ------------------
+// Grid j has n1 = 2^k - 1 interior nodes per side.  Every vector (and every
+// stencil plane) of that grid is stored with pitch p = n1 + 1 = 2^k along
+// each axis: element (x, y[, z]) lives at  G + x + p*y [+ p*p*z]  for
+// 0 <= x, y, z < p.  Coordinates equal to p-1 are pad entries that are always
+// zero; because the pitch is exactly n1 + 1, the pad of row y-1 sits at the
+// address of (x = -1, y), the pad row of plane z-1 at (y = -1, z), and so on,
+// so one pad layer serves as the zero Dirichlet ghost on both sides of every
+// axis.  A guard of G = p*p + p + 1 (3D; p + 1 in 2D) zero elements in front
+// makes (-1,-1,-1) addressable.  Stencils therefore need no boundary tests,
+// interpolation reads zero parents outside the grid, and sums over a whole
+// padded array equal sums over the interior unknowns.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mpcg.h"
+
+namespace mpcg {
+
+constexpr int kMaxCols = MPCG_MAX_COLS;
+constexpr int kMaxWindow = MPCG_MAX_WINDOW;
+constexpr int kMaxLevels = 12;
+constexpr int kBlock = 256;
+
+struct GridDesc {
+  int dim;        // 2 or 3
+  int n1;         // interior nodes per side
+  int lp;         // log2(pitch)
+  int p;          // pitch = n1 + 1
+  long long G;    // guard elements before the first entry
+  long long npts; // p^dim (entries of the padded box)
+  long long len;  // G + npts (allocated elements per vector)
+  long long n;    // interior unknowns n1^dim
+};
+
+inline GridDesc make_grid(int dim, int n1) {
+  GridDesc g;
+  g.dim = dim;
+  g.n1 = n1;
+  g.p = n1 + 1;
+  int lp = 0;
+  while ((1 << lp) < g.p) ++lp;
+  g.lp = lp;
+  long long p = g.p;
+  g.G = dim == 3 ? p * p + p + 1 : p + 1;
+  g.npts = dim == 3 ? p * p * p : p * p;
+  g.len = g.G + g.npts;
+  g.n = dim == 3 ? (long long)n1 * n1 * n1 : (long long)n1 * n1;
+  return g;
+}
+
+// Linear offset of a stencil neighbour.
+__host__ __device__ inline long long nb_offset(int p, int dx, int dy, int dz) {
+  return (long long)dx + (long long)dy * p + (long long)dz * p * p;
+}
+
+// Solver state kept in device memory so that a captured iteration can run
+// without host involvement.
+struct DevState {
+  int k;          // x updates done
+  int count;      // blocks in the window
+  int newest;     // ring slot of the newest block
+  int done;       // 0 running, 1 converged, 2 maxit, 3 breakdown
+  int maxit;
+  int ncols;      // active column count C of this solver
+  int m;          // window length
+  int dropped_total;
+  double rtol;
+  double bnorm;
+  double rnorm;
+  double delta;
+  double tau;
+  double alpha[kMaxCols];
+  double beta[kMaxWindow][kMaxCols][kMaxCols];
+  double gpinv[kMaxWindow][kMaxCols][kMaxCols];
+};
+
+template <typename T>
+struct Window {
+  T* P[kMaxWindow];
+  T* AP[kMaxWindow];
+};
+
+}  // namespace mpcg

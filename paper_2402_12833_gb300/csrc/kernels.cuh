@@ -1,0 +1,99 @@
+// Host-side launchers of the libmpcg kernels (internal).
+#pragma once
+
+#include "common.cuh"
+
+namespace mpcg {
+
+// Maximum number of thread blocks of the grid-stride reduction kernels; the
+// partial-sum buffers are sized for it.
+constexpr int kRedBlocks = 1216;     // 152 SMs x 8
+constexpr int kGramBlocks = 304;     // 152 SMs x 2
+
+inline int grid_for(long long work, int cap) {
+  long long b = (work + kBlock - 1) / kBlock;
+  if (b < 1) b = 1;
+  return (int)(b < cap ? b : cap);
+}
+
+// ---- stencil.cu ----------------------------------------------------------
+// compact interior <-> padded layout (ncols columns; compact leading dim ld)
+template <typename TI, typename TO>
+void launch_pack(const GridDesc& g, const TI* src, long long ld, TO* dst, int ncols, cudaStream_t s);
+template <typename TI, typename TO>
+void launch_unpack(const GridDesc& g, const TI* src, TO* dst, long long ld, int ncols, cudaStream_t s);
+
+// Y = A X over C columns; if zaz != nullptr also partials of X_b^T Y_b
+// (value-major, stride kRedBlocks).  `state` (may be null) gates on done.
+template <typename T>
+void launch_spmm(const GridDesc& g, const T* st, const T* X, T* Y, int C, double* zaz,
+                 const DevState* state, cudaStream_t s);
+// r = b - A x; partials [||r||^2, ||b||^2]
+template <typename T>
+void launch_residual(const GridDesc& g, const T* st, const T* b, const T* x, T* r, double* part,
+                     cudaStream_t s);
+// coarse = P^T fine
+template <typename T>
+void launch_restrict(const GridDesc& gf, const GridDesc& gc, const T* rf, T* rc,
+                     const DevState* state, cudaStream_t s);
+// damped Jacobi: mode 0: out = dinv r; mode 1: two sweeps from zero;
+// mode 2: out = sin + dinv (r - A sin)
+template <typename T>
+void launch_jacobi(const GridDesc& g, const T* st, const T* dinv, const T* r, const T* sin, T* out,
+                   int mode, const DevState* state, cudaStream_t s);
+// fine[c] = P coarse[c] for c < ncols (column stride: grid len)
+template <typename T>
+void launch_prolong(const GridDesc& gc, const GridDesc& gf, const T* coarse, T* fine, int ncols,
+                    const DevState* state, cudaStream_t s);
+// coarse stencil = P^T A P (FP64)
+void launch_galerkin(const GridDesc& gf, const GridDesc& gc, const double* stf, double* stc,
+                     cudaStream_t s);
+// dinv = omega / centre coefficient (0 at pads)
+template <typename T>
+void launch_dinv(const GridDesc& g, const double* st, T* dinv, double omega, cudaStream_t s);
+void launch_convert_f32(const double* src, float* dst, long long count, cudaStream_t s);
+
+// ---- block.cu --------------------------------------------------------------
+// W partials: rows jj*C+a (window block jj, newest first), cols b:
+//   sum_i AP_slot(jj)[a][i] * Z[b][i]
+template <typename T>
+void launch_gram_window(const GridDesc& g, Window<T> win, const T* Z, int C, double* part,
+                        const DevState* state, cudaStream_t s);
+// P_new = Z - sum P_j beta_j, AP_new = AZ - sum AP_j beta_j into the next
+// ring slot; partials of sym(P^T AP) (upper triangle) and P^T r.
+template <typename T>
+void launch_orth_update(const GridDesc& g, Window<T> win, const T* Z, const T* AZ, const T* r,
+                        int C, double* part, const DevState* state, cudaStream_t s);
+// x += P alpha, r -= AP alpha (newest block); partial of ||r||^2
+template <typename T>
+void launch_update_xr(const GridDesc& g, Window<T> win, T* x, T* r, int C, double* part,
+                      const DevState* state, cudaStream_t s);
+
+// ---- small.cu ------------------------------------------------------------
+void launch_init(DevState* st, const double* part_res, int nblk, double* res_hist,
+                 cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
+void launch_small_beta(DevState* st, const double* part_W, int C, cudaStream_t s);
+void launch_small_alpha(DevState* st, const double* part_G, const double* part_zaz, int C,
+                        double* alpha_hist, cudaStream_t s);
+void launch_check(DevState* st, const double* part_r, int nblk, double* res_hist,
+                  cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
+void launch_set_params(DevState* st, double rtol, int maxit, int m, int C, double delta, double tau,
+                       cudaStream_t s);
+// Cholesky of the dense coarsest matrix (in place, lower); info[0] = 0 or the
+// failing pivot + 1
+void launch_dense_from_stencil(const GridDesc& g, const double* st, double* dense, cudaStream_t s);
+void launch_cholesky(double* a, int n, int* info, cudaStream_t s);
+// out = A0^{-1} r via the Cholesky factor; r, out in padded layout of grid g
+template <typename T>
+void launch_coarse_solve(const GridDesc& g, const double* L, const T* r, T* out,
+                         const DevState* state, cudaStream_t s);
+// ||r||^2 style sum of partials (value-major) into out[nv]
+void launch_sum_partials(const double* part, int nv, int nblk, double* out, cudaStream_t s);
+// x64 += scale * d (padded, FP32 d); scale read from device
+void launch_axpy_mixed(const GridDesc& g, double* x, const float* d, const double* scale,
+                       cudaStream_t s);
+// b32 = r64 / ||r64|| from device norm-squared
+void launch_scale_to_f32(const GridDesc& g, const double* r, const double* nrm2, float* out,
+                         cudaStream_t s);
+
+}  // namespace mpcg

@@ -1,0 +1,194 @@
+"""Thin Python binding of libmpcg (argument marshalling only).
+
+The functions carry the names of the C entry points declared in
+``include/mpcg.h``; every computation runs in the CUDA library.  Device
+arrays are passed as raw pointers (``tensor.data_ptr()``); host arrays as
+numpy buffers.  A missing library raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libmpcg.so")
+
+MPCG_OK = 0
+MPCG_NOT_CONVERGED = 1
+MPCG_ERR_ARG = -1
+MPCG_ERR_CUDA = -2
+MPCG_ERR_NOT_SPD = -3
+MPCG_ERR_BREAKDOWN = -4
+MPCG_ERR_TIMEOUT = -5
+MPCG_ERR_OOM = -6
+MPCG_FORMAT_STENCIL = 0
+MPCG_FP64 = 0
+MPCG_MIXED = 1
+MPCG_MAX_COLS = 12
+MPCG_MAX_WINDOW = 16
+
+
+class MpcgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libmpcg status {status}: {msg}")
+        self.status = status
+
+
+class mg_operator(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nodes", C.c_int), ("format", C.c_int), ("values_dev", C.c_void_p)]
+
+
+class mpcg_options(C.Structure):
+    _fields_ = [("m", C.c_int), ("nu", C.c_int), ("omega", C.c_double), ("pinv_tau", C.c_double),
+                ("drop_delta", C.c_double), ("precision", C.c_int), ("inner_rtol", C.c_double),
+                ("inner_pinv_tau", C.c_double), ("inner_drop_delta", C.c_double), ("max_outer", C.c_int),
+                ("stream", C.c_void_p)]
+
+
+_lib = None
+
+# name -> (restype, argtypes); mirrors include/mpcg.h
+_SIGS = {
+    "mpcg_default_options": (C.c_int, [C.POINTER(mpcg_options)]),
+    "mg_hierarchy_setup": (C.c_int, [C.POINTER(mg_operator), C.c_int, C.POINTER(mpcg_options), C.POINTER(C.c_void_p)]),
+    "mpcg_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int),
+                             C.c_void_p, C.c_void_p]),
+    "mg_num_levels": (C.c_int, [C.c_void_p]),
+    "mg_num_columns": (C.c_int, [C.c_void_p]),
+    "mg_level_size": (C.c_longlong, [C.c_void_p, C.c_int]),
+    "mg_apply_operator": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    "mg_corrections": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mg_get_operator": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "mg_hierarchy_destroy": (None, [C.c_void_p]),
+    "mpcg_last_error": (C.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libmpcg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_2402_12833_gb300.build.build()")
+        lib = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def mpcg_last_error() -> str:
+    return load().mpcg_last_error().decode()
+
+
+def _check(status: int, allow=(MPCG_OK,)) -> int:
+    if status not in allow:
+        raise MpcgError(status, mpcg_last_error())
+    return status
+
+
+def mpcg_default_options(**overrides) -> mpcg_options:
+    o = mpcg_options()
+    _check(load().mpcg_default_options(C.byref(o)))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a) -> int:
+    """Address of a torch tensor or numpy array (contiguous float64)."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"] and not a.flags["F_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data
+    raise TypeError(type(a))
+
+
+def mg_hierarchy_setup(values_dev, dim: int, nodes: int, levels: int, options: mpcg_options | None = None) -> int:
+    """Return an opaque hierarchy handle for the fine stencil ``values_dev``
+    (device float64 array of shape (3**dim, n))."""
+    op = mg_operator(dim, nodes, MPCG_FORMAT_STENCIL, _ptr(values_dev))
+    h = C.c_void_p()
+    opt = options if options is not None else mpcg_default_options()
+    _check(load().mg_hierarchy_setup(C.byref(op), levels, C.byref(opt), C.byref(h)))
+    return h.value
+
+
+def mpcg_solve(h: int, b, x, rtol: float = 1e-8, maxit: int = 500, histories: bool = True,
+               ncols: int | None = None):
+    """Run the solver; returns (status, iterations, res_hist, alpha_hist).
+    ``b`` and ``x`` are device tensors or host numpy arrays of n doubles."""
+    it = C.c_int(0)
+    ncols = mg_num_columns(h) if ncols is None else ncols
+    rh = np.zeros(maxit + 1) if histories else None
+    ah = np.zeros(maxit * ncols) if histories else None
+    st = load().mpcg_solve(h, _ptr(b), _ptr(x), rtol, maxit, C.byref(it),
+                           rh.ctypes.data if histories else None, ah.ctypes.data if histories else None)
+    _check(st, allow=(MPCG_OK, MPCG_NOT_CONVERGED))
+    k = it.value
+    if histories:
+        return st, k, rh[: k + 1].copy(), ah[: k * ncols].reshape(k, ncols).copy()
+    return st, k, None, None
+
+
+def mg_num_levels(h: int) -> int:
+    return load().mg_num_levels(h)
+
+
+def mg_num_columns(h: int) -> int:
+    return load().mg_num_columns(h)
+
+
+def mg_level_size(h: int, level: int) -> int:
+    return load().mg_level_size(h, level)
+
+
+def mg_apply_operator(h: int, level: int, X_dev, Y_dev, ncols: int) -> None:
+    _check(load().mg_apply_operator(h, level, _ptr(X_dev), _ptr(Y_dev), ncols))
+
+
+def mg_corrections(h: int, r_dev, Z_dev) -> None:
+    _check(load().mg_corrections(h, _ptr(r_dev), _ptr(Z_dev)))
+
+
+def mg_get_operator(h: int, level: int, planes_dev) -> None:
+    _check(load().mg_get_operator(h, level, _ptr(planes_dev)))
+
+
+def mg_hierarchy_destroy(h: int) -> None:
+    if h:
+        load().mg_hierarchy_destroy(h)
+
+
+class Hierarchy:
+    """Owning wrapper of a hierarchy handle (torch tensors for device memory)."""
+
+    def __init__(self, stencil_dev, dim: int, nodes: int, levels: int, **options):
+        self.options = mpcg_default_options(**options)
+        self.dim, self.nodes, self.levels = dim, nodes, levels
+        self._keep = stencil_dev
+        self.h = mg_hierarchy_setup(stencil_dev, dim, nodes, levels, self.options)
+
+    def solve(self, b, x, rtol=1e-8, maxit=500, histories=True):
+        return mpcg_solve(self.h, b, x, rtol, maxit, histories)
+
+    def close(self):
+        if self.h:
+            mg_hierarchy_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

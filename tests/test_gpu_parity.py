@@ -1,0 +1,234 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP64 path): operators and single kernels agree to ~1e-13
+relative (different summation order only); full solves agree in iteration
+count to +-1 and in the solution to 1e-10 relative.  Mixed precision: the
+true FP64 residual reaches rtol and the error against the FP64 oracle
+solution is reported and bounded.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import mg as omg
+from oracle import mpcg as ompcg
+from oracle.operators import stencil_to_csr
+from paper_2402_12833_gb300 import problems as pb
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_12833_gb300 import build, mpcg
+    build.build()
+    mpcg.load()
+    return mpcg
+
+
+def _hier(M, prob, levels=None, **opts):
+    st = torch.from_numpy(np.ascontiguousarray(prob.stencil)).cuda()
+    return M.Hierarchy(st, prob.dim, prob.nodes, levels or prob.levels, **opts)
+
+
+def _oracle(prob, levels=None):
+    return omg.Hierarchy(prob.dim, prob.n1, prob.stencil, levels or prob.levels)
+
+
+PROBS = {
+    "poisson2d_65": lambda: pb.poisson_random(2, 65, 1),
+    "kappa2d_65": lambda: pb.diffusion_macro(2, 65, 3),
+    "kappa2d_33_normal": lambda: pb.diffusion_macro(2, 33, 11, rhs="normal", rhs_seed=5),
+    "poisson3d_17": lambda: pb.poisson_random(3, 17, 2),
+    "kappa3d_17": lambda: pb.diffusion_macro(3, 17, 4, rhs="normal", rhs_seed=6),
+}
+
+
+@pytest.mark.parametrize("name", ["kappa2d_65", "kappa3d_17"])
+def test_galerkin_operators_match_oracle(M, name):
+    prob = PROBS[name]()
+    H = _hier(M, prob)
+    O = _oracle(prob)
+    S = 3 ** prob.dim
+    for j in range(prob.levels):
+        n = M.mg_level_size(H.h, j)
+        planes = torch.zeros((S, n), dtype=torch.float64, device="cuda")
+        M.mg_get_operator(H.h, j, planes)
+        A = stencil_to_csr(prob.dim, O.n1[j], planes.cpu().numpy())
+        ref = O.A[j]
+        err = abs(A - ref).max()
+        assert err <= 1e-13 * abs(ref).max(), (j, err)
+
+
+@pytest.mark.parametrize("name", ["poisson2d_65", "kappa3d_17"])
+@pytest.mark.parametrize("ncols", [1, 5, 12, 13])
+def test_block_spmm_matches_oracle(M, name, ncols):
+    prob = PROBS[name]()
+    H = _hier(M, prob)
+    O = _oracle(prob)
+    for j in (0, prob.levels - 1):
+        n = O.A[j].shape[0]
+        X = pb.normal(100 + j, n * ncols).reshape(ncols, n)
+        Xd = torch.from_numpy(X).cuda()
+        Yd = torch.zeros_like(Xd)
+        M.mg_apply_operator(H.h, j, Xd, Yd, ncols)
+        ref = (O.A[j] @ X.T).T
+        scale = abs(O.A[j]).max() * np.abs(X).max()
+        assert np.abs(Yd.cpu().numpy() - ref).max() <= 1e-14 * scale * 27
+
+
+@pytest.mark.parametrize("name", ["poisson2d_65", "kappa2d_65", "poisson3d_17", "kappa3d_17"])
+def test_mg_columns_match_oracle(M, name):
+    prob = PROBS[name]()
+    H = _hier(M, prob)
+    O = _oracle(prob)
+    r = pb.normal(7, prob.n)
+    Zd = torch.zeros((prob.levels, prob.n), dtype=torch.float64, device="cuda")
+    M.mg_corrections(H.h, torch.from_numpy(r).cuda(), Zd)
+    Z = Zd.cpu().numpy().T
+    ref = O.mg_columns(r)
+    for l in range(prob.levels):
+        assert np.abs(Z[:, l] - ref[:, l]).max() <= 1e-12 * np.abs(ref[:, l]).max(), l
+
+
+def _solve_pair(M, prob, m=5, rtol=1e-8, maxit=800, levels=None):
+    H = _hier(M, prob, levels=levels, m=m)
+    O = _oracle(prob, levels)
+    b = torch.from_numpy(prob.b).cuda()
+    x = torch.zeros_like(b)
+    st, k, rh, ah = H.solve(b, x, rtol=rtol, maxit=maxit)
+    ref = ompcg.mpcg(O.A[-1], prob.b, O.mg_columns, m=m, rtol=rtol, maxit=maxit)
+    return st, k, x.cpu().numpy(), rh, ah, ref, O
+
+
+@pytest.mark.parametrize("name,m", [("poisson2d_65", 5), ("poisson2d_65", 1), ("kappa2d_65", 5),
+                                    ("kappa2d_33_normal", 1), ("kappa2d_33_normal", 10),
+                                    ("poisson3d_17", 5), ("kappa3d_17", 5), ("kappa3d_17", 2)])
+def test_solve_matches_oracle(M, name, m):
+    prob = PROBS[name]()
+    st, k, x, rh, ah, ref, O = _solve_pair(M, prob, m=m)
+    assert st == M.MPCG_OK
+    assert ref.converged
+    assert abs(k - ref.iters) <= 1, (k, ref.iters)
+    assert np.linalg.norm(x - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
+    # residual histories agree while they are far above round-off
+    kk = min(k, ref.iters, 6)
+    assert np.allclose(rh[:kk + 1], ref.res_hist[:kk + 1], rtol=1e-6)
+    # first alpha vector
+    assert np.allclose(ah[0], ref.alpha_hist[0], rtol=1e-8, atol=1e-12 * np.abs(ref.alpha_hist[0]).max())
+    # the true residual of the GPU solution
+    tr = np.linalg.norm(prob.b - O.A[-1] @ x) / np.linalg.norm(prob.b)
+    assert tr <= 1.01e-8
+
+
+def test_manufactured_rhs_converges_in_one_iteration(M):
+    prob = pb.poisson_manufactured_2d(65)
+    st, k, x, rh, ah, ref, O = _solve_pair(M, prob)
+    assert k == ref.iters == 1
+    assert np.abs(x - pb.manufactured_u(2, 65)).max() < 1e-3
+
+
+def test_single_grid_exact_solve(M):
+    prob = pb.poisson_random(2, 5, 3)
+    st, k, x, rh, ah, ref, O = _solve_pair(M, prob, rtol=1e-13)
+    assert k == 1 and ref.iters == 1
+    assert np.allclose(x, ref.x, rtol=1e-13, atol=1e-15)
+
+
+def test_two_levels_tiny_3d(M):
+    prob = pb.diffusion_macro(3, 9, 2, rhs="normal", rhs_seed=1)
+    st, k, x, rh, ah, ref, O = _solve_pair(M, prob, rtol=1e-12)
+    assert abs(k - ref.iters) <= 1
+    assert np.linalg.norm(x - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
+
+
+def test_nonzero_initial_guess_and_fewer_levels(M):
+    prob = pb.diffusion_macro(2, 65, 8, rhs="normal", rhs_seed=2)
+    levels = 3
+    H = _hier(M, prob, levels=levels)
+    O = _oracle(prob, levels)
+    x0 = pb.normal(33, prob.n)
+    x = torch.from_numpy(x0.copy()).cuda()
+    st, k, rh, ah = H.solve(torch.from_numpy(prob.b).cuda(), x, rtol=1e-9, maxit=600)
+    ref = ompcg.mpcg(O.A[-1], prob.b, O.mg_columns, x0=x0, rtol=1e-9, maxit=600)
+    assert abs(k - ref.iters) <= 1
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
+
+
+def test_host_buffers_give_the_device_result(M):
+    prob = PROBS["kappa2d_65"]()
+    H = _hier(M, prob)
+    xd = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    st, k, _, _ = H.solve(torch.from_numpy(prob.b).cuda(), xd, maxit=600)
+    xh = np.zeros(prob.n)
+    st2, k2, _, _ = H.solve(prob.b.copy(), xh, maxit=600)
+    assert k == k2
+    assert np.array_equal(xd.cpu().numpy(), xh)
+
+
+def test_repeated_solves_are_bitwise_identical(M):
+    prob = PROBS["kappa3d_17"]()
+    H = _hier(M, prob)
+    b = torch.from_numpy(prob.b).cuda()
+    outs = []
+    for _ in range(3):
+        x = torch.zeros_like(b)
+        H.solve(b, x)
+        outs.append(x.cpu().numpy())
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
+
+
+def test_not_converged_status(M):
+    prob = PROBS["kappa2d_65"]()
+    H = _hier(M, prob)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    st, k, rh, ah = H.solve(torch.from_numpy(prob.b).cuda(), x, maxit=3)
+    assert st == M.MPCG_NOT_CONVERGED and k == 3 and len(rh) == 4
+
+
+def test_zero_rhs_returns_immediately(M):
+    prob = PROBS["poisson2d_65"]()
+    H = _hier(M, prob)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    st, k, rh, ah = H.solve(torch.zeros_like(x), x)
+    assert st == M.MPCG_OK and k == 0 and torch.count_nonzero(x) == 0
+
+
+def test_not_spd_coarse_operator_is_reported(M):
+    prob = pb.poisson_random(2, 17, 1)
+    st = torch.from_numpy(-prob.stencil).cuda()
+    with pytest.raises(M.MpcgError) as e:
+        M.Hierarchy(st, 2, 17, prob.levels)
+    assert e.value.status == M.MPCG_ERR_NOT_SPD
+
+
+def test_bad_arguments_are_rejected(M):
+    prob = pb.poisson_random(2, 17, 1)
+    st = torch.from_numpy(prob.stencil).cuda()
+    with pytest.raises(M.MpcgError) as e:
+        M.Hierarchy(st, 2, 17, 5)           # 17 nodes allow at most 4 grids
+    assert e.value.status == M.MPCG_ERR_ARG
+    with pytest.raises(M.MpcgError):
+        M.Hierarchy(st, 2, 18, 2)
+    with pytest.raises(M.MpcgError):
+        M.Hierarchy(st, 2, 17, 2, m=0)
+
+
+@pytest.mark.parametrize("name", ["kappa2d_65", "poisson3d_17"])
+def test_mixed_precision_reaches_fp64_tolerance(M, name):
+    prob = PROBS[name]()
+    H = _hier(M, prob, precision=M.MPCG_MIXED)
+    O = _oracle(prob)
+    b = torch.from_numpy(prob.b).cuda()
+    x = torch.zeros_like(b)
+    st, k, rh, ah = H.solve(b, x, rtol=1e-8, maxit=2000)
+    assert st == M.MPCG_OK
+    xg = x.cpu().numpy()
+    tr = np.linalg.norm(prob.b - O.A[-1] @ xg) / np.linalg.norm(prob.b)
+    assert tr <= 1e-8
+    ref = ompcg.mpcg(O.A[-1], prob.b, O.mg_columns, rtol=1e-12, maxit=2000)
+    err = np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x)
+    assert err <= 1e-5, err
