@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark: additive-MG MPCG, DOFs/s to a 1e-8 relative residual.
+
+Workload (one "step" = one complete solve to rtol 1e-8): 3D Poisson, Q1
+hexahedral FE on the unit cube, 129^3 nodes (2,048,383 interior DOFs), zero
+Dirichlet data, N(0,1) right-hand side (seed 2 + rank), 6 nested grids
+(coarsest 5^3 nodes, Cholesky), damped Jacobi nu = 2, omega = 2/3, MPCG window
+m = 5.  The headline value is the mixed-precision form (FP32 stencil, smoothing,
+transfers and block updates; FP64 Gram reductions, pseudo-inverse, coarse
+Cholesky and iterative refinement on the true FP64 residual); the plain FP64
+form is measured in the same run and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank solves its own independent problem (weak scaling,
+no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NODES, DIM, RHS_SEED, M_WINDOW, RTOL, MAXIT = 129, 3, 2, 5, 1e-8, 1000
+WORKLOAD = (f"3D Poisson Q1 FE, unit cube, {NODES}^3 nodes ({(NODES - 2) ** 3:,} DOFs), N(0,1) RHS, "
+            f"6 grids (5^3 coarsest, Cholesky), damped Jacobi nu=2 w=2/3, MPCG m={M_WINDOW}, rtol {RTOL:g}")
+METRIC = "MPCG-AMG DOFs/s to 1e-8 rel. residual"
+
+
+def _rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- algorithmic bytes / flops
+def kernel_work(cls: str, n: int, C: int, cnt: int, w: int):
+    """Algorithmic HBM bytes and flops of one launch on the fine grid (per
+    interior DOF figures x n; cnt = blocks in the window at that launch)."""
+    S = 27
+    if cls == "orth_update":      # read Z, AZ, P_j, AP_j, r; write P, AP; sym Gram + P^T r
+        return (2 * cnt * C + 4 * C + 1) * w * n, 2 * (2 * cnt * C * C + C * (C + 1) + C) * n
+    if cls == "gram_window":      # read AP_j, Z
+        return (cnt + 1) * C * w * n, 2 * cnt * C * C * n
+    if cls == "spmm":             # read stencil, Z; write AZ (+ Z^T AZ)
+        return (S + 2 * C) * w * n, 2 * (S * C + C) * n
+    if cls == "update_xr":        # read P, AP, x, r; write x, r
+        return (2 * C + 4) * w * n, 2 * (2 * C + 1) * n
+    return None, None
+
+
+def roofline(trace, n, C, m, w, peaks, fp64_alu_peak_tflops):
+    """Dominant kernel class by total time; achieved = algorithmic bytes
+    (or flops) summed over its launches / summed CUDA-event durations."""
+    tot = {}
+    for cls, ms in trace:
+        tot[cls] = tot.get(cls, 0.0) + ms
+    dom = max(tot, key=tot.get)
+    cnt = 0
+    bytes_sum = flops_sum = 0.0
+    launches = 0
+    dur = 0.0
+    for cls, ms in trace:
+        if cls == "init":
+            cnt = 0
+        if cls == dom:
+            b, f = kernel_work(cls, n, C, cnt, w)
+            if b is not None:
+                bytes_sum += b
+                flops_sum += f
+            dur += ms
+            launches += 1
+        if cls == "small_alpha":
+            cnt = min(cnt + 1, m)
+    share = tot[dom] / sum(tot.values())
+    if bytes_sum == 0:
+        return dom, None, share, tot
+    if w == 8:   # FP64 arithmetic on GB300 runs far below the HBM roofline: ALU bound
+        ach = flops_sum / (dur * 1e-3) / 1e12
+        out = {"bound": "alu", "achieved": ach, "peak": fp64_alu_peak_tflops, "unit": "TFLOP/s",
+               "frac": ach / fp64_alu_peak_tflops, "traffic": None,
+               "hbm_GBps": bytes_sum / (dur * 1e-3) / 1e9}
+    else:
+        ach = bytes_sum / (dur * 1e-3) / 1e9
+        out = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+               "frac": ach / peaks["hbm_gbs"], "traffic": None}
+    out.update({"kernel": dom, "launches": launches, "avg_launch_us": dur / launches * 1e3,
+                "algorithmic_bytes_per_launch": bytes_sum / launches, "share_of_solve": share})
+    return dom, out, share, tot
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"], "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+# FP64 FMA issue rate of GB300: 2 per SM per clock (152 SMs, 2.07 GHz max) ->
+# 152 * 2 * 2 flop * 2.07e9 = 1.26 TFLOP/s.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+# ---------------------------------------------------------------------------- oracle (CPU) legs
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from paper_2402_12833_gb300 import problems as pb
+from oracle import mg as omg, mpcg as ompcg
+prob = pb.poisson_random({dim}, {nodes}, {seed})
+t0 = time.perf_counter()
+H = omg.Hierarchy(prob.dim, prob.n1, prob.stencil, prob.levels)
+t1 = time.perf_counter()
+times = []
+for rep in range({warmup} + {steps}):
+    ta = time.perf_counter()
+    res = ompcg.mpcg(H.A[-1], prob.b, H.mg_columns, m={m}, rtol={rtol}, maxit={maxit})
+    if rep >= {warmup}:
+        times.append(time.perf_counter() - ta)
+print(json.dumps({{"setup_s": t1 - t0, "solve_s": sum(times) / len(times), "iters": res.iters, "n": prob.n,
+                  "res": res.res_hist[-1], "steps": len(times)}}))
+"""
+
+
+def oracle_cmd(warmup: int, steps: int, seed: int = RHS_SEED):
+    """The FP64 oracle as it stands, single-threaded, in a fresh process:
+    hierarchy setup once, then warmup + steps full solves."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET.format(root=ROOT, dim=DIM, nodes=NODES, seed=seed, m=M_WINDOW, rtol=RTOL,
+                                 maxit=MAXIT, warmup=warmup, steps=steps)
+    return [sys.executable, "-c", code], env
+
+
+def bench_reference(args):
+    rank, world, _ = _rank()
+    if rank != 0:
+        return 0
+    # each step is one full oracle solve of the workload (~10-20 s on one core);
+    # a single untimed warm-up solve stands in for the W warm-up steps
+    cmd, env = oracle_cmd(1, args.steps)
+    out = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=3600)
+    if out.returncode != 0:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + out.stderr[-200:]}))
+        return 0
+    o = json.loads(out.stdout.strip().splitlines()[-1])
+    steps = [o]
+    t = o["solve_s"]
+    n = o["n"]
+    v = n / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DOFs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": v, "unit": "DOFs/s", "cores": 1, "kind": "oracle",
+                             "sample": f"full solve of the workload per step ({steps[0]['iters']} iterations; "
+                                       f"hierarchy setup {steps[0]['setup_s']:.1f} s excluded)"},
+            "e2e": {"value": v, "unit": "DOFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------- GPU leg
+def bench_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _rank()
+    # the CPU baseline runs in a fresh process started before any CUDA work
+    oracle_proc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cmd, env = oracle_cmd(0, 1)
+        oracle_proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2402_12833_gb300 import build as _build
+    from paper_2402_12833_gb300 import mpcg as M
+    from paper_2402_12833_gb300 import problems as pb
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    M.load()
+
+    prob = pb.poisson_random(DIM, NODES, RHS_SEED + rank)
+    n = prob.n
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    st = torch.from_numpy(prob.stencil).cuda()
+    ug = 0 if args.direct else 1
+    H = {"mixed": M.Hierarchy(st, DIM, NODES, prob.levels, m=M_WINDOW, precision=M.MPCG_MIXED, stream=sptr,
+                              use_graph=ug),
+         "fp64": M.Hierarchy(st, DIM, NODES, prob.levels, m=M_WINDOW, precision=M.MPCG_FP64, stream=sptr,
+                             use_graph=ug)}
+    b = torch.from_numpy(prob.b).cuda()
+    x = torch.zeros_like(b)
+    peaks = load_peaks()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    res = {}
+    clocks = None
+    keys = ("fp64", "mixed") if args.only is None else (args.only,)
+    for key in keys:
+        h = H[key]
+        for _ in range(args.warmup):
+            x.zero_()
+            h.solve(b, x, rtol=RTOL, maxit=MAXIT, histories=False)
+        barrier()
+        torch.cuda.synchronize()
+        if key == "mixed" and rank == 0:
+            clk = Clocks(local)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        iters = []
+        torch.cuda.nvtx.range_push("timed_step")
+        e0.record(stream)
+        for _ in range(args.steps):
+            x.zero_()
+            st_, k, _, _ = h.solve(b, x, rtol=RTOL, maxit=MAXIT, histories=False)
+            iters.append(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        barrier()
+        if key == "mixed" and rank == 0:
+            clocks = clk.stop()
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        launches = M.mg_last_launches(h.h)
+        # true FP64 residual of the last solution (one extra SpMV through the library)
+        Ax = torch.empty_like(b)
+        M.mg_apply_operator(h.h, prob.levels - 1, x, Ax, 1)
+        true_res = float(torch.linalg.norm(b - Ax) / torch.linalg.norm(b))
+        res[key] = {"ms_per_step": ms, "value": world * n / (ms * 1e-3), "iters": iters[-1],
+                    "launches_per_step": launches, "true_rel_residual": true_res,
+                    "x": x.detach().clone() if key == "fp64" else None}
+
+    if args.only is not None:
+        r = res[args.only]
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "only": args.only, "value": r["value"], "unit": "DOFs/s",
+                              "ms_per_step": r["ms_per_step"], "iterations": r["iters"],
+                              "true_rel_residual": r["true_rel_residual"], "launches_per_step": r["launches_per_step"],
+                              "clocks": clocks}))
+        if oracle_proc is not None:
+            oracle_proc.kill()
+        for h in H.values():
+            h.close()
+        return 0
+
+    # per-kernel durations from a live profiled solve (CUDA events on the solve stream)
+    prof = {}
+    for key, w in (("mixed", 4), ("fp64", 8)):
+        x.zero_()
+        _, k, classes, trace = M.mpcg_solve_profiled(H[key].h, b, x, RTOL, MAXIT)
+        dom, rl, share, tot = roofline(trace, n, prob.levels, M_WINDOW, w, peaks, FP64_PEAK_TFLOPS)
+        prof[key] = {"roofline": rl, "class_ms": {c: round(v, 4) for c, v in tot.items()}}
+    # mixed vs fp64 solution difference
+    x.zero_()
+    H["mixed"].solve(b, x, rtol=RTOL, maxit=MAXIT, histories=False)
+    mix_vs_fp64 = float(torch.linalg.norm(x - res["fp64"]["x"]) / torch.linalg.norm(res["fp64"]["x"]))
+
+    # end to end through the C ABI with pinned host buffers
+    bh = torch.from_numpy(prob.b).pin_memory().numpy()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
+    for _ in range(max(1, args.warmup // 2)):
+        xh[:] = 0.0
+        M.mpcg_solve(H["mixed"].h, bh, xh, RTOL, MAXIT, histories=False)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xh[:] = 0.0
+        M.mpcg_solve(H["mixed"].h, bh, xh, RTOL, MAXIT, histories=False)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+    barrier()
+
+    cpu = None
+    if oracle_proc is not None:
+        out, err = oracle_proc.communicate(timeout=1800)
+        if oracle_proc.returncode == 0:
+            o = json.loads(out.strip().splitlines()[-1])
+            cpu = {"value": o["n"] / o["solve_s"], "unit": "DOFs/s", "cores": 1, "kind": "oracle",
+                   "sample": f"one full FP64 solve of the same workload ({o['iters']} iterations, "
+                             f"{o['solve_s']:.1f} s; hierarchy setup {o['setup_s']:.1f} s excluded)",
+                   "iters": o["iters"]}
+        else:
+            cpu = {"value": None, "unit": "DOFs/s", "cores": 1, "kind": "oracle", "sample": "failed: " + err[-300:]}
+
+    if rank == 0:
+        mx = res["mixed"]
+        line = {
+            "metric": METRIC, "value": mx["value"], "unit": "DOFs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mx["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "mixed: FP32 bulk, FP64 Gram/pinv/Cholesky/refinement",
+                       "dofs_per_rank": n, "parallelism": f"{world} independent problems (one per GPU)",
+                       "l2": "working set ~1 GB per solve > 129 MB L2 (no flush needed)"},
+            "iterations": mx["iters"], "true_rel_residual": mx["true_rel_residual"],
+            "rel_diff_vs_fp64_solution": mix_vs_fp64,
+            "roofline": prof["mixed"]["roofline"],
+            "fp64": {"value": res["fp64"]["value"], "unit": "DOFs/s", "ms_per_step": res["fp64"]["ms_per_step"],
+                     "iterations": res["fp64"]["iters"], "true_rel_residual": res["fp64"]["true_rel_residual"],
+                     "roofline": prof["fp64"]["roofline"]},
+            "kernel_ms_per_solve": {"mixed": prof["mixed"]["class_ms"], "fp64": prof["fp64"]["class_ms"]},
+            "e2e": {"value": world * n / e2e_s, "unit": "DOFs/s", "h2d_bytes_per_step": 2 * 8 * n,
+                    "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": mx["launches_per_step"] * args.steps,
+            "clocks": clocks,
+            "peaks": peaks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    for h in H.values():
+        h.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--direct", action="store_true",
+                    help="launch kernels directly instead of one graph per solve (for ncu launch lists)")
+    ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
+                    help="time one precision only and print its figures (profiling runs)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: warmup raised to 3", file=sys.stderr)
+        args.warmup = 3
+    if args.impl == "reference":
+        return bench_reference(args)
+    return bench_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -92,6 +92,8 @@ typedef struct {
   double inner_pinv_tau; /* MPCG_MIXED: cutoff used inside the FP32 inner solve */
   double inner_drop_delta;
   int max_outer;         /* MPCG_MIXED: maximum refinement steps */
+  int use_graph;         /* 1: run each solve as one CUDA graph with a device-side
+                            loop; 0: launch the kernels directly (same results) */
   void* stream;          /* cudaStream_t */
 } mpcg_options;
 
@@ -156,6 +158,29 @@ mpcg_status mg_corrections(mg_hierarchy* h, const double* r_dev, double* Z_dev);
 /* Copy grid `level`'s Galerkin operator in the stencil format above into
  * planes_dev (3^dim * n_level doubles, device). */
 mpcg_status mg_get_operator(mg_hierarchy* h, int level, double* planes_dev);
+
+/*
+ * Measurement support (not part of the method).  Kernel launches are grouped
+ * in MPCG_NUM_KERNEL_CLASSES classes named by mpcg_kernel_class_name():
+ * pack, residual, init, restrict, coarse_solve, prolong, jacobi, spmm,
+ * gram_window, small_beta, orth_update, small_alpha, update_xr, check, aux.
+ *
+ * mpcg_solve_profiled runs mpcg_solve with direct kernel launches (no graph)
+ * and a CUDA event pair around every launch on the hierarchy's stream; it
+ * returns per class the summed device time in ms (class_ms) and the launch
+ * count (class_launches), both arrays of MPCG_NUM_KERNEL_CLASSES entries or
+ * NULL, and, if trace_cls / trace_ms are not NULL, the class and duration of
+ * every launch in launch order (at most trace_cap entries; *trace_len gets
+ * the full count).  The numerical result equals that of mpcg_solve.
+ * mg_last_launches returns how many kernels the last mpcg_solve or
+ * mpcg_solve_profiled call on h executed (graph launches counted per node).
+ */
+#define MPCG_NUM_KERNEL_CLASSES 15
+const char* mpcg_kernel_class_name(int cls);
+mpcg_status mpcg_solve_profiled(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit,
+                                int* iters_out, double* class_ms, long long* class_launches,
+                                int* trace_cls, float* trace_ms, long long trace_cap, long long* trace_len);
+long long mg_last_launches(const mg_hierarchy* h);
 
 /* Release everything the hierarchy owns.  NULL is ignored. */
 void mg_hierarchy_destroy(mg_hierarchy* h);

@@ -95,6 +95,7 @@ struct Solver {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool use_graph = false;
+  long long prologue_launches = 0, body_launches = 0;
   void drop_graph() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -111,7 +112,76 @@ struct Solver {
   }
 };
 
+enum KClass {
+  K_PACK, K_RESIDUAL, K_INIT, K_RESTRICT, K_COARSE, K_PROLONG, K_JACOBI, K_SPMM, K_GRAM, K_BETA, K_ORTH,
+  K_ALPHA, K_UPDATE, K_CHECK, K_AUX, K_COUNT
+};
+const char* const kClassNames[K_COUNT] = {"pack", "residual", "init", "restrict", "coarse_solve", "prolong",
+                                          "jacobi", "spmm", "gram_window", "small_beta", "orth_update",
+                                          "small_alpha", "update_xr", "check", "aux"};
+
+// Launch accounting and optional per-launch CUDA-event timing (direct
+// launches only; never active while a graph is captured).
+struct Profiler {
+  bool on = false;
+  long long* target = nullptr;      // launch counter currently charged
+  long long live = 0;               // launches executed by the current call
+  long long count[K_COUNT] = {};
+  double ms[K_COUNT] = {};
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, size_t>> pending;
+  std::vector<std::pair<int, float>> trace;   // (class, ms) of every timed launch, in order
+  size_t used = 0;
+  void begin(int cls, cudaStream_t s) {
+    ++*(target ? target : &live);
+    if (!on) return;
+    if (used + 2 > pool.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        pool.push_back(e);
+      }
+    }
+    cudaEventRecord(pool[used], s);
+    pending.push_back({cls, used});
+    used += 2;
+  }
+  void end(cudaStream_t s) {
+    if (on) cudaEventRecord(pool[pending.back().second + 1], s);
+  }
+  void flush() {
+    for (auto& pr : pending) {
+      float t = 0.f;
+      cudaEventSynchronize(pool[pr.second + 1]);
+      cudaEventElapsedTime(&t, pool[pr.second], pool[pr.second + 1]);
+      ms[pr.first] += t;
+      count[pr.first] += 1;
+      trace.push_back({pr.first, t});
+    }
+    pending.clear();
+    used = 0;
+  }
+  void reset() {
+    trace.clear();
+    pending.clear();
+    used = 0;
+    live = 0;
+    for (int i = 0; i < K_COUNT; ++i) count[i] = 0, ms[i] = 0.0;
+  }
+  void release() {
+    for (auto e : pool) cudaEventDestroy(e);
+    pool.clear();
+  }
+};
+
 }  // namespace
+
+#define LAUNCH(h, cls, s, ...)        \
+  do {                                \
+    (h)->prof.begin((cls), (s));      \
+    __VA_ARGS__;                      \
+    (h)->prof.end((s));               \
+  } while (0)
 
 struct mg_hierarchy {
   int device = 0;
@@ -129,6 +199,9 @@ struct mg_hierarchy {
   Solver<float> s32;
   double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *nrm = nullptr, *part_mix = nullptr;
   double* stage = nullptr;   // 2 n doubles: staging for host b and x
+  Profiler prof;
+  bool force_direct = false;
+  long long last_launches = 0;
 };
 
 namespace {
@@ -205,35 +278,35 @@ template <typename T>
 void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState* state, cudaStream_t s) {
   const int J = h->levels - 1;
   if (J == 0) {
-    launch_coarse_solve<T>(h->lev[0].g, h->L0, r, Z, state, s);
+    LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->L0, r, Z, state, s));
     return;
   }
   const T* rj = r;
   for (int j = J; j >= 1; --j) {
-    launch_restrict<T>(h->lev[j].g, h->lev[j - 1].g, rj, S.rlev[j - 1], state, s);
+    LAUNCH(h, K_RESTRICT, s, launch_restrict<T>(h->lev[j].g, h->lev[j - 1].g, rj, S.rlev[j - 1], state, s));
     rj = S.rlev[j - 1];
   }
-  launch_coarse_solve<T>(h->lev[0].g, h->L0, S.rlev[0], S.zc[0], state, s);
+  LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->L0, S.rlev[0], S.zc[0], state, s));
   const int nu = h->opt.nu;
   for (int j = 1; j <= J; ++j) {
     const Level& L = h->lev[j];
     T* dst = j == J ? Z : S.zc[j];
-    launch_prolong<T>(h->lev[j - 1].g, L.g, S.zc[j - 1], dst, j, state, s);
+    LAUNCH(h, K_PROLONG, s, launch_prolong<T>(h->lev[j - 1].g, L.g, S.zc[j - 1], dst, j, state, s));
     const T* rr = j == J ? r : S.rlev[j];
     T* out = dst + (size_t)j * L.g.len;
     const T* st = st_of<T>(L);
     const T* di = dinv_of<T>(L);
     if (nu == 1) {
-      launch_jacobi<T>(L.g, st, di, rr, nullptr, out, 0, state, s);
+      LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, nullptr, out, 0, state, s));
     } else if (nu == 2) {
-      launch_jacobi<T>(L.g, st, di, rr, nullptr, out, 1, state, s);
+      LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, nullptr, out, 1, state, s));
     } else {
       T* a = S.tmp[j];
       T* b = S.tmp2[j];
-      launch_jacobi<T>(L.g, st, di, rr, nullptr, a, 1, state, s);
+      LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, nullptr, a, 1, state, s));
       for (int k = 3; k <= nu; ++k) {
         T* o = k == nu ? out : b;
-        launch_jacobi<T>(L.g, st, di, rr, a, o, 2, state, s);
+        LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, a, o, 2, state, s));
         T* t = a;
         a = b;
         b = t;
@@ -246,8 +319,8 @@ template <typename T>
 void enqueue_prologue(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond, int use_cond,
                       cudaStream_t s) {
   const Level& L = h->lev[h->levels - 1];
-  launch_residual<T>(L.g, st_of<T>(L), S.b, S.x, S.r, S.part_res, s);
-  launch_init(S.state, S.part_res, kRedBlocks, S.res_hist, cond, use_cond, s);
+  LAUNCH(h, K_RESIDUAL, s, launch_residual<T>(L.g, st_of<T>(L), S.b, S.x, S.r, S.part_res, s));
+  LAUNCH(h, K_INIT, s, launch_init(S.state, S.part_res, kRedBlocks, S.res_hist, cond, use_cond, s));
 }
 
 template <typename T>
@@ -255,13 +328,13 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
   const Level& L = h->lev[h->levels - 1];
   const int C = S.C;
   enqueue_mg<T>(h, S, S.r, S.Z, S.state, s);
-  launch_spmm<T>(L.g, st_of<T>(L), S.Z, S.AZ, C, S.part_zaz, S.state, s);
-  launch_gram_window<T>(L.g, S.win, S.Z, C, S.part_W, S.state, s);
-  launch_small_beta(S.state, S.part_W, C, s);
-  launch_orth_update<T>(L.g, S.win, S.Z, S.AZ, S.r, C, S.part_G, S.state, s);
-  launch_small_alpha(S.state, S.part_G, S.part_zaz, C, S.alpha_hist, s);
-  launch_update_xr<T>(L.g, S.win, S.x, S.r, C, S.part_r, S.state, s);
-  launch_check(S.state, S.part_r, kRedBlocks, S.res_hist, cond, use_cond, s);
+  LAUNCH(h, K_SPMM, s, launch_spmm<T>(L.g, st_of<T>(L), S.Z, S.AZ, C, S.part_zaz, S.state, s));
+  LAUNCH(h, K_GRAM, s, launch_gram_window<T>(L.g, S.win, S.Z, C, S.part_W, S.state, s));
+  LAUNCH(h, K_BETA, s, launch_small_beta(S.state, S.part_W, C, s));
+  LAUNCH(h, K_ORTH, s, launch_orth_update<T>(L.g, S.win, S.Z, S.AZ, S.r, C, S.part_G, S.state, s));
+  LAUNCH(h, K_ALPHA, s, launch_small_alpha(S.state, S.part_G, S.part_zaz, C, S.alpha_hist, s));
+  LAUNCH(h, K_UPDATE, s, launch_update_xr<T>(L.g, S.win, S.x, S.r, C, S.part_r, S.state, s));
+  LAUNCH(h, K_CHECK, s, launch_check(S.state, S.part_r, kRedBlocks, S.res_hist, cond, use_cond, s));
 }
 
 // Capture prologue + while(cond){body} as one graph.  On any failure the
@@ -281,7 +354,10 @@ void build_graph(mg_hierarchy* h, Solver<T>& S) {
     cudaGetLastError();
     return;
   }
+  S.prologue_launches = 0;
+  h->prof.target = &S.prologue_launches;
   enqueue_prologue<T>(h, S, cond, 1, cs);
+  h->prof.target = nullptr;
   cudaStreamCaptureStatus st;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
@@ -303,7 +379,10 @@ void build_graph(mg_hierarchy* h, Solver<T>& S) {
     ok = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
          cudaSuccess;
     if (ok) {
+      S.body_launches = 0;
+      h->prof.target = &S.body_launches;
       enqueue_body<T>(h, S, cond, 1, cs);
+      h->prof.target = nullptr;
       cudaGraph_t b2 = nullptr;
       ok = cudaStreamEndCapture(cs, &b2) == cudaSuccess;
     }
@@ -324,8 +403,10 @@ void build_graph(mg_hierarchy* h, Solver<T>& S) {
 template <typename T>
 mpcg_status run_solver(mg_hierarchy* h, Solver<T>& S, DevState* host_state) {
   cudaStream_t s = h->stream;
-  if (!S.use_graph) build_graph<T>(h, S);
-  if (S.use_graph) {
+  const bool direct = h->force_direct || !h->opt.use_graph;
+  if (!S.use_graph && !direct) build_graph<T>(h, S);
+  const bool graph = S.use_graph && !direct;
+  if (graph) {
     CK(cudaGraphLaunch(S.exec, s));
   } else {
     // direct launches; the host reads the done flag after every iteration
@@ -335,6 +416,7 @@ mpcg_status run_solver(mg_hierarchy* h, Solver<T>& S, DevState* host_state) {
       int done = 0;
       CK(cudaMemcpyAsync(&done, &S.state->done, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
+      h->prof.flush();
       if (done) break;
       enqueue_body<T>(h, S, dummy, 0, s);
     }
@@ -342,6 +424,11 @@ mpcg_status run_solver(mg_hierarchy* h, Solver<T>& S, DevState* host_state) {
   CK(cudaMemcpyAsync(host_state, S.state, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
+  if (graph) {
+    // the loop body ran once per x update, plus once more after a breakdown
+    const long long bodies = host_state->k + (host_state->done == 3 ? 1 : 0);
+    h->prof.live += S.prologue_launches + bodies * S.body_launches;
+  }
   return MPCG_OK;
 }
 
@@ -405,6 +492,7 @@ mpcg_status mpcg_default_options(mpcg_options* opt) {
   opt->inner_pinv_tau = 1e-6;
   opt->inner_drop_delta = 1e-5;
   opt->max_outer = 20;
+  opt->use_graph = 1;
   opt->stream = nullptr;
   return MPCG_OK;
 }
@@ -423,6 +511,7 @@ void mg_hierarchy_destroy(mg_hierarchy* h) {
   h->s64.release();
   h->s32.release();
   h->mem.release();
+  h->prof.release();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
@@ -534,12 +623,12 @@ static mpcg_status solve_fp64(mg_hierarchy* h, const double* b, double* x, doubl
   cudaStream_t s = h->stream;
   const GridDesc& gf = h->lev[h->levels - 1].g;
   CKS(ensure_hist(h, S, maxit));
-  launch_pack<double, double>(gf, b, gf.n, S.b, 1, s);
-  launch_pack<double, double>(gf, x, gf.n, S.x, 1, s);
-  launch_set_params(S.state, rtol, maxit, S.m, S.C, h->opt.drop_delta, h->opt.pinv_tau, s);
+  LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, b, gf.n, S.b, 1, s));
+  LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, x, gf.n, S.x, 1, s));
+  LAUNCH(h, K_AUX, s, launch_set_params(S.state, rtol, maxit, S.m, S.C, h->opt.drop_delta, h->opt.pinv_tau, s));
   DevState hs;
   CKS(run_solver<double>(h, S, &hs));
-  launch_unpack<double, double>(gf, S.x, x, gf.n, 1, s);
+  LAUNCH(h, K_PACK, s, launch_unpack<double, double>(gf, S.x, x, gf.n, 1, s));
   if (res_hist) CK(cudaMemcpyAsync(res_hist, S.res_hist, sizeof(double) * (hs.k + 1), cudaMemcpyDeviceToHost, s));
   if (alpha_hist && hs.k > 0)
     CK(cudaMemcpyAsync(alpha_hist, S.alpha_hist, sizeof(double) * hs.k * S.C, cudaMemcpyDeviceToHost, s));
@@ -561,14 +650,14 @@ static mpcg_status solve_mixed(mg_hierarchy* h, const double* b, double* x, doub
   const Level& L = h->lev[h->levels - 1];
   const GridDesc& gf = L.g;
   CKS(ensure_hist(h, S, maxit));
-  launch_pack<double, double>(gf, b, gf.n, h->b64, 1, s);
-  launch_pack<double, double>(gf, x, gf.n, h->x64, 1, s);
+  LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, b, gf.n, h->b64, 1, s));
+  LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, x, gf.n, h->x64, 1, s));
   int total = 0, nhist = 0;
   mpcg_status result = MPCG_NOT_CONVERGED;
   std::vector<double> inner(maxit + 1);
   for (int outer = 0; outer <= h->opt.max_outer; ++outer) {
-    launch_residual<double>(gf, L.st64, h->b64, h->x64, h->r64, h->part_mix, s);
-    launch_sum_partials(h->part_mix, 2, kRedBlocks, h->nrm, s);
+    LAUNCH(h, K_RESIDUAL, s, launch_residual<double>(gf, L.st64, h->b64, h->x64, h->r64, h->part_mix, s));
+    LAUNCH(h, K_AUX, s, launch_sum_partials(h->part_mix, 2, kRedBlocks, h->nrm, s));
     double nrm[2];
     CK(cudaMemcpyAsync(nrm, h->nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -584,10 +673,10 @@ static mpcg_status solve_mixed(mg_hierarchy* h, const double* b, double* x, doub
       break;
     }
     if (total >= maxit || outer == h->opt.max_outer) break;
-    launch_scale_to_f32(gf, h->r64, h->nrm, S.b, s);
+    LAUNCH(h, K_AUX, s, launch_scale_to_f32(gf, h->r64, h->nrm, S.b, s));
     CK(cudaMemsetAsync(S.x, 0, sizeof(float) * gf.len, s));
-    launch_set_params(S.state, h->opt.inner_rtol, maxit - total, S.m, S.C, h->opt.inner_drop_delta,
-                      h->opt.inner_pinv_tau, s);
+    LAUNCH(h, K_AUX, s, launch_set_params(S.state, h->opt.inner_rtol, maxit - total, S.m, S.C, h->opt.inner_drop_delta,
+                                          h->opt.inner_pinv_tau, s));
     DevState hs;
     CKS(run_solver<float>(h, S, &hs));
     if (res_hist && hs.k > 0) {
@@ -601,10 +690,10 @@ static mpcg_status solve_mixed(mg_hierarchy* h, const double* b, double* x, doub
       result = MPCG_ERR_BREAKDOWN;
       break;
     }
-    launch_axpy_mixed(gf, h->x64, S.x, h->nrm, s);
+    LAUNCH(h, K_AUX, s, launch_axpy_mixed(gf, h->x64, S.x, h->nrm, s));
     if (hs.k == 0) break;
   }
-  launch_unpack<double, double>(gf, h->x64, x, gf.n, 1, s);
+  LAUNCH(h, K_PACK, s, launch_unpack<double, double>(gf, h->x64, x, gf.n, 1, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
   if (iters_out) *iters_out = total;
@@ -641,12 +730,43 @@ mpcg_status mpcg_solve(mg_hierarchy* h, const double* b, double* x, double rtol,
       xd = h->stage + gf.n;
     }
   }
+  h->prof.reset();
   mpcg_status st = h->opt.precision == MPCG_MIXED
                        ? solve_mixed(h, bd, xd, rtol, maxit, iters_out, res_hist)
                        : solve_fp64(h, bd, xd, rtol, maxit, iters_out, res_hist, alpha_hist);
+  h->prof.flush();
+  h->last_launches = h->prof.live;
   if (!xdev && (st >= 0 || st == MPCG_ERR_BREAKDOWN)) {
     CK(cudaMemcpyAsync(x, xd, nb, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+  }
+  return st;
+}
+
+const char* mpcg_kernel_class_name(int cls) {
+  return cls >= 0 && cls < K_COUNT ? kClassNames[cls] : "";
+}
+
+long long mg_last_launches(const mg_hierarchy* h) { return h ? h->last_launches : -1; }
+
+mpcg_status mpcg_solve_profiled(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, int* iters_out,
+                                double* class_ms, long long* class_launches, int* trace_cls, float* trace_ms,
+                                long long trace_cap, long long* trace_len) {
+  CKS(check_h(h));
+  h->prof.on = true;
+  h->force_direct = true;
+  mpcg_status st = mpcg_solve(h, b, x, rtol, maxit, iters_out, nullptr, nullptr);
+  h->prof.on = false;
+  h->force_direct = false;
+  for (int i = 0; i < K_COUNT; ++i) {
+    if (class_ms) class_ms[i] = h->prof.ms[i];
+    if (class_launches) class_launches[i] = h->prof.count[i];
+  }
+  const long long nt = (long long)h->prof.trace.size();
+  if (trace_len) *trace_len = nt;
+  for (long long i = 0; i < nt && i < trace_cap; ++i) {
+    if (trace_cls) trace_cls[i] = h->prof.trace[i].first;
+    if (trace_ms) trace_ms[i] = h->prof.trace[i].second;
   }
   return st;
 }

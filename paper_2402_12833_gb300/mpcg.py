@@ -44,7 +44,7 @@ class mpcg_options(C.Structure):
     _fields_ = [("m", C.c_int), ("nu", C.c_int), ("omega", C.c_double), ("pinv_tau", C.c_double),
                 ("drop_delta", C.c_double), ("precision", C.c_int), ("inner_rtol", C.c_double),
                 ("inner_pinv_tau", C.c_double), ("inner_drop_delta", C.c_double), ("max_outer", C.c_int),
-                ("stream", C.c_void_p)]
+                ("use_graph", C.c_int), ("stream", C.c_void_p)]
 
 
 _lib = None
@@ -63,7 +63,13 @@ _SIGS = {
     "mg_get_operator": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "mg_hierarchy_destroy": (None, [C.c_void_p]),
     "mpcg_last_error": (C.c_char_p, []),
+    "mpcg_kernel_class_name": (C.c_char_p, [C.c_int]),
+    "mpcg_solve_profiled": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                                      C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_longlong, C.POINTER(C.c_longlong)]),
+    "mg_last_launches": (C.c_longlong, [C.c_void_p]),
 }
+MPCG_NUM_KERNEL_CLASSES = 15
 
 
 def load(path: str = LIB_PATH):
@@ -139,6 +145,32 @@ def mpcg_solve(h: int, b, x, rtol: float = 1e-8, maxit: int = 500, histories: bo
     if histories:
         return st, k, rh[: k + 1].copy(), ah[: k * ncols].reshape(k, ncols).copy()
     return st, k, None, None
+
+
+def mpcg_kernel_class_name(cls: int) -> str:
+    return load().mpcg_kernel_class_name(cls).decode()
+
+
+def mpcg_solve_profiled(h: int, b, x, rtol: float = 1e-8, maxit: int = 500, trace_cap: int = 1 << 16):
+    """Solve with per-launch CUDA-event timing; returns (status, iterations,
+    {class name: (total ms, launches)}, [(class name, ms) per launch])."""
+    it = C.c_int(0)
+    ms = np.zeros(MPCG_NUM_KERNEL_CLASSES)
+    cnt = np.zeros(MPCG_NUM_KERNEL_CLASSES, dtype=np.int64)
+    tc = np.zeros(trace_cap, dtype=np.int32)
+    tm = np.zeros(trace_cap, dtype=np.float32)
+    tl = C.c_longlong(0)
+    st = load().mpcg_solve_profiled(h, _ptr(b), _ptr(x), rtol, maxit, C.byref(it), ms.ctypes.data, cnt.ctypes.data,
+                                    tc.ctypes.data, tm.ctypes.data, trace_cap, C.byref(tl))
+    _check(st, allow=(MPCG_OK, MPCG_NOT_CONVERGED))
+    names = [mpcg_kernel_class_name(i) for i in range(MPCG_NUM_KERNEL_CLASSES)]
+    n = min(tl.value, trace_cap)
+    trace = [(names[int(c)], float(t)) for c, t in zip(tc[:n], tm[:n])]
+    return st, it.value, {names[i]: (float(ms[i]), int(cnt[i])) for i in range(MPCG_NUM_KERNEL_CLASSES)}, trace
+
+
+def mg_last_launches(h: int) -> int:
+    return load().mg_last_launches(h)
 
 
 def mg_num_levels(h: int) -> int:
