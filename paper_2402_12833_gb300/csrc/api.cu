@@ -191,6 +191,7 @@ struct mg_hierarchy {
   cudaStream_t cap_stream = nullptr;
   Level lev[kMaxLevels];
   double* L0 = nullptr;
+  double* rdiag0 = nullptr;
   int n0 = 0;
   int* info = nullptr;
   bool have32 = false;
@@ -251,9 +252,9 @@ mpcg_status build_solver(mg_hierarchy* h, Solver<T>& S) {
   CKS(S.mem.get(&S.state, 1, s));
   CKS(S.mem.get(&S.part_res, 2 * kRedBlocks, s));
   CKS(S.mem.get(&S.part_zaz, (size_t)C * kRedBlocks, s));
-  CKS(S.mem.get(&S.part_W, (size_t)S.m * C * C * kGramBlocks, s));
-  CKS(S.mem.get(&S.part_G, (size_t)(C * (C + 1) / 2 + C) * kRedBlocks, s));
-  CKS(S.mem.get(&S.part_r, kRedBlocks, s));
+  CKS(S.mem.get(&S.part_W, (size_t)S.m * C * C * gram_chunks(gf), s));
+  CKS(S.mem.get(&S.part_G, (size_t)(C * (C + 1) / 2 + C) * stream_blocks(gf), s));
+  CKS(S.mem.get(&S.part_r, stream_blocks(gf), s));
   S.built = true;
   return MPCG_OK;
 }
@@ -278,7 +279,7 @@ template <typename T>
 void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState* state, cudaStream_t s) {
   const int J = h->levels - 1;
   if (J == 0) {
-    LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->L0, r, Z, state, s));
+    LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->L0, h->rdiag0, r, Z, state, s));
     return;
   }
   const T* rj = r;
@@ -286,7 +287,7 @@ void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState*
     LAUNCH(h, K_RESTRICT, s, launch_restrict<T>(h->lev[j].g, h->lev[j - 1].g, rj, S.rlev[j - 1], state, s));
     rj = S.rlev[j - 1];
   }
-  LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->L0, S.rlev[0], S.zc[0], state, s));
+  LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->L0, h->rdiag0, S.rlev[0], S.zc[0], state, s));
   const int nu = h->opt.nu;
   for (int j = 1; j <= J; ++j) {
     const Level& L = h->lev[j];
@@ -329,12 +330,13 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
   const int C = S.C;
   enqueue_mg<T>(h, S, S.r, S.Z, S.state, s);
   LAUNCH(h, K_SPMM, s, launch_spmm<T>(L.g, st_of<T>(L), S.Z, S.AZ, C, S.part_zaz, S.state, s));
-  LAUNCH(h, K_GRAM, s, launch_gram_window<T>(L.g, S.win, S.Z, C, S.part_W, S.state, s));
-  LAUNCH(h, K_BETA, s, launch_small_beta(S.state, S.part_W, C, s));
+  LAUNCH(h, K_GRAM, s, launch_gram_window<T>(L.g, S.win, S.Z, C, S.m, S.part_W, S.state, s));
+  LAUNCH(h, K_BETA, s, launch_small_beta(S.state, S.part_W, gram_chunks(L.g), C, s));
   LAUNCH(h, K_ORTH, s, launch_orth_update<T>(L.g, S.win, S.Z, S.AZ, S.r, C, S.part_G, S.state, s));
-  LAUNCH(h, K_ALPHA, s, launch_small_alpha(S.state, S.part_G, S.part_zaz, C, S.alpha_hist, s));
+  LAUNCH(h, K_ALPHA, s, launch_small_alpha(S.state, S.part_G, stream_blocks(L.g), S.part_zaz, grid_for(L.g.npts, kRedBlocks), kRedBlocks, C,
+                                          S.alpha_hist, s));
   LAUNCH(h, K_UPDATE, s, launch_update_xr<T>(L.g, S.win, S.x, S.r, C, S.part_r, S.state, s));
-  LAUNCH(h, K_CHECK, s, launch_check(S.state, S.part_r, kRedBlocks, S.res_hist, cond, use_cond, s));
+  LAUNCH(h, K_CHECK, s, launch_check(S.state, S.part_r, stream_blocks(L.g), S.res_hist, cond, use_cond, s));
 }
 
 // Capture prologue + while(cond){body} as one graph.  On any failure the
@@ -592,8 +594,9 @@ mpcg_status mg_hierarchy_setup(const mg_operator* A, int levels, const mpcg_opti
   for (int j = 0; j < levels; ++j) launch_dinv<double>(h->lev[j].g, h->lev[j].st64, h->lev[j].dinv64, opt.omega, s);
   if ((st = h->mem.get(&h->L0, (size_t)n0 * n0, s)) != MPCG_OK) return fail(st);
   if ((st = h->mem.get(&h->info, 4, s)) != MPCG_OK) return fail(st);
+  if ((st = h->mem.get(&h->rdiag0, n0, s)) != MPCG_OK) return fail(st);
   launch_dense_from_stencil(h->lev[0].g, h->lev[0].st64, h->L0, s);
-  launch_cholesky(h->L0, (int)n0, h->info, s);
+  launch_cholesky(h->L0, h->rdiag0, (int)n0, h->info, s);
   int info = 0;
   if (cudaMemcpyAsync(&info, h->info, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {

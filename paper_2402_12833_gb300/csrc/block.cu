@@ -1,23 +1,59 @@
 // Tall-skinny block kernels of the MPCG step (Section 2.2, Algorithm 1):
-//   * the Gram blocks (A P_j)^T Z against the stored window,
+//   * the Gram blocks W_j = (A P_j)^T Z against the stored window,
 //   * the A-orthogonalisation P = Z - sum_j P_j beta_j with the same
 //     recurrence for A P, fused with the new Gram matrix sym(P^T A P) and
 //     the right-hand side P^T r,
 //   * the update x += P alpha, r -= A P alpha with ||r||^2.
 //
+// These kernels stream the padded arrays (pads are zero, so they take part
+// harmlessly) in 16-byte vectors: 4 floats or 2 doubles per thread and step.
 // Reductions are deterministic: every block writes its partial sums
 // (value-major, fixed block count) and one small kernel adds them in a fixed
 // order.  Partial sums accumulate in FP64; in the FP32 path each thread first
-// sums its own products in FP32 over a short run (at most 16 products per
-// value in the Gram kernel, the points of one grid-stride sweep elsewhere).
+// sums its own products in FP32 over at most 64 points.
 #include "kernels.cuh"
 
 namespace mpcg {
 
 namespace {
 
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using V = float4;
+  static constexpr int W = 4;
+  __device__ static __forceinline__ void load(const float* p, float (&v)[4]) {
+    const float4 q = __ldcs(reinterpret_cast<const float4*>(p));
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
+  __device__ static __forceinline__ void load_keep(const float* p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
+  __device__ static __forceinline__ void store(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct Vec<double> {
+  using V = double2;
+  static constexpr int W = 2;
+  __device__ static __forceinline__ void load(const double* p, double (&v)[2]) {
+    const double2 q = __ldcs(reinterpret_cast<const double2*>(p));
+    v[0] = q.x; v[1] = q.y;
+  }
+  __device__ static __forceinline__ void load_keep(const double* p, double (&v)[2]) {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x; v[1] = q.y;
+  }
+  __device__ static __forceinline__ void store(double* p, const double (&v)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+
 template <int NV>
-__device__ __forceinline__ void block_sum_store(double (&v)[NV], double* part, int stride) {
+__device__ __forceinline__ void block_sum_store(double (&v)[NV], double* part, int stride, int slot) {
   __shared__ double sh[kBlock / 32][NV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -31,61 +67,56 @@ __device__ __forceinline__ void block_sum_store(double (&v)[NV], double* part, i
   for (int i = threadIdx.x; i < NV; i += blockDim.x) {
     double a = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += sh[w][i];
-    part[(long long)i * stride + blockIdx.x] = a;
+    part[(long long)i * stride + slot] = a;
   }
 }
 
-constexpr int kTD = 16;   // points per shared-memory tile of the Gram kernel
-
+// W_jj[a][b] = sum_i AP_slot(jj)[a][i] Z[b][i].  Block b works on window
+// block jj = b % m and on the contiguous point chunk b / m, so that the
+// blocks running together read the same chunk of Z (L2 reuse).
 template <typename T, int C>
 __global__ void __launch_bounds__(kBlock) k_gram_window(GridDesc g, Window<T> win, const T* __restrict__ Z,
-                                                        double* part, const DevState* state) {
+                                                        double* part, int nchunks, const DevState* state) {
   if (state->done) return;
-  const int cnt = state->count;
-  if (cnt == 0) return;
-  const int m = state->m, newest = state->newest;
-  const int nx = cnt * C;
-  constexpr int kMaxE = (kMaxWindow * C * C + kBlock - 1) / kBlock;
-  __shared__ T Xs[kMaxWindow * C][kTD];
-  __shared__ T Ys[C][kTD];
-  __shared__ const T* rowp[kMaxWindow * C];
-  for (int r = threadIdx.x; r < nx; r += blockDim.x) {
-    const int jj = r / C, a = r % C;
-    const int slot = (newest - jj + m) % m;
-    rowp[r] = win.AP[slot] + (long long)a * g.len + g.G;
+  const int m = state->m;
+  const int jj = blockIdx.x % m, chunk = blockIdx.x / m;
+  if (jj >= state->count) return;
+  const int slot = (state->newest - jj + m) % m;
+  const T* AP = win.AP[slot] + g.G;
+  const T* Zb = Z + g.G;
+  constexpr int W = Vec<T>::W;
+  const long long ngroups = g.npts / W;
+  const long long per = (ngroups + nchunks - 1) / nchunks;
+  const long long g0 = (long long)chunk * per;
+  const long long g1 = g0 + per < ngroups ? g0 + per : ngroups;
+  // the chunk count keeps every thread at <= 16 vector groups (64 points in
+  // FP32) before its partial sums are widened to FP64
+  T acc[C][C];
+#pragma unroll
+  for (int a = 0; a < C; ++a)
+#pragma unroll
+    for (int b = 0; b < C; ++b) acc[a][b] = 0;
+  for (long long q = g0 + threadIdx.x; q < g1; q += blockDim.x) {
+    const long long i = q * W;
+    T z[C][W], ap[C][W];
+#pragma unroll
+    for (int b = 0; b < C; ++b) Vec<T>::load_keep(Zb + (long long)b * g.len + i, z[b]);
+#pragma unroll
+    for (int a = 0; a < C; ++a) Vec<T>::load(AP + (long long)a * g.len + i, ap[a]);
+#pragma unroll
+    for (int a = 0; a < C; ++a)
+#pragma unroll
+      for (int b = 0; b < C; ++b)
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[a][b] = fma(ap[a][w], z[b][w], acc[a][b]);
   }
-  double acc[kMaxE];
+  double accd[C * C];
 #pragma unroll
-  for (int q = 0; q < kMaxE; ++q) acc[q] = 0.0;
-  __syncthreads();
-  const long long ntiles = (g.npts + kTD - 1) / kTD;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long base = tile * kTD;
-    for (int e = threadIdx.x; e < (nx + C) * kTD; e += blockDim.x) {
-      const int r = e / kTD, d = e % kTD;
-      const long long i = base + d;
-      if (r < nx) Xs[r][d] = i < g.npts ? rowp[r][i] : (T)0;
-      else Ys[r - nx][d] = i < g.npts ? Z[(long long)(r - nx) * g.len + g.G + i] : (T)0;
-    }
-    __syncthreads();
+  for (int a = 0; a < C; ++a)
 #pragma unroll
-    for (int q = 0; q < kMaxE; ++q) {
-      const int e = threadIdx.x + q * kBlock;
-      if (e < nx * C) {
-        const int r = e / C, b = e % C;
-        T s = 0;
-#pragma unroll
-        for (int d = 0; d < kTD; ++d) s = fma(Xs[r][d], Ys[b][d], s);
-        acc[q] += (double)s;
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int q = 0; q < kMaxE; ++q) {
-    const int e = threadIdx.x + q * kBlock;
-    if (e < nx * C) part[(long long)e * kGramBlocks + blockIdx.x] = acc[q];
-  }
+    for (int b = 0; b < C; ++b) accd[a * C + b] = (double)acc[a][b];
+  double* pj = part + (long long)jj * C * C * nchunks;
+  block_sum_store<C * C>(accd, pj, nchunks, chunk);
 }
 
 template <typename T, int C>
@@ -104,58 +135,75 @@ __global__ void __launch_bounds__(kBlock) k_orth_update(GridDesc g, Window<T> wi
   }
   for (int jj = threadIdx.x; jj < cnt; jj += blockDim.x) {
     const int slot = (newest - jj + m) % m;
-    pp[jj] = win.P[slot];
-    app[jj] = win.AP[slot];
+    pp[jj] = win.P[slot] + g.G;
+    app[jj] = win.AP[slot] + g.G;
   }
   __syncthreads();
-  T* Pn = win.P[ns];
-  T* APn = win.AP[ns];
+  T* Pn = win.P[ns] + g.G;
+  T* APn = win.AP[ns] + g.G;
+  const T* Zb = Z + g.G;
+  const T* AZb = AZ + g.G;
+  const T* rb = r + g.G;
+  constexpr int W = Vec<T>::W;
   constexpr int NG = C * (C + 1) / 2;
   T acc[NG + C];
 #pragma unroll
   for (int i = 0; i < NG + C; ++i) acc[i] = 0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.npts;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long idx = g.G + t;
-    T p[C], ap[C];
+  const long long ngroups = g.npts / W;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long i = q * W;
+    T p[C][W], ap[C][W];
 #pragma unroll
     for (int b = 0; b < C; ++b) {
-      p[b] = Z[(long long)b * g.len + idx];
-      ap[b] = AZ[(long long)b * g.len + idx];
+      Vec<T>::load(Zb + (long long)b * g.len + i, p[b]);
+      Vec<T>::load(AZb + (long long)b * g.len + i, ap[b]);
     }
     for (int jj = 0; jj < cnt; ++jj) {
       const T* Pj = pp[jj];
       const T* APj = app[jj];
+      T pa[C][W], apa[C][W];
 #pragma unroll
       for (int a = 0; a < C; ++a) {
-        const T pa = Pj[(long long)a * g.len + idx];
-        const T apa = APj[(long long)a * g.len + idx];
+        Vec<T>::load(Pj + (long long)a * g.len + i, pa[a]);
+        Vec<T>::load(APj + (long long)a * g.len + i, apa[a]);
+      }
+#pragma unroll
+      for (int a = 0; a < C; ++a)
 #pragma unroll
         for (int b = 0; b < C; ++b) {
-          p[b] = fma(-pa, beta[jj][a][b], p[b]);
-          ap[b] = fma(-apa, beta[jj][a][b], ap[b]);
+          const T bt = beta[jj][a][b];
+#pragma unroll
+          for (int w = 0; w < W; ++w) {
+            p[b][w] = fma(-pa[a][w], bt, p[b][w]);
+            ap[b][w] = fma(-apa[a][w], bt, ap[b][w]);
+          }
         }
-      }
     }
-    const T rv = r[idx];
+    T rv[W];
+    Vec<T>::load(rb + i, rv);
     int k = 0;
 #pragma unroll
     for (int a = 0; a < C; ++a) {
-      Pn[(long long)a * g.len + idx] = p[a];
-      APn[(long long)a * g.len + idx] = ap[a];
+      Vec<T>::store(Pn + (long long)a * g.len + i, p[a]);
+      Vec<T>::store(APn + (long long)a * g.len + i, ap[a]);
 #pragma unroll
       for (int b = a; b < C; ++b) {
-        acc[k] = fma(p[a], ap[b], acc[k]);
-        acc[k] = fma(p[b], ap[a], acc[k]);
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          acc[k] = fma(p[a][w], ap[b][w], acc[k]);
+          acc[k] = fma(p[b][w], ap[a][w], acc[k]);
+        }
         ++k;
       }
-      acc[NG + a] = fma(p[a], rv, acc[NG + a]);
+#pragma unroll
+      for (int w = 0; w < W; ++w) acc[NG + a] = fma(p[a][w], rv[w], acc[NG + a]);
     }
   }
   double accd[NG + C];
 #pragma unroll
   for (int i = 0; i < NG + C; ++i) accd[i] = (double)acc[i];
-  block_sum_store<NG + C>(accd, part, kRedBlocks);
+  block_sum_store<NG + C>(accd, part, gridDim.x, blockIdx.x);
 }
 
 template <typename T, int C>
@@ -163,28 +211,45 @@ __global__ void __launch_bounds__(kBlock) k_update_xr(GridDesc g, Window<T> win,
                                                       T* __restrict__ r, double* part, const DevState* state) {
   if (state->done) return;
   const int newest = state->newest;
-  const T* P = win.P[newest];
-  const T* AP = win.AP[newest];
+  const T* P = win.P[newest] + g.G;
+  const T* AP = win.AP[newest] + g.G;
+  T* xb = x + g.G;
+  T* rb = r + g.G;
   T al[C];
 #pragma unroll
   for (int a = 0; a < C; ++a) al[a] = (T)state->alpha[a];
+  constexpr int W = Vec<T>::W;
   T acc = 0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.npts;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long idx = g.G + t;
-    T px = 0, apx = 0;
+  const long long ngroups = g.npts / W;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long i = q * W;
+    T px[W] = {}, apx[W] = {};
 #pragma unroll
     for (int a = 0; a < C; ++a) {
-      px = fma(P[(long long)a * g.len + idx], al[a], px);
-      apx = fma(AP[(long long)a * g.len + idx], al[a], apx);
+      T pv[W], av[W];
+      Vec<T>::load(P + (long long)a * g.len + i, pv);
+      Vec<T>::load(AP + (long long)a * g.len + i, av);
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        px[w] = fma(pv[w], al[a], px[w]);
+        apx[w] = fma(av[w], al[a], apx[w]);
+      }
     }
-    x[idx] += px;
-    const T rv = r[idx] - apx;
-    r[idx] = rv;
-    acc = fma(rv, rv, acc);
+    T xv[W], rv[W];
+    Vec<T>::load_keep(xb + i, xv);
+    Vec<T>::load_keep(rb + i, rv);
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      xv[w] += px[w];
+      rv[w] -= apx[w];
+      acc = fma(rv[w], rv[w], acc);
+    }
+    Vec<T>::store(xb + i, xv);
+    Vec<T>::store(rb + i, rv);
   }
   double v[1] = {(double)acc};
-  block_sum_store<1>(v, part, kRedBlocks);
+  block_sum_store<1>(v, part, gridDim.x, blockIdx.x);
 }
 
 }  // namespace
@@ -206,30 +271,48 @@ __global__ void __launch_bounds__(kBlock) k_update_xr(GridDesc g, Window<T> win,
     default: break;                                                                              \
   }
 
+int gram_chunks(const GridDesc& g) {
+  // at most 16 vector groups (64 points) per thread and chunk
+  const long long groups = g.npts / 2;   // conservative for both vector widths
+  long long c = (groups + kBlock * 16 - 1) / (kBlock * 16);
+  if (c < 1) c = 1;
+  return (int)(c < kGramChunksMax ? c : kGramChunksMax);
+}
+
+int stream_blocks(const GridDesc& g) {
+  const long long groups = g.npts / 2;
+  long long need = (groups + kBlock * 16 - 1) / (kBlock * 16);   // <= 64 points per thread
+  long long fill = (groups + kBlock - 1) / kBlock;                // no idle threads
+  long long nb = kStreamBlocks < fill ? kStreamBlocks : fill;
+  if (need > nb) nb = need;
+  if (nb < 1) nb = 1;
+  return (int)(nb < kStreamBlocksMax ? nb : kStreamBlocksMax);
+}
+
 template <typename T>
-void launch_gram_window(const GridDesc& g, Window<T> win, const T* Z, int C, double* part, const DevState* state,
-                        cudaStream_t s) {
-  const int nb = kGramBlocks;
-  MPCG_C_SWITCH(C, (k_gram_window<T, CC><<<nb, kBlock, 0, s>>>(g, win, Z, part, state)));
+void launch_gram_window(const GridDesc& g, Window<T> win, const T* Z, int C, int m, double* part,
+                        const DevState* state, cudaStream_t s) {
+  const int nch = gram_chunks(g);
+  MPCG_C_SWITCH(C, (k_gram_window<T, CC><<<nch * m, kBlock, 0, s>>>(g, win, Z, part, nch, state)));
 }
 
 template <typename T>
 void launch_orth_update(const GridDesc& g, Window<T> win, const T* Z, const T* AZ, const T* r, int C, double* part,
                         const DevState* state, cudaStream_t s) {
-  const int nb = kRedBlocks;
+  const int nb = stream_blocks(g);
   MPCG_C_SWITCH(C, (k_orth_update<T, CC><<<nb, kBlock, 0, s>>>(g, win, Z, AZ, r, part, state)));
 }
 
 template <typename T>
 void launch_update_xr(const GridDesc& g, Window<T> win, T* x, T* r, int C, double* part, const DevState* state,
                       cudaStream_t s) {
-  const int nb = kRedBlocks;
+  const int nb = stream_blocks(g);
   MPCG_C_SWITCH(C, (k_update_xr<T, CC><<<nb, kBlock, 0, s>>>(g, win, x, r, part, state)));
 }
 
-template void launch_gram_window<double>(const GridDesc&, Window<double>, const double*, int, double*,
+template void launch_gram_window<double>(const GridDesc&, Window<double>, const double*, int, int, double*,
                                          const DevState*, cudaStream_t);
-template void launch_gram_window<float>(const GridDesc&, Window<float>, const float*, int, double*,
+template void launch_gram_window<float>(const GridDesc&, Window<float>, const float*, int, int, double*,
                                         const DevState*, cudaStream_t);
 template void launch_orth_update<double>(const GridDesc&, Window<double>, const double*, const double*,
                                          const double*, int, double*, const DevState*, cudaStream_t);

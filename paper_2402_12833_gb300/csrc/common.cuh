@@ -10,7 +10,9 @@
 // address of (x = -1, y), the pad row of plane z-1 at (y = -1, z), and so on,
 // so one pad layer serves as the zero Dirichlet ghost on both sides of every
 // axis.  A guard of G = p*p + p + 1 (3D; p + 1 in 2D) zero elements in front
-// makes (-1,-1,-1) addressable.  Stencils therefore need no boundary tests,
+// makes (-1,-1,-1) addressable (G is rounded up to a multiple of 32, and
+// every vector occupies len = G + p^dim rounded up to 32 elements).
+// Stencils therefore need no boundary tests,
 // interpolation reads zero parents outside the grid, and sums over a whole
 // padded array equal sums over the interior unknowns.
 #pragma once
@@ -47,9 +49,12 @@ inline GridDesc make_grid(int dim, int n1) {
   while ((1 << lp) < g.p) ++lp;
   g.lp = lp;
   long long p = g.p;
-  g.G = dim == 3 ? p * p + p + 1 : p + 1;
+  // guard rounded up to 32 elements so that every padded box starts on a
+  // 128-byte boundary (vector loads of 4 floats / 2 doubles stay aligned)
+  const long long guard = dim == 3 ? p * p + p + 1 : p + 1;
+  g.G = (guard + 31) / 32 * 32;
   g.npts = dim == 3 ? p * p * p : p * p;
-  g.len = g.G + g.npts;
+  g.len = (g.G + g.npts + 31) / 32 * 32;
   g.n = dim == 3 ? (long long)n1 * n1 * n1 : (long long)n1 * n1;
   return g;
 }

@@ -7,8 +7,15 @@ namespace mpcg {
 
 // Maximum number of thread blocks of the grid-stride reduction kernels; the
 // partial-sum buffers are sized for it.
-constexpr int kRedBlocks = 1216;     // 152 SMs x 8
-constexpr int kGramBlocks = 304;     // 152 SMs x 2
+constexpr int kRedBlocks = 1216;         // 152 SMs x 8 (stencil kernels with partial sums)
+constexpr int kStreamBlocks = 608;       // 152 SMs x 4 (streaming block kernels)
+constexpr int kStreamBlocksMax = 8192;
+constexpr int kGramChunksMax = 4096;
+
+// Grid sizes of the streaming block kernels and of the window Gram kernel;
+// both keep every thread at <= 64 points per FP32 partial sum.
+int stream_blocks(const GridDesc& g);
+int gram_chunks(const GridDesc& g);
 
 inline int grid_for(long long work, int cap) {
   long long b = (work + kBlock - 1) / kBlock;
@@ -57,7 +64,7 @@ void launch_convert_f32(const double* src, float* dst, long long count, cudaStre
 // W partials: rows jj*C+a (window block jj, newest first), cols b:
 //   sum_i AP_slot(jj)[a][i] * Z[b][i]
 template <typename T>
-void launch_gram_window(const GridDesc& g, Window<T> win, const T* Z, int C, double* part,
+void launch_gram_window(const GridDesc& g, Window<T> win, const T* Z, int C, int m, double* part,
                         const DevState* state, cudaStream_t s);
 // P_new = Z - sum P_j beta_j, AP_new = AZ - sum AP_j beta_j into the next
 // ring slot; partials of sym(P^T AP) (upper triangle) and P^T r.
@@ -72,9 +79,9 @@ void launch_update_xr(const GridDesc& g, Window<T> win, T* x, T* r, int C, doubl
 // ---- small.cu ------------------------------------------------------------
 void launch_init(DevState* st, const double* part_res, int nblk, double* res_hist,
                  cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
-void launch_small_beta(DevState* st, const double* part_W, int C, cudaStream_t s);
-void launch_small_alpha(DevState* st, const double* part_G, const double* part_zaz, int C,
-                        double* alpha_hist, cudaStream_t s);
+void launch_small_beta(DevState* st, const double* part_W, int nchunks, int C, cudaStream_t s);
+void launch_small_alpha(DevState* st, const double* part_G, int nblk_G, const double* part_zaz, int nblk_zaz,
+                        int zaz_stride, int C, double* alpha_hist, cudaStream_t s);
 void launch_check(DevState* st, const double* part_r, int nblk, double* res_hist,
                   cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
 void launch_set_params(DevState* st, double rtol, int maxit, int m, int C, double delta, double tau,
@@ -82,10 +89,10 @@ void launch_set_params(DevState* st, double rtol, int maxit, int m, int C, doubl
 // Cholesky of the dense coarsest matrix (in place, lower); info[0] = 0 or the
 // failing pivot + 1
 void launch_dense_from_stencil(const GridDesc& g, const double* st, double* dense, cudaStream_t s);
-void launch_cholesky(double* a, int n, int* info, cudaStream_t s);
+void launch_cholesky(double* a, double* rdiag, int n, int* info, cudaStream_t s);
 // out = A0^{-1} r via the Cholesky factor; r, out in padded layout of grid g
 template <typename T>
-void launch_coarse_solve(const GridDesc& g, const double* L, const T* r, T* out,
+void launch_coarse_solve(const GridDesc& g, const double* L, const double* rdiag, const T* r, T* out,
                          const DevState* state, cudaStream_t s);
 // ||r||^2 style sum of partials (value-major) into out[nv]
 void launch_sum_partials(const double* part, int nv, int nblk, double* out, cudaStream_t s);

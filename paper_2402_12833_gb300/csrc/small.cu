@@ -4,9 +4,14 @@
 // the column-drop rule and the scaled pseudo-inverse, the convergence test,
 // and the exact coarsest-level solve (dense Cholesky, S_0 of Section 2.1).
 //
-// The pseudo-inverse diagonalises D G D (D = diag(G_ii)^{-1/2}) with the
-// cyclic Jacobi eigenvalue method in round-robin (parallel) ordering, one
-// warp per matrix, and inverts the eigenvalues above tau * lambda_max.
+// Scaled pseudo-inverse: with D = diag(G_ii)^{-1/2} on the active columns,
+// G^+ = D (D G D)^+ D, where (D G D)^+ keeps the eigenvalues above
+// tau * lambda_max.  D G D has unit diagonal, so lambda_max <= n_active and
+// lambda_min >= 1 / trace((D G D)^{-1}); when a Cholesky factorisation
+// succeeds and 1 / trace(inverse) > tau * n_active, every eigenvalue is kept
+// and the pseudo-inverse is the inverse, computed from the factor.  Otherwise
+// the cyclic Jacobi eigenvalue method (round-robin ordering, one warp)
+// diagonalises D G D and the small eigenvalues are cut.
 #include <math.h>
 
 #include "kernels.cuh"
@@ -20,44 +25,34 @@ namespace {
 __device__ void reduce_values(const double* __restrict__ part, int nv, int nblk, int stride, double* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int v = warp; v < nv; v += nw) {
-    double a = 0.0;
-    for (int b = lane; b < nblk; b += 32) a += part[(long long)v * stride + b];
+    const double* p = part + (long long)v * stride;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int b = lane;
+    for (; b + 96 < nblk; b += 128) {
+      a0 += p[b];
+      a1 += p[b + 32];
+      a2 += p[b + 64];
+      a3 += p[b + 96];
+    }
+    for (; b < nblk; b += 32) a0 += p[b];
+    double a = (a0 + a1) + (a2 + a3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (lane == 0) out[v] = a;
   }
 }
 
-constexpr int kPad = 16;   // padded matrix size for the eigen solver (>= kMaxCols, even)
+constexpr int kPad = 16;   // padded matrix size for the small solvers (>= kMaxCols, even)
 
-// Scaled pseudo-inverse of the symmetric n x n matrix G (row-major, ld kPad)
-// restricted to the columns with act[i] != 0.  Result in Gp (ld kPad).  Runs
-// on one warp; Gs, V, scratch are shared arrays of kPad*kPad.
-__device__ void warp_pinv(const double* G, const int* act, int n, double tau, double* Gp, double* A, double* V,
-                          double* d, int* map, double* rot_c, double* rot_s, int* rot_p, int* rot_q) {
+// Jacobi eigenvalue pseudo-inverse of the na x na matrix A (ld kPad, active
+// part already scaled to unit diagonal); result into Ah (ld kPad).  One warp.
+__device__ void warp_jacobi_pinv(double* A, double* V, int na, double tau, double* Ah, double* rot_c, double* rot_s,
+                                 int* rot_p, int* rot_q, double* lam) {
   const int lane = threadIdx.x & 31;
-  // active index map
-  if (lane == 0) {
-    int k = 0;
-    for (int i = 0; i < n; ++i)
-      if (act[i]) map[k++] = i;
-    map[kPad - 1] = k;       // count stored in the last slot
-  }
+  for (int e = lane; e < kPad * kPad; e += 32) V[e] = (e / kPad == e % kPad) ? 1.0 : 0.0;
   __syncwarp();
-  const int na = map[kPad - 1];
-  for (int e = lane; e < kPad * kPad; e += 32) Gp[e] = 0.0;
-  if (na == 0) { __syncwarp(); return; }
-  for (int i = lane; i < na; i += 32) d[i] = 1.0 / sqrt(G[map[i] * kPad + map[i]]);
-  __syncwarp();
-  const int np = (na + 1) & ~1;   // even size; index na is a dummy when na is odd
-  for (int e = lane; e < kPad * kPad; e += 32) {
-    const int i = e / kPad, j = e % kPad;
-    A[e] = (i < na && j < na) ? d[i] * G[map[i] * kPad + map[j]] * d[j] : 0.0;
-    V[e] = (i == j) ? 1.0 : 0.0;
-  }
-  __syncwarp();
+  const int np = (na + 1) & ~1;
   for (int sweep = 0; sweep < 30; ++sweep) {
-    // convergence: off-diagonal Frobenius norm vs total
     double off = 0.0, tot = 0.0;
     for (int e = lane; e < na * na; e += 32) {
       const int i = e / na, j = e % na;
@@ -85,14 +80,13 @@ __device__ void warp_pinv(const double* G, const int* act, int n, double tau, do
             const double app = A[p * kPad + p], aqq = A[q * kPad + q];
             const double theta = (aqq - app) / (2.0 * apq);
             const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
+            c = rsqrt(t * t + 1.0);
             s = t * c;
           }
         }
         rot_p[lane] = p; rot_q[lane] = q; rot_c[lane] = c; rot_s[lane] = s;
       }
       __syncwarp();
-      // A <- A J (columns), then A <- J^T A (rows), V <- V J
       for (int e = lane; e < npairs * np; e += 32) {
         const int k = e / np, i = e % np;
         const int p = rot_p[k], q = rot_q[k];
@@ -116,20 +110,69 @@ __device__ void warp_pinv(const double* G, const int* act, int n, double tau, do
       __syncwarp();
     }
   }
-  // eigenvalues on the diagonal; inverse of those above tau * max
   double lmax = 0.0;
   for (int i = 0; i < na; ++i) lmax = fmax(lmax, A[i * kPad + i]);
+  if (lane < na) {
+    const double l = A[lane * kPad + lane];
+    lam[lane] = l > tau * lmax ? 1.0 / l : 0.0;
+  }
   __syncwarp();
   for (int e = lane; e < na * na; e += 32) {
     const int i = e / na, j = e % na;
     double s = 0.0;
-    for (int k = 0; k < na; ++k) {
-      const double lk = A[k * kPad + k];
-      if (lk > tau * lmax) s += V[i * kPad + k] * V[j * kPad + k] / lk;
-    }
-    Gp[map[i] * kPad + map[j]] = d[i] * s * d[j];
+    for (int k = 0; k < na; ++k) s += V[i * kPad + k] * V[j * kPad + k] * lam[k];
+    Ah[i * kPad + j] = s;
   }
   __syncwarp();
+}
+
+// Inverse of the SPD na x na matrix A (ld kPad) through its Cholesky factor,
+// into Ah.  A is overwritten.  Returns false if a pivot is not positive or
+// the inverse does not certify lambda_min > tau * na (see the file comment).
+__device__ bool warp_chol_inverse(double* A, double* X, int na, double tau, double* Ah, double* dinv) {
+  const int lane = threadIdx.x & 31;
+  bool ok = true;
+  for (int k = 0; k < na; ++k) {
+    const double piv = A[k * kPad + k];
+    if (!(piv > 0.0)) { ok = false; break; }
+    const double li = rsqrt(piv);
+    __syncwarp();
+    if (lane == 0) { A[k * kPad + k] = piv * li; dinv[k] = li; }
+    for (int i = k + 1 + lane; i < na; i += 32) A[i * kPad + k] *= li;
+    __syncwarp();
+    const int mm = na - k - 1;
+    for (int e = lane; e < mm * mm; e += 32) {
+      const int i = k + 1 + e / mm, j = k + 1 + e % mm;
+      if (j <= i) A[i * kPad + j] -= A[i * kPad + k] * A[j * kPad + k];
+    }
+    __syncwarp();
+  }
+  if (!ok) return false;
+  // X = L^{-1}: lane j owns column j
+  if (lane < na) {
+    const int j = lane;
+    for (int i = 0; i < na; ++i) X[i * kPad + j] = 0.0;
+    X[j * kPad + j] = dinv[j];
+    for (int i = j + 1; i < na; ++i) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s += A[i * kPad + k] * X[k * kPad + j];
+      X[i * kPad + j] = -s * dinv[i];
+    }
+  }
+  __syncwarp();
+  double tr = 0.0;
+  for (int e = lane; e < na * na; e += 32) {
+    const int a = e / na, b = e % na;
+    const int k0 = a > b ? a : b;
+    double s = 0.0;
+    for (int k = k0; k < na; ++k) s += X[k * kPad + a] * X[k * kPad + b];
+    Ah[a * kPad + b] = s;
+    if (a == b) tr += s;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+  __syncwarp();
+  return tr > 0.0 && 1.0 / tr > tau * na;
 }
 
 __global__ void k_set_params(DevState* st, double rtol, int maxit, int m, int C, double delta, double tau) {
@@ -144,7 +187,7 @@ __global__ void k_set_params(DevState* st, double rtol, int maxit, int m, int C,
 __global__ void k_init(DevState* st, const double* part_res, int nblk, double* res_hist,
                        cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ double v[2];
-  reduce_values(part_res, 2, nblk, kRedBlocks, v);
+  reduce_values(part_res, 2, nblk, nblk, v);
   __syncthreads();
   if (threadIdx.x == 0) {
     st->k = 0;
@@ -163,13 +206,13 @@ __global__ void k_init(DevState* st, const double* part_res, int nblk, double* r
   }
 }
 
-__global__ void k_small_beta(DevState* st, const double* part_W, int C) {
+__global__ void k_small_beta(DevState* st, const double* part_W, int nchunks, int C) {
   if (st->done) return;
   const int cnt = st->count;
   if (cnt == 0) return;
   const int m = st->m, newest = st->newest;
   __shared__ double W[kMaxWindow * kMaxCols * kMaxCols];
-  reduce_values(part_W, cnt * C * C, kGramBlocks, kGramBlocks, W);
+  reduce_values(part_W, cnt * C * C, nchunks, nchunks, W);
   __syncthreads();
   for (int e = threadIdx.x; e < cnt * C * C; e += blockDim.x) {
     const int jj = e / (C * C), a = (e / C) % C, b = e % C;
@@ -180,67 +223,99 @@ __global__ void k_small_beta(DevState* st, const double* part_W, int C) {
   }
 }
 
-__global__ void k_small_alpha(DevState* st, const double* part_G, const double* part_zaz, int C,
-                              double* alpha_hist) {
+__global__ void k_small_alpha(DevState* st, const double* part_G, int nblk_G, const double* part_zaz, int nblk_zaz,
+                              int zaz_stride, int C, double* alpha_hist) {
   if (st->done) return;
   const int NG = C * (C + 1) / 2;
   __shared__ double red[kMaxCols * (kMaxCols + 1) / 2 + 2 * kMaxCols];
-  __shared__ double G[kPad * kPad], Gp[kPad * kPad], A[kPad * kPad], V[kPad * kPad];
-  __shared__ double dsc[kPad], rc[kPad], rs[kPad];
+  __shared__ double G[kPad * kPad], Gp[kPad * kPad], A[kPad * kPad], X[kPad * kPad], Ah[kPad * kPad];
+  __shared__ double dsc[kPad], rc[kPad], rs[kPad], lam[kPad];
   __shared__ int act[kPad], map[kPad], rp[kPad], rq[kPad];
-  reduce_values(part_G, NG + C, kRedBlocks, kRedBlocks, red);
-  reduce_values(part_zaz, C, kRedBlocks, kRedBlocks, red + NG + C);
+  __shared__ int nact_sh;
+  reduce_values(part_G, NG + C, nblk_G, nblk_G, red);
+  reduce_values(part_zaz, C, nblk_zaz, zaz_stride, red + NG + C);
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  if (lane == 0) {
     // G = sym(P^T A P): the partials hold p_a ap_b + p_b ap_a for a <= b
-    for (int e = lane; e < kPad * kPad; e += 32) G[e] = 0.0;
-    __syncwarp();
-    if (lane == 0) {
-      int k = 0, nact = 0;
-      for (int a = 0; a < C; ++a)
-        for (int b = a; b < C; ++b) {
-          const double v = 0.5 * red[k++];
-          G[a * kPad + b] = v;
-          G[b * kPad + a] = v;
-        }
-      int bad = 0;
-      for (int a = 0; a < C; ++a) {
-        const double pap = G[a * kPad + a], zaz = red[NG + C + a];
-        if (!isfinite(pap) || !isfinite(zaz)) bad = 1;
-        act[a] = pap > st->delta * zaz ? 1 : 0;
-        nact += act[a];
+    int k = 0, na = 0, bad = 0;
+    for (int a = 0; a < C; ++a)
+      for (int b = a; b < C; ++b) {
+        const double v = 0.5 * red[k++];
+        G[a * kPad + b] = v;
+        G[b * kPad + a] = v;
       }
-      for (int a = 0; a < C; ++a)
-        if (!act[a]) {
-          for (int b = 0; b < C; ++b) G[a * kPad + b] = G[b * kPad + a] = 0.0;
-          st->dropped_total += 1;
-        }
-      if (bad || nact == 0) st->done = 3;
+    for (int a = 0; a < C; ++a) {
+      const double pap = G[a * kPad + a], zaz = red[NG + C + a];
+      if (!isfinite(pap) || !isfinite(zaz)) bad = 1;
+      act[a] = (pap > st->delta * zaz && pap > 0.0) ? 1 : 0;   // column-drop rule
+      if (act[a]) map[na++] = a;
+      else st->dropped_total += 1;
+    }
+    nact_sh = na;
+    if (bad || na == 0) st->done = 3;
+  }
+  __syncwarp();
+  const int na = nact_sh;
+  for (int e = lane; e < kPad * kPad; e += 32) Gp[e] = 0.0;
+  if (lane < na) dsc[lane] = rsqrt(G[map[lane] * kPad + map[lane]]);
+  __syncwarp();
+  if (na > 0) {
+    for (int e = lane; e < kPad * kPad; e += 32) {
+      const int i = e / kPad, j = e % kPad;
+      A[e] = (i < na && j < na) ? dsc[i] * G[map[i] * kPad + map[j]] * dsc[j] : 0.0;
     }
     __syncwarp();
-    warp_pinv(G, act, C, st->tau, Gp, A, V, dsc, map, rc, rs, rp, rq);
-    const int ns = (st->newest + 1) % st->m;
-    for (int e = lane; e < C * C; e += 32) st->gpinv[ns][e / C][e % C] = Gp[(e / C) * kPad + e % C];
-    if (lane < C) {
-      double s = 0.0;
-      for (int b = 0; b < C; ++b) s += Gp[lane * kPad + b] * red[NG + b];
-      st->alpha[lane] = s;
-      if (alpha_hist) alpha_hist[(long long)st->k * C + lane] = s;
+    const bool ok = warp_chol_inverse(A, X, na, st->tau, Ah, lam);
+    if (!ok) {
+      for (int e = lane; e < kPad * kPad; e += 32) {
+        const int i = e / kPad, j = e % kPad;
+        A[e] = (i < na && j < na) ? dsc[i] * G[map[i] * kPad + map[j]] * dsc[j] : 0.0;
+      }
+      __syncwarp();
+      warp_jacobi_pinv(A, X, na, st->tau, Ah, rc, rs, rp, rq, lam);
+    }
+    for (int e = lane; e < na * na; e += 32) {
+      const int i = e / na, j = e % na;
+      Gp[map[i] * kPad + map[j]] = dsc[i] * Ah[i * kPad + j] * dsc[j];
     }
     __syncwarp();
-    if (lane == 0) {
-      st->newest = ns;
-      if (st->count < st->m) st->count += 1;
-    }
+  }
+  const int ns = (st->newest + 1) % st->m;
+  for (int e = lane; e < C * C; e += 32) st->gpinv[ns][e / C][e % C] = Gp[(e / C) * kPad + e % C];
+  if (lane < C) {
+    double s = 0.0;
+    for (int b = 0; b < C; ++b) s += Gp[lane * kPad + b] * red[NG + b];
+    st->alpha[lane] = s;
+    if (alpha_hist) alpha_hist[(long long)st->k * C + lane] = s;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    st->newest = ns;
+    if (st->count < st->m) st->count += 1;
   }
 }
 
 __global__ void k_check(DevState* st, const double* part_r, int nblk, double* res_hist,
                         cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ double v[1];
+  __shared__ double w[kBlock / 32];
   const int was_done = st->done;
-  if (!was_done) reduce_values(part_r, 1, nblk, kRedBlocks, v);
+  if (!was_done) {
+    // one value: every thread takes a strided share, then a fixed tree
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) a += part_r[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += w[i];
+      v[0] = t;
+    }
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     int done = was_done;
@@ -274,8 +349,9 @@ __global__ void k_dense_from_stencil(GridDesc g, const double* __restrict__ st, 
   }
 }
 
-// Right-looking dense Cholesky A = L L^T (lower triangle overwritten), one block.
-__global__ void k_cholesky(double* a, int n, int* info) {
+// Right-looking dense Cholesky A = L L^T (lower triangle overwritten), one
+// block; rdiag[i] = 1 / L_ii for the solves.
+__global__ void k_cholesky(double* a, double* rdiag, int n, int* info) {
   __shared__ int fail;
   if (threadIdx.x == 0) fail = 0;
   __syncthreads();
@@ -283,12 +359,16 @@ __global__ void k_cholesky(double* a, int n, int* info) {
     if (threadIdx.x == 0) {
       const double piv = a[(long long)k * n + k];
       if (!(piv > 0.0) || !isfinite(piv)) fail = k + 1;
-      else a[(long long)k * n + k] = sqrt(piv);
+      else {
+        const double l = sqrt(piv);
+        a[(long long)k * n + k] = l;
+        rdiag[k] = 1.0 / l;
+      }
     }
     __syncthreads();
     if (fail) break;
-    const double lkk = a[(long long)k * n + k];
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) a[(long long)i * n + k] /= lkk;
+    const double rk = rdiag[k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) a[(long long)i * n + k] *= rk;
     __syncthreads();
     const int m = n - k - 1;
     for (long long e = threadIdx.x; e < (long long)m * m; e += blockDim.x) {
@@ -301,13 +381,19 @@ __global__ void k_cholesky(double* a, int n, int* info) {
 }
 
 // out = A0^{-1} r by forward and backward substitution with the Cholesky
-// factor; one warp, column-oriented.
+// factor; one warp, column-oriented, the factor staged in shared memory.
 template <typename T>
-__global__ void k_coarse_solve(GridDesc g, const double* __restrict__ L, const T* __restrict__ r, T* __restrict__ out,
-                               const DevState* state) {
+__global__ void k_coarse_solve(GridDesc g, const double* __restrict__ L, const double* __restrict__ rdiag,
+                               const T* __restrict__ r, T* __restrict__ out, const DevState* state) {
   if (state && state->done) return;
-  extern __shared__ double y[];
+  extern __shared__ double sm[];
   const int n = (int)g.n, lane = threadIdx.x;
+  double* y = sm;
+  double* Ls = sm + n;
+  const bool stage = n <= 64;
+  if (stage)
+    for (int e = lane; e < n * n; e += 32) Ls[e] = L[e];
+  const double* Lp = stage ? Ls : L;
   auto padded = [&](int i) {
     const int x = i % g.n1, yy = (i / g.n1) % g.n1, z = i / (g.n1 * g.n1);
     return g.G + x + (long long)g.p * yy + (long long)g.p * g.p * z;
@@ -315,24 +401,24 @@ __global__ void k_coarse_solve(GridDesc g, const double* __restrict__ L, const T
   for (int i = lane; i < n; i += 32) y[i] = (double)r[padded(i)];
   __syncwarp();
   for (int i = 0; i < n; ++i) {
-    const double yi = y[i] / L[(long long)i * n + i];
+    const double yi = y[i] * rdiag[i];
     __syncwarp();
     if (lane == 0) y[i] = yi;
-    for (int k = i + 1 + lane; k < n; k += 32) y[k] -= L[(long long)k * n + i] * yi;
+    for (int k = i + 1 + lane; k < n; k += 32) y[k] -= Lp[(long long)k * n + i] * yi;
     __syncwarp();
   }
   for (int i = n - 1; i >= 0; --i) {
-    const double xi = y[i] / L[(long long)i * n + i];
+    const double xi = y[i] * rdiag[i];
     __syncwarp();
     if (lane == 0) y[i] = xi;
-    for (int k = lane; k < i; k += 32) y[k] -= L[(long long)i * n + k] * xi;
+    for (int k = lane; k < i; k += 32) y[k] -= Lp[(long long)i * n + k] * xi;
     __syncwarp();
   }
   for (int i = lane; i < n; i += 32) out[padded(i)] = (T)y[i];
 }
 
 __global__ void k_sum_partials(const double* part, int nv, int nblk, double* out) {
-  reduce_values(part, nv, nblk, kRedBlocks, out);
+  reduce_values(part, nv, nblk, nblk, out);
 }
 
 __global__ void k_axpy_mixed(GridDesc g, double* __restrict__ x, const float* __restrict__ d,
@@ -365,12 +451,12 @@ void launch_init(DevState* st, const double* part_res, int nblk, double* res_his
                  int use_cond, cudaStream_t s) {
   k_init<<<1, kBlock, 0, s>>>(st, part_res, nblk, res_hist, cond, use_cond);
 }
-void launch_small_beta(DevState* st, const double* part_W, int C, cudaStream_t s) {
-  k_small_beta<<<1, 1024, 0, s>>>(st, part_W, C);
+void launch_small_beta(DevState* st, const double* part_W, int nchunks, int C, cudaStream_t s) {
+  k_small_beta<<<1, 1024, 0, s>>>(st, part_W, nchunks, C);
 }
-void launch_small_alpha(DevState* st, const double* part_G, const double* part_zaz, int C, double* alpha_hist,
-                        cudaStream_t s) {
-  k_small_alpha<<<1, kBlock, 0, s>>>(st, part_G, part_zaz, C, alpha_hist);
+void launch_small_alpha(DevState* st, const double* part_G, int nblk_G, const double* part_zaz, int nblk_zaz,
+                        int zaz_stride, int C, double* alpha_hist, cudaStream_t s) {
+  k_small_alpha<<<1, kBlock, 0, s>>>(st, part_G, nblk_G, part_zaz, nblk_zaz, zaz_stride, C, alpha_hist);
 }
 void launch_check(DevState* st, const double* part_r, int nblk, double* res_hist, cudaGraphConditionalHandle cond,
                   int use_cond, cudaStream_t s) {
@@ -379,16 +465,19 @@ void launch_check(DevState* st, const double* part_r, int nblk, double* res_hist
 void launch_dense_from_stencil(const GridDesc& g, const double* st, double* dense, cudaStream_t s) {
   k_dense_from_stencil<<<(int)((g.n + 127) / 128), 128, 0, s>>>(g, st, dense);
 }
-void launch_cholesky(double* a, int n, int* info, cudaStream_t s) { k_cholesky<<<1, 512, 0, s>>>(a, n, info); }
-template <typename T>
-void launch_coarse_solve(const GridDesc& g, const double* L, const T* r, T* out, const DevState* state,
-                         cudaStream_t s) {
-  k_coarse_solve<T><<<1, 32, (size_t)g.n * sizeof(double), s>>>(g, L, r, out, state);
+void launch_cholesky(double* a, double* rdiag, int n, int* info, cudaStream_t s) {
+  k_cholesky<<<1, 512, 0, s>>>(a, rdiag, n, info);
 }
-template void launch_coarse_solve<double>(const GridDesc&, const double*, const double*, double*, const DevState*,
-                                          cudaStream_t);
-template void launch_coarse_solve<float>(const GridDesc&, const double*, const float*, float*, const DevState*,
-                                         cudaStream_t);
+template <typename T>
+void launch_coarse_solve(const GridDesc& g, const double* L, const double* rdiag, const T* r, T* out,
+                         const DevState* state, cudaStream_t s) {
+  const size_t sh = (size_t)g.n * sizeof(double) * (g.n <= 64 ? g.n + 1 : 1);
+  k_coarse_solve<T><<<1, 32, sh, s>>>(g, L, rdiag, r, out, state);
+}
+template void launch_coarse_solve<double>(const GridDesc&, const double*, const double*, const double*, double*,
+                                          const DevState*, cudaStream_t);
+template void launch_coarse_solve<float>(const GridDesc&, const double*, const double*, const float*, float*,
+                                         const DevState*, cudaStream_t);
 void launch_sum_partials(const double* part, int nv, int nblk, double* out, cudaStream_t s) {
   k_sum_partials<<<1, kBlock, 0, s>>>(part, nv, nblk, out);
 }
