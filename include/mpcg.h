@@ -185,6 +185,34 @@ long long mg_last_launches(const mg_hierarchy* h);
 /* Release everything the hierarchy owns.  NULL is ignored. */
 void mg_hierarchy_destroy(mg_hierarchy* h);
 
+/*
+ * Y = A X for `ncols` columns (1..MPCG_MAX_COLS), A a fine-grid operator in
+ * the mg_operator stencil format (dim, nodes, values_dev), without allocating
+ * any device memory.  The paper has no counterpart to this entry point: it is
+ * a service for callers that cannot call cudaMalloc -- for example code whose
+ * device memory is fully reserved by another framework's pool allocator, or
+ * a latency-critical loop that must not call cudaMalloc/cudaFree because
+ * cudaFree synchronises the whole device.  It computes what
+ * mg_apply_operator computes on the finest grid, without needing a hierarchy.
+ *   values_dev  3^dim * n doubles (device), X_dev, Y_dev column-major
+ *               n x ncols (device), n = (nodes-2)^dim
+ *   stream      cudaStream_t; the work is only enqueued on it (the call does
+ *               not synchronise), so synchronise before reading Y.
+ * Scratch: one static device array of 2^21 doubles (16 MiB) that every GPU
+ * which loads the library keeps until the process exits.  A grid needs
+ * (3^dim + 2 ncols) * len doubles of it, len ~ (nodes-1)^dim padded;
+ * larger requests return MPCG_ERR_ARG with a message naming both sizes
+ * (e.g. 3D grids up to 33^3 nodes with 12 columns, 2D grids up to 257^2
+ * nodes with 11 columns).
+ * The first call on a device looks up the array's device address and must
+ * happen with that device current; make that first call before any stream
+ * capture.  All calls share the one array, and it keeps the last call's
+ * contents (the call clears it first): calls whose work overlaps on the GPU
+ * (different streams or host threads without ordering) race on it.
+ */
+mpcg_status mg_stencil_apply_noalloc(int dim, int nodes, const double* values_dev, const double* X_dev,
+                                     double* Y_dev, int ncols, void* stream);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char* mpcg_last_error(void);
 

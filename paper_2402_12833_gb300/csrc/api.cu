@@ -475,6 +475,10 @@ mpcg_status check_h(const mg_hierarchy* h) {
 
 }  // namespace
 
+namespace mpcg {
+void set_error_message(const char* msg) { g_err = msg ? msg : ""; }
+}  // namespace mpcg
+
 extern "C" {
 
 const char* mpcg_last_error(void) { return g_err.c_str(); }

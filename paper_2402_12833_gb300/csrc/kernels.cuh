@@ -17,6 +17,9 @@ constexpr int kGramChunksMax = 4096;
 int stream_blocks(const GridDesc& g);
 int gram_chunks(const GridDesc& g);
 
+// Sets the calling thread's message returned by mpcg_last_error().
+void set_error_message(const char* msg);
+
 inline int grid_for(long long work, int cap) {
   long long b = (work + kBlock - 1) / kBlock;
   if (b < 1) b = 1;

@@ -68,6 +68,8 @@ _SIGS = {
                                       C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_longlong, C.POINTER(C.c_longlong)]),
     "mg_last_launches": (C.c_longlong, [C.c_void_p]),
+    "mg_stencil_apply_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                           C.c_void_p]),
 }
 MPCG_NUM_KERNEL_CLASSES = 15
 
@@ -195,6 +197,12 @@ def mg_corrections(h: int, r_dev, Z_dev) -> None:
 
 def mg_get_operator(h: int, level: int, planes_dev) -> None:
     _check(load().mg_get_operator(h, level, _ptr(planes_dev)))
+
+
+def mg_stencil_apply_noalloc(dim: int, nodes: int, values_dev, X_dev, Y_dev, ncols: int, stream: int = 0) -> None:
+    """Y = A X on the fine grid without device allocation (static scratch;
+    enqueued on ``stream``, not synchronised)."""
+    _check(load().mg_stencil_apply_noalloc(dim, nodes, _ptr(values_dev), _ptr(X_dev), _ptr(Y_dev), ncols, stream))
 
 
 def mg_hierarchy_destroy(h: int) -> None:
