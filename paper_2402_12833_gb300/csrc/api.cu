@@ -250,8 +250,8 @@ mpcg_status build_solver(mg_hierarchy* h, Solver<T>& S) {
     }
   }
   CKS(S.mem.get(&S.state, 1, s));
-  CKS(S.mem.get(&S.part_res, 2 * kRedBlocks, s));
-  CKS(S.mem.get(&S.part_zaz, (size_t)C * kRedBlocks, s));
+  CKS(S.mem.get(&S.part_res, 2 * (size_t)stream_blocks(gf), s));
+  CKS(S.mem.get(&S.part_zaz, (size_t)C * stream_blocks(gf), s));
   CKS(S.mem.get(&S.part_W, (size_t)S.m * C * C * gram_chunks(gf), s));
   CKS(S.mem.get(&S.part_G, (size_t)(C * (C + 1) / 2 + C) * stream_blocks(gf), s));
   CKS(S.mem.get(&S.part_r, stream_blocks(gf), s));
@@ -321,7 +321,7 @@ void enqueue_prologue(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle 
                       cudaStream_t s) {
   const Level& L = h->lev[h->levels - 1];
   LAUNCH(h, K_RESIDUAL, s, launch_residual<T>(L.g, st_of<T>(L), S.b, S.x, S.r, S.part_res, s));
-  LAUNCH(h, K_INIT, s, launch_init(S.state, S.part_res, kRedBlocks, S.res_hist, cond, use_cond, s));
+  LAUNCH(h, K_INIT, s, launch_init(S.state, S.part_res, stream_blocks(L.g), S.res_hist, cond, use_cond, s));
 }
 
 template <typename T>
@@ -333,7 +333,7 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
   LAUNCH(h, K_GRAM, s, launch_gram_window<T>(L.g, S.win, S.Z, C, S.m, S.part_W, S.state, s));
   LAUNCH(h, K_BETA, s, launch_small_beta(S.state, S.part_W, gram_chunks(L.g), C, s));
   LAUNCH(h, K_ORTH, s, launch_orth_update<T>(L.g, S.win, S.Z, S.AZ, S.r, C, S.part_G, S.state, s));
-  LAUNCH(h, K_ALPHA, s, launch_small_alpha(S.state, S.part_G, stream_blocks(L.g), S.part_zaz, grid_for(L.g.npts, kRedBlocks), kRedBlocks, C,
+  LAUNCH(h, K_ALPHA, s, launch_small_alpha(S.state, S.part_G, stream_blocks(L.g), S.part_zaz, stream_blocks(L.g), stream_blocks(L.g), C,
                                           S.alpha_hist, s));
   LAUNCH(h, K_UPDATE, s, launch_update_xr<T>(L.g, S.win, S.x, S.r, C, S.part_r, S.state, s));
   LAUNCH(h, K_CHECK, s, launch_check(S.state, S.part_r, stream_blocks(L.g), S.res_hist, cond, use_cond, s));
@@ -459,7 +459,7 @@ mpcg_status build_f32(mg_hierarchy* h) {
   CKS(h->mem.get(&h->x64, gf.len, s));
   CKS(h->mem.get(&h->r64, gf.len, s));
   CKS(h->mem.get(&h->nrm, 4, s));
-  CKS(h->mem.get(&h->part_mix, 2 * kRedBlocks, s));
+  CKS(h->mem.get(&h->part_mix, 2 * (size_t)stream_blocks(gf), s));
   CK(cudaGetLastError());
   h->have32 = true;
   return MPCG_OK;
@@ -542,8 +542,8 @@ mpcg_status mg_hierarchy_setup(const mg_operator* A, int levels, const mpcg_opti
     return MPCG_ERR_ARG;
   }
   const int q = A->nodes - 1;
-  if (q < 2 || (q & (q - 1)) != 0 || q > (1 << 15)) {
-    set_err("nodes - 1 must be a power of two in [2, 32768] (nodes = %d)", A->nodes);
+  if (q < 4 || (q & (q - 1)) != 0 || q > (1 << 15)) {
+    set_err("nodes - 1 must be a power of two in [4, 32768] (nodes = %d)", A->nodes);
     return MPCG_ERR_ARG;
   }
   int k = 0;
@@ -664,7 +664,7 @@ static mpcg_status solve_mixed(mg_hierarchy* h, const double* b, double* x, doub
   std::vector<double> inner(maxit + 1);
   for (int outer = 0; outer <= h->opt.max_outer; ++outer) {
     LAUNCH(h, K_RESIDUAL, s, launch_residual<double>(gf, L.st64, h->b64, h->x64, h->r64, h->part_mix, s));
-    LAUNCH(h, K_AUX, s, launch_sum_partials(h->part_mix, 2, kRedBlocks, h->nrm, s));
+    LAUNCH(h, K_AUX, s, launch_sum_partials(h->part_mix, 2, stream_blocks(gf), h->nrm, s));
     double nrm[2];
     CK(cudaMemcpyAsync(nrm, h->nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

@@ -9,67 +9,14 @@
 // harmlessly) in 16-byte vectors: 4 floats or 2 doubles per thread and step.
 // Reductions are deterministic: every block writes its partial sums
 // (value-major, fixed block count) and one small kernel adds them in a fixed
-// order.  Partial sums accumulate in FP64; in the FP32 path each thread first
-// sums its own products in FP32 over at most 64 points.
+// order.  In the FP32 path each thread sums at most 64 points in FP32 and the
+// warp adds its 32 lanes in FP32; everything above the warp is FP64.
 #include "kernels.cuh"
+#include "vec.cuh"
 
 namespace mpcg {
 
 namespace {
-
-template <typename T>
-struct Vec;
-template <>
-struct Vec<float> {
-  using V = float4;
-  static constexpr int W = 4;
-  __device__ static __forceinline__ void load(const float* p, float (&v)[4]) {
-    const float4 q = __ldcs(reinterpret_cast<const float4*>(p));
-    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-  }
-  __device__ static __forceinline__ void load_keep(const float* p, float (&v)[4]) {
-    const float4 q = *reinterpret_cast<const float4*>(p);
-    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-  }
-  __device__ static __forceinline__ void store(float* p, const float (&v)[4]) {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  }
-};
-template <>
-struct Vec<double> {
-  using V = double2;
-  static constexpr int W = 2;
-  __device__ static __forceinline__ void load(const double* p, double (&v)[2]) {
-    const double2 q = __ldcs(reinterpret_cast<const double2*>(p));
-    v[0] = q.x; v[1] = q.y;
-  }
-  __device__ static __forceinline__ void load_keep(const double* p, double (&v)[2]) {
-    const double2 q = *reinterpret_cast<const double2*>(p);
-    v[0] = q.x; v[1] = q.y;
-  }
-  __device__ static __forceinline__ void store(double* p, const double (&v)[2]) {
-    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
-  }
-};
-
-template <int NV>
-__device__ __forceinline__ void block_sum_store(double (&v)[NV], double* part, int stride, int slot) {
-  __shared__ double sh[kBlock / 32][NV];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double a = v[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) sh[warp][i] = a;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < NV; i += blockDim.x) {
-    double a = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += sh[w][i];
-    part[(long long)i * stride + slot] = a;
-  }
-}
 
 // W_jj[a][b] = sum_i AP_slot(jj)[a][i] Z[b][i].  Block b works on window
 // block jj = b % m and on the contiguous point chunk b / m, so that the
@@ -90,12 +37,10 @@ __global__ void __launch_bounds__(kBlock) k_gram_window(GridDesc g, Window<T> wi
   const long long g0 = (long long)chunk * per;
   const long long g1 = g0 + per < ngroups ? g0 + per : ngroups;
   // the chunk count keeps every thread at <= 16 vector groups (64 points in
-  // FP32) before its partial sums are widened to FP64
-  T acc[C][C];
+  // FP32) before its partial sums enter the reduction
+  T acc[C * C];
 #pragma unroll
-  for (int a = 0; a < C; ++a)
-#pragma unroll
-    for (int b = 0; b < C; ++b) acc[a][b] = 0;
+  for (int e = 0; e < C * C; ++e) acc[e] = 0;
   for (long long q = g0 + threadIdx.x; q < g1; q += blockDim.x) {
     const long long i = q * W;
     T z[C][W], ap[C][W];
@@ -108,15 +53,10 @@ __global__ void __launch_bounds__(kBlock) k_gram_window(GridDesc g, Window<T> wi
 #pragma unroll
       for (int b = 0; b < C; ++b)
 #pragma unroll
-        for (int w = 0; w < W; ++w) acc[a][b] = fma(ap[a][w], z[b][w], acc[a][b]);
+        for (int w = 0; w < W; ++w) acc[a * C + b] = fma(ap[a][w], z[b][w], acc[a * C + b]);
   }
-  double accd[C * C];
-#pragma unroll
-  for (int a = 0; a < C; ++a)
-#pragma unroll
-    for (int b = 0; b < C; ++b) accd[a * C + b] = (double)acc[a][b];
   double* pj = part + (long long)jj * C * C * nchunks;
-  block_sum_store<C * C>(accd, pj, nchunks, chunk);
+  block_sum_store<T, C * C>(acc, pj, nchunks, chunk);
 }
 
 template <typename T, int C>
@@ -200,10 +140,7 @@ __global__ void __launch_bounds__(kBlock) k_orth_update(GridDesc g, Window<T> wi
       for (int w = 0; w < W; ++w) acc[NG + a] = fma(p[a][w], rv[w], acc[NG + a]);
     }
   }
-  double accd[NG + C];
-#pragma unroll
-  for (int i = 0; i < NG + C; ++i) accd[i] = (double)acc[i];
-  block_sum_store<NG + C>(accd, part, gridDim.x, blockIdx.x);
+  block_sum_store<T, NG + C>(acc, part, gridDim.x, blockIdx.x);
 }
 
 template <typename T, int C>
@@ -219,7 +156,7 @@ __global__ void __launch_bounds__(kBlock) k_update_xr(GridDesc g, Window<T> win,
 #pragma unroll
   for (int a = 0; a < C; ++a) al[a] = (T)state->alpha[a];
   constexpr int W = Vec<T>::W;
-  T acc = 0;
+  T acc[1] = {0};
   const long long ngroups = g.npts / W;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
        q += (long long)gridDim.x * blockDim.x) {
@@ -243,13 +180,12 @@ __global__ void __launch_bounds__(kBlock) k_update_xr(GridDesc g, Window<T> win,
     for (int w = 0; w < W; ++w) {
       xv[w] += px[w];
       rv[w] -= apx[w];
-      acc = fma(rv[w], rv[w], acc);
+      acc[0] = fma(rv[w], rv[w], acc[0]);
     }
     Vec<T>::store(xb + i, xv);
     Vec<T>::store(rb + i, rv);
   }
-  double v[1] = {(double)acc};
-  block_sum_store<1>(v, part, gridDim.x, blockIdx.x);
+  block_sum_store<T, 1>(acc, part, gridDim.x, blockIdx.x);
 }
 
 }  // namespace
@@ -272,8 +208,8 @@ __global__ void __launch_bounds__(kBlock) k_update_xr(GridDesc g, Window<T> win,
   }
 
 int gram_chunks(const GridDesc& g) {
-  // at most 16 vector groups (64 points) per thread and chunk
-  const long long groups = g.npts / 2;   // conservative for both vector widths
+  // 16 vector groups (64 points in FP32, 32 in FP64) per thread and chunk
+  const long long groups = g.npts / 4;
   long long c = (groups + kBlock * 16 - 1) / (kBlock * 16);
   if (c < 1) c = 1;
   return (int)(c < kGramChunksMax ? c : kGramChunksMax);

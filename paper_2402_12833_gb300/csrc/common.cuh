@@ -10,8 +10,10 @@
 // address of (x = -1, y), the pad row of plane z-1 at (y = -1, z), and so on,
 // so one pad layer serves as the zero Dirichlet ghost on both sides of every
 // axis.  A guard of G = p*p + p + 1 (3D; p + 1 in 2D) zero elements in front
-// makes (-1,-1,-1) addressable (G is rounded up to a multiple of 32, and
-// every vector occupies len = G + p^dim rounded up to 32 elements).
+// makes (-1,-1,-1) addressable (G is rounded up to a multiple of 32); a second
+// zero guard of G elements follows the box, so every vector occupies
+// len = 2G + p^dim rounded up to 32 elements and every neighbour of every
+// box entry, pads included, lies inside the vector's own zeroed storage.
 // Stencils therefore need no boundary tests,
 // interpolation reads zero parents outside the grid, and sums over a whole
 // padded array equal sums over the interior unknowns.
@@ -54,7 +56,10 @@ inline GridDesc make_grid(int dim, int n1) {
   const long long guard = dim == 3 ? p * p + p + 1 : p + 1;
   g.G = (guard + 31) / 32 * 32;
   g.npts = dim == 3 ? p * p * p : p * p;
-  g.len = (g.G + g.npts + 31) / 32 * 32;
+  // a zero guard of G elements after the box as well: the vectorised stencil
+  // kernels evaluate pad entries too, and the neighbours of the last pad
+  // plane reach up to p*p + p elements past the box
+  g.len = (2 * g.G + g.npts + 31) / 32 * 32;
   g.n = dim == 3 ? (long long)n1 * n1 * n1 : (long long)n1 * n1;
   return g;
 }

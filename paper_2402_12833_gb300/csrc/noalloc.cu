@@ -58,8 +58,8 @@ extern "C" mpcg_status mg_stencil_apply_noalloc(int dim, int nodes, const double
   using namespace mpcg;
   if (dim != 2 && dim != 3) return fail(MPCG_ERR_ARG, "mg_stencil_apply_noalloc: dim must be 2 or 3");
   const int q = nodes - 1;
-  if (q < 2 || (q & (q - 1)) != 0 || q > (1 << 15))
-    return fail(MPCG_ERR_ARG, "mg_stencil_apply_noalloc: nodes - 1 must be a power of two >= 2");
+  if (q < 4 || (q & (q - 1)) != 0 || q > (1 << 15))
+    return fail(MPCG_ERR_ARG, "mg_stencil_apply_noalloc: nodes - 1 must be a power of two >= 4");
   if (ncols < 1 || ncols > MPCG_MAX_COLS)
     return fail(MPCG_ERR_ARG, "mg_stencil_apply_noalloc: ncols must be in 1..MPCG_MAX_COLS");
   if (!values_dev || !X_dev || !Y_dev) return fail(MPCG_ERR_ARG, "mg_stencil_apply_noalloc: NULL pointer");

@@ -3,45 +3,18 @@
 // (Section 2.1), damped-Jacobi smoothing (Eq. 3), and the Galerkin product
 // P^T A P that builds the coarse operators.
 //
-// All kernels work on the padded layout described in common.cuh: one thread
-// per entry of the padded box, pad entries written as zero.
+// The stencil kernels work on the padded layout described in common.cuh and
+// give every thread a group of W consecutive x-points (W = 4 floats or
+// 2 doubles: one 16-byte load per stencil plane and per grid row, plus one
+// scalar on each side for the x-neighbours).  Stencil coefficients are zero
+// at pad entries, so every output at a pad entry is exactly zero without a
+// test.
 #include "kernels.cuh"
+#include "vec.cuh"
 
 namespace mpcg {
 
 namespace {
-
-__device__ __forceinline__ void decode(const GridDesc& g, long long t, int& x, int& y, int& z) {
-  const int mask = g.p - 1;
-  x = (int)(t & mask);
-  y = (int)((t >> g.lp) & mask);
-  z = (int)(t >> (2 * g.lp));
-}
-
-__device__ __forceinline__ bool interior(const GridDesc& g, int x, int y, int z) {
-  return x < g.n1 && y < g.n1 && (g.dim == 2 || z < g.n1);
-}
-
-// Sum NV per-thread values over the block, written value-major to
-// part[v * stride + blockIdx.x].  Fixed reduction order (deterministic).
-template <int NV>
-__device__ __forceinline__ void block_sum_store(double (&v)[NV], double* part, int stride) {
-  __shared__ double sh[kBlock / 32][NV > 0 ? NV : 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double a = v[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) sh[warp][i] = a;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < NV; i += blockDim.x) {
-    double a = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += sh[w][i];
-    part[(long long)i * stride + blockIdx.x] = a;
-  }
-}
 
 // ---------------------------------------------------------------------------
 template <typename TI, typename TO>
@@ -74,86 +47,109 @@ __global__ void k_unpack(GridDesc g, const TI* __restrict__ src, TO* __restrict_
   }
 }
 
-// Apply the 3^DIM stencil at padded index idx to vector v.
-template <typename T, int DIM>
-__device__ __forceinline__ T stencil_apply(const T (&a)[DIM == 3 ? 27 : 9], const T* __restrict__ v,
-                                           long long idx, int p) {
-  T acc = 0;
-  const long long pp = (long long)p * p;
+// A grid row segment around a group: v[-1], v[0..W-1] (one aligned vector
+// load), v[W].  Returned as e[0..W+1] with e[k] = v[k-1].
+template <typename T>
+__device__ __forceinline__ void load_row(const T* __restrict__ p, T (&e)[Vec<T>::W + 2]) {
+  constexpr int W = Vec<T>::W;
+  T mid[W];
+  Vec<T>::load_keep(p, mid);
+  e[0] = p[-1];
 #pragma unroll
-  for (int dz = 0; dz < (DIM == 3 ? 3 : 1); ++dz) {
-#pragma unroll
-    for (int dy = 0; dy < 3; ++dy) {
-      const T* row = v + idx + (long long)(dy - 1) * p + (DIM == 3 ? (long long)(dz - 1) * pp : 0);
-      const int s = dz * 9 + dy * 3;
-      acc = fma(a[s + 0], row[-1], acc);
-      acc = fma(a[s + 1], row[0], acc);
-      acc = fma(a[s + 2], row[1], acc);
-    }
-  }
-  return acc;
+  for (int w = 0; w < W; ++w) e[w + 1] = mid[w];
+  e[W + 1] = p[W];
 }
 
-template <typename T, int DIM>
-__device__ __forceinline__ void load_stencil(T (&a)[DIM == 3 ? 27 : 9], const T* __restrict__ st, long long len,
-                                             long long idx) {
+// Row offsets of the 3^DIM stencil around the group start, row k = dy + 3 dz.
+template <int DIM>
+__device__ __forceinline__ long long row_offset(int k, long long p) {
+  const int dy = k % 3 - 1, dz = DIM == 3 ? k / 3 - 1 : 0;
+  return dy * p + dz * p * p;
+}
+
+// acc[c][w] += sum over the stencil of A(point w) * X_c(neighbour), C columns.
+template <typename T, int DIM, int C>
+__device__ __forceinline__ void stencil_group(const T* __restrict__ st, long long len, const T* __restrict__ X,
+                                              long long idx, long long p, T (&acc)[C][Vec<T>::W]) {
+  constexpr int W = Vec<T>::W;
+  constexpr int R = DIM == 3 ? 9 : 3;
 #pragma unroll
-  for (int s = 0; s < (DIM == 3 ? 27 : 9); ++s) a[s] = st[s * len + idx];
+  for (int k = 0; k < R; ++k) {
+    const long long ro = row_offset<DIM>(k, p);
+    T a0[W], a1[W], a2[W];
+    Vec<T>::load(st + (long long)(3 * k + 0) * len + idx, a0);
+    Vec<T>::load(st + (long long)(3 * k + 1) * len + idx, a1);
+    Vec<T>::load(st + (long long)(3 * k + 2) * len + idx, a2);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      T e[W + 2];
+      load_row<T>(X + (long long)c * len + idx + ro, e);
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        acc[c][w] = fma(a0[w], e[w], acc[c][w]);
+        acc[c][w] = fma(a1[w], e[w + 1], acc[c][w]);
+        acc[c][w] = fma(a2[w], e[w + 2], acc[c][w]);
+      }
+    }
+  }
 }
 
 template <typename T, int DIM, int C, bool ZAZ>
 __global__ void __launch_bounds__(kBlock) k_spmm(GridDesc g, const T* __restrict__ st, const T* __restrict__ X,
                                                  T* __restrict__ Y, double* zaz, const DevState* state) {
   if (state && state->done) return;
-  constexpr int S = DIM == 3 ? 27 : 9;
-  double acc[ZAZ ? C : 1];
+  constexpr int W = Vec<T>::W;
+  T zacc[ZAZ ? C : 1];
 #pragma unroll
-  for (int c = 0; c < (ZAZ ? C : 1); ++c) acc[c] = 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.npts;
-       t += (long long)gridDim.x * blockDim.x) {
-    int x, y, z;
-    decode(g, t, x, y, z);
-    const long long idx = g.G + t;
-    if (interior(g, x, y, z)) {
-      T a[S];
-      load_stencil<T, DIM>(a, st, g.len, idx);
+  for (int c = 0; c < (ZAZ ? C : 1); ++c) zacc[c] = 0;
+  const long long ngroups = g.npts / W;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long idx = g.G + q * W;
+    T acc[C][W];
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const T* Xc = X + (long long)c * g.len;
-        const T yv = stencil_apply<T, DIM>(a, Xc, idx, g.p);
-        Y[(long long)c * g.len + idx] = yv;
-        if (ZAZ) acc[c] += (double)Xc[idx] * (double)yv;
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int w = 0; w < W; ++w) acc[c][w] = 0;
+    stencil_group<T, DIM, C>(st, g.len, X, idx, g.p, acc);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      Vec<T>::store(Y + (long long)c * g.len + idx, acc[c]);
+      if (ZAZ) {
+        T xc[W];
+        Vec<T>::load_keep(X + (long long)c * g.len + idx, xc);
+#pragma unroll
+        for (int w = 0; w < W; ++w) zacc[c] = fma(xc[w], acc[c][w], zacc[c]);
       }
-    } else {
-#pragma unroll
-      for (int c = 0; c < C; ++c) Y[(long long)c * g.len + idx] = (T)0;
     }
   }
-  if (ZAZ) block_sum_store<ZAZ ? C : 1>(acc, zaz, kRedBlocks);
+  if (ZAZ) block_sum_store<T, ZAZ ? C : 1>(zacc, zaz, gridDim.x, blockIdx.x);
 }
 
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBlock) k_residual(GridDesc g, const T* __restrict__ st, const T* __restrict__ b,
                                                      const T* __restrict__ xv, T* __restrict__ r, double* part) {
-  constexpr int S = DIM == 3 ? 27 : 9;
-  double acc[2] = {0.0, 0.0};
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.npts;
-       t += (long long)gridDim.x * blockDim.x) {
-    int x, y, z;
-    decode(g, t, x, y, z);
-    const long long idx = g.G + t;
-    if (interior(g, x, y, z)) {
-      T a[S];
-      load_stencil<T, DIM>(a, st, g.len, idx);
-      const T rv = b[idx] - stencil_apply<T, DIM>(a, xv, idx, g.p);
-      r[idx] = rv;
-      acc[0] += (double)rv * (double)rv;
-      acc[1] += (double)b[idx] * (double)b[idx];
-    } else {
-      r[idx] = (T)0;
+  constexpr int W = Vec<T>::W;
+  T sums[2] = {0, 0};
+  const long long ngroups = g.npts / W;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long idx = g.G + q * W;
+    T acc[1][W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) acc[0][w] = 0;
+    stencil_group<T, DIM, 1>(st, g.len, xv, idx, g.p, acc);
+    T bv[W], rv[W];
+    Vec<T>::load(b + idx, bv);
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      rv[w] = bv[w] - acc[0][w];
+      sums[0] = fma(rv[w], rv[w], sums[0]);
+      sums[1] = fma(bv[w], bv[w], sums[1]);
     }
+    Vec<T>::store(r + idx, rv);
   }
-  block_sum_store<2>(acc, part, kRedBlocks);
+  block_sum_store<T, 2>(sums, part, gridDim.x, blockIdx.x);
 }
 
 // Restriction R = P^T: coarse node I sits on fine node 2I+1 (per axis); the
@@ -188,94 +184,118 @@ __global__ void __launch_bounds__(kBlock) k_restrict(GridDesc gf, GridDesc gc, c
   rc[idc] = acc;
 }
 
-// Damped Jacobi (Eq. 3 with M = D / omega, dinv = omega / diag).
+// Damped Jacobi (Eq. 3 with M = D / omega, dinv = omega / diag), c_0 = 0:
+//   mode 0: out = dinv r                          (one sweep)
+//   mode 1: out = s1 + dinv (r - A s1), s1 = dinv r  (two sweeps, s1 formed
+//           at the neighbours on the fly)
+//   mode 2: out = sin + dinv (r - A sin)           (a further sweep)
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBlock) k_jacobi(GridDesc g, const T* __restrict__ st, const T* __restrict__ dinv,
                                                    const T* __restrict__ r, const T* __restrict__ sin,
                                                    T* __restrict__ out, int mode, const DevState* state) {
   if (state && state->done) return;
-  constexpr int S = DIM == 3 ? 27 : 9;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= g.npts) return;
-  int x, y, z;
-  decode(g, t, x, y, z);
-  const long long idx = g.G + t;
-  if (!interior(g, x, y, z)) {
-    out[idx] = (T)0;
-    return;
-  }
-  const T di = dinv[idx], ri = r[idx];
+  constexpr int W = Vec<T>::W;
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= g.npts / W) return;
+  const long long idx = g.G + q * W;
+  T di[W], ri[W], o[W];
+  Vec<T>::load_keep(dinv + idx, di);
+  Vec<T>::load_keep(r + idx, ri);
   if (mode == 0) {
-    out[idx] = di * ri;
+#pragma unroll
+    for (int w = 0; w < W; ++w) o[w] = di[w] * ri[w];
+    Vec<T>::store(out + idx, o);
     return;
   }
-  T a[S];
-  load_stencil<T, DIM>(a, st, g.len, idx);
+  T acc[1][W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) acc[0][w] = 0;
   if (mode == 1) {
-    // s1 = dinv r everywhere; s2 = s1 + dinv (r - A s1), evaluated with s1
-    // formed on the fly at the neighbours
-    const long long p = g.p, pp = p * p;
-    T acc = 0;
+    constexpr int R = DIM == 3 ? 9 : 3;
 #pragma unroll
-    for (int dz = 0; dz < (DIM == 3 ? 3 : 1); ++dz)
+    for (int k = 0; k < R; ++k) {
+      const long long ro = row_offset<DIM>(k, g.p);
+      T a0[W], a1[W], a2[W], ed[W + 2], er[W + 2];
+      Vec<T>::load(st + (long long)(3 * k + 0) * g.len + idx, a0);
+      Vec<T>::load(st + (long long)(3 * k + 1) * g.len + idx, a1);
+      Vec<T>::load(st + (long long)(3 * k + 2) * g.len + idx, a2);
+      load_row<T>(dinv + idx + ro, ed);
+      load_row<T>(r + idx + ro, er);
 #pragma unroll
-      for (int dy = 0; dy < 3; ++dy)
+      for (int w = 0; w < W; ++w) {
+        acc[0][w] = fma(a0[w], ed[w] * er[w], acc[0][w]);
+        acc[0][w] = fma(a1[w], ed[w + 1] * er[w + 1], acc[0][w]);
+        acc[0][w] = fma(a2[w], ed[w + 2] * er[w + 2], acc[0][w]);
+      }
+    }
 #pragma unroll
-        for (int dx = 0; dx < 3; ++dx) {
-          const long long o = (dx - 1) + (dy - 1) * p + (DIM == 3 ? (dz - 1) * pp : 0);
-          acc = fma(a[dz * 9 + dy * 3 + dx], dinv[idx + o] * r[idx + o], acc);
-        }
-    const T s1 = di * ri;
-    out[idx] = s1 + di * (ri - acc);
+    for (int w = 0; w < W; ++w) {
+      const T s1 = di[w] * ri[w];
+      o[w] = s1 + di[w] * (ri[w] - acc[0][w]);
+    }
   } else {
-    const T ax = stencil_apply<T, DIM>(a, sin, idx, g.p);
-    out[idx] = sin[idx] + di * (ri - ax);
+    stencil_group<T, DIM, 1>(st, g.len, sin, idx, g.p, acc);
+    T sv[W];
+    Vec<T>::load_keep(sin + idx, sv);
+#pragma unroll
+    for (int w = 0; w < W; ++w) o[w] = sv[w] + di[w] * (ri[w] - acc[0][w]);
   }
+  Vec<T>::store(out + idx, o);
 }
 
 // Prolongation P: bilinear / trilinear interpolation from the coarse grid.
+// A group of W fine points starting at even x0 needs the coarse values
+// x0/2 - 1 .. x0/2 + W/2 - 1 of each contributing coarse row:
+//   fine x0 + 2k     = (c[x0/2 + k - 1] + c[x0/2 + k]) / 2
+//   fine x0 + 2k + 1 =  c[x0/2 + k]
+// Parents outside the grid are pad entries of the coarse layout (zero).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBlock) k_prolong(GridDesc gc, GridDesc gf, const T* __restrict__ coarse,
                                                     T* __restrict__ fine, int ncols, const DevState* state) {
   if (state && state->done) return;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= gf.npts) return;
-  int x, y, z;
-  decode(gf, t, x, y, z);
-  const long long idf = gf.G + t;
-  if (!interior(gf, x, y, z)) {
-    for (int c = 0; c < ncols; ++c) fine[(long long)c * gf.len + idf] = (T)0;
-    return;
-  }
-  // per axis: parents (c0, c1) with weights (w0, w1); out-of-grid parents are
-  // pad entries of the coarse layout and read as zero
-  int cx0, cx1, cy0, cy1, cz0 = 0, cz1 = 0;
-  T wx0, wx1, wy0, wy1, wz0 = 1, wz1 = 0;
+  constexpr int W = Vec<T>::W;
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= gf.npts / W) return;
+  const long long t0 = q * W;
+  int x0, y, z;
+  decode(gf, t0, x0, y, z);
+  const long long idf = gf.G + t0;
+  // per axis: parents (c0, c1) with weights (w0, w1)
   auto par = [](int i, int& c0, int& c1, T& w0, T& w1) {
     if (i & 1) { c0 = c1 = i >> 1; w0 = (T)1; w1 = (T)0; }
     else { c0 = (i >> 1) - 1; c1 = i >> 1; w0 = w1 = (T)0.5; }
   };
-  par(x, cx0, cx1, wx0, wx1);
+  int cy0, cy1, cz0 = 0, cz1 = 0;
+  T wy0, wy1, wz0 = 1, wz1 = 0;
   par(y, cy0, cy1, wy0, wy1);
   if (DIM == 3) par(z, cz0, cz1, wz0, wz1);
   const long long pc = gc.p, ppc = pc * pc;
+  const int cx = x0 >> 1;
   for (int c = 0; c < ncols; ++c) {
     const T* C0 = coarse + (long long)c * gc.len + gc.G;
-    T acc = 0;
+    T row[W / 2 + 1];
+#pragma unroll
+    for (int k = 0; k <= W / 2; ++k) row[k] = 0;
 #pragma unroll
     for (int kz = 0; kz < (DIM == 3 ? 2 : 1); ++kz) {
-      const int cz = kz ? cz1 : cz0;
+      const int czz = kz ? cz1 : cz0;
       const T wz = kz ? wz1 : wz0;
 #pragma unroll
       for (int ky = 0; ky < 2; ++ky) {
-        const int cy = ky ? cy1 : cy0;
-        const T wy = ky ? wy1 : wy0;
-        const T* row = C0 + pc * cy + (DIM == 3 ? ppc * cz : 0);
-        acc = fma(wz * wy * wx0, row[cx0], acc);
-        acc = fma(wz * wy * wx1, row[cx1], acc);
+        const int cyy = ky ? cy1 : cy0;
+        const T wgt = wz * (ky ? wy1 : wy0);
+        const T* rp = C0 + pc * cyy + (DIM == 3 ? ppc * czz : 0) + cx - 1;
+#pragma unroll
+        for (int k = 0; k <= W / 2; ++k) row[k] = fma(wgt, rp[k], row[k]);
       }
     }
-    fine[(long long)c * gf.len + idf] = acc;
+    T o[W];
+#pragma unroll
+    for (int k = 0; k < W / 2; ++k) {
+      o[2 * k] = (T)0.5 * (row[k] + row[k + 1]);
+      o[2 * k + 1] = row[k + 1];
+    }
+    Vec<T>::store(fine + (long long)c * gf.len + idf, o);
   }
 }
 
@@ -316,12 +336,12 @@ __global__ void __launch_bounds__(kBlock) k_galerkin(GridDesc gf, GridDesc gc, c
             else { D0[k] = (f[k] - 1) / 2; D1[k] = (f[k] + 1) / 2; np[k] = 2; w[k] = 0.5; }
           }
           const double base = we * a * w[0] * w[1] * w[2];
-          const int C[3] = {X, Y, Z};
+          const int Cc[3] = {X, Y, Z};
           for (int iz = 0; iz < np[2]; ++iz)
             for (int iy = 0; iy < np[1]; ++iy)
               for (int ix = 0; ix < np[0]; ++ix) {
                 const int Dx = ix ? D1[0] : D0[0], Dy = iy ? D1[1] : D0[1], Dz = iz ? D1[2] : D0[2];
-                const int cx = C[0] + Dx, cy = C[1] + Dy, cz = C[2] + Dz;
+                const int cx = Cc[0] + Dx, cy = Cc[1] + Dy, cz = Cc[2] + Dz;
                 if (cx < 0 || cx >= nc || cy < 0 || cy >= nc) continue;
                 if (DIM == 3 && (cz < 0 || cz >= nc)) continue;
                 acc[(Dx + 1) + 3 * (Dy + 1) + (DIM == 3 ? 9 * (Dz + 1) : 0)] += base;
@@ -349,6 +369,9 @@ __global__ void k_convert_f32(const double* __restrict__ src, float* __restrict_
 
 inline int blocks_for(long long n) { return (int)((n + kBlock - 1) / kBlock); }
 
+template <typename T>
+constexpr int vw() { return 16 / (int)sizeof(T); }
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -368,7 +391,7 @@ template void launch_unpack<float, double>(const GridDesc&, const float*, double
 template <typename T, int DIM>
 static void spmm_dim(const GridDesc& g, const T* st, const T* X, T* Y, int C, double* zaz, const DevState* state,
                      cudaStream_t s) {
-  const int nb = grid_for(g.npts, kRedBlocks);
+  const int nb = stream_blocks(g);
 #define MPCG_SPMM_CASE(CC)                                                                      \
   case CC:                                                                                      \
     if (zaz) k_spmm<T, DIM, CC, true><<<nb, kBlock, 0, s>>>(g, st, X, Y, zaz, state);           \
@@ -396,7 +419,7 @@ template void launch_spmm<float>(const GridDesc&, const float*, const float*, fl
 
 template <typename T>
 void launch_residual(const GridDesc& g, const T* st, const T* b, const T* x, T* r, double* part, cudaStream_t s) {
-  const int nb = kRedBlocks;   // fixed so the partial count is known
+  const int nb = stream_blocks(g);
   if (g.dim == 3) k_residual<T, 3><<<nb, kBlock, 0, s>>>(g, st, b, x, r, part);
   else k_residual<T, 2><<<nb, kBlock, 0, s>>>(g, st, b, x, r, part);
 }
@@ -419,8 +442,9 @@ template void launch_restrict<float>(const GridDesc&, const GridDesc&, const flo
 template <typename T>
 void launch_jacobi(const GridDesc& g, const T* st, const T* dinv, const T* r, const T* sin, T* out, int mode,
                    const DevState* state, cudaStream_t s) {
-  if (g.dim == 3) k_jacobi<T, 3><<<blocks_for(g.npts), kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
-  else k_jacobi<T, 2><<<blocks_for(g.npts), kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
+  const int nb = blocks_for(g.npts / vw<T>());
+  if (g.dim == 3) k_jacobi<T, 3><<<nb, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
+  else k_jacobi<T, 2><<<nb, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
 }
 template void launch_jacobi<double>(const GridDesc&, const double*, const double*, const double*, const double*,
                                     double*, int, const DevState*, cudaStream_t);
@@ -430,8 +454,9 @@ template void launch_jacobi<float>(const GridDesc&, const float*, const float*, 
 template <typename T>
 void launch_prolong(const GridDesc& gc, const GridDesc& gf, const T* coarse, T* fine, int ncols,
                     const DevState* state, cudaStream_t s) {
-  if (gf.dim == 3) k_prolong<T, 3><<<blocks_for(gf.npts), kBlock, 0, s>>>(gc, gf, coarse, fine, ncols, state);
-  else k_prolong<T, 2><<<blocks_for(gf.npts), kBlock, 0, s>>>(gc, gf, coarse, fine, ncols, state);
+  const int nb = blocks_for(gf.npts / vw<T>());
+  if (gf.dim == 3) k_prolong<T, 3><<<nb, kBlock, 0, s>>>(gc, gf, coarse, fine, ncols, state);
+  else k_prolong<T, 2><<<nb, kBlock, 0, s>>>(gc, gf, coarse, fine, ncols, state);
 }
 template void launch_prolong<double>(const GridDesc&, const GridDesc&, const double*, double*, int,
                                      const DevState*, cudaStream_t);

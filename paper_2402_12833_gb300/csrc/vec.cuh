@@ -1,0 +1,81 @@
+// Device helpers shared by the streaming kernels: 16-byte vector access to
+// the padded arrays (4 floats or 2 doubles per thread and step) and
+// deterministic block reductions that write value-major partial sums.
+#pragma once
+
+#include "common.cuh"
+
+namespace mpcg {
+
+template <typename T>
+struct Vec;
+
+template <>
+struct Vec<float> {
+  static constexpr int W = 4;
+  // streamed once: evict-first
+  __device__ static __forceinline__ void load(const float* p, float (&v)[4]) {
+    const float4 q = __ldcs(reinterpret_cast<const float4*>(p));
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
+  // re-read by neighbours or other blocks: default caching
+  __device__ static __forceinline__ void load_keep(const float* p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
+  __device__ static __forceinline__ void store(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+
+template <>
+struct Vec<double> {
+  static constexpr int W = 2;
+  __device__ static __forceinline__ void load(const double* p, double (&v)[2]) {
+    const double2 q = __ldcs(reinterpret_cast<const double2*>(p));
+    v[0] = q.x; v[1] = q.y;
+  }
+  __device__ static __forceinline__ void load_keep(const double* p, double (&v)[2]) {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x; v[1] = q.y;
+  }
+  __device__ static __forceinline__ void store(double* p, const double (&v)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+
+// Block sum of NV per-thread values, written to part[i * stride + slot].
+// The warp stage sums in T (FP32 in the FP32 path: a fixed pairwise tree over
+// 32 lanes); the cross-warp stage sums in FP64 in a fixed order.  Every
+// thread of the block must call it.
+template <typename T, int NV>
+__device__ __forceinline__ void block_sum_store(const T (&v)[NV], double* part, long long stride, int slot) {
+  __shared__ double sh[kBlock / 32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    T a = v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) sh[warp][i] = (double)a;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NV; i += blockDim.x) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += sh[w][i];
+    part[(long long)i * stride + slot] = a;
+  }
+}
+
+__device__ __forceinline__ void decode(const GridDesc& g, long long t, int& x, int& y, int& z) {
+  const int mask = g.p - 1;
+  x = (int)(t & mask);
+  y = (int)((t >> g.lp) & mask);
+  z = (int)(t >> (2 * g.lp));
+}
+
+__device__ __forceinline__ bool interior(const GridDesc& g, int x, int y, int z) {
+  return x < g.n1 && y < g.n1 && (g.dim == 2 || z < g.n1);
+}
+
+}  // namespace mpcg
