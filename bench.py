@@ -41,7 +41,7 @@ def _rank():
 
 # ---------------------------------------------------------------------------- clocks
 class Clocks:
-    """nvidia-smi samples every 200 ms while the timed region runs."""
+    """nvidia-smi samples every 50 ms while the timed region runs."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -50,7 +50,7 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -100,22 +100,48 @@ def kernel_work(cls: str, n: int, C: int, cnt: int, w: int):
     return None, None
 
 
-def roofline(trace, n, C, m, w, peaks, fp64_alu_peak_tflops):
+def level_dofs(nodes, dim, levels):
+    """Interior unknowns of every grid, coarsest first."""
+    return [((nodes - 1) // 2 ** (levels - 1 - j) - 1) ** dim for j in range(levels)]
+
+
+def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops):
     """Dominant kernel class by total time; achieved = algorithmic bytes
-    (or flops) summed over its launches / summed CUDA-event durations."""
+    (or flops) summed over its launches / summed CUDA-event durations.
+
+    The grid of each multilevel launch follows the launch order of one MG
+    chain: the smoothings of grids J, J-1, ..., 1 (nu = 2: one launch each),
+    the restrictions from grids J, ..., 1, the prolongations into 1, ..., J."""
+    J = len(ns) - 1
+    S = 27
     tot = {}
     for cls, ms in trace:
         tot[cls] = tot.get(cls, 0.0) + ms
     dom = max(tot, key=tot.get)
     cnt = 0
+    jj = jr = J
+    jp = 1
     bytes_sum = flops_sum = 0.0
     launches = 0
     dur = 0.0
     for cls, ms in trace:
+        b = f = None
         if cls == "init":
             cnt = 0
+        if cls in ("init", "check"):
+            jj, jr, jp = J, J, 1
+        if cls == "jacobi":
+            b, f = (S + 3) * w * ns[jj], (2 * S + 4) * ns[jj]
+            jj -= 1
+        elif cls == "restrict":
+            b, f = (ns[jr] + ns[jr - 1]) * w, 2 * 27 * ns[jr - 1]
+            jr -= 1
+        elif cls == "prolong":
+            b, f = jp * (ns[jp - 1] + ns[jp]) * w, 2 * 8 * jp * ns[jp]
+            jp += 1
+        elif cls in ("orth_update", "gram_window", "spmm", "update_xr"):
+            b, f = kernel_work(cls, ns[J], C, cnt, w)
         if cls == dom:
-            b, f = kernel_work(cls, n, C, cnt, w)
             if b is not None:
                 bytes_sum += b
                 flops_sum += f
@@ -315,7 +341,8 @@ def bench_ours(args):
     for key, w in (("mixed", 4), ("fp64", 8)):
         x.zero_()
         _, k, classes, trace = M.mpcg_solve_profiled(H[key].h, b, x, RTOL, MAXIT)
-        dom, rl, share, tot = roofline(trace, n, prob.levels, M_WINDOW, w, peaks, FP64_PEAK_TFLOPS)
+        dom, rl, share, tot = roofline(trace, level_dofs(NODES, DIM, prob.levels), prob.levels, M_WINDOW, w, peaks,
+                                       FP64_PEAK_TFLOPS)
         prof[key] = {"roofline": rl, "class_ms": {c: round(v, 4) for c, v in tot.items()}}
     # mixed vs fp64 solution difference
     x.zero_()
@@ -382,7 +409,7 @@ def bench_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")

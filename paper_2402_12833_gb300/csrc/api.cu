@@ -91,6 +91,8 @@ struct Solver {
   Window<T> win = {};
   DevState* state = nullptr;
   double *part_res = nullptr, *part_zaz = nullptr, *part_W = nullptr, *part_G = nullptr, *part_r = nullptr;
+  double* small_scratch = nullptr;   // reduced values of the small solves
+  unsigned* counters = nullptr;      // last-block counters of small_beta / small_alpha
   double *res_hist = nullptr, *alpha_hist = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -189,6 +191,10 @@ struct mg_hierarchy {
   mpcg_options opt;
   cudaStream_t stream = 0;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t side[2] = {nullptr, nullptr};   // branches of the MG chain
+  cudaEvent_t ev_fork = nullptr, ev_fine = nullptr;
+  cudaEvent_t ev_r[kMaxLevels] = {}, ev_sm[kMaxLevels] = {};
+  double* A0inv = nullptr;
   Level lev[kMaxLevels];
   double* L0 = nullptr;
   double* rdiag0 = nullptr;
@@ -255,6 +261,8 @@ mpcg_status build_solver(mg_hierarchy* h, Solver<T>& S) {
   CKS(S.mem.get(&S.part_W, (size_t)S.m * C * C * gram_chunks(gf), s));
   CKS(S.mem.get(&S.part_G, (size_t)(C * (C + 1) / 2 + C) * stream_blocks(gf), s));
   CKS(S.mem.get(&S.part_r, stream_blocks(gf), s));
+  CKS(S.mem.get(&S.small_scratch, kSmallScratchAlpha + kMaxCols * kMaxCols + 3 * kMaxCols, s));
+  CKS(S.mem.get(&S.counters, 2, s));
   S.built = true;
   return MPCG_OK;
 }
@@ -275,45 +283,71 @@ mpcg_status ensure_hist(mg_hierarchy* h, Solver<T>& S, int maxit) {
 // The additive MG block Z = MG(r) (Section 2.2): restrict r to every grid,
 // solve on the coarsest, smooth on the others, prolong every correction to
 // the fine grid.  Column l of Z is the correction of grid l.
+// nu damped-Jacobi sweeps from zero on grid j: rr -> out.
+template <typename T>
+void enqueue_smooth(mg_hierarchy* h, Solver<T>& S, int j, const T* rr, T* out, const DevState* state,
+                    cudaStream_t s) {
+  const Level& L = h->lev[j];
+  const T* st = st_of<T>(L);
+  const T* di = dinv_of<T>(L);
+  const int nu = h->opt.nu;
+  if (nu == 1) {
+    LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, nullptr, out, 0, state, s));
+  } else if (nu == 2) {
+    LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, nullptr, out, 1, state, s));
+  } else {
+    T* a = S.tmp[j];
+    T* b = S.tmp2[j];
+    LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, nullptr, a, 1, state, s));
+    for (int k = 3; k <= nu; ++k) {
+      T* o = k == nu ? out : b;
+      LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, a, o, 2, state, s));
+      T* t = a;
+      a = b;
+      b = t;
+    }
+  }
+}
+
+// The additive structure makes the level corrections independent once the
+// residual has been restricted (Section 2.1): the fine-grid smoothing (which
+// needs only r) runs on a second stream, the coarse smoothings on a third as
+// their restricted residuals appear, while the main stream carries the
+// restriction chain, the coarse solve and the prolongation chain.  Under
+// graph capture the three streams become parallel graph branches.
 template <typename T>
 void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState* state, cudaStream_t s) {
   const int J = h->levels - 1;
   if (J == 0) {
-    LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->L0, h->rdiag0, r, Z, state, s));
+    LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->A0inv, r, Z, state, s));
     return;
   }
+  // a profiled solve keeps every launch on one stream so that each event
+  // pair brackets exactly one kernel running alone
+  cudaStream_t s2 = h->prof.on ? s : h->side[0], s3 = h->prof.on ? s : h->side[1];
+  cudaEventRecord(h->ev_fork, s);
+  cudaStreamWaitEvent(s2, h->ev_fork, 0);
+  enqueue_smooth<T>(h, S, J, r, Z + (size_t)J * h->lev[J].g.len, state, s2);
+  cudaEventRecord(h->ev_fine, s2);
   const T* rj = r;
   for (int j = J; j >= 1; --j) {
     LAUNCH(h, K_RESTRICT, s, launch_restrict<T>(h->lev[j].g, h->lev[j - 1].g, rj, S.rlev[j - 1], state, s));
     rj = S.rlev[j - 1];
-  }
-  LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->L0, h->rdiag0, S.rlev[0], S.zc[0], state, s));
-  const int nu = h->opt.nu;
-  for (int j = 1; j <= J; ++j) {
-    const Level& L = h->lev[j];
-    T* dst = j == J ? Z : S.zc[j];
-    LAUNCH(h, K_PROLONG, s, launch_prolong<T>(h->lev[j - 1].g, L.g, S.zc[j - 1], dst, j, state, s));
-    const T* rr = j == J ? r : S.rlev[j];
-    T* out = dst + (size_t)j * L.g.len;
-    const T* st = st_of<T>(L);
-    const T* di = dinv_of<T>(L);
-    if (nu == 1) {
-      LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, nullptr, out, 0, state, s));
-    } else if (nu == 2) {
-      LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, nullptr, out, 1, state, s));
-    } else {
-      T* a = S.tmp[j];
-      T* b = S.tmp2[j];
-      LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, nullptr, a, 1, state, s));
-      for (int k = 3; k <= nu; ++k) {
-        T* o = k == nu ? out : b;
-        LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, a, o, 2, state, s));
-        T* t = a;
-        a = b;
-        b = t;
-      }
+    if (j - 1 >= 1) {   // smoothing of grid j-1 can start now
+      cudaEventRecord(h->ev_r[j - 1], s);
+      cudaStreamWaitEvent(s3, h->ev_r[j - 1], 0);
+      enqueue_smooth<T>(h, S, j - 1, S.rlev[j - 1], S.zc[j - 1] + (size_t)(j - 1) * h->lev[j - 1].g.len, state, s3);
+      cudaEventRecord(h->ev_sm[j - 1], s3);
     }
   }
+  LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->A0inv, S.rlev[0], S.zc[0], state, s));
+  for (int j = 1; j <= J; ++j) {
+    // prolong columns 0..j-1 of grid j-1; column j-1 is grid j-1's smoothing
+    if (j - 1 >= 1) cudaStreamWaitEvent(s, h->ev_sm[j - 1], 0);
+    T* dst = j == J ? Z : S.zc[j];
+    LAUNCH(h, K_PROLONG, s, launch_prolong<T>(h->lev[j - 1].g, h->lev[j].g, S.zc[j - 1], dst, j, state, s));
+  }
+  cudaStreamWaitEvent(s, h->ev_fine, 0);
 }
 
 template <typename T>
@@ -331,10 +365,11 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
   enqueue_mg<T>(h, S, S.r, S.Z, S.state, s);
   LAUNCH(h, K_SPMM, s, launch_spmm<T>(L.g, st_of<T>(L), S.Z, S.AZ, C, S.part_zaz, S.state, s));
   LAUNCH(h, K_GRAM, s, launch_gram_window<T>(L.g, S.win, S.Z, C, S.m, S.part_W, S.state, s));
-  LAUNCH(h, K_BETA, s, launch_small_beta(S.state, S.part_W, gram_chunks(L.g), C, s));
+  LAUNCH(h, K_BETA, s, launch_small_beta(S.state, S.part_W, gram_chunks(L.g), C, S.small_scratch, S.counters, s));
   LAUNCH(h, K_ORTH, s, launch_orth_update<T>(L.g, S.win, S.Z, S.AZ, S.r, C, S.part_G, S.state, s));
-  LAUNCH(h, K_ALPHA, s, launch_small_alpha(S.state, S.part_G, stream_blocks(L.g), S.part_zaz, stream_blocks(L.g), stream_blocks(L.g), C,
-                                          S.alpha_hist, s));
+  LAUNCH(h, K_ALPHA, s, launch_small_alpha(S.state, S.part_G, stream_blocks(L.g), S.part_zaz, stream_blocks(L.g),
+                                          stream_blocks(L.g), C, S.alpha_hist, S.small_scratch + kSmallScratchAlpha,
+                                          S.counters + 1, s));
   LAUNCH(h, K_UPDATE, s, launch_update_xr<T>(L.g, S.win, S.x, S.r, C, S.part_r, S.state, s));
   LAUNCH(h, K_CHECK, s, launch_check(S.state, S.part_r, stream_blocks(L.g), S.res_hist, cond, use_cond, s));
 }
@@ -519,6 +554,14 @@ void mg_hierarchy_destroy(mg_hierarchy* h) {
   h->mem.release();
   h->prof.release();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (auto sd : h->side)
+    if (sd) cudaStreamDestroy(sd);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_fine) cudaEventDestroy(h->ev_fine);
+  for (int j = 0; j < kMaxLevels; ++j) {
+    if (h->ev_r[j]) cudaEventDestroy(h->ev_r[j]);
+    if (h->ev_sm[j]) cudaEventDestroy(h->ev_sm[j]);
+  }
   delete h;
 }
 
@@ -580,6 +623,17 @@ mpcg_status mg_hierarchy_setup(const mg_operator* A, int levels, const mpcg_opti
     mg_hierarchy_destroy(h);
     return s;
   };
+  bool ev_ok = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&h->ev_fine, cudaEventDisableTiming) == cudaSuccess &&
+               cudaStreamCreateWithFlags(&h->side[0], cudaStreamNonBlocking) == cudaSuccess &&
+               cudaStreamCreateWithFlags(&h->side[1], cudaStreamNonBlocking) == cudaSuccess;
+  for (int j = 0; j < kMaxLevels && ev_ok; ++j)
+    ev_ok = cudaEventCreateWithFlags(&h->ev_r[j], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&h->ev_sm[j], cudaEventDisableTiming) == cudaSuccess;
+  if (!ev_ok) {
+    set_err("creating streams/events failed");
+    return fail(MPCG_ERR_CUDA);
+  }
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     set_err("cudaStreamCreateWithFlags failed");
     return fail(MPCG_ERR_CUDA);
@@ -610,6 +664,12 @@ mpcg_status mg_hierarchy_setup(const mg_operator* A, int levels, const mpcg_opti
   if (info != 0) {
     set_err("coarsest operator is not positive definite (Cholesky pivot %d)", info);
     return fail(MPCG_ERR_NOT_SPD);
+  }
+  {
+    double* X = nullptr;
+    if ((st = h->mem.get(&h->A0inv, (size_t)n0 * n0, s)) != MPCG_OK) return fail(st);
+    if ((st = h->mem.get(&X, (size_t)n0 * n0, s)) != MPCG_OK) return fail(st);
+    launch_coarse_inverse(h->L0, h->rdiag0, X, h->A0inv, (int)n0, s);
   }
   if ((st = build_solver<double>(h, h->s64)) != MPCG_OK) return fail(st);
   if (opt.precision == MPCG_MIXED) {

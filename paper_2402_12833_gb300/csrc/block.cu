@@ -22,7 +22,7 @@ namespace {
 // block jj = b % m and on the contiguous point chunk b / m, so that the
 // blocks running together read the same chunk of Z (L2 reuse).
 template <typename T, int C>
-__global__ void __launch_bounds__(kBlock) k_gram_window(GridDesc g, Window<T> win, const T* __restrict__ Z,
+__global__ void __launch_bounds__(kBlock, 3) k_gram_window(GridDesc g, Window<T> win, const T* __restrict__ Z,
                                                         double* part, int nchunks, const DevState* state) {
   if (state->done) return;
   const int m = state->m;
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kBlock) k_gram_window(GridDesc g, Window<T> wi
 }
 
 template <typename T, int C>
-__global__ void __launch_bounds__(kBlock) k_orth_update(GridDesc g, Window<T> win, const T* __restrict__ Z,
+__global__ void __launch_bounds__(kBlock, 2) k_orth_update(GridDesc g, Window<T> win, const T* __restrict__ Z,
                                                         const T* __restrict__ AZ, const T* __restrict__ r,
                                                         double* part, const DevState* state) {
   if (state->done) return;
@@ -208,9 +208,9 @@ __global__ void __launch_bounds__(kBlock) k_update_xr(GridDesc g, Window<T> win,
   }
 
 int gram_chunks(const GridDesc& g) {
-  // 16 vector groups (64 points in FP32, 32 in FP64) per thread and chunk
+  // 8 vector groups (32 points in FP32, 16 in FP64) per thread and chunk
   const long long groups = g.npts / 4;
-  long long c = (groups + kBlock * 16 - 1) / (kBlock * 16);
+  long long c = (groups + kBlock * 8 - 1) / (kBlock * 8);
   if (c < 1) c = 1;
   return (int)(c < kGramChunksMax ? c : kGramChunksMax);
 }

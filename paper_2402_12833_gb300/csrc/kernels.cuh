@@ -82,9 +82,16 @@ void launch_update_xr(const GridDesc& g, Window<T> win, T* x, T* r, int C, doubl
 // ---- small.cu ------------------------------------------------------------
 void launch_init(DevState* st, const double* part_res, int nblk, double* res_hist,
                  cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
-void launch_small_beta(DevState* st, const double* part_W, int nchunks, int C, cudaStream_t s);
+// The small solves reduce their partial sums with kSmallGrid blocks; the last
+// block to finish (atomic counter, zero between launches) does the solve.
+// scratch holds the reduced values (>= m C^2 + C^2 + 3C doubles).
+constexpr int kSmallGrid = 96;
+constexpr int kSmallScratchAlpha = kMaxWindow * kMaxCols * kMaxCols;   // offset of small_alpha's values
+void launch_small_beta(DevState* st, const double* part_W, int nchunks, int C, double* scratch, unsigned* counter,
+                       cudaStream_t s);
 void launch_small_alpha(DevState* st, const double* part_G, int nblk_G, const double* part_zaz, int nblk_zaz,
-                        int zaz_stride, int C, double* alpha_hist, cudaStream_t s);
+                        int zaz_stride, int C, double* alpha_hist, double* scratch, unsigned* counter,
+                        cudaStream_t s);
 void launch_check(DevState* st, const double* part_r, int nblk, double* res_hist,
                   cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
 void launch_set_params(DevState* st, double rtol, int maxit, int m, int C, double delta, double tau,
@@ -93,10 +100,12 @@ void launch_set_params(DevState* st, double rtol, int maxit, int m, int C, doubl
 // failing pivot + 1
 void launch_dense_from_stencil(const GridDesc& g, const double* st, double* dense, cudaStream_t s);
 void launch_cholesky(double* a, double* rdiag, int n, int* info, cudaStream_t s);
-// out = A0^{-1} r via the Cholesky factor; r, out in padded layout of grid g
+// inv = A0^{-1} from the Cholesky factor (X: n*n scratch)
+void launch_coarse_inverse(const double* L, const double* rdiag, double* X, double* inv, int n, cudaStream_t s);
+// out = A0^{-1} r; r, out in the padded layout of grid g
 template <typename T>
-void launch_coarse_solve(const GridDesc& g, const double* L, const double* rdiag, const T* r, T* out,
-                         const DevState* state, cudaStream_t s);
+void launch_coarse_solve(const GridDesc& g, const double* inv, const T* r, T* out, const DevState* state,
+                         cudaStream_t s);
 // ||r||^2 style sum of partials (value-major) into out[nv]
 void launch_sum_partials(const double* part, int nv, int nblk, double* out, cudaStream_t s);
 // x64 += scale * d (padded, FP32 d); scale read from device

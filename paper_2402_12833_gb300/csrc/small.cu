@@ -42,6 +42,45 @@ __device__ void reduce_values(const double* __restrict__ part, int nv, int nblk,
   }
 }
 
+// Multi-block reduction of value-major partial sums.  Value v (of nv) is
+// summed by block v % gridDim.x over its nblk partials in a fixed order and
+// written to red[v].  Exactly one block -- the last to finish -- gets true,
+// after which every red[v] is visible to it (read them with __ldcg).  The
+// counter is zero between launches.  Values below nv_a come from part_a
+// (stride stride_a, nblk_a partials), the rest from part_b.
+__device__ bool reduce_values_grid(const double* __restrict__ part_a, int nv_a, int nblk_a, int stride_a,
+                                   const double* __restrict__ part_b, int nv_b, int nblk_b, int stride_b,
+                                   double* red, unsigned* counter) {
+  __shared__ double wsum[32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int v = blockIdx.x; v < nv_a + nv_b; v += gridDim.x) {
+    const double* p = v < nv_a ? part_a + (long long)v * stride_a : part_b + (long long)(v - nv_a) * stride_b;
+    const int nb = v < nv_a ? nblk_a : nblk_b;
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) a += p[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) wsum[warp] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+      red[v] = t;
+    }
+    __syncthreads();
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+  return last;
+}
+
 constexpr int kPad = 16;   // padded matrix size for the small solvers (>= kMaxCols, even)
 
 // Jacobi eigenvalue pseudo-inverse of the na x na matrix A (ld kPad, active
@@ -206,13 +245,17 @@ __global__ void k_init(DevState* st, const double* part_res, int nblk, double* r
   }
 }
 
-__global__ void k_small_beta(DevState* st, const double* part_W, int nchunks, int C) {
+// beta_j = G_j^+ W_j for the window blocks: the W partial sums are reduced by
+// all blocks of the grid, the last block forms beta.
+__global__ void k_small_beta(DevState* st, const double* part_W, int nchunks, int C, double* scratch,
+                             unsigned* counter) {
   if (st->done) return;
   const int cnt = st->count;
   if (cnt == 0) return;
   const int m = st->m, newest = st->newest;
+  if (!reduce_values_grid(part_W, cnt * C * C, nchunks, nchunks, nullptr, 0, 0, 0, scratch, counter)) return;
   __shared__ double W[kMaxWindow * kMaxCols * kMaxCols];
-  reduce_values(part_W, cnt * C * C, nchunks, nchunks, W);
+  for (int e = threadIdx.x; e < cnt * C * C; e += blockDim.x) W[e] = __ldcg(scratch + e);
   __syncthreads();
   for (int e = threadIdx.x; e < cnt * C * C; e += blockDim.x) {
     const int jj = e / (C * C), a = (e / C) % C, b = e % C;
@@ -224,7 +267,7 @@ __global__ void k_small_beta(DevState* st, const double* part_W, int nchunks, in
 }
 
 __global__ void k_small_alpha(DevState* st, const double* part_G, int nblk_G, const double* part_zaz, int nblk_zaz,
-                              int zaz_stride, int C, double* alpha_hist) {
+                              int zaz_stride, int C, double* alpha_hist, double* scratch, unsigned* counter) {
   if (st->done) return;
   const int NG = C * (C + 1) / 2;
   __shared__ double red[kMaxCols * (kMaxCols + 1) / 2 + 2 * kMaxCols];
@@ -232,8 +275,9 @@ __global__ void k_small_alpha(DevState* st, const double* part_G, int nblk_G, co
   __shared__ double dsc[kPad], rc[kPad], rs[kPad], lam[kPad];
   __shared__ int act[kPad], map[kPad], rp[kPad], rq[kPad];
   __shared__ int nact_sh;
-  reduce_values(part_G, NG + C, nblk_G, nblk_G, red);
-  reduce_values(part_zaz, C, nblk_zaz, zaz_stride, red + NG + C);
+  if (!reduce_values_grid(part_G, NG + C, nblk_G, nblk_G, part_zaz, C, nblk_zaz, zaz_stride, scratch, counter))
+    return;
+  for (int e = threadIdx.x; e < NG + 2 * C; e += blockDim.x) red[e] = __ldcg(scratch + e);
   __syncthreads();
   if (threadIdx.x >= 32) return;
   const int lane = threadIdx.x;
@@ -380,41 +424,49 @@ __global__ void k_cholesky(double* a, double* rdiag, int n, int* info) {
   if (threadIdx.x == 0) info[0] = fail;
 }
 
-// out = A0^{-1} r by forward and backward substitution with the Cholesky
-// factor; one warp, column-oriented, the factor staged in shared memory.
+// A0^{-1} = L^{-T} L^{-1} from the Cholesky factor A0 = L L^T (setup, one
+// block): X = L^{-1} by forward substitution, one column per thread, then
+// inv = X^T X.  The per-iteration coarse solve is then one parallel
+// matrix-vector product instead of two sequential substitutions.
+__global__ void k_coarse_inverse(const double* __restrict__ L, const double* __restrict__ rdiag, double* X,
+                                 double* inv, int n) {
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    for (int i = 0; i < j; ++i) X[(long long)i * n + j] = 0.0;
+    X[(long long)j * n + j] = rdiag[j];
+    for (int i = j + 1; i < n; ++i) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s += L[(long long)i * n + k] * X[(long long)k * n + j];
+      X[(long long)i * n + j] = -s * rdiag[i];
+    }
+  }
+  __syncthreads();
+  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+    const int a = (int)(e / n), b = (int)(e % n);
+    double s = 0.0;
+    for (int k = a > b ? a : b; k < n; ++k) s += X[(long long)k * n + a] * X[(long long)k * n + b];
+    inv[e] = s;
+  }
+}
+
+// out = A0^{-1} r (the exact coarsest solve S_0), one row per thread.
 template <typename T>
-__global__ void k_coarse_solve(GridDesc g, const double* __restrict__ L, const double* __restrict__ rdiag,
-                               const T* __restrict__ r, T* __restrict__ out, const DevState* state) {
+__global__ void k_coarse_solve(GridDesc g, const double* __restrict__ inv, const T* __restrict__ r,
+                               T* __restrict__ out, const DevState* state) {
   if (state && state->done) return;
-  extern __shared__ double sm[];
-  const int n = (int)g.n, lane = threadIdx.x;
-  double* y = sm;
-  double* Ls = sm + n;
-  const bool stage = n <= 64;
-  if (stage)
-    for (int e = lane; e < n * n; e += 32) Ls[e] = L[e];
-  const double* Lp = stage ? Ls : L;
+  extern __shared__ double y[];
+  const int n = (int)g.n;
   auto padded = [&](int i) {
     const int x = i % g.n1, yy = (i / g.n1) % g.n1, z = i / (g.n1 * g.n1);
     return g.G + x + (long long)g.p * yy + (long long)g.p * g.p * z;
   };
-  for (int i = lane; i < n; i += 32) y[i] = (double)r[padded(i)];
-  __syncwarp();
-  for (int i = 0; i < n; ++i) {
-    const double yi = y[i] * rdiag[i];
-    __syncwarp();
-    if (lane == 0) y[i] = yi;
-    for (int k = i + 1 + lane; k < n; k += 32) y[k] -= Lp[(long long)k * n + i] * yi;
-    __syncwarp();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = (double)r[padded(i)];
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double* row = inv + (long long)i * n;
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s = fma(row[j], y[j], s);
+    out[padded(i)] = (T)s;
   }
-  for (int i = n - 1; i >= 0; --i) {
-    const double xi = y[i] * rdiag[i];
-    __syncwarp();
-    if (lane == 0) y[i] = xi;
-    for (int k = lane; k < i; k += 32) y[k] -= Lp[(long long)i * n + k] * xi;
-    __syncwarp();
-  }
-  for (int i = lane; i < n; i += 32) out[padded(i)] = (T)y[i];
 }
 
 __global__ void k_sum_partials(const double* part, int nv, int nblk, double* out) {
@@ -451,12 +503,15 @@ void launch_init(DevState* st, const double* part_res, int nblk, double* res_his
                  int use_cond, cudaStream_t s) {
   k_init<<<1, kBlock, 0, s>>>(st, part_res, nblk, res_hist, cond, use_cond);
 }
-void launch_small_beta(DevState* st, const double* part_W, int nchunks, int C, cudaStream_t s) {
-  k_small_beta<<<1, 1024, 0, s>>>(st, part_W, nchunks, C);
+void launch_small_beta(DevState* st, const double* part_W, int nchunks, int C, double* scratch, unsigned* counter,
+                       cudaStream_t s) {
+  k_small_beta<<<kSmallGrid, kBlock, 0, s>>>(st, part_W, nchunks, C, scratch, counter);
 }
 void launch_small_alpha(DevState* st, const double* part_G, int nblk_G, const double* part_zaz, int nblk_zaz,
-                        int zaz_stride, int C, double* alpha_hist, cudaStream_t s) {
-  k_small_alpha<<<1, kBlock, 0, s>>>(st, part_G, nblk_G, part_zaz, nblk_zaz, zaz_stride, C, alpha_hist);
+                        int zaz_stride, int C, double* alpha_hist, double* scratch, unsigned* counter,
+                        cudaStream_t s) {
+  k_small_alpha<<<kSmallGrid, kBlock, 0, s>>>(st, part_G, nblk_G, part_zaz, nblk_zaz, zaz_stride, C, alpha_hist,
+                                              scratch, counter);
 }
 void launch_check(DevState* st, const double* part_r, int nblk, double* res_hist, cudaGraphConditionalHandle cond,
                   int use_cond, cudaStream_t s) {
@@ -468,16 +523,18 @@ void launch_dense_from_stencil(const GridDesc& g, const double* st, double* dens
 void launch_cholesky(double* a, double* rdiag, int n, int* info, cudaStream_t s) {
   k_cholesky<<<1, 512, 0, s>>>(a, rdiag, n, info);
 }
-template <typename T>
-void launch_coarse_solve(const GridDesc& g, const double* L, const double* rdiag, const T* r, T* out,
-                         const DevState* state, cudaStream_t s) {
-  const size_t sh = (size_t)g.n * sizeof(double) * (g.n <= 64 ? g.n + 1 : 1);
-  k_coarse_solve<T><<<1, 32, sh, s>>>(g, L, rdiag, r, out, state);
+void launch_coarse_inverse(const double* L, const double* rdiag, double* X, double* inv, int n, cudaStream_t s) {
+  k_coarse_inverse<<<1, 256, 0, s>>>(L, rdiag, X, inv, n);
 }
-template void launch_coarse_solve<double>(const GridDesc&, const double*, const double*, const double*, double*,
-                                          const DevState*, cudaStream_t);
-template void launch_coarse_solve<float>(const GridDesc&, const double*, const double*, const float*, float*,
-                                         const DevState*, cudaStream_t);
+template <typename T>
+void launch_coarse_solve(const GridDesc& g, const double* inv, const T* r, T* out, const DevState* state,
+                         cudaStream_t s) {
+  k_coarse_solve<T><<<1, 128, (size_t)g.n * sizeof(double), s>>>(g, inv, r, out, state);
+}
+template void launch_coarse_solve<double>(const GridDesc&, const double*, const double*, double*, const DevState*,
+                                          cudaStream_t);
+template void launch_coarse_solve<float>(const GridDesc&, const double*, const float*, float*, const DevState*,
+                                         cudaStream_t);
 void launch_sum_partials(const double* part, int nv, int nblk, double* out, cudaStream_t s) {
   k_sum_partials<<<1, kBlock, 0, s>>>(part, nv, nblk, out);
 }
