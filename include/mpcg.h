@@ -175,12 +175,53 @@ mpcg_status mg_get_operator(mg_hierarchy* h, int level, double* planes_dev);
  * mg_last_launches returns how many kernels the last mpcg_solve or
  * mpcg_solve_profiled call on h executed (graph launches counted per node).
  */
-#define MPCG_NUM_KERNEL_CLASSES 15
+#define MPCG_NUM_KERNEL_CLASSES 16
 const char* mpcg_kernel_class_name(int cls);
 mpcg_status mpcg_solve_profiled(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit,
                                 int* iters_out, double* class_ms, long long* class_launches,
                                 int* trace_cls, float* trace_ms, long long trace_cap, long long* trace_len);
 long long mg_last_launches(const mg_hierarchy* h);
+
+/*
+ * Learned search column (an extension beyond the paper; 2D grids).
+ * A 3x3 convolutional network N with channels 2 -> 16 -> 16 -> 16 -> 1 (ReLU
+ * after the first three, zero padding, no bias; bfloat16 weights and
+ * activations, FP32 accumulation) maps the scaled residual r/||r|| and the
+ * coefficient channel c = log10(diag A)/3 - mean(...) to an approximate
+ * error y.  Once attached, every MPCG iteration appends z = ||r|| y as one
+ * more column of Z, which the energy minimisation weights like the others
+ * (zero weight, or a dropped column, when it does not help).
+ * Parameters: mg_learned_num_params() floats, layer by layer, each layer
+ * W[co][ci][ky][kx] (tap (ky, kx) multiplies the input at (x+kx-1, y+ky-1)).
+ */
+typedef struct {
+  int epochs;        /* passes over the training pairs */
+  int batch;         /* pairs per Adam step, 1..MPCG_MAX_COLS (same problem) */
+  double lr, beta1, beta2, eps;   /* Adam (Kingma & Ba) */
+  unsigned long long seed;        /* shuffling */
+} mg_train_opts;
+
+int mg_learned_num_params(void);
+/* Attach weights (host or device floats); mpcg_solve then uses
+ * mg_num_levels()+1 columns.  Errors: MPCG_ERR_ARG (3D grid, wrong count). */
+mpcg_status mg_learned_attach(mg_hierarchy* h, const float* params, int nparams);
+mpcg_status mg_learned_detach(mg_hierarchy* h);
+/* y = N(rhat, c) for nimg images on h's fine grid (device, n floats each,
+ * rhat already scaled); needs attached weights. */
+mpcg_status mg_learned_forward(mg_hierarchy* h, const float* rhat_dev, float* y_dev, int nimg);
+/*
+ * Train the network on the GPU: pairs (rhat_i, e_i) of scaled residuals and
+ * the matching errors (device, npairs x n floats, compact layout) belonging to
+ * problem pair_prob[i] (host ints) among hs[0..nprob-1] (same fine grid).
+ * Loss per pair: the A-angle 1 - (e^T A y)^2 / ((e^T A e)(y^T A y)), A in FP32;
+ * forward and backward run in the library's kernels, Adam on FP32 master
+ * weights.  params (host or device floats) holds the initial weights on entry
+ * and the trained ones on return; loss_hist (host, epochs doubles, may be
+ * NULL) gets the mean loss of every epoch.
+ */
+mpcg_status mg_learned_train(mg_hierarchy* const* hs, int nprob, const int* pair_prob, int npairs,
+                             const float* rhat_dev, const float* e_dev, const mg_train_opts* opts,
+                             float* params, double* loss_hist);
 
 /* Release everything the hierarchy owns.  NULL is ignored. */
 void mg_hierarchy_destroy(mg_hierarchy* h);

@@ -116,11 +116,11 @@ struct Solver {
 
 enum KClass {
   K_PACK, K_RESIDUAL, K_INIT, K_RESTRICT, K_COARSE, K_PROLONG, K_JACOBI, K_SPMM, K_GRAM, K_BETA, K_ORTH,
-  K_ALPHA, K_UPDATE, K_CHECK, K_AUX, K_COUNT
+  K_ALPHA, K_UPDATE, K_CHECK, K_AUX, K_NET, K_COUNT
 };
 const char* const kClassNames[K_COUNT] = {"pack", "residual", "init", "restrict", "coarse_solve", "prolong",
                                           "jacobi", "spmm", "gram_window", "small_beta", "orth_update",
-                                          "small_alpha", "update_xr", "check", "aux"};
+                                          "small_alpha", "update_xr", "check", "aux", "net"};
 
 // Launch accounting and optional per-launch CUDA-event timing (direct
 // launches only; never active while a graph is captured).
@@ -148,6 +148,8 @@ struct Profiler {
     pending.push_back({cls, used});
     used += 2;
   }
+  // launches beyond the first inside one LAUNCH (a multi-kernel step)
+  void extra(long long k) { *(target ? target : &live) += k; }
   void end(cudaStream_t s) {
     if (on) cudaEventRecord(pool[pending.back().second + 1], s);
   }
@@ -209,6 +211,12 @@ struct mg_hierarchy {
   Profiler prof;
   bool force_direct = false;
   long long last_launches = 0;
+  // learned search column (extension): appended as column `levels`
+  bool net_on = false;
+  float* net_wq = nullptr;     // bfloat16-valued weights
+  float* net_c = nullptr;      // coefficient channel on the fine grid
+  NetActs net_acts = {};       // inference activations
+  Alloc net_mem;
 };
 
 namespace {
@@ -232,7 +240,7 @@ mpcg_status build_solver(mg_hierarchy* h, Solver<T>& S) {
   cudaStream_t s = h->stream;
   const int J = h->levels - 1;
   const GridDesc& gf = h->lev[J].g;
-  S.C = h->levels;
+  S.C = h->levels + (h->net_on ? 1 : 0);
   S.m = h->opt.m;
   const int C = S.C;
   CKS(S.mem.get(&S.x, gf.len, s));
@@ -363,6 +371,12 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
   const Level& L = h->lev[h->levels - 1];
   const int C = S.C;
   enqueue_mg<T>(h, S, S.r, S.Z, S.state, s);
+  if (h->net_on) {
+    LAUNCH(h, K_NET, s,
+           launch_net_forward<T>(L.g, 1, S.r, L.g.len, h->net_c, h->net_wq, S.state, h->net_acts, nullptr,
+                                 S.Z + (size_t)(C - 1) * L.g.len, s));
+    h->prof.extra(4);
+  }
   LAUNCH(h, K_SPMM, s, launch_spmm<T>(L.g, st_of<T>(L), S.Z, S.AZ, C, S.part_zaz, S.state, s));
   LAUNCH(h, K_GRAM, s, launch_gram_window<T>(L.g, S.win, S.Z, C, S.m, S.part_W, S.state, s));
   LAUNCH(h, K_BETA, s, launch_small_beta(S.state, S.part_W, gram_chunks(L.g), C, S.small_scratch, S.counters, s));
@@ -539,7 +553,7 @@ mpcg_status mpcg_default_options(mpcg_options* opt) {
 }
 
 int mg_num_levels(const mg_hierarchy* h) { return h ? h->levels : -1; }
-int mg_num_columns(const mg_hierarchy* h) { return h ? h->levels : -1; }
+int mg_num_columns(const mg_hierarchy* h) { return h ? h->levels + (h->net_on ? 1 : 0) : -1; }
 long long mg_level_size(const mg_hierarchy* h, int level) {
   if (!h || level < 0 || level >= h->levels) return -1;
   return h->lev[level].g.n;
@@ -553,6 +567,7 @@ void mg_hierarchy_destroy(mg_hierarchy* h) {
   h->s32.release();
   h->mem.release();
   h->prof.release();
+  h->net_mem.release();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (auto sd : h->side)
     if (sd) cudaStreamDestroy(sd);
@@ -900,6 +915,285 @@ mpcg_status mg_get_operator(mg_hierarchy* h, int level, double* planes) {
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaGetLastError());
   return MPCG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Learned search column (an extension beyond the paper).
+namespace {
+
+mpcg_status net_check_grid(const mg_hierarchy* h) {
+  if (h->dim != 2) {
+    set_err("the learned column is implemented for 2D grids");
+    return MPCG_ERR_ARG;
+  }
+  return MPCG_OK;
+}
+
+// Coefficient channel and inference buffers of hierarchy h.
+mpcg_status net_prepare(mg_hierarchy* h) {
+  if (h->net_c) return MPCG_OK;
+  cudaStream_t s = h->stream;
+  const Level& L = h->lev[h->levels - 1];
+  double* part = nullptr;
+  CKS(h->net_mem.get(&h->net_c, L.g.len, s));
+  CKS(h->net_mem.get(&part, 256, s));
+  CKS(h->net_mem.get(&h->net_wq, kNetParams, s));
+  CKS(h->net_mem.get(&h->net_acts.a0, (size_t)L.g.len * kNetIn, s));
+  CKS(h->net_mem.get(&h->net_acts.a1, (size_t)L.g.len * kNetC1, s));
+  CKS(h->net_mem.get(&h->net_acts.a2, (size_t)L.g.len * kNetW, s));
+  CKS(h->net_mem.get(&h->net_acts.a3, (size_t)L.g.len * kNetW, s));
+  launch_net_coef(L.g, L.dinv64, h->opt.omega, h->net_c, part, s);
+  CK(cudaGetLastError());
+  return MPCG_OK;
+}
+
+// Copy n floats from host or device memory into device memory.
+mpcg_status copy_floats(float* dst, const float* src, int n, cudaStream_t s) {
+  CK(cudaMemcpyAsync(dst, src, sizeof(float) * n, is_device_pointer(src) ? cudaMemcpyDeviceToDevice
+                                                                         : cudaMemcpyHostToDevice, s));
+  return MPCG_OK;
+}
+
+// Rebuild the solvers after the column count changed.
+mpcg_status rebuild_solvers(mg_hierarchy* h) {
+  CK(cudaStreamSynchronize(h->stream));
+  const bool had32 = h->s32.built;
+  h->s64.release();
+  h->s32.release();
+  CKS(build_solver<double>(h, h->s64));
+  if (had32) CKS(build_solver<float>(h, h->s32));
+  return MPCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mg_learned_num_params(void) { return kNetParams; }
+
+mpcg_status mg_learned_attach(mg_hierarchy* h, const float* params, int nparams) {
+  g_err.clear();
+  CKS(check_h(h));
+  CKS(net_check_grid(h));
+  if (!params || nparams != kNetParams) {
+    set_err("params must hold mg_learned_num_params() = %d floats", kNetParams);
+    return MPCG_ERR_ARG;
+  }
+  if (h->levels + 1 > MPCG_MAX_COLS) {
+    set_err("too many grids for an extra column");
+    return MPCG_ERR_ARG;
+  }
+  CK(cudaSetDevice(h->device));
+  CKS(net_prepare(h));
+  float* tmp = nullptr;
+  CK(cudaMalloc(&tmp, sizeof(float) * kNetParams));
+  mpcg_status st = copy_floats(tmp, params, kNetParams, h->stream);
+  if (st == MPCG_OK) launch_round_bf16(tmp, h->net_wq, kNetParams, h->stream);
+  cudaStreamSynchronize(h->stream);
+  cudaFree(tmp);
+  if (st != MPCG_OK) return st;
+  CK(cudaGetLastError());
+  if (!h->net_on) {
+    h->net_on = true;
+    CKS(rebuild_solvers(h));
+  }
+  return MPCG_OK;
+}
+
+mpcg_status mg_learned_detach(mg_hierarchy* h) {
+  g_err.clear();
+  CKS(check_h(h));
+  CK(cudaSetDevice(h->device));
+  if (h->net_on) {
+    h->net_on = false;
+    CKS(rebuild_solvers(h));
+  }
+  return MPCG_OK;
+}
+
+mpcg_status mg_learned_forward(mg_hierarchy* h, const float* rhat_dev, float* y_dev, int nimg) {
+  g_err.clear();
+  CKS(check_h(h));
+  CKS(net_check_grid(h));
+  if (!h->net_on || !rhat_dev || !y_dev || nimg < 1) {
+    set_err("attach weights first; rhat, y must be device arrays of nimg >= 1 images");
+    return MPCG_ERR_ARG;
+  }
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = h->stream;
+  const GridDesc& g = h->lev[h->levels - 1].g;
+  Alloc tmp;
+  float *r = nullptr, *y = nullptr;
+  NetActs a;
+  mpcg_status st = MPCG_OK;
+  if ((st = tmp.get(&r, (size_t)nimg * g.len, s)) == MPCG_OK && (st = tmp.get(&y, (size_t)nimg * g.len, s)) == MPCG_OK &&
+      (st = tmp.get(&a.a0, (size_t)nimg * g.len * kNetIn, s)) == MPCG_OK &&
+      (st = tmp.get(&a.a1, (size_t)nimg * g.len * kNetC1, s)) == MPCG_OK &&
+      (st = tmp.get(&a.a2, (size_t)nimg * g.len * kNetW, s)) == MPCG_OK &&
+      (st = tmp.get(&a.a3, (size_t)nimg * g.len * kNetW, s)) == MPCG_OK) {
+    launch_pack<float, float>(g, rhat_dev, g.n, r, nimg, s);
+    launch_net_forward<float>(g, nimg, r, g.len, h->net_c, h->net_wq, nullptr, a, y, (float*)nullptr, s);
+    launch_unpack<float, float>(g, y, y_dev, g.n, nimg, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      set_err("learned forward failed");
+      st = MPCG_ERR_CUDA;
+    }
+  }
+  tmp.release();
+  return st;
+}
+
+mpcg_status mg_learned_train(mg_hierarchy* const* hs, int nprob, const int* pair_prob, int npairs,
+                             const float* rhat_dev, const float* e_dev, const mg_train_opts* opts, float* params,
+                             double* loss_hist) {
+  g_err.clear();
+  if (!hs || nprob < 1 || !pair_prob || npairs < 1 || !rhat_dev || !e_dev || !opts || !params) {
+    set_err("mg_learned_train: bad arguments");
+    return MPCG_ERR_ARG;
+  }
+  const int B = opts->batch;
+  if (B < 1 || B > MPCG_MAX_COLS || opts->epochs < 0) {
+    set_err("batch must be in 1..%d and epochs >= 0", MPCG_MAX_COLS);
+    return MPCG_ERR_ARG;
+  }
+  for (int i = 0; i < nprob; ++i) {
+    CKS(check_h(hs[i]));
+    CKS(net_check_grid(hs[i]));
+    if (hs[i]->lev[hs[i]->levels - 1].g.n1 != hs[0]->lev[hs[0]->levels - 1].g.n1) {
+      set_err("all training problems must share the fine grid size");
+      return MPCG_ERR_ARG;
+    }
+  }
+  for (int i = 0; i < npairs; ++i)
+    if (pair_prob[i] < 0 || pair_prob[i] >= nprob) {
+      set_err("pair_prob[%d] out of range", i);
+      return MPCG_ERR_ARG;
+    }
+  mg_hierarchy* h0 = hs[0];
+  CK(cudaSetDevice(h0->device));
+  cudaStream_t s = h0->stream;
+  const GridDesc g = h0->lev[h0->levels - 1].g;
+  if (g.p > 1024) {
+    set_err("training grids are limited to 1025 nodes per side");
+    return MPCG_ERR_ARG;
+  }
+  for (int i = 0; i < nprob; ++i) {
+    CKS(build_f32(hs[i]));
+    CKS(net_prepare(hs[i]));
+  }
+  net_prepare_attributes(g);
+  Alloc mem;
+  mpcg_status st = MPCG_OK;
+  auto get = [&](auto** p, size_t n) {
+    if (st == MPCG_OK) st = mem.get(p, n, s);
+  };
+  float *R, *E, *AE, *rb, *eb, *aeb, *y, *ay, *dy, *master, *m, *v, *wq;
+  double *dots, *coef, *loss;
+  NetActs a;
+  NetGrads gr;
+  const size_t L = g.len;
+  const int nw = net_wgrad_blocks(g, B);
+  get(&R, (size_t)npairs * L);
+  get(&E, (size_t)npairs * L);
+  get(&AE, (size_t)npairs * L);
+  get(&rb, B * L);
+  get(&eb, B * L);
+  get(&aeb, B * L);
+  get(&y, B * L);
+  get(&ay, B * L);
+  get(&dy, B * L);
+  get(&a.a0, B * L * kNetIn);
+  get(&a.a1, B * L * kNetC1);
+  get(&a.a2, B * L * kNetW);
+  get(&a.a3, B * L * kNetW);
+  get(&gr.d1, B * L * kNetW);
+  get(&gr.d2, B * L * kNetW);
+  get(&gr.d3, B * L * kNetW);
+  get(&gr.part[0], (size_t)kNetC1 * kNetIn * 9 * nw);
+  get(&gr.part[1], (size_t)kNetW * kNetC1 * 9 * nw);
+  get(&gr.part[2], (size_t)kNetW * kNetW * 9 * nw);
+  get(&gr.part[3], (size_t)kNetW * 9 * nw);
+  get(&master, kNetParams);
+  get(&m, kNetParams);
+  get(&v, kNetParams);
+  get(&wq, kNetParams);
+  get(&dots, 3 * 64 * B);
+  get(&coef, 2 * B);
+  get(&loss, 1);
+  double** parts_dev = nullptr;
+  int* nblk_dev = nullptr;
+  get(&parts_dev, 4);
+  get(&nblk_dev, 4);
+  if (st != MPCG_OK) {
+    mem.release();
+    return st;
+  }
+  int nblk_h[4] = {nw, nw, nw, nw};
+  cudaMemcpyAsync(parts_dev, gr.part, sizeof(gr.part), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(nblk_dev, nblk_h, sizeof(nblk_h), cudaMemcpyHostToDevice, s);
+  copy_floats(master, params, kNetParams, s);
+  launch_round_bf16(master, wq, kNetParams, s);
+  // training set in the padded layout, and A e per pair (FP32 operators)
+  launch_pack<float, float>(g, rhat_dev, g.n, R, npairs, s);
+  launch_pack<float, float>(g, e_dev, g.n, E, npairs, s);
+  for (int i = 0; i < npairs; ++i) {
+    const Level& Lp = hs[pair_prob[i]]->lev[hs[pair_prob[i]]->levels - 1];
+    launch_spmm<float>(g, Lp.st32, E + (size_t)i * L, AE + (size_t)i * L, 1, nullptr, nullptr, s);
+  }
+  // batches: pairs grouped by problem, shuffled within a problem and across
+  // batches by a seeded 64-bit LCG (Knuth's MMIX constants)
+  unsigned long long lcg = opts->seed * 2862933555777941757ULL + 3037000493ULL;
+  auto rnd = [&](unsigned long long n) {
+    lcg = lcg * 6364136223846793005ULL + 1442695040888963407ULL;
+    return (lcg >> 33) % n;
+  };
+  std::vector<std::vector<int>> byprob(nprob);
+  for (int i = 0; i < npairs; ++i) byprob[pair_prob[i]].push_back(i);
+  int step = 0;
+  for (int ep = 0; ep < opts->epochs && st == MPCG_OK; ++ep) {
+    std::vector<std::vector<int>> batches;
+    for (auto& lst : byprob) {
+      for (size_t i = lst.size(); i > 1; --i) std::swap(lst[i - 1], lst[rnd(i)]);
+      for (size_t i = 0; i < lst.size(); i += B)
+        batches.emplace_back(lst.begin() + i, lst.begin() + std::min(lst.size(), i + (size_t)B));
+    }
+    for (size_t i = batches.size(); i > 1; --i) std::swap(batches[i - 1], batches[rnd(i)]);
+    cudaMemsetAsync(loss, 0, sizeof(double), s);
+    for (auto& bt : batches) {
+      const int nb = (int)bt.size();
+      for (int k = 0; k < nb; ++k) {
+        cudaMemcpyAsync(rb + k * L, R + (size_t)bt[k] * L, sizeof(float) * L, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(eb + k * L, E + (size_t)bt[k] * L, sizeof(float) * L, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(aeb + k * L, AE + (size_t)bt[k] * L, sizeof(float) * L, cudaMemcpyDeviceToDevice, s);
+      }
+      mg_hierarchy* hp = hs[pair_prob[bt[0]]];
+      const float* c = hp->net_c;
+      launch_net_forward<float>(g, nb, rb, L, c, wq, nullptr, a, y, (float*)nullptr, s);
+      launch_spmm<float>(g, hp->lev[hp->levels - 1].st32, y, ay, nb, nullptr, nullptr, s);
+      launch_net_loss_grad(g, nb, y, ay, eb, aeb, dots, coef, loss, dy, s);
+      launch_net_backward(g, nb, wq, a, dy, gr, s);
+      ++step;
+      launch_net_adam(parts_dev, nblk_dev, master, m, v, wq, step, (float)opts->lr, (float)opts->beta1,
+                      (float)opts->beta2, (float)opts->eps, s);
+    }
+    double lh = 0.0;
+    if (cudaMemcpyAsync(&lh, loss, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      set_err("training step failed: %s", cudaGetErrorString(cudaGetLastError()));
+      st = MPCG_ERR_CUDA;
+      break;
+    }
+    if (loss_hist) loss_hist[ep] = lh / (double)batches.size();
+  }
+  if (st == MPCG_OK) {
+    cudaMemcpyAsync(params, master, sizeof(float) * kNetParams,
+                    is_device_pointer(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) st = MPCG_ERR_CUDA;
+  }
+  mem.release();
+  return st;
 }
 
 }  // extern "C"

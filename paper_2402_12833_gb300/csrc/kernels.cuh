@@ -1,6 +1,8 @@
 // Host-side launchers of the libmpcg kernels (internal).
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace mpcg {
@@ -114,5 +116,41 @@ void launch_axpy_mixed(const GridDesc& g, double* x, const float* d, const doubl
 // b32 = r64 / ||r64|| from device norm-squared
 void launch_scale_to_f32(const GridDesc& g, const double* r, const double* nrm2, float* out,
                          cudaStream_t s);
+
+// ---- learned.cu ----------------------------------------------------------
+// Network 2 -> 16 -> 16 -> 16 -> 1 (3x3), parameters packed layer by layer,
+// each W[co][ci][ky][kx].
+constexpr int kNetIn = 2, kNetC1 = 16, kNetW = 16;
+constexpr int kNetOff1 = 0;
+constexpr int kNetOff2 = kNetOff1 + kNetC1 * kNetIn * 9;
+constexpr int kNetOff3 = kNetOff2 + kNetW * kNetC1 * 9;
+constexpr int kNetOff4 = kNetOff3 + kNetW * kNetW * 9;
+constexpr int kNetParams = kNetOff4 + kNetW * 9;
+
+struct NetActs {   // [B][len][C] bfloat16, zero pads
+  __nv_bfloat16 *a0, *a1, *a2, *a3;
+};
+struct NetGrads {  // data gradients [B][len][16] float; weight-gradient partials per layer
+  float *d1, *d2, *d3;
+  double* part[4];
+};
+
+int net_blocks(const GridDesc& g, int B);
+int net_wgrad_blocks(const GridDesc& g, int B);
+size_t net_wgrad_smem(const GridDesc& g);
+// y = N(r s, c) with s = 1/||r|| from state (or 1 without state); writes y
+// (float, may be null) and/or z = ||r|| y (T, may be null); 2D grids.
+template <typename T>
+void launch_net_forward(const GridDesc& g, int B, const T* r, long long r_ld, const float* c, const float* wq,
+                        const DevState* state, NetActs acts, float* y, T* z, cudaStream_t s);
+void launch_net_backward(const GridDesc& g, int B, const float* wq, NetActs acts, const float* dy, NetGrads gr,
+                         cudaStream_t s);
+void launch_net_loss_grad(const GridDesc& g, int B, const float* y, const float* Ay, const float* e,
+                          const float* Ae, double* part, double* coef, double* loss_sum, float* dy, cudaStream_t s);
+void launch_net_adam(const double* const* parts_dev, const int* nblk_dev, float* master, float* m, float* v, float* wq,
+                     int step, float lr, float b1, float b2, float eps, cudaStream_t s);
+void launch_round_bf16(const float* src, float* dst, int n, cudaStream_t s);
+void launch_net_coef(const GridDesc& g, const double* dinv, double omega, float* c, double* part, cudaStream_t s);
+void net_prepare_attributes(const GridDesc& g);
 
 }  // namespace mpcg

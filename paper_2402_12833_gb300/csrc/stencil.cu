@@ -387,6 +387,8 @@ template void launch_pack<double, double>(const GridDesc&, const double*, long l
 template void launch_pack<double, float>(const GridDesc&, const double*, long long, float*, int, cudaStream_t);
 template void launch_unpack<double, double>(const GridDesc&, const double*, double*, long long, int, cudaStream_t);
 template void launch_unpack<float, double>(const GridDesc&, const float*, double*, long long, int, cudaStream_t);
+template void launch_pack<float, float>(const GridDesc&, const float*, long long, float*, int, cudaStream_t);
+template void launch_unpack<float, float>(const GridDesc&, const float*, float*, long long, int, cudaStream_t);
 
 template <typename T, int DIM>
 static void spmm_dim(const GridDesc& g, const T* st, const T* X, T* Y, int C, double* zaz, const DevState* state,

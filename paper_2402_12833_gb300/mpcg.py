@@ -47,6 +47,11 @@ class mpcg_options(C.Structure):
                 ("use_graph", C.c_int), ("stream", C.c_void_p)]
 
 
+class mg_train_opts(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("eps", C.c_double), ("seed", C.c_ulonglong)]
+
+
 _lib = None
 
 # name -> (restype, argtypes); mirrors include/mpcg.h
@@ -70,8 +75,14 @@ _SIGS = {
     "mg_last_launches": (C.c_longlong, [C.c_void_p]),
     "mg_stencil_apply_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                            C.c_void_p]),
+    "mg_learned_num_params": (C.c_int, []),
+    "mg_learned_attach": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "mg_learned_detach": (C.c_int, [C.c_void_p]),
+    "mg_learned_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "mg_learned_train": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                   C.POINTER(mg_train_opts), C.c_void_p, C.c_void_p]),
 }
-MPCG_NUM_KERNEL_CLASSES = 15
+MPCG_NUM_KERNEL_CLASSES = 16
 
 
 def load(path: str = LIB_PATH):
@@ -203,6 +214,37 @@ def mg_stencil_apply_noalloc(dim: int, nodes: int, values_dev, X_dev, Y_dev, nco
     """Y = A X on the fine grid without device allocation (static scratch;
     enqueued on ``stream``, not synchronised)."""
     _check(load().mg_stencil_apply_noalloc(dim, nodes, _ptr(values_dev), _ptr(X_dev), _ptr(Y_dev), ncols, stream))
+
+
+def mg_learned_num_params() -> int:
+    return load().mg_learned_num_params()
+
+
+def mg_learned_attach(h: int, params) -> None:
+    p = np.ascontiguousarray(params, dtype=np.float32) if isinstance(params, np.ndarray) else params
+    _check(load().mg_learned_attach(h, _ptr(p), mg_learned_num_params()))
+
+
+def mg_learned_detach(h: int) -> None:
+    _check(load().mg_learned_detach(h))
+
+
+def mg_learned_forward(h: int, rhat_dev, y_dev, nimg: int = 1) -> None:
+    _check(load().mg_learned_forward(h, _ptr(rhat_dev), _ptr(y_dev), nimg))
+
+
+def mg_learned_train(handles, pair_prob, rhat_dev, e_dev, params: np.ndarray, epochs: int = 10, batch: int = 8,
+                     lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, seed: int = 7):
+    """Train in place: ``params`` (host float32 array) holds the initial and
+    returns the trained weights; returns the per-epoch mean loss."""
+    hs = (C.c_void_p * len(handles))(*handles)
+    pp = np.ascontiguousarray(pair_prob, dtype=np.int32)
+    o = mg_train_opts(epochs, batch, lr, beta1, beta2, eps, seed)
+    loss = np.zeros(max(epochs, 1))
+    assert params.dtype == np.float32 and params.flags["C_CONTIGUOUS"]
+    _check(load().mg_learned_train(hs, len(handles), pp.ctypes.data, len(pp), _ptr(rhat_dev), _ptr(e_dev),
+                                   C.byref(o), params.ctypes.data, loss.ctypes.data))
+    return loss[:epochs]
 
 
 def mg_hierarchy_destroy(h: int) -> None:
