@@ -135,6 +135,30 @@ mpcg_status mg_hierarchy_setup(const mg_operator* A_fine, int levels,
 mpcg_status mpcg_solve(mg_hierarchy* h, const double* b, double* x, double rtol,
                        int maxit, int* iters_out, double* res_hist, double* alpha_hist);
 
+/*
+ * Batches of independent problems on the same grid (each with its own
+ * operator): one hierarchy holds all nprob problems and every kernel works on
+ * the whole batch (problem index = grid dimension y).  mpcg_solve on such a
+ * hierarchy takes b and x as nprob problems of n unknowns back to back,
+ * iters_out as nprob ints, res_hist as nprob blocks of maxit+1 doubles and
+ * alpha_hist as nprob blocks of maxit*ncols doubles; one graph launch (per
+ * refinement step in MPCG_MIXED) runs until every problem has converged,
+ * each problem stopping on its own tolerance.  The status is the worst of
+ * the problems'.  mg_apply_operator, mg_corrections, mg_get_operator and the
+ * learned column take single-problem hierarchies only.
+ */
+mpcg_status mg_hierarchy_setup_batched(const mg_operator* ops, int nprob, int levels, const mpcg_options* opt,
+                                       mg_hierarchy** out);
+int mg_num_problems(const mg_hierarchy* h);
+/*
+ * Problems of uneven size: one batched hierarchy per grid size (nclass of
+ * them, preferably each with its own stream in its options), solved
+ * concurrently.  b[c], x[c], iters[c] are the arguments of mpcg_solve for
+ * class c (iters may be NULL).  Returns the worst status of all problems.
+ */
+mpcg_status mpcg_solve_batched(mg_hierarchy* const* hs, int nclass, const double* const* b, double* const* x,
+                               double rtol, int maxit, int* const* iters);
+
 /* Number of grids and of search columns (grids + appended columns). */
 int mg_num_levels(const mg_hierarchy* h);
 int mg_num_columns(const mg_hierarchy* h);

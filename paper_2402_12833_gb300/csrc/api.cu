@@ -93,6 +93,8 @@ struct Solver {
   double *part_res = nullptr, *part_zaz = nullptr, *part_W = nullptr, *part_G = nullptr, *part_r = nullptr;
   double* small_scratch = nullptr;   // reduced values of the small solves
   unsigned* counters = nullptr;      // last-block counters of small_beta / small_alpha
+  int* flag = nullptr;               // "some problem still running" (batched loop condition)
+  int* kdone = nullptr;              // gathered (iterations, done) per problem
   double *res_hist = nullptr, *alpha_hist = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -190,6 +192,8 @@ struct Profiler {
 struct mg_hierarchy {
   int device = 0;
   int dim = 2, levels = 1;
+  int nb = 1;                  // problems in the batch (same grid, own operators)
+  int* active = nullptr;       // mixed path: problems still refining
   mpcg_options opt;
   cudaStream_t stream = 0;
   cudaStream_t cap_stream = nullptr;
@@ -243,34 +247,37 @@ mpcg_status build_solver(mg_hierarchy* h, Solver<T>& S) {
   S.C = h->levels + (h->net_on ? 1 : 0);
   S.m = h->opt.m;
   const int C = S.C;
-  CKS(S.mem.get(&S.x, gf.len, s));
-  CKS(S.mem.get(&S.r, gf.len, s));
-  CKS(S.mem.get(&S.b, gf.len, s));
-  CKS(S.mem.get(&S.Z, (size_t)C * gf.len, s));
-  CKS(S.mem.get(&S.AZ, (size_t)C * gf.len, s));
+  const size_t nb = (size_t)h->nb;   // all buffers hold the whole batch
+  CKS(S.mem.get(&S.x, gf.cp, s));
+  CKS(S.mem.get(&S.r, gf.cp, s));
+  CKS(S.mem.get(&S.b, gf.cp, s));
+  CKS(S.mem.get(&S.Z, (size_t)C * gf.cp, s));
+  CKS(S.mem.get(&S.AZ, (size_t)C * gf.cp, s));
   for (int j = 0; j < S.m; ++j) {
-    CKS(S.mem.get(&S.win.P[j], (size_t)C * gf.len, s));
-    CKS(S.mem.get(&S.win.AP[j], (size_t)C * gf.len, s));
+    CKS(S.mem.get(&S.win.P[j], (size_t)C * gf.cp, s));
+    CKS(S.mem.get(&S.win.AP[j], (size_t)C * gf.cp, s));
   }
   for (int j = 0; j <= J; ++j) {
     const GridDesc& g = h->lev[j].g;
     if (j < J) {
-      CKS(S.mem.get(&S.rlev[j], g.len, s));
-      CKS(S.mem.get(&S.zc[j], (size_t)(j + 1) * g.len, s));
+      CKS(S.mem.get(&S.rlev[j], g.cp, s));
+      CKS(S.mem.get(&S.zc[j], (size_t)(j + 1) * g.cp, s));
     }
     if (h->opt.nu > 2) {
-      CKS(S.mem.get(&S.tmp[j], g.len, s));
-      CKS(S.mem.get(&S.tmp2[j], g.len, s));
+      CKS(S.mem.get(&S.tmp[j], g.cp, s));
+      CKS(S.mem.get(&S.tmp2[j], g.cp, s));
     }
   }
-  CKS(S.mem.get(&S.state, 1, s));
-  CKS(S.mem.get(&S.part_res, 2 * (size_t)stream_blocks(gf), s));
-  CKS(S.mem.get(&S.part_zaz, (size_t)C * stream_blocks(gf), s));
-  CKS(S.mem.get(&S.part_W, (size_t)S.m * C * C * gram_chunks(gf), s));
-  CKS(S.mem.get(&S.part_G, (size_t)(C * (C + 1) / 2 + C) * stream_blocks(gf), s));
-  CKS(S.mem.get(&S.part_r, stream_blocks(gf), s));
-  CKS(S.mem.get(&S.small_scratch, kSmallScratchAlpha + kMaxCols * kMaxCols + 3 * kMaxCols, s));
-  CKS(S.mem.get(&S.counters, 2, s));
+  CKS(S.mem.get(&S.state, nb, s));
+  CKS(S.mem.get(&S.part_res, nb * 2 * stream_blocks(gf), s));
+  CKS(S.mem.get(&S.part_zaz, nb * C * stream_blocks(gf), s));
+  CKS(S.mem.get(&S.part_W, nb * S.m * C * C * gram_chunks(gf), s));
+  CKS(S.mem.get(&S.part_G, nb * (C * (C + 1) / 2 + C) * stream_blocks(gf), s));
+  CKS(S.mem.get(&S.part_r, nb * stream_blocks(gf), s));
+  CKS(S.mem.get(&S.small_scratch, nb * kSmallScratch, s));
+  CKS(S.mem.get(&S.counters, 2 * nb, s));
+  CKS(S.mem.get(&S.flag, 1, s));
+  CKS(S.mem.get(&S.kdone, 2 * nb, s));
   S.built = true;
   return MPCG_OK;
 }
@@ -282,15 +289,12 @@ mpcg_status ensure_hist(mg_hierarchy* h, Solver<T>& S, int maxit) {
   S.hist_mem.release();
   int cap = 64;
   while (cap < maxit + 1) cap *= 2;
-  CKS(S.hist_mem.get(&S.res_hist, cap, h->stream));
-  CKS(S.hist_mem.get(&S.alpha_hist, (size_t)cap * S.C, h->stream));
+  CKS(S.hist_mem.get(&S.res_hist, (size_t)cap * h->nb, h->stream));
+  CKS(S.hist_mem.get(&S.alpha_hist, (size_t)cap * S.C * h->nb, h->stream));
   S.hist_cap = cap;
   return MPCG_OK;
 }
 
-// The additive MG block Z = MG(r) (Section 2.2): restrict r to every grid,
-// solve on the coarsest, smooth on the others, prolong every correction to
-// the fine grid.  Column l of Z is the correction of grid l.
 // nu damped-Jacobi sweeps from zero on grid j: rr -> out.
 template <typename T>
 void enqueue_smooth(mg_hierarchy* h, Solver<T>& S, int j, const T* rr, T* out, const DevState* state,
@@ -335,7 +339,7 @@ void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState*
   cudaStream_t s2 = h->prof.on ? s : h->side[0], s3 = h->prof.on ? s : h->side[1];
   cudaEventRecord(h->ev_fork, s);
   cudaStreamWaitEvent(s2, h->ev_fork, 0);
-  enqueue_smooth<T>(h, S, J, r, Z + (size_t)J * h->lev[J].g.len, state, s2);
+  enqueue_smooth<T>(h, S, J, r, Z + (size_t)J * h->lev[J].g.cp, state, s2);
   cudaEventRecord(h->ev_fine, s2);
   const T* rj = r;
   for (int j = J; j >= 1; --j) {
@@ -344,7 +348,7 @@ void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState*
     if (j - 1 >= 1) {   // smoothing of grid j-1 can start now
       cudaEventRecord(h->ev_r[j - 1], s);
       cudaStreamWaitEvent(s3, h->ev_r[j - 1], 0);
-      enqueue_smooth<T>(h, S, j - 1, S.rlev[j - 1], S.zc[j - 1] + (size_t)(j - 1) * h->lev[j - 1].g.len, state, s3);
+      enqueue_smooth<T>(h, S, j - 1, S.rlev[j - 1], S.zc[j - 1] + (size_t)(j - 1) * h->lev[j - 1].g.cp, state, s3);
       cudaEventRecord(h->ev_sm[j - 1], s3);
     }
   }
@@ -359,11 +363,25 @@ void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState*
 }
 
 template <typename T>
+void enqueue_any(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
+
+template <typename T>
 void enqueue_prologue(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond, int use_cond,
                       cudaStream_t s) {
   const Level& L = h->lev[h->levels - 1];
   LAUNCH(h, K_RESIDUAL, s, launch_residual<T>(L.g, st_of<T>(L), S.b, S.x, S.r, S.part_res, s));
-  LAUNCH(h, K_INIT, s, launch_init(S.state, S.part_res, stream_blocks(L.g), S.res_hist, cond, use_cond, s));
+  // a batch decides its loop condition from all problems (enqueue_any)
+  LAUNCH(h, K_INIT, s, launch_init(S.state, h->nb, S.part_res, stream_blocks(L.g), S.res_hist, S.hist_cap, cond,
+                                   use_cond && h->nb == 1, s));
+  enqueue_any<T>(h, S, cond, use_cond, s);
+}
+
+// Batched graphs: the loop runs while any problem of the batch runs.
+template <typename T>
+void enqueue_any(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
+  if (h->nb == 1) return;
+  LAUNCH(h, K_CHECK, s, launch_any_running(S.state, h->nb, S.flag, s));
+  if (use_cond) LAUNCH(h, K_CHECK, s, launch_set_cond(S.flag, cond, s));
 }
 
 template <typename T>
@@ -379,13 +397,16 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
   }
   LAUNCH(h, K_SPMM, s, launch_spmm<T>(L.g, st_of<T>(L), S.Z, S.AZ, C, S.part_zaz, S.state, s));
   LAUNCH(h, K_GRAM, s, launch_gram_window<T>(L.g, S.win, S.Z, C, S.m, S.part_W, S.state, s));
-  LAUNCH(h, K_BETA, s, launch_small_beta(S.state, S.part_W, gram_chunks(L.g), C, S.small_scratch, S.counters, s));
+  LAUNCH(h, K_BETA, s, launch_small_beta(S.state, h->nb, S.part_W, gram_chunks(L.g), C, S.small_scratch, S.counters,
+                                         s));
   LAUNCH(h, K_ORTH, s, launch_orth_update<T>(L.g, S.win, S.Z, S.AZ, S.r, C, S.part_G, S.state, s));
-  LAUNCH(h, K_ALPHA, s, launch_small_alpha(S.state, S.part_G, stream_blocks(L.g), S.part_zaz, stream_blocks(L.g),
-                                          stream_blocks(L.g), C, S.alpha_hist, S.small_scratch + kSmallScratchAlpha,
-                                          S.counters + 1, s));
+  LAUNCH(h, K_ALPHA, s, launch_small_alpha(S.state, h->nb, S.part_G, stream_blocks(L.g), S.part_zaz,
+                                          stream_blocks(L.g), stream_blocks(L.g), C, S.alpha_hist,
+                                          (long long)S.hist_cap * C, S.small_scratch, S.counters, s));
   LAUNCH(h, K_UPDATE, s, launch_update_xr<T>(L.g, S.win, S.x, S.r, C, S.part_r, S.state, s));
-  LAUNCH(h, K_CHECK, s, launch_check(S.state, S.part_r, stream_blocks(L.g), S.res_hist, cond, use_cond, s));
+  LAUNCH(h, K_CHECK, s, launch_check(S.state, h->nb, S.part_r, stream_blocks(L.g), S.res_hist, S.hist_cap, cond,
+                                     use_cond && h->nb == 1, s));
+  enqueue_any<T>(h, S, cond, use_cond, s);
 }
 
 // Capture prologue + while(cond){body} as one graph.  On any failure the
@@ -450,9 +471,11 @@ void build_graph(mg_hierarchy* h, Solver<T>& S) {
   S.use_graph = true;
 }
 
-// Run prologue + loop for solver S (buffers b, x already filled).
+// Run prologue + loop for solver S (buffers b, x already filled).  Returns
+// per problem kd[2b] = iterations and kd[2b+1] = termination (1 converged,
+// 2 maxit, 3 breakdown).
 template <typename T>
-mpcg_status run_solver(mg_hierarchy* h, Solver<T>& S, DevState* host_state) {
+mpcg_status run_solver(mg_hierarchy* h, Solver<T>& S, std::vector<int>& kd) {
   cudaStream_t s = h->stream;
   const bool direct = h->force_direct || !h->opt.use_graph;
   if (!S.use_graph && !direct) build_graph<T>(h, S);
@@ -460,24 +483,38 @@ mpcg_status run_solver(mg_hierarchy* h, Solver<T>& S, DevState* host_state) {
   if (graph) {
     CK(cudaGraphLaunch(S.exec, s));
   } else {
-    // direct launches; the host reads the done flag after every iteration
+    // direct launches; the host reads the running flag after every iteration
     cudaGraphConditionalHandle dummy = 0;
     enqueue_prologue<T>(h, S, dummy, 0, s);
     for (;;) {
-      int done = 0;
-      CK(cudaMemcpyAsync(&done, &S.state->done, sizeof(int), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
+      int running = 0;
+      if (h->nb == 1) {
+        CK(cudaMemcpyAsync(&running, &S.state->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        running = running == 0;
+      } else {
+        CK(cudaMemcpyAsync(&running, S.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemsetAsync(S.flag, 0, sizeof(int), s));
+        CK(cudaStreamSynchronize(s));
+      }
       h->prof.flush();
-      if (done) break;
+      if (!running) break;
       enqueue_body<T>(h, S, dummy, 0, s);
     }
   }
-  CK(cudaMemcpyAsync(host_state, S.state, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  kd.assign(2 * (size_t)h->nb, 0);
+  launch_gather_kd(S.state, h->nb, S.kdone, s);
+  CK(cudaMemcpyAsync(kd.data(), S.kdone, sizeof(int) * 2 * h->nb, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
   if (graph) {
-    // the loop body ran once per x update, plus once more after a breakdown
-    const long long bodies = host_state->k + (host_state->done == 3 ? 1 : 0);
+    // the loop body ran once per x update of the slowest problem, plus once
+    // more after a breakdown
+    long long bodies = 0;
+    for (int b = 0; b < h->nb; ++b) {
+      const long long kb = kd[2 * b] + (kd[2 * b + 1] == 3 ? 1 : 0);
+      if (kb > bodies) bodies = kb;
+    }
     h->prof.live += S.prologue_launches + bodies * S.body_launches;
   }
   return MPCG_OK;
@@ -498,17 +535,18 @@ mpcg_status build_f32(mg_hierarchy* h) {
   const int S = h->dim == 3 ? 27 : 9;
   for (int j = 0; j < h->levels; ++j) {
     Level& L = h->lev[j];
-    CKS(h->mem.get(&L.st32, (size_t)S * L.g.len, s));
-    CKS(h->mem.get(&L.dinv32, L.g.len, s));
-    launch_convert_f32(L.st64, L.st32, (long long)S * L.g.len, s);
-    launch_convert_f32(L.dinv64, L.dinv32, L.g.len, s);
+    CKS(h->mem.get(&L.st32, (size_t)S * L.g.cp, s));
+    CKS(h->mem.get(&L.dinv32, L.g.cp, s));
+    launch_convert_f32(L.st64, L.st32, (long long)S * L.g.cp, s);
+    launch_convert_f32(L.dinv64, L.dinv32, L.g.cp, s);
   }
   const GridDesc& gf = h->lev[h->levels - 1].g;
-  CKS(h->mem.get(&h->b64, gf.len, s));
-  CKS(h->mem.get(&h->x64, gf.len, s));
-  CKS(h->mem.get(&h->r64, gf.len, s));
-  CKS(h->mem.get(&h->nrm, 4, s));
-  CKS(h->mem.get(&h->part_mix, 2 * (size_t)stream_blocks(gf), s));
+  CKS(h->mem.get(&h->b64, gf.cp, s));
+  CKS(h->mem.get(&h->x64, gf.cp, s));
+  CKS(h->mem.get(&h->r64, gf.cp, s));
+  CKS(h->mem.get(&h->nrm, 2 * (size_t)h->nb + 2, s));
+  CKS(h->mem.get(&h->part_mix, 2 * (size_t)h->nb * stream_blocks(gf), s));
+  CKS(h->mem.get(&h->active, h->nb, s));
   CK(cudaGetLastError());
   h->have32 = true;
   return MPCG_OK;
@@ -517,6 +555,15 @@ mpcg_status build_f32(mg_hierarchy* h) {
 mpcg_status check_h(const mg_hierarchy* h) {
   if (!h) {
     set_err("hierarchy is NULL");
+    return MPCG_ERR_ARG;
+  }
+  return MPCG_OK;
+}
+
+mpcg_status check_single(const mg_hierarchy* h) {
+  CKS(check_h(h));
+  if (h->nb != 1) {
+    set_err("this entry point takes a single-problem hierarchy");
     return MPCG_ERR_ARG;
   }
   return MPCG_OK;
@@ -580,13 +627,24 @@ void mg_hierarchy_destroy(mg_hierarchy* h) {
   delete h;
 }
 
-mpcg_status mg_hierarchy_setup(const mg_operator* A, int levels, const mpcg_options* opt_in, mg_hierarchy** out) {
+static mpcg_status setup_impl(const mg_operator* ops, int nb, int levels, const mpcg_options* opt_in,
+                              mg_hierarchy** out) {
   g_err.clear();
   if (!out) {
     set_err("out pointer is NULL");
     return MPCG_ERR_ARG;
   }
   *out = nullptr;
+  if (!ops || nb < 1) {
+    set_err("need at least one operator");
+    return MPCG_ERR_ARG;
+  }
+  const mg_operator* A = ops;
+  for (int b = 0; b < nb; ++b)
+    if (!ops[b].values_dev || ops[b].dim != A->dim || ops[b].nodes != A->nodes || ops[b].format != A->format) {
+      set_err("operator %d: NULL values or a grid that differs from operator 0", b);
+      return MPCG_ERR_ARG;
+    }
   if (!A || !A->values_dev) {
     set_err("operator or its values pointer is NULL");
     return MPCG_ERR_ARG;
@@ -630,6 +688,7 @@ mpcg_status mg_hierarchy_setup(const mg_operator* A, int levels, const mpcg_opti
   cudaGetDevice(&h->device);
   h->dim = A->dim;
   h->levels = levels;
+  h->nb = nb;
   h->opt = opt;
   h->stream = (cudaStream_t)opt.stream;
   h->n0 = (int)n0;
@@ -656,35 +715,42 @@ mpcg_status mg_hierarchy_setup(const mg_operator* A, int levels, const mpcg_opti
   const int S = A->dim == 3 ? 27 : 9;
   cudaStream_t s = h->stream;
   for (int j = 0; j < levels; ++j) {
-    h->lev[j].g = make_grid(A->dim, (q >> (levels - 1 - j)) - 1);
-    if ((st = h->mem.get(&h->lev[j].st64, (size_t)S * h->lev[j].g.len, s)) != MPCG_OK) return fail(st);
-    if ((st = h->mem.get(&h->lev[j].dinv64, h->lev[j].g.len, s)) != MPCG_OK) return fail(st);
+    h->lev[j].g = make_grid(A->dim, (q >> (levels - 1 - j)) - 1, nb);
+    if ((st = h->mem.get(&h->lev[j].st64, (size_t)S * h->lev[j].g.cp, s)) != MPCG_OK) return fail(st);
+    if ((st = h->mem.get(&h->lev[j].dinv64, h->lev[j].g.cp, s)) != MPCG_OK) return fail(st);
   }
   const int J = levels - 1;
-  // fine stencil: compact [S][n] -> padded [S][len]
-  launch_pack<double, double>(h->lev[J].g, A->values_dev, h->lev[J].g.n, h->lev[J].st64, S, s);
+  // fine stencils: compact [S][n] per problem -> padded planes
+  for (int b = 0; b < nb; ++b)
+    launch_pack<double, double>(h->lev[J].g, ops[b].values_dev, h->lev[J].g.n,
+                                h->lev[J].st64 + (size_t)b * h->lev[J].g.len, S, s);
   for (int j = J; j >= 1; --j) launch_galerkin(h->lev[j].g, h->lev[j - 1].g, h->lev[j].st64, h->lev[j - 1].st64, s);
   for (int j = 0; j < levels; ++j) launch_dinv<double>(h->lev[j].g, h->lev[j].st64, h->lev[j].dinv64, opt.omega, s);
-  if ((st = h->mem.get(&h->L0, (size_t)n0 * n0, s)) != MPCG_OK) return fail(st);
-  if ((st = h->mem.get(&h->info, 4, s)) != MPCG_OK) return fail(st);
-  if ((st = h->mem.get(&h->rdiag0, n0, s)) != MPCG_OK) return fail(st);
-  launch_dense_from_stencil(h->lev[0].g, h->lev[0].st64, h->L0, s);
-  launch_cholesky(h->L0, h->rdiag0, (int)n0, h->info, s);
-  int info = 0;
-  if (cudaMemcpyAsync(&info, h->info, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+  const size_t nn = (size_t)n0 * n0;
+  if ((st = h->mem.get(&h->L0, nn * nb, s)) != MPCG_OK) return fail(st);
+  if ((st = h->mem.get(&h->info, nb, s)) != MPCG_OK) return fail(st);
+  if ((st = h->mem.get(&h->rdiag0, (size_t)n0 * nb, s)) != MPCG_OK) return fail(st);
+  for (int b = 0; b < nb; ++b) {
+    launch_dense_from_stencil(h->lev[0].g, h->lev[0].st64 + (size_t)b * h->lev[0].g.len, h->L0 + nn * b, s);
+    launch_cholesky(h->L0 + nn * b, h->rdiag0 + (size_t)n0 * b, (int)n0, h->info + b, s);
+  }
+  std::vector<int> info(nb, 0);
+  if (cudaMemcpyAsync(info.data(), h->info, sizeof(int) * nb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     set_err("setup kernels failed: %s", cudaGetErrorString(cudaGetLastError()));
     return fail(MPCG_ERR_CUDA);
   }
-  if (info != 0) {
-    set_err("coarsest operator is not positive definite (Cholesky pivot %d)", info);
-    return fail(MPCG_ERR_NOT_SPD);
-  }
+  for (int b = 0; b < nb; ++b)
+    if (info[b] != 0) {
+      set_err("coarsest operator of problem %d is not positive definite (Cholesky pivot %d)", b, info[b]);
+      return fail(MPCG_ERR_NOT_SPD);
+    }
   {
     double* X = nullptr;
-    if ((st = h->mem.get(&h->A0inv, (size_t)n0 * n0, s)) != MPCG_OK) return fail(st);
-    if ((st = h->mem.get(&X, (size_t)n0 * n0, s)) != MPCG_OK) return fail(st);
-    launch_coarse_inverse(h->L0, h->rdiag0, X, h->A0inv, (int)n0, s);
+    if ((st = h->mem.get(&h->A0inv, nn * nb, s)) != MPCG_OK) return fail(st);
+    if ((st = h->mem.get(&X, nn, s)) != MPCG_OK) return fail(st);
+    for (int b = 0; b < nb; ++b)
+      launch_coarse_inverse(h->L0 + nn * b, h->rdiag0 + (size_t)n0 * b, X, h->A0inv + nn * b, (int)n0, s);
   }
   if ((st = build_solver<double>(h, h->s64)) != MPCG_OK) return fail(st);
   if (opt.precision == MPCG_MIXED) {
@@ -699,28 +765,53 @@ mpcg_status mg_hierarchy_setup(const mg_operator* A, int levels, const mpcg_opti
   return MPCG_OK;
 }
 
+mpcg_status mg_hierarchy_setup(const mg_operator* A_fine, int levels, const mpcg_options* opt, mg_hierarchy** out) {
+  return setup_impl(A_fine, 1, levels, opt, out);
+}
+
+mpcg_status mg_hierarchy_setup_batched(const mg_operator* ops, int nprob, int levels, const mpcg_options* opt,
+                                       mg_hierarchy** out) {
+  return setup_impl(ops, nprob, levels, opt, out);
+}
+
+int mg_num_problems(const mg_hierarchy* h) { return h ? h->nb : -1; }
+
 static mpcg_status solve_fp64(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, int* iters_out,
                               double* res_hist, double* alpha_hist) {
   Solver<double>& S = h->s64;
   cudaStream_t s = h->stream;
   const GridDesc& gf = h->lev[h->levels - 1].g;
+  const int nb = h->nb;
   CKS(ensure_hist(h, S, maxit));
-  LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, b, gf.n, S.b, 1, s));
-  LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, x, gf.n, S.x, 1, s));
-  LAUNCH(h, K_AUX, s, launch_set_params(S.state, rtol, maxit, S.m, S.C, h->opt.drop_delta, h->opt.pinv_tau, s));
-  DevState hs;
-  CKS(run_solver<double>(h, S, &hs));
-  LAUNCH(h, K_PACK, s, launch_unpack<double, double>(gf, S.x, x, gf.n, 1, s));
-  if (res_hist) CK(cudaMemcpyAsync(res_hist, S.res_hist, sizeof(double) * (hs.k + 1), cudaMemcpyDeviceToHost, s));
-  if (alpha_hist && hs.k > 0)
-    CK(cudaMemcpyAsync(alpha_hist, S.alpha_hist, sizeof(double) * hs.k * S.C, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  if (iters_out) *iters_out = hs.k;
-  if (hs.done == 3) {
-    set_err("breakdown at iteration %d (non-finite value or every column dropped)", hs.k);
-    return MPCG_ERR_BREAKDOWN;
+  for (int p = 0; p < nb; ++p) {
+    LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, b + (size_t)p * gf.n, gf.n, S.b + (size_t)p * gf.len, 1, s));
+    LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, x + (size_t)p * gf.n, gf.n, S.x + (size_t)p * gf.len, 1, s));
   }
-  return hs.done == 1 ? MPCG_OK : MPCG_NOT_CONVERGED;
+  LAUNCH(h, K_AUX, s, launch_set_params(S.state, nb, rtol, maxit, S.m, S.C, h->opt.drop_delta, h->opt.pinv_tau, s));
+  std::vector<int> kd;
+  CKS(run_solver<double>(h, S, kd));
+  for (int p = 0; p < nb; ++p) {
+    LAUNCH(h, K_PACK, s, launch_unpack<double, double>(gf, S.x + (size_t)p * gf.len, x + (size_t)p * gf.n, gf.n, 1, s));
+    const int k = kd[2 * p];
+    if (res_hist)
+      CK(cudaMemcpyAsync(res_hist + (size_t)p * (maxit + 1), S.res_hist + (size_t)p * S.hist_cap,
+                         sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, s));
+    if (alpha_hist && k > 0)
+      CK(cudaMemcpyAsync(alpha_hist + (size_t)p * maxit * S.C, S.alpha_hist + (size_t)p * S.hist_cap * S.C,
+                         sizeof(double) * k * S.C, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  mpcg_status result = MPCG_OK;
+  for (int p = 0; p < nb; ++p) {
+    if (iters_out) iters_out[p] = kd[2 * p];
+    if (kd[2 * p + 1] == 3) {
+      set_err("breakdown in problem %d at iteration %d (non-finite value or every column dropped)", p, kd[2 * p]);
+      result = MPCG_ERR_BREAKDOWN;
+    } else if (kd[2 * p + 1] != 1 && result == MPCG_OK) {
+      result = MPCG_NOT_CONVERGED;
+    }
+  }
+  return result;
 }
 
 static mpcg_status solve_mixed(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, int* iters_out,
@@ -732,53 +823,85 @@ static mpcg_status solve_mixed(mg_hierarchy* h, const double* b, double* x, doub
   const Level& L = h->lev[h->levels - 1];
   const GridDesc& gf = L.g;
   CKS(ensure_hist(h, S, maxit));
-  LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, b, gf.n, h->b64, 1, s));
-  LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, x, gf.n, h->x64, 1, s));
-  int total = 0, nhist = 0;
-  mpcg_status result = MPCG_NOT_CONVERGED;
-  std::vector<double> inner(maxit + 1);
+  const int nb = h->nb;
+  for (int p = 0; p < nb; ++p) {
+    LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, b + (size_t)p * gf.n, gf.n, h->b64 + (size_t)p * gf.len, 1, s));
+    LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, x + (size_t)p * gf.n, gf.n, h->x64 + (size_t)p * gf.len, 1, s));
+  }
+  // every problem refines on its own true FP64 residual; the problems run
+  // their FP32 inner solves together, converged ones with a zero right-hand
+  // side (their inner solve stops at once)
+  std::vector<int> total(nb, 0), nhist(nb, 0), status(nb, 0), act(nb, 1);
+  std::vector<double> nrm(2 * (size_t)nb), inner(maxit + 1);
   for (int outer = 0; outer <= h->opt.max_outer; ++outer) {
     LAUNCH(h, K_RESIDUAL, s, launch_residual<double>(gf, L.st64, h->b64, h->x64, h->r64, h->part_mix, s));
-    LAUNCH(h, K_AUX, s, launch_sum_partials(h->part_mix, 2, stream_blocks(gf), h->nrm, s));
-    double nrm[2];
-    CK(cudaMemcpyAsync(nrm, h->nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LAUNCH(h, K_AUX, s, launch_sum_partials(h->part_mix, nb, 2, stream_blocks(gf), h->nrm, s));
+    CK(cudaMemcpyAsync(nrm.data(), h->nrm, 2 * sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    const double rn = sqrt(nrm[0]), bn = sqrt(nrm[1]);
-    if (!isfinite(rn)) {
-      set_err("non-finite residual in refinement step %d", outer);
-      result = MPCG_ERR_BREAKDOWN;
-      break;
+    int running = 0, budget = 0;
+    for (int p = 0; p < nb; ++p) {
+      if (!act[p]) continue;
+      const double rn = sqrt(nrm[2 * p]), bn = sqrt(nrm[2 * p + 1]);
+      double* rh = res_hist ? res_hist + (size_t)p * (maxit + 1) : nullptr;
+      if (outer == 0 && rh) rh[nhist[p]++] = bn > 0 ? rn / bn : 0.0;
+      if (!isfinite(rn)) {
+        status[p] = 3;
+        act[p] = 0;
+      } else if (bn == 0.0 || rn <= rtol * bn) {
+        status[p] = 1;
+        act[p] = 0;
+      } else if (total[p] >= maxit || outer == h->opt.max_outer) {
+        status[p] = 2;
+        act[p] = 0;
+      } else {
+        ++running;
+        budget = std::max(budget, maxit - total[p]);
+      }
     }
-    if (outer == 0 && res_hist) res_hist[nhist++] = bn > 0 ? rn / bn : 0.0;
-    if (bn == 0.0 || rn <= rtol * bn) {
-      result = MPCG_OK;
-      break;
-    }
-    if (total >= maxit || outer == h->opt.max_outer) break;
-    LAUNCH(h, K_AUX, s, launch_scale_to_f32(gf, h->r64, h->nrm, S.b, s));
-    CK(cudaMemsetAsync(S.x, 0, sizeof(float) * gf.len, s));
-    LAUNCH(h, K_AUX, s, launch_set_params(S.state, h->opt.inner_rtol, maxit - total, S.m, S.C, h->opt.inner_drop_delta,
+    if (!running) break;
+    CK(cudaMemcpyAsync(h->active, act.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s));
+    LAUNCH(h, K_AUX, s, launch_scale_to_f32(gf, h->r64, h->nrm, h->active, S.b, s));
+    CK(cudaMemsetAsync(S.x, 0, sizeof(float) * gf.cp, s));
+    LAUNCH(h, K_AUX, s, launch_set_params(S.state, nb, h->opt.inner_rtol, budget, S.m, S.C, h->opt.inner_drop_delta,
                                           h->opt.inner_pinv_tau, s));
-    DevState hs;
-    CKS(run_solver<float>(h, S, &hs));
-    if (res_hist && hs.k > 0) {
-      CK(cudaMemcpyAsync(inner.data(), S.res_hist, sizeof(double) * (hs.k + 1), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      for (int i = 1; i <= hs.k && nhist <= maxit; ++i) res_hist[nhist++] = inner[i] * rn / bn;
-    }
-    total += hs.k;
-    if (hs.done == 3) {
-      set_err("breakdown in the FP32 inner solve of refinement step %d", outer);
-      result = MPCG_ERR_BREAKDOWN;
-      break;
+    std::vector<int> kd;
+    CKS(run_solver<float>(h, S, kd));
+    for (int p = 0; p < nb; ++p) {
+      if (!act[p]) continue;
+      const int k = kd[2 * p];
+      if (res_hist && k > 0) {
+        double* rh = res_hist + (size_t)p * (maxit + 1);
+        const double rn = sqrt(nrm[2 * p]), bn = sqrt(nrm[2 * p + 1]);
+        CK(cudaMemcpyAsync(inner.data(), S.res_hist + (size_t)p * S.hist_cap, sizeof(double) * (k + 1),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int i = 1; i <= k && nhist[p] <= maxit; ++i) rh[nhist[p]++] = inner[i] * rn / bn;
+      }
+      total[p] += k;
+      if (kd[2 * p + 1] == 3) {
+        status[p] = 3;
+        act[p] = 0;
+      } else if (k == 0) {
+        status[p] = 2;
+        act[p] = 0;
+      }
     }
     LAUNCH(h, K_AUX, s, launch_axpy_mixed(gf, h->x64, S.x, h->nrm, s));
-    if (hs.k == 0) break;
   }
-  LAUNCH(h, K_PACK, s, launch_unpack<double, double>(gf, h->x64, x, gf.n, 1, s));
+  for (int p = 0; p < nb; ++p)
+    LAUNCH(h, K_PACK, s, launch_unpack<double, double>(gf, h->x64 + (size_t)p * gf.len, x + (size_t)p * gf.n, gf.n, 1, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
-  if (iters_out) *iters_out = total;
+  mpcg_status result = MPCG_OK;
+  for (int p = 0; p < nb; ++p) {
+    if (iters_out) iters_out[p] = total[p];
+    if (status[p] == 3) {
+      set_err("breakdown in the FP32 inner solve of problem %d", p);
+      result = MPCG_ERR_BREAKDOWN;
+    } else if (status[p] != 1 && result == MPCG_OK) {
+      result = MPCG_NOT_CONVERGED;
+    }
+  }
   return result;
 }
 
@@ -797,19 +920,20 @@ mpcg_status mpcg_solve(mg_hierarchy* h, const double* b, double* x, double rtol,
   CK(cudaSetDevice(h->device));
   cudaStream_t s = h->stream;
   const GridDesc& gf = h->lev[h->levels - 1].g;
-  const size_t nb = sizeof(double) * gf.n;
+  const size_t ntot = (size_t)gf.n * h->nb;   // unknowns of all problems of the batch
+  const size_t nb = sizeof(double) * ntot;
   const bool bdev = is_device_pointer(b), xdev = is_device_pointer(x);
   const double* bd = b;
   double* xd = x;
   if (!bdev || !xdev) {
-    if (!h->stage) CKS(h->mem.get(&h->stage, 2 * (size_t)gf.n, s));
+    if (!h->stage) CKS(h->mem.get(&h->stage, 2 * ntot, s));
     if (!bdev) {
       CK(cudaMemcpyAsync(h->stage, b, nb, cudaMemcpyHostToDevice, s));
       bd = h->stage;
     }
     if (!xdev) {
-      CK(cudaMemcpyAsync(h->stage + gf.n, x, nb, cudaMemcpyHostToDevice, s));
-      xd = h->stage + gf.n;
+      CK(cudaMemcpyAsync(h->stage + ntot, x, nb, cudaMemcpyHostToDevice, s));
+      xd = h->stage + ntot;
     }
   }
   h->prof.reset();
@@ -855,7 +979,7 @@ mpcg_status mpcg_solve_profiled(mg_hierarchy* h, const double* b, double* x, dou
 
 mpcg_status mg_apply_operator(mg_hierarchy* h, int level, const double* X, double* Y, int ncols) {
   g_err.clear();
-  CKS(check_h(h));
+  CKS(check_single(h));
   if (level < 0 || level >= h->levels || ncols < 1 || !X || !Y) {
     set_err("bad level, column count or pointer");
     return MPCG_ERR_ARG;
@@ -884,7 +1008,7 @@ mpcg_status mg_apply_operator(mg_hierarchy* h, int level, const double* X, doubl
 
 mpcg_status mg_corrections(mg_hierarchy* h, const double* r, double* Z) {
   g_err.clear();
-  CKS(check_h(h));
+  CKS(check_single(h));
   if (!r || !Z) {
     set_err("NULL pointer");
     return MPCG_ERR_ARG;
@@ -903,7 +1027,7 @@ mpcg_status mg_corrections(mg_hierarchy* h, const double* r, double* Z) {
 
 mpcg_status mg_get_operator(mg_hierarchy* h, int level, double* planes) {
   g_err.clear();
-  CKS(check_h(h));
+  CKS(check_single(h));
   if (level < 0 || level >= h->levels || !planes) {
     set_err("bad level or pointer");
     return MPCG_ERR_ARG;
@@ -924,8 +1048,8 @@ mpcg_status mg_get_operator(mg_hierarchy* h, int level, double* planes) {
 namespace {
 
 mpcg_status net_check_grid(const mg_hierarchy* h) {
-  if (h->dim != 2) {
-    set_err("the learned column is implemented for 2D grids");
+  if (h->dim != 2 || h->nb != 1) {
+    set_err("the learned column is implemented for single (unbatched) 2D problems");
     return MPCG_ERR_ARG;
   }
   return MPCG_OK;

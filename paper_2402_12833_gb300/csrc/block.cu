@@ -6,7 +6,8 @@
 //   * the update x += P alpha, r -= A P alpha with ||r||^2.
 //
 // These kernels stream the padded arrays (pads are zero, so they take part
-// harmlessly) in 16-byte vectors: 4 floats or 2 doubles per thread and step.
+// harmlessly) in 16-byte vectors: 4 floats or 2 doubles per thread and step;
+// blockIdx.y selects the problem of a batch (see common.cuh).
 // Reductions are deterministic: every block writes its partial sums
 // (value-major, fixed block count) and one small kernel adds them in a fixed
 // order.  In the FP32 path each thread sums at most 64 points in FP32 and the
@@ -24,13 +25,16 @@ namespace {
 template <typename T, int C>
 __global__ void __launch_bounds__(kBlock, 3) k_gram_window(GridDesc g, Window<T> win, const T* __restrict__ Z,
                                                         double* part, int nchunks, const DevState* state) {
+  const int pb = blockIdx.y;
+  state += pb;
   if (state->done) return;
   const int m = state->m;
   const int jj = blockIdx.x % m, chunk = blockIdx.x / m;
   if (jj >= state->count) return;
   const int slot = (state->newest - jj + m) % m;
-  const T* AP = win.AP[slot] + g.G;
-  const T* Zb = Z + g.G;
+  const long long bo = (long long)pb * g.len + g.G;
+  const T* AP = win.AP[slot] + bo;
+  const T* Zb = Z + bo;
   constexpr int W = Vec<T>::W;
   const long long ngroups = g.npts / W;
   const long long per = (ngroups + nchunks - 1) / nchunks;
@@ -45,9 +49,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_gram_window(GridDesc g, Window<T>
     const long long i = q * W;
     T z[C][W], ap[C][W];
 #pragma unroll
-    for (int b = 0; b < C; ++b) Vec<T>::load_keep(Zb + (long long)b * g.len + i, z[b]);
+    for (int b = 0; b < C; ++b) Vec<T>::load_keep(Zb + (long long)b * g.cp + i, z[b]);
 #pragma unroll
-    for (int a = 0; a < C; ++a) Vec<T>::load(AP + (long long)a * g.len + i, ap[a]);
+    for (int a = 0; a < C; ++a) Vec<T>::load(AP + (long long)a * g.cp + i, ap[a]);
 #pragma unroll
     for (int a = 0; a < C; ++a)
 #pragma unroll
@@ -55,7 +59,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_gram_window(GridDesc g, Window<T>
 #pragma unroll
         for (int w = 0; w < W; ++w) acc[a * C + b] = fma(ap[a][w], z[b][w], acc[a * C + b]);
   }
-  double* pj = part + (long long)jj * C * C * nchunks;
+  double* pj = part + ((long long)pb * m + jj) * C * C * nchunks;
   block_sum_store<T, C * C>(acc, pj, nchunks, chunk);
 }
 
@@ -63,9 +67,12 @@ template <typename T, int C>
 __global__ void __launch_bounds__(kBlock, 2) k_orth_update(GridDesc g, Window<T> win, const T* __restrict__ Z,
                                                         const T* __restrict__ AZ, const T* __restrict__ r,
                                                         double* part, const DevState* state) {
+  const int pb = blockIdx.y;
+  state += pb;
   if (state->done) return;
   const int cnt = state->count, m = state->m, newest = state->newest;
   const int ns = (newest + 1) % m;
+  const long long bo = (long long)pb * g.len + g.G;
   __shared__ T beta[kMaxWindow][C][C];
   __shared__ const T* pp[kMaxWindow];
   __shared__ const T* app[kMaxWindow];
@@ -75,15 +82,15 @@ __global__ void __launch_bounds__(kBlock, 2) k_orth_update(GridDesc g, Window<T>
   }
   for (int jj = threadIdx.x; jj < cnt; jj += blockDim.x) {
     const int slot = (newest - jj + m) % m;
-    pp[jj] = win.P[slot] + g.G;
-    app[jj] = win.AP[slot] + g.G;
+    pp[jj] = win.P[slot] + bo;
+    app[jj] = win.AP[slot] + bo;
   }
   __syncthreads();
-  T* Pn = win.P[ns] + g.G;
-  T* APn = win.AP[ns] + g.G;
-  const T* Zb = Z + g.G;
-  const T* AZb = AZ + g.G;
-  const T* rb = r + g.G;
+  T* Pn = win.P[ns] + bo;
+  T* APn = win.AP[ns] + bo;
+  const T* Zb = Z + bo;
+  const T* AZb = AZ + bo;
+  const T* rb = r + bo;
   constexpr int W = Vec<T>::W;
   constexpr int NG = C * (C + 1) / 2;
   T acc[NG + C];
@@ -96,8 +103,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_orth_update(GridDesc g, Window<T>
     T p[C][W], ap[C][W];
 #pragma unroll
     for (int b = 0; b < C; ++b) {
-      Vec<T>::load(Zb + (long long)b * g.len + i, p[b]);
-      Vec<T>::load(AZb + (long long)b * g.len + i, ap[b]);
+      Vec<T>::load(Zb + (long long)b * g.cp + i, p[b]);
+      Vec<T>::load(AZb + (long long)b * g.cp + i, ap[b]);
     }
     for (int jj = 0; jj < cnt; ++jj) {
       const T* Pj = pp[jj];
@@ -105,8 +112,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_orth_update(GridDesc g, Window<T>
       T pa[C][W], apa[C][W];
 #pragma unroll
       for (int a = 0; a < C; ++a) {
-        Vec<T>::load(Pj + (long long)a * g.len + i, pa[a]);
-        Vec<T>::load(APj + (long long)a * g.len + i, apa[a]);
+        Vec<T>::load(Pj + (long long)a * g.cp + i, pa[a]);
+        Vec<T>::load(APj + (long long)a * g.cp + i, apa[a]);
       }
 #pragma unroll
       for (int a = 0; a < C; ++a)
@@ -125,8 +132,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_orth_update(GridDesc g, Window<T>
     int k = 0;
 #pragma unroll
     for (int a = 0; a < C; ++a) {
-      Vec<T>::store(Pn + (long long)a * g.len + i, p[a]);
-      Vec<T>::store(APn + (long long)a * g.len + i, ap[a]);
+      Vec<T>::store(Pn + (long long)a * g.cp + i, p[a]);
+      Vec<T>::store(APn + (long long)a * g.cp + i, ap[a]);
 #pragma unroll
       for (int b = a; b < C; ++b) {
 #pragma unroll
@@ -140,18 +147,21 @@ __global__ void __launch_bounds__(kBlock, 2) k_orth_update(GridDesc g, Window<T>
       for (int w = 0; w < W; ++w) acc[NG + a] = fma(p[a][w], rv[w], acc[NG + a]);
     }
   }
-  block_sum_store<T, NG + C>(acc, part, gridDim.x, blockIdx.x);
+  block_sum_store<T, NG + C>(acc, part + (long long)pb * (NG + C) * gridDim.x, gridDim.x, blockIdx.x);
 }
 
 template <typename T, int C>
 __global__ void __launch_bounds__(kBlock) k_update_xr(GridDesc g, Window<T> win, T* __restrict__ x,
                                                       T* __restrict__ r, double* part, const DevState* state) {
+  const int pb = blockIdx.y;
+  state += pb;
   if (state->done) return;
   const int newest = state->newest;
-  const T* P = win.P[newest] + g.G;
-  const T* AP = win.AP[newest] + g.G;
-  T* xb = x + g.G;
-  T* rb = r + g.G;
+  const long long bo = (long long)pb * g.len + g.G;
+  const T* P = win.P[newest] + bo;
+  const T* AP = win.AP[newest] + bo;
+  T* xb = x + bo;
+  T* rb = r + bo;
   T al[C];
 #pragma unroll
   for (int a = 0; a < C; ++a) al[a] = (T)state->alpha[a];
@@ -165,8 +175,8 @@ __global__ void __launch_bounds__(kBlock) k_update_xr(GridDesc g, Window<T> win,
 #pragma unroll
     for (int a = 0; a < C; ++a) {
       T pv[W], av[W];
-      Vec<T>::load(P + (long long)a * g.len + i, pv);
-      Vec<T>::load(AP + (long long)a * g.len + i, av);
+      Vec<T>::load(P + (long long)a * g.cp + i, pv);
+      Vec<T>::load(AP + (long long)a * g.cp + i, av);
 #pragma unroll
       for (int w = 0; w < W; ++w) {
         px[w] = fma(pv[w], al[a], px[w]);
@@ -185,7 +195,7 @@ __global__ void __launch_bounds__(kBlock) k_update_xr(GridDesc g, Window<T> win,
     Vec<T>::store(xb + i, xv);
     Vec<T>::store(rb + i, rv);
   }
-  block_sum_store<T, 1>(acc, part, gridDim.x, blockIdx.x);
+  block_sum_store<T, 1>(acc, part + (long long)pb * gridDim.x, gridDim.x, blockIdx.x);
 }
 
 }  // namespace
@@ -229,21 +239,21 @@ template <typename T>
 void launch_gram_window(const GridDesc& g, Window<T> win, const T* Z, int C, int m, double* part,
                         const DevState* state, cudaStream_t s) {
   const int nch = gram_chunks(g);
-  MPCG_C_SWITCH(C, (k_gram_window<T, CC><<<nch * m, kBlock, 0, s>>>(g, win, Z, part, nch, state)));
+  MPCG_C_SWITCH(C, (k_gram_window<T, CC><<<dim3(nch * m, g.nb), kBlock, 0, s>>>(g, win, Z, part, nch, state)));
 }
 
 template <typename T>
 void launch_orth_update(const GridDesc& g, Window<T> win, const T* Z, const T* AZ, const T* r, int C, double* part,
                         const DevState* state, cudaStream_t s) {
   const int nb = stream_blocks(g);
-  MPCG_C_SWITCH(C, (k_orth_update<T, CC><<<nb, kBlock, 0, s>>>(g, win, Z, AZ, r, part, state)));
+  MPCG_C_SWITCH(C, (k_orth_update<T, CC><<<dim3(nb, g.nb), kBlock, 0, s>>>(g, win, Z, AZ, r, part, state)));
 }
 
 template <typename T>
 void launch_update_xr(const GridDesc& g, Window<T> win, T* x, T* r, int C, double* part, const DevState* state,
                       cudaStream_t s) {
   const int nb = stream_blocks(g);
-  MPCG_C_SWITCH(C, (k_update_xr<T, CC><<<nb, kBlock, 0, s>>>(g, win, x, r, part, state)));
+  MPCG_C_SWITCH(C, (k_update_xr<T, CC><<<dim3(nb, g.nb), kBlock, 0, s>>>(g, win, x, r, part, state)));
 }
 
 template void launch_gram_window<double>(const GridDesc&, Window<double>, const double*, int, int, double*,

@@ -31,6 +31,12 @@ constexpr int kMaxWindow = MPCG_MAX_WINDOW;
 constexpr int kMaxLevels = 12;
 constexpr int kBlock = 256;
 
+// A batch of nb problems on the same grid stores every vector, column and
+// stencil plane as nb consecutive padded arrays of len elements: problem b of
+// column c starts at c * cp + b * len with the column pitch cp = nb * len.
+// Because each padded array carries its own zero guards, stencils and
+// transfers never reach from one problem into the next.  Kernels take the
+// problem index from blockIdx.y (nb = 1 is the single-problem case).
 struct GridDesc {
   int dim;        // 2 or 3
   int n1;         // interior nodes per side
@@ -38,12 +44,15 @@ struct GridDesc {
   int p;          // pitch = n1 + 1
   long long G;    // guard elements before the first entry
   long long npts; // p^dim (entries of the padded box)
-  long long len;  // G + npts (allocated elements per vector)
+  long long len;  // 2G + npts rounded up (elements per problem per vector)
   long long n;    // interior unknowns n1^dim
+  int nb;         // problems in the batch
+  long long cp;   // column / plane pitch = nb * len
 };
 
-inline GridDesc make_grid(int dim, int n1) {
+inline GridDesc make_grid(int dim, int n1, int nb = 1) {
   GridDesc g;
+  g.nb = nb;
   g.dim = dim;
   g.n1 = n1;
   g.p = n1 + 1;
@@ -61,6 +70,7 @@ inline GridDesc make_grid(int dim, int n1) {
   // plane reach up to p*p + p elements past the box
   g.len = (2 * g.G + g.npts + 31) / 32 * 32;
   g.n = dim == 3 ? (long long)n1 * n1 * n1 : (long long)n1 * n1;
+  g.cp = (long long)nb * g.len;
   return g;
 }
 

@@ -82,22 +82,27 @@ void launch_update_xr(const GridDesc& g, Window<T> win, T* x, T* r, int C, doubl
                       const DevState* state, cudaStream_t s);
 
 // ---- small.cu ------------------------------------------------------------
-void launch_init(DevState* st, const double* part_res, int nblk, double* res_hist,
+void launch_init(DevState* st, int nb, const double* part_res, int nblk, double* res_hist, long long hist_stride,
                  cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
 // The small solves reduce their partial sums with kSmallGrid blocks; the last
 // block to finish (atomic counter, zero between launches) does the solve.
 // scratch holds the reduced values (>= m C^2 + C^2 + 3C doubles).
 constexpr int kSmallGrid = 96;
 constexpr int kSmallScratchAlpha = kMaxWindow * kMaxCols * kMaxCols;   // offset of small_alpha's values
-void launch_small_beta(DevState* st, const double* part_W, int nchunks, int C, double* scratch, unsigned* counter,
-                       cudaStream_t s);
-void launch_small_alpha(DevState* st, const double* part_G, int nblk_G, const double* part_zaz, int nblk_zaz,
-                        int zaz_stride, int C, double* alpha_hist, double* scratch, unsigned* counter,
-                        cudaStream_t s);
-void launch_check(DevState* st, const double* part_r, int nblk, double* res_hist,
+constexpr int kSmallScratch = kSmallScratchAlpha + kMaxCols * kMaxCols + 3 * kMaxCols;   // per problem
+void launch_small_beta(DevState* st, int nb, const double* part_W, int nchunks, int C, double* scratch,
+                       unsigned* counter, cudaStream_t s);
+void launch_small_alpha(DevState* st, int nb, const double* part_G, int nblk_G, const double* part_zaz, int nblk_zaz,
+                        int zaz_stride, int C, double* alpha_hist, long long ahist_stride, double* scratch,
+                        unsigned* counter, cudaStream_t s);
+void launch_check(DevState* st, int nb, const double* part_r, int nblk, double* res_hist, long long hist_stride,
                   cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
-void launch_set_params(DevState* st, double rtol, int maxit, int m, int C, double delta, double tau,
+void launch_set_params(DevState* st, int nb, double rtol, int maxit, int m, int C, double delta, double tau,
                        cudaStream_t s);
+// batched graphs: flag |= any problem running; then cond = flag, flag = 0
+void launch_any_running(const DevState* st, int nb, int* flag, cudaStream_t s);
+void launch_set_cond(int* flag, cudaGraphConditionalHandle cond, cudaStream_t s);
+void launch_gather_kd(const DevState* st, int nb, int* out, cudaStream_t s);
 // Cholesky of the dense coarsest matrix (in place, lower); info[0] = 0 or the
 // failing pivot + 1
 void launch_dense_from_stencil(const GridDesc& g, const double* st, double* dense, cudaStream_t s);
@@ -109,12 +114,12 @@ template <typename T>
 void launch_coarse_solve(const GridDesc& g, const double* inv, const T* r, T* out, const DevState* state,
                          cudaStream_t s);
 // ||r||^2 style sum of partials (value-major) into out[nv]
-void launch_sum_partials(const double* part, int nv, int nblk, double* out, cudaStream_t s);
+void launch_sum_partials(const double* part, int nb, int nv, int nblk, double* out, cudaStream_t s);
 // x64 += scale * d (padded, FP32 d); scale read from device
 void launch_axpy_mixed(const GridDesc& g, double* x, const float* d, const double* scale,
                        cudaStream_t s);
 // b32 = r64 / ||r64|| from device norm-squared
-void launch_scale_to_f32(const GridDesc& g, const double* r, const double* nrm2, float* out,
+void launch_scale_to_f32(const GridDesc& g, const double* r, const double* nrm2, const int* active, float* out,
                          cudaStream_t s);
 
 // ---- learned.cu ----------------------------------------------------------

@@ -215,6 +215,7 @@ __device__ bool warp_chol_inverse(double* A, double* X, int na, double tau, doub
 }
 
 __global__ void k_set_params(DevState* st, double rtol, int maxit, int m, int C, double delta, double tau) {
+  st += blockIdx.x;
   st->rtol = rtol;
   st->maxit = maxit;
   st->m = m;
@@ -223,9 +224,13 @@ __global__ void k_set_params(DevState* st, double rtol, int maxit, int m, int C,
   st->tau = tau;
 }
 
-__global__ void k_init(DevState* st, const double* part_res, int nblk, double* res_hist,
+__global__ void k_init(DevState* st, const double* part_res, int nblk, double* res_hist, long long hist_stride,
                        cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ double v[2];
+  const int pb = blockIdx.x;
+  st += pb;
+  part_res += (long long)pb * 2 * nblk;
+  if (res_hist) res_hist += pb * hist_stride;
   reduce_values(part_res, 2, nblk, nblk, v);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -249,6 +254,11 @@ __global__ void k_init(DevState* st, const double* part_res, int nblk, double* r
 // all blocks of the grid, the last block forms beta.
 __global__ void k_small_beta(DevState* st, const double* part_W, int nchunks, int C, double* scratch,
                              unsigned* counter) {
+  const int pb = blockIdx.y;
+  st += pb;
+  scratch += (long long)pb * kSmallScratch;
+  counter += 2 * pb;
+  part_W += (long long)pb * st->m * C * C * nchunks;
   if (st->done) return;
   const int cnt = st->count;
   if (cnt == 0) return;
@@ -267,9 +277,17 @@ __global__ void k_small_beta(DevState* st, const double* part_W, int nchunks, in
 }
 
 __global__ void k_small_alpha(DevState* st, const double* part_G, int nblk_G, const double* part_zaz, int nblk_zaz,
-                              int zaz_stride, int C, double* alpha_hist, double* scratch, unsigned* counter) {
-  if (st->done) return;
+                              int zaz_stride, int C, double* alpha_hist, long long ahist_stride, double* scratch,
+                              unsigned* counter) {
   const int NG = C * (C + 1) / 2;
+  const int pb = blockIdx.y;
+  st += pb;
+  part_G += (long long)pb * (NG + C) * nblk_G;
+  part_zaz += (long long)pb * C * zaz_stride;
+  if (alpha_hist) alpha_hist += pb * ahist_stride;
+  scratch += (long long)pb * kSmallScratch + kSmallScratchAlpha;
+  counter += 2 * pb + 1;
+  if (st->done) return;
   __shared__ double red[kMaxCols * (kMaxCols + 1) / 2 + 2 * kMaxCols];
   __shared__ double G[kPad * kPad], Gp[kPad * kPad], A[kPad * kPad], X[kPad * kPad], Ah[kPad * kPad];
   __shared__ double dsc[kPad], rc[kPad], rs[kPad], lam[kPad];
@@ -341,10 +359,14 @@ __global__ void k_small_alpha(DevState* st, const double* part_G, int nblk_G, co
   }
 }
 
-__global__ void k_check(DevState* st, const double* part_r, int nblk, double* res_hist,
+__global__ void k_check(DevState* st, const double* part_r, int nblk, double* res_hist, long long hist_stride,
                         cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ double v[1];
   __shared__ double w[kBlock / 32];
+  const int pb = blockIdx.x;
+  st += pb;
+  part_r += (long long)pb * nblk;
+  if (res_hist) res_hist += pb * hist_stride;
   const int was_done = st->done;
   if (!was_done) {
     // one value: every thread takes a strided share, then a fixed tree
@@ -389,7 +411,7 @@ __global__ void k_dense_from_stencil(GridDesc g, const double* __restrict__ st, 
     const int nx = x + dx, ny = y + dy, nz = z + dz;
     if (nx < 0 || nx >= g.n1 || ny < 0 || ny >= g.n1 || nz < 0 || (g.dim == 3 ? nz >= g.n1 : nz != 0)) continue;
     const long long j = nx + (long long)g.n1 * ny + (long long)g.n1 * g.n1 * nz;
-    dense[i * n + j] = st[s * g.len + idx];
+    dense[i * n + j] = st[s * g.cp + idx];
   }
 }
 
@@ -452,9 +474,13 @@ __global__ void k_coarse_inverse(const double* __restrict__ L, const double* __r
 template <typename T>
 __global__ void k_coarse_solve(GridDesc g, const double* __restrict__ inv, const T* __restrict__ r,
                                T* __restrict__ out, const DevState* state) {
-  if (state && state->done) return;
+  const int pb = blockIdx.x;
+  if (state && state[pb].done) return;
   extern __shared__ double y[];
   const int n = (int)g.n;
+  inv += (long long)pb * n * n;
+  r += (long long)pb * g.len;
+  out += (long long)pb * g.len;
   auto padded = [&](int i) {
     const int x = i % g.n1, yy = (i / g.n1) % g.n1, z = i / (g.n1 * g.n1);
     return g.G + x + (long long)g.p * yy + (long long)g.p * g.p * z;
@@ -469,53 +495,79 @@ __global__ void k_coarse_solve(GridDesc g, const double* __restrict__ inv, const
   }
 }
 
+// out[b * nv + v] = sum of problem b's partials of value v.
 __global__ void k_sum_partials(const double* part, int nv, int nblk, double* out) {
-  reduce_values(part, nv, nblk, nblk, out);
+  const int pb = blockIdx.x;
+  reduce_values(part + (long long)pb * nv * nblk, nv, nblk, nblk, out + (long long)pb * nv);
 }
 
+// x64 += ||r64|| d per problem (nrm2 holds [||r||^2, ||b||^2] per problem).
 __global__ void k_axpy_mixed(GridDesc g, double* __restrict__ x, const float* __restrict__ d,
                              const double* __restrict__ nrm2) {
-  const double sc = sqrt(nrm2[0]);
+  const int pb = blockIdx.y;
+  const double sc = sqrt(nrm2[2 * pb]);
+  const long long o = (long long)pb * g.len + g.G;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.npts;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long idx = g.G + t;
-    x[idx] = fma(sc, (double)d[idx], x[idx]);
+       t += (long long)gridDim.x * blockDim.x)
+    x[o + t] = fma(sc, (double)d[o + t], x[o + t]);
+}
+
+// b32 = r64 / ||r64|| per problem; active[b] == 0 gives b32 = 0 (the inner
+// solve of a converged problem then stops at once).
+__global__ void k_scale_to_f32(GridDesc g, const double* __restrict__ r, const double* __restrict__ nrm2,
+                               const int* __restrict__ active, float* __restrict__ out) {
+  const int pb = blockIdx.y;
+  const bool on = !active || active[pb];
+  const double inv = on && nrm2[2 * pb] > 0.0 ? 1.0 / sqrt(nrm2[2 * pb]) : 0.0;
+  const long long o = (long long)pb * g.len + g.G;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.npts;
+       t += (long long)gridDim.x * blockDim.x)
+    out[o + t] = (float)(r[o + t] * inv);
+}
+
+// flag |= some problem of the batch is still running.
+__global__ void k_any_running(const DevState* st, int nb, int* flag) {
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+    if (st[b].done == 0) atomicOr(flag, 1);
+}
+
+// out[2b] = iterations, out[2b+1] = done of problem b.
+__global__ void k_gather_kd(const DevState* st, int nb, int* out) {
+  for (int b = threadIdx.x + blockIdx.x * blockDim.x; b < nb; b += blockDim.x * gridDim.x) {
+    out[2 * b] = st[b].k;
+    out[2 * b + 1] = st[b].done;
   }
 }
 
-__global__ void k_scale_to_f32(GridDesc g, const double* __restrict__ r, const double* __restrict__ nrm2,
-                               float* __restrict__ out) {
-  const double inv = nrm2[0] > 0.0 ? 1.0 / sqrt(nrm2[0]) : 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.npts;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long idx = g.G + t;
-    out[idx] = (float)(r[idx] * inv);
-  }
+// The loop condition of a batched graph: continue while any problem runs.
+__global__ void k_set_cond(int* flag, cudaGraphConditionalHandle cond) {
+  cudaGraphSetConditional(cond, *flag ? 1u : 0u);
+  *flag = 0;
 }
 
 }  // namespace
 
-void launch_set_params(DevState* st, double rtol, int maxit, int m, int C, double delta, double tau,
+void launch_set_params(DevState* st, int nb, double rtol, int maxit, int m, int C, double delta, double tau,
                        cudaStream_t s) {
-  k_set_params<<<1, 1, 0, s>>>(st, rtol, maxit, m, C, delta, tau);
+  k_set_params<<<nb, 1, 0, s>>>(st, rtol, maxit, m, C, delta, tau);
 }
-void launch_init(DevState* st, const double* part_res, int nblk, double* res_hist, cudaGraphConditionalHandle cond,
-                 int use_cond, cudaStream_t s) {
-  k_init<<<1, kBlock, 0, s>>>(st, part_res, nblk, res_hist, cond, use_cond);
+void launch_init(DevState* st, int nb, const double* part_res, int nblk, double* res_hist, long long hist_stride,
+                 cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
+  k_init<<<nb, kBlock, 0, s>>>(st, part_res, nblk, res_hist, hist_stride, cond, use_cond);
 }
-void launch_small_beta(DevState* st, const double* part_W, int nchunks, int C, double* scratch, unsigned* counter,
-                       cudaStream_t s) {
-  k_small_beta<<<kSmallGrid, kBlock, 0, s>>>(st, part_W, nchunks, C, scratch, counter);
+void launch_small_beta(DevState* st, int nb, const double* part_W, int nchunks, int C, double* scratch,
+                       unsigned* counter, cudaStream_t s) {
+  k_small_beta<<<dim3(kSmallGrid, nb), kBlock, 0, s>>>(st, part_W, nchunks, C, scratch, counter);
 }
-void launch_small_alpha(DevState* st, const double* part_G, int nblk_G, const double* part_zaz, int nblk_zaz,
-                        int zaz_stride, int C, double* alpha_hist, double* scratch, unsigned* counter,
-                        cudaStream_t s) {
-  k_small_alpha<<<kSmallGrid, kBlock, 0, s>>>(st, part_G, nblk_G, part_zaz, nblk_zaz, zaz_stride, C, alpha_hist,
-                                              scratch, counter);
+void launch_small_alpha(DevState* st, int nb, const double* part_G, int nblk_G, const double* part_zaz, int nblk_zaz,
+                        int zaz_stride, int C, double* alpha_hist, long long ahist_stride, double* scratch,
+                        unsigned* counter, cudaStream_t s) {
+  k_small_alpha<<<dim3(kSmallGrid, nb), kBlock, 0, s>>>(st, part_G, nblk_G, part_zaz, nblk_zaz, zaz_stride, C,
+                                                        alpha_hist, ahist_stride, scratch, counter);
 }
-void launch_check(DevState* st, const double* part_r, int nblk, double* res_hist, cudaGraphConditionalHandle cond,
-                  int use_cond, cudaStream_t s) {
-  k_check<<<1, kBlock, 0, s>>>(st, part_r, nblk, res_hist, cond, use_cond);
+void launch_check(DevState* st, int nb, const double* part_r, int nblk, double* res_hist, long long hist_stride,
+                  cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
+  k_check<<<nb, kBlock, 0, s>>>(st, part_r, nblk, res_hist, hist_stride, cond, use_cond);
 }
 void launch_dense_from_stencil(const GridDesc& g, const double* st, double* dense, cudaStream_t s) {
   k_dense_from_stencil<<<(int)((g.n + 127) / 128), 128, 0, s>>>(g, st, dense);
@@ -529,20 +581,30 @@ void launch_coarse_inverse(const double* L, const double* rdiag, double* X, doub
 template <typename T>
 void launch_coarse_solve(const GridDesc& g, const double* inv, const T* r, T* out, const DevState* state,
                          cudaStream_t s) {
-  k_coarse_solve<T><<<1, 128, (size_t)g.n * sizeof(double), s>>>(g, inv, r, out, state);
+  k_coarse_solve<T><<<g.nb, 128, (size_t)g.n * sizeof(double), s>>>(g, inv, r, out, state);
 }
 template void launch_coarse_solve<double>(const GridDesc&, const double*, const double*, double*, const DevState*,
                                           cudaStream_t);
 template void launch_coarse_solve<float>(const GridDesc&, const double*, const float*, float*, const DevState*,
                                          cudaStream_t);
-void launch_sum_partials(const double* part, int nv, int nblk, double* out, cudaStream_t s) {
-  k_sum_partials<<<1, kBlock, 0, s>>>(part, nv, nblk, out);
+void launch_sum_partials(const double* part, int nb, int nv, int nblk, double* out, cudaStream_t s) {
+  k_sum_partials<<<nb, kBlock, 0, s>>>(part, nv, nblk, out);
 }
 void launch_axpy_mixed(const GridDesc& g, double* x, const float* d, const double* scale, cudaStream_t s) {
-  k_axpy_mixed<<<grid_for(g.npts, 4096), kBlock, 0, s>>>(g, x, d, scale);
+  k_axpy_mixed<<<dim3(grid_for(g.npts, 1024), g.nb), kBlock, 0, s>>>(g, x, d, scale);
 }
-void launch_scale_to_f32(const GridDesc& g, const double* r, const double* nrm2, float* out, cudaStream_t s) {
-  k_scale_to_f32<<<grid_for(g.npts, 4096), kBlock, 0, s>>>(g, r, nrm2, out);
+void launch_scale_to_f32(const GridDesc& g, const double* r, const double* nrm2, const int* active, float* out,
+                         cudaStream_t s) {
+  k_scale_to_f32<<<dim3(grid_for(g.npts, 1024), g.nb), kBlock, 0, s>>>(g, r, nrm2, active, out);
+}
+void launch_any_running(const DevState* st, int nb, int* flag, cudaStream_t s) {
+  k_any_running<<<1, kBlock, 0, s>>>(st, nb, flag);
+}
+void launch_set_cond(int* flag, cudaGraphConditionalHandle cond, cudaStream_t s) {
+  k_set_cond<<<1, 1, 0, s>>>(flag, cond);
+}
+void launch_gather_kd(const DevState* st, int nb, int* out, cudaStream_t s) {
+  k_gather_kd<<<(nb + kBlock - 1) / kBlock, kBlock, 0, s>>>(st, nb, out);
 }
 
 }  // namespace mpcg

@@ -8,7 +8,8 @@
 // 2 doubles: one 16-byte load per stencil plane and per grid row, plus one
 // scalar on each side for the x-neighbours).  Stencil coefficients are zero
 // at pad entries, so every output at a pad entry is exactly zero without a
-// test.
+// test.  blockIdx.y selects the problem of a batch (offset b * len; columns
+// and stencil planes are cp = nb * len apart).
 #include "kernels.cuh"
 #include "vec.cuh"
 
@@ -28,7 +29,7 @@ __global__ void k_pack(GridDesc g, const TI* __restrict__ src, long long ld, TO*
     const long long q = i / g.n1;
     const int y = (int)(q % g.n1);
     const int z = (int)(q / g.n1);
-    dst[(long long)c * g.len + g.G + x + (long long)g.p * y + (long long)g.p * g.p * z] = (TO)src[(long long)c * ld + i];
+    dst[(long long)c * g.cp + g.G + x + (long long)g.p * y + (long long)g.p * g.p * z] = (TO)src[(long long)c * ld + i];
   }
 }
 
@@ -43,7 +44,7 @@ __global__ void k_unpack(GridDesc g, const TI* __restrict__ src, TO* __restrict_
     const long long q = i / g.n1;
     const int y = (int)(q % g.n1);
     const int z = (int)(q / g.n1);
-    dst[(long long)c * ld + i] = (TO)src[(long long)c * g.len + g.G + x + (long long)g.p * y + (long long)g.p * g.p * z];
+    dst[(long long)c * ld + i] = (TO)src[(long long)c * g.cp + g.G + x + (long long)g.p * y + (long long)g.p * g.p * z];
   }
 }
 
@@ -67,9 +68,10 @@ __device__ __forceinline__ long long row_offset(int k, long long p) {
   return dy * p + dz * p * p;
 }
 
-// acc[c][w] += sum over the stencil of A(point w) * X_c(neighbour), C columns.
+// acc[c][w] += sum over the stencil of A(point w) * X_c(neighbour), C columns;
+// pitch = distance between stencil planes and between columns.
 template <typename T, int DIM, int C>
-__device__ __forceinline__ void stencil_group(const T* __restrict__ st, long long len, const T* __restrict__ X,
+__device__ __forceinline__ void stencil_group(const T* __restrict__ st, long long pitch, const T* __restrict__ X,
                                               long long idx, long long p, T (&acc)[C][Vec<T>::W]) {
   constexpr int W = Vec<T>::W;
   constexpr int R = DIM == 3 ? 9 : 3;
@@ -77,13 +79,13 @@ __device__ __forceinline__ void stencil_group(const T* __restrict__ st, long lon
   for (int k = 0; k < R; ++k) {
     const long long ro = row_offset<DIM>(k, p);
     T a0[W], a1[W], a2[W];
-    Vec<T>::load(st + (long long)(3 * k + 0) * len + idx, a0);
-    Vec<T>::load(st + (long long)(3 * k + 1) * len + idx, a1);
-    Vec<T>::load(st + (long long)(3 * k + 2) * len + idx, a2);
+    Vec<T>::load(st + (long long)(3 * k + 0) * pitch + idx, a0);
+    Vec<T>::load(st + (long long)(3 * k + 1) * pitch + idx, a1);
+    Vec<T>::load(st + (long long)(3 * k + 2) * pitch + idx, a2);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       T e[W + 2];
-      load_row<T>(X + (long long)c * len + idx + ro, e);
+      load_row<T>(X + (long long)c * pitch + idx + ro, e);
 #pragma unroll
       for (int w = 0; w < W; ++w) {
         acc[c][w] = fma(a0[w], e[w], acc[c][w]);
@@ -97,48 +99,52 @@ __device__ __forceinline__ void stencil_group(const T* __restrict__ st, long lon
 template <typename T, int DIM, int C, bool ZAZ>
 __global__ void __launch_bounds__(kBlock) k_spmm(GridDesc g, const T* __restrict__ st, const T* __restrict__ X,
                                                  T* __restrict__ Y, double* zaz, const DevState* state) {
-  if (state && state->done) return;
+  const int pb = blockIdx.y;
+  if (state && state[pb].done) return;
   constexpr int W = Vec<T>::W;
+  const long long bo = (long long)pb * g.len;
   T zacc[ZAZ ? C : 1];
 #pragma unroll
   for (int c = 0; c < (ZAZ ? C : 1); ++c) zacc[c] = 0;
   const long long ngroups = g.npts / W;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
        q += (long long)gridDim.x * blockDim.x) {
-    const long long idx = g.G + q * W;
+    const long long idx = bo + g.G + q * W;
     T acc[C][W];
 #pragma unroll
     for (int c = 0; c < C; ++c)
 #pragma unroll
       for (int w = 0; w < W; ++w) acc[c][w] = 0;
-    stencil_group<T, DIM, C>(st, g.len, X, idx, g.p, acc);
+    stencil_group<T, DIM, C>(st, g.cp, X, idx, g.p, acc);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      Vec<T>::store(Y + (long long)c * g.len + idx, acc[c]);
+      Vec<T>::store(Y + (long long)c * g.cp + idx, acc[c]);
       if (ZAZ) {
         T xc[W];
-        Vec<T>::load_keep(X + (long long)c * g.len + idx, xc);
+        Vec<T>::load_keep(X + (long long)c * g.cp + idx, xc);
 #pragma unroll
         for (int w = 0; w < W; ++w) zacc[c] = fma(xc[w], acc[c][w], zacc[c]);
       }
     }
   }
-  if (ZAZ) block_sum_store<T, ZAZ ? C : 1>(zacc, zaz, gridDim.x, blockIdx.x);
+  if (ZAZ) block_sum_store<T, ZAZ ? C : 1>(zacc, zaz + (long long)pb * C * gridDim.x, gridDim.x, blockIdx.x);
 }
 
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBlock) k_residual(GridDesc g, const T* __restrict__ st, const T* __restrict__ b,
                                                      const T* __restrict__ xv, T* __restrict__ r, double* part) {
   constexpr int W = Vec<T>::W;
+  const int pb = blockIdx.y;
+  const long long bo = (long long)pb * g.len;
   T sums[2] = {0, 0};
   const long long ngroups = g.npts / W;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
        q += (long long)gridDim.x * blockDim.x) {
-    const long long idx = g.G + q * W;
+    const long long idx = bo + g.G + q * W;
     T acc[1][W];
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[0][w] = 0;
-    stencil_group<T, DIM, 1>(st, g.len, xv, idx, g.p, acc);
+    stencil_group<T, DIM, 1>(st, g.cp, xv, idx, g.p, acc);
     T bv[W], rv[W];
     Vec<T>::load(b + idx, bv);
 #pragma unroll
@@ -149,7 +155,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(GridDesc g, const T* __rest
     }
     Vec<T>::store(r + idx, rv);
   }
-  block_sum_store<T, 2>(sums, part, gridDim.x, blockIdx.x);
+  block_sum_store<T, 2>(sums, part + (long long)pb * 2 * gridDim.x, gridDim.x, blockIdx.x);
 }
 
 // Restriction R = P^T: coarse node I sits on fine node 2I+1 (per axis); the
@@ -157,9 +163,12 @@ __global__ void __launch_bounds__(kBlock) k_residual(GridDesc g, const T* __rest
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBlock) k_restrict(GridDesc gf, GridDesc gc, const T* __restrict__ rf,
                                                      T* __restrict__ rc, const DevState* state) {
-  if (state && state->done) return;
+  const int pb = blockIdx.y;
+  if (state && state[pb].done) return;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= gc.npts) return;
+  rf += (long long)pb * gf.len;
+  rc += (long long)pb * gc.len;
   int X, Y, Z;
   decode(gc, t, X, Y, Z);
   const long long idc = gc.G + t;
@@ -193,11 +202,12 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kBlock) k_jacobi(GridDesc g, const T* __restrict__ st, const T* __restrict__ dinv,
                                                    const T* __restrict__ r, const T* __restrict__ sin,
                                                    T* __restrict__ out, int mode, const DevState* state) {
-  if (state && state->done) return;
+  const int pb = blockIdx.y;
+  if (state && state[pb].done) return;
   constexpr int W = Vec<T>::W;
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= g.npts / W) return;
-  const long long idx = g.G + q * W;
+  const long long idx = (long long)pb * g.len + g.G + q * W;
   T di[W], ri[W], o[W];
   Vec<T>::load_keep(dinv + idx, di);
   Vec<T>::load_keep(r + idx, ri);
@@ -216,9 +226,9 @@ __global__ void __launch_bounds__(kBlock) k_jacobi(GridDesc g, const T* __restri
     for (int k = 0; k < R; ++k) {
       const long long ro = row_offset<DIM>(k, g.p);
       T a0[W], a1[W], a2[W], ed[W + 2], er[W + 2];
-      Vec<T>::load(st + (long long)(3 * k + 0) * g.len + idx, a0);
-      Vec<T>::load(st + (long long)(3 * k + 1) * g.len + idx, a1);
-      Vec<T>::load(st + (long long)(3 * k + 2) * g.len + idx, a2);
+      Vec<T>::load(st + (long long)(3 * k + 0) * g.cp + idx, a0);
+      Vec<T>::load(st + (long long)(3 * k + 1) * g.cp + idx, a1);
+      Vec<T>::load(st + (long long)(3 * k + 2) * g.cp + idx, a2);
       load_row<T>(dinv + idx + ro, ed);
       load_row<T>(r + idx + ro, er);
 #pragma unroll
@@ -234,7 +244,7 @@ __global__ void __launch_bounds__(kBlock) k_jacobi(GridDesc g, const T* __restri
       o[w] = s1 + di[w] * (ri[w] - acc[0][w]);
     }
   } else {
-    stencil_group<T, DIM, 1>(st, g.len, sin, idx, g.p, acc);
+    stencil_group<T, DIM, 1>(st, g.cp, sin, idx, g.p, acc);
     T sv[W];
     Vec<T>::load_keep(sin + idx, sv);
 #pragma unroll
@@ -252,14 +262,15 @@ __global__ void __launch_bounds__(kBlock) k_jacobi(GridDesc g, const T* __restri
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBlock) k_prolong(GridDesc gc, GridDesc gf, const T* __restrict__ coarse,
                                                     T* __restrict__ fine, int ncols, const DevState* state) {
-  if (state && state->done) return;
+  const int pb = blockIdx.y;
+  if (state && state[pb].done) return;
   constexpr int W = Vec<T>::W;
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= gf.npts / W) return;
   const long long t0 = q * W;
   int x0, y, z;
   decode(gf, t0, x0, y, z);
-  const long long idf = gf.G + t0;
+  const long long idf = (long long)pb * gf.len + gf.G + t0;
   // per axis: parents (c0, c1) with weights (w0, w1)
   auto par = [](int i, int& c0, int& c1, T& w0, T& w1) {
     if (i & 1) { c0 = c1 = i >> 1; w0 = (T)1; w1 = (T)0; }
@@ -272,7 +283,7 @@ __global__ void __launch_bounds__(kBlock) k_prolong(GridDesc gc, GridDesc gf, co
   const long long pc = gc.p, ppc = pc * pc;
   const int cx = x0 >> 1;
   for (int c = 0; c < ncols; ++c) {
-    const T* C0 = coarse + (long long)c * gc.len + gc.G;
+    const T* C0 = coarse + (long long)c * gc.cp + (long long)pb * gc.len + gc.G;
     T row[W / 2 + 1];
 #pragma unroll
     for (int k = 0; k <= W / 2; ++k) row[k] = 0;
@@ -295,7 +306,7 @@ __global__ void __launch_bounds__(kBlock) k_prolong(GridDesc gc, GridDesc gf, co
       o[2 * k] = (T)0.5 * (row[k] + row[k + 1]);
       o[2 * k + 1] = row[k + 1];
     }
-    Vec<T>::store(fine + (long long)c * gf.len + idf, o);
+    Vec<T>::store(fine + (long long)c * gf.cp + idf, o);
   }
 }
 
@@ -304,13 +315,16 @@ template <int DIM>
 __global__ void __launch_bounds__(kBlock) k_galerkin(GridDesc gf, GridDesc gc, const double* __restrict__ stf,
                                                      double* __restrict__ stc) {
   constexpr int S = DIM == 3 ? 27 : 9;
+  const int pb = blockIdx.y;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= gc.npts) return;
+  stf += (long long)pb * gf.len;
+  stc += (long long)pb * gc.len;
   int X, Y, Z;
   decode(gc, t, X, Y, Z);
   const long long idc = gc.G + t;
   if (!interior(gc, X, Y, Z)) {
-    for (int s = 0; s < S; ++s) stc[s * gc.len + idc] = 0.0;
+    for (int s = 0; s < S; ++s) stc[s * gc.cp + idc] = 0.0;
     return;
   }
   double acc[S];
@@ -324,7 +338,7 @@ __global__ void __launch_bounds__(kBlock) k_galerkin(GridDesc gf, GridDesc gc, c
         const double we = (ex ? 0.5 : 1.0) * (ey ? 0.5 : 1.0) * (ez ? 0.5 : 1.0);
         const long long idf = gf.G + (2 * X + 1 + ex) + pf * (2 * Y + 1 + ey) + (DIM == 3 ? ppf * (2 * Z + 1 + ez) : 0);
         for (int s = 0; s < S; ++s) {
-          const double a = stf[s * gf.len + idf];
+          const double a = stf[s * gf.cp + idf];
           if (a == 0.0) continue;
           const int f[3] = {ex + (s % 3 - 1), ey + ((s / 3) % 3 - 1), DIM == 3 ? ez + (s / 9 - 1) : 0};
           // coarse parents of the fine column node, relative to (X, Y, Z)
@@ -348,18 +362,19 @@ __global__ void __launch_bounds__(kBlock) k_galerkin(GridDesc gf, GridDesc gc, c
               }
         }
       }
-  for (int s = 0; s < S; ++s) stc[s * gc.len + idc] = acc[s];
+  for (int s = 0; s < S; ++s) stc[s * gc.cp + idc] = acc[s];
 }
 
 template <typename T>
 __global__ void k_dinv(GridDesc g, const double* __restrict__ st, T* __restrict__ dinv, double omega) {
+  const int pb = blockIdx.y;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= g.npts) return;
   int x, y, z;
   decode(g, t, x, y, z);
-  const long long idx = g.G + t;
+  const long long idx = (long long)pb * g.len + g.G + t;
   const int centre = g.dim == 3 ? 13 : 4;
-  dinv[idx] = interior(g, x, y, z) ? (T)(omega / st[centre * g.len + idx]) : (T)0;
+  dinv[idx] = interior(g, x, y, z) ? (T)(omega / st[centre * g.cp + idx]) : (T)0;
 }
 
 __global__ void k_convert_f32(const double* __restrict__ src, float* __restrict__ dst, long long count) {
@@ -393,11 +408,11 @@ template void launch_unpack<float, float>(const GridDesc&, const float*, float*,
 template <typename T, int DIM>
 static void spmm_dim(const GridDesc& g, const T* st, const T* X, T* Y, int C, double* zaz, const DevState* state,
                      cudaStream_t s) {
-  const int nb = stream_blocks(g);
+  const dim3 grid(stream_blocks(g), g.nb);
 #define MPCG_SPMM_CASE(CC)                                                                      \
   case CC:                                                                                      \
-    if (zaz) k_spmm<T, DIM, CC, true><<<nb, kBlock, 0, s>>>(g, st, X, Y, zaz, state);           \
-    else k_spmm<T, DIM, CC, false><<<nb, kBlock, 0, s>>>(g, st, X, Y, zaz, state);             \
+    if (zaz) k_spmm<T, DIM, CC, true><<<grid, kBlock, 0, s>>>(g, st, X, Y, zaz, state);         \
+    else k_spmm<T, DIM, CC, false><<<grid, kBlock, 0, s>>>(g, st, X, Y, zaz, state);           \
     break;
   switch (C) {
     MPCG_SPMM_CASE(1) MPCG_SPMM_CASE(2) MPCG_SPMM_CASE(3) MPCG_SPMM_CASE(4) MPCG_SPMM_CASE(5)
@@ -421,9 +436,9 @@ template void launch_spmm<float>(const GridDesc&, const float*, const float*, fl
 
 template <typename T>
 void launch_residual(const GridDesc& g, const T* st, const T* b, const T* x, T* r, double* part, cudaStream_t s) {
-  const int nb = stream_blocks(g);
-  if (g.dim == 3) k_residual<T, 3><<<nb, kBlock, 0, s>>>(g, st, b, x, r, part);
-  else k_residual<T, 2><<<nb, kBlock, 0, s>>>(g, st, b, x, r, part);
+  const dim3 grid(stream_blocks(g), g.nb);
+  if (g.dim == 3) k_residual<T, 3><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part);
+  else k_residual<T, 2><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part);
 }
 template void launch_residual<double>(const GridDesc&, const double*, const double*, const double*, double*,
                                       double*, cudaStream_t);
@@ -433,8 +448,9 @@ template void launch_residual<float>(const GridDesc&, const float*, const float*
 template <typename T>
 void launch_restrict(const GridDesc& gf, const GridDesc& gc, const T* rf, T* rc, const DevState* state,
                      cudaStream_t s) {
-  if (gc.dim == 3) k_restrict<T, 3><<<blocks_for(gc.npts), kBlock, 0, s>>>(gf, gc, rf, rc, state);
-  else k_restrict<T, 2><<<blocks_for(gc.npts), kBlock, 0, s>>>(gf, gc, rf, rc, state);
+  const dim3 grid(blocks_for(gc.npts), gc.nb);
+  if (gc.dim == 3) k_restrict<T, 3><<<grid, kBlock, 0, s>>>(gf, gc, rf, rc, state);
+  else k_restrict<T, 2><<<grid, kBlock, 0, s>>>(gf, gc, rf, rc, state);
 }
 template void launch_restrict<double>(const GridDesc&, const GridDesc&, const double*, double*, const DevState*,
                                       cudaStream_t);
@@ -444,9 +460,9 @@ template void launch_restrict<float>(const GridDesc&, const GridDesc&, const flo
 template <typename T>
 void launch_jacobi(const GridDesc& g, const T* st, const T* dinv, const T* r, const T* sin, T* out, int mode,
                    const DevState* state, cudaStream_t s) {
-  const int nb = blocks_for(g.npts / vw<T>());
-  if (g.dim == 3) k_jacobi<T, 3><<<nb, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
-  else k_jacobi<T, 2><<<nb, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
+  const dim3 grid(blocks_for(g.npts / vw<T>()), g.nb);
+  if (g.dim == 3) k_jacobi<T, 3><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
+  else k_jacobi<T, 2><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
 }
 template void launch_jacobi<double>(const GridDesc&, const double*, const double*, const double*, const double*,
                                     double*, int, const DevState*, cudaStream_t);
@@ -456,9 +472,9 @@ template void launch_jacobi<float>(const GridDesc&, const float*, const float*, 
 template <typename T>
 void launch_prolong(const GridDesc& gc, const GridDesc& gf, const T* coarse, T* fine, int ncols,
                     const DevState* state, cudaStream_t s) {
-  const int nb = blocks_for(gf.npts / vw<T>());
-  if (gf.dim == 3) k_prolong<T, 3><<<nb, kBlock, 0, s>>>(gc, gf, coarse, fine, ncols, state);
-  else k_prolong<T, 2><<<nb, kBlock, 0, s>>>(gc, gf, coarse, fine, ncols, state);
+  const dim3 grid(blocks_for(gf.npts / vw<T>()), gf.nb);
+  if (gf.dim == 3) k_prolong<T, 3><<<grid, kBlock, 0, s>>>(gc, gf, coarse, fine, ncols, state);
+  else k_prolong<T, 2><<<grid, kBlock, 0, s>>>(gc, gf, coarse, fine, ncols, state);
 }
 template void launch_prolong<double>(const GridDesc&, const GridDesc&, const double*, double*, int,
                                      const DevState*, cudaStream_t);
@@ -466,13 +482,14 @@ template void launch_prolong<float>(const GridDesc&, const GridDesc&, const floa
                                     cudaStream_t);
 
 void launch_galerkin(const GridDesc& gf, const GridDesc& gc, const double* stf, double* stc, cudaStream_t s) {
-  if (gc.dim == 3) k_galerkin<3><<<blocks_for(gc.npts), kBlock, 0, s>>>(gf, gc, stf, stc);
-  else k_galerkin<2><<<blocks_for(gc.npts), kBlock, 0, s>>>(gf, gc, stf, stc);
+  const dim3 grid(blocks_for(gc.npts), gc.nb);
+  if (gc.dim == 3) k_galerkin<3><<<grid, kBlock, 0, s>>>(gf, gc, stf, stc);
+  else k_galerkin<2><<<grid, kBlock, 0, s>>>(gf, gc, stf, stc);
 }
 
 template <typename T>
 void launch_dinv(const GridDesc& g, const double* st, T* dinv, double omega, cudaStream_t s) {
-  k_dinv<T><<<blocks_for(g.npts), kBlock, 0, s>>>(g, st, dinv, omega);
+  k_dinv<T><<<dim3(blocks_for(g.npts), g.nb), kBlock, 0, s>>>(g, st, dinv, omega);
 }
 template void launch_dinv<double>(const GridDesc&, const double*, double*, double, cudaStream_t);
 template void launch_dinv<float>(const GridDesc&, const double*, float*, double, cudaStream_t);

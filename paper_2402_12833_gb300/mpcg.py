@@ -75,6 +75,11 @@ _SIGS = {
     "mg_last_launches": (C.c_longlong, [C.c_void_p]),
     "mg_stencil_apply_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                            C.c_void_p]),
+    "mg_hierarchy_setup_batched": (C.c_int, [C.POINTER(mg_operator), C.c_int, C.c_int, C.POINTER(mpcg_options),
+                                             C.POINTER(C.c_void_p)]),
+    "mg_num_problems": (C.c_int, [C.c_void_p]),
+    "mpcg_solve_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p),
+                                     C.POINTER(C.c_void_p), C.c_double, C.c_int, C.POINTER(C.c_void_p)]),
     "mg_learned_num_params": (C.c_int, []),
     "mg_learned_attach": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "mg_learned_detach": (C.c_int, [C.c_void_p]),
@@ -250,6 +255,58 @@ def mg_learned_train(handles, pair_prob, rhat_dev, e_dev, params: np.ndarray, ep
 def mg_hierarchy_destroy(h: int) -> None:
     if h:
         load().mg_hierarchy_destroy(h)
+
+
+def mg_num_problems(h: int) -> int:
+    return load().mg_num_problems(h)
+
+
+class BatchedHierarchy:
+    """Owning wrapper of a batched hierarchy: nprob problems on one grid."""
+
+    def __init__(self, stencils, dim: int, nodes: int, levels: int, **options):
+        self.options = mpcg_default_options(**options)
+        self._keep = list(stencils)
+        ops = (mg_operator * len(self._keep))(*[mg_operator(dim, nodes, MPCG_FORMAT_STENCIL, _ptr(s))
+                                                for s in self._keep])
+        h = C.c_void_p()
+        _check(load().mg_hierarchy_setup_batched(ops, len(self._keep), levels, C.byref(self.options), C.byref(h)))
+        self.h = h.value
+        self.nprob = len(self._keep)
+        self.n = (nodes - 2) ** dim
+
+    def solve(self, b, x, rtol=1e-8, maxit=500):
+        """b, x: nprob x n (device tensors or host arrays); returns (status, iterations[nprob])."""
+        it = np.zeros(self.nprob, dtype=np.int32)
+        st = load().mpcg_solve(self.h, _ptr(b), _ptr(x), rtol, maxit, it.ctypes.data_as(C.POINTER(C.c_int)),
+                               None, None)
+        _check(st, allow=(MPCG_OK, MPCG_NOT_CONVERGED))
+        return st, it
+
+    def close(self):
+        if self.h:
+            mg_hierarchy_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mpcg_solve_batched(classes, bs, xs, rtol=1e-8, maxit=500):
+    """Solve every BatchedHierarchy in ``classes`` concurrently; returns
+    (status, [iterations per class])."""
+    n = len(classes)
+    hs = (C.c_void_p * n)(*[c.h for c in classes])
+    bp = (C.c_void_p * n)(*[_ptr(b) for b in bs])
+    xp = (C.c_void_p * n)(*[_ptr(x) for x in xs])
+    its = [np.zeros(c.nprob, dtype=np.int32) for c in classes]
+    ip = (C.c_void_p * n)(*[i.ctypes.data for i in its])
+    st = load().mpcg_solve_batched(hs, n, bp, xp, rtol, maxit, ip)
+    _check(st, allow=(MPCG_OK, MPCG_NOT_CONVERGED))
+    return st, its
 
 
 class Hierarchy:

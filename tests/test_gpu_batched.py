@@ -1,0 +1,100 @@
+"""Batched solves: many independent problems per launch, uneven sizes across
+concurrent size classes.  A problem solved inside a batch must give the
+result of its own single solve (same kernels, same reduction layout: the
+comparison is bitwise), and every problem must reach its tolerance."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import mg as omg
+from paper_2402_12833_gb300 import problems as pb
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_12833_gb300 import build, mpcg
+    build.build()
+    mpcg.load()
+    return mpcg
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _single(M, prob, **opts):
+    H = M.Hierarchy(_dev(prob.stencil), prob.dim, prob.nodes, prob.levels, **opts)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    st, k, _, _ = H.solve(_dev(prob.b), x, rtol=1e-8, maxit=2000, histories=False)
+    return k, x.cpu().numpy()
+
+
+def _true_res(prob, x):
+    O = omg.Hierarchy(prob.dim, prob.n1, prob.stencil, prob.levels)
+    return np.linalg.norm(prob.b - O.A[-1] @ x) / np.linalg.norm(prob.b)
+
+
+@pytest.mark.parametrize("nodes,dim", [(33, 2), (9, 3)])
+def test_batch_equals_single_solves_bitwise(M, nodes, dim):
+    probs = [pb.diffusion_macro(dim, nodes, 300 + i, rhs="normal", rhs_seed=400 + i) for i in range(4)]
+    B = M.BatchedHierarchy([_dev(p.stencil) for p in probs], dim, nodes, probs[0].levels)
+    b = _dev(np.stack([p.b for p in probs]))
+    x = torch.zeros_like(b)
+    st, its = B.solve(b, x, rtol=1e-8, maxit=2000)
+    assert st == M.MPCG_OK
+    X = x.cpu().numpy()
+    for i, p in enumerate(probs):
+        k, xs = _single(M, p)
+        assert its[i] == k
+        assert np.array_equal(X[i], xs)
+
+
+def test_batch_mixed_precision_reaches_tolerance(M):
+    probs = [pb.diffusion_macro(2, 65, 500 + i, rhs="normal", rhs_seed=600 + i) for i in range(5)]
+    B = M.BatchedHierarchy([_dev(p.stencil) for p in probs], 2, 65, probs[0].levels, precision=M.MPCG_MIXED)
+    b = _dev(np.stack([p.b for p in probs]))
+    x = torch.zeros_like(b)
+    st, its = B.solve(b, x, rtol=1e-8, maxit=3000)
+    assert st == M.MPCG_OK
+    X = x.cpu().numpy()
+    for i, p in enumerate(probs):
+        assert _true_res(p, X[i]) <= 1e-8
+        k, xs = _single(M, p, precision=M.MPCG_MIXED)
+        assert np.linalg.norm(X[i] - xs) <= 1e-6 * np.linalg.norm(xs)
+
+
+def test_zero_rhs_problem_in_a_batch(M):
+    probs = [pb.poisson_random(2, 33, 1), pb.poisson_random(2, 33, 2)]
+    probs[1].b = np.zeros_like(probs[1].b)
+    B = M.BatchedHierarchy([_dev(p.stencil) for p in probs], 2, 33, probs[0].levels)
+    b = _dev(np.stack([p.b for p in probs]))
+    x = torch.zeros_like(b)
+    st, its = B.solve(b, x)
+    assert st == M.MPCG_OK and its[1] == 0 and its[0] > 0
+    assert torch.count_nonzero(x[1]) == 0
+
+
+def test_uneven_batch_in_concurrent_classes(M):
+    sizes = {33: 3, 65: 2, 129: 1}
+    classes, bs, xs, probs = [], [], [], []
+    streams = [torch.cuda.Stream() for _ in sizes]
+    for (nodes, cnt), strm in zip(sizes.items(), streams):
+        ps = [pb.batch_problem(len(probs) + i, nodes) for i in range(cnt)]
+        probs.append(ps)
+        classes.append(M.BatchedHierarchy([_dev(p.stencil) for p in ps], 2, nodes, ps[0].levels,
+                                          precision=M.MPCG_MIXED, stream=strm.cuda_stream))
+        bs.append(_dev(np.stack([p.b for p in ps])))
+        xs.append(torch.zeros_like(bs[-1]))
+    torch.cuda.synchronize()
+    st, its = M.mpcg_solve_batched(classes, bs, xs, rtol=1e-8, maxit=4000)
+    assert st == M.MPCG_OK
+    for ps, x, it in zip(probs, xs, its):
+        X = x.cpu().numpy()
+        for i, p in enumerate(ps):
+            assert it[i] > 0
+            assert _true_res(p, X[i]) <= 1e-8
