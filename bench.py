@@ -406,8 +406,144 @@ def bench_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------- extra workloads
+def _timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3) / steps
+
+
+def bench_batched(args):
+    """256 independent 2D high-contrast problems (sides drawn from 33..513, own
+    kappa and N(0,1) RHS), mixed precision, rtol 1e-8 each: one batched
+    hierarchy per side length, the classes solved concurrently."""
+    import numpy as np
+    import torch
+    from paper_2402_12833_gb300 import build as _build
+    from paper_2402_12833_gb300 import mpcg as M
+    from paper_2402_12833_gb300 import problems as pb
+    _build.build()
+    M.load()
+    sizes = pb.batch_sizes(256, seed=4)
+    by = {}
+    for i, s in enumerate(sizes):
+        by.setdefault(s, []).append(i)
+    classes, bs, xs, ns = [], [], [], 0
+    streams = []
+    for nodes in sorted(by):
+        ps = [pb.batch_problem(i, nodes) for i in by[nodes]]
+        strm = torch.cuda.Stream()
+        streams.append(strm)
+        classes.append(M.BatchedHierarchy([torch.from_numpy(p.stencil).cuda() for p in ps], 2, nodes, ps[0].levels,
+                                          m=M_WINDOW, precision=M.MPCG_MIXED, stream=strm.cuda_stream))
+        bs.append(torch.from_numpy(np.stack([p.b for p in ps])).cuda())
+        xs.append(torch.zeros_like(bs[-1]))
+        ns += len(ps) * ps[0].n
+    torch.cuda.synchronize()
+    its = None
+
+    def step():
+        nonlocal its
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        _, its = M.mpcg_solve_batched(classes, bs, xs, rtol=RTOL, maxit=20000)
+
+    ms = _timed(step, args.steps, max(1, args.warmup // 3), torch.cuda.current_stream())
+    launches = sum(M.mg_last_launches(c.h) for c in classes)
+    print(json.dumps({
+        "metric": METRIC, "workload": "batched", "value": ns / (ms * 1e-3), "unit": "DOFs/s", "n_gpus": 1,
+        "steps": args.steps, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "256 x 2D diffusion, sides U{33,65,129,257,513}, log10 kappa U[-2,4] on 16x16 macro "
+                               "cells, N(0,1) RHS, levels to 5x5, MPCG m=5, mixed precision, rtol 1e-8 each",
+                   "problems_per_side": {str(k): len(v) for k, v in sorted(by.items())}, "total_dofs": ns},
+        "max_iterations_per_side": {str(k): int(i.max()) for k, i in zip(sorted(by), its)},
+        "gpu_launches_per_step": launches}))
+    return 0
+
+
+def bench_learned(args):
+    """2D high-contrast diffusion, 1025^2 nodes, 9 grids, f = 1, kappa seed 3:
+    the mixed-precision solver without and with the learned column; the
+    network is trained on the GPU on 4096 (residual, error) pairs of 129^2
+    problems with kappa seeds 1000..1015 made by the solver itself."""
+    import numpy as np
+    import torch
+    from paper_2402_12833_gb300 import build as _build
+    from paper_2402_12833_gb300 import mpcg as M
+    from paper_2402_12833_gb300 import problems as pb
+    _build.build()
+    M.load()
+    t0 = time.perf_counter()
+    hs, R, E, owner = [], [], [], []
+    for i, sd in enumerate(range(1000, 1016)):
+        prob = pb.diffusion_macro(2, 129, sd)
+        H = M.Hierarchy(torch.from_numpy(prob.stencil).cuda(), 2, 129, prob.levels, m=M_WINDOW)
+        b = torch.from_numpy(prob.b).cuda()
+        xs = torch.zeros_like(b)
+        H.solve(b, xs, rtol=1e-12, maxit=20000, histories=False)
+        Ax = torch.empty_like(b)
+        for k in range(1, 257):
+            x = torch.zeros_like(b)
+            H.solve(b, x, rtol=1e-30, maxit=k, histories=False)
+            M.mg_apply_operator(H.h, prob.levels - 1, x, Ax, 1)
+            r = b - Ax
+            nr = torch.linalg.norm(r)
+            R.append((r / nr).float())
+            E.append(((xs - x) / nr).float())
+            owner.append(i)
+        hs.append(H)
+    gen_s = time.perf_counter() - t0
+    params = pb.net_init_params(7)
+    t0 = time.perf_counter()
+    loss = M.mg_learned_train([h.h for h in hs], owner, torch.stack(R).contiguous(), torch.stack(E).contiguous(),
+                              params, epochs=args.epochs, batch=8, lr=1e-3)
+    train_s = time.perf_counter() - t0
+    prob = pb.diffusion_macro(2, 1025, 3)
+    st = torch.from_numpy(prob.stencil).cuda()
+    b = torch.from_numpy(prob.b).cuda()
+    out = {}
+    for key in ("plain", "learned"):
+        H = M.Hierarchy(st, 2, 1025, prob.levels, m=M_WINDOW, precision=M.MPCG_MIXED)
+        if key == "learned":
+            M.mg_learned_attach(H.h, params)
+        x = torch.zeros_like(b)
+        res = {}
+
+        def step():
+            x.zero_()
+            res["st"], res["k"], _, _ = H.solve(b, x, rtol=RTOL, maxit=50000, histories=False)
+
+        ms = _timed(step, args.steps, 1, torch.cuda.current_stream())
+        out[key] = {"ms_per_solve": ms, "iterations": int(res["k"]), "status": int(res["st"]),
+                    "dofs_per_s": prob.n / (ms * 1e-3)}
+        H.close()
+    print(json.dumps({
+        "metric": METRIC, "workload": "learned", "value": out["learned"]["dofs_per_s"], "unit": "DOFs/s",
+        "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64+bf16", "data": "synthetic",
+        "config": {"workload": "2D diffusion 1025^2, 9 grids, log10 kappa U[-2,4] on 16x16 macro cells (seed 3), "
+                               "f = 1, MPCG m=5, mixed precision, rtol 1e-8; network 2-16-16-16-1 trained on 4096 "
+                               "pairs from 129^2 problems (kappa seeds 1000-1015)"},
+        "plain": out["plain"], "learned": out["learned"],
+        "training": {"pairs": len(R), "epochs": args.epochs, "loss_first": float(loss[0]),
+                     "loss_last": float(loss[-1]), "pair_generation_s": gen_s, "train_s": train_s}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", choices=["poisson3d", "batched", "learned"], default="poisson3d",
+                    help="poisson3d: the headline line; batched / learned: the batch and learned-column workloads")
+    ap.add_argument("--epochs", type=int, default=20, help="training epochs of the learned workload")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
@@ -423,6 +559,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return bench_reference(args)
+    if args.workload == "batched":
+        return bench_batched(args)
+    if args.workload == "learned":
+        return bench_learned(args)
     return bench_ours(args)
 
 

@@ -56,16 +56,9 @@ def bf16(x) -> np.ndarray:
 
 
 def init_params(seed: int = 7) -> np.ndarray:
-    """Kaiming-uniform weights, U(-b, b) with b = sqrt(6 / fan_in), drawn from
-    the splitmix64 uniforms of the input module."""
-    from paper_2402_12833_gb300.problems import uniform
-    parts = []
-    for i in range(4):
-        fan_in = CHANS[i] * 9
-        b = np.sqrt(6.0 / fan_in)
-        u = uniform(seed * 1000 + i, CHANS[i + 1] * CHANS[i] * 9)
-        parts.append((2.0 * u - 1.0) * b)
-    return np.concatenate(parts).astype(np.float32)
+    """The seeded initial weights (an input, drawn by the input module)."""
+    from paper_2402_12833_gb300.problems import net_init_params
+    return net_init_params(seed, CHANS)
 
 
 def coefficient_channel(diag: np.ndarray) -> np.ndarray:

@@ -296,6 +296,18 @@ def anisotropic_2d(nodes: int, kxx: float, kyy: float = 1.0) -> Problem:
     return Problem(2, nodes, levels_for_nodes(nodes), st, b, name=f"aniso2d_{nodes}_{kxx:g}")
 
 
+def net_init_params(seed: int = 7, chans=(2, 16, 16, 16, 1)) -> np.ndarray:
+    """Initial weights of the learned column's 3x3 network, layer by layer
+    W[co][ci][ky][kx]: Kaiming-uniform draws U(-b, b), b = sqrt(6 / (9 ci)),
+    from the splitmix64 uniforms above (float32)."""
+    parts = []
+    for i in range(len(chans) - 1):
+        b = np.sqrt(6.0 / (chans[i] * 9))
+        u = uniform(seed * 1000 + i, chans[i + 1] * chans[i] * 9)
+        parts.append((2.0 * u - 1.0) * b)
+    return np.concatenate(parts).astype(np.float32)
+
+
 def batch_sizes(count: int = 256, seed: int = 4, choices=(33, 65, 129, 257, 513)) -> list[int]:
     """Side lengths of a batch of 2D problems, drawn uniformly from ``choices``."""
     u = uniform(seed, count)
