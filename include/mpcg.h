@@ -7,10 +7,10 @@
  * block Z = [z^0 | ... | z^L] of per-level additive multigrid corrections
  * z^l = P_l^L S_l (R_L^l r) (Section 2.2; restriction R = P^T and composite
  * transfers by successive two-level transfers, Section 2.1; damped-Jacobi
- * smoothing S_l^nu on levels l >= 1, Eq. 3; an exact Cholesky solve on the
+ * smoothing S_l^nu on levels l >= 1, Eq. 2; an exact Cholesky solve on the
  * coarsest level), A-orthogonalises it against the last m search blocks,
  * and updates x and r with the energy-optimal coefficients
- * alpha = (P^T A P)^+ P^T r (Section 2.2, Eq. 5 and Eq. 6).
+ * alpha = (P^T A P)^+ P^T r (the step-size formula of Section 2.2 and Eq. 4).
  *
  * Problem class (Section 1): a symmetric positive definite matrix from a Q1
  * finite-element discretisation on a uniform structured grid of the unit
@@ -83,7 +83,7 @@ typedef struct {
  * inner_rtol = 1e-4, inner pinv_tau = 1e-6, inner drop_delta = 1e-5. */
 typedef struct {
   int m;                 /* truncation window: stored search blocks, 1..MPCG_MAX_WINDOW */
-  int nu;                /* damped-Jacobi sweeps per level, >= 1 (Eq. 3, c_0 = 0) */
+  int nu;                /* damped-Jacobi sweeps per level, >= 1 (Eq. 2, c_0 = 0) */
   double omega;          /* Jacobi damping */
   double pinv_tau;       /* eigenvalue cutoff of the scaled pseudo-inverse (FP64 path) */
   double drop_delta;     /* column-drop threshold on A-norm^2 ratios (FP64 path) */

@@ -10,7 +10,7 @@ arithmetic).
 
 Modules
   operators  - stencil -> CSR, prolongations (Section 2.1), Galerkin products
-  mg         - the additive MG level corrections (Eq. 3, Eq. 4) as columns
+  mg         - the additive MG level corrections (Eq. 2, Eq. 3) as columns
   mpcg       - Algorithm 1 with the truncated window, pseudo-inverse, drop rule
   pcg        - textbook additive-MG PCG, used only as an independent pin
 """

@@ -5,13 +5,13 @@ j-1 to grid j; R_j = P_j^T (no rescaling); coarse operators by Galerkin
 products A_{j-1} = P_j^T A_j P_j.
 
 Level operators:
-  * smoother on every level j >= 1 (Eq. 3 with M_j = D_j / omega, damped
+  * smoother on every level j >= 1 (Eq. 2 with M_j = D_j / omega, damped
     Jacobi): starting from c_0 = 0, nu sweeps s <- s + omega D^{-1}(g - A s);
   * the coarsest grid gets S_0 = A_0^{-1}, applied with a dense Cholesky factor.
 
 MG(r) returns the block Z = [z^0 | ... | z^J] of Section 2.2 with
 z^l = P_J ... P_{l+1} S_l (P_{l+1}^T ... P_J^T r), coarse column first.  The sum
-of the columns is the additive MG correction of Eq. 4.
+of the columns is the additive MG correction of Eq. 3.
 """
 from __future__ import annotations
 
@@ -54,7 +54,7 @@ class Hierarchy:
         return self.levels - 1
 
     def smooth(self, j: int, g: np.ndarray) -> np.ndarray:
-        """Damped Jacobi, nu sweeps from zero (Eq. 3 with c_0 = 0)."""
+        """Damped Jacobi, nu sweeps from zero (Eq. 2 with c_0 = 0)."""
         s = np.zeros_like(g)
         for _ in range(self.nu):
             s = s + self.omega * self.Dinv[j] * (g - self.A[j] @ s)
@@ -91,5 +91,5 @@ class Hierarchy:
         return Z
 
     def additive_mg(self, r: np.ndarray) -> np.ndarray:
-        """B r of Eq. 4 (the sum of the level corrections)."""
+        """B r of Eq. 3 (the sum of the level corrections)."""
         return self.mg_columns(r).sum(axis=1)

@@ -1,7 +1,7 @@
 """Textbook preconditioned CG (Hestenes-Stiefel recurrence), FP64.
 
 Used only as an independent pin: with the additive MG preconditioner B of
-Eq. 4 this is the additive MG-PCG method the paper compares against
+Eq. 3 this is the additive MG-PCG method the paper compares against
 (Section 2.1 and Section 3.1); MPCG given the single summed column B r must
 reproduce its iterates.
 """

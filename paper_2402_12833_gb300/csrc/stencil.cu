@@ -1,6 +1,6 @@
 // Structured-grid kernels: layout conversion, block stencil SpMM (the A Z
 // product of Section 2.2), residual, restriction R = P^T and prolongation P
-// (Section 2.1), damped-Jacobi smoothing (Eq. 3), and the Galerkin product
+// (Section 2.1), damped-Jacobi smoothing (Eq. 2), and the Galerkin product
 // P^T A P that builds the coarse operators.
 //
 // The stencil kernels work on the padded layout described in common.cuh and
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kBlock) k_restrict(GridDesc gf, GridDesc gc, c
   rc[idc] = acc;
 }
 
-// Damped Jacobi (Eq. 3 with M = D / omega, dinv = omega / diag), c_0 = 0:
+// Damped Jacobi (Eq. 2 with M = D / omega, dinv = omega / diag), c_0 = 0:
 //   mode 0: out = dinv r                          (one sweep)
 //   mode 1: out = s1 + dinv (r - A s1), s1 = dinv r  (two sweeps, s1 formed
 //           at the neighbours on the fly)

@@ -73,7 +73,7 @@ def test_galerkin_equals_rediscretisation_coarse_aligned_kappa():
 # ---------------------------------------------------------------- level operators
 
 def test_two_sweep_jacobi_closed_form():
-    """Eq. 3 with c_0 = 0, nu = 2, M = D/omega: S g = 2 w D^-1 g - w^2 D^-1 A D^-1 g."""
+    """Eq. 2 with c_0 = 0, nu = 2, M = D/omega: S g = 2 w D^-1 g - w^2 D^-1 A D^-1 g."""
     prob = pb.diffusion_macro(2, 33, 5)
     H = _hier(prob)
     j = H.J
@@ -95,7 +95,7 @@ def test_coarse_solve_matches_dense_solve():
 
 
 def test_columns_sum_to_additive_mg_eq4():
-    """sum_l z^l = B r of Eq. 4, with B built from dense composite transfers
+    """sum_l z^l = B r of Eq. 3, with B built from dense composite transfers
     and dense level operators (no successive application)."""
     prob = pb.diffusion_macro(2, 17, 4)
     H = _hier(prob)
