@@ -180,24 +180,53 @@ def _eliminate_dirichlet(dim: int, planes_int: np.ndarray) -> np.ndarray:
     return out
 
 
+ALL_FACES = 0x3F
+
+
+def face_flags(dim: int, faces: int):
+    """Per axis (x first): (lo, hi) = 1 where that face is a Dirichlet face.
+    Bit 2a of ``faces`` is the low face of axis a, bit 2a+1 the high face."""
+    return [((faces >> (2 * a)) & 1, (faces >> (2 * a + 1)) & 1) for a in range(dim)]
+
+
+def grid_shape(dim: int, nodes: int, faces: int = ALL_FACES):
+    """Unknown nodes per axis (x first): nodes minus the Dirichlet faces."""
+    return tuple(nodes - lo - hi for lo, hi in face_flags(dim, faces))
+
+
 @dataclasses.dataclass
 class Problem:
-    """A structured Q1 problem: operator stencil, right-hand side and metadata."""
+    """A structured Q1 problem: operator stencil, right-hand side and metadata.
+
+    Scalar problems (``ncomp == 1``) use the stencil format described above.
+    Vector problems (``ncomp == 3``, 3D elasticity) have unknowns
+    ``i = a + 3 * node`` (component a fastest, nodes lexicographic over the
+    unknown nodes, x fastest) and a stencil of shape ``(3 * 27, n)``: plane
+    ``b * 27 + s`` holds, for every row unknown (node, a), the coefficient
+    coupling it to unknown (node + offset_s, b)."""
     dim: int
     nodes: int               # nodes per side, boundary included
     levels: int              # grids in the nested hierarchy (coarsest has 5 nodes per side)
-    stencil: np.ndarray      # (3**dim, n) float64, the format described above
+    stencil: np.ndarray      # (ncomp * 3**dim, n) float64, the format described above
     b: np.ndarray            # (n,) float64
     name: str = ""
     kappa: np.ndarray | None = None   # element coefficient field, if any
+    ncomp: int = 1           # unknowns per node
+    faces: int = ALL_FACES   # Dirichlet faces (bit 2a: low face of axis a, 2a+1: high face)
 
     @property
     def n1(self) -> int:
+        if self.faces != ALL_FACES:
+            raise AttributeError("n1 is defined for all-Dirichlet grids only; use shape")
         return self.nodes - 2
 
     @property
+    def shape(self):
+        return grid_shape(self.dim, self.nodes, self.faces)
+
+    @property
     def n(self) -> int:
-        return self.n1 ** self.dim
+        return self.ncomp * int(np.prod(self.shape))
 
 
 def assemble_diffusion(dim: int, nodes: int, kappa=None, kdiag=None) -> np.ndarray:
@@ -317,3 +346,104 @@ def batch_sizes(count: int = 256, seed: int = 4, choices=(33, 65, 129, 257, 513)
 def batch_problem(index: int, nodes: int) -> Problem:
     """Problem ``index`` of the batched workload: own kappa seed and N(0,1) RHS."""
     return diffusion_macro(2, nodes, kappa_seed=10000 + index, rhs="normal", rhs_seed=20000 + index)
+
+
+# ---------------------------------------------------------------------------
+# 3D linear elasticity (vector Q1)
+# ---------------------------------------------------------------------------
+
+def q1_elasticity(h: float, E: float = 1.0, nu: float = 0.3) -> np.ndarray:
+    """24 x 24 element stiffness of isotropic linear elasticity on a cube
+    element of side h: sum over the 2x2x2 Gauss points of B^T D B |J| w.
+    Unknown 3*a + c is component c of local node a (corner bits, x fastest).
+    Strains in Voigt order (xx, yy, zz, yz, xz, xy) with engineering shears;
+    D from the Lame constants lambda = E nu / ((1+nu)(1-2nu)), mu = E / (2(1+nu))."""
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    mu = E / (2.0 * (1.0 + nu))
+    D = np.zeros((6, 6))
+    D[:3, :3] = lam
+    D[0, 0] = D[1, 1] = D[2, 2] = lam + 2.0 * mu
+    D[3, 3] = D[4, 4] = D[5, 5] = mu
+    gp = (0.5 - 0.5 / math.sqrt(3.0), 0.5 + 0.5 / math.sqrt(3.0))   # Gauss points on [0, 1]
+    K = np.zeros((24, 24))
+    for tz in gp:
+        for ty in gp:
+            for tx in gp:
+                t = (tx, ty, tz)
+                B = np.zeros((6, 24))
+                for a in range(8):
+                    bits = [(a >> k) & 1 for k in range(3)]
+                    f = [t[k] if bits[k] else 1.0 - t[k] for k in range(3)]
+                    df = [1.0 if bits[k] else -1.0 for k in range(3)]
+                    # d N_a / d x_k = d N_a / d t_k / h
+                    g = [df[k] * f[(k + 1) % 3] * f[(k + 2) % 3] / h for k in range(3)]
+                    c = 3 * a
+                    B[0, c + 0] = g[0]
+                    B[1, c + 1] = g[1]
+                    B[2, c + 2] = g[2]
+                    B[3, c + 1], B[3, c + 2] = g[2], g[1]
+                    B[4, c + 0], B[4, c + 2] = g[2], g[0]
+                    B[5, c + 0], B[5, c + 1] = g[1], g[0]
+                K += B.T @ D @ B * (h ** 3 / 8.0)          # |J| w = h^3 * (1/2)^3
+    return K
+
+
+def _eliminate_faces(dim: int, planes: np.ndarray, faces: int) -> np.ndarray:
+    """Rows of the unknown nodes only (planes over all nodes in, numpy order
+    [..., z, y, x]), with the couplings to Dirichlet nodes set to zero."""
+    flags = face_flags(dim, faces)
+    sl = tuple(slice(lo, planes.shape[-1 - ax] - hi) for ax, (lo, hi) in reversed(list(enumerate(flags))))
+    out = planes[(Ellipsis,) + sl].copy()
+    nplanes = 3 ** dim
+    for q in range(out.shape[0]):
+        off = _offsets(dim)[q % nplanes]
+        for ax, o in enumerate(off):
+            lo, hi = flags[ax]
+            if (o < 0 and lo) or (o > 0 and hi):
+                npax = out.ndim - 1 - ax
+                idx = [slice(None)] * out.ndim
+                idx[npax] = 0 if o < 0 else out.shape[npax] - 1
+                out[(q,) + tuple(idx[1:])] = 0.0
+    return out
+
+
+def assemble_elasticity(nodes: int, E: float = 1.0, nu: float = 0.3, faces: int = 0x1) -> np.ndarray:
+    """Stencil (81, 3 n_nodes) of Q1 elasticity on the unit cube with the
+    Dirichlet (clamped) faces in ``faces`` (default: x = 0 only), in the
+    vector format of :class:`Problem`."""
+    h = 1.0 / (nodes - 1)
+    ne = nodes - 1
+    K = q1_elasticity(h, E, nu)
+    full = np.zeros((3, 27, 3) + (nodes,) * 3)      # [b][s][a][z][y][x]
+    for la in range(8):
+        abits = [(la >> k) & 1 for k in range(3)]
+        sl = tuple(slice(abits[k], abits[k] + ne) for k in (2, 1, 0))
+        for lb in range(8):
+            bbits = [(lb >> k) & 1 for k in range(3)]
+            s = plane_index(tuple(bb - aa for aa, bb in zip(abits, bbits)))
+            for a in range(3):
+                for b in range(3):
+                    full[(b, s, a) + sl] += K[3 * la + a, 3 * lb + b]
+    full = full.reshape((81, 3) + (nodes,) * 3)
+    # eliminate per (plane, component) and order rows as (node, component)
+    planes = np.stack([_eliminate_faces(3, full[:, a], faces) for a in range(3)], axis=-1)   # [q][z][y][x][a]
+    return planes.reshape(81, -1)
+
+
+def elasticity_body_force(nodes: int, force=(0.0, 0.0, -1.0), faces: int = 0x1) -> np.ndarray:
+    """b_(node, a) = force_a * integral of the node's hat function, for the
+    unknown nodes (the consistent load of a constant body force)."""
+    h = 1.0 / (nodes - 1)
+    ne = nodes - 1
+    full = _assemble_full(3, nodes, q1_mass(3, h), np.ones((ne,) * 3))
+    vol = full.sum(axis=0)                                # sum_j M_ij = integral of N_i
+    flags = face_flags(3, faces)
+    sl = tuple(slice(lo, nodes - hi) for lo, hi in reversed(flags))
+    vol = vol[sl].reshape(-1)
+    return (vol[:, None] * np.asarray(force, dtype=np.float64)[None, :]).reshape(-1)
+
+
+def elasticity_cantilever(nodes: int = 65, E: float = 1.0, nu: float = 0.3) -> Problem:
+    """The unit cube clamped at x = 0 under the body force (0, 0, -1)."""
+    return Problem(3, nodes, levels_for_nodes(nodes), assemble_elasticity(nodes, E, nu),
+                   elasticity_body_force(nodes), name=f"elasticity3d_{nodes}", ncomp=3, faces=0x1)

@@ -280,7 +280,7 @@ def test_mpcg_fewer_iterations_than_pcg_on_poisson():
 def test_planted_wrong_prolongation_weight_fails_interpolation_pin(monkeypatch):
     import oracle.operators as ops
 
-    def bad_p1(nc):
+    def bad_p1(nc, lo=1, hi=1):
         nf = 2 * nc + 1
         rows, cols, vals = [], [], []
         for I in range(nc):
