@@ -14,10 +14,12 @@
  *
  * Problem class (Section 1): a symmetric positive definite matrix from a Q1
  * finite-element discretisation on a uniform structured grid of the unit
- * square or cube, homogeneous Dirichlet nodes eliminated.
+ * square or cube, homogeneous Dirichlet nodes eliminated; scalar unknowns
+ * (diffusion) or three displacement components per node (3D elasticity).
  *
  * Conventions for every entry point
- *   - Vectors hold the n interior unknowns in lexicographic order, x fastest.
+ *   - Vectors hold the n unknowns in lexicographic node order, x fastest
+ *     (components of a node consecutive for vector problems).
  *   - Pointers named *_dev are CUDA device pointers owned by the caller; the
  *     library never frees them.  mpcg_solve also accepts host pointers for b
  *     and x (pinned or pageable) and stages them through device memory.
@@ -63,18 +65,38 @@ enum { MPCG_FP64 = 0, MPCG_MIXED = 1 };
  *   nodes      nodes per side of the grid, boundary included; nodes - 1 must
  *              be a power of two >= 4 (so that the grid can be coarsened
  *              down to 5 nodes per side)
- *   values_dev device array of 3^dim * n doubles, n = (nodes-2)^dim: plane s
- *              (s = (dx+1) + 3(dy+1) [+ 9(dz+1)]) holds for every row the
- *              coefficient coupling it to the neighbour at offset
- *              (dx, dy[, dz]).  Couplings to eliminated boundary nodes must be
- *              zero.  The matrix must be symmetric positive definite.
- *              Read during mg_hierarchy_setup only.
+ *   dofs_per_node
+ *              1 (scalar problems such as the diffusion equation of
+ *              Section 1), or 3 in 3D (linear elasticity: unknown
+ *              i = a + 3 * node is displacement component a of the node)
+ *   dirichlet_faces
+ *              the faces whose nodes are eliminated (homogeneous Dirichlet):
+ *              bit 2a = low face of axis a (x = 0, y = 0, z = 0 for a = 0,1,2),
+ *              bit 2a+1 = high face; MPCG_ALL_FACES for all of them.  Nodes
+ *              on the other faces are unknowns (natural boundary).  In 2D
+ *              the z bits are ignored.  The unknown nodes are numbered
+ *              lexicographically, x fastest.
+ *   values_dev device array of S * n doubles, S = dofs_per_node * 3^dim,
+ *              n the number of unknowns: plane b * 3^dim + s
+ *              (s = (dx+1) + 3(dy+1) [+ 9(dz+1)]) holds for every row
+ *              unknown (node, a) the coefficient coupling it to the unknown
+ *              (node + (dx, dy[, dz]), b).  Couplings to eliminated or
+ *              absent nodes must be zero.  The matrix must be symmetric
+ *              positive definite.  Read during mg_hierarchy_setup only.
+ * The coarse grids keep the same faces; transfers act componentwise, and
+ * the smoother of a vector problem is block Jacobi over each node's
+ * dofs_per_node x dofs_per_node diagonal block.  Vector problems allow at
+ * most 8 grids.
  */
+#define MPCG_ALL_FACES 0x3Fu
+
 typedef struct {
   int dim;
   int nodes;
   int format;                 /* MPCG_FORMAT_STENCIL */
   const double* values_dev;
+  int dofs_per_node;          /* 1, or 3 (3D) */
+  unsigned dirichlet_faces;   /* MPCG_ALL_FACES for the pure Dirichlet problem */
 } mg_operator;
 
 /* Solver options.  mpcg_default_options() fills the paper's / the default

@@ -46,6 +46,8 @@ void set_err(const char* fmt, ...) {
 
 struct Level {
   GridDesc g;
+  int nplanes = 0;   // stencil planes: ncomp * 3^dim
+  int ndinv = 0;     // inverse-diagonal planes: ncomp
   double* st64 = nullptr;
   float* st32 = nullptr;
   double* dinv64 = nullptr;
@@ -263,7 +265,7 @@ mpcg_status build_solver(mg_hierarchy* h, Solver<T>& S) {
       CKS(S.mem.get(&S.rlev[j], g.cp, s));
       CKS(S.mem.get(&S.zc[j], (size_t)(j + 1) * g.cp, s));
     }
-    if (h->opt.nu > 2) {
+    if (h->opt.nu > 2 || (g.ncomp > 1 && h->opt.nu > 1)) {
       CKS(S.mem.get(&S.tmp[j], g.cp, s));
       CKS(S.mem.get(&S.tmp2[j], g.cp, s));
     }
@@ -303,6 +305,20 @@ void enqueue_smooth(mg_hierarchy* h, Solver<T>& S, int j, const T* rr, T* out, c
   const T* st = st_of<T>(L);
   const T* di = dinv_of<T>(L);
   const int nu = h->opt.nu;
+  if (L.g.ncomp > 1) {
+    // block Jacobi: the first sweep from zero, then nu - 1 further sweeps
+    T* a = S.tmp[j];
+    T* b = S.tmp2[j];
+    LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, nullptr, nu == 1 ? out : a, 0, state, s));
+    for (int k = 2; k <= nu; ++k) {
+      T* o = k == nu ? out : b;
+      LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, a, o, 2, state, s));
+      T* t = a;
+      a = b;
+      b = t;
+    }
+    return;
+  }
   if (nu == 1) {
     LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, nullptr, out, 0, state, s));
   } else if (nu == 2) {
@@ -532,13 +548,12 @@ bool is_device_pointer(const void* p) {
 mpcg_status build_f32(mg_hierarchy* h) {
   if (h->have32) return MPCG_OK;
   cudaStream_t s = h->stream;
-  const int S = h->dim == 3 ? 27 : 9;
   for (int j = 0; j < h->levels; ++j) {
     Level& L = h->lev[j];
-    CKS(h->mem.get(&L.st32, (size_t)S * L.g.cp, s));
-    CKS(h->mem.get(&L.dinv32, L.g.cp, s));
-    launch_convert_f32(L.st64, L.st32, (long long)S * L.g.cp, s);
-    launch_convert_f32(L.dinv64, L.dinv32, L.g.cp, s);
+    CKS(h->mem.get(&L.st32, (size_t)L.nplanes * L.g.cp, s));
+    CKS(h->mem.get(&L.dinv32, (size_t)L.ndinv * L.g.cp, s));
+    launch_convert_f32(L.st64, L.st32, (long long)L.nplanes * L.g.cp, s);
+    launch_convert_f32(L.dinv64, L.dinv32, (long long)L.ndinv * L.g.cp, s);
   }
   const GridDesc& gf = h->lev[h->levels - 1].g;
   CKS(h->mem.get(&h->b64, gf.cp, s));
@@ -641,7 +656,8 @@ static mpcg_status setup_impl(const mg_operator* ops, int nb, int levels, const 
   }
   const mg_operator* A = ops;
   for (int b = 0; b < nb; ++b)
-    if (!ops[b].values_dev || ops[b].dim != A->dim || ops[b].nodes != A->nodes || ops[b].format != A->format) {
+    if (!ops[b].values_dev || ops[b].dim != A->dim || ops[b].nodes != A->nodes || ops[b].format != A->format ||
+        ops[b].dofs_per_node != A->dofs_per_node || ops[b].dirichlet_faces != A->dirichlet_faces) {
       set_err("operator %d: NULL values or a grid that differs from operator 0", b);
       return MPCG_ERR_ARG;
     }
@@ -662,11 +678,21 @@ static mpcg_status setup_impl(const mg_operator* ops, int nb, int levels, const 
     set_err("nodes - 1 must be a power of two in [4, 32768] (nodes = %d)", A->nodes);
     return MPCG_ERR_ARG;
   }
+  const int ncomp = A->dofs_per_node;
+  if (ncomp != 1 && !(ncomp == 3 && A->dim == 3)) {
+    set_err("dofs_per_node must be 1, or 3 in 3D (got %d)", ncomp);
+    return MPCG_ERR_ARG;
+  }
+  if (A->dirichlet_faces > MPCG_ALL_FACES) {
+    set_err("dirichlet_faces 0x%x has bits beyond the six faces", A->dirichlet_faces);
+    return MPCG_ERR_ARG;
+  }
+  const unsigned faces = A->dim == 2 ? (A->dirichlet_faces & 0xFu) : A->dirichlet_faces;   // 2D: no z faces
   int k = 0;
   while ((1 << k) < q) ++k;
-  if (levels < 1 || levels > k || levels > kMaxLevels || levels > MPCG_MAX_COLS) {
-    set_err("levels = %d invalid for %d nodes per side (1..%d)", levels, A->nodes,
-            k < MPCG_MAX_COLS ? k : MPCG_MAX_COLS);
+  const int maxcols = ncomp > 1 ? kMaxVecCols : MPCG_MAX_COLS;
+  if (levels < 1 || levels > k || levels > kMaxLevels || levels > maxcols) {
+    set_err("levels = %d invalid for %d nodes per side (1..%d)", levels, A->nodes, k < maxcols ? k : maxcols);
     return MPCG_ERR_ARG;
   }
   mpcg_options opt;
@@ -677,9 +703,7 @@ static mpcg_status setup_impl(const mg_operator* ops, int nb, int levels, const 
     set_err("invalid options (m in 1..%d, nu >= 1, omega > 0, tau/delta >= 0, max_outer >= 1)", MPCG_MAX_WINDOW);
     return MPCG_ERR_ARG;
   }
-  const int n1c = (q >> (levels - 1)) - 1;
-  long long n0 = 1;
-  for (int d = 0; d < A->dim; ++d) n0 *= n1c;
+  const long long n0 = make_grid_nodes(A->dim, (q >> (levels - 1)) + 1, faces, ncomp).n;
   if (n0 > 1024) {
     set_err("coarsest grid has %lld unknowns (> 1024); use more levels", n0);
     return MPCG_ERR_ARG;
@@ -712,12 +736,19 @@ static mpcg_status setup_impl(const mg_operator* ops, int nb, int levels, const 
     set_err("cudaStreamCreateWithFlags failed");
     return fail(MPCG_ERR_CUDA);
   }
-  const int S = A->dim == 3 ? 27 : 9;
+  const int S = (A->dim == 3 ? 27 : 9) * ncomp;
   cudaStream_t s = h->stream;
   for (int j = 0; j < levels; ++j) {
-    h->lev[j].g = make_grid(A->dim, (q >> (levels - 1 - j)) - 1, nb);
-    if ((st = h->mem.get(&h->lev[j].st64, (size_t)S * h->lev[j].g.cp, s)) != MPCG_OK) return fail(st);
-    if ((st = h->mem.get(&h->lev[j].dinv64, h->lev[j].g.cp, s)) != MPCG_OK) return fail(st);
+    Level& L = h->lev[j];
+    L.g = make_grid_nodes(A->dim, (q >> (levels - 1 - j)) + 1, faces, ncomp, nb);
+    L.nplanes = S;
+    L.ndinv = ncomp;
+    if (L.g.npts >= (1LL << 31)) {
+      set_err("grid too large (%lld padded entries per vector)", L.g.npts);
+      return fail(MPCG_ERR_ARG);
+    }
+    if ((st = h->mem.get(&L.st64, (size_t)S * L.g.cp, s)) != MPCG_OK) return fail(st);
+    if ((st = h->mem.get(&L.dinv64, (size_t)ncomp * L.g.cp, s)) != MPCG_OK) return fail(st);
   }
   const int J = levels - 1;
   // fine stencils: compact [S][n] per problem -> padded planes
@@ -988,7 +1019,8 @@ mpcg_status mg_apply_operator(mg_hierarchy* h, int level, const double* X, doubl
   cudaStream_t s = h->stream;
   const Level& L = h->lev[level];
   double *xp = nullptr, *yp = nullptr;
-  const int chunk = ncols < kMaxCols ? ncols : kMaxCols;
+  const int maxc = L.g.ncomp > 1 ? kMaxVecCols : kMaxCols;
+  const int chunk = ncols < maxc ? ncols : maxc;
   CK(cudaMalloc(&xp, sizeof(double) * chunk * L.g.len));
   CK(cudaMalloc(&yp, sizeof(double) * chunk * L.g.len));
   cudaMemsetAsync(xp, 0, sizeof(double) * chunk * L.g.len, s);
@@ -1034,8 +1066,7 @@ mpcg_status mg_get_operator(mg_hierarchy* h, int level, double* planes) {
   }
   CK(cudaSetDevice(h->device));
   const Level& L = h->lev[level];
-  const int S = h->dim == 3 ? 27 : 9;
-  launch_unpack<double, double>(L.g, L.st64, planes, L.g.n, S, h->stream);
+  launch_unpack<double, double>(L.g, L.st64, planes, L.g.n, L.nplanes, h->stream);
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaGetLastError());
   return MPCG_OK;
@@ -1048,8 +1079,9 @@ mpcg_status mg_get_operator(mg_hierarchy* h, int level, double* planes) {
 namespace {
 
 mpcg_status net_check_grid(const mg_hierarchy* h) {
-  if (h->dim != 2 || h->nb != 1) {
-    set_err("the learned column is implemented for single (unbatched) 2D problems");
+  const GridDesc& g = h->lev[h->levels - 1].g;
+  if (h->dim != 2 || h->nb != 1 || g.ncomp != 1 || g.nx != g.ny || g.px != g.py || g.lp < 0) {
+    set_err("the learned column is implemented for single (unbatched) scalar 2D problems with Dirichlet faces");
     return MPCG_ERR_ARG;
   }
   return MPCG_OK;

@@ -398,21 +398,26 @@ __global__ void k_check(DevState* st, const double* part_r, int nblk, double* re
   }
 }
 
+// Dense matrix of the coarsest operator: row i = a + ncomp * node takes
+// plane b * 3^dim + s at the row's padded entry as the coefficient of the
+// unknown (node + offset_s, b).
 __global__ void k_dense_from_stencil(GridDesc g, const double* __restrict__ st, double* __restrict__ dense) {
   const long long n = g.n;
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int x = (int)(i % g.n1), y = (int)((i / g.n1) % g.n1), z = (int)(i / ((long long)g.n1 * g.n1));
-  const long long idx = g.G + x + (long long)g.p * y + (long long)g.p * g.p * z;
+  const long long node = i / g.ncomp;
+  const int x = (int)(node % g.nx), y = (int)((node / g.nx) % g.ny), z = (int)(node / ((long long)g.nx * g.ny));
+  const long long idx = padded_index(g, i);
   const int S = g.dim == 3 ? 27 : 9;
-  for (int j = 0; j < n; ++j) dense[i * n + j] = 0.0;
-  for (int s = 0; s < S; ++s) {
-    const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = g.dim == 3 ? s / 9 - 1 : 0;
-    const int nx = x + dx, ny = y + dy, nz = z + dz;
-    if (nx < 0 || nx >= g.n1 || ny < 0 || ny >= g.n1 || nz < 0 || (g.dim == 3 ? nz >= g.n1 : nz != 0)) continue;
-    const long long j = nx + (long long)g.n1 * ny + (long long)g.n1 * g.n1 * nz;
-    dense[i * n + j] = st[s * g.cp + idx];
-  }
+  for (long long j = 0; j < n; ++j) dense[i * n + j] = 0.0;
+  for (int b = 0; b < g.ncomp; ++b)
+    for (int s = 0; s < S; ++s) {
+      const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = g.dim == 3 ? s / 9 - 1 : 0;
+      const int ox = x + dx, oy = y + dy, oz = z + dz;
+      if (ox < 0 || ox >= g.nx || oy < 0 || oy >= g.ny || oz < 0 || oz >= g.nz) continue;
+      const long long j = b + (long long)g.ncomp * (ox + (long long)g.nx * oy + (long long)g.nx * g.ny * oz);
+      dense[i * n + j] = st[(long long)(b * S + s) * g.cp + idx];
+    }
 }
 
 // Right-looking dense Cholesky A = L L^T (lower triangle overwritten), one
@@ -481,16 +486,15 @@ __global__ void k_coarse_solve(GridDesc g, const double* __restrict__ inv, const
   inv += (long long)pb * n * n;
   r += (long long)pb * g.len;
   out += (long long)pb * g.len;
-  auto padded = [&](int i) {
-    const int x = i % g.n1, yy = (i / g.n1) % g.n1, z = i / (g.n1 * g.n1);
-    return g.G + x + (long long)g.p * yy + (long long)g.p * g.p * z;
-  };
+  auto padded = [&](int i) { return padded_index(g, i); };
   for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = (double)r[padded(i)];
   __syncthreads();
+  // the computed inverse is exactly symmetric (entry (a, b) and (b, a) sum
+  // the same products in the same order), so row i is read as column i:
+  // consecutive threads read consecutive entries
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double* row = inv + (long long)i * n;
     double s = 0.0;
-    for (int j = 0; j < n; ++j) s = fma(row[j], y[j], s);
+    for (int j = 0; j < n; ++j) s = fma(inv[(long long)j * n + i], y[j], s);
     out[padded(i)] = (T)s;
   }
 }
@@ -581,7 +585,7 @@ void launch_coarse_inverse(const double* L, const double* rdiag, double* X, doub
 template <typename T>
 void launch_coarse_solve(const GridDesc& g, const double* inv, const T* r, T* out, const DevState* state,
                          cudaStream_t s) {
-  k_coarse_solve<T><<<g.nb, 128, (size_t)g.n * sizeof(double), s>>>(g, inv, r, out, state);
+  k_coarse_solve<T><<<g.nb, g.n > 128 ? 512 : 128, (size_t)g.n * sizeof(double), s>>>(g, inv, r, out, state);
 }
 template void launch_coarse_solve<double>(const GridDesc&, const double*, const double*, double*, const DevState*,
                                           cudaStream_t);

@@ -25,11 +25,7 @@ __global__ void k_pack(GridDesc g, const TI* __restrict__ src, long long ld, TO*
        t += (long long)gridDim.x * blockDim.x) {
     const int c = (int)(t / n);
     const long long i = t - (long long)c * n;
-    const int x = (int)(i % g.n1);
-    const long long q = i / g.n1;
-    const int y = (int)(q % g.n1);
-    const int z = (int)(q / g.n1);
-    dst[(long long)c * g.cp + g.G + x + (long long)g.p * y + (long long)g.p * g.p * z] = (TO)src[(long long)c * ld + i];
+    dst[(long long)c * g.cp + padded_index(g, i)] = (TO)src[(long long)c * ld + i];
   }
 }
 
@@ -40,11 +36,7 @@ __global__ void k_unpack(GridDesc g, const TI* __restrict__ src, TO* __restrict_
        t += (long long)gridDim.x * blockDim.x) {
     const int c = (int)(t / n);
     const long long i = t - (long long)c * n;
-    const int x = (int)(i % g.n1);
-    const long long q = i / g.n1;
-    const int y = (int)(q % g.n1);
-    const int z = (int)(q / g.n1);
-    dst[(long long)c * ld + i] = (TO)src[(long long)c * g.cp + g.G + x + (long long)g.p * y + (long long)g.p * g.p * z];
+    dst[(long long)c * ld + i] = (TO)src[(long long)c * g.cp + padded_index(g, i)];
   }
 }
 
@@ -63,21 +55,22 @@ __device__ __forceinline__ void load_row(const T* __restrict__ p, T (&e)[Vec<T>:
 
 // Row offsets of the 3^DIM stencil around the group start, row k = dy + 3 dz.
 template <int DIM>
-__device__ __forceinline__ long long row_offset(int k, long long p) {
+__device__ __forceinline__ long long row_offset(int k, long long px, long long pxy) {
   const int dy = k % 3 - 1, dz = DIM == 3 ? k / 3 - 1 : 0;
-  return dy * p + dz * p * p;
+  return dy * px + dz * pxy;
 }
 
 // acc[c][w] += sum over the stencil of A(point w) * X_c(neighbour), C columns;
 // pitch = distance between stencil planes and between columns.
 template <typename T, int DIM, int C>
 __device__ __forceinline__ void stencil_group(const T* __restrict__ st, long long pitch, const T* __restrict__ X,
-                                              long long idx, long long p, T (&acc)[C][Vec<T>::W]) {
+                                              long long idx, long long px, long long pxy,
+                                              T (&acc)[C][Vec<T>::W]) {
   constexpr int W = Vec<T>::W;
   constexpr int R = DIM == 3 ? 9 : 3;
 #pragma unroll
   for (int k = 0; k < R; ++k) {
-    const long long ro = row_offset<DIM>(k, p);
+    const long long ro = row_offset<DIM>(k, px, pxy);
     T a0[W], a1[W], a2[W];
     Vec<T>::load(st + (long long)(3 * k + 0) * pitch + idx, a0);
     Vec<T>::load(st + (long long)(3 * k + 1) * pitch + idx, a1);
@@ -115,7 +108,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm(GridDesc g, const T* __restrict
     for (int c = 0; c < C; ++c)
 #pragma unroll
       for (int w = 0; w < W; ++w) acc[c][w] = 0;
-    stencil_group<T, DIM, C>(st, g.cp, X, idx, g.p, acc);
+    stencil_group<T, DIM, C>(st, g.cp, X, idx, g.px, g.pxy, acc);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       Vec<T>::store(Y + (long long)c * g.cp + idx, acc[c]);
@@ -144,7 +137,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(GridDesc g, const T* __rest
     T acc[1][W];
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[0][w] = 0;
-    stencil_group<T, DIM, 1>(st, g.cp, xv, idx, g.p, acc);
+    stencil_group<T, DIM, 1>(st, g.cp, xv, idx, g.px, g.pxy, acc);
     T bv[W], rv[W];
     Vec<T>::load(b + idx, bv);
 #pragma unroll
@@ -158,8 +151,10 @@ __global__ void __launch_bounds__(kBlock) k_residual(GridDesc g, const T* __rest
   block_sum_store<T, 2>(sums, part + (long long)pb * 2 * gridDim.x, gridDim.x, blockIdx.x);
 }
 
-// Restriction R = P^T: coarse node I sits on fine node 2I+1 (per axis); the
-// fine nodes at distance one carry weight 1/2 per differing axis.
+// Restriction R = P^T: coarse node I sits on fine node 2I + lo (per axis,
+// lo = 1 when the low face is Dirichlet); the fine nodes at distance one
+// carry weight 1/2 per differing axis.  Vector unknowns restrict
+// componentwise.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBlock) k_restrict(GridDesc gf, GridDesc gc, const T* __restrict__ rf,
                                                      T* __restrict__ rc, const DevState* state) {
@@ -169,15 +164,16 @@ __global__ void __launch_bounds__(kBlock) k_restrict(GridDesc gf, GridDesc gc, c
   if (t >= gc.npts) return;
   rf += (long long)pb * gf.len;
   rc += (long long)pb * gc.len;
-  int X, Y, Z;
-  decode(gc, t, X, Y, Z);
+  int X, Y, Z, a;
+  decode(gc, t, X, Y, Z, a);
   const long long idc = gc.G + t;
   if (!interior(gc, X, Y, Z)) {
     rc[idc] = (T)0;
     return;
   }
-  const long long pf = gf.p, pp = pf * pf;
-  const long long idf = gf.G + (2 * X + 1) + pf * (2 * Y + 1) + (DIM == 3 ? pp * (2 * Z + 1) : 0);
+  const long long pf = gf.px, pp = gf.pxy;
+  const long long idf = gf.G + a * gf.cstride + (2 * X + gf.lox) + pf * (2 * Y + gf.loy) +
+                        (DIM == 3 ? pp * (2 * Z + gf.loz) : 0);
   T acc = 0;
 #pragma unroll
   for (int ez = (DIM == 3 ? -1 : 0); ez <= (DIM == 3 ? 1 : 0); ++ez) {
@@ -224,7 +220,7 @@ __global__ void __launch_bounds__(kBlock) k_jacobi(GridDesc g, const T* __restri
     constexpr int R = DIM == 3 ? 9 : 3;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-      const long long ro = row_offset<DIM>(k, g.p);
+      const long long ro = row_offset<DIM>(k, g.px, g.pxy);
       T a0[W], a1[W], a2[W], ed[W + 2], er[W + 2];
       Vec<T>::load(st + (long long)(3 * k + 0) * g.cp + idx, a0);
       Vec<T>::load(st + (long long)(3 * k + 1) * g.cp + idx, a1);
@@ -244,7 +240,7 @@ __global__ void __launch_bounds__(kBlock) k_jacobi(GridDesc g, const T* __restri
       o[w] = s1 + di[w] * (ri[w] - acc[0][w]);
     }
   } else {
-    stencil_group<T, DIM, 1>(st, g.cp, sin, idx, g.p, acc);
+    stencil_group<T, DIM, 1>(st, g.cp, sin, idx, g.px, g.pxy, acc);
     T sv[W];
     Vec<T>::load_keep(sin + idx, sv);
 #pragma unroll
@@ -254,11 +250,15 @@ __global__ void __launch_bounds__(kBlock) k_jacobi(GridDesc g, const T* __restri
 }
 
 // Prolongation P: bilinear / trilinear interpolation from the coarse grid.
-// A group of W fine points starting at even x0 needs the coarse values
-// x0/2 - 1 .. x0/2 + W/2 - 1 of each contributing coarse row:
-//   fine x0 + 2k     = (c[x0/2 + k - 1] + c[x0/2 + k]) / 2
-//   fine x0 + 2k + 1 =  c[x0/2 + k]
-// Parents outside the grid are pad entries of the coarse layout (zero).
+// Fine unknown i of an axis is global node g = i + lo; even g sits on coarse
+// node g/2, odd g takes half of coarse nodes (g-1)/2 and (g+1)/2 (coarse
+// unknown index = global - lo).  A group of W fine points starting at x0
+// (a multiple of 4, so even) reads coarse values x0/2 - lo .. x0/2 - lo + W/2
+// of each contributing coarse row:
+//   lo = 1: fine x0 + 2k = (c[k] + c[k+1]) / 2, fine x0 + 2k + 1 = c[k+1]
+//   lo = 0: fine x0 + 2k = c[k],               fine x0 + 2k + 1 = (c[k] + c[k+1]) / 2
+// Parents outside the grid are pad entries of the coarse layout (zero);
+// fine pad entries are written as zero.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBlock) k_prolong(GridDesc gc, GridDesc gf, const T* __restrict__ coarse,
                                                     T* __restrict__ fine, int ncols, const DevState* state) {
@@ -268,22 +268,31 @@ __global__ void __launch_bounds__(kBlock) k_prolong(GridDesc gc, GridDesc gf, co
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= gf.npts / W) return;
   const long long t0 = q * W;
-  int x0, y, z;
-  decode(gf, t0, x0, y, z);
+  int x0, y, z, a;
+  decode(gf, t0, x0, y, z, a);
   const long long idf = (long long)pb * gf.len + gf.G + t0;
+  const bool rowpad = y >= gf.ny || (DIM == 3 && z >= gf.nz);
   // per axis: parents (c0, c1) with weights (w0, w1)
-  auto par = [](int i, int& c0, int& c1, T& w0, T& w1) {
-    if (i & 1) { c0 = c1 = i >> 1; w0 = (T)1; w1 = (T)0; }
-    else { c0 = (i >> 1) - 1; c1 = i >> 1; w0 = w1 = (T)0.5; }
+  auto par = [](int i, int lo, int& c0, int& c1, T& w0, T& w1) {
+    const int g = i + lo;
+    if ((g & 1) == 0) { c0 = c1 = (g >> 1) - lo; w0 = (T)1; w1 = (T)0; }
+    else { c0 = ((g - 1) >> 1) - lo; c1 = c0 + 1; w0 = w1 = (T)0.5; }
   };
   int cy0, cy1, cz0 = 0, cz1 = 0;
   T wy0, wy1, wz0 = 1, wz1 = 0;
-  par(y, cy0, cy1, wy0, wy1);
-  if (DIM == 3) par(z, cz0, cz1, wz0, wz1);
-  const long long pc = gc.p, ppc = pc * pc;
-  const int cx = x0 >> 1;
+  par(y, gf.loy, cy0, cy1, wy0, wy1);
+  if (DIM == 3) par(z, gf.loz, cz0, cz1, wz0, wz1);
+  const long long pc = gc.px, ppc = gc.pxy;
+  const int cxb = (x0 >> 1) - gf.lox;
   for (int c = 0; c < ncols; ++c) {
-    const T* C0 = coarse + (long long)c * gc.cp + (long long)pb * gc.len + gc.G;
+    T o[W];
+    if (rowpad) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) o[w] = 0;
+      Vec<T>::store(fine + (long long)c * gf.cp + idf, o);
+      continue;
+    }
+    const T* C0 = coarse + (long long)c * gc.cp + (long long)pb * gc.len + gc.G + a * gc.cstride;
     T row[W / 2 + 1];
 #pragma unroll
     for (int k = 0; k <= W / 2; ++k) row[k] = 0;
@@ -295,22 +304,34 @@ __global__ void __launch_bounds__(kBlock) k_prolong(GridDesc gc, GridDesc gf, co
       for (int ky = 0; ky < 2; ++ky) {
         const int cyy = ky ? cy1 : cy0;
         const T wgt = wz * (ky ? wy1 : wy0);
-        const T* rp = C0 + pc * cyy + (DIM == 3 ? ppc * czz : 0) + cx - 1;
+        const T* rp = C0 + pc * cyy + (DIM == 3 ? ppc * czz : 0) + cxb;
 #pragma unroll
         for (int k = 0; k <= W / 2; ++k) row[k] = fma(wgt, rp[k], row[k]);
       }
     }
-    T o[W];
+    if (gf.lox) {
 #pragma unroll
-    for (int k = 0; k < W / 2; ++k) {
-      o[2 * k] = (T)0.5 * (row[k] + row[k + 1]);
-      o[2 * k + 1] = row[k + 1];
+      for (int k = 0; k < W / 2; ++k) {
+        o[2 * k] = (T)0.5 * (row[k] + row[k + 1]);
+        o[2 * k + 1] = row[k + 1];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < W / 2; ++k) {
+        o[2 * k] = row[k];
+        o[2 * k + 1] = (T)0.5 * (row[k] + row[k + 1]);
+      }
     }
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+      if (x0 + w >= gf.nx) o[w] = 0;
     Vec<T>::store(fine + (long long)c * gf.cp + idf, o);
   }
 }
 
-// Galerkin product A_c = P^T A_f P, one coarse row per thread.
+// Galerkin product A_c = P^T A_f P, one coarse row per thread.  For vector
+// unknowns P interpolates componentwise, so every component pair (a, b) is a
+// scalar Galerkin product of its own plane group b * 3^DIM + s.
 template <int DIM>
 __global__ void __launch_bounds__(kBlock) k_galerkin(GridDesc gf, GridDesc gc, const double* __restrict__ stf,
                                                      double* __restrict__ stc) {
@@ -320,66 +341,264 @@ __global__ void __launch_bounds__(kBlock) k_galerkin(GridDesc gf, GridDesc gc, c
   if (t >= gc.npts) return;
   stf += (long long)pb * gf.len;
   stc += (long long)pb * gc.len;
-  int X, Y, Z;
-  decode(gc, t, X, Y, Z);
+  int X, Y, Z, comp;
+  decode(gc, t, X, Y, Z, comp);
   const long long idc = gc.G + t;
   if (!interior(gc, X, Y, Z)) {
-    for (int s = 0; s < S; ++s) stc[s * gc.cp + idc] = 0.0;
+    for (int s = 0; s < S * gc.ncomp; ++s) stc[s * gc.cp + idc] = 0.0;
     return;
   }
-  double acc[S];
+  const long long pf = gf.px, ppf = gf.pxy;
+  for (int b = 0; b < gc.ncomp; ++b) {
+    double acc[S];
 #pragma unroll
-  for (int s = 0; s < S; ++s) acc[s] = 0.0;
-  const long long pf = gf.p, ppf = pf * pf;
-  const int nc = gc.n1;
-  for (int ez = (DIM == 3 ? -1 : 0); ez <= (DIM == 3 ? 1 : 0); ++ez)
-    for (int ey = -1; ey <= 1; ++ey)
-      for (int ex = -1; ex <= 1; ++ex) {
-        const double we = (ex ? 0.5 : 1.0) * (ey ? 0.5 : 1.0) * (ez ? 0.5 : 1.0);
-        const long long idf = gf.G + (2 * X + 1 + ex) + pf * (2 * Y + 1 + ey) + (DIM == 3 ? ppf * (2 * Z + 1 + ez) : 0);
-        for (int s = 0; s < S; ++s) {
-          const double a = stf[s * gf.cp + idf];
-          if (a == 0.0) continue;
-          const int f[3] = {ex + (s % 3 - 1), ey + ((s / 3) % 3 - 1), DIM == 3 ? ez + (s / 9 - 1) : 0};
-          // coarse parents of the fine column node, relative to (X, Y, Z)
-          int D0[3], D1[3], np[3];
-          double w[3];
-          for (int k = 0; k < 3; ++k) {
-            if (k == 2 && DIM == 2) { D0[k] = D1[k] = 0; np[k] = 1; w[k] = 1.0; continue; }
-            if ((f[k] & 1) == 0) { D0[k] = D1[k] = f[k] / 2; np[k] = 1; w[k] = 1.0; }
-            else { D0[k] = (f[k] - 1) / 2; D1[k] = (f[k] + 1) / 2; np[k] = 2; w[k] = 0.5; }
+    for (int s = 0; s < S; ++s) acc[s] = 0.0;
+    const double* sfb = stf + (long long)b * S * gf.cp;
+    for (int ez = (DIM == 3 ? -1 : 0); ez <= (DIM == 3 ? 1 : 0); ++ez)
+      for (int ey = -1; ey <= 1; ++ey)
+        for (int ex = -1; ex <= 1; ++ex) {
+          const double we = (ex ? 0.5 : 1.0) * (ey ? 0.5 : 1.0) * (ez ? 0.5 : 1.0);
+          const long long idf = gf.G + comp * gf.cstride + (2 * X + gf.lox + ex) + pf * (2 * Y + gf.loy + ey) +
+                                (DIM == 3 ? ppf * (2 * Z + gf.loz + ez) : 0);
+          for (int s = 0; s < S; ++s) {
+            const double a = sfb[s * gf.cp + idf];
+            if (a == 0.0) continue;
+            // offset of the fine column node from the fine image of (X, Y, Z);
+            // the image has even global index on every axis, so the column's
+            // coarse parents are D = f/2 (f even) or (f -+ 1)/2 (f odd)
+            const int f[3] = {ex + (s % 3 - 1), ey + ((s / 3) % 3 - 1), DIM == 3 ? ez + (s / 9 - 1) : 0};
+            int D0[3], D1[3], np[3];
+            double w[3];
+            for (int k = 0; k < 3; ++k) {
+              if (k == 2 && DIM == 2) { D0[k] = D1[k] = 0; np[k] = 1; w[k] = 1.0; continue; }
+              if ((f[k] & 1) == 0) { D0[k] = D1[k] = f[k] / 2; np[k] = 1; w[k] = 1.0; }
+              else { D0[k] = (f[k] - 1) / 2; D1[k] = (f[k] + 1) / 2; np[k] = 2; w[k] = 0.5; }
+            }
+            const double base = we * a * w[0] * w[1] * w[2];
+            const int Cc[3] = {X, Y, Z};
+            for (int iz = 0; iz < np[2]; ++iz)
+              for (int iy = 0; iy < np[1]; ++iy)
+                for (int ix = 0; ix < np[0]; ++ix) {
+                  const int Dx = ix ? D1[0] : D0[0], Dy = iy ? D1[1] : D0[1], Dz = iz ? D1[2] : D0[2];
+                  const int cx = Cc[0] + Dx, cy = Cc[1] + Dy, cz = Cc[2] + Dz;
+                  if (cx < 0 || cx >= gc.nx || cy < 0 || cy >= gc.ny) continue;   // Dirichlet parent
+                  if (DIM == 3 && (cz < 0 || cz >= gc.nz)) continue;
+                  acc[(Dx + 1) + 3 * (Dy + 1) + (DIM == 3 ? 9 * (Dz + 1) : 0)] += base;
+                }
           }
-          const double base = we * a * w[0] * w[1] * w[2];
-          const int Cc[3] = {X, Y, Z};
-          for (int iz = 0; iz < np[2]; ++iz)
-            for (int iy = 0; iy < np[1]; ++iy)
-              for (int ix = 0; ix < np[0]; ++ix) {
-                const int Dx = ix ? D1[0] : D0[0], Dy = iy ? D1[1] : D0[1], Dz = iz ? D1[2] : D0[2];
-                const int cx = Cc[0] + Dx, cy = Cc[1] + Dy, cz = Cc[2] + Dz;
-                if (cx < 0 || cx >= nc || cy < 0 || cy >= nc) continue;
-                if (DIM == 3 && (cz < 0 || cz >= nc)) continue;
-                acc[(Dx + 1) + 3 * (Dy + 1) + (DIM == 3 ? 9 * (Dz + 1) : 0)] += base;
-              }
         }
-      }
-  for (int s = 0; s < S; ++s) stc[s * gc.cp + idc] = acc[s];
+    for (int s = 0; s < S; ++s) stc[(b * S + s) * gc.cp + idc] = acc[s];
+  }
 }
 
+// Damped inverse diagonal omega D^{-1}.  Vector unknowns: D is the 3 x 3
+// block of a node's unknowns (the centre planes of the three plane groups);
+// dinv plane b at the row of component a holds omega (D^{-1})_{ab}.
 template <typename T>
 __global__ void k_dinv(GridDesc g, const double* __restrict__ st, T* __restrict__ dinv, double omega) {
   const int pb = blockIdx.y;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= g.npts) return;
-  int x, y, z;
-  decode(g, t, x, y, z);
+  int x, y, z, comp;
+  decode(g, t, x, y, z, comp);
   const long long idx = (long long)pb * g.len + g.G + t;
+  const int S = g.dim == 3 ? 27 : 9;
   const int centre = g.dim == 3 ? 13 : 4;
-  dinv[idx] = interior(g, x, y, z) ? (T)(omega / st[centre * g.cp + idx]) : (T)0;
+  const bool in = interior(g, x, y, z);
+  if (g.ncomp == 1) {
+    dinv[idx] = in ? (T)(omega / st[centre * g.cp + idx]) : (T)0;
+    return;
+  }
+  if (!in) {
+    for (int b = 0; b < 3; ++b) dinv[b * g.cp + idx] = (T)0;
+    return;
+  }
+  const long long node = idx - comp * g.cstride;
+  double D[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) D[a][b] = st[(long long)(b * S + centre) * g.cp + node + a * g.cstride];
+  // inverse by the adjugate: (D^{-1})_{ab} = cofactor_{ba} / det
+  const double c00 = D[1][1] * D[2][2] - D[1][2] * D[2][1];
+  const double c01 = D[1][2] * D[2][0] - D[1][0] * D[2][2];
+  const double c02 = D[1][0] * D[2][1] - D[1][1] * D[2][0];
+  const double det = D[0][0] * c00 + D[0][1] * c01 + D[0][2] * c02;
+  double inv[3][3];
+  inv[0][0] = c00;
+  inv[1][0] = c01;
+  inv[2][0] = c02;
+  inv[0][1] = D[0][2] * D[2][1] - D[0][1] * D[2][2];
+  inv[1][1] = D[0][0] * D[2][2] - D[0][2] * D[2][0];
+  inv[2][1] = D[0][1] * D[2][0] - D[0][0] * D[2][1];
+  inv[0][2] = D[0][1] * D[1][2] - D[0][2] * D[1][1];
+  inv[1][2] = D[0][2] * D[1][0] - D[0][0] * D[1][2];
+  inv[2][2] = D[0][0] * D[1][1] - D[0][1] * D[1][0];
+  for (int b = 0; b < 3; ++b) dinv[b * g.cp + idx] = (T)(omega * inv[comp][b] / det);
 }
 
 __global__ void k_convert_f32(const double* __restrict__ src, float* __restrict__ dst, long long count) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
     dst[i] = (float)src[i];
+}
+
+// ---------------------------------------------------------------------------
+// Vector unknowns (3D elasticity, three components per node).  Plane
+// b * 27 + s at the row of component a holds the coupling of unknown
+// (node, a) to (node + offset_s, b).  One thread takes W consecutive x-points
+// of a node row for all three components, so each neighbour row of X is
+// loaded once for the three outputs; the 81 planes of a row are read once.
+
+// acc[a][c][w] += (A X_c)_a at the group starting at idx0 (component 0).
+template <typename T, int C>
+__device__ __forceinline__ void vstencil_group(const T* __restrict__ st, long long pitch, const T* __restrict__ X,
+                                               long long idx0, long long cs, long long px, long long pxy,
+                                               T (&acc)[3][C][Vec<T>::W]) {
+  constexpr int W = Vec<T>::W;
+#pragma unroll 1
+  for (int k = 0; k < 9; ++k) {
+    const long long ro = row_offset<3>(k, px, pxy);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      T e[C][W + 2];
+#pragma unroll
+      for (int c = 0; c < C; ++c) load_row<T>(X + (long long)c * pitch + idx0 + b * cs + ro, e[c]);
+      const T* sp = st + (long long)(b * 27 + 3 * k) * pitch + idx0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        T a0[W], a1[W], a2[W];
+        Vec<T>::load(sp + a * cs, a0);
+        Vec<T>::load(sp + pitch + a * cs, a1);
+        Vec<T>::load(sp + 2 * pitch + a * cs, a2);
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+          for (int w = 0; w < W; ++w) {
+            acc[a][c][w] = fma(a0[w], e[c][w], acc[a][c][w]);
+            acc[a][c][w] = fma(a1[w], e[c][w + 1], acc[a][c][w]);
+            acc[a][c][w] = fma(a2[w], e[c][w + 2], acc[a][c][w]);
+          }
+      }
+    }
+  }
+}
+
+template <typename T, int C, bool ZAZ>
+__global__ void __launch_bounds__(kBlock) k_vspmm(GridDesc g, const T* __restrict__ st, const T* __restrict__ X,
+                                                  T* __restrict__ Y, double* zaz, const DevState* state) {
+  const int pb = blockIdx.y;
+  if (state && state[pb].done) return;
+  constexpr int W = Vec<T>::W;
+  const long long bo = (long long)pb * g.len;
+  T zacc[ZAZ ? C : 1];
+#pragma unroll
+  for (int c = 0; c < (ZAZ ? C : 1); ++c) zacc[c] = 0;
+  const long long ngroups = g.cstride / W;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long idx0 = bo + g.G + q * W;
+    T acc[3][C][W];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[a][c][w] = 0;
+    vstencil_group<T, C>(st, g.cp, X, idx0, g.cstride, g.px, g.pxy, acc);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const long long o = (long long)c * g.cp + idx0 + a * g.cstride;
+        Vec<T>::store(Y + o, acc[a][c]);
+        if (ZAZ) {
+          T xc[W];
+          Vec<T>::load_keep(X + o, xc);
+#pragma unroll
+          for (int w = 0; w < W; ++w) zacc[c] = fma(xc[w], acc[a][c][w], zacc[c]);
+        }
+      }
+  }
+  if (ZAZ) block_sum_store<T, ZAZ ? C : 1>(zacc, zaz + (long long)pb * C * gridDim.x, gridDim.x, blockIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_vresidual(GridDesc g, const T* __restrict__ st, const T* __restrict__ b,
+                                                      const T* __restrict__ xv, T* __restrict__ r, double* part) {
+  constexpr int W = Vec<T>::W;
+  const int pb = blockIdx.y;
+  const long long bo = (long long)pb * g.len;
+  T sums[2] = {0, 0};
+  const long long ngroups = g.cstride / W;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long idx0 = bo + g.G + q * W;
+    T acc[3][1][W];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int w = 0; w < W; ++w) acc[a][0][w] = 0;
+    vstencil_group<T, 1>(st, g.cp, xv, idx0, g.cstride, g.px, g.pxy, acc);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T bv[W], rv[W];
+      Vec<T>::load(b + idx0 + a * g.cstride, bv);
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        rv[w] = bv[w] - acc[a][0][w];
+        sums[0] = fma(rv[w], rv[w], sums[0]);
+        sums[1] = fma(bv[w], bv[w], sums[1]);
+      }
+      Vec<T>::store(r + idx0 + a * g.cstride, rv);
+    }
+  }
+  block_sum_store<T, 2>(sums, part + (long long)pb * 2 * gridDim.x, gridDim.x, blockIdx.x);
+}
+
+// Block Jacobi (Eq. 2 with M = D / omega, D the 3 x 3 node blocks), c_0 = 0:
+//   mode 0: out = dinv r                      (one sweep)
+//   mode 2: out = sin + dinv (r - A sin)      (a further sweep)
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_vjacobi(GridDesc g, const T* __restrict__ st, const T* __restrict__ dinv,
+                                                    const T* __restrict__ r, const T* __restrict__ sin,
+                                                    T* __restrict__ out, int mode, const DevState* state) {
+  const int pb = blockIdx.y;
+  if (state && state[pb].done) return;
+  constexpr int W = Vec<T>::W;
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= g.cstride / W) return;
+  const long long idx0 = (long long)pb * g.len + g.G + q * W;
+  const long long cs = g.cstride;
+  T t[3][W];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) Vec<T>::load_keep(r + idx0 + b * cs, t[b]);
+  if (mode == 2) {
+    T acc[3][1][W];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int w = 0; w < W; ++w) acc[a][0][w] = 0;
+    vstencil_group<T, 1>(st, g.cp, sin, idx0, cs, g.px, g.pxy, acc);
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int w = 0; w < W; ++w) t[b][w] -= acc[b][0][w];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    T o[W];
+    if (mode == 2) Vec<T>::load_keep(sin + idx0 + a * cs, o);
+    else {
+#pragma unroll
+      for (int w = 0; w < W; ++w) o[w] = 0;
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      T d[W];
+      Vec<T>::load_keep(dinv + (long long)b * g.cp + idx0 + a * cs, d);
+#pragma unroll
+      for (int w = 0; w < W; ++w) o[w] = fma(d[w], t[b][w], o[w]);
+    }
+    Vec<T>::store(out + idx0 + a * cs, o);
+  }
 }
 
 inline int blocks_for(long long n) { return (int)((n + kBlock - 1) / kBlock); }
@@ -424,9 +643,27 @@ static void spmm_dim(const GridDesc& g, const T* st, const T* X, T* Y, int C, do
 }
 
 template <typename T>
+static void vspmm(const GridDesc& g, const T* st, const T* X, T* Y, int C, double* zaz, const DevState* state,
+                  cudaStream_t s) {
+  const dim3 grid(stream_blocks(g), g.nb);
+#define MPCG_VSPMM_CASE(CC)                                                                     \
+  case CC:                                                                                      \
+    if (zaz) k_vspmm<T, CC, true><<<grid, kBlock, 0, s>>>(g, st, X, Y, zaz, state);             \
+    else k_vspmm<T, CC, false><<<grid, kBlock, 0, s>>>(g, st, X, Y, zaz, state);               \
+    break;
+  switch (C) {
+    MPCG_VSPMM_CASE(1) MPCG_VSPMM_CASE(2) MPCG_VSPMM_CASE(3) MPCG_VSPMM_CASE(4) MPCG_VSPMM_CASE(5)
+    MPCG_VSPMM_CASE(6) MPCG_VSPMM_CASE(7) MPCG_VSPMM_CASE(8)
+    default: break;
+  }
+#undef MPCG_VSPMM_CASE
+}
+
+template <typename T>
 void launch_spmm(const GridDesc& g, const T* st, const T* X, T* Y, int C, double* zaz, const DevState* state,
                  cudaStream_t s) {
-  if (g.dim == 3) spmm_dim<T, 3>(g, st, X, Y, C, zaz, state, s);
+  if (g.ncomp == 3) vspmm<T>(g, st, X, Y, C, zaz, state, s);
+  else if (g.dim == 3) spmm_dim<T, 3>(g, st, X, Y, C, zaz, state, s);
   else spmm_dim<T, 2>(g, st, X, Y, C, zaz, state, s);
 }
 template void launch_spmm<double>(const GridDesc&, const double*, const double*, double*, int, double*,
@@ -437,7 +674,8 @@ template void launch_spmm<float>(const GridDesc&, const float*, const float*, fl
 template <typename T>
 void launch_residual(const GridDesc& g, const T* st, const T* b, const T* x, T* r, double* part, cudaStream_t s) {
   const dim3 grid(stream_blocks(g), g.nb);
-  if (g.dim == 3) k_residual<T, 3><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part);
+  if (g.ncomp == 3) k_vresidual<T><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part);
+  else if (g.dim == 3) k_residual<T, 3><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part);
   else k_residual<T, 2><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part);
 }
 template void launch_residual<double>(const GridDesc&, const double*, const double*, const double*, double*,
@@ -460,6 +698,11 @@ template void launch_restrict<float>(const GridDesc&, const GridDesc&, const flo
 template <typename T>
 void launch_jacobi(const GridDesc& g, const T* st, const T* dinv, const T* r, const T* sin, T* out, int mode,
                    const DevState* state, cudaStream_t s) {
+  if (g.ncomp == 3) {   // block Jacobi: modes 0 and 2 only
+    k_vjacobi<T><<<dim3(blocks_for(g.cstride / vw<T>()), g.nb), kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode,
+                                                                              state);
+    return;
+  }
   const dim3 grid(blocks_for(g.npts / vw<T>()), g.nb);
   if (g.dim == 3) k_jacobi<T, 3><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
   else k_jacobi<T, 2><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);

@@ -67,15 +67,30 @@ __device__ __forceinline__ void block_sum_store(const T (&v)[NV], double* part, 
   }
 }
 
+// Box index t (0 <= t < npts) -> node (x, y, z) and component.
+__device__ __forceinline__ void decode(const GridDesc& g, long long t, int& x, int& y, int& z, int& comp) {
+  const unsigned u = (unsigned)t;
+  const unsigned q1 = fdiv(u, g.dvx);
+  x = (int)(u - q1 * (unsigned)g.px);
+  const unsigned q2 = fdiv(q1, g.dvy);
+  y = (int)(q1 - q2 * (unsigned)g.py);
+  if (g.dim == 3) {
+    const unsigned q3 = fdiv(q2, g.dvz);
+    z = (int)(q2 - q3 * (unsigned)g.pz);
+    comp = (int)q3;
+  } else {
+    z = 0;
+    comp = (int)q2;
+  }
+}
+
 __device__ __forceinline__ void decode(const GridDesc& g, long long t, int& x, int& y, int& z) {
-  const int mask = g.p - 1;
-  x = (int)(t & mask);
-  y = (int)((t >> g.lp) & mask);
-  z = (int)(t >> (2 * g.lp));
+  int comp;
+  decode(g, t, x, y, z, comp);
 }
 
 __device__ __forceinline__ bool interior(const GridDesc& g, int x, int y, int z) {
-  return x < g.n1 && y < g.n1 && (g.dim == 2 || z < g.n1);
+  return x < g.nx && y < g.ny && (g.dim == 2 || z < g.nz);
 }
 
 }  // namespace mpcg

@@ -36,8 +36,12 @@ class MpcgError(RuntimeError):
         self.status = status
 
 
+MPCG_ALL_FACES = 0x3F
+
+
 class mg_operator(C.Structure):
-    _fields_ = [("dim", C.c_int), ("nodes", C.c_int), ("format", C.c_int), ("values_dev", C.c_void_p)]
+    _fields_ = [("dim", C.c_int), ("nodes", C.c_int), ("format", C.c_int), ("values_dev", C.c_void_p),
+                ("dofs_per_node", C.c_int), ("dirichlet_faces", C.c_uint)]
 
 
 class mpcg_options(C.Structure):
@@ -138,10 +142,11 @@ def _ptr(a) -> int:
     raise TypeError(type(a))
 
 
-def mg_hierarchy_setup(values_dev, dim: int, nodes: int, levels: int, options: mpcg_options | None = None) -> int:
+def mg_hierarchy_setup(values_dev, dim: int, nodes: int, levels: int, options: mpcg_options | None = None,
+                       dofs_per_node: int = 1, faces: int = MPCG_ALL_FACES) -> int:
     """Return an opaque hierarchy handle for the fine stencil ``values_dev``
-    (device float64 array of shape (3**dim, n))."""
-    op = mg_operator(dim, nodes, MPCG_FORMAT_STENCIL, _ptr(values_dev))
+    (device float64 array of shape (dofs_per_node * 3**dim, n))."""
+    op = mg_operator(dim, nodes, MPCG_FORMAT_STENCIL, _ptr(values_dev), dofs_per_node, faces)
     h = C.c_void_p()
     opt = options if options is not None else mpcg_default_options()
     _check(load().mg_hierarchy_setup(C.byref(op), levels, C.byref(opt), C.byref(h)))
@@ -264,16 +269,17 @@ def mg_num_problems(h: int) -> int:
 class BatchedHierarchy:
     """Owning wrapper of a batched hierarchy: nprob problems on one grid."""
 
-    def __init__(self, stencils, dim: int, nodes: int, levels: int, **options):
+    def __init__(self, stencils, dim: int, nodes: int, levels: int, dofs_per_node: int = 1,
+                 faces: int = MPCG_ALL_FACES, **options):
         self.options = mpcg_default_options(**options)
         self._keep = list(stencils)
-        ops = (mg_operator * len(self._keep))(*[mg_operator(dim, nodes, MPCG_FORMAT_STENCIL, _ptr(s))
-                                                for s in self._keep])
+        ops = (mg_operator * len(self._keep))(*[mg_operator(dim, nodes, MPCG_FORMAT_STENCIL, _ptr(s),
+                                                            dofs_per_node, faces) for s in self._keep])
         h = C.c_void_p()
         _check(load().mg_hierarchy_setup_batched(ops, len(self._keep), levels, C.byref(self.options), C.byref(h)))
         self.h = h.value
         self.nprob = len(self._keep)
-        self.n = (nodes - 2) ** dim
+        self.n = mg_level_size(self.h, levels - 1)
 
     def solve(self, b, x, rtol=1e-8, maxit=500):
         """b, x: nprob x n (device tensors or host arrays); returns (status, iterations[nprob])."""
@@ -312,11 +318,12 @@ def mpcg_solve_batched(classes, bs, xs, rtol=1e-8, maxit=500):
 class Hierarchy:
     """Owning wrapper of a hierarchy handle (torch tensors for device memory)."""
 
-    def __init__(self, stencil_dev, dim: int, nodes: int, levels: int, **options):
+    def __init__(self, stencil_dev, dim: int, nodes: int, levels: int, dofs_per_node: int = 1,
+                 faces: int = MPCG_ALL_FACES, **options):
         self.options = mpcg_default_options(**options)
         self.dim, self.nodes, self.levels = dim, nodes, levels
         self._keep = stencil_dev
-        self.h = mg_hierarchy_setup(stencil_dev, dim, nodes, levels, self.options)
+        self.h = mg_hierarchy_setup(stencil_dev, dim, nodes, levels, self.options, dofs_per_node, faces)
 
     def solve(self, b, x, rtol=1e-8, maxit=500, histories=True):
         return mpcg_solve(self.h, b, x, rtol, maxit, histories)

@@ -229,16 +229,31 @@ class Problem:
         return self.ncomp * int(np.prod(self.shape))
 
 
-def assemble_diffusion(dim: int, nodes: int, kappa=None, kdiag=None) -> np.ndarray:
+def assemble_diffusion(dim: int, nodes: int, kappa=None, kdiag=None, faces: int = ALL_FACES) -> np.ndarray:
     """Stencil planes (3**dim, n) of the Q1 diffusion operator with element
-    coefficient field ``kappa`` (default 1) and anisotropy ``kdiag``."""
+    coefficient field ``kappa`` (default 1) and anisotropy ``kdiag``; the
+    nodes of the Dirichlet faces ``faces`` are eliminated, the other boundary
+    nodes are unknowns (natural boundary condition)."""
     h = 1.0 / (nodes - 1)
     ne = nodes - 1
     coef = np.ones((ne,) * dim) if kappa is None else np.asarray(kappa, dtype=np.float64)
     ke = q1_stiffness(dim, h, kdiag)
     full = _assemble_full(dim, nodes, ke, coef)
-    planes = _eliminate_dirichlet(dim, _interior(dim, full))
+    if faces == ALL_FACES:
+        planes = _eliminate_dirichlet(dim, _interior(dim, full))
+    else:
+        planes = _eliminate_faces(dim, full, faces)
     return planes.reshape(3 ** dim, -1)
+
+
+def diffusion_faces(dim: int, nodes: int, faces: int, rhs_seed: int, kappa_seed: int | None = None) -> Problem:
+    """Diffusion with Dirichlet data on the faces in ``faces`` only (the
+    others carry the natural condition), N(0,1) right-hand side."""
+    kap = None if kappa_seed is None else macro_kappa(dim, nodes, kappa_seed)
+    st = assemble_diffusion(dim, nodes, kappa=kap, faces=faces)
+    n = int(np.prod(grid_shape(dim, nodes, faces)))
+    return Problem(dim, nodes, levels_for_nodes(nodes), st, normal(rhs_seed, n), kappa=kap,
+                   name=f"diffusion{dim}d_{nodes}_faces{faces:x}", faces=faces)
 
 
 def load_vector(dim: int, nodes: int, fvals: np.ndarray) -> np.ndarray:

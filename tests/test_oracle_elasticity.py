@@ -220,3 +220,20 @@ def test_planted_point_jacobi_fails_block_jacobi_pin(monkeypatch):
     monkeypatch.setattr(omg, "block_diag_inverse", point_diag)
     with pytest.raises(AssertionError):
         test_two_sweep_block_jacobi_closed_form()
+
+
+@pytest.mark.parametrize("dim,faces", [(2, 0x1), (2, 0x5), (3, 0x1), (3, 0x2A)])
+def test_free_faces_galerkin_and_tiny_solve(dim, faces):
+    """Diffusion with natural conditions on some faces: Galerkin products equal
+    the rediscretised operators, and MPCG reaches the dense solution."""
+    nodes = 17 if dim == 2 else 9
+    prob = pb.diffusion_faces(dim, nodes, faces, rhs_seed=3)
+    H = omg.Hierarchy(dim, None, prob.stencil, prob.levels, nodes=nodes, faces=faces)
+    for j in range(H.levels - 1):
+        Nj = (nodes - 1) // 2 ** (H.levels - 1 - j) + 1
+        ref = stencil_to_csr(dim, pb.grid_shape(dim, Nj, faces), pb.assemble_diffusion(dim, Nj, faces=faces))
+        assert abs(H.A[j] - ref).max() < 1e-13 * abs(ref).max()
+    A = H.A[-1]
+    res = ompcg.mpcg(A, prob.b, H.mg_columns, rtol=1e-12, maxit=500)
+    x = np.linalg.solve(A.toarray(), prob.b)
+    assert np.linalg.norm(res.x - x) <= 1e-10 * np.linalg.norm(x)
