@@ -85,10 +85,10 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------- algorithmic bytes / flops
-def kernel_work(cls: str, n: int, C: int, cnt: int, w: int):
+def kernel_work(cls: str, n: int, C: int, cnt: int, w: int, S: int = 27):
     """Algorithmic HBM bytes and flops of one launch on the fine grid (per
-    interior DOF figures x n; cnt = blocks in the window at that launch)."""
-    S = 27
+    unknown figures x n; cnt = blocks in the window at that launch; S =
+    stencil coefficients per unknown: 27 for 3D scalar, 81 for elasticity)."""
     if cls == "orth_update":      # read Z, AZ, P_j, AP_j, r; write P, AP; sym Gram + P^T r
         return (2 * cnt * C + 4 * C + 1) * w * n, 2 * (2 * cnt * C * C + C * (C + 1) + C) * n
     if cls == "gram_window":      # read AP_j, Z
@@ -105,15 +105,16 @@ def level_dofs(nodes, dim, levels):
     return [((nodes - 1) // 2 ** (levels - 1 - j) - 1) ** dim for j in range(levels)]
 
 
-def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops):
+def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops, S=27, vector=False):
     """Dominant kernel class by total time; achieved = algorithmic bytes
     (or flops) summed over its launches / summed CUDA-event durations.
 
     The grid of each multilevel launch follows the launch order of one MG
-    chain: the smoothings of grids J, J-1, ..., 1 (nu = 2: one launch each),
-    the restrictions from grids J, ..., 1, the prolongations into 1, ..., J."""
+    chain: the smoothings of grids J, J-1, ..., 1 (nu = 2: one fused launch
+    each; vector problems: a first sweep and a second sweep per grid), the
+    restrictions from grids J, ..., 1, the prolongations into 1, ..., J."""
     J = len(ns) - 1
-    S = 27
+    jsub = 0
     tot = {}
     for cls, ms in trace:
         tot[cls] = tot.get(cls, 0.0) + ms
@@ -129,8 +130,15 @@ def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops):
         if cls == "init":
             cnt = 0
         if cls in ("init", "check"):
-            jj, jr, jp = J, J, 1
-        if cls == "jacobi":
+            jj, jr, jp, jsub = J, J, 1, 0
+        if cls == "jacobi" and vector:
+            if jsub == 0:     # s1 = D^-1 r: read r, 3 inverse-block planes; write s1
+                b, f = 5 * w * ns[jj], 2 * 3 * ns[jj]
+            else:             # s = s1 + D^-1 (r - A s1)
+                b, f = (S + 6) * w * ns[jj], 2 * (S + 4) * ns[jj]
+                jj -= 1
+            jsub ^= 1
+        elif cls == "jacobi":
             b, f = (S + 3) * w * ns[jj], (2 * S + 4) * ns[jj]
             jj -= 1
         elif cls == "restrict":
@@ -140,7 +148,7 @@ def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops):
             b, f = jp * (ns[jp - 1] + ns[jp]) * w, 2 * 8 * jp * ns[jp]
             jp += 1
         elif cls in ("orth_update", "gram_window", "spmm", "update_xr"):
-            b, f = kernel_work(cls, ns[J], C, cnt, w)
+            b, f = kernel_work(cls, ns[J], C, cnt, w, S)
         if cls == dom:
             if b is not None:
                 bytes_sum += b
@@ -471,6 +479,110 @@ def bench_batched(args):
     return 0
 
 
+ELAST_ORACLE = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from paper_2402_12833_gb300 import problems as pb
+from oracle import mg as omg, mpcg as ompcg
+prob = pb.elasticity_cantilever({nodes})
+t0 = time.perf_counter()
+H = omg.Hierarchy(3, None, prob.stencil, prob.levels, nodes=prob.nodes, faces=prob.faces, ncomp=3)
+t1 = time.perf_counter()
+res = ompcg.mpcg(H.A[-1], prob.b, H.mg_columns, m={m}, rtol={rtol}, maxit={maxit})
+t2 = time.perf_counter()
+print(json.dumps({{"setup_s": t1 - t0, "solve_s": t2 - t1, "iters": res.iters, "n": prob.n}}))
+"""
+
+
+def bench_elasticity(args):
+    """3D linear elasticity (Q1 hexahedra, E = 1, nu = 0.3) on the unit cube
+    with 65^3 nodes, clamped at x = 0, body force (0, 0, -1): 811,200
+    unknowns, 5 grids (coarsest 300 unknowns), 3 x 3 block Jacobi nu = 2,
+    MPCG m = 5, rtol 1e-8; mixed precision (headline of this line) and FP64."""
+    import torch
+    from paper_2402_12833_gb300 import build as _build
+    from paper_2402_12833_gb300 import mpcg as M
+    from paper_2402_12833_gb300 import problems as pb
+    nodes = 65
+    oracle_proc = None
+    if not args.no_cpu_baseline:
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        code = ELAST_ORACLE.format(root=ROOT, nodes=nodes, m=M_WINDOW, rtol=RTOL, maxit=MAXIT)
+        oracle_proc = subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                       text=True, env=env)
+    _build.build()
+    M.load()
+    prob = pb.elasticity_cantilever(nodes)
+    n = prob.n
+    stream = torch.cuda.current_stream()
+    st = torch.from_numpy(prob.stencil).cuda()
+    b = torch.from_numpy(prob.b).cuda()
+    x = torch.zeros_like(b)
+    peaks = load_peaks()
+    out = {}
+    clocks = None
+    for key, prec, w in (("fp64", M.MPCG_FP64, 8), ("mixed", M.MPCG_MIXED, 4)):
+        H = M.Hierarchy(st, 3, nodes, prob.levels, dofs_per_node=3, faces=prob.faces, m=M_WINDOW, precision=prec,
+                        stream=stream.cuda_stream)
+        ns = [M.mg_level_size(H.h, j) for j in range(prob.levels)]
+        res = {}
+
+        def step():
+            x.zero_()
+            res["st"], res["k"], _, _ = H.solve(b, x, rtol=RTOL, maxit=MAXIT, histories=False)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if key == "mixed":
+            clk = Clocks(0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if key == "mixed":
+            clocks = clk.stop()
+        ms = e0.elapsed_time(e1) / args.steps
+        launches = M.mg_last_launches(H.h)
+        Ax = torch.empty_like(b)
+        M.mg_apply_operator(H.h, prob.levels - 1, x, Ax, 1)
+        true_res = float(torch.linalg.norm(b - Ax) / torch.linalg.norm(b))
+        x.zero_()
+        _, _, classes, trace = M.mpcg_solve_profiled(H.h, b, x, RTOL, MAXIT)
+        dom, rl, share, tot = roofline(trace, ns, prob.levels, M_WINDOW, w, peaks, FP64_PEAK_TFLOPS, S=81,
+                                       vector=True)
+        out[key] = {"value": n / (ms * 1e-3), "ms_per_step": ms, "iterations": int(res["k"]),
+                    "status": int(res["st"]), "true_rel_residual": true_res, "launches_per_step": launches,
+                    "roofline": rl, "kernel_ms_per_solve": {c: round(v, 4) for c, v in tot.items()}}
+        H.close()
+    cpu = None
+    if oracle_proc is not None:
+        o_out, o_err = oracle_proc.communicate(timeout=1800)
+        if oracle_proc.returncode == 0:
+            o = json.loads(o_out.strip().splitlines()[-1])
+            cpu = {"value": o["n"] / o["solve_s"], "unit": "DOFs/s", "cores": 1, "kind": "oracle",
+                   "sample": f"one full FP64 solve of the same workload ({o['iters']} iterations, "
+                             f"{o['solve_s']:.1f} s; hierarchy setup {o['setup_s']:.1f} s excluded)"}
+        else:
+            cpu = {"value": None, "kind": "oracle", "sample": "failed: " + o_err[-300:]}
+    mx = out["mixed"]
+    print(json.dumps({
+        "metric": METRIC, "workload": "elasticity", "value": mx["value"], "unit": "DOFs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mx["ms_per_step"], "higher_is_better": True,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "3D linear elasticity, Q1 hexahedra, E=1, nu=0.3, unit cube 65^3 nodes clamped at "
+                               "x=0, body force (0,0,-1): 811,200 unknowns, 5 grids (300-unknown coarsest, "
+                               "Cholesky), 3x3 block Jacobi nu=2 w=2/3, MPCG m=5, rtol 1e-8",
+                   "l2": "working set ~0.7 GB per solve > 129 MB L2 (no flush needed)"},
+        "iterations": mx["iterations"], "true_rel_residual": mx["true_rel_residual"], "roofline": mx["roofline"],
+        "fp64": out["fp64"], "kernel_ms_per_solve": mx["kernel_ms_per_solve"],
+        "gpu_launches": mx["launches_per_step"] * args.steps, "clocks": clocks, "peaks": peaks,
+        "cpu_baseline": cpu}))
+    return 0
+
+
 def bench_learned(args):
     """2D high-contrast diffusion, 1025^2 nodes, 9 grids, f = 1, kappa seed 3:
     the mixed-precision solver without and with the learned column; the
@@ -541,8 +653,8 @@ def bench_learned(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["poisson3d", "batched", "learned"], default="poisson3d",
-                    help="poisson3d: the headline line; batched / learned: the batch and learned-column workloads")
+    ap.add_argument("--workload", choices=["poisson3d", "batched", "learned", "elasticity"], default="poisson3d",
+                    help="poisson3d: the headline line; batched / learned / elasticity: the other workloads")
     ap.add_argument("--epochs", type=int, default=20, help="training epochs of the learned workload")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
@@ -561,6 +673,8 @@ def main():
         return bench_reference(args)
     if args.workload == "batched":
         return bench_batched(args)
+    if args.workload == "elasticity":
+        return bench_elasticity(args)
     if args.workload == "learned":
         return bench_learned(args)
     return bench_ours(args)
