@@ -89,8 +89,11 @@ class Hierarchy:
         unknowns D is the block diagonal of the node blocks."""
         s = np.zeros_like(g)
         for _ in range(self.nu):
-            s = s + self.omega * (self.Dinv[j] @ (g - self.A[j] @ s) if self.ncomp > 1
-                                  else self.Dinv[j] * (g - self.A[j] @ s))
+            # M^{-1} = omega D^{-1} of Eq. 2, formed first, then applied
+            if self.ncomp > 1:
+                s = s + (self.omega * self.Dinv[j]) @ (g - self.A[j] @ s)
+            else:
+                s = s + self.omega * self.Dinv[j] * (g - self.A[j] @ s)
         return s
 
     def coarse_solve(self, g: np.ndarray) -> np.ndarray:
