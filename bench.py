@@ -521,9 +521,12 @@ def bench_elasticity(args):
     peaks = load_peaks()
     out = {}
     clocks = None
-    for key, prec, w in (("fp64", M.MPCG_FP64, 8), ("mixed", M.MPCG_MIXED, 4)):
+    legs = (("fp64", M.MPCG_FP64, 8), ("mixed", M.MPCG_MIXED, 4))
+    if args.only:
+        legs = tuple(l for l in legs if l[0] == args.only)
+    for key, prec, w in legs:
         H = M.Hierarchy(st, 3, nodes, prob.levels, dofs_per_node=3, faces=prob.faces, m=M_WINDOW, precision=prec,
-                        stream=stream.cuda_stream)
+                        stream=stream.cuda_stream, use_graph=0 if args.direct else 1)
         ns = [M.mg_level_size(H.h, j) for j in range(prob.levels)]
         res = {}
 
@@ -549,6 +552,11 @@ def bench_elasticity(args):
         Ax = torch.empty_like(b)
         M.mg_apply_operator(H.h, prob.levels - 1, x, Ax, 1)
         true_res = float(torch.linalg.norm(b - Ax) / torch.linalg.norm(b))
+        if args.only:
+            print(json.dumps({"workload": "elasticity", "only": key, "value": n / (ms * 1e-3), "ms_per_step": ms,
+                              "iterations": int(res["k"]), "true_rel_residual": true_res}))
+            H.close()
+            continue
         x.zero_()
         _, _, classes, trace = M.mpcg_solve_profiled(H.h, b, x, RTOL, MAXIT)
         dom, rl, share, tot = roofline(trace, ns, prob.levels, M_WINDOW, w, peaks, FP64_PEAK_TFLOPS, S=81,
@@ -557,6 +565,10 @@ def bench_elasticity(args):
                     "status": int(res["st"]), "true_rel_residual": true_res, "launches_per_step": launches,
                     "roofline": rl, "kernel_ms_per_solve": {c: round(v, 4) for c, v in tot.items()}}
         H.close()
+    if args.only:
+        if oracle_proc is not None:
+            oracle_proc.kill()
+        return 0
     cpu = None
     if oracle_proc is not None:
         o_out, o_err = oracle_proc.communicate(timeout=1800)

@@ -475,28 +475,33 @@ __global__ void k_coarse_inverse(const double* __restrict__ L, const double* __r
   }
 }
 
-// out = A0^{-1} r (the exact coarsest solve S_0), one row per thread.
+// out = A0^{-1} r (the exact coarsest solve S_0): one warp per row, lanes
+// striding over the (contiguous) row, a fixed shuffle tree for the sum.
+// Every block stages the whole right-hand side in shared memory.
+constexpr int kCoarseRowsPerBlock = 8;
+
 template <typename T>
-__global__ void k_coarse_solve(GridDesc g, const double* __restrict__ inv, const T* __restrict__ r,
-                               T* __restrict__ out, const DevState* state) {
-  const int pb = blockIdx.x;
+__global__ void __launch_bounds__(32 * kCoarseRowsPerBlock) k_coarse_solve(GridDesc g, const double* __restrict__ inv,
+                                                                           const T* __restrict__ r,
+                                                                           T* __restrict__ out, const DevState* state) {
+  const int pb = blockIdx.y;
   if (state && state[pb].done) return;
   extern __shared__ double y[];
   const int n = (int)g.n;
   inv += (long long)pb * n * n;
   r += (long long)pb * g.len;
   out += (long long)pb * g.len;
-  auto padded = [&](int i) { return padded_index(g, i); };
-  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = (double)r[padded(i)];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = (double)r[padded_index(g, i)];
   __syncthreads();
-  // the computed inverse is exactly symmetric (entry (a, b) and (b, a) sum
-  // the same products in the same order), so row i is read as column i:
-  // consecutive threads read consecutive entries
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double s = 0.0;
-    for (int j = 0; j < n; ++j) s = fma(inv[(long long)j * n + i], y[j], s);
-    out[padded(i)] = (T)s;
-  }
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kCoarseRowsPerBlock + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const double* row = inv + (long long)i * n;
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) s = fma(row[j], y[j], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[padded_index(g, i)] = (T)s;
 }
 
 // out[b * nv + v] = sum of problem b's partials of value v.
@@ -585,7 +590,8 @@ void launch_coarse_inverse(const double* L, const double* rdiag, double* X, doub
 template <typename T>
 void launch_coarse_solve(const GridDesc& g, const double* inv, const T* r, T* out, const DevState* state,
                          cudaStream_t s) {
-  k_coarse_solve<T><<<g.nb, g.n > 128 ? 512 : 128, (size_t)g.n * sizeof(double), s>>>(g, inv, r, out, state);
+  const dim3 grid((unsigned)((g.n + kCoarseRowsPerBlock - 1) / kCoarseRowsPerBlock), g.nb);
+  k_coarse_solve<T><<<grid, 32 * kCoarseRowsPerBlock, (size_t)g.n * sizeof(double), s>>>(g, inv, r, out, state);
 }
 template void launch_coarse_solve<double>(const GridDesc&, const double*, const double*, double*, const DevState*,
                                           cudaStream_t);
