@@ -481,6 +481,11 @@ __device__ __forceinline__ void vstencil_group(const T* __restrict__ st, long lo
   }
 }
 
+// Block SpMM of a vector operator: one thread per (output component a, group
+// of W x-points), so that the C columns' accumulators stay few (the
+// three-component accumulators of vstencil_group would cap occupancy at one
+// block per SM for C = 5).  Consecutive threads take consecutive groups of
+// the same component.
 template <typename T, int C, bool ZAZ>
 __global__ void __launch_bounds__(kBlock) k_vspmm(GridDesc g, const T* __restrict__ st, const T* __restrict__ X,
                                                   T* __restrict__ Y, double* zaz, const DevState* state) {
@@ -488,34 +493,54 @@ __global__ void __launch_bounds__(kBlock) k_vspmm(GridDesc g, const T* __restric
   if (state && state[pb].done) return;
   constexpr int W = Vec<T>::W;
   const long long bo = (long long)pb * g.len;
+  const long long cs = g.cstride;
   T zacc[ZAZ ? C : 1];
 #pragma unroll
   for (int c = 0; c < (ZAZ ? C : 1); ++c) zacc[c] = 0;
-  const long long ngroups = g.cstride / W;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
-       q += (long long)gridDim.x * blockDim.x) {
-    const long long idx0 = bo + g.G + q * W;
-    T acc[3][C][W];
+  const long long ngroups = cs / W;
+  for (long long item = blockIdx.x * (long long)blockDim.x + threadIdx.x; item < 3 * ngroups;
+       item += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(item / ngroups);
+    const long long idx0 = bo + g.G + (item - a * ngroups) * W;
+    T acc[C][W];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < C; ++c)
 #pragma unroll
-      for (int c = 0; c < C; ++c)
+      for (int w = 0; w < W; ++w) acc[c][w] = 0;
+#pragma unroll 1
+    for (int k = 0; k < 9; ++k) {
+      const long long ro = row_offset<3>(k, g.px, g.pxy);
 #pragma unroll
-        for (int w = 0; w < W; ++w) acc[a][c][w] = 0;
-    vstencil_group<T, C>(st, g.cp, X, idx0, g.cstride, g.px, g.pxy, acc);
+      for (int b = 0; b < 3; ++b) {
+        const T* sp = st + (long long)(b * 27 + 3 * k) * g.cp + idx0 + a * cs;
+        T a0[W], a1[W], a2[W];
+        Vec<T>::load(sp, a0);
+        Vec<T>::load(sp + g.cp, a1);
+        Vec<T>::load(sp + 2 * g.cp, a2);
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < C; ++c) {
+          T e[W + 2];
+          load_row<T>(X + (long long)c * g.cp + idx0 + b * cs + ro, e);
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const long long o = (long long)c * g.cp + idx0 + a * g.cstride;
-        Vec<T>::store(Y + o, acc[a][c]);
-        if (ZAZ) {
-          T xc[W];
-          Vec<T>::load_keep(X + o, xc);
-#pragma unroll
-          for (int w = 0; w < W; ++w) zacc[c] = fma(xc[w], acc[a][c][w], zacc[c]);
+          for (int w = 0; w < W; ++w) {
+            acc[c][w] = fma(a0[w], e[w], acc[c][w]);
+            acc[c][w] = fma(a1[w], e[w + 1], acc[c][w]);
+            acc[c][w] = fma(a2[w], e[w + 2], acc[c][w]);
+          }
         }
       }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const long long o = (long long)c * g.cp + idx0 + a * cs;
+      Vec<T>::store(Y + o, acc[c]);
+      if (ZAZ) {
+        T xc[W];
+        Vec<T>::load_keep(X + o, xc);
+#pragma unroll
+        for (int w = 0; w < W; ++w) zacc[c] = fma(xc[w], acc[c][w], zacc[c]);
+      }
+    }
   }
   if (ZAZ) block_sum_store<T, ZAZ ? C : 1>(zacc, zaz + (long long)pb * C * gridDim.x, gridDim.x, blockIdx.x);
 }
