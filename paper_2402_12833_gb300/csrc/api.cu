@@ -306,16 +306,14 @@ void enqueue_smooth(mg_hierarchy* h, Solver<T>& S, int j, const T* rr, T* out, c
   const T* di = dinv_of<T>(L);
   const int nu = h->opt.nu;
   if (L.g.ncomp > 1) {
-    // block Jacobi: the first sweep from zero, then nu - 1 further sweeps
-    T* a = S.tmp[j];
-    T* b = S.tmp2[j];
-    LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, nullptr, nu == 1 ? out : a, 0, state, s));
+    // block Jacobi: s = D^-1 r, then nu - 1 sweeps t = r - A s, s += D^-1 t
+    // (the update is pointwise, so it runs in place)
+    T* sv = nu == 1 ? out : S.tmp[j];
+    T* t = S.tmp2[j];
+    LAUNCH(h, K_JACOBI, s, launch_vblock<T>(L.g, di, rr, nullptr, sv, state, s));
     for (int k = 2; k <= nu; ++k) {
-      T* o = k == nu ? out : b;
-      LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, a, o, 2, state, s));
-      T* t = a;
-      a = b;
-      b = t;
+      LAUNCH(h, K_JACOBI, s, launch_vres<T>(L.g, st, rr, sv, t, state, s));
+      LAUNCH(h, K_JACOBI, s, launch_vblock<T>(L.g, di, t, sv, k == nu ? out : sv, state, s));
     }
     return;
   }

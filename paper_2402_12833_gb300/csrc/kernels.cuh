@@ -53,6 +53,14 @@ void launch_restrict(const GridDesc& gf, const GridDesc& gc, const T* rf, T* rc,
 template <typename T>
 void launch_jacobi(const GridDesc& g, const T* st, const T* dinv, const T* r, const T* sin, T* out,
                    int mode, const DevState* state, cudaStream_t s);
+// Vector operators (3 unknowns per node): t = r - A x (one sweep's residual)
+// and the block-Jacobi update out = (sin or 0) + dinv t (in place allowed).
+template <typename T>
+void launch_vres(const GridDesc& g, const T* st, const T* r, const T* x, T* t, const DevState* state,
+                 cudaStream_t s);
+template <typename T>
+void launch_vblock(const GridDesc& g, const T* dinv, const T* t, const T* sin, T* out, const DevState* state,
+                   cudaStream_t s);
 // fine[c] = P coarse[c] for c < ncols (column stride: grid len)
 template <typename T>
 void launch_prolong(const GridDesc& gc, const GridDesc& gf, const T* coarse, T* fine, int ncols,

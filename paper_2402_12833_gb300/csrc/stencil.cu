@@ -443,49 +443,14 @@ __global__ void k_convert_f32(const double* __restrict__ src, float* __restrict_
 // ---------------------------------------------------------------------------
 // Vector unknowns (3D elasticity, three components per node).  Plane
 // b * 27 + s at the row of component a holds the coupling of unknown
-// (node, a) to (node + offset_s, b).  One thread takes W consecutive x-points
-// of a node row for all three components, so each neighbour row of X is
-// loaded once for the three outputs; the 81 planes of a row are read once.
-
-// acc[a][c][w] += (A X_c)_a at the group starting at idx0 (component 0).
-template <typename T, int C>
-__device__ __forceinline__ void vstencil_group(const T* __restrict__ st, long long pitch, const T* __restrict__ X,
-                                               long long idx0, long long cs, long long px, long long pxy,
-                                               T (&acc)[3][C][Vec<T>::W]) {
-  constexpr int W = Vec<T>::W;
-#pragma unroll 1
-  for (int k = 0; k < 9; ++k) {
-    const long long ro = row_offset<3>(k, px, pxy);
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      T e[C][W + 2];
-#pragma unroll
-      for (int c = 0; c < C; ++c) load_row<T>(X + (long long)c * pitch + idx0 + b * cs + ro, e[c]);
-      const T* sp = st + (long long)(b * 27 + 3 * k) * pitch + idx0;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        T a0[W], a1[W], a2[W];
-        Vec<T>::load(sp + a * cs, a0);
-        Vec<T>::load(sp + pitch + a * cs, a1);
-        Vec<T>::load(sp + 2 * pitch + a * cs, a2);
-#pragma unroll
-        for (int c = 0; c < C; ++c)
-#pragma unroll
-          for (int w = 0; w < W; ++w) {
-            acc[a][c][w] = fma(a0[w], e[c][w], acc[a][c][w]);
-            acc[a][c][w] = fma(a1[w], e[c][w + 1], acc[a][c][w]);
-            acc[a][c][w] = fma(a2[w], e[c][w + 2], acc[a][c][w]);
-          }
-      }
-    }
-  }
-}
+// (node, a) to (node + offset_s, b); component b of a node sits cstride
+// after component 0, so the 81 couplings of a row are 27 neighbours in each
+// of three component boxes.
 
 // Block SpMM of a vector operator: one thread per (output component a, group
-// of W x-points), so that the C columns' accumulators stay few (the
-// three-component accumulators of vstencil_group would cap occupancy at one
-// block per SM for C = 5).  Consecutive threads take consecutive groups of
-// the same component.
+// of W x-points), so that only the C columns' accumulators are live (all
+// three components per thread would cap occupancy at one block per SM for
+// C = 5).  Consecutive threads take consecutive groups of the same component.
 template <typename T, int C, bool ZAZ>
 __global__ void __launch_bounds__(kBlock) k_vspmm(GridDesc g, const T* __restrict__ st, const T* __restrict__ X,
                                                   T* __restrict__ Y, double* zaz, const DevState* state) {
@@ -545,46 +510,68 @@ __global__ void __launch_bounds__(kBlock) k_vspmm(GridDesc g, const T* __restric
   if (ZAZ) block_sum_store<T, ZAZ ? C : 1>(zacc, zaz + (long long)pb * C * gridDim.x, gridDim.x, blockIdx.x);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_vresidual(GridDesc g, const T* __restrict__ st, const T* __restrict__ b,
-                                                      const T* __restrict__ xv, T* __restrict__ r, double* part) {
-  constexpr int W = Vec<T>::W;
+// r = b - A x for a vector operator, one thread per (component, group), the
+// whole 81-coefficient row unrolled so that a thread's loads are in flight
+// together (the coarse grids of the hierarchy are latency-bound).  NORMS:
+// per-block partial sums of |r|^2 and |b|^2 (grid-stride, for the residual
+// of the refinement); otherwise one group per thread (the smoother).
+template <typename T, bool NORMS>
+__global__ void __launch_bounds__(kBlock, 3) k_vres(GridDesc g, const T* __restrict__ st, const T* __restrict__ b,
+                                                    const T* __restrict__ xv, T* __restrict__ r, double* part,
+                                                    const DevState* state) {
   const int pb = blockIdx.y;
+  if (state && state[pb].done) return;
+  constexpr int W = Vec<T>::W;
   const long long bo = (long long)pb * g.len;
+  const long long cs = g.cstride;
+  const long long ngroups = cs / W;
   T sums[2] = {0, 0};
-  const long long ngroups = g.cstride / W;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
-       q += (long long)gridDim.x * blockDim.x) {
-    const long long idx0 = bo + g.G + q * W;
-    T acc[3][1][W];
+  for (long long item = blockIdx.x * (long long)blockDim.x + threadIdx.x; item < 3 * ngroups;
+       item += NORMS ? (long long)gridDim.x * blockDim.x : 3 * ngroups) {
+    const int a = (int)(item / ngroups);
+    const long long idx0 = bo + g.G + (item - a * ngroups) * W;
+    T acc[W];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int w = 0; w < W; ++w) acc[w] = 0;
 #pragma unroll
-      for (int w = 0; w < W; ++w) acc[a][0][w] = 0;
-    vstencil_group<T, 1>(st, g.cp, xv, idx0, g.cstride, g.px, g.pxy, acc);
+    for (int k = 0; k < 9; ++k) {
+      const long long ro = row_offset<3>(k, g.px, g.pxy);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      T bv[W], rv[W];
-      Vec<T>::load(b + idx0 + a * g.cstride, bv);
+      for (int bb = 0; bb < 3; ++bb) {
+        const T* sp = st + (long long)(bb * 27 + 3 * k) * g.cp + idx0 + a * cs;
+        T a0[W], a1[W], a2[W], e[W + 2];
+        Vec<T>::load(sp, a0);
+        Vec<T>::load(sp + g.cp, a1);
+        Vec<T>::load(sp + 2 * g.cp, a2);
+        load_row<T>(xv + idx0 + bb * cs + ro, e);
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        rv[w] = bv[w] - acc[a][0][w];
+        for (int w = 0; w < W; ++w) {
+          acc[w] = fma(a0[w], e[w], acc[w]);
+          acc[w] = fma(a1[w], e[w + 1], acc[w]);
+          acc[w] = fma(a2[w], e[w + 2], acc[w]);
+        }
+      }
+    }
+    T bv[W], rv[W];
+    Vec<T>::load(b + idx0 + a * cs, bv);
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      rv[w] = bv[w] - acc[w];
+      if (NORMS) {
         sums[0] = fma(rv[w], rv[w], sums[0]);
         sums[1] = fma(bv[w], bv[w], sums[1]);
       }
-      Vec<T>::store(r + idx0 + a * g.cstride, rv);
     }
+    Vec<T>::store(r + idx0 + a * cs, rv);
   }
-  block_sum_store<T, 2>(sums, part + (long long)pb * 2 * gridDim.x, gridDim.x, blockIdx.x);
+  if (NORMS) block_sum_store<T, 2>(sums, part + (long long)pb * 2 * gridDim.x, gridDim.x, blockIdx.x);
 }
 
-// Block Jacobi (Eq. 2 with M = D / omega, D the 3 x 3 node blocks), c_0 = 0:
-//   mode 0: out = dinv r                      (one sweep)
-//   mode 2: out = sin + dinv (r - A sin)      (a further sweep)
+// Block-Jacobi update (Eq. 2 with M = D / omega, D the 3 x 3 node blocks):
+// out = (sin or 0) + dinv t, pointwise per node (in place is allowed).
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_vjacobi(GridDesc g, const T* __restrict__ st, const T* __restrict__ dinv,
-                                                    const T* __restrict__ r, const T* __restrict__ sin,
-                                                    T* __restrict__ out, int mode, const DevState* state) {
+__global__ void __launch_bounds__(kBlock) k_vblock(GridDesc g, const T* __restrict__ dinv, const T* t,
+                                                   const T* sin, T* out, const DevState* state) {
   const int pb = blockIdx.y;
   if (state && state[pb].done) return;
   constexpr int W = Vec<T>::W;
@@ -592,25 +579,13 @@ __global__ void __launch_bounds__(kBlock) k_vjacobi(GridDesc g, const T* __restr
   if (q >= g.cstride / W) return;
   const long long idx0 = (long long)pb * g.len + g.G + q * W;
   const long long cs = g.cstride;
-  T t[3][W];
+  T tv[3][W];
 #pragma unroll
-  for (int b = 0; b < 3; ++b) Vec<T>::load_keep(r + idx0 + b * cs, t[b]);
-  if (mode == 2) {
-    T acc[3][1][W];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int w = 0; w < W; ++w) acc[a][0][w] = 0;
-    vstencil_group<T, 1>(st, g.cp, sin, idx0, cs, g.px, g.pxy, acc);
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int w = 0; w < W; ++w) t[b][w] -= acc[b][0][w];
-  }
+  for (int b = 0; b < 3; ++b) Vec<T>::load_keep(t + idx0 + b * cs, tv[b]);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     T o[W];
-    if (mode == 2) Vec<T>::load_keep(sin + idx0 + a * cs, o);
+    if (sin) Vec<T>::load_keep(sin + idx0 + a * cs, o);
     else {
 #pragma unroll
       for (int w = 0; w < W; ++w) o[w] = 0;
@@ -620,7 +595,7 @@ __global__ void __launch_bounds__(kBlock) k_vjacobi(GridDesc g, const T* __restr
       T d[W];
       Vec<T>::load_keep(dinv + (long long)b * g.cp + idx0 + a * cs, d);
 #pragma unroll
-      for (int w = 0; w < W; ++w) o[w] = fma(d[w], t[b][w], o[w]);
+      for (int w = 0; w < W; ++w) o[w] = fma(d[w], tv[b][w], o[w]);
     }
     Vec<T>::store(out + idx0 + a * cs, o);
   }
@@ -699,7 +674,7 @@ template void launch_spmm<float>(const GridDesc&, const float*, const float*, fl
 template <typename T>
 void launch_residual(const GridDesc& g, const T* st, const T* b, const T* x, T* r, double* part, cudaStream_t s) {
   const dim3 grid(stream_blocks(g), g.nb);
-  if (g.ncomp == 3) k_vresidual<T><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part);
+  if (g.ncomp == 3) k_vres<T, true><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part, nullptr);
   else if (g.dim == 3) k_residual<T, 3><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part);
   else k_residual<T, 2><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part);
 }
@@ -723,15 +698,32 @@ template void launch_restrict<float>(const GridDesc&, const GridDesc&, const flo
 template <typename T>
 void launch_jacobi(const GridDesc& g, const T* st, const T* dinv, const T* r, const T* sin, T* out, int mode,
                    const DevState* state, cudaStream_t s) {
-  if (g.ncomp == 3) {   // block Jacobi: modes 0 and 2 only
-    k_vjacobi<T><<<dim3(blocks_for(g.cstride / vw<T>()), g.nb), kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode,
-                                                                              state);
-    return;
-  }
+  if (g.ncomp != 1) return;   // vector grids smooth with launch_vres / launch_vblock
   const dim3 grid(blocks_for(g.npts / vw<T>()), g.nb);
   if (g.dim == 3) k_jacobi<T, 3><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
   else k_jacobi<T, 2><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
 }
+template <typename T>
+void launch_vres(const GridDesc& g, const T* st, const T* r, const T* x, T* t, const DevState* state,
+                 cudaStream_t s) {
+  k_vres<T, false><<<dim3(blocks_for(3 * (g.cstride / vw<T>())), g.nb), kBlock, 0, s>>>(g, st, r, x, t, nullptr,
+                                                                                        state);
+}
+template void launch_vres<double>(const GridDesc&, const double*, const double*, const double*, double*,
+                                  const DevState*, cudaStream_t);
+template void launch_vres<float>(const GridDesc&, const float*, const float*, const float*, float*,
+                                 const DevState*, cudaStream_t);
+
+template <typename T>
+void launch_vblock(const GridDesc& g, const T* dinv, const T* t, const T* sin, T* out, const DevState* state,
+                   cudaStream_t s) {
+  k_vblock<T><<<dim3(blocks_for(g.cstride / vw<T>()), g.nb), kBlock, 0, s>>>(g, dinv, t, sin, out, state);
+}
+template void launch_vblock<double>(const GridDesc&, const double*, const double*, const double*, double*,
+                                    const DevState*, cudaStream_t);
+template void launch_vblock<float>(const GridDesc&, const float*, const float*, const float*, float*,
+                                   const DevState*, cudaStream_t);
+
 template void launch_jacobi<double>(const GridDesc&, const double*, const double*, const double*, const double*,
                                     double*, int, const DevState*, cudaStream_t);
 template void launch_jacobi<float>(const GridDesc&, const float*, const float*, const float*, const float*, float*,
