@@ -603,7 +603,7 @@ mpcg_status mpcg_default_options(mpcg_options* opt) {
   opt->pinv_tau = 1e-12;
   opt->drop_delta = 1e-10;
   opt->precision = MPCG_FP64;
-  opt->inner_rtol = 1e-4;
+  opt->inner_rtol = 3e-3;
   opt->inner_pinv_tau = 1e-6;
   opt->inner_drop_delta = 1e-5;
   opt->max_outer = 20;
