@@ -177,6 +177,31 @@ def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops, S=27, vector=False
     return dom, out, share, tot
 
 
+def measured_traffic(key: str):
+    """DRAM bytes per launch of a kernel class, from the ncu summaries under
+    profiles/ (lines "traffic: key=<leg>:<class> bytes_per_launch=<B>
+    source=<file> sha256=<hash>").  None unless the kernel's source file is
+    unchanged since the counters were taken."""
+    import glob
+    import hashlib
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            for line in f:
+                if not line.startswith("traffic: "):
+                    continue
+                kv = dict(t.split("=", 1) for t in line.split()[1:])
+                if kv.get("key") != key:
+                    continue
+                src = os.path.join(ROOT, "paper_2402_12833_gb300", "csrc", kv["source"])
+                if not os.path.exists(src):
+                    return None
+                with open(src, "rb") as g:
+                    if hashlib.sha256(g.read()).hexdigest() != kv["sha256"]:
+                        return None
+                return float(kv["bytes_per_launch"])
+    return None
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -365,6 +390,8 @@ def bench_ours(args):
         _, k, classes, trace = M.mpcg_solve_profiled(H[key].h, b, x, RTOL, MAXIT)
         dom, rl, share, tot = roofline(trace, level_dofs(NODES, DIM, prob.levels), prob.levels, M_WINDOW, w, peaks,
                                        FP64_PEAK_TFLOPS)
+        if rl is not None:
+            rl["traffic"] = measured_traffic(f"poisson3d_{key}:{dom}")
         prof[key] = {"roofline": rl, "class_ms": {c: round(v, 4) for c, v in tot.items()}}
     # mixed vs fp64 solution difference
     x.zero_()
@@ -567,11 +594,13 @@ def bench_elasticity(args):
         if key == "mixed":
             clk = Clocks(0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed_step")
         e0.record(stream)
         for _ in range(args.steps):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         if key == "mixed":
             clocks = clk.stop()
         ms = e0.elapsed_time(e1) / args.steps
@@ -588,6 +617,8 @@ def bench_elasticity(args):
         _, _, classes, trace = M.mpcg_solve_profiled(H.h, b, x, RTOL, MAXIT)
         dom, rl, share, tot = roofline(trace, ns, prob.levels, M_WINDOW, w, peaks, FP64_PEAK_TFLOPS, S=81,
                                        vector=True)
+        if rl is not None:
+            rl["traffic"] = measured_traffic(f"elasticity_{key}:{dom}")
         out[key] = {"value": n / (ms * 1e-3), "ms_per_step": ms, "iterations": int(res["k"]),
                     "status": int(res["st"]), "true_rel_residual": true_res, "launches_per_step": launches,
                     "roofline": rl, "kernel_ms_per_solve": {c: round(v, 4) for c, v in tot.items()}}
