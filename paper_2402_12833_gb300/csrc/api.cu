@@ -222,6 +222,7 @@ struct mg_hierarchy {
   float* net_wq = nullptr;     // bfloat16-valued weights
   float* net_c = nullptr;      // coefficient channel on the fine grid
   NetActs net_acts = {};       // inference activations
+  int* net_err = nullptr;      // set by the tensor-core inference kernel on a timed-out wait
   Alloc net_mem;
 };
 
@@ -405,9 +406,8 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
   enqueue_mg<T>(h, S, S.r, S.Z, S.state, s);
   if (h->net_on) {
     LAUNCH(h, K_NET, s,
-           launch_net_forward<T>(L.g, 1, S.r, L.g.len, h->net_c, h->net_wq, S.state, h->net_acts, nullptr,
-                                 S.Z + (size_t)(C - 1) * L.g.len, s));
-    h->prof.extra(4);
+           launch_net_infer<T>(L.g, 1, S.r, L.g.len, h->net_c, h->net_wq, S.state, nullptr,
+                               S.Z + (size_t)(C - 1) * L.g.len, h->net_err, s));
   }
   LAUNCH(h, K_SPMM, s, launch_spmm<T>(L.g, st_of<T>(L), S.Z, S.AZ, C, S.part_zaz, S.state, s));
   LAUNCH(h, K_GRAM, s, launch_gram_window<T>(L.g, S.win, S.Z, C, S.m, S.part_W, S.state, s));
@@ -971,6 +971,15 @@ mpcg_status mpcg_solve(mg_hierarchy* h, const double* b, double* x, double rtol,
                        : solve_fp64(h, bd, xd, rtol, maxit, iters_out, res_hist, alpha_hist);
   h->prof.flush();
   h->last_launches = h->prof.live;
+  if (h->net_on && h->net_err) {
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, h->net_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (err) {
+      set_err("learned column: a tensor-core wait timed out");
+      st = MPCG_ERR_TIMEOUT;
+    }
+  }
   if (!xdev && (st >= 0 || st == MPCG_ERR_BREAKDOWN)) {
     CK(cudaMemcpyAsync(x, xd, nb, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1098,6 +1107,8 @@ mpcg_status net_prepare(mg_hierarchy* h) {
   CKS(h->net_mem.get(&h->net_acts.a1, (size_t)L.g.len * kNetC1, s));
   CKS(h->net_mem.get(&h->net_acts.a2, (size_t)L.g.len * kNetW, s));
   CKS(h->net_mem.get(&h->net_acts.a3, (size_t)L.g.len * kNetW, s));
+  CKS(h->net_mem.get(&h->net_err, 1, s));
+  net_infer_prepare_attributes();
   launch_net_coef(L.g, L.dinv64, h->opt.omega, h->net_c, part, s);
   CK(cudaGetLastError());
   return MPCG_OK;
@@ -1180,19 +1191,19 @@ mpcg_status mg_learned_forward(mg_hierarchy* h, const float* rhat_dev, float* y_
   const GridDesc& g = h->lev[h->levels - 1].g;
   Alloc tmp;
   float *r = nullptr, *y = nullptr;
-  NetActs a;
   mpcg_status st = MPCG_OK;
-  if ((st = tmp.get(&r, (size_t)nimg * g.len, s)) == MPCG_OK && (st = tmp.get(&y, (size_t)nimg * g.len, s)) == MPCG_OK &&
-      (st = tmp.get(&a.a0, (size_t)nimg * g.len * kNetIn, s)) == MPCG_OK &&
-      (st = tmp.get(&a.a1, (size_t)nimg * g.len * kNetC1, s)) == MPCG_OK &&
-      (st = tmp.get(&a.a2, (size_t)nimg * g.len * kNetW, s)) == MPCG_OK &&
-      (st = tmp.get(&a.a3, (size_t)nimg * g.len * kNetW, s)) == MPCG_OK) {
+  if ((st = tmp.get(&r, (size_t)nimg * g.len, s)) == MPCG_OK && (st = tmp.get(&y, (size_t)nimg * g.len, s)) == MPCG_OK) {
     launch_pack<float, float>(g, rhat_dev, g.n, r, nimg, s);
-    launch_net_forward<float>(g, nimg, r, g.len, h->net_c, h->net_wq, nullptr, a, y, (float*)nullptr, s);
+    launch_net_infer<float>(g, nimg, r, g.len, h->net_c, h->net_wq, nullptr, y, (float*)nullptr, h->net_err, s);
     launch_unpack<float, float>(g, y, y_dev, g.n, nimg, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    int err = 0;
+    if (cudaMemcpyAsync(&err, h->net_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
       set_err("learned forward failed");
       st = MPCG_ERR_CUDA;
+    } else if (err) {
+      set_err("learned forward: a tensor-core wait timed out");
+      st = MPCG_ERR_TIMEOUT;
     }
   }
   tmp.release();

@@ -1,0 +1,282 @@
+// Learned-column inference on the fifth-generation tensor cores: the whole
+// four-layer network (3x3 convolutions 2 -> 16 -> 16 -> 16 -> 1, ReLU after
+// the first three, zero padding, bfloat16 weights and activations, FP32
+// accumulation) fused in one kernel per output tile.
+//
+// Each layer is an implicit GEMM: for one row of 128 tile pixels (M = 128)
+// and one tap (dy, dx) of the 3x3 stencil, D[pixel][co] += A[pixel][ci] *
+// B[co][ci] with A the input activations shifted by the tap and B the tap's
+// 16 x 16 weight slice (K = 16 input channels, N = 16 output channels), so a
+// row is nine tcgen05.mma (kind::f16, bf16 inputs, FP32 accumulator in tensor
+// memory).  One elected thread issues the MMAs; tcgen05.commit signals an
+// mbarrier; the four warps read the accumulator back with tcgen05.ld, apply
+// ReLU and the domain mask, round to bfloat16 and write the next layer's
+// activations to shared memory.  Layer 1 has two input channels (zero-padded
+// to 16), layer 4 one output channel (zero-padded weights, column 0 read).
+//
+// Tile: 120 x 8 output pixels with a 4-pixel halo (four layers of 3x3), i.e.
+// 128 x 16 activation pixels; layer l computes rows l .. 15 - l, so the halo
+// rows and columns become invalid one ring per layer and the central 120 x 8
+// outputs are exact.  Pixels outside the problem's grid are held at zero in
+// every layer (the zero padding of each convolution).
+//
+// Operand layouts (shared memory, K-major, no swizzle): a core matrix is 8
+// rows x 16 bytes (8 bf16 of K) stored contiguously; the descriptor's
+// leading byte offset (LBO) steps between the two K halves (128 bytes), the
+// stride byte offset (SBO) between consecutive groups of 8 rows (256 bytes).
+// Every tap's A tile is staged into this compact layout, so an operand never
+// spans more than 4 KiB of shared memory.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace mpcg {
+
+namespace {
+
+constexpr int kTW = 120;           // output tile width
+constexpr int kTH = 8;             // output tile height
+constexpr int kHalo = 4;
+constexpr int kEW = kTW + 2 * kHalo;   // 128 = M of one MMA row
+constexpr int kEH = kTH + 2 * kHalo;   // 16
+constexpr int kXS = kEW + 2;           // stored row length: x = -1 and x = 128 are zero columns
+constexpr int kThreads = 128;          // four warps: TMEM lanes 0..127
+constexpr int kTmemCols = 32;
+constexpr long long kWaitLimit = 1LL << 22;
+
+// shared memory map (bytes)
+constexpr int kActBytes = kEH * kXS * 16 * 2;        // one activation buffer [y][x+1][16] bf16
+constexpr int kStageBytes = 9 * 128 * 16 * 2;        // nine staged A tiles
+constexpr int kWBytes = 4 * 9 * 16 * 16 * 2;         // four layers x nine taps of B
+constexpr int kOffAct0 = 0;
+constexpr int kOffAct1 = kOffAct0 + kActBytes;
+constexpr int kOffStage = kOffAct1 + kActBytes;
+constexpr int kOffW = kOffStage + kStageBytes;
+constexpr int kOffBar = kOffW + kWBytes;
+constexpr int kSmemBytes = kOffBar + 64;
+
+// instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits
+// 17-22, M >> 4 at bits 24-28
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, LBO and SBO (all >> 4),
+// descriptor version 1 at bits 46-47, base offset 0, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// byte offset of element (row, k) in a compact K-major tile of 16 columns
+__device__ __forceinline__ int canon(int row, int k) {
+  return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; false if the phase did not complete within the limit
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long long i = 0; i < kWaitLimit; ++i)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+      :
+      : "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// The fused forward pass.  r: the residual (type T, padded layout, image b
+// at b * r_ld; scaled by 1 / ||r|| from the solver state when state is
+// given), c: coefficient channel (padded), wq: bfloat16-valued weights as
+// floats, y: optional float output, z: optional output ||r|| y (type T).
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_net_infer_tc(GridDesc g, const T* __restrict__ r, long long r_ld, const float* __restrict__ c,
+                   const float* __restrict__ wq, const DevState* state, float* __restrict__ y, T* __restrict__ z,
+                   int* err) {
+  if (state && state->done) return;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __nv_bfloat16* act[2] = {reinterpret_cast<__nv_bfloat16*>(smem + kOffAct0),
+                           reinterpret_cast<__nv_bfloat16*>(smem + kOffAct1)};
+  unsigned char* stage = smem + kOffStage;
+  unsigned char* wsm = smem + kOffW;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 8);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int b = blockIdx.z;
+  const int gx0 = blockIdx.x * kTW - kHalo, gy0 = blockIdx.y * kTH - kHalo;
+  const int n1 = g.n1;
+  const long long p = g.p;
+
+  // tensor memory: 32 columns (two 16-column accumulators)
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // zero both activation buffers (the x = -1 / x = 128 columns stay zero)
+  for (int i = tid; i < 2 * kActBytes / 16; i += kThreads) reinterpret_cast<uint4*>(smem + kOffAct0)[i] = make_uint4(0, 0, 0, 0);
+  // weights: layer L, tap t -> B[n = co][k = ci] in the compact layout
+  for (int e = tid; e < 4 * 9 * 256; e += kThreads) {
+    const int L = e / (9 * 256), t = (e / 256) % 9, n = (e / 16) % 16, k = e % 16;
+    float w = 0.f;
+    if (L == 0) { if (k < kNetIn) w = wq[kNetOff1 + (n * kNetIn + k) * 9 + t]; }
+    else if (L == 1) w = wq[kNetOff2 + (n * kNetC1 + k) * 9 + t];
+    else if (L == 2) w = wq[kNetOff3 + (n * kNetW + k) * 9 + t];
+    else { if (n == 0) w = wq[kNetOff4 + k * 9 + t]; }
+    *reinterpret_cast<__nv_bfloat16*>(wsm + (L * 9 + t) * 512 + canon(n, k)) = __float2bfloat16_rn(w);
+  }
+  __syncthreads();
+  // input tile: channel 0 = bf16(r / ||r||), channel 1 = bf16(c), zero outside the grid
+  const float sc = state ? (float)(state->rnorm > 0.0 ? 1.0 / state->rnorm : 0.0) : 1.f;
+  const T* rb = r + (long long)b * r_ld;
+  for (int i = tid; i < kEH * kEW; i += kThreads) {
+    const int yy = i / kEW, xx = i % kEW;
+    const int gx = gx0 + xx, gy = gy0 + yy;
+    float v0 = 0.f, v1 = 0.f;
+    if (gx >= 0 && gx < n1 && gy >= 0 && gy < n1) {
+      const long long idx = g.G + gx + p * gy;
+      v0 = (float)rb[idx] * sc;
+      v1 = c[idx];
+    }
+    __nv_bfloat16* dst = act[0] + ((long long)yy * kXS + xx + 1) * 16;
+    dst[0] = __float2bfloat16_rn(v0);
+    dst[1] = __float2bfloat16_rn(v1);
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t bar_addr = smem_u32(bar);
+  const uint32_t stage_addr = smem_u32(stage), w_addr = smem_u32(wsm);
+  uint32_t phase = 0;
+  bool failed = false;
+  const double zscale = state ? state->rnorm : 1.0;
+
+  for (int L = 0; L < 4 && !failed; ++L) {
+    const __nv_bfloat16* in = act[L & 1];
+    __nv_bfloat16* out = act[(L + 1) & 1];
+    for (int row = L + 1; row < kEH - (L + 1); ++row) {
+      // stage the nine shifted A tiles: thread = pixel x of the row
+      {
+        const int x = tid;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+          const int dy = t / 3 - 1, dx = t % 3 - 1;
+          const uint4* src = reinterpret_cast<const uint4*>(in + ((long long)(row + dy) * kXS + x + dx + 1) * 16);
+          unsigned char* dst = stage + t * 4096;
+          *reinterpret_cast<uint4*>(dst + canon(x, 0)) = src[0];
+          *reinterpret_cast<uint4*>(dst + canon(x, 8)) = src[1];
+        }
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        fence_after();
+#pragma unroll
+        for (int t = 0; t < 9; ++t)
+          mma_bf16(tmem, sdesc(stage_addr + t * 4096, 128, 256), sdesc(w_addr + (L * 9 + t) * 512, 128, 256),
+                   t > 0 ? 1u : 0u);
+        mma_commit(bar_addr);
+      }
+      const bool ok = mbar_wait(bar_addr, phase);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      fence_after();
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), v);
+      const int x = tid;
+      const int gx = gx0 + x, gy = gy0 + row;
+      const bool inside = gx >= 0 && gx < n1 && gy >= 0 && gy < n1;
+      if (L < 3) {
+        __nv_bfloat16* dst = out + ((long long)row * kXS + x + 1) * 16;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) dst[k] = __float2bfloat16_rn(inside ? fmaxf(v[k], 0.f) : 0.f);
+      } else if (inside && x >= kHalo && x < kHalo + kTW && row >= kHalo && row < kHalo + kTH) {
+        const long long o = (long long)b * g.len + g.G + gx + p * gy;
+        if (y) y[o] = v[0];
+        if (z) z[o] = (T)(zscale * (double)v[0]);
+      }
+      fence_before();
+      __syncthreads();
+    }
+  }
+  if (failed) {
+    if (tid == 0) atomicExch(err, 1);
+    // let any MMA still in flight finish (bounded) before freeing its memory
+    mbar_wait(bar_addr, phase);
+  }
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+}  // namespace
+
+size_t net_infer_smem() { return kSmemBytes; }
+
+template <typename T>
+void launch_net_infer(const GridDesc& g, int B, const T* r, long long r_ld, const float* c, const float* wq,
+                      const DevState* state, float* y, T* z, int* err, cudaStream_t s) {
+  const dim3 grid((unsigned)((g.n1 + kTW - 1) / kTW), (unsigned)((g.n1 + kTH - 1) / kTH), (unsigned)B);
+  k_net_infer_tc<T><<<grid, kThreads, kSmemBytes, s>>>(g, r, r_ld, c, wq, state, y, z, err);
+}
+template void launch_net_infer<double>(const GridDesc&, int, const double*, long long, const float*, const float*,
+                                       const DevState*, float*, double*, int*, cudaStream_t);
+template void launch_net_infer<float>(const GridDesc&, int, const float*, long long, const float*, const float*,
+                                      const DevState*, float*, float*, int*, cudaStream_t);
+
+void net_infer_prepare_attributes() {
+  cudaFuncSetAttribute(k_net_infer_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  cudaFuncSetAttribute(k_net_infer_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+}
+
+}  // namespace mpcg
