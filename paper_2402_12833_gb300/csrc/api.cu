@@ -223,6 +223,7 @@ struct mg_hierarchy {
   float* net_c = nullptr;      // coefficient channel on the fine grid
   NetActs net_acts = {};       // inference activations
   int* net_err = nullptr;      // set by the tensor-core inference kernel on a timed-out wait
+  unsigned char* net_wtc = nullptr;   // weights packed for the tensor-core kernel
   Alloc net_mem;
 };
 
@@ -406,7 +407,7 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
   enqueue_mg<T>(h, S, S.r, S.Z, S.state, s);
   if (h->net_on) {
     LAUNCH(h, K_NET, s,
-           launch_net_infer<T>(L.g, 1, S.r, L.g.len, h->net_c, h->net_wq, S.state, nullptr,
+           launch_net_infer<T>(L.g, 1, S.r, L.g.len, h->net_c, h->net_wtc, S.state, nullptr,
                                S.Z + (size_t)(C - 1) * L.g.len, h->net_err, s));
   }
   LAUNCH(h, K_SPMM, s, launch_spmm<T>(L.g, st_of<T>(L), S.Z, S.AZ, C, S.part_zaz, S.state, s));
@@ -1108,6 +1109,7 @@ mpcg_status net_prepare(mg_hierarchy* h) {
   CKS(h->net_mem.get(&h->net_acts.a2, (size_t)L.g.len * kNetW, s));
   CKS(h->net_mem.get(&h->net_acts.a3, (size_t)L.g.len * kNetW, s));
   CKS(h->net_mem.get(&h->net_err, 1, s));
+  CKS(h->net_mem.get(&h->net_wtc, (size_t)net_tc_weight_bytes(), s));
   net_infer_prepare_attributes();
   launch_net_coef(L.g, L.dinv64, h->opt.omega, h->net_c, part, s);
   CK(cudaGetLastError());
@@ -1155,7 +1157,10 @@ mpcg_status mg_learned_attach(mg_hierarchy* h, const float* params, int nparams)
   float* tmp = nullptr;
   CK(cudaMalloc(&tmp, sizeof(float) * kNetParams));
   mpcg_status st = copy_floats(tmp, params, kNetParams, h->stream);
-  if (st == MPCG_OK) launch_round_bf16(tmp, h->net_wq, kNetParams, h->stream);
+  if (st == MPCG_OK) {
+    launch_round_bf16(tmp, h->net_wq, kNetParams, h->stream);
+    launch_net_pack_tc(h->net_wq, h->net_wtc, h->stream);
+  }
   cudaStreamSynchronize(h->stream);
   cudaFree(tmp);
   if (st != MPCG_OK) return st;
@@ -1194,7 +1199,7 @@ mpcg_status mg_learned_forward(mg_hierarchy* h, const float* rhat_dev, float* y_
   mpcg_status st = MPCG_OK;
   if ((st = tmp.get(&r, (size_t)nimg * g.len, s)) == MPCG_OK && (st = tmp.get(&y, (size_t)nimg * g.len, s)) == MPCG_OK) {
     launch_pack<float, float>(g, rhat_dev, g.n, r, nimg, s);
-    launch_net_infer<float>(g, nimg, r, g.len, h->net_c, h->net_wq, nullptr, y, (float*)nullptr, h->net_err, s);
+    launch_net_infer<float>(g, nimg, r, g.len, h->net_c, h->net_wtc, nullptr, y, (float*)nullptr, h->net_err, s);
     launch_unpack<float, float>(g, y, y_dev, g.n, nimg, s);
     int err = 0;
     if (cudaMemcpyAsync(&err, h->net_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -156,13 +156,15 @@ size_t net_wgrad_smem(const GridDesc& g);
 template <typename T>
 void launch_net_forward(const GridDesc& g, int B, const T* r, long long r_ld, const float* c, const float* wq,
                         const DevState* state, NetActs acts, float* y, T* z, cudaStream_t s);
-// Fused tensor-core inference (all four layers per output tile); err is set
-// to 1 if a bounded wait on the MMA completion runs out.
+// Fused tensor-core inference (all four layers per output tile); wtc holds
+// the weights packed by launch_net_pack_tc (net_tc_weight_bytes() bytes);
+// err is set to 1 if a bounded wait on the MMA completion runs out.
 template <typename T>
-void launch_net_infer(const GridDesc& g, int B, const T* r, long long r_ld, const float* c, const float* wq,
+void launch_net_infer(const GridDesc& g, int B, const T* r, long long r_ld, const float* c, const void* wtc,
                       const DevState* state, float* y, T* z, int* err, cudaStream_t s);
+void launch_net_pack_tc(const float* wq, void* wtc, cudaStream_t s);
+int net_tc_weight_bytes();
 void net_infer_prepare_attributes();
-size_t net_infer_smem();
 void launch_net_backward(const GridDesc& g, int B, const float* wq, NetActs acts, const float* dy, NetGrads gr,
                          cudaStream_t s);
 void launch_net_loss_grad(const GridDesc& g, int B, const float* y, const float* Ay, const float* e,

@@ -22,10 +22,14 @@
 //
 // Operand layouts (shared memory, K-major, no swizzle): a core matrix is 8
 // rows x 16 bytes (8 bf16 of K) stored contiguously; the descriptor's
-// leading byte offset (LBO) steps between the two K halves (128 bytes), the
-// stride byte offset (SBO) between consecutive groups of 8 rows (256 bytes).
-// Every tap's A tile is staged into this compact layout, so an operand never
-// spans more than 4 KiB of shared memory.
+// leading byte offset (LBO) steps between the two K halves, the stride byte
+// offset (SBO) between consecutive groups of 8 rows.  Activations are kept as
+// two planes (channels 0-7 and 8-15) of [row][x + 1] pixels x 16 bytes, so
+// the A operand of tap (dy, dx) for a row is simply the 128 consecutive
+// pixels starting at (row + dy, dx): SBO = 128 bytes, LBO = one plane.  The
+// weights are packed once per attach into the compact tile layout (LBO = 128,
+// SBO = 256 bytes).  Rows are software-pipelined over two TMEM accumulators:
+// the MMAs of row i + 1 run while the warps drain row i.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -41,18 +45,18 @@ constexpr int kHalo = 4;
 constexpr int kEW = kTW + 2 * kHalo;   // 128 = M of one MMA row
 constexpr int kEH = kTH + 2 * kHalo;   // 16
 constexpr int kXS = kEW + 2;           // stored row length: x = -1 and x = 128 are zero columns
+constexpr int kNPix = kEH * kXS;       // pixels of one activation buffer
+constexpr int kPlane = kNPix * 16;     // bytes of one channel plane
 constexpr int kThreads = 128;          // four warps: TMEM lanes 0..127
-constexpr int kTmemCols = 32;
+constexpr int kTmemCols = 32;          // two 16-column accumulators
 constexpr long long kWaitLimit = 1LL << 22;
 
 // shared memory map (bytes)
-constexpr int kActBytes = kEH * kXS * 16 * 2;        // one activation buffer [y][x+1][16] bf16
-constexpr int kStageBytes = 9 * 128 * 16 * 2;        // nine staged A tiles
+constexpr int kActBytes = 2 * kPlane;                // one activation buffer (two planes)
 constexpr int kWBytes = 4 * 9 * 16 * 16 * 2;         // four layers x nine taps of B
 constexpr int kOffAct0 = 0;
 constexpr int kOffAct1 = kOffAct0 + kActBytes;
-constexpr int kOffStage = kOffAct1 + kActBytes;
-constexpr int kOffW = kOffStage + kStageBytes;
+constexpr int kOffW = kOffAct1 + kActBytes;
 constexpr int kOffBar = kOffW + kWBytes;
 constexpr int kSmemBytes = kOffBar + 64;
 
@@ -71,7 +75,7 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 }
 
 // byte offset of element (row, k) in a compact K-major tile of 16 columns
-__device__ __forceinline__ int canon(int row, int k) {
+__host__ __device__ __forceinline__ int canon(int row, int k) {
   return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
@@ -126,30 +130,40 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// the nine MMAs of one activation row into TMEM columns col0 .. col0 + 15
+__device__ __forceinline__ void issue_row(uint32_t tmem, int col0, uint32_t act_in, uint32_t w_layer, int row) {
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    const int dy = t / 3 - 1, dx = t % 3 - 1;
+    const uint32_t a = act_in + (uint32_t)(((row + dy) * kXS + dx + 1) * 16);
+    mma_bf16(tmem + (uint32_t)col0, sdesc(a, kPlane, 128), sdesc(w_layer + t * 512, 128, 256), t > 0 ? 1u : 0u);
+  }
+}
+
 // The fused forward pass.  r: the residual (type T, padded layout, image b
 // at b * r_ld; scaled by 1 / ||r|| from the solver state when state is
-// given), c: coefficient channel (padded), wq: bfloat16-valued weights as
-// floats, y: optional float output, z: optional output ||r|| y (type T).
+// given), c: coefficient channel (padded), wtc: the packed bfloat16 weights,
+// y: optional float output, z: optional output ||r|| y (type T).
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1)
     k_net_infer_tc(GridDesc g, const T* __restrict__ r, long long r_ld, const float* __restrict__ c,
-                   const float* __restrict__ wq, const DevState* state, float* __restrict__ y, T* __restrict__ z,
+                   const uint4* __restrict__ wtc, const DevState* state, float* __restrict__ y, T* __restrict__ z,
                    int* err) {
   if (state && state->done) return;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __nv_bfloat16* act[2] = {reinterpret_cast<__nv_bfloat16*>(smem + kOffAct0),
-                           reinterpret_cast<__nv_bfloat16*>(smem + kOffAct1)};
-  unsigned char* stage = smem + kOffStage;
-  unsigned char* wsm = smem + kOffW;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 8);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 16);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int b = blockIdx.z;
   const int gx0 = blockIdx.x * kTW - kHalo, gy0 = blockIdx.y * kTH - kHalo;
   const int n1 = g.n1;
   const long long p = g.p;
 
-  // tensor memory: 32 columns (two 16-column accumulators)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(kTmemCols)
@@ -158,20 +172,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 1)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // zero both activation buffers (the x = -1 / x = 128 columns stay zero)
   for (int i = tid; i < 2 * kActBytes / 16; i += kThreads) reinterpret_cast<uint4*>(smem + kOffAct0)[i] = make_uint4(0, 0, 0, 0);
-  // weights: layer L, tap t -> B[n = co][k = ci] in the compact layout
-  for (int e = tid; e < 4 * 9 * 256; e += kThreads) {
-    const int L = e / (9 * 256), t = (e / 256) % 9, n = (e / 16) % 16, k = e % 16;
-    float w = 0.f;
-    if (L == 0) { if (k < kNetIn) w = wq[kNetOff1 + (n * kNetIn + k) * 9 + t]; }
-    else if (L == 1) w = wq[kNetOff2 + (n * kNetC1 + k) * 9 + t];
-    else if (L == 2) w = wq[kNetOff3 + (n * kNetW + k) * 9 + t];
-    else { if (n == 0) w = wq[kNetOff4 + k * 9 + t]; }
-    *reinterpret_cast<__nv_bfloat16*>(wsm + (L * 9 + t) * 512 + canon(n, k)) = __float2bfloat16_rn(w);
-  }
+  for (int i = tid; i < kWBytes / 16; i += kThreads) reinterpret_cast<uint4*>(smem + kOffW)[i] = wtc[i];
   __syncthreads();
   // input tile: channel 0 = bf16(r / ||r||), channel 1 = bf16(c), zero outside the grid
   const float sc = state ? (float)(state->rnorm > 0.0 ? 1.0 / state->rnorm : 0.0) : 1.f;
@@ -185,93 +191,114 @@ __global__ void __launch_bounds__(kThreads, 1)
       v0 = (float)rb[idx] * sc;
       v1 = c[idx];
     }
-    __nv_bfloat16* dst = act[0] + ((long long)yy * kXS + xx + 1) * 16;
-    dst[0] = __float2bfloat16_rn(v0);
-    dst[1] = __float2bfloat16_rn(v1);
+    *reinterpret_cast<uint4*>(smem + kOffAct0 + (yy * kXS + xx + 1) * 16) = make_uint4(pack_bf16x2(v0, v1), 0, 0, 0);
   }
+  fence_async_smem();
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t bar_addr = smem_u32(bar);
-  const uint32_t stage_addr = smem_u32(stage), w_addr = smem_u32(wsm);
-  uint32_t phase = 0;
+  const uint32_t bar0 = smem_u32(bar), w_addr = smem_u32(smem + kOffW);
+  const uint32_t act_addr[2] = {smem_u32(smem + kOffAct0), smem_u32(smem + kOffAct1)};
+  unsigned issued = 0, waited = 0;
   bool failed = false;
   const double zscale = state ? state->rnorm : 1.0;
+  const int x = tid;
+  const int gx = gx0 + x;
 
   for (int L = 0; L < 4 && !failed; ++L) {
-    const __nv_bfloat16* in = act[L & 1];
-    __nv_bfloat16* out = act[(L + 1) & 1];
-    for (int row = L + 1; row < kEH - (L + 1); ++row) {
-      // stage the nine shifted A tiles: thread = pixel x of the row
-      {
-        const int x = tid;
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-          const int dy = t / 3 - 1, dx = t % 3 - 1;
-          const uint4* src = reinterpret_cast<const uint4*>(in + ((long long)(row + dy) * kXS + x + dx + 1) * 16);
-          unsigned char* dst = stage + t * 4096;
-          *reinterpret_cast<uint4*>(dst + canon(x, 0)) = src[0];
-          *reinterpret_cast<uint4*>(dst + canon(x, 8)) = src[1];
+    const uint32_t ain = act_addr[L & 1], wl = w_addr + L * 9 * 512;
+    unsigned char* out = smem + (L & 1 ? kOffAct0 : kOffAct1);
+    const int r0 = L + 1, nrows = kEH - 2 * (L + 1);
+    if (tid == 0) {
+      fence_after();
+      issue_row(tmem, 16 * (issued & 1), ain, wl, r0);
+      mma_commit(bar0 + 8 * (issued & 1));
+    }
+    ++issued;
+    for (int i = 0; i < nrows; ++i) {
+      if (i + 1 < nrows) {   // keep the tensor core busy with the next row
+        if (tid == 0) {
+          issue_row(tmem, 16 * (issued & 1), ain, wl, r0 + i + 1);
+          mma_commit(bar0 + 8 * (issued & 1));
         }
+        ++issued;
       }
-      fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
-        fence_after();
-#pragma unroll
-        for (int t = 0; t < 9; ++t)
-          mma_bf16(tmem, sdesc(stage_addr + t * 4096, 128, 256), sdesc(w_addr + (L * 9 + t) * 512, 128, 256),
-                   t > 0 ? 1u : 0u);
-        mma_commit(bar_addr);
-      }
-      const bool ok = mbar_wait(bar_addr, phase);
-      phase ^= 1u;
+      const unsigned h = waited & 1;
+      const bool ok = mbar_wait(bar0 + 8 * h, (waited >> 1) & 1);
+      ++waited;
       if (__syncthreads_or(!ok)) {
         failed = true;
         break;
       }
       fence_after();
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), v);
-      const int x = tid;
-      const int gx = gx0 + x, gy = gy0 + row;
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * h, v);
+      const int row = r0 + i, gy = gy0 + row;
       const bool inside = gx >= 0 && gx < n1 && gy >= 0 && gy < n1;
       if (L < 3) {
-        __nv_bfloat16* dst = out + ((long long)row * kXS + x + 1) * 16;
+        uint32_t q[8];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) dst[k] = __float2bfloat16_rn(inside ? fmaxf(v[k], 0.f) : 0.f);
+        for (int k = 0; k < 8; ++k)
+          q[k] = inside ? pack_bf16x2(fmaxf(v[2 * k], 0.f), fmaxf(v[2 * k + 1], 0.f)) : 0u;
+        const int off = (row * kXS + x + 1) * 16;
+        *reinterpret_cast<uint4*>(out + off) = make_uint4(q[0], q[1], q[2], q[3]);
+        *reinterpret_cast<uint4*>(out + kPlane + off) = make_uint4(q[4], q[5], q[6], q[7]);
       } else if (inside && x >= kHalo && x < kHalo + kTW && row >= kHalo && row < kHalo + kTH) {
         const long long o = (long long)b * g.len + g.G + gx + p * gy;
         if (y) y[o] = v[0];
         if (z) z[o] = (T)(zscale * (double)v[0]);
       }
+      fence_async_smem();
       fence_before();
       __syncthreads();
+      if (tid == 0) fence_after();
     }
   }
   if (failed) {
     if (tid == 0) atomicExch(err, 1);
-    // let any MMA still in flight finish (bounded) before freeing its memory
-    mbar_wait(bar_addr, phase);
+    // let the MMAs still in flight finish (bounded) before freeing their memory
+    while (waited < issued) {
+      mbar_wait(bar0 + 8 * (waited & 1), (waited >> 1) & 1);
+      ++waited;
+    }
   }
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// Pack the bfloat16-valued weights into the compact B tiles of the four
+// layers (zero-padded to 16 x 16 per tap).
+__global__ void k_net_pack_tc(const float* __restrict__ wq, __nv_bfloat16* __restrict__ wtc) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 4 * 9 * 256; e += gridDim.x * blockDim.x) {
+    const int L = e / (9 * 256), t = (e / 256) % 9, n = (e / 16) % 16, k = e % 16;
+    float w = 0.f;
+    if (L == 0) { if (k < kNetIn) w = wq[kNetOff1 + (n * kNetIn + k) * 9 + t]; }
+    else if (L == 1) w = wq[kNetOff2 + (n * kNetC1 + k) * 9 + t];
+    else if (L == 2) w = wq[kNetOff3 + (n * kNetW + k) * 9 + t];
+    else { if (n == 0) w = wq[kNetOff4 + k * 9 + t]; }
+    wtc[((L * 9 + t) * 512 + canon(n, k)) / 2] = __float2bfloat16_rn(w);
+  }
+}
+
 }  // namespace
 
-size_t net_infer_smem() { return kSmemBytes; }
+int net_tc_weight_bytes() { return kWBytes; }
+
+void launch_net_pack_tc(const float* wq, void* wtc, cudaStream_t s) {
+  k_net_pack_tc<<<36, 256, 0, s>>>(wq, reinterpret_cast<__nv_bfloat16*>(wtc));
+}
 
 template <typename T>
-void launch_net_infer(const GridDesc& g, int B, const T* r, long long r_ld, const float* c, const float* wq,
+void launch_net_infer(const GridDesc& g, int B, const T* r, long long r_ld, const float* c, const void* wtc,
                       const DevState* state, float* y, T* z, int* err, cudaStream_t s) {
   const dim3 grid((unsigned)((g.n1 + kTW - 1) / kTW), (unsigned)((g.n1 + kTH - 1) / kTH), (unsigned)B);
-  k_net_infer_tc<T><<<grid, kThreads, kSmemBytes, s>>>(g, r, r_ld, c, wq, state, y, z, err);
+  k_net_infer_tc<T><<<grid, kThreads, kSmemBytes, s>>>(g, r, r_ld, c, reinterpret_cast<const uint4*>(wtc), state, y,
+                                                        z, err);
 }
-template void launch_net_infer<double>(const GridDesc&, int, const double*, long long, const float*, const float*,
+template void launch_net_infer<double>(const GridDesc&, int, const double*, long long, const float*, const void*,
                                        const DevState*, float*, double*, int*, cudaStream_t);
-template void launch_net_infer<float>(const GridDesc&, int, const float*, long long, const float*, const float*,
+template void launch_net_infer<float>(const GridDesc&, int, const float*, long long, const float*, const void*,
                                       const DevState*, float*, float*, int*, cudaStream_t);
 
 void net_infer_prepare_attributes() {
