@@ -28,8 +28,11 @@
 // the A operand of tap (dy, dx) for a row is simply the 128 consecutive
 // pixels starting at (row + dy, dx): SBO = 128 bytes, LBO = one plane.  The
 // weights are packed once per attach into the compact tile layout (LBO = 128,
-// SBO = 256 bytes).  Rows are software-pipelined over two TMEM accumulators:
-// the MMAs of row i + 1 run while the warps drain row i.
+// SBO = 256 bytes).  Per layer the issuing thread enqueues the MMAs of all
+// rows at once, each row into its own TMEM columns and signalling its own
+// mbarrier, and every warp drains the rows in order as they complete (a
+// warp reads only its own 32 TMEM lanes, so no block barrier is needed
+// between rows).
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -48,7 +51,8 @@ constexpr int kXS = kEW + 2;           // stored row length: x = -1 and x = 128 
 constexpr int kNPix = kEH * kXS;       // pixels of one activation buffer
 constexpr int kPlane = kNPix * 16;     // bytes of one channel plane
 constexpr int kThreads = 128;          // four warps: TMEM lanes 0..127
-constexpr int kTmemCols = 32;          // two 16-column accumulators
+constexpr int kMaxRows = kEH - 2;      // rows computed by the first layer
+constexpr int kTmemCols = 256;         // one 16-column accumulator per row of a layer
 constexpr long long kWaitLimit = 1LL << 22;
 
 // shared memory map (bytes)
@@ -58,7 +62,7 @@ constexpr int kOffAct0 = 0;
 constexpr int kOffAct1 = kOffAct0 + kActBytes;
 constexpr int kOffW = kOffAct1 + kActBytes;
 constexpr int kOffBar = kOffW + kWBytes;
-constexpr int kSmemBytes = kOffBar + 64;
+constexpr int kSmemBytes = kOffBar + 8 * kMaxRows + 16;
 
 // instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits
@@ -157,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (state && state->done) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 16);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 8 * kMaxRows);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int b = blockIdx.z;
   const int gx0 = blockIdx.x * kTW - kHalo, gy0 = blockIdx.y * kTH - kHalo;
@@ -170,11 +174,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 1)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
+  if (tid < kMaxRows) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + tid)) : "memory");
+  if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   // zero both activation buffers (the x = -1 / x = 128 columns stay zero)
   for (int i = tid; i < 2 * kActBytes / 16; i += kThreads) reinterpret_cast<uint4*>(smem + kOffAct0)[i] = make_uint4(0, 0, 0, 0);
   for (int i = tid; i < kWBytes / 16; i += kThreads) reinterpret_cast<uint4*>(smem + kOffW)[i] = wtc[i];
@@ -200,7 +201,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tmem_slot;
   const uint32_t bar0 = smem_u32(bar), w_addr = smem_u32(smem + kOffW);
   const uint32_t act_addr[2] = {smem_u32(smem + kOffAct0), smem_u32(smem + kOffAct1)};
-  unsigned issued = 0, waited = 0;
+  uint32_t parity = 0;            // bit i: phase of row barrier i to wait for next
+  uint32_t pending = 0;           // bit i: row barrier i has a commit not yet waited for
   bool failed = false;
   const double zscale = state ? state->rnorm : 1.0;
   const int x = tid;
@@ -212,28 +214,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int r0 = L + 1, nrows = kEH - 2 * (L + 1);
     if (tid == 0) {
       fence_after();
-      issue_row(tmem, 16 * (issued & 1), ain, wl, r0);
-      mma_commit(bar0 + 8 * (issued & 1));
-    }
-    ++issued;
-    for (int i = 0; i < nrows; ++i) {
-      if (i + 1 < nrows) {   // keep the tensor core busy with the next row
-        if (tid == 0) {
-          issue_row(tmem, 16 * (issued & 1), ain, wl, r0 + i + 1);
-          mma_commit(bar0 + 8 * (issued & 1));
-        }
-        ++issued;
+      for (int i = 0; i < nrows; ++i) {
+        issue_row(tmem, 16 * i, ain, wl, r0 + i);
+        mma_commit(bar0 + 8 * i);
       }
-      const unsigned h = waited & 1;
-      const bool ok = mbar_wait(bar0 + 8 * h, (waited >> 1) & 1);
-      ++waited;
-      if (__syncthreads_or(!ok)) {
+    }
+    pending = (1u << nrows) - 1u;
+    for (int i = 0; i < nrows; ++i) {
+      const bool ok = mbar_wait(bar0 + 8 * i, (parity >> i) & 1u);
+      if (!ok) {
         failed = true;
         break;
       }
+      parity ^= 1u << i;
+      pending &= ~(1u << i);
       fence_after();
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * h, v);
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * i, v);
       const int row = r0 + i, gy = gy0 + row;
       const bool inside = gx >= 0 && gx < n1 && gy >= 0 && gy < n1;
       if (L < 3) {
@@ -249,19 +246,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (y) y[o] = v[0];
         if (z) z[o] = (T)(zscale * (double)v[0]);
       }
-      fence_async_smem();
-      fence_before();
-      __syncthreads();
-      if (tid == 0) fence_after();
     }
+    // the layer's outputs feed the next layer's MMAs (async proxy)
+    fence_async_smem();
+    fence_before();
+    failed = __syncthreads_or(failed);
   }
   if (failed) {
     if (tid == 0) atomicExch(err, 1);
     // let the MMAs still in flight finish (bounded) before freeing their memory
-    while (waited < issued) {
-      mbar_wait(bar0 + 8 * (waited & 1), (waited >> 1) & 1);
-      ++waited;
-    }
+    for (int i = 0; i < kMaxRows; ++i)
+      if ((pending >> i) & 1u) mbar_wait(bar0 + 8 * i, (parity >> i) & 1u);
   }
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
