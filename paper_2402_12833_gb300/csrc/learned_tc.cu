@@ -55,6 +55,9 @@ constexpr int kMaxRows = kEH - 2;      // rows computed by the first layer
 constexpr int kTmemCols = 256;         // one 16-column accumulator per row of a layer
 constexpr long long kWaitLimit = 1LL << 22;
 
+static_assert(kEW == kThreads, "one thread per tile column");
+static_assert(kEH == 16 && kThreads == 128, "halo-column zeroing maps 16 rows x 2 sides x 2 planes x 2 buffers");
+
 // shared memory map (bytes)
 constexpr int kActBytes = 2 * kPlane;                // one activation buffer (two planes)
 constexpr int kWBytes = 4 * 9 * 16 * 16 * 2;         // four layers x nine taps of B
@@ -176,23 +179,36 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (tid < kMaxRows) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + tid)) : "memory");
   if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  // zero both activation buffers (the x = -1 / x = 128 columns stay zero)
-  for (int i = tid; i < 2 * kActBytes / 16; i += kThreads) reinterpret_cast<uint4*>(smem + kOffAct0)[i] = make_uint4(0, 0, 0, 0);
+  // zero the x = -1 and x = 128 columns of every row, plane and buffer (the
+  // only activation entries that no layer writes but later layers read)
+  {
+    const int row = tid & 15, side = (tid >> 4) & 1, plane = (tid >> 5) & 1, buf = tid >> 6;
+    *reinterpret_cast<uint4*>(smem + buf * kActBytes + plane * kPlane + (row * kXS + side * (kXS - 1)) * 16) =
+        make_uint4(0, 0, 0, 0);
+  }
   for (int i = tid; i < kWBytes / 16; i += kThreads) reinterpret_cast<uint4*>(smem + kOffW)[i] = wtc[i];
-  __syncthreads();
-  // input tile: channel 0 = bf16(r / ||r||), channel 1 = bf16(c), zero outside the grid
-  const float sc = state ? (float)(state->rnorm > 0.0 ? 1.0 / state->rnorm : 0.0) : 1.f;
-  const T* rb = r + (long long)b * r_ld;
-  for (int i = tid; i < kEH * kEW; i += kThreads) {
-    const int yy = i / kEW, xx = i % kEW;
-    const int gx = gx0 + xx, gy = gy0 + yy;
-    float v0 = 0.f, v1 = 0.f;
-    if (gx >= 0 && gx < n1 && gy >= 0 && gy < n1) {
-      const long long idx = g.G + gx + p * gy;
-      v0 = (float)rb[idx] * sc;
-      v1 = c[idx];
+  // input tile (thread = column x, all 16 rows, loads issued together):
+  // channel 0 = bf16(r / ||r||), channel 1 = bf16(c), zero outside the grid
+  {
+    const float sc = state ? (float)(state->rnorm > 0.0 ? 1.0 / state->rnorm : 0.0) : 1.f;
+    const T* rb = r + (long long)b * r_ld;
+    const int gxx = gx0 + tid;
+    const bool colok = gxx >= 0 && gxx < n1;
+    float v0[kEH], v1[kEH];
+#pragma unroll
+    for (int yy = 0; yy < kEH; ++yy) {
+      const int gy = gy0 + yy;
+      const bool ok = colok && gy >= 0 && gy < n1;
+      const long long idx = g.G + gxx + p * gy;
+      v0[yy] = ok ? (float)rb[idx] * sc : 0.f;
+      v1[yy] = ok ? c[idx] : 0.f;
     }
-    *reinterpret_cast<uint4*>(smem + kOffAct0 + (yy * kXS + xx + 1) * 16) = make_uint4(pack_bf16x2(v0, v1), 0, 0, 0);
+#pragma unroll
+    for (int yy = 0; yy < kEH; ++yy) {
+      const int off = (yy * kXS + tid + 1) * 16;
+      *reinterpret_cast<uint4*>(smem + kOffAct0 + off) = make_uint4(pack_bf16x2(v0[yy], v1[yy]), 0, 0, 0);
+      *reinterpret_cast<uint4*>(smem + kOffAct0 + kPlane + off) = make_uint4(0, 0, 0, 0);
+    }
   }
   fence_async_smem();
   fence_before();
