@@ -667,7 +667,7 @@ def bench_learned(args):
     M.load()
     t0 = time.perf_counter()
     hs, R, E, owner = [], [], [], []
-    for i, sd in enumerate(range(1000, 1016)):
+    for i, sd in enumerate(range(1000, 1016) if args.epochs > 0 else ()):
         prob = pb.diffusion_macro(2, 129, sd)
         H = M.Hierarchy(torch.from_numpy(prob.stencil).cuda(), 2, 129, prob.levels, m=M_WINDOW)
         b = torch.from_numpy(prob.b).cuda()
@@ -687,8 +687,10 @@ def bench_learned(args):
     gen_s = time.perf_counter() - t0
     params = pb.net_init_params(7)
     t0 = time.perf_counter()
-    loss = M.mg_learned_train([h.h for h in hs], owner, torch.stack(R).contiguous(), torch.stack(E).contiguous(),
-                              params, epochs=args.epochs, batch=8, lr=1e-3)
+    loss = [float("nan")]
+    if args.epochs > 0:   # --epochs 0: the initial (untrained) weights, inference cost only
+        loss = M.mg_learned_train([h.h for h in hs], owner, torch.stack(R).contiguous(),
+                                  torch.stack(E).contiguous(), params, epochs=args.epochs, batch=8, lr=1e-3)
     train_s = time.perf_counter() - t0
     prob = pb.diffusion_macro(2, 1025, 3)
     st = torch.from_numpy(prob.stencil).cuda()
@@ -708,6 +710,12 @@ def bench_learned(args):
         ms = _timed(step, args.steps, 1, torch.cuda.current_stream())
         out[key] = {"ms_per_solve": ms, "iterations": int(res["k"]), "status": int(res["st"]),
                     "dofs_per_s": prob.n / (ms * 1e-3)}
+        if key == "learned":   # live CUDA-event time of the fused tensor-core network kernel
+            x.zero_()
+            _, _, _, trace = M.mpcg_solve_profiled(H.h, b, x, RTOL, 50000)
+            net = [t for c, t in trace if c == "net"]
+            if net:
+                out[key]["net_us_per_application"] = 1e3 * sum(net) / len(net)
         H.close()
     print(json.dumps({
         "metric": METRIC, "workload": "learned", "value": out["learned"]["dofs_per_s"], "unit": "DOFs/s",
