@@ -28,7 +28,13 @@
 // the A operand of tap (dy, dx) for a row is simply the 128 consecutive
 // pixels starting at (row + dy, dx): SBO = 128 bytes, LBO = one plane.  The
 // weights are packed once per attach into the compact tile layout (LBO = 128,
-// SBO = 256 bytes).  Per layer the issuing thread enqueues the MMAs of all
+// SBO = 256 bytes).  The activations are updated in place: input row q of
+// layer L lives in slot q - L, and output row r is written to slot r - L - 1
+// (its slot as an input of layer L + 1) once row r's MMAs have completed --
+// by then every MMA that reads input row r - 1 (rows r - 2 .. r) is done, and
+// the commits complete in issue order.  This halves the shared memory, so two
+// CTAs share an SM and hide each other's latencies.
+// Per layer the issuing thread enqueues the MMAs of all
 // rows at once, each row into its own TMEM columns and signalling its own
 // mbarrier, and every warp drains the rows in order as they complete (a
 // warp reads only its own 32 TMEM lanes, so no block barrier is needed
@@ -56,14 +62,13 @@ constexpr int kTmemCols = 256;         // one 16-column accumulator per row of a
 constexpr long long kWaitLimit = 1LL << 22;
 
 static_assert(kEW == kThreads, "one thread per tile column");
-static_assert(kEH == 16 && kThreads == 128, "halo-column zeroing maps 16 rows x 2 sides x 2 planes x 2 buffers");
+static_assert(kEH == 16 && kThreads == 128, "halo-column zeroing maps 16 rows x 2 sides x 2 planes (x 2 passes)");
 
-// shared memory map (bytes)
-constexpr int kActBytes = 2 * kPlane;                // one activation buffer (two planes)
+// shared memory map (bytes): one activation buffer, updated in place
+constexpr int kActBytes = 2 * kPlane;                // two planes
 constexpr int kWBytes = 4 * 9 * 16 * 16 * 2;         // four layers x nine taps of B
 constexpr int kOffAct0 = 0;
-constexpr int kOffAct1 = kOffAct0 + kActBytes;
-constexpr int kOffW = kOffAct1 + kActBytes;
+constexpr int kOffW = kOffAct0 + kActBytes;
 constexpr int kOffBar = kOffW + kWBytes;
 constexpr int kSmemBytes = kOffBar + 8 * kMaxRows + 16;
 
@@ -142,12 +147,13 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// the nine MMAs of one activation row into TMEM columns col0 .. col0 + 15
-__device__ __forceinline__ void issue_row(uint32_t tmem, int col0, uint32_t act_in, uint32_t w_layer, int row) {
+// the nine MMAs of one activation row into TMEM columns col0 .. col0 + 15;
+// `slot` is the storage slot of input row `row`
+__device__ __forceinline__ void issue_row(uint32_t tmem, int col0, uint32_t act_in, uint32_t w_layer, int slot) {
 #pragma unroll
   for (int t = 0; t < 9; ++t) {
     const int dy = t / 3 - 1, dx = t % 3 - 1;
-    const uint32_t a = act_in + (uint32_t)(((row + dy) * kXS + dx + 1) * 16);
+    const uint32_t a = act_in + (uint32_t)(((slot + dy) * kXS + dx + 1) * 16);
     mma_bf16(tmem + (uint32_t)col0, sdesc(a, kPlane, 128), sdesc(w_layer + t * 512, 128, 256), t > 0 ? 1u : 0u);
   }
 }
@@ -157,7 +163,7 @@ __device__ __forceinline__ void issue_row(uint32_t tmem, int col0, uint32_t act_
 // given), c: coefficient channel (padded), wtc: the packed bfloat16 weights,
 // y: optional float output, z: optional output ||r|| y (type T).
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     k_net_infer_tc(GridDesc g, const T* __restrict__ r, long long r_ld, const float* __restrict__ c,
                    const uint4* __restrict__ wtc, const DevState* state, float* __restrict__ y, T* __restrict__ z,
                    int* err) {
@@ -179,11 +185,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (tid < kMaxRows) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + tid)) : "memory");
   if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  // zero the x = -1 and x = 128 columns of every row, plane and buffer (the
-  // only activation entries that no layer writes but later layers read)
-  {
-    const int row = tid & 15, side = (tid >> 4) & 1, plane = (tid >> 5) & 1, buf = tid >> 6;
-    *reinterpret_cast<uint4*>(smem + buf * kActBytes + plane * kPlane + (row * kXS + side * (kXS - 1)) * 16) =
+  // zero the x = -1 and x = 128 columns of every slot and plane (the only
+  // activation entries that no layer writes but later layers read)
+  if (tid < 64) {
+    const int row = tid & 15, side = (tid >> 4) & 1, plane = (tid >> 5) & 1;
+    *reinterpret_cast<uint4*>(smem + kOffAct0 + plane * kPlane + (row * kXS + side * (kXS - 1)) * 16) =
         make_uint4(0, 0, 0, 0);
   }
   for (int i = tid; i < kWBytes / 16; i += kThreads) reinterpret_cast<uint4*>(smem + kOffW)[i] = wtc[i];
@@ -216,7 +222,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t bar0 = smem_u32(bar), w_addr = smem_u32(smem + kOffW);
-  const uint32_t act_addr[2] = {smem_u32(smem + kOffAct0), smem_u32(smem + kOffAct1)};
+  const uint32_t act_addr = smem_u32(smem + kOffAct0);
+  unsigned char* act = smem + kOffAct0;
   uint32_t parity = 0;            // bit i: phase of row barrier i to wait for next
   uint32_t pending = 0;           // bit i: row barrier i has a commit not yet waited for
   bool failed = false;
@@ -225,13 +232,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int gx = gx0 + x;
 
   for (int L = 0; L < 4 && !failed; ++L) {
-    const uint32_t ain = act_addr[L & 1], wl = w_addr + L * 9 * 512;
-    unsigned char* out = smem + (L & 1 ? kOffAct0 : kOffAct1);
+    const uint32_t wl = w_addr + L * 9 * 512;
     const int r0 = L + 1, nrows = kEH - 2 * (L + 1);
     if (tid == 0) {
       fence_after();
       for (int i = 0; i < nrows; ++i) {
-        issue_row(tmem, 16 * i, ain, wl, r0 + i);
+        issue_row(tmem, 16 * i, act_addr, wl, r0 + i - L);
         mma_commit(bar0 + 8 * i);
       }
     }
@@ -254,9 +260,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int k = 0; k < 8; ++k)
           q[k] = inside ? pack_bf16x2(fmaxf(v[2 * k], 0.f), fmaxf(v[2 * k + 1], 0.f)) : 0u;
-        const int off = (row * kXS + x + 1) * 16;
-        *reinterpret_cast<uint4*>(out + off) = make_uint4(q[0], q[1], q[2], q[3]);
-        *reinterpret_cast<uint4*>(out + kPlane + off) = make_uint4(q[4], q[5], q[6], q[7]);
+        const int off = ((row - L - 1) * kXS + x + 1) * 16;   // in place: slot of input row row - 1
+        *reinterpret_cast<uint4*>(act + off) = make_uint4(q[0], q[1], q[2], q[3]);
+        *reinterpret_cast<uint4*>(act + kPlane + off) = make_uint4(q[4], q[5], q[6], q[7]);
       } else if (inside && x >= kHalo && x < kHalo + kTW && row >= kHalo && row < kHalo + kTH) {
         const long long o = (long long)b * g.len + g.G + gx + p * gy;
         if (y) y[o] = v[0];
