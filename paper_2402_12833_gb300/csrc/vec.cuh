@@ -44,26 +44,65 @@ struct Vec<double> {
   }
 };
 
+// Number of values a lane holds after `steps` halvings of nv values.
+__host__ __device__ constexpr int rs_count(int nv, int steps) {
+  return steps == 0 ? nv : rs_count((nv + 1) / 2, steps - 1);
+}
+
+// One butterfly reduce-scatter step across lanes `o` apart: the lane pair
+// splits its K values into a lower and an upper half (the upper half padded
+// with zeros to H values); the lane without bit o keeps the lower half, the
+// other the upper half, each adding its partner's copy.  `base` and `nvalid`
+// track the first value index of the lane's half and how many of its values
+// are real (an odd split leaves padding that must not claim an index).
+template <typename T, int NV, int K, int O>
+__device__ __forceinline__ void rs_step(T (&a)[NV], int& base, int& nvalid, int lane) {
+  constexpr int H = (K + 1) / 2;
+  const bool up = (lane & O) != 0;
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    const T lo = a[i];
+    const T hi = (H + i < K) ? a[H + i] : T(0);
+    const T send = up ? lo : hi;
+    const T keep = up ? hi : lo;
+    a[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+  }
+  if (up) {
+    base += H;
+    nvalid = nvalid > H ? nvalid - H : 0;
+  } else {
+    nvalid = nvalid < H ? nvalid : H;
+  }
+}
+
 // Block sum of NV per-thread values, written to part[i * stride + slot].
-// The warp stage sums in T (FP32 in the FP32 path: a fixed pairwise tree over
-// 32 lanes); the cross-warp stage sums in FP64 in a fixed order.  Every
-// thread of the block must call it.
+// The warp stage sums in T (FP32 in the FP32 path) by a butterfly
+// reduce-scatter (lane pairs 16, 8, 4, 2, 1 apart exchange half of their
+// values, so a warp spends about NV shuffles instead of 5 NV); the
+// cross-warp stage sums in FP64 in a fixed order.  Every thread of the block
+// must call it.
 template <typename T, int NV>
 __device__ __forceinline__ void block_sum_store(const T (&v)[NV], double* part, long long stride, int slot) {
   __shared__ double sh[kBlock / 32][NV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T a[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    T a = v[i];
+  for (int i = 0; i < NV; ++i) a[i] = v[i];
+  int base = 0, nvalid = NV;
+  rs_step<T, NV, rs_count(NV, 0), 16>(a, base, nvalid, lane);
+  rs_step<T, NV, rs_count(NV, 1), 8>(a, base, nvalid, lane);
+  rs_step<T, NV, rs_count(NV, 2), 4>(a, base, nvalid, lane);
+  rs_step<T, NV, rs_count(NV, 3), 2>(a, base, nvalid, lane);
+  rs_step<T, NV, rs_count(NV, 4), 1>(a, base, nvalid, lane);
+  constexpr int K5 = rs_count(NV, 5);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) sh[warp][i] = (double)a;
-  }
+  for (int i = 0; i < K5; ++i)
+    if (i < nvalid) sh[warp][base + i] = (double)a[i];
   __syncthreads();
   for (int i = threadIdx.x; i < NV; i += blockDim.x) {
-    double a = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += sh[w][i];
-    part[(long long)i * stride + slot] = a;
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w][i];
+    part[(long long)i * stride + slot] = s;
   }
 }
 
