@@ -40,17 +40,56 @@ __global__ void k_unpack(GridDesc g, const TI* __restrict__ src, TO* __restrict_
   }
 }
 
+// Lanes of a warp take consecutive groups of W points, so the neighbours
+// v[-1] and v[W] of a group are the last element of the left lane's vector
+// and the first of the right lane's: they come by warp shuffles, and only a
+// lane whose neighbour lane is idle (warp edge, tail) loads them itself.
+struct WarpRow {
+  int lane;
+  bool active;     // this lane has a group
+  unsigned act;    // active lanes of the warp
+};
+
+__device__ __forceinline__ WarpRow warp_row(bool active) {
+  WarpRow w;
+  w.lane = threadIdx.x & 31;
+  w.active = active;
+  w.act = __ballot_sync(0xffffffffu, active);
+  return w;
+}
+
 // A grid row segment around a group: v[-1], v[0..W-1] (one aligned vector
-// load), v[W].  Returned as e[0..W+1] with e[k] = v[k-1].
+// load), v[W].  Returned as e[0..W+1] with e[k] = v[k-1].  Every lane of the
+// warp must call it (idle lanes read nothing).
 template <typename T>
-__device__ __forceinline__ void load_row(const T* __restrict__ p, T (&e)[Vec<T>::W + 2]) {
+__device__ __forceinline__ void load_row(const T* __restrict__ p, T (&e)[Vec<T>::W + 2], const WarpRow& wr) {
   constexpr int W = Vec<T>::W;
   T mid[W];
-  Vec<T>::load_keep(p, mid);
-  e[0] = p[-1];
+  if (wr.active) Vec<T>::load_keep(p, mid);
+  else {
+#pragma unroll
+    for (int w = 0; w < W; ++w) mid[w] = 0;
+  }
+  T left = __shfl_up_sync(0xffffffffu, mid[W - 1], 1);
+  T right = __shfl_down_sync(0xffffffffu, mid[0], 1);
+  const bool lnb = wr.lane > 0 && ((wr.act >> (wr.lane - 1)) & 1u);
+  const bool rnb = wr.lane < 31 && ((wr.act >> (wr.lane + 1)) & 1u);
+  if (wr.active && !lnb) left = p[-1];
+  if (wr.active && !rnb) right = p[W];
+  e[0] = left;
 #pragma unroll
   for (int w = 0; w < W; ++w) e[w + 1] = mid[w];
-  e[W + 1] = p[W];
+  e[W + 1] = right;
+}
+
+// Plane coefficients of a group (zero for an idle lane).
+template <typename T>
+__device__ __forceinline__ void load_plane(const T* __restrict__ p, T (&v)[Vec<T>::W], bool active) {
+  if (active) Vec<T>::load(p, v);
+  else {
+#pragma unroll
+    for (int w = 0; w < Vec<T>::W; ++w) v[w] = 0;
+  }
 }
 
 // Row offsets of the 3^DIM stencil around the group start, row k = dy + 3 dz.
@@ -65,20 +104,20 @@ __device__ __forceinline__ long long row_offset(int k, long long px, long long p
 template <typename T, int DIM, int C>
 __device__ __forceinline__ void stencil_group(const T* __restrict__ st, long long pitch, const T* __restrict__ X,
                                               long long idx, long long px, long long pxy,
-                                              T (&acc)[C][Vec<T>::W]) {
+                                              T (&acc)[C][Vec<T>::W], const WarpRow& wr) {
   constexpr int W = Vec<T>::W;
   constexpr int R = DIM == 3 ? 9 : 3;
 #pragma unroll
   for (int k = 0; k < R; ++k) {
     const long long ro = row_offset<DIM>(k, px, pxy);
     T a0[W], a1[W], a2[W];
-    Vec<T>::load(st + (long long)(3 * k + 0) * pitch + idx, a0);
-    Vec<T>::load(st + (long long)(3 * k + 1) * pitch + idx, a1);
-    Vec<T>::load(st + (long long)(3 * k + 2) * pitch + idx, a2);
+    load_plane<T>(st + (long long)(3 * k + 0) * pitch + idx, a0, wr.active);
+    load_plane<T>(st + (long long)(3 * k + 1) * pitch + idx, a1, wr.active);
+    load_plane<T>(st + (long long)(3 * k + 2) * pitch + idx, a2, wr.active);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       T e[W + 2];
-      load_row<T>(X + (long long)c * pitch + idx + ro, e);
+      load_row<T>(X + (long long)c * pitch + idx + ro, e, wr);
 #pragma unroll
       for (int w = 0; w < W; ++w) {
         acc[c][w] = fma(a0[w], e[w], acc[c][w]);
@@ -90,7 +129,7 @@ __device__ __forceinline__ void stencil_group(const T* __restrict__ st, long lon
 }
 
 template <typename T, int DIM, int C, bool ZAZ>
-__global__ void __launch_bounds__(kBlock) k_spmm(GridDesc g, const T* __restrict__ st, const T* __restrict__ X,
+__global__ void __launch_bounds__(kBlock, C <= 8 ? 3 : 2) k_spmm(GridDesc g, const T* __restrict__ st, const T* __restrict__ X,
                                                  T* __restrict__ Y, double* zaz, const DevState* state) {
   const int pb = blockIdx.y;
   if (state && state[pb].done) return;
@@ -100,15 +139,18 @@ __global__ void __launch_bounds__(kBlock) k_spmm(GridDesc g, const T* __restrict
 #pragma unroll
   for (int c = 0; c < (ZAZ ? C : 1); ++c) zacc[c] = 0;
   const long long ngroups = g.npts / W;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
-       q += (long long)gridDim.x * blockDim.x) {
+  for (long long q0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); q0 < ngroups;
+       q0 += (long long)gridDim.x * blockDim.x) {
+    const long long q = q0 + (threadIdx.x & 31);
+    const WarpRow wr = warp_row(q < ngroups);
     const long long idx = bo + g.G + q * W;
     T acc[C][W];
 #pragma unroll
     for (int c = 0; c < C; ++c)
 #pragma unroll
       for (int w = 0; w < W; ++w) acc[c][w] = 0;
-    stencil_group<T, DIM, C>(st, g.cp, X, idx, g.px, g.pxy, acc);
+    stencil_group<T, DIM, C>(st, g.cp, X, idx, g.px, g.pxy, acc, wr);
+    if (!wr.active) continue;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       Vec<T>::store(Y + (long long)c * g.cp + idx, acc[c]);
@@ -131,13 +173,16 @@ __global__ void __launch_bounds__(kBlock) k_residual(GridDesc g, const T* __rest
   const long long bo = (long long)pb * g.len;
   T sums[2] = {0, 0};
   const long long ngroups = g.npts / W;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
-       q += (long long)gridDim.x * blockDim.x) {
+  for (long long q0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); q0 < ngroups;
+       q0 += (long long)gridDim.x * blockDim.x) {
+    const long long q = q0 + (threadIdx.x & 31);
+    const WarpRow wr = warp_row(q < ngroups);
     const long long idx = bo + g.G + q * W;
     T acc[1][W];
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[0][w] = 0;
-    stencil_group<T, DIM, 1>(st, g.cp, xv, idx, g.px, g.pxy, acc);
+    stencil_group<T, DIM, 1>(st, g.cp, xv, idx, g.px, g.pxy, acc, wr);
+    if (!wr.active) continue;
     T bv[W], rv[W];
     Vec<T>::load(b + idx, bv);
 #pragma unroll
@@ -195,19 +240,24 @@ __global__ void __launch_bounds__(kBlock) k_restrict(GridDesc gf, GridDesc gc, c
 //           at the neighbours on the fly)
 //   mode 2: out = sin + dinv (r - A sin)           (a further sweep)
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kBlock) k_jacobi(GridDesc g, const T* __restrict__ st, const T* __restrict__ dinv,
+__global__ void __launch_bounds__(kBlock, 4) k_jacobi(GridDesc g, const T* __restrict__ st, const T* __restrict__ dinv,
                                                    const T* __restrict__ r, const T* __restrict__ sin,
                                                    T* __restrict__ out, int mode, const DevState* state) {
   const int pb = blockIdx.y;
   if (state && state[pb].done) return;
   constexpr int W = Vec<T>::W;
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= g.npts / W) return;
+  const long long q0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31);
+  if (q0 >= g.npts / W) return;   // whole warp idle
+  const long long q = q0 + (threadIdx.x & 31);
+  const WarpRow wr = warp_row(q < g.npts / W);
   const long long idx = (long long)pb * g.len + g.G + q * W;
-  T di[W], ri[W], o[W];
-  Vec<T>::load_keep(dinv + idx, di);
-  Vec<T>::load_keep(r + idx, ri);
+  T di[W] = {}, ri[W] = {}, o[W];
+  if (wr.active) {
+    Vec<T>::load_keep(dinv + idx, di);
+    Vec<T>::load_keep(r + idx, ri);
+  }
   if (mode == 0) {
+    if (!wr.active) return;
 #pragma unroll
     for (int w = 0; w < W; ++w) o[w] = di[w] * ri[w];
     Vec<T>::store(out + idx, o);
@@ -222,11 +272,11 @@ __global__ void __launch_bounds__(kBlock) k_jacobi(GridDesc g, const T* __restri
     for (int k = 0; k < R; ++k) {
       const long long ro = row_offset<DIM>(k, g.px, g.pxy);
       T a0[W], a1[W], a2[W], ed[W + 2], er[W + 2];
-      Vec<T>::load(st + (long long)(3 * k + 0) * g.cp + idx, a0);
-      Vec<T>::load(st + (long long)(3 * k + 1) * g.cp + idx, a1);
-      Vec<T>::load(st + (long long)(3 * k + 2) * g.cp + idx, a2);
-      load_row<T>(dinv + idx + ro, ed);
-      load_row<T>(r + idx + ro, er);
+      load_plane<T>(st + (long long)(3 * k + 0) * g.cp + idx, a0, wr.active);
+      load_plane<T>(st + (long long)(3 * k + 1) * g.cp + idx, a1, wr.active);
+      load_plane<T>(st + (long long)(3 * k + 2) * g.cp + idx, a2, wr.active);
+      load_row<T>(dinv + idx + ro, ed, wr);
+      load_row<T>(r + idx + ro, er, wr);
 #pragma unroll
       for (int w = 0; w < W; ++w) {
         acc[0][w] = fma(a0[w], ed[w] * er[w], acc[0][w]);
@@ -240,13 +290,14 @@ __global__ void __launch_bounds__(kBlock) k_jacobi(GridDesc g, const T* __restri
       o[w] = s1 + di[w] * (ri[w] - acc[0][w]);
     }
   } else {
-    stencil_group<T, DIM, 1>(st, g.cp, sin, idx, g.px, g.pxy, acc);
+    stencil_group<T, DIM, 1>(st, g.cp, sin, idx, g.px, g.pxy, acc, wr);
+    if (!wr.active) return;
     T sv[W];
     Vec<T>::load_keep(sin + idx, sv);
 #pragma unroll
     for (int w = 0; w < W; ++w) o[w] = sv[w] + di[w] * (ri[w] - acc[0][w]);
   }
-  Vec<T>::store(out + idx, o);
+  if (wr.active) Vec<T>::store(out + idx, o);
 }
 
 // Prolongation P: bilinear / trilinear interpolation from the coarse grid.
@@ -463,9 +514,12 @@ __global__ void __launch_bounds__(kBlock) k_vspmm(GridDesc g, const T* __restric
 #pragma unroll
   for (int c = 0; c < (ZAZ ? C : 1); ++c) zacc[c] = 0;
   const long long ngroups = cs / W;
-  for (long long item = blockIdx.x * (long long)blockDim.x + threadIdx.x; item < 3 * ngroups;
-       item += (long long)gridDim.x * blockDim.x) {
-    const int a = (int)(item / ngroups);
+  for (long long i0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); i0 < 3 * ngroups;
+       i0 += (long long)gridDim.x * blockDim.x) {
+    // consecutive items are contiguous groups, also across a component change
+    const long long item = i0 + (threadIdx.x & 31);
+    const WarpRow wr = warp_row(item < 3 * ngroups);
+    const int a = wr.active ? (int)(item / ngroups) : 0;
     const long long idx0 = bo + g.G + (item - a * ngroups) * W;
     T acc[C][W];
 #pragma unroll
@@ -479,13 +533,13 @@ __global__ void __launch_bounds__(kBlock) k_vspmm(GridDesc g, const T* __restric
       for (int b = 0; b < 3; ++b) {
         const T* sp = st + (long long)(b * 27 + 3 * k) * g.cp + idx0 + a * cs;
         T a0[W], a1[W], a2[W];
-        Vec<T>::load(sp, a0);
-        Vec<T>::load(sp + g.cp, a1);
-        Vec<T>::load(sp + 2 * g.cp, a2);
+        load_plane<T>(sp, a0, wr.active);
+        load_plane<T>(sp + g.cp, a1, wr.active);
+        load_plane<T>(sp + 2 * g.cp, a2, wr.active);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           T e[W + 2];
-          load_row<T>(X + (long long)c * g.cp + idx0 + b * cs + ro, e);
+          load_row<T>(X + (long long)c * g.cp + idx0 + b * cs + ro, e, wr);
 #pragma unroll
           for (int w = 0; w < W; ++w) {
             acc[c][w] = fma(a0[w], e[w], acc[c][w]);
@@ -495,6 +549,7 @@ __global__ void __launch_bounds__(kBlock) k_vspmm(GridDesc g, const T* __restric
         }
       }
     }
+    if (!wr.active) continue;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       const long long o = (long long)c * g.cp + idx0 + a * cs;
@@ -526,9 +581,11 @@ __global__ void __launch_bounds__(kBlock, 3) k_vres(GridDesc g, const T* __restr
   const long long cs = g.cstride;
   const long long ngroups = cs / W;
   T sums[2] = {0, 0};
-  for (long long item = blockIdx.x * (long long)blockDim.x + threadIdx.x; item < 3 * ngroups;
-       item += NORMS ? (long long)gridDim.x * blockDim.x : 3 * ngroups) {
-    const int a = (int)(item / ngroups);
+  for (long long i0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); i0 < 3 * ngroups;
+       i0 += NORMS ? (long long)gridDim.x * blockDim.x : 3 * ngroups) {
+    const long long item = i0 + (threadIdx.x & 31);
+    const WarpRow wr = warp_row(item < 3 * ngroups);
+    const int a = wr.active ? (int)(item / ngroups) : 0;
     const long long idx0 = bo + g.G + (item - a * ngroups) * W;
     T acc[W];
 #pragma unroll
@@ -540,10 +597,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_vres(GridDesc g, const T* __restr
       for (int bb = 0; bb < 3; ++bb) {
         const T* sp = st + (long long)(bb * 27 + 3 * k) * g.cp + idx0 + a * cs;
         T a0[W], a1[W], a2[W], e[W + 2];
-        Vec<T>::load(sp, a0);
-        Vec<T>::load(sp + g.cp, a1);
-        Vec<T>::load(sp + 2 * g.cp, a2);
-        load_row<T>(xv + idx0 + bb * cs + ro, e);
+        load_plane<T>(sp, a0, wr.active);
+        load_plane<T>(sp + g.cp, a1, wr.active);
+        load_plane<T>(sp + 2 * g.cp, a2, wr.active);
+        load_row<T>(xv + idx0 + bb * cs + ro, e, wr);
 #pragma unroll
         for (int w = 0; w < W; ++w) {
           acc[w] = fma(a0[w], e[w], acc[w]);
@@ -552,6 +609,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_vres(GridDesc g, const T* __restr
         }
       }
     }
+    if (!wr.active) continue;
     T bv[W], rv[W];
     Vec<T>::load(b + idx0 + a * cs, bv);
 #pragma unroll
