@@ -40,56 +40,46 @@ __global__ void k_unpack(GridDesc g, const TI* __restrict__ src, TO* __restrict_
   }
 }
 
-// Lanes of a warp take consecutive groups of W points, so the neighbours
-// v[-1] and v[W] of a group are the last element of the left lane's vector
-// and the first of the right lane's: they come by warp shuffles, and only a
-// lane whose neighbour lane is idle (warp edge, tail) loads them itself.
-struct WarpRow {
-  int lane;
-  bool active;     // this lane has a group
-  unsigned act;    // active lanes of the warp
-};
-
-__device__ __forceinline__ WarpRow warp_row(bool active) {
-  WarpRow w;
-  w.lane = threadIdx.x & 31;
-  w.active = active;
-  w.act = __ballot_sync(0xffffffffu, active);
-  return w;
-}
-
 // A grid row segment around a group: v[-1], v[0..W-1] (one aligned vector
-// load), v[W].  Returned as e[0..W+1] with e[k] = v[k-1].  Every lane of the
-// warp must call it (idle lanes read nothing).
+// load), v[W].  Returned as e[0..W+1] with e[k] = v[k-1].
 template <typename T>
-__device__ __forceinline__ void load_row(const T* __restrict__ p, T (&e)[Vec<T>::W + 2], const WarpRow& wr) {
+__device__ __forceinline__ void load_row(const T* __restrict__ p, T (&e)[Vec<T>::W + 2]) {
   constexpr int W = Vec<T>::W;
   T mid[W];
-  if (wr.active) Vec<T>::load_keep(p, mid);
+  Vec<T>::load_keep(p, mid);
+  e[0] = p[-1];
+#pragma unroll
+  for (int w = 0; w < W; ++w) e[w + 1] = mid[w];
+  e[W + 1] = p[W];
+}
+
+// The same row segment with the neighbours v[-1] and v[W] taken from the
+// adjacent lanes' vectors by warp shuffles (lanes of a warp hold consecutive
+// groups); a lane whose neighbour lane is idle (warp edge, tail) loads them
+// itself.  Every lane of the warp must call it; an idle lane (active =
+// false) reads nothing.  Fewer L1 wavefronts than the scalar loads; used by
+// the Jacobi sweep, which reads two rows per stencil row (measured faster
+// there, slower in the multi-column SpMM, whose loads then wait longer).
+template <typename T>
+__device__ __forceinline__ void load_row_shfl(const T* __restrict__ p, T (&e)[Vec<T>::W + 2], bool active,
+                                              unsigned act, int lane) {
+  constexpr int W = Vec<T>::W;
+  T mid[W];
+  if (active) Vec<T>::load_keep(p, mid);
   else {
 #pragma unroll
     for (int w = 0; w < W; ++w) mid[w] = 0;
   }
   T left = __shfl_up_sync(0xffffffffu, mid[W - 1], 1);
   T right = __shfl_down_sync(0xffffffffu, mid[0], 1);
-  const bool lnb = wr.lane > 0 && ((wr.act >> (wr.lane - 1)) & 1u);
-  const bool rnb = wr.lane < 31 && ((wr.act >> (wr.lane + 1)) & 1u);
-  if (wr.active && !lnb) left = p[-1];
-  if (wr.active && !rnb) right = p[W];
+  const bool lnb = lane > 0 && ((act >> (lane - 1)) & 1u);
+  const bool rnb = lane < 31 && ((act >> (lane + 1)) & 1u);
+  if (active && !lnb) left = p[-1];
+  if (active && !rnb) right = p[W];
   e[0] = left;
 #pragma unroll
   for (int w = 0; w < W; ++w) e[w + 1] = mid[w];
   e[W + 1] = right;
-}
-
-// Plane coefficients of a group (zero for an idle lane).
-template <typename T>
-__device__ __forceinline__ void load_plane(const T* __restrict__ p, T (&v)[Vec<T>::W], bool active) {
-  if (active) Vec<T>::load(p, v);
-  else {
-#pragma unroll
-    for (int w = 0; w < Vec<T>::W; ++w) v[w] = 0;
-  }
 }
 
 // Row offsets of the 3^DIM stencil around the group start, row k = dy + 3 dz.
@@ -104,20 +94,20 @@ __device__ __forceinline__ long long row_offset(int k, long long px, long long p
 template <typename T, int DIM, int C>
 __device__ __forceinline__ void stencil_group(const T* __restrict__ st, long long pitch, const T* __restrict__ X,
                                               long long idx, long long px, long long pxy,
-                                              T (&acc)[C][Vec<T>::W], const WarpRow& wr) {
+                                              T (&acc)[C][Vec<T>::W]) {
   constexpr int W = Vec<T>::W;
   constexpr int R = DIM == 3 ? 9 : 3;
 #pragma unroll
   for (int k = 0; k < R; ++k) {
     const long long ro = row_offset<DIM>(k, px, pxy);
     T a0[W], a1[W], a2[W];
-    load_plane<T>(st + (long long)(3 * k + 0) * pitch + idx, a0, wr.active);
-    load_plane<T>(st + (long long)(3 * k + 1) * pitch + idx, a1, wr.active);
-    load_plane<T>(st + (long long)(3 * k + 2) * pitch + idx, a2, wr.active);
+    Vec<T>::load(st + (long long)(3 * k + 0) * pitch + idx, a0);
+    Vec<T>::load(st + (long long)(3 * k + 1) * pitch + idx, a1);
+    Vec<T>::load(st + (long long)(3 * k + 2) * pitch + idx, a2);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       T e[W + 2];
-      load_row<T>(X + (long long)c * pitch + idx + ro, e, wr);
+      load_row<T>(X + (long long)c * pitch + idx + ro, e);
 #pragma unroll
       for (int w = 0; w < W; ++w) {
         acc[c][w] = fma(a0[w], e[w], acc[c][w]);
@@ -129,7 +119,7 @@ __device__ __forceinline__ void stencil_group(const T* __restrict__ st, long lon
 }
 
 template <typename T, int DIM, int C, bool ZAZ>
-__global__ void __launch_bounds__(kBlock, C <= 8 ? 3 : 2) k_spmm(GridDesc g, const T* __restrict__ st, const T* __restrict__ X,
+__global__ void __launch_bounds__(kBlock) k_spmm(GridDesc g, const T* __restrict__ st, const T* __restrict__ X,
                                                  T* __restrict__ Y, double* zaz, const DevState* state) {
   const int pb = blockIdx.y;
   if (state && state[pb].done) return;
@@ -139,18 +129,15 @@ __global__ void __launch_bounds__(kBlock, C <= 8 ? 3 : 2) k_spmm(GridDesc g, con
 #pragma unroll
   for (int c = 0; c < (ZAZ ? C : 1); ++c) zacc[c] = 0;
   const long long ngroups = g.npts / W;
-  for (long long q0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); q0 < ngroups;
-       q0 += (long long)gridDim.x * blockDim.x) {
-    const long long q = q0 + (threadIdx.x & 31);
-    const WarpRow wr = warp_row(q < ngroups);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
+       q += (long long)gridDim.x * blockDim.x) {
     const long long idx = bo + g.G + q * W;
     T acc[C][W];
 #pragma unroll
     for (int c = 0; c < C; ++c)
 #pragma unroll
       for (int w = 0; w < W; ++w) acc[c][w] = 0;
-    stencil_group<T, DIM, C>(st, g.cp, X, idx, g.px, g.pxy, acc, wr);
-    if (!wr.active) continue;
+    stencil_group<T, DIM, C>(st, g.cp, X, idx, g.px, g.pxy, acc);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       Vec<T>::store(Y + (long long)c * g.cp + idx, acc[c]);
@@ -173,16 +160,13 @@ __global__ void __launch_bounds__(kBlock) k_residual(GridDesc g, const T* __rest
   const long long bo = (long long)pb * g.len;
   T sums[2] = {0, 0};
   const long long ngroups = g.npts / W;
-  for (long long q0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); q0 < ngroups;
-       q0 += (long long)gridDim.x * blockDim.x) {
-    const long long q = q0 + (threadIdx.x & 31);
-    const WarpRow wr = warp_row(q < ngroups);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
+       q += (long long)gridDim.x * blockDim.x) {
     const long long idx = bo + g.G + q * W;
     T acc[1][W];
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[0][w] = 0;
-    stencil_group<T, DIM, 1>(st, g.cp, xv, idx, g.px, g.pxy, acc, wr);
-    if (!wr.active) continue;
+    stencil_group<T, DIM, 1>(st, g.cp, xv, idx, g.px, g.pxy, acc);
     T bv[W], rv[W];
     Vec<T>::load(b + idx, bv);
 #pragma unroll
@@ -246,18 +230,20 @@ __global__ void __launch_bounds__(kBlock, 4) k_jacobi(GridDesc g, const T* __res
   const int pb = blockIdx.y;
   if (state && state[pb].done) return;
   constexpr int W = Vec<T>::W;
+  const long long ngroups = g.npts / W;
   const long long q0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31);
-  if (q0 >= g.npts / W) return;   // whole warp idle
-  const long long q = q0 + (threadIdx.x & 31);
-  const WarpRow wr = warp_row(q < g.npts / W);
+  if (q0 >= ngroups) return;   // the whole warp is idle
+  const int lane = threadIdx.x & 31;
+  const long long q = q0 + lane;
+  const bool active = q < ngroups;
   const long long idx = (long long)pb * g.len + g.G + q * W;
   T di[W] = {}, ri[W] = {}, o[W];
-  if (wr.active) {
+  if (active) {
     Vec<T>::load_keep(dinv + idx, di);
     Vec<T>::load_keep(r + idx, ri);
   }
   if (mode == 0) {
-    if (!wr.active) return;
+    if (!active) return;
 #pragma unroll
     for (int w = 0; w < W; ++w) o[w] = di[w] * ri[w];
     Vec<T>::store(out + idx, o);
@@ -267,16 +253,19 @@ __global__ void __launch_bounds__(kBlock, 4) k_jacobi(GridDesc g, const T* __res
 #pragma unroll
   for (int w = 0; w < W; ++w) acc[0][w] = 0;
   if (mode == 1) {
+    const unsigned act = __ballot_sync(0xffffffffu, active);
     constexpr int R = DIM == 3 ? 9 : 3;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
       const long long ro = row_offset<DIM>(k, g.px, g.pxy);
-      T a0[W], a1[W], a2[W], ed[W + 2], er[W + 2];
-      load_plane<T>(st + (long long)(3 * k + 0) * g.cp + idx, a0, wr.active);
-      load_plane<T>(st + (long long)(3 * k + 1) * g.cp + idx, a1, wr.active);
-      load_plane<T>(st + (long long)(3 * k + 2) * g.cp + idx, a2, wr.active);
-      load_row<T>(dinv + idx + ro, ed, wr);
-      load_row<T>(r + idx + ro, er, wr);
+      T a0[W] = {}, a1[W] = {}, a2[W] = {}, ed[W + 2], er[W + 2];
+      if (active) {
+        Vec<T>::load(st + (long long)(3 * k + 0) * g.cp + idx, a0);
+        Vec<T>::load(st + (long long)(3 * k + 1) * g.cp + idx, a1);
+        Vec<T>::load(st + (long long)(3 * k + 2) * g.cp + idx, a2);
+      }
+      load_row_shfl<T>(dinv + idx + ro, ed, active, act, lane);
+      load_row_shfl<T>(r + idx + ro, er, active, act, lane);
 #pragma unroll
       for (int w = 0; w < W; ++w) {
         acc[0][w] = fma(a0[w], ed[w] * er[w], acc[0][w]);
@@ -290,14 +279,14 @@ __global__ void __launch_bounds__(kBlock, 4) k_jacobi(GridDesc g, const T* __res
       o[w] = s1 + di[w] * (ri[w] - acc[0][w]);
     }
   } else {
-    stencil_group<T, DIM, 1>(st, g.cp, sin, idx, g.px, g.pxy, acc, wr);
-    if (!wr.active) return;
+    if (!active) return;
+    stencil_group<T, DIM, 1>(st, g.cp, sin, idx, g.px, g.pxy, acc);
     T sv[W];
     Vec<T>::load_keep(sin + idx, sv);
 #pragma unroll
     for (int w = 0; w < W; ++w) o[w] = sv[w] + di[w] * (ri[w] - acc[0][w]);
   }
-  if (wr.active) Vec<T>::store(out + idx, o);
+  if (active) Vec<T>::store(out + idx, o);
 }
 
 // Prolongation P: bilinear / trilinear interpolation from the coarse grid.
@@ -514,12 +503,9 @@ __global__ void __launch_bounds__(kBlock) k_vspmm(GridDesc g, const T* __restric
 #pragma unroll
   for (int c = 0; c < (ZAZ ? C : 1); ++c) zacc[c] = 0;
   const long long ngroups = cs / W;
-  for (long long i0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); i0 < 3 * ngroups;
-       i0 += (long long)gridDim.x * blockDim.x) {
-    // consecutive items are contiguous groups, also across a component change
-    const long long item = i0 + (threadIdx.x & 31);
-    const WarpRow wr = warp_row(item < 3 * ngroups);
-    const int a = wr.active ? (int)(item / ngroups) : 0;
+  for (long long item = blockIdx.x * (long long)blockDim.x + threadIdx.x; item < 3 * ngroups;
+       item += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(item / ngroups);
     const long long idx0 = bo + g.G + (item - a * ngroups) * W;
     T acc[C][W];
 #pragma unroll
@@ -533,13 +519,13 @@ __global__ void __launch_bounds__(kBlock) k_vspmm(GridDesc g, const T* __restric
       for (int b = 0; b < 3; ++b) {
         const T* sp = st + (long long)(b * 27 + 3 * k) * g.cp + idx0 + a * cs;
         T a0[W], a1[W], a2[W];
-        load_plane<T>(sp, a0, wr.active);
-        load_plane<T>(sp + g.cp, a1, wr.active);
-        load_plane<T>(sp + 2 * g.cp, a2, wr.active);
+        Vec<T>::load(sp, a0);
+        Vec<T>::load(sp + g.cp, a1);
+        Vec<T>::load(sp + 2 * g.cp, a2);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           T e[W + 2];
-          load_row<T>(X + (long long)c * g.cp + idx0 + b * cs + ro, e, wr);
+          load_row<T>(X + (long long)c * g.cp + idx0 + b * cs + ro, e);
 #pragma unroll
           for (int w = 0; w < W; ++w) {
             acc[c][w] = fma(a0[w], e[w], acc[c][w]);
@@ -549,7 +535,6 @@ __global__ void __launch_bounds__(kBlock) k_vspmm(GridDesc g, const T* __restric
         }
       }
     }
-    if (!wr.active) continue;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       const long long o = (long long)c * g.cp + idx0 + a * cs;
@@ -581,11 +566,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_vres(GridDesc g, const T* __restr
   const long long cs = g.cstride;
   const long long ngroups = cs / W;
   T sums[2] = {0, 0};
-  for (long long i0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); i0 < 3 * ngroups;
-       i0 += NORMS ? (long long)gridDim.x * blockDim.x : 3 * ngroups) {
-    const long long item = i0 + (threadIdx.x & 31);
-    const WarpRow wr = warp_row(item < 3 * ngroups);
-    const int a = wr.active ? (int)(item / ngroups) : 0;
+  for (long long item = blockIdx.x * (long long)blockDim.x + threadIdx.x; item < 3 * ngroups;
+       item += NORMS ? (long long)gridDim.x * blockDim.x : 3 * ngroups) {
+    const int a = (int)(item / ngroups);
     const long long idx0 = bo + g.G + (item - a * ngroups) * W;
     T acc[W];
 #pragma unroll
@@ -597,10 +580,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_vres(GridDesc g, const T* __restr
       for (int bb = 0; bb < 3; ++bb) {
         const T* sp = st + (long long)(bb * 27 + 3 * k) * g.cp + idx0 + a * cs;
         T a0[W], a1[W], a2[W], e[W + 2];
-        load_plane<T>(sp, a0, wr.active);
-        load_plane<T>(sp + g.cp, a1, wr.active);
-        load_plane<T>(sp + 2 * g.cp, a2, wr.active);
-        load_row<T>(xv + idx0 + bb * cs + ro, e, wr);
+        Vec<T>::load(sp, a0);
+        Vec<T>::load(sp + g.cp, a1);
+        Vec<T>::load(sp + 2 * g.cp, a2);
+        load_row<T>(xv + idx0 + bb * cs + ro, e);
 #pragma unroll
         for (int w = 0; w < W; ++w) {
           acc[w] = fma(a0[w], e[w], acc[w]);
@@ -609,7 +592,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_vres(GridDesc g, const T* __restr
         }
       }
     }
-    if (!wr.active) continue;
     T bv[W], rv[W];
     Vec<T>::load(b + idx0 + a * cs, bv);
 #pragma unroll
