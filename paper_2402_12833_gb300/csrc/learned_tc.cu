@@ -34,11 +34,13 @@
 // by then every MMA that reads input row r - 1 (rows r - 2 .. r) is done, and
 // the commits complete in issue order.  This halves the shared memory, so two
 // CTAs share an SM and hide each other's latencies.
-// Per layer the issuing thread enqueues the MMAs of all
-// rows at once, each row into its own TMEM columns and signalling its own
-// mbarrier, and every warp drains the rows in order as they complete (a
-// warp reads only its own 32 TMEM lanes, so no block barrier is needed
-// between rows).
+// Two warpgroups split the rows of a layer by parity: the first thread of
+// each enqueues the MMAs of its rows at once, each row into its own TMEM
+// columns and signalling its own mbarrier, and its four warps drain those
+// rows in order as they complete (a warp reads only its own 32 TMEM lanes,
+// so no block barrier is needed between rows).  A commit covers only its
+// issuing thread's MMAs, so before overwriting input row r - 1 a warpgroup
+// also waits for row r - 1 of the other parity.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -56,13 +58,13 @@ constexpr int kEH = kTH + 2 * kHalo;   // 16
 constexpr int kXS = kEW + 2;           // stored row length: x = -1 and x = 128 are zero columns
 constexpr int kNPix = kEH * kXS;       // pixels of one activation buffer
 constexpr int kPlane = kNPix * 16;     // bytes of one channel plane
-constexpr int kThreads = 128;          // four warps: TMEM lanes 0..127
+constexpr int kThreads = 256;          // two warpgroups; warp w reads TMEM lanes 32 (w % 4) ..
 constexpr int kMaxRows = kEH - 2;      // rows computed by the first layer
 constexpr int kTmemCols = 256;         // one 16-column accumulator per row of a layer
 constexpr long long kWaitLimit = 1LL << 22;
 
-static_assert(kEW == kThreads, "one thread per tile column");
-static_assert(kEH == 16 && kThreads == 128, "halo-column zeroing maps 16 rows x 2 sides x 2 planes (x 2 passes)");
+static_assert(kEW * 2 == kThreads, "one thread per tile column in each warpgroup");
+static_assert(kEH == 16, "halo-column zeroing maps 16 rows x 2 sides x 2 planes");
 
 // shared memory map (bytes): one activation buffer, updated in place
 constexpr int kActBytes = 2 * kPlane;                // two planes
@@ -171,7 +173,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 8 * kMaxRows);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, wg = tid >> 7, lanes = (warp & 3) * 32;
+  const int x = tid & 127;   // tile column of this thread in its warpgroup
   const int b = blockIdx.z;
   const int gx0 = blockIdx.x * kTW - kHalo, gy0 = blockIdx.y * kTH - kHalo;
   const int n1 = g.n1;
@@ -193,26 +196,28 @@ __global__ void __launch_bounds__(kThreads, 2)
         make_uint4(0, 0, 0, 0);
   }
   for (int i = tid; i < kWBytes / 16; i += kThreads) reinterpret_cast<uint4*>(smem + kOffW)[i] = wtc[i];
-  // input tile (thread = column x, all 16 rows, loads issued together):
-  // channel 0 = bf16(r / ||r||), channel 1 = bf16(c), zero outside the grid
+  // input tile (thread = column x, eight rows per warpgroup, loads issued
+  // together): channel 0 = bf16(r / ||r||), channel 1 = bf16(c), zero
+  // outside the grid
   {
     const float sc = state ? (float)(state->rnorm > 0.0 ? 1.0 / state->rnorm : 0.0) : 1.f;
     const T* rb = r + (long long)b * r_ld;
-    const int gxx = gx0 + tid;
+    const int gxx = gx0 + x;
     const bool colok = gxx >= 0 && gxx < n1;
-    float v0[kEH], v1[kEH];
+    constexpr int kRows = kEH / 2;
+    float v0[kRows], v1[kRows];
 #pragma unroll
-    for (int yy = 0; yy < kEH; ++yy) {
-      const int gy = gy0 + yy;
+    for (int k = 0; k < kRows; ++k) {
+      const int gy = gy0 + wg * kRows + k;
       const bool ok = colok && gy >= 0 && gy < n1;
       const long long idx = g.G + gxx + p * gy;
-      v0[yy] = ok ? (float)rb[idx] * sc : 0.f;
-      v1[yy] = ok ? c[idx] : 0.f;
+      v0[k] = ok ? (float)rb[idx] * sc : 0.f;
+      v1[k] = ok ? c[idx] : 0.f;
     }
 #pragma unroll
-    for (int yy = 0; yy < kEH; ++yy) {
-      const int off = (yy * kXS + tid + 1) * 16;
-      *reinterpret_cast<uint4*>(smem + kOffAct0 + off) = make_uint4(pack_bf16x2(v0[yy], v1[yy]), 0, 0, 0);
+    for (int k = 0; k < kRows; ++k) {
+      const int off = ((wg * kRows + k) * kXS + x + 1) * 16;
+      *reinterpret_cast<uint4*>(smem + kOffAct0 + off) = make_uint4(pack_bf16x2(v0[k], v1[k]), 0, 0, 0);
       *reinterpret_cast<uint4*>(smem + kOffAct0 + kPlane + off) = make_uint4(0, 0, 0, 0);
     }
   }
@@ -224,35 +229,40 @@ __global__ void __launch_bounds__(kThreads, 2)
   const uint32_t bar0 = smem_u32(bar), w_addr = smem_u32(smem + kOffW);
   const uint32_t act_addr = smem_u32(smem + kOffAct0);
   unsigned char* act = smem + kOffAct0;
-  uint32_t parity = 0;            // bit i: phase of row barrier i to wait for next
-  uint32_t pending = 0;           // bit i: row barrier i has a commit not yet waited for
   bool failed = false;
   const double zscale = state ? state->rnorm : 1.0;
-  const int x = tid;
   const int gx = gx0 + x;
+  // phase of row barrier j at layer L: completions in earlier layers, where
+  // layer l has rows 0 .. kEH - 2l - 3
+  auto phase = [](int j, int L) {
+    int n = 0;
+    for (int l = 0; l < L; ++l) n += j < kEH - 2 * (l + 1) ? 1 : 0;
+    return (uint32_t)(n & 1);
+  };
 
+  int Lrun = 0;   // layers whose MMAs were issued
   for (int L = 0; L < 4 && !failed; ++L) {
+    Lrun = L + 1;
     const uint32_t wl = w_addr + L * 9 * 512;
     const int r0 = L + 1, nrows = kEH - 2 * (L + 1);
-    if (tid == 0) {
+    if ((tid & 127) == 0) {   // one issuer per warpgroup: rows of its parity
       fence_after();
-      for (int i = 0; i < nrows; ++i) {
+      for (int i = wg; i < nrows; i += 2) {
         issue_row(tmem, 16 * i, act_addr, wl, r0 + i - L);
         mma_commit(bar0 + 8 * i);
       }
     }
-    pending = (1u << nrows) - 1u;
-    for (int i = 0; i < nrows; ++i) {
-      const bool ok = mbar_wait(bar0 + 8 * i, (parity >> i) & 1u);
+    for (int i = wg; i < nrows; i += 2) {
+      bool ok = mbar_wait(bar0 + 8 * i, phase(i, L));
+      // the other parity's row i - 1 also reads input row r - 1 (overwritten below)
+      if (ok && L < 3 && i >= 1) ok = mbar_wait(bar0 + 8 * (i - 1), phase(i - 1, L));
       if (!ok) {
         failed = true;
         break;
       }
-      parity ^= 1u << i;
-      pending &= ~(1u << i);
       fence_after();
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * i, v);
+      tmem_ld16(tmem + ((uint32_t)lanes << 16) + 16 * i, v);
       const int row = r0 + i, gy = gy0 + row;
       const bool inside = gx >= 0 && gx < n1 && gy >= 0 && gy < n1;
       if (L < 3) {
@@ -269,16 +279,21 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (z) z[o] = (T)(zscale * (double)v[0]);
       }
     }
-    // the layer's outputs feed the next layer's MMAs (async proxy)
+    // the layer's outputs feed the next layer's MMAs (async proxy); every
+    // row barrier of the layer has completed once all threads pass here
+    if (!failed)
+      for (int i = 1 - wg; i < nrows; i += 2)
+        if (!mbar_wait(bar0 + 8 * i, phase(i, L))) failed = true;
     fence_async_smem();
     fence_before();
     failed = __syncthreads_or(failed);
   }
   if (failed) {
     if (tid == 0) atomicExch(err, 1);
-    // let the MMAs still in flight finish (bounded) before freeing their memory
-    for (int i = 0; i < kMaxRows; ++i)
-      if ((pending >> i) & 1u) mbar_wait(bar0 + 8 * i, (parity >> i) & 1u);
+    // let the MMAs of the last issued layer finish (bounded) before freeing
+    // their memory; earlier layers completed before it was issued
+    const int L = Lrun - 1;
+    for (int i = 0; i < kEH - 2 * (L + 1); ++i) mbar_wait(bar0 + 8 * i, phase(i, L));
   }
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
