@@ -149,14 +149,23 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// the nine MMAs of one activation row into TMEM columns col0 .. col0 + 15;
-// `slot` is the storage slot of input row `row`
-__device__ __forceinline__ void issue_row(uint32_t tmem, int col0, uint32_t act_in, uint32_t w_layer, int slot) {
-#pragma unroll
+// The MMAs of the rows i0, i0 + 2, ... < nrows of a layer, tap-major: the
+// nine taps of one row accumulate into the same TMEM columns and would run
+// as a dependent chain, so every row gets tap t before any row gets tap
+// t + 1.  Row i (input slot slot0 + i) accumulates into columns 16 i ..
+// 16 i + 15 and signals barrier i after its last tap (a commit covers all
+// earlier MMAs of the issuing thread).
+__device__ __forceinline__ void issue_rows(uint32_t tmem, uint32_t act_in, uint32_t w_layer, int slot0, int i0,
+                                           int nrows, uint32_t bar0) {
+#pragma unroll 1
   for (int t = 0; t < 9; ++t) {
     const int dy = t / 3 - 1, dx = t % 3 - 1;
-    const uint32_t a = act_in + (uint32_t)(((slot + dy) * kXS + dx + 1) * 16);
-    mma_bf16(tmem + (uint32_t)col0, sdesc(a, kPlane, 128), sdesc(w_layer + t * 512, 128, 256), t > 0 ? 1u : 0u);
+    const uint64_t bd = sdesc(w_layer + t * 512, 128, 256);
+    for (int i = i0; i < nrows; i += 2) {
+      const uint32_t a = act_in + (uint32_t)(((slot0 + i + dy) * kXS + dx + 1) * 16);
+      mma_bf16(tmem + (uint32_t)(16 * i), sdesc(a, kPlane, 128), bd, t > 0 ? 1u : 0u);
+      if (t == 8) mma_commit(bar0 + 8 * i);
+    }
   }
 }
 
@@ -247,10 +256,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int r0 = L + 1, nrows = kEH - 2 * (L + 1);
     if ((tid & 127) == 0) {   // one issuer per warpgroup: rows of its parity
       fence_after();
-      for (int i = wg; i < nrows; i += 2) {
-        issue_row(tmem, 16 * i, act_addr, wl, r0 + i - L);
-        mma_commit(bar0 + 8 * i);
-      }
+      issue_rows(tmem, act_addr, wl, r0 - L, wg, nrows, bar0);
     }
     for (int i = wg; i < nrows; i += 2) {
       bool ok = mbar_wait(bar0 + 8 * i, phase(i, L));
