@@ -3,42 +3,42 @@
 // the first three, zero padding, bfloat16 weights and activations, FP32
 // accumulation) fused in one kernel per output tile.
 //
-// Each layer is an implicit GEMM per row of 128 tile pixels (M = 128): the
-// three taps of one stencil row dy are stacked along N, D[pixel][dx, co] =
-// sum_ci A[pixel][ci] B_dy[(dx, co)][ci] with A the unshifted input row
-// y + dy and B_dy the 48 x 16 weight slices of taps (dy, -1), (dy, 0),
-// (dy, +1) (K = 16 input channels, N = 48), so a row is three tcgen05.mma
-// (kind::f16, bf16 inputs, FP32 accumulator in tensor memory) accumulating
-// over dy.  The shift in x is applied after the multiply:
-// out(x) = D[x - 1][dx = -1] + D[x][dx = 0] + D[x + 1][dx = +1], with the
-// neighbours' columns taken from the adjacent TMEM lanes by warp shuffles
-// (and through shared memory across the warp edges).  One elected thread
-// issues the MMAs; tcgen05.commit signals an mbarrier per row; the four
-// warps read the accumulator back with tcgen05.ld, apply ReLU and the
-// domain mask, round to bfloat16 and write the next layer's activations.
-// Layer 1 has two input channels (zero-padded to 16), layer 4 one output
-// channel (zero-padded weights, column 0 of each block read).
+// Each layer is an implicit GEMM: for one row of 128 tile pixels (M = 128)
+// and one tap (dy, dx) of the 3x3 stencil, D[pixel][co] += A[pixel][ci] *
+// B[co][ci] with A the input activations shifted by the tap and B the tap's
+// 16 x 16 weight slice (K = 16 input channels, N = 16 output channels), so a
+// row is nine tcgen05.mma (kind::f16, bf16 inputs, FP32 accumulator in tensor
+// memory).  One elected thread issues the MMAs; tcgen05.commit signals an
+// mbarrier; the four warps read the accumulator back with tcgen05.ld, apply
+// ReLU and the domain mask, round to bfloat16 and write the next layer's
+// activations to shared memory.  Layer 1 has two input channels (zero-padded
+// to 16), layer 4 one output channel (zero-padded weights, column 0 read).
 //
 // Tile: 120 x 8 output pixels with a 4-pixel halo (four layers of 3x3), i.e.
-// 128 x 16 activation pixels; layer l computes rows l .. 15 - l, and the
-// halo rows and columns become invalid one ring per layer (the tile's edge
-// columns miss their outer neighbour), so the central 120 x 8 outputs are
-// exact.  Pixels outside the problem's grid are held at zero in every layer
-// (the zero padding of each convolution).
+// 128 x 16 activation pixels; layer l computes rows l .. 15 - l, so the halo
+// rows and columns become invalid one ring per layer and the central 120 x 8
+// outputs are exact.  Pixels outside the problem's grid are held at zero in
+// every layer (the zero padding of each convolution).
 //
 // Operand layouts (shared memory, K-major, no swizzle): a core matrix is 8
 // rows x 16 bytes (8 bf16 of K) stored contiguously; the descriptor's
 // leading byte offset (LBO) steps between the two K halves, the stride byte
 // offset (SBO) between consecutive groups of 8 rows.  Activations are kept as
 // two planes (channels 0-7 and 8-15) of [row][x + 1] pixels x 16 bytes, so
-// the A operand of a row is its 128 consecutive pixels: SBO = 128 bytes, LBO
-// = one plane.  The weights are packed once per attach into compact 48 x 16
-// tiles (LBO = 128, SBO = 256 bytes).  The activations are updated in place:
-// input row q of layer L lives in slot q - L, and output row r is written to
-// slot r - L - 1 (its slot as an input of layer L + 1) once row r's MMAs
-// have completed -- by then every MMA that reads input row r - 1 (rows
-// r - 2 .. r) is done, since a commit covers all earlier MMAs of its thread.
-// Rows go through TMEM in batches of five (48 columns each).
+// the A operand of tap (dy, dx) for a row is simply the 128 consecutive
+// pixels starting at (row + dy, dx): SBO = 128 bytes, LBO = one plane.  The
+// weights are packed once per attach into the compact tile layout (LBO = 128,
+// SBO = 256 bytes).  The activations are updated in place: input row q of
+// layer L lives in slot q - L, and output row r is written to slot r - L - 1
+// (its slot as an input of layer L + 1) once row r's MMAs have completed --
+// by then every MMA that reads input row r - 1 (rows r - 2 .. r) is done, and
+// the commits complete in issue order.  This halves the shared memory, so two
+// CTAs share an SM and hide each other's latencies.
+// Per layer the issuing thread enqueues the MMAs of all
+// rows at once, each row into its own TMEM columns and signalling its own
+// mbarrier, and every warp drains the rows in order as they complete (a
+// warp reads only its own 32 TMEM lanes, so no block barrier is needed
+// between rows).
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -58,28 +58,24 @@ constexpr int kNPix = kEH * kXS;       // pixels of one activation buffer
 constexpr int kPlane = kNPix * 16;     // bytes of one channel plane
 constexpr int kThreads = 128;          // four warps: TMEM lanes 0..127
 constexpr int kMaxRows = kEH - 2;      // rows computed by the first layer
-constexpr int kN = 48;                 // MMA N: three taps x 16 output channels
-constexpr int kBatch = 5;              // rows in TMEM at a time
-constexpr int kTmemCols = 256;         // kBatch accumulators of kN columns
+constexpr int kTmemCols = 256;         // one 16-column accumulator per row of a layer
 constexpr long long kWaitLimit = 1LL << 22;
 
 static_assert(kEW == kThreads, "one thread per tile column");
-static_assert(kThreads == 128, "four warps cover the 128 TMEM lanes");
+static_assert(kEH == 16 && kThreads == 128, "halo-column zeroing maps 16 rows x 2 sides x 2 planes (x 2 passes)");
 
 // shared memory map (bytes): one activation buffer, updated in place
 constexpr int kActBytes = 2 * kPlane;                // two planes
-constexpr int kBBytes = kN * 16 * 2;                 // one 48 x 16 B tile
-constexpr int kWBytes = 4 * 3 * kBBytes;             // four layers x three stencil rows
+constexpr int kWBytes = 4 * 9 * 16 * 16 * 2;         // four layers x nine taps of B
 constexpr int kOffAct0 = 0;
 constexpr int kOffW = kOffAct0 + kActBytes;
 constexpr int kOffBar = kOffW + kWBytes;
-constexpr int kOffXch = kOffBar + 8 * kBatch + 16;   // warp-edge exchange: [warp][2][16] floats
-constexpr int kSmemBytes = kOffXch + 4 * 2 * 16 * 4;
+constexpr int kSmemBytes = kOffBar + 8 * kMaxRows + 16;
 
 // instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits
 // 17-22, M >> 4 at bits 24-28
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -91,7 +87,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 }
 
 // byte offset of element (row, k) in a compact K-major tile of 16 columns
-// (rows in groups of 8, the two K halves of a group 128 bytes apart)
 __host__ __device__ __forceinline__ int canon(int row, int k) {
   return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
@@ -152,19 +147,14 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// The three MMAs of rows i0 .. i0 + nb - 1 of a layer (input slot of row i:
-// slot0 + i), row j of the batch into TMEM columns kN j .. kN j + 47, each
-// signalling barrier j.
-__device__ __forceinline__ void issue_batch(uint32_t tmem, uint32_t act_in, uint32_t w_layer, int slot0, int i0,
-                                            int nb, uint32_t bar0) {
-  for (int j = 0; j < nb; ++j) {
+// the nine MMAs of one activation row into TMEM columns col0 .. col0 + 15;
+// `slot` is the storage slot of input row `row`
+__device__ __forceinline__ void issue_row(uint32_t tmem, int col0, uint32_t act_in, uint32_t w_layer, int slot) {
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {   // stencil row dy = t - 1
-      const uint32_t a = act_in + (uint32_t)(((slot0 + i0 + j + t - 1) * kXS + 1) * 16);
-      mma_bf16(tmem + (uint32_t)(kN * j), sdesc(a, kPlane, 128), sdesc(w_layer + t * kBBytes, 128, 256),
-               t > 0 ? 1u : 0u);
-    }
-    mma_commit(bar0 + 8 * j);
+  for (int t = 0; t < 9; ++t) {
+    const int dy = t / 3 - 1, dx = t % 3 - 1;
+    const uint32_t a = act_in + (uint32_t)(((slot + dy) * kXS + dx + 1) * 16);
+    mma_bf16(tmem + (uint32_t)col0, sdesc(a, kPlane, 128), sdesc(w_layer + t * 512, 128, 256), t > 0 ? 1u : 0u);
   }
 }
 
@@ -180,9 +170,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (state && state->done) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 8 * kBatch);
-  float* xch = reinterpret_cast<float*>(smem + kOffXch);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 8 * kMaxRows);
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int b = blockIdx.z;
   const int gx0 = blockIdx.x * kTW - kHalo, gy0 = blockIdx.y * kTH - kHalo;
   const int n1 = g.n1;
@@ -194,8 +183,15 @@ __global__ void __launch_bounds__(kThreads, 2)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid < kBatch) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + tid)) : "memory");
+  if (tid < kMaxRows) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + tid)) : "memory");
   if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  // zero the x = -1 and x = 128 columns of every slot and plane (the only
+  // activation entries that no layer writes but later layers read)
+  if (tid < 64) {
+    const int row = tid & 15, side = (tid >> 4) & 1, plane = (tid >> 5) & 1;
+    *reinterpret_cast<uint4*>(smem + kOffAct0 + plane * kPlane + (row * kXS + side * (kXS - 1)) * 16) =
+        make_uint4(0, 0, 0, 0);
+  }
   for (int i = tid; i < kWBytes / 16; i += kThreads) reinterpret_cast<uint4*>(smem + kOffW)[i] = wtc[i];
   // input tile (thread = column x, all 16 rows, loads issued together):
   // channel 0 = bf16(r / ||r||), channel 1 = bf16(c), zero outside the grid
@@ -228,105 +224,77 @@ __global__ void __launch_bounds__(kThreads, 2)
   const uint32_t bar0 = smem_u32(bar), w_addr = smem_u32(smem + kOffW);
   const uint32_t act_addr = smem_u32(smem + kOffAct0);
   unsigned char* act = smem + kOffAct0;
-  uint32_t parity = 0;            // bit j: phase of barrier j to wait for next
-  uint32_t pending = 0;           // bit j: barrier j has a commit not yet waited for
+  uint32_t parity = 0;            // bit i: phase of row barrier i to wait for next
+  uint32_t pending = 0;           // bit i: row barrier i has a commit not yet waited for
   bool failed = false;
   const double zscale = state ? state->rnorm : 1.0;
   const int x = tid;
   const int gx = gx0 + x;
-  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
 
   for (int L = 0; L < 4 && !failed; ++L) {
-    const uint32_t wl = w_addr + L * 3 * kBBytes;
+    const uint32_t wl = w_addr + L * 9 * 512;
     const int r0 = L + 1, nrows = kEH - 2 * (L + 1);
-    for (int i0 = 0; i0 < nrows && !failed; i0 += kBatch) {
-      const int nb = nrows - i0 < kBatch ? nrows - i0 : kBatch;
-      if (tid == 0) {
-        fence_after();
-        issue_batch(tmem, act_addr, wl, r0 - L, i0, nb, bar0);
+    if (tid == 0) {
+      fence_after();
+      for (int i = 0; i < nrows; ++i) {
+        issue_row(tmem, 16 * i, act_addr, wl, r0 + i - L);
+        mma_commit(bar0 + 8 * i);
       }
-      pending = (1u << nb) - 1u;
-      for (int j = 0; j < nb; ++j) {
-        // block-wide agreement: every thread takes the same path (the
-        // rows' block barriers below must be reached by all threads)
-        const bool ok = __syncthreads_and(mbar_wait(bar0 + 8 * j, (parity >> j) & 1u));
-        if (!ok) {
-          failed = true;
-          break;
-        }
-        parity ^= 1u << j;
-        pending &= ~(1u << j);
-        fence_after();
-        float dm[16], d0[16], dp[16];
-        tmem_ld16(tl + kN * j, dm);        // taps dx = -1 of this lane's pixel
-        tmem_ld16(tl + kN * j + 16, d0);   // dx = 0
-        tmem_ld16(tl + kN * j + 32, dp);   // dx = +1
-        // out(x) = dm(x - 1) + d0(x) + dp(x + 1); across warp edges through
-        // shared memory
-        if (lane == 31) {
-#pragma unroll
-          for (int k = 0; k < 16; ++k) xch[(warp * 2 + 0) * 16 + k] = dm[k];
-        }
-        if (lane == 0) {
-#pragma unroll
-          for (int k = 0; k < 16; ++k) xch[(warp * 2 + 1) * 16 + k] = dp[k];
-        }
-        __syncthreads();
-        float o[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          float left = __shfl_up_sync(0xffffffffu, dm[k], 1);
-          float right = __shfl_down_sync(0xffffffffu, dp[k], 1);
-          if (lane == 0) left = warp > 0 ? xch[((warp - 1) * 2 + 0) * 16 + k] : 0.f;
-          if (lane == 31) right = warp < 3 ? xch[((warp + 1) * 2 + 1) * 16 + k] : 0.f;
-          o[k] = left + d0[k] + right;
-        }
-        const int row = r0 + i0 + j, gy = gy0 + row;
-        const bool inside = gx >= 0 && gx < n1 && gy >= 0 && gy < n1;
-        if (L < 3) {
-          uint32_t q[8];
-#pragma unroll
-          for (int k = 0; k < 8; ++k)
-            q[k] = inside ? pack_bf16x2(fmaxf(o[2 * k], 0.f), fmaxf(o[2 * k + 1], 0.f)) : 0u;
-          const int off = ((row - L - 1) * kXS + x + 1) * 16;   // in place: slot of input row row - 1
-          *reinterpret_cast<uint4*>(act + off) = make_uint4(q[0], q[1], q[2], q[3]);
-          *reinterpret_cast<uint4*>(act + kPlane + off) = make_uint4(q[4], q[5], q[6], q[7]);
-        } else if (inside && x >= kHalo && x < kHalo + kTW && row >= kHalo && row < kHalo + kTH) {
-          const long long oi = (long long)b * g.len + g.G + gx + p * gy;
-          if (y) y[oi] = o[0];
-          if (z) z[oi] = (T)(zscale * (double)o[0]);
-        }
-        __syncthreads();   // the exchange buffer is reused by the next row
-      }
-      // the batch's TMEM columns are reused and its outputs are read by the
-      // next layer's MMAs (async proxy)
-      fence_async_smem();
-      fence_before();
-      failed = __syncthreads_or(failed);
     }
+    pending = (1u << nrows) - 1u;
+    for (int i = 0; i < nrows; ++i) {
+      const bool ok = mbar_wait(bar0 + 8 * i, (parity >> i) & 1u);
+      if (!ok) {
+        failed = true;
+        break;
+      }
+      parity ^= 1u << i;
+      pending &= ~(1u << i);
+      fence_after();
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * i, v);
+      const int row = r0 + i, gy = gy0 + row;
+      const bool inside = gx >= 0 && gx < n1 && gy >= 0 && gy < n1;
+      if (L < 3) {
+        uint32_t q[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          q[k] = inside ? pack_bf16x2(fmaxf(v[2 * k], 0.f), fmaxf(v[2 * k + 1], 0.f)) : 0u;
+        const int off = ((row - L - 1) * kXS + x + 1) * 16;   // in place: slot of input row row - 1
+        *reinterpret_cast<uint4*>(act + off) = make_uint4(q[0], q[1], q[2], q[3]);
+        *reinterpret_cast<uint4*>(act + kPlane + off) = make_uint4(q[4], q[5], q[6], q[7]);
+      } else if (inside && x >= kHalo && x < kHalo + kTW && row >= kHalo && row < kHalo + kTH) {
+        const long long o = (long long)b * g.len + g.G + gx + p * gy;
+        if (y) y[o] = v[0];
+        if (z) z[o] = (T)(zscale * (double)v[0]);
+      }
+    }
+    // the layer's outputs feed the next layer's MMAs (async proxy)
+    fence_async_smem();
+    fence_before();
+    failed = __syncthreads_or(failed);
   }
   if (failed) {
     if (tid == 0) atomicExch(err, 1);
     // let the MMAs still in flight finish (bounded) before freeing their memory
-    for (int j = 0; j < kBatch; ++j)
-      if ((pending >> j) & 1u) mbar_wait(bar0 + 8 * j, (parity >> j) & 1u);
+    for (int i = 0; i < kMaxRows; ++i)
+      if ((pending >> i) & 1u) mbar_wait(bar0 + 8 * i, (parity >> i) & 1u);
   }
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-// Pack the bfloat16-valued weights into the compact B tiles: layer L,
-// stencil row ky, row n = 16 kx + co, column k = ci (zero-padded channels).
+// Pack the bfloat16-valued weights into the compact B tiles of the four
+// layers (zero-padded to 16 x 16 per tap).
 __global__ void k_net_pack_tc(const float* __restrict__ wq, __nv_bfloat16* __restrict__ wtc) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 4 * 3 * kN * 16; e += gridDim.x * blockDim.x) {
-    const int L = e / (3 * kN * 16), ky = (e / (kN * 16)) % 3, n = (e / 16) % kN, k = e % 16;
-    const int kx = n / 16, co = n % 16, t = 3 * ky + kx;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 4 * 9 * 256; e += gridDim.x * blockDim.x) {
+    const int L = e / (9 * 256), t = (e / 256) % 9, n = (e / 16) % 16, k = e % 16;
     float w = 0.f;
-    if (L == 0) { if (k < kNetIn) w = wq[kNetOff1 + (co * kNetIn + k) * 9 + t]; }
-    else if (L == 1) w = wq[kNetOff2 + (co * kNetC1 + k) * 9 + t];
-    else if (L == 2) w = wq[kNetOff3 + (co * kNetW + k) * 9 + t];
-    else { if (co == 0) w = wq[kNetOff4 + k * 9 + t]; }
-    wtc[((L * 3 + ky) * kBBytes + canon(n, k)) / 2] = __float2bfloat16_rn(w);
+    if (L == 0) { if (k < kNetIn) w = wq[kNetOff1 + (n * kNetIn + k) * 9 + t]; }
+    else if (L == 1) w = wq[kNetOff2 + (n * kNetC1 + k) * 9 + t];
+    else if (L == 2) w = wq[kNetOff3 + (n * kNetW + k) * 9 + t];
+    else { if (n == 0) w = wq[kNetOff4 + k * 9 + t]; }
+    wtc[((L * 9 + t) * 512 + canon(n, k)) / 2] = __float2bfloat16_rn(w);
   }
 }
 
