@@ -36,7 +36,8 @@ METRIC = "MPCG-AMG DOFs/s to 1e-8 rel. residual"
 
 
 def _rank():
-    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+    from paper_2402_12833_gb300.multi import rank_env
+    return rank_env()
 
 
 # ---------------------------------------------------------------------------- clocks
@@ -298,7 +299,8 @@ def bench_ours(args):
         dist.barrier()
     M.load()
 
-    prob = pb.poisson_random(DIM, NODES, RHS_SEED + rank)
+    from paper_2402_12833_gb300.multi import problem_seed
+    prob = pb.poisson_random(DIM, NODES, problem_seed(RHS_SEED, rank))
     n = prob.n
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
@@ -317,11 +319,8 @@ def bench_ours(args):
             dist.barrier()
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        from paper_2402_12833_gb300.multi import max_over_ranks as mor
+        return mor(v, device="cuda")
 
     res = {}
     clocks = None
@@ -478,15 +477,27 @@ def bench_batched(args):
     hierarchy per side length, the classes solved concurrently."""
     import numpy as np
     import torch
+    import torch.distributed as dist
     from paper_2402_12833_gb300 import build as _build
     from paper_2402_12833_gb300 import mpcg as M
+    from paper_2402_12833_gb300 import multi
     from paper_2402_12833_gb300 import problems as pb
-    _build.build()
+    rank, world, local = multi.rank_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
     M.load()
     sizes = pb.batch_sizes(256, seed=4)
+    # the 256 independent problems are dealt to the ranks by DOF count (no
+    # communication on the data path)
+    mine = multi.shard_batch([(s - 2) ** 2 for s in sizes], rank, world)
     by = {}
-    for i, s in enumerate(sizes):
-        by.setdefault(s, []).append(i)
+    for i in mine:
+        by.setdefault(sizes[i], []).append(i)
     classes, bs, xs, ns = [], [], [], 0
     streams = []
     for nodes in sorted(by):
@@ -508,14 +519,24 @@ def bench_batched(args):
         torch.cuda.synchronize()
         _, its = M.mpcg_solve_batched(classes, bs, xs, rtol=RTOL, maxit=20000)
 
-    ms = _timed(step, args.steps, max(1, args.warmup // 3), torch.cuda.current_stream())
+    if world > 1:
+        dist.barrier()
+    ms = multi.max_over_ranks(_timed(step, args.steps, max(1, args.warmup // 3), torch.cuda.current_stream()),
+                              device="cuda")
     launches = sum(M.mg_last_launches(c.h) for c in classes)
+    ns_all = multi.sum_over_ranks(ns, device="cuda")
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
     print(json.dumps({
-        "metric": METRIC, "workload": "batched", "value": ns / (ms * 1e-3), "unit": "DOFs/s", "n_gpus": 1,
-        "steps": args.steps, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+        "metric": METRIC, "workload": "batched", "value": ns_all / (ms * 1e-3), "unit": "DOFs/s", "n_gpus": world,
+        "scaling": "strong", "steps": args.steps, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32+f64",
+        "data": "synthetic",
         "config": {"workload": "256 x 2D diffusion, sides U{33,65,129,257,513}, log10 kappa U[-2,4] on 16x16 macro "
                                "cells, N(0,1) RHS, levels to 5x5, MPCG m=5, mixed precision, rtol 1e-8 each",
-                   "problems_per_side": {str(k): len(v) for k, v in sorted(by.items())}, "total_dofs": ns},
+                   "problems_per_side_rank0": {str(k): len(v) for k, v in sorted(by.items())},
+                   "total_dofs": int(ns_all)},
         "max_iterations_per_side": {str(k): int(i.max()) for k, i in zip(sorted(by), its)},
         "gpu_launches_per_step": launches}))
     return 0
