@@ -199,7 +199,7 @@ struct mg_hierarchy {
   mpcg_options opt;
   cudaStream_t stream = 0;
   cudaStream_t cap_stream = nullptr;
-  cudaStream_t side[2] = {nullptr, nullptr};   // branches of the MG chain
+  cudaStream_t side[kMaxLevels] = {};   // branches of the MG chain: fine smoothing, one per coarse grid
   cudaEvent_t ev_fork = nullptr, ev_fine = nullptr;
   cudaEvent_t ev_r[kMaxLevels] = {}, ev_sm[kMaxLevels] = {};
   double* A0inv = nullptr;
@@ -339,10 +339,11 @@ void enqueue_smooth(mg_hierarchy* h, Solver<T>& S, int j, const T* rr, T* out, c
 
 // The additive structure makes the level corrections independent once the
 // residual has been restricted (Section 2.1): the fine-grid smoothing (which
-// needs only r) runs on a second stream, the coarse smoothings on a third as
-// their restricted residuals appear, while the main stream carries the
-// restriction chain, the coarse solve and the prolongation chain.  Under
-// graph capture the three streams become parallel graph branches.
+// needs only r) runs on one side stream, and every coarse grid's smoothing on
+// a side stream of its own, starting as soon as its restricted residual
+// exists, while the main stream carries the restriction chain, the coarse
+// solve and the prolongation chain.  Under graph capture the side streams
+// become parallel graph branches.
 template <typename T>
 void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState* state, cudaStream_t s) {
   const int J = h->levels - 1;
@@ -352,7 +353,7 @@ void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState*
   }
   // a profiled solve keeps every launch on one stream so that each event
   // pair brackets exactly one kernel running alone
-  cudaStream_t s2 = h->prof.on ? s : h->side[0], s3 = h->prof.on ? s : h->side[1];
+  cudaStream_t s2 = h->prof.on ? s : h->side[0];
   cudaEventRecord(h->ev_fork, s);
   cudaStreamWaitEvent(s2, h->ev_fork, 0);
   enqueue_smooth<T>(h, S, J, r, Z + (size_t)J * h->lev[J].g.cp, state, s2);
@@ -361,7 +362,8 @@ void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState*
   for (int j = J; j >= 1; --j) {
     LAUNCH(h, K_RESTRICT, s, launch_restrict<T>(h->lev[j].g, h->lev[j - 1].g, rj, S.rlev[j - 1], state, s));
     rj = S.rlev[j - 1];
-    if (j - 1 >= 1) {   // smoothing of grid j-1 can start now
+    if (j - 1 >= 1) {   // smoothing of grid j-1 can start now, on its own branch
+      cudaStream_t s3 = h->prof.on ? s : h->side[j - 1];
       cudaEventRecord(h->ev_r[j - 1], s);
       cudaStreamWaitEvent(s3, h->ev_r[j - 1], 0);
       enqueue_smooth<T>(h, S, j - 1, S.rlev[j - 1], S.zc[j - 1] + (size_t)(j - 1) * h->lev[j - 1].g.cp, state, s3);
@@ -722,8 +724,9 @@ static mpcg_status setup_impl(const mg_operator* ops, int nb, int levels, const 
   };
   bool ev_ok = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
                cudaEventCreateWithFlags(&h->ev_fine, cudaEventDisableTiming) == cudaSuccess &&
-               cudaStreamCreateWithFlags(&h->side[0], cudaStreamNonBlocking) == cudaSuccess &&
-               cudaStreamCreateWithFlags(&h->side[1], cudaStreamNonBlocking) == cudaSuccess;
+               cudaStreamCreateWithFlags(&h->side[0], cudaStreamNonBlocking) == cudaSuccess;
+  for (int j = 1; j < levels && ev_ok; ++j)
+    ev_ok = cudaStreamCreateWithFlags(&h->side[j], cudaStreamNonBlocking) == cudaSuccess;
   for (int j = 0; j < kMaxLevels && ev_ok; ++j)
     ev_ok = cudaEventCreateWithFlags(&h->ev_r[j], cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&h->ev_sm[j], cudaEventDisableTiming) == cudaSuccess;
