@@ -114,7 +114,7 @@ def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops, S=27, vector=False
     chain: the smoothings of grids J, J-1, ..., 1 (nu = 2: one fused launch
     each; vector problems: the first sweep, the residual and the block
     update of the second sweep per grid), the
-    restrictions from grids J, ..., 1, the prolongations into 1, ..., J."""
+    restrictions from grids J, ..., 1, one composite prolongation."""
     J = len(ns) - 1
     jsub = 0
     tot = {}
@@ -148,9 +148,8 @@ def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops, S=27, vector=False
         elif cls == "restrict":
             b, f = (ns[jr] + ns[jr - 1]) * w, 2 * 27 * ns[jr - 1]
             jr -= 1
-        elif cls == "prolong":
-            b, f = jp * (ns[jp - 1] + ns[jp]) * w, 2 * 8 * jp * ns[jp]
-            jp += 1
+        elif cls == "prolong":   # composite: write J fine columns, read every coarse correction once
+            b, f = (J * ns[J] + sum(ns[:J])) * w, 2 * 8 * J * ns[J]
         elif cls in ("orth_update", "gram_window", "spmm", "update_xr"):
             b, f = kernel_work(cls, ns[J], C, cnt, w, S)
         if cls == dom:

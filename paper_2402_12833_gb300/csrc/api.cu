@@ -371,12 +371,15 @@ void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState*
     }
   }
   LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->A0inv, S.rlev[0], S.zc[0], state, s));
-  for (int j = 1; j <= J; ++j) {
-    // prolong columns 0..j-1 of grid j-1; column j-1 is grid j-1's smoothing
-    if (j - 1 >= 1) cudaStreamWaitEvent(s, h->ev_sm[j - 1], 0);
-    T* dst = j == J ? Z : S.zc[j];
-    LAUNCH(h, K_PROLONG, s, launch_prolong<T>(h->lev[j - 1].g, h->lev[j].g, S.zc[j - 1], dst, j, state, s));
+  // every grid's correction straight to the fine grid in one launch
+  const T* src[kMaxLevels];
+  GridDesc gcs[kMaxLevels];
+  for (int j = 0; j < J; ++j) {
+    if (j >= 1) cudaStreamWaitEvent(s, h->ev_sm[j], 0);
+    src[j] = S.zc[j] + (size_t)j * h->lev[j].g.cp;
+    gcs[j] = h->lev[j].g;
   }
+  LAUNCH(h, K_PROLONG, s, launch_prolong_all<T>(h->lev[J].g, src, gcs, J, Z, state, s));
   cudaStreamWaitEvent(s, h->ev_fine, 0);
 }
 

@@ -66,6 +66,11 @@ template <typename T>
 void launch_prolong(const GridDesc& gc, const GridDesc& gf, const T* coarse, T* fine, int ncols,
                     const DevState* state, cudaStream_t s);
 // coarse stencil = P^T A P (FP64)
+// Z columns 0 .. J-1 on the fine grid gf from grid j's correction coarse[j]
+// (grid descriptor gcs[j]) by the composite multilinear interpolation.
+template <typename T>
+void launch_prolong_all(const GridDesc& gf, const T* const* coarse, const GridDesc* gcs, int J, T* Z,
+                        const DevState* state, cudaStream_t s);
 void launch_galerkin(const GridDesc& gf, const GridDesc& gc, const double* stf, double* stc,
                      cudaStream_t s);
 // dinv = omega / centre coefficient (0 at pads)

@@ -369,6 +369,81 @@ __global__ void __launch_bounds__(kBlock) k_prolong(GridDesc gc, GridDesc gf, co
   }
 }
 
+// Composite prolongation P_J ... P_{j+1} of every coarse grid's correction
+// straight to the fine grid (Section 2.1 allows the composite transfers to be
+// formed explicitly): the nested Q1 spaces make it the multilinear
+// interpolation of grid j's values at the fine nodes.  Along an axis with
+// s = 2^(J-j), fine global node g lies between coarse global nodes g >> m
+// and (g >> m) + 1 with weights 1 - f/s and f/s, f = g mod s (exact binary
+// fractions); coarse parents outside the grid are pad entries (zero).  One
+// launch writes columns 0 .. J-1 of Z (column J is the fine smoothing),
+// equal to successive two-grid prolongation up to the summation order.
+template <typename T>
+struct CoarseSrc {
+  const T* v[kMaxLevels];      // grid j's correction (padded, problem 0)
+  GridDesc g[kMaxLevels];
+};
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBlock) k_prolong_all(GridDesc gf, CoarseSrc<T> src, int J, T* __restrict__ Z,
+                                                        const DevState* state) {
+  const int pb = blockIdx.y;
+  if (state && state[pb].done) return;
+  constexpr int W = Vec<T>::W;
+  constexpr int NR = W / 2 + 2;   // coarse x values a group needs at s = 2
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= gf.npts / W) return;
+  const long long t0 = q * W;
+  int x0, y, z, a;
+  decode(gf, t0, x0, y, z, a);
+  const long long idf = (long long)pb * gf.len + gf.G + t0;
+  const bool rowpad = y >= gf.ny || (DIM == 3 && z >= gf.nz);
+  for (int j = 0; j < J; ++j) {
+    T o[W];
+    if (rowpad) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) o[w] = 0;
+    } else {
+      const GridDesc& gc = src.g[j];
+      const int m = J - j;
+      const int sm1 = (1 << m) - 1;
+      const T inv_s = (T)1 / (T)(1 << m);
+      const int gy = y + gf.loy, gz = z + gf.loz;
+      const int cy0 = (gy >> m) - gc.loy, cz0 = DIM == 3 ? (gz >> m) - gc.loz : 0;
+      const T wy1 = (T)(gy & sm1) * inv_s, wz1 = DIM == 3 ? (T)(gz & sm1) * inv_s : (T)0;
+      const int gx0 = x0 + gf.lox;
+      const int X0 = gx0 >> m;
+      const T* base = src.v[j] + (long long)pb * gc.len + gc.G + a * gc.cstride + (X0 - gc.lox);
+      T row[NR];
+#pragma unroll
+      for (int k = 0; k < NR; ++k) row[k] = 0;
+#pragma unroll
+      for (int kz = 0; kz < (DIM == 3 ? 2 : 1); ++kz) {
+        const T wz = DIM == 3 ? (kz ? wz1 : (T)1 - wz1) : (T)1;
+#pragma unroll
+        for (int ky = 0; ky < 2; ++ky) {
+          const T wgt = wz * (ky ? wy1 : (T)1 - wy1);
+          const T* rp = base + gc.px * (long long)(cy0 + ky) + (DIM == 3 ? gc.pxy * (cz0 + kz) : 0);
+#pragma unroll
+          for (int k = 0; k < NR; ++k) row[k] = fma(wgt, rp[k], row[k]);
+        }
+      }
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        const int gx = gx0 + w;
+        const int k = (gx >> m) - X0;
+        const T wx1 = (T)(gx & sm1) * inv_s;
+        T v = row[0];
+#pragma unroll
+        for (int kk = 0; kk < NR - 1; ++kk)
+          if (kk == k) v = fma(wx1, row[kk + 1] - row[kk], row[kk]);
+        o[w] = x0 + w < gf.nx ? v : (T)0;
+      }
+    }
+    Vec<T>::store(Z + (long long)j * gf.cp + idf, o);
+  }
+}
+
 // Galerkin product A_c = P^T A_f P, one coarse row per thread.  For vector
 // unknowns P interpolates componentwise, so every component pair (a, b) is a
 // scalar Galerkin product of its own plane group b * 3^DIM + s.
@@ -780,6 +855,23 @@ template void launch_prolong<double>(const GridDesc&, const GridDesc&, const dou
                                      const DevState*, cudaStream_t);
 template void launch_prolong<float>(const GridDesc&, const GridDesc&, const float*, float*, int, const DevState*,
                                     cudaStream_t);
+
+template <typename T>
+void launch_prolong_all(const GridDesc& gf, const T* const* coarse, const GridDesc* gcs, int J, T* Z,
+                        const DevState* state, cudaStream_t s) {
+  CoarseSrc<T> src = {};
+  for (int j = 0; j < J; ++j) {
+    src.v[j] = coarse[j];
+    src.g[j] = gcs[j];
+  }
+  const dim3 grid(blocks_for(gf.npts / vw<T>()), gf.nb);
+  if (gf.dim == 3) k_prolong_all<T, 3><<<grid, kBlock, 0, s>>>(gf, src, J, Z, state);
+  else k_prolong_all<T, 2><<<grid, kBlock, 0, s>>>(gf, src, J, Z, state);
+}
+template void launch_prolong_all<double>(const GridDesc&, const double* const*, const GridDesc*, int, double*,
+                                         const DevState*, cudaStream_t);
+template void launch_prolong_all<float>(const GridDesc&, const float* const*, const GridDesc*, int, float*,
+                                        const DevState*, cudaStream_t);
 
 void launch_galerkin(const GridDesc& gf, const GridDesc& gc, const double* stf, double* stc, cudaStream_t s) {
   const dim3 grid(blocks_for(gc.npts), gc.nb);
