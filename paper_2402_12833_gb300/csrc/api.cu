@@ -214,6 +214,14 @@ struct mg_hierarchy {
   Solver<float> s32;
   double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *nrm = nullptr, *part_mix = nullptr;
   double* stage = nullptr;   // 2 n doubles: staging for host b and x
+  // mixed precision as one graph (refinement loop on the device)
+  int* mix = nullptr;        // per problem: inner iterations, status, active
+  int* outer = nullptr;      // refinement steps taken
+  cudaGraph_t mgraph = nullptr;
+  cudaGraphExec_t mexec = nullptr;
+  double mg_rtol = -1.0;
+  int mg_maxit = -1, mg_hist = -1;
+  long long mg_head = 0, mg_tail = 0, mg_iprol = 0, mg_ibody = 0;   // launches per part
   Profiler prof;
   bool force_direct = false;
   long long last_launches = 0;
@@ -566,6 +574,8 @@ mpcg_status build_f32(mg_hierarchy* h) {
   CKS(h->mem.get(&h->nrm, 2 * (size_t)h->nb + 2, s));
   CKS(h->mem.get(&h->part_mix, 2 * (size_t)h->nb * stream_blocks(gf), s));
   CKS(h->mem.get(&h->active, h->nb, s));
+  CKS(h->mem.get(&h->mix, 3 * (size_t)h->nb, s));
+  CKS(h->mem.get(&h->outer, 1, s));
   CK(cudaGetLastError());
   h->have32 = true;
   return MPCG_OK;
@@ -629,6 +639,8 @@ void mg_hierarchy_destroy(mg_hierarchy* h) {
   if (!h) return;
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
+  if (h->mexec) cudaGraphExecDestroy(h->mexec);
+  if (h->mgraph) cudaGraphDestroy(h->mgraph);
   h->s64.release();
   h->s32.release();
   h->mem.release();
@@ -850,6 +862,171 @@ static mpcg_status solve_fp64(mg_hierarchy* h, const double* b, double* x, doubl
   return result;
 }
 
+// The mixed-precision solve as one CUDA graph: an outer conditional while
+// node (FP64 residual, device-side decision, scaling, FP32 inner solve,
+// FP64 update) whose body holds the inner solver's prologue and its own
+// conditional while node.  No host round trip per refinement step.
+static void drop_mixed_graph(mg_hierarchy* h) {
+  if (h->mexec) cudaGraphExecDestroy(h->mexec);
+  if (h->mgraph) cudaGraphDestroy(h->mgraph);
+  h->mexec = nullptr;
+  h->mgraph = nullptr;
+  h->mg_rtol = -1.0;
+  h->mg_maxit = h->mg_hist = -1;
+}
+
+static cudaGraphNode_t add_while(cudaStream_t cs, cudaGraph_t g, cudaGraphConditionalHandle c, cudaGraph_t* body,
+                                 bool* ok) {
+  cudaStreamCaptureStatus st;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = c;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  *ok = *ok && cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &deps, nullptr, &ndeps) == cudaSuccess;
+  *ok = *ok && cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp) == cudaSuccess;
+  *ok = *ok && cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                   cudaSuccess;
+  if (*ok) *body = cp.conditional.phGraph_out[0];
+  return node;
+}
+
+static bool build_mixed_graph(mg_hierarchy* h, double rtol, int maxit) {
+  drop_mixed_graph(h);
+  Solver<float>& S = h->s32;
+  const int J = h->levels - 1;
+  const Level& L = h->lev[J];
+  const GridDesc& gf = L.g;
+  const int nb = h->nb;
+  cudaStream_t cs = h->cap_stream;
+  cudaGraph_t graph = nullptr, obody = nullptr, ibody = nullptr;
+  cudaGraphConditionalHandle c_out, c_in;
+  bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
+  ok = ok && cudaGraphConditionalHandleCreate(&c_out, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  ok = ok && cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                 cudaSuccess;
+  if (!ok) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return false;
+  }
+  long long init_launches = 0;   // the one init launch is counted per solve by the caller
+  h->prof.target = &init_launches;
+  LAUNCH(h, K_AUX, cs, launch_mix_init(h->mix, h->active, nb, h->outer, cs));
+  add_while(cs, graph, c_out, &obody, &ok);
+  cudaGraph_t tmp = nullptr;
+  ok = (cudaStreamEndCapture(cs, &tmp) == cudaSuccess) && ok;
+  // outer body: residual, decision, scaling, inner solve, update
+  ok = ok && cudaStreamBeginCaptureToGraph(cs, obody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                 cudaSuccess;
+  if (ok) {
+    h->mg_head = 0;
+    h->prof.target = &h->mg_head;
+    LAUNCH(h, K_RESIDUAL, cs, launch_residual<double>(gf, L.st64, h->b64, h->x64, h->r64, h->part_mix, cs));
+    LAUNCH(h, K_AUX, cs, launch_sum_partials(h->part_mix, nb, 2, stream_blocks(gf), h->nrm, cs));
+    LAUNCH(h, K_AUX, cs, launch_outer_check(h->mix, h->active, nb, h->nrm, rtol, maxit, h->opt.max_outer, h->outer,
+                                            S.state, h->opt.inner_rtol, S.m, S.C, h->opt.inner_drop_delta,
+                                            h->opt.inner_pinv_tau, c_out, cs));
+    LAUNCH(h, K_AUX, cs, launch_scale_to_f32(gf, h->r64, h->nrm, h->active, S.b, cs));
+    ok = cudaMemsetAsync(S.x, 0, sizeof(float) * gf.cp, cs) == cudaSuccess;
+    ok = ok && cudaGraphConditionalHandleCreate(&c_in, obody, 0, 0) == cudaSuccess;
+    if (ok) {
+      h->mg_iprol = 0;
+      h->prof.target = &h->mg_iprol;
+      enqueue_prologue<float>(h, S, c_in, 1, cs);
+      add_while(cs, obody, c_in, &ibody, &ok);
+      h->mg_tail = 0;
+      h->prof.target = &h->mg_tail;
+      LAUNCH(h, K_AUX, cs, launch_outer_accumulate(h->mix, nb, S.state, cs));
+      LAUNCH(h, K_AUX, cs, launch_axpy_mixed(gf, h->x64, S.x, h->nrm, cs));
+    }
+    h->prof.target = nullptr;
+    ok = (cudaStreamEndCapture(cs, &tmp) == cudaSuccess) && ok;
+  }
+  // inner body: one MPCG iteration
+  ok = ok && cudaStreamBeginCaptureToGraph(cs, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                 cudaSuccess;
+  if (ok) {
+    h->mg_ibody = 0;
+    h->prof.target = &h->mg_ibody;
+    enqueue_body<float>(h, S, c_in, 1, cs);
+    h->prof.target = nullptr;
+    ok = (cudaStreamEndCapture(cs, &tmp) == cudaSuccess) && ok;
+  }
+  h->prof.target = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+  if (!ok) {
+    cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return false;
+  }
+  h->mgraph = graph;
+  h->mexec = exec;
+  h->mg_rtol = rtol;
+  h->mg_maxit = maxit;
+  h->mg_hist = S.hist_cap;
+  return true;
+}
+
+namespace {
+void drop_mixed_graph_fwd(mg_hierarchy* h) { drop_mixed_graph(h); }
+}  // namespace
+
+// The graph form of solve_mixed (no histories).  Returns MPCG_ERR_CUDA with
+// *fallback = true when the graph cannot be built (the caller then runs the
+// host-driven loop).
+static mpcg_status solve_mixed_graph(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit,
+                                     int* iters_out, bool* fallback) {
+  *fallback = false;
+  CKS(build_f32(h));
+  CKS(build_solver<float>(h, h->s32));
+  Solver<float>& S = h->s32;
+  CKS(ensure_hist(h, S, maxit));
+  cudaStream_t s = h->stream;
+  const GridDesc& gf = h->lev[h->levels - 1].g;
+  const int nb = h->nb;
+  if (!h->mexec || h->mg_rtol != rtol || h->mg_maxit != maxit || h->mg_hist != S.hist_cap) {
+    if (!build_mixed_graph(h, rtol, maxit)) {
+      *fallback = true;
+      return MPCG_ERR_CUDA;
+    }
+  }
+  for (int p = 0; p < nb; ++p) {
+    LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, b + (size_t)p * gf.n, gf.n, h->b64 + (size_t)p * gf.len, 1, s));
+    LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, x + (size_t)p * gf.n, gf.n, h->x64 + (size_t)p * gf.len, 1, s));
+  }
+  CK(cudaGraphLaunch(h->mexec, s));
+  for (int p = 0; p < nb; ++p)
+    LAUNCH(h, K_PACK, s, launch_unpack<double, double>(gf, h->x64 + (size_t)p * gf.len, x + (size_t)p * gf.n, gf.n, 1, s));
+  std::vector<int> mix(3 * (size_t)nb);
+  int steps = 0;
+  CK(cudaMemcpyAsync(mix.data(), h->mix, sizeof(int) * 3 * nb, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&steps, h->outer, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  // launches executed: init, per step the head, inner prologue and tail, per
+  // inner iteration the body (the slowest problem's count for a batch)
+  long long kmax = 0;
+  for (int p = 0; p < nb; ++p) kmax = std::max<long long>(kmax, mix[3 * p]);
+  h->prof.live += 1 + (long long)steps * (h->mg_head + h->mg_iprol + h->mg_tail) + kmax * h->mg_ibody;
+  mpcg_status result = MPCG_OK;
+  for (int p = 0; p < nb; ++p) {
+    if (iters_out) iters_out[p] = mix[3 * p];
+    const int status = mix[3 * p + 1];
+    if (status == 3) {
+      set_err("breakdown in the FP32 inner solve of problem %d", p);
+      result = MPCG_ERR_BREAKDOWN;
+    } else if (status != 1 && result == MPCG_OK) {
+      result = MPCG_NOT_CONVERGED;
+    }
+  }
+  return result;
+}
+
 static mpcg_status solve_mixed(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, int* iters_out,
                                double* res_hist) {
   CKS(build_f32(h));
@@ -973,9 +1150,15 @@ mpcg_status mpcg_solve(mg_hierarchy* h, const double* b, double* x, double rtol,
     }
   }
   h->prof.reset();
-  mpcg_status st = h->opt.precision == MPCG_MIXED
-                       ? solve_mixed(h, bd, xd, rtol, maxit, iters_out, res_hist)
-                       : solve_fp64(h, bd, xd, rtol, maxit, iters_out, res_hist, alpha_hist);
+  mpcg_status st;
+  if (h->opt.precision == MPCG_MIXED) {
+    bool fallback = true;
+    st = MPCG_OK;
+    if (h->opt.use_graph && !h->force_direct && !res_hist) st = solve_mixed_graph(h, bd, xd, rtol, maxit, iters_out, &fallback);
+    if (fallback) st = solve_mixed(h, bd, xd, rtol, maxit, iters_out, res_hist);
+  } else {
+    st = solve_fp64(h, bd, xd, rtol, maxit, iters_out, res_hist, alpha_hist);
+  }
   h->prof.flush();
   h->last_launches = h->prof.live;
   if (h->net_on && h->net_err) {
@@ -1130,8 +1313,10 @@ mpcg_status copy_floats(float* dst, const float* src, int n, cudaStream_t s) {
 }
 
 // Rebuild the solvers after the column count changed.
+void drop_mixed_graph_fwd(mg_hierarchy* h);
 mpcg_status rebuild_solvers(mg_hierarchy* h) {
   CK(cudaStreamSynchronize(h->stream));
+  drop_mixed_graph_fwd(h);
   const bool had32 = h->s32.built;
   h->s64.release();
   h->s32.release();

@@ -127,6 +127,13 @@ template <typename T>
 void launch_coarse_solve(const GridDesc& g, const double* inv, const T* r, T* out, const DevState* state,
                          cudaStream_t s);
 // ||r||^2 style sum of partials (value-major) into out[nv]
+// Device side of the mixed-precision refinement loop: mix holds per problem
+// {inner iterations so far, status, active}.
+void launch_mix_init(int* mix, int* active, int nb, int* outer, cudaStream_t s);
+void launch_outer_check(int* mix, int* active, int nb, const double* nrm, double rtol, int maxit, int max_outer,
+                        int* outer, DevState* st, double inner_rtol, int m, int C, double delta, double tau,
+                        cudaGraphConditionalHandle cond, cudaStream_t s);
+void launch_outer_accumulate(int* mix, int nb, const DevState* st, cudaStream_t s);
 void launch_sum_partials(const double* part, int nb, int nv, int nblk, double* out, cudaStream_t s);
 // x64 += scale * d (padded, FP32 d); scale read from device
 void launch_axpy_mixed(const GridDesc& g, double* x, const float* d, const double* scale,

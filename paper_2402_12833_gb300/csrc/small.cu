@@ -535,6 +535,71 @@ __global__ void k_scale_to_f32(GridDesc g, const double* __restrict__ r, const d
 }
 
 // flag |= some problem of the batch is still running.
+// Device side of the mixed-precision refinement loop (one graph per solve):
+// mix[p] = {inner iterations so far, status (0 running, 1 converged, 2 out
+// of iterations or steps, 3 breakdown), active}.
+__global__ void k_mix_init(int* mix, int* active, int nb, int* outer) {
+  for (int p = threadIdx.x; p < nb; p += blockDim.x) {
+    mix[3 * p + 0] = 0;
+    mix[3 * p + 1] = 0;
+    mix[3 * p + 2] = 1;
+    active[p] = 1;
+  }
+  if (threadIdx.x == 0) *outer = 0;
+}
+
+// After the FP64 residual: decide every problem's state from |r|^2 and |b|^2
+// (nrm[2p], nrm[2p+1]), hand the running ones their inner parameters
+// (tolerance, remaining iterations, window, columns, drop and cutoff
+// thresholds), and set the outer loop's condition (some problem running).
+__global__ void k_outer_check(int* mix, int* active, int nb, const double* nrm, double rtol, int maxit,
+                              int max_outer, int* outer, DevState* st, double inner_rtol, int m, int C,
+                              double delta, double tau, cudaGraphConditionalHandle cond) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  const int step = *outer;
+  for (int p = threadIdx.x; p < nb; p += blockDim.x) {
+    int* mp = mix + 3 * p;
+    int budget = 0;
+    if (mp[2]) {
+      const double rn = sqrt(nrm[2 * p]), bn = sqrt(nrm[2 * p + 1]);
+      if (!isfinite(rn)) { mp[1] = 3; mp[2] = 0; }
+      else if (bn == 0.0 || rn <= rtol * bn) { mp[1] = 1; mp[2] = 0; }
+      else if (mp[0] >= maxit || step >= max_outer) { mp[1] = 2; mp[2] = 0; }
+      else {
+        budget = maxit - mp[0];
+        atomicOr(&any, 1);
+      }
+    }
+    active[p] = mp[2];
+    st[p].rtol = inner_rtol;
+    st[p].maxit = budget;
+    st[p].m = m;
+    st[p].ncols = C;
+    st[p].delta = delta;
+    st[p].tau = tau;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *outer = step + 1;
+    cudaGraphSetConditional(cond, any ? 1u : 0u);
+  }
+}
+
+// After an inner solve: count its iterations, stop problems that broke down
+// or made no progress.
+__global__ void k_outer_accumulate(int* mix, int nb, const DevState* st) {
+  for (int p = threadIdx.x; p < nb; p += blockDim.x) {
+    int* mp = mix + 3 * p;
+    if (!mp[2]) continue;
+    const int k = st[p].k;
+    mp[0] += k;
+    if (st[p].done == 3) { mp[1] = 3; mp[2] = 0; }
+    else if (k == 0) { mp[1] = 2; mp[2] = 0; }
+  }
+}
+
 __global__ void k_any_running(const DevState* st, int nb, int* flag) {
   for (int b = threadIdx.x; b < nb; b += blockDim.x)
     if (st[b].done == 0) atomicOr(flag, 1);
@@ -597,6 +662,18 @@ template void launch_coarse_solve<double>(const GridDesc&, const double*, const 
                                           cudaStream_t);
 template void launch_coarse_solve<float>(const GridDesc&, const double*, const float*, float*, const DevState*,
                                          cudaStream_t);
+void launch_mix_init(int* mix, int* active, int nb, int* outer, cudaStream_t s) {
+  k_mix_init<<<1, kBlock, 0, s>>>(mix, active, nb, outer);
+}
+void launch_outer_check(int* mix, int* active, int nb, const double* nrm, double rtol, int maxit, int max_outer,
+                        int* outer, DevState* st, double inner_rtol, int m, int C, double delta, double tau,
+                        cudaGraphConditionalHandle cond, cudaStream_t s) {
+  k_outer_check<<<1, kBlock, 0, s>>>(mix, active, nb, nrm, rtol, maxit, max_outer, outer, st, inner_rtol, m, C, delta,
+                                     tau, cond);
+}
+void launch_outer_accumulate(int* mix, int nb, const DevState* st, cudaStream_t s) {
+  k_outer_accumulate<<<1, kBlock, 0, s>>>(mix, nb, st);
+}
 void launch_sum_partials(const double* part, int nb, int nv, int nblk, double* out, cudaStream_t s) {
   k_sum_partials<<<nb, kBlock, 0, s>>>(part, nv, nblk, out);
 }
