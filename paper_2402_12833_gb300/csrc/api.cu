@@ -366,8 +366,15 @@ void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState*
   cudaStreamWaitEvent(s2, h->ev_fork, 0);
   enqueue_smooth<T>(h, S, J, r, Z + (size_t)J * h->lev[J].g.cp, state, s2);
   cudaEventRecord(h->ev_fine, s2);
+  // grids of at most kTailPoints padded points (scalar unknowns, two sweeps)
+  // go through one single-block launch: their restrictions, smoothings and
+  // the coarse solve are latency-bound as separate launches
+  int jt = -1;
+  if (h->lev[0].g.ncomp == 1 && h->opt.nu == 2)
+    for (int j = 0; j < J; ++j)
+      if (h->lev[j].g.npts <= kTailPoints) jt = j;
   const T* rj = r;
-  for (int j = J; j >= 1; --j) {
+  for (int j = J; j >= (jt >= 0 ? jt + 2 : 1); --j) {
     LAUNCH(h, K_RESTRICT, s, launch_restrict<T>(h->lev[j].g, h->lev[j - 1].g, rj, S.rlev[j - 1], state, s));
     rj = S.rlev[j - 1];
     if (j - 1 >= 1) {   // smoothing of grid j-1 can start now, on its own branch
@@ -378,12 +385,28 @@ void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState*
       cudaEventRecord(h->ev_sm[j - 1], s3);
     }
   }
-  LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->A0inv, S.rlev[0], S.zc[0], state, s));
+  if (jt >= 0) {
+    GridDesc tg[kMaxLevels];
+    const T* tst[kMaxLevels];
+    const T* tdi[kMaxLevels];
+    T* tr[kMaxLevels];
+    T* tz[kMaxLevels];
+    for (int j = 0; j <= jt + 1; ++j) {
+      tg[j] = h->lev[j].g;
+      tst[j] = st_of<T>(h->lev[j]);
+      tdi[j] = dinv_of<T>(h->lev[j]);
+      tr[j] = j <= jt ? S.rlev[j] : nullptr;
+      tz[j] = j <= jt ? S.zc[j] + (size_t)j * h->lev[j].g.cp : nullptr;
+    }
+    LAUNCH(h, K_COARSE, s, launch_coarse_tail<T>(jt, tg, tst, tdi, tr, tz, rj, h->A0inv, state, s));
+  } else {
+    LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->A0inv, S.rlev[0], S.zc[0], state, s));
+  }
   // every grid's correction straight to the fine grid in one launch
   const T* src[kMaxLevels];
   GridDesc gcs[kMaxLevels];
   for (int j = 0; j < J; ++j) {
-    if (j >= 1) cudaStreamWaitEvent(s, h->ev_sm[j], 0);
+    if (j >= 1 && j > jt) cudaStreamWaitEvent(s, h->ev_sm[j], 0);
     src[j] = S.zc[j] + (size_t)j * h->lev[j].g.cp;
     gcs[j] = h->lev[j].g;
   }

@@ -10,6 +10,7 @@ namespace mpcg {
 // Maximum number of thread blocks of the grid-stride reduction kernels; the
 // partial-sum buffers are sized for it.
 constexpr int kRedBlocks = 1216;         // 152 SMs x 8 (stencil kernels with partial sums)
+constexpr int kTailPoints = 4096;     // grids this small go through the single-block MG tail
 constexpr int kStreamBlocks = 608;       // 152 SMs x 4 (streaming block kernels)
 constexpr int kStreamBlocksMax = 8192;
 constexpr int kGramChunksMax = 4096;
@@ -66,6 +67,12 @@ template <typename T>
 void launch_prolong(const GridDesc& gc, const GridDesc& gf, const T* coarse, T* fine, int ncols,
                     const DevState* state, cudaStream_t s);
 // coarse stencil = P^T A P (FP64)
+// The small-grid tail of the MG chain in one block (scalar unknowns, nu = 2):
+// restrictions from grid jt + 1 (residual rin) down to 0 into r[j], Jacobi
+// smoothing of grids 1 .. jt into z[j], coarse solve into z[0].
+template <typename T>
+void launch_coarse_tail(int jt, const GridDesc* g, const T* const* st, const T* const* dinv, T* const* r,
+                        T* const* z, const T* rin, const double* a0inv, const DevState* state, cudaStream_t s);
 // Z columns 0 .. J-1 on the fine grid gf from grid j's correction coarse[j]
 // (grid descriptor gcs[j]) by the composite multilinear interpolation.
 template <typename T>

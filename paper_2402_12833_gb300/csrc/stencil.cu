@@ -444,6 +444,93 @@ __global__ void __launch_bounds__(kBlock) k_prolong_all(GridDesc gf, CoarseSrc<T
   }
 }
 
+// The small-grid tail of the MG chain in one block (scalar unknowns, two
+// Jacobi sweeps): the restrictions from grid jt + 1 down to grid 0, the
+// damped-Jacobi smoothing of grids 1 .. jt and the exact coarsest solve.
+// Grids this small are latency-bound as separate launches; one block of
+// 1024 threads takes them in turn with block barriers in between.
+template <typename T>
+struct TailArgs {
+  int jt;                          // finest grid of the tail
+  GridDesc g[kMaxLevels];
+  const T* st[kMaxLevels];         // stencil planes of grid j
+  const T* dinv[kMaxLevels];       // damped inverse diagonal of grid j
+  T* r[kMaxLevels];                // restricted residual of grid j (j <= jt)
+  T* z[kMaxLevels];                // correction of grid j (grid 0: the coarse solve)
+  const T* rin;                    // residual of grid jt + 1
+  const double* a0inv;             // explicit inverse of the coarsest operator
+};
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(1024) k_coarse_tail(TailArgs<T> a, const DevState* state) {
+  const int pb = blockIdx.y;
+  if (state && state[pb].done) return;
+  constexpr int S = DIM == 3 ? 27 : 9;
+  // restrictions jt + 1 -> jt -> ... -> 0
+  for (int j = a.jt; j >= 0; --j) {
+    const GridDesc& gf = a.g[j + 1];
+    const GridDesc& gc = a.g[j];
+    const T* rf = (j == a.jt ? a.rin : a.r[j + 1]) + (long long)pb * gf.len;
+    T* rc = a.r[j] + (long long)pb * gc.len;
+    for (long long t = threadIdx.x; t < gc.npts; t += blockDim.x) {
+      int X, Y, Z, c;
+      decode(gc, t, X, Y, Z, c);
+      T acc = 0;
+      if (interior(gc, X, Y, Z)) {
+        const long long pf = gf.px, pp = gf.pxy;
+        const long long idf = gf.G + (2 * X + gf.lox) + pf * (2 * Y + gf.loy) + (DIM == 3 ? pp * (2 * Z + gf.loz) : 0);
+        for (int ez = (DIM == 3 ? -1 : 0); ez <= (DIM == 3 ? 1 : 0); ++ez)
+          for (int ey = -1; ey <= 1; ++ey)
+            for (int ex = -1; ex <= 1; ++ex) {
+              const T w = (T)((ex ? 0.5 : 1.0) * (ey ? 0.5 : 1.0) * (ez ? 0.5 : 1.0));
+              acc = fma(w, rf[idf + ex + pf * ey + pp * ez], acc);
+            }
+      }
+      rc[gc.G + t] = acc;
+    }
+    __syncthreads();
+  }
+  // two damped-Jacobi sweeps from zero on grids 1 .. jt (Eq. 2, c_0 = 0):
+  // out = s1 + dinv (r - A s1) with s1 = dinv r formed at the neighbours
+  for (int j = 1; j <= a.jt; ++j) {
+    const GridDesc& g = a.g[j];
+    const long long bo = (long long)pb * g.len + g.G;
+    const T* st = a.st[j] + bo;
+    const T* di = a.dinv[j] + bo;
+    const T* rr = a.r[j] + bo;
+    T* out = a.z[j] + bo;
+    for (long long t = threadIdx.x; t < g.npts; t += blockDim.x) {
+      T acc = 0;
+      for (int s = 0; s < S; ++s) {
+        const long long off = (s % 3 - 1) + g.px * ((s / 3) % 3 - 1) + (DIM == 3 ? g.pxy * (s / 9 - 1) : 0);
+        acc = fma(st[(long long)s * g.cp + t], di[t + off] * rr[t + off], acc);
+      }
+      const T s1 = di[t] * rr[t];
+      out[t] = s1 + di[t] * (rr[t] - acc);
+    }
+  }
+  // exact coarsest solve: warp per row of the explicit inverse
+  {
+    extern __shared__ double yv[];
+    const GridDesc& g = a.g[0];
+    const int n = (int)g.n;
+    const double* inv = a.a0inv + (long long)pb * n * n;
+    const T* r0 = a.r[0] + (long long)pb * g.len;
+    T* out = a.z[0] + (long long)pb * g.len;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) yv[i] = (double)r0[padded_index(g, i)];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int i = threadIdx.x >> 5; i < n; i += blockDim.x >> 5) {
+      const double* row = inv + (long long)i * n;
+      double s = 0.0;
+      for (int k = lane; k < n; k += 32) s = fma(row[k], yv[k], s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) out[padded_index(g, i)] = (T)s;
+    }
+  }
+}
+
 // Galerkin product A_c = P^T A_f P, one coarse row per thread.  For vector
 // unknowns P interpolates componentwise, so every component pair (a, b) is a
 // scalar Galerkin product of its own plane group b * 3^DIM + s.
@@ -855,6 +942,32 @@ template void launch_prolong<double>(const GridDesc&, const GridDesc&, const dou
                                      const DevState*, cudaStream_t);
 template void launch_prolong<float>(const GridDesc&, const GridDesc&, const float*, float*, int, const DevState*,
                                     cudaStream_t);
+
+template <typename T>
+void launch_coarse_tail(int jt, const GridDesc* g, const T* const* st, const T* const* dinv, T* const* r,
+                        T* const* z, const T* rin, const double* a0inv, const DevState* state, cudaStream_t s) {
+  TailArgs<T> a = {};
+  a.jt = jt;
+  for (int j = 0; j <= jt + 1; ++j) {
+    a.g[j] = g[j];
+    a.st[j] = st[j];
+    a.dinv[j] = dinv[j];
+    a.r[j] = r[j];
+    a.z[j] = z[j];
+  }
+  a.rin = rin;
+  a.a0inv = a0inv;
+  const dim3 grid(1, g[0].nb);
+  const size_t smem = (size_t)g[0].n * sizeof(double);
+  if (g[0].dim == 3) k_coarse_tail<T, 3><<<grid, 1024, smem, s>>>(a, state);
+  else k_coarse_tail<T, 2><<<grid, 1024, smem, s>>>(a, state);
+}
+template void launch_coarse_tail<double>(int, const GridDesc*, const double* const*, const double* const*,
+                                         double* const*, double* const*, const double*, const double*,
+                                         const DevState*, cudaStream_t);
+template void launch_coarse_tail<float>(int, const GridDesc*, const float* const*, const float* const*,
+                                        float* const*, float* const*, const float*, const double*, const DevState*,
+                                        cudaStream_t);
 
 template <typename T>
 void launch_prolong_all(const GridDesc& gf, const T* const* coarse, const GridDesc* gcs, int J, T* Z,
