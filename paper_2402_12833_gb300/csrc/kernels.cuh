@@ -10,7 +10,7 @@ namespace mpcg {
 // Maximum number of thread blocks of the grid-stride reduction kernels; the
 // partial-sum buffers are sized for it.
 constexpr int kRedBlocks = 1216;         // 152 SMs x 8 (stencil kernels with partial sums)
-constexpr int kTailPoints = 4096;     // grids this small go through the single-block MG tail
+constexpr int kTailPoints = 512;      // grids this small go through the single-block MG tail
 constexpr int kStreamBlocks = 608;       // 152 SMs x 4 (streaming block kernels)
 constexpr int kStreamBlocksMax = 8192;
 constexpr int kGramChunksMax = 4096;
