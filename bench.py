@@ -673,6 +673,54 @@ def bench_elasticity(args):
     return 0
 
 
+def bench_example1(args):
+    """Section 3, Example 1 on the GPU: anisotropic diffusion, 160 x 160
+    elements, 4 grids (20 x 20 coarsest), k_xx = 10^-n (n = 0..7), k_yy = 1,
+    f = 1, zero Dirichlet data, FP64, rtol 1e-8: iterations and time of
+    additive MG-MPCG (one column per grid, m = 5 and m = 1) and additive MG-PCG
+    (the summed correction B r as a single direction, m = 1), with the
+    oracle's iteration counts beside them."""
+    import torch
+    from oracle import mg as omg
+    from oracle import mpcg as ompcg
+    from paper_2402_12833_gb300 import build as _build
+    from paper_2402_12833_gb300 import mpcg as M
+    from paper_2402_12833_gb300 import problems as pb
+    _build.build()
+    M.load()
+    rows = []
+    for n in range(8):
+        kxx = 10.0 ** (-n)
+        prob = pb.example1(kxx)
+        st = torch.from_numpy(prob.stencil).cuda()
+        b = torch.from_numpy(prob.b).cuda()
+        x = torch.zeros_like(b)
+        row = {"kxx": kxx}
+        for key, opts in (("mpcg_m5", dict(m=5)), ("mpcg_m1", dict(m=1)), ("pcg", dict(m=1, sum_columns=1))):
+            H = M.Hierarchy(st, 2, prob.nodes, prob.levels, **opts)
+            res = {}
+
+            def step():
+                x.zero_()
+                res["st"], res["k"], _, _ = H.solve(b, x, rtol=RTOL, maxit=20000, histories=False)
+
+            ms = _timed(step, args.steps, 1, torch.cuda.current_stream())
+            row[key] = {"iterations": int(res["k"]), "ms": ms, "status": int(res["st"])}
+            H.close()
+        O = omg.Hierarchy(2, prob.n1, prob.stencil, prob.levels)
+        row["oracle_iterations"] = {
+            "mpcg_m5": ompcg.mpcg(O.A[-1], prob.b, O.mg_columns, m=5, rtol=RTOL, maxit=20000).iters,
+            "pcg": ompcg.mpcg(O.A[-1], prob.b, lambda r: O.additive_mg(r)[:, None], m=1, rtol=RTOL,
+                              maxit=20000).iters}
+        rows.append(row)
+    print(json.dumps({"metric": "iterations to 1e-8 rel. residual", "workload": "example1",
+                      "config": {"workload": "Section 3 Example 1: (0,1)^2, 160x160 Q1 elements, 4 grids (20x20 "
+                                             "coarsest), K = diag(k_xx, 1), f = 1, zero Dirichlet, damped Jacobi "
+                                             "nu=2 w=2/3, FP64, rtol 1e-8"},
+                      "rows": rows}))
+    return 0
+
+
 def bench_learned(args):
     """2D high-contrast diffusion, 1025^2 nodes, 9 grids, f = 1, kappa seed 3:
     the mixed-precision solver without and with the learned column; the
@@ -751,7 +799,8 @@ def bench_learned(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["poisson3d", "batched", "learned", "elasticity"], default="poisson3d",
+    ap.add_argument("--workload", choices=["poisson3d", "batched", "learned", "elasticity", "example1"],
+                    default="poisson3d",
                     help="poisson3d: the headline line; batched / learned / elasticity: the other workloads")
     ap.add_argument("--epochs", type=int, default=20, help="training epochs of the learned workload")
     ap.add_argument("--gpus", type=int, default=1)
@@ -773,6 +822,8 @@ def main():
         return bench_batched(args)
     if args.workload == "elasticity":
         return bench_elasticity(args)
+    if args.workload == "example1":
+        return bench_example1(args)
     if args.workload == "learned":
         return bench_learned(args)
     return bench_ours(args)

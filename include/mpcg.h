@@ -62,9 +62,9 @@ enum { MPCG_FP64 = 0, MPCG_MIXED = 1 };
 /*
  * A fine-grid operator in stencil form.
  *   dim        2 or 3
- *   nodes      nodes per side of the grid, boundary included; nodes - 1 must
- *              be a power of two >= 4 (so that the grid can be coarsened
- *              down to 5 nodes per side)
+ *   nodes      nodes per side of the grid, boundary included; nodes - 1 (the
+ *              elements per side) must be divisible by 2^(levels-1) with at
+ *              least 2 elements per side left on the coarsest grid
  *   dofs_per_node
  *              1 (scalar problems such as the diffusion equation of
  *              Section 1), or 3 in 3D (linear elasticity: unknown
@@ -102,7 +102,8 @@ typedef struct {
 /* Solver options.  mpcg_default_options() fills the paper's / the default
  * values: m = 5 (Section 3 uses the last 5 blocks), nu = 2, omega = 2/3,
  * pinv_tau = 1e-12, drop_delta = 1e-10, precision MPCG_FP64,
- * inner_rtol = 3e-3, inner pinv_tau = 1e-6, inner drop_delta = 1e-5.  The FP32
+ * inner_rtol = 3e-3, inner pinv_tau = 1e-6, inner drop_delta = 1e-5,
+ * use_graph = 1, sum_columns = 0.  The FP32
  * inner solves converge in fewer total iterations when restarted often (the
  * FP64 refinement renews the residual and the search space), hence the
  * loose inner tolerance. */
@@ -119,6 +120,10 @@ typedef struct {
   int max_outer;         /* MPCG_MIXED: maximum refinement steps */
   int use_graph;         /* 1: run each solve as one CUDA graph with a device-side
                             loop; 0: launch the kernels directly (same results) */
+  int sum_columns;       /* 1: use the sum of the grids' corrections, B r of Eq. 3,
+                            as a single search direction (additive MG as one
+                            preconditioner; with m = 1 this is additive-MG PCG,
+                            the paper's comparison method); 0: one column per grid */
   void* stream;          /* cudaStream_t */
 } mpcg_options;
 

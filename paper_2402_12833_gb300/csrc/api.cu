@@ -90,6 +90,7 @@ struct Solver {
   T* tmp[kMaxLevels] = {};
   T* tmp2[kMaxLevels] = {};
   T *x = nullptr, *r = nullptr, *b = nullptr, *Z = nullptr, *AZ = nullptr;
+  T* Zmg = nullptr;   // the per-grid columns when they are summed into one
   Window<T> win = {};
   DevState* state = nullptr;
   double *part_res = nullptr, *part_zaz = nullptr, *part_W = nullptr, *part_G = nullptr, *part_r = nullptr;
@@ -256,7 +257,7 @@ mpcg_status build_solver(mg_hierarchy* h, Solver<T>& S) {
   cudaStream_t s = h->stream;
   const int J = h->levels - 1;
   const GridDesc& gf = h->lev[J].g;
-  S.C = h->levels + (h->net_on ? 1 : 0);
+  S.C = h->opt.sum_columns ? 1 : h->levels + (h->net_on ? 1 : 0);
   S.m = h->opt.m;
   const int C = S.C;
   const size_t nb = (size_t)h->nb;   // all buffers hold the whole batch
@@ -264,6 +265,7 @@ mpcg_status build_solver(mg_hierarchy* h, Solver<T>& S) {
   CKS(S.mem.get(&S.r, gf.cp, s));
   CKS(S.mem.get(&S.b, gf.cp, s));
   CKS(S.mem.get(&S.Z, (size_t)C * gf.cp, s));
+  if (h->opt.sum_columns) CKS(S.mem.get(&S.Zmg, (size_t)h->levels * gf.cp, s));
   CKS(S.mem.get(&S.AZ, (size_t)C * gf.cp, s));
   for (int j = 0; j < S.m; ++j) {
     CKS(S.mem.get(&S.win.P[j], (size_t)C * gf.cp, s));
@@ -440,7 +442,12 @@ template <typename T>
 void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
   const Level& L = h->lev[h->levels - 1];
   const int C = S.C;
-  enqueue_mg<T>(h, S, S.r, S.Z, S.state, s);
+  if (h->opt.sum_columns) {   // additive MG as one preconditioner: Z = B r (Eq. 3)
+    enqueue_mg<T>(h, S, S.r, S.Zmg, S.state, s);
+    LAUNCH(h, K_AUX, s, launch_sum_columns<T>(L.g, S.Zmg, h->levels, S.Z, S.state, s));
+  } else {
+    enqueue_mg<T>(h, S, S.r, S.Z, S.state, s);
+  }
   if (h->net_on) {
     LAUNCH(h, K_NET, s,
            launch_net_infer<T>(L.g, 1, S.r, L.g.len, h->net_c, h->net_wtc, S.state, nullptr,
@@ -647,12 +654,15 @@ mpcg_status mpcg_default_options(mpcg_options* opt) {
   opt->inner_drop_delta = 1e-5;
   opt->max_outer = 20;
   opt->use_graph = 1;
+  opt->sum_columns = 0;
   opt->stream = nullptr;
   return MPCG_OK;
 }
 
 int mg_num_levels(const mg_hierarchy* h) { return h ? h->levels : -1; }
-int mg_num_columns(const mg_hierarchy* h) { return h ? h->levels + (h->net_on ? 1 : 0) : -1; }
+int mg_num_columns(const mg_hierarchy* h) {
+  return h ? (h->opt.sum_columns ? 1 : h->levels + (h->net_on ? 1 : 0)) : -1;
+}
 long long mg_level_size(const mg_hierarchy* h, int level) {
   if (!h || level < 0 || level >= h->levels) return -1;
   return h->lev[level].g.n;
@@ -712,9 +722,9 @@ static mpcg_status setup_impl(const mg_operator* ops, int nb, int levels, const 
     set_err("dim must be 2 or 3 (got %d)", A->dim);
     return MPCG_ERR_ARG;
   }
-  const int q = A->nodes - 1;
-  if (q < 4 || (q & (q - 1)) != 0 || q > (1 << 15)) {
-    set_err("nodes - 1 must be a power of two in [4, 32768] (nodes = %d)", A->nodes);
+  const int q = A->nodes - 1;   // elements per side
+  if (q < 2 || q > (1 << 15)) {
+    set_err("nodes - 1 must be in [2, 32768] (nodes = %d)", A->nodes);
     return MPCG_ERR_ARG;
   }
   const int ncomp = A->dofs_per_node;
@@ -727,19 +737,24 @@ static mpcg_status setup_impl(const mg_operator* ops, int nb, int levels, const 
     return MPCG_ERR_ARG;
   }
   const unsigned faces = A->dim == 2 ? (A->dirichlet_faces & 0xFu) : A->dirichlet_faces;   // 2D: no z faces
-  int k = 0;
-  while ((1 << k) < q) ++k;
+  // uniform coarsening halves the elements per side: nodes - 1 must be
+  // divisible by 2^(levels-1), leaving at least 2 elements on the coarsest grid
   const int maxcols = ncomp > 1 ? kMaxVecCols : MPCG_MAX_COLS;
-  if (levels < 1 || levels > k || levels > kMaxLevels || levels > maxcols) {
-    set_err("levels = %d invalid for %d nodes per side (1..%d)", levels, A->nodes, k < maxcols ? k : maxcols);
+  if (levels < 1 || levels > kMaxLevels || levels > maxcols || (q % (1 << (levels - 1))) != 0 ||
+      (q >> (levels - 1)) < 2) {
+    set_err("levels = %d invalid for %d nodes per side (nodes - 1 must be a multiple of 2^(levels-1) with at "
+            "least 2 elements per side left on the coarsest grid; at most %d levels)",
+            levels, A->nodes, maxcols < kMaxLevels ? maxcols : kMaxLevels);
     return MPCG_ERR_ARG;
   }
   mpcg_options opt;
   if (opt_in) opt = *opt_in;
   else mpcg_default_options(&opt);
   if (opt.m < 1 || opt.m > MPCG_MAX_WINDOW || opt.nu < 1 || !(opt.omega > 0.0) || opt.pinv_tau < 0.0 ||
-      opt.drop_delta < 0.0 || (opt.precision != MPCG_FP64 && opt.precision != MPCG_MIXED) || opt.max_outer < 1) {
-    set_err("invalid options (m in 1..%d, nu >= 1, omega > 0, tau/delta >= 0, max_outer >= 1)", MPCG_MAX_WINDOW);
+      opt.drop_delta < 0.0 || (opt.precision != MPCG_FP64 && opt.precision != MPCG_MIXED) || opt.max_outer < 1 ||
+      (opt.sum_columns != 0 && opt.sum_columns != 1)) {
+    set_err("invalid options (m in 1..%d, nu >= 1, omega > 0, tau/delta >= 0, max_outer >= 1, sum_columns 0/1)",
+            MPCG_MAX_WINDOW);
     return MPCG_ERR_ARG;
   }
   const long long n0 = make_grid_nodes(A->dim, (q >> (levels - 1)) + 1, faces, ncomp).n;
@@ -1269,9 +1284,10 @@ mpcg_status mg_corrections(mg_hierarchy* h, const double* r, double* Z) {
   cudaStream_t s = h->stream;
   Solver<double>& S = h->s64;
   const GridDesc& gf = h->lev[h->levels - 1].g;
+  double* Zc = h->opt.sum_columns ? S.Zmg : S.Z;   // the per-grid columns
   launch_pack<double, double>(gf, r, gf.n, S.r, 1, s);
-  enqueue_mg<double>(h, S, S.r, S.Z, nullptr, s);
-  launch_unpack<double, double>(gf, S.Z, Z, gf.n, h->levels, s);
+  enqueue_mg<double>(h, S, S.r, Zc, nullptr, s);
+  launch_unpack<double, double>(gf, Zc, Z, gf.n, h->levels, s);
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
   return MPCG_OK;
@@ -1362,8 +1378,8 @@ mpcg_status mg_learned_attach(mg_hierarchy* h, const float* params, int nparams)
     set_err("params must hold mg_learned_num_params() = %d floats", kNetParams);
     return MPCG_ERR_ARG;
   }
-  if (h->levels + 1 > MPCG_MAX_COLS) {
-    set_err("too many grids for an extra column");
+  if (h->levels + 1 > MPCG_MAX_COLS || h->opt.sum_columns) {
+    set_err("too many grids for an extra column, or the columns are summed into one");
     return MPCG_ERR_ARG;
   }
   CK(cudaSetDevice(h->device));

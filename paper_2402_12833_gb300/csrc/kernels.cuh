@@ -67,6 +67,9 @@ template <typename T>
 void launch_prolong(const GridDesc& gc, const GridDesc& gf, const T* coarse, T* fine, int ncols,
                     const DevState* state, cudaStream_t s);
 // coarse stencil = P^T A P (FP64)
+// out = Zc[0] + ... + Zc[ncols-1] (columns cp apart).
+template <typename T>
+void launch_sum_columns(const GridDesc& g, const T* Zc, int ncols, T* out, const DevState* state, cudaStream_t s);
 // The small-grid tail of the MG chain in one block (scalar unknowns, nu = 2):
 // restrictions from grid jt + 1 (residual rin) down to 0 into r[j], Jacobi
 // smoothing of grids 1 .. jt into z[j], coarse solve into z[0].

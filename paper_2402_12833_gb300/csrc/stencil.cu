@@ -943,6 +943,29 @@ template void launch_prolong<double>(const GridDesc&, const GridDesc&, const dou
 template void launch_prolong<float>(const GridDesc&, const GridDesc&, const float*, float*, int, const DevState*,
                                     cudaStream_t);
 
+// out = sum of the ncols columns of Zc (the additive MG correction B r of
+// Eq. 3 as a single search direction), columns added in order.
+template <typename T>
+__global__ void k_sum_columns(GridDesc g, const T* __restrict__ Zc, int ncols, T* __restrict__ out,
+                              const DevState* state) {
+  const int pb = blockIdx.y;
+  if (state && state[pb].done) return;
+  const long long o = (long long)pb * g.len + g.G;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.npts;
+       t += (long long)gridDim.x * blockDim.x) {
+    T v = Zc[o + t];
+    for (int c = 1; c < ncols; ++c) v += Zc[(long long)c * g.cp + o + t];
+    out[o + t] = v;
+  }
+}
+
+template <typename T>
+void launch_sum_columns(const GridDesc& g, const T* Zc, int ncols, T* out, const DevState* state, cudaStream_t s) {
+  k_sum_columns<T><<<dim3(stream_blocks(g), g.nb), kBlock, 0, s>>>(g, Zc, ncols, out, state);
+}
+template void launch_sum_columns<double>(const GridDesc&, const double*, int, double*, const DevState*, cudaStream_t);
+template void launch_sum_columns<float>(const GridDesc&, const float*, int, float*, const DevState*, cudaStream_t);
+
 template <typename T>
 void launch_coarse_tail(int jt, const GridDesc* g, const T* const* st, const T* const* dinv, T* const* r,
                         T* const* z, const T* rin, const double* a0inv, const DevState* state, cudaStream_t s) {

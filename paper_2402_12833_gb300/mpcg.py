@@ -48,7 +48,7 @@ class mpcg_options(C.Structure):
     _fields_ = [("m", C.c_int), ("nu", C.c_int), ("omega", C.c_double), ("pinv_tau", C.c_double),
                 ("drop_delta", C.c_double), ("precision", C.c_int), ("inner_rtol", C.c_double),
                 ("inner_pinv_tau", C.c_double), ("inner_drop_delta", C.c_double), ("max_outer", C.c_int),
-                ("use_graph", C.c_int), ("stream", C.c_void_p)]
+                ("use_graph", C.c_int), ("sum_columns", C.c_int), ("stream", C.c_void_p)]
 
 
 class mg_train_opts(C.Structure):

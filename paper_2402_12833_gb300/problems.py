@@ -333,11 +333,21 @@ def diffusion_macro(dim: int, nodes: int, kappa_seed: int, rhs: str = "ones", rh
                    name=f"diffusion{dim}d_{nodes}_k{kappa_seed}")
 
 
-def anisotropic_2d(nodes: int, kxx: float, kyy: float = 1.0) -> Problem:
-    """Example 1's anisotropic operator K = diag(kxx, kyy) with f = 1."""
+def anisotropic_2d(nodes: int, kxx: float, kyy: float = 1.0, levels: int | None = None) -> Problem:
+    """Example 1's anisotropic operator K = diag(kxx, kyy) with f = 1 and zero
+    Dirichlet data (the paper states neither; these are the readings)."""
     st = assemble_diffusion(2, nodes, kdiag=(kxx, kyy))
     b = load_vector(2, nodes, np.ones((nodes, nodes)))
-    return Problem(2, nodes, levels_for_nodes(nodes), st, b, name=f"aniso2d_{nodes}_{kxx:g}")
+    return Problem(2, nodes, levels_for_nodes(nodes) if levels is None else levels, st, b,
+                   name=f"aniso2d_{nodes}_{kxx:g}")
+
+
+def example1(kxx: float, nodes: int = 161, levels: int = 4) -> Problem:
+    """Section 3, Example 1: the unit square with 160 x 160 elements and a
+    4-grid hierarchy (20 x 20 elements on the coarsest grid), K = diag(kxx, 1)."""
+    if (nodes - 1) % (1 << (levels - 1)):
+        raise ValueError("nodes - 1 must be divisible by 2^(levels-1)")
+    return anisotropic_2d(nodes, kxx, 1.0, levels)
 
 
 def net_init_params(seed: int = 7, chans=(2, 16, 16, 16, 1)) -> np.ndarray:

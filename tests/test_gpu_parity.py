@@ -248,3 +248,43 @@ def test_mixed_precision_reaches_fp64_tolerance(M, name):
     ref = ompcg.mpcg(O.A[-1], prob.b, O.mg_columns, rtol=1e-12, maxit=2000)
     err = np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x)
     assert err <= 1e-5, err
+
+
+def test_summed_column_solve_is_additive_mg_pcg(M):
+    """sum_columns = 1 with a one-block window: the paper's additive MG-PCG
+    comparison method, against textbook PCG with the oracle's B of Eq. 3."""
+    from oracle.pcg import pcg
+    prob = pb.example1(1e-2)
+    H = _hier(M, prob, m=1, sum_columns=1)
+    assert M.mg_num_columns(H.h) == 1
+    O = _oracle(prob)
+    b = torch.from_numpy(prob.b).cuda()
+    x = torch.zeros_like(b)
+    st, k, rh, ah = H.solve(b, x, rtol=1e-8, maxit=3000)
+    xr, kr, hist = pcg(O.A[-1], prob.b, O.additive_mg, rtol=1e-8, maxit=3000)
+    assert st == M.MPCG_OK
+    assert abs(k - kr) <= 1, (k, kr)
+    assert np.linalg.norm(x.cpu().numpy() - xr) <= 1e-10 * np.linalg.norm(xr)
+    assert np.allclose(rh[:6], hist[:6], rtol=1e-6)
+
+
+@pytest.mark.parametrize("kxx", [1.0, 1e-3, 1e-6])
+def test_example1_hierarchy_and_solve_match_oracle(M, kxx):
+    """Example 1 (160 x 160 elements, 4 grids, 20 x 20 coarsest): a grid whose
+    element count is not a power of two."""
+    prob = pb.example1(kxx)
+    H = _hier(M, prob)
+    O = _oracle(prob)
+    for j in range(prob.levels):
+        n = M.mg_level_size(H.h, j)
+        planes = torch.zeros((9, n), dtype=torch.float64, device="cuda")
+        M.mg_get_operator(H.h, j, planes)
+        A = stencil_to_csr(2, O.n1[j], planes.cpu().numpy())
+        assert abs(A - O.A[j]).max() <= 1e-13 * abs(O.A[j]).max()
+    b = torch.from_numpy(prob.b).cuda()
+    x = torch.zeros_like(b)
+    st, k, rh, ah = H.solve(b, x, rtol=1e-8, maxit=3000)
+    ref = ompcg.mpcg(O.A[-1], prob.b, O.mg_columns, m=5, rtol=1e-8, maxit=3000)
+    assert st == M.MPCG_OK and ref.converged
+    assert abs(k - ref.iters) <= max(1, int(np.ceil(0.05 * ref.iters))), (k, ref.iters)
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-9 * np.linalg.norm(ref.x)

@@ -237,3 +237,22 @@ def test_free_faces_galerkin_and_tiny_solve(dim, faces):
     res = ompcg.mpcg(A, prob.b, H.mg_columns, rtol=1e-12, maxit=500)
     x = np.linalg.solve(A.toarray(), prob.b)
     assert np.linalg.norm(res.x - x) <= 1e-10 * np.linalg.norm(x)
+
+
+def test_example1_grid_hierarchy_and_pcg_equivalence():
+    """Example 1's 160 x 160 elements on 4 grids (20 x 20 coarsest): the
+    Galerkin operators equal the rediscretised anisotropic operators, and MPCG
+    with the single summed column is additive-MG PCG."""
+    from oracle.pcg import pcg
+    prob = pb.example1(1e-3)
+    H = omg.Hierarchy(2, prob.nodes - 2, prob.stencil, prob.levels)
+    assert [N for N in (sh[0] + 2 for sh in H.shape)] == [21, 41, 81, 161]
+    for j in range(H.levels - 1):
+        Nj = H.shape[j][0] + 2
+        ref = stencil_to_csr(2, Nj - 2, pb.assemble_diffusion(2, Nj, kdiag=(1e-3, 1.0)))
+        assert abs(H.A[j] - ref).max() < 1e-13 * abs(ref).max()
+    A = H.A[-1]
+    res = ompcg.mpcg(A, prob.b, lambda r: H.additive_mg(r)[:, None], m=1, rtol=1e-8, maxit=2000)
+    x, k, hist = pcg(A, prob.b, H.additive_mg, rtol=1e-8, maxit=2000)
+    assert res.iters == k
+    assert np.linalg.norm(res.x - x) <= 1e-10 * np.linalg.norm(x)
