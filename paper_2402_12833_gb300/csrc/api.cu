@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
@@ -102,6 +103,9 @@ struct Solver {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool use_graph = false;
+  // x starts at zero and r = b, |r|^2, |b|^2 partials are written before the
+  // prologue (the inner solves of the mixed-precision refinement)
+  bool zero_start = false;
   long long prologue_launches = 0, body_launches = 0;
   void drop_graph() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -259,6 +263,9 @@ mpcg_status build_solver(mg_hierarchy* h, Solver<T>& S) {
   const GridDesc& gf = h->lev[J].g;
   S.C = h->opt.sum_columns ? 1 : h->levels + (h->net_on ? 1 : 0);
   S.m = h->opt.m;
+  // the FP32 solver only runs the inner solves of the refinement, which
+  // start from zero with r = b written by launch_start_inner
+  S.zero_start = std::is_same<T, float>::value;
   const int C = S.C;
   const size_t nb = (size_t)h->nb;   // all buffers hold the whole batch
   CKS(S.mem.get(&S.x, gf.cp, s));
@@ -423,7 +430,8 @@ template <typename T>
 void enqueue_prologue(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond, int use_cond,
                       cudaStream_t s) {
   const Level& L = h->lev[h->levels - 1];
-  LAUNCH(h, K_RESIDUAL, s, launch_residual<T>(L.g, st_of<T>(L), S.b, S.x, S.r, S.part_res, s));
+  // a solve from a zero iterate has r = b, written by its start kernel
+  if (!S.zero_start) LAUNCH(h, K_RESIDUAL, s, launch_residual<T>(L.g, st_of<T>(L), S.b, S.x, S.r, S.part_res, s));
   // a batch decides its loop condition from all problems (enqueue_any)
   LAUNCH(h, K_INIT, s, launch_init(S.state, h->nb, S.part_res, stream_blocks(L.g), S.res_hist, S.hist_cap, cond,
                                    use_cond && h->nb == 1, s));
@@ -968,7 +976,7 @@ static bool build_mixed_graph(mg_hierarchy* h, double rtol, int maxit) {
     LAUNCH(h, K_AUX, cs, launch_outer_check(h->mix, h->active, nb, h->nrm, rtol, maxit, h->opt.max_outer, h->outer,
                                             S.state, h->opt.inner_rtol, S.m, S.C, h->opt.inner_drop_delta,
                                             h->opt.inner_pinv_tau, c_out, cs));
-    LAUNCH(h, K_AUX, cs, launch_scale_to_f32(gf, h->r64, h->nrm, h->active, S.b, cs));
+    LAUNCH(h, K_AUX, cs, launch_start_inner(gf, h->r64, h->nrm, h->active, S.b, S.r, S.part_res, cs));
     ok = cudaMemsetAsync(S.x, 0, sizeof(float) * gf.cp, cs) == cudaSuccess;
     ok = ok && cudaGraphConditionalHandleCreate(&c_in, obody, 0, 0) == cudaSuccess;
     if (ok) {
@@ -1111,7 +1119,7 @@ static mpcg_status solve_mixed(mg_hierarchy* h, const double* b, double* x, doub
     }
     if (!running) break;
     CK(cudaMemcpyAsync(h->active, act.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s));
-    LAUNCH(h, K_AUX, s, launch_scale_to_f32(gf, h->r64, h->nrm, h->active, S.b, s));
+    LAUNCH(h, K_AUX, s, launch_start_inner(gf, h->r64, h->nrm, h->active, S.b, S.r, S.part_res, s));
     CK(cudaMemsetAsync(S.x, 0, sizeof(float) * gf.cp, s));
     LAUNCH(h, K_AUX, s, launch_set_params(S.state, nb, h->opt.inner_rtol, budget, S.m, S.C, h->opt.inner_drop_delta,
                                           h->opt.inner_pinv_tau, s));

@@ -198,6 +198,64 @@ __global__ void __launch_bounds__(kBlock) k_update_xr(GridDesc g, Window<T> win,
   block_sum_store<T, 1>(acc, part + (long long)pb * gridDim.x, gridDim.x, blockIdx.x);
 }
 
+// Mixed-precision refinement, start of an inner FP32 solve: with the outer
+// residual r64 and |r64|^2 in nrm2[2p], b32 = r64 / |r64| (zero for an
+// inactive problem, whose inner solve then stops at once).  The inner iterate
+// starts at zero, so the inner residual is b32 itself: it is written to r32
+// as well, with the block partials of |r32|^2 and |b32|^2 that the residual
+// kernel would have produced (value-major, stride gridDim.x).
+__global__ void __launch_bounds__(kBlock) k_start_inner(GridDesc g, const double* __restrict__ r64,
+                                                        const double* __restrict__ nrm2,
+                                                        const int* __restrict__ active, float* __restrict__ b32,
+                                                        float* __restrict__ r32, double* part) {
+  const int pb = blockIdx.y;
+  const bool on = !active || active[pb];
+  const double inv = on && nrm2[2 * pb] > 0.0 ? 1.0 / sqrt(nrm2[2 * pb]) : 0.0;
+  const long long o = (long long)pb * g.len + g.G;
+  float sums[2] = {0.f, 0.f};
+  const long long ngroups = g.npts / 4;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long i = o + q * 4;
+    double lo[2], hi[2];
+    Vec<double>::load(r64 + i, lo);
+    Vec<double>::load(r64 + i + 2, hi);
+    const float v[4] = {(float)(lo[0] * inv), (float)(lo[1] * inv), (float)(hi[0] * inv), (float)(hi[1] * inv)};
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      sums[0] = fmaf(v[w], v[w], sums[0]);
+      sums[1] = fmaf(v[w], v[w], sums[1]);
+    }
+    Vec<float>::store(b32 + i, v);
+    Vec<float>::store(r32 + i, v);
+  }
+  block_sum_store<float, 2>(sums, part + (long long)pb * 2 * gridDim.x, gridDim.x, blockIdx.x);
+}
+
+// End of an inner solve: x64 += |r64| d32 (nrm2[2p] = |r64|^2).
+__global__ void __launch_bounds__(kBlock) k_axpy_mixed(GridDesc g, double* __restrict__ x,
+                                                       const float* __restrict__ d, const double* __restrict__ nrm2) {
+  const int pb = blockIdx.y;
+  const double sc = sqrt(nrm2[2 * pb]);
+  const long long o = (long long)pb * g.len + g.G;
+  const long long ngroups = g.npts / 4;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long i = o + q * 4;
+    float dv[4];
+    double lo[2], hi[2];
+    Vec<float>::load(d + i, dv);
+    Vec<double>::load_keep(x + i, lo);
+    Vec<double>::load_keep(x + i + 2, hi);
+    lo[0] = fma(sc, (double)dv[0], lo[0]);
+    lo[1] = fma(sc, (double)dv[1], lo[1]);
+    hi[0] = fma(sc, (double)dv[2], hi[0]);
+    hi[1] = fma(sc, (double)dv[3], hi[1]);
+    Vec<double>::store(x + i, lo);
+    Vec<double>::store(x + i + 2, hi);
+  }
+}
+
 }  // namespace
 
 #define MPCG_C_SWITCH(C, BODY)                                                                   \
@@ -254,6 +312,14 @@ void launch_update_xr(const GridDesc& g, Window<T> win, T* x, T* r, int C, doubl
                       cudaStream_t s) {
   const int nb = stream_blocks(g);
   MPCG_C_SWITCH(C, (k_update_xr<T, CC><<<dim3(nb, g.nb), kBlock, 0, s>>>(g, win, x, r, part, state)));
+}
+
+void launch_start_inner(const GridDesc& g, const double* r64, const double* nrm2, const int* active, float* b32,
+                        float* r32, double* part, cudaStream_t s) {
+  k_start_inner<<<dim3(stream_blocks(g), g.nb), kBlock, 0, s>>>(g, r64, nrm2, active, b32, r32, part);
+}
+void launch_axpy_mixed(const GridDesc& g, double* x, const float* d, const double* scale, cudaStream_t s) {
+  k_axpy_mixed<<<dim3(stream_blocks(g), g.nb), kBlock, 0, s>>>(g, x, d, scale);
 }
 
 template void launch_gram_window<double>(const GridDesc&, Window<double>, const double*, int, int, double*,

@@ -148,9 +148,10 @@ void launch_sum_partials(const double* part, int nb, int nv, int nblk, double* o
 // x64 += scale * d (padded, FP32 d); scale read from device
 void launch_axpy_mixed(const GridDesc& g, double* x, const float* d, const double* scale,
                        cudaStream_t s);
-// b32 = r64 / ||r64|| from device norm-squared
-void launch_scale_to_f32(const GridDesc& g, const double* r, const double* nrm2, const int* active, float* out,
-                         cudaStream_t s);
+// start of an inner FP32 solve from a zero iterate: b32 = r32 = r64 / ||r64||
+// (device norm-squared) and the residual partials of ||r32||^2, ||b32||^2
+void launch_start_inner(const GridDesc& g, const double* r64, const double* nrm2, const int* active, float* b32,
+                        float* r32, double* part, cudaStream_t s);
 
 // ---- learned.cu ----------------------------------------------------------
 // Network 2 -> 16 -> 16 -> 16 -> 1 (3x3), parameters packed layer by layer,

@@ -510,30 +510,6 @@ __global__ void k_sum_partials(const double* part, int nv, int nblk, double* out
   reduce_values(part + (long long)pb * nv * nblk, nv, nblk, nblk, out + (long long)pb * nv);
 }
 
-// x64 += ||r64|| d per problem (nrm2 holds [||r||^2, ||b||^2] per problem).
-__global__ void k_axpy_mixed(GridDesc g, double* __restrict__ x, const float* __restrict__ d,
-                             const double* __restrict__ nrm2) {
-  const int pb = blockIdx.y;
-  const double sc = sqrt(nrm2[2 * pb]);
-  const long long o = (long long)pb * g.len + g.G;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.npts;
-       t += (long long)gridDim.x * blockDim.x)
-    x[o + t] = fma(sc, (double)d[o + t], x[o + t]);
-}
-
-// b32 = r64 / ||r64|| per problem; active[b] == 0 gives b32 = 0 (the inner
-// solve of a converged problem then stops at once).
-__global__ void k_scale_to_f32(GridDesc g, const double* __restrict__ r, const double* __restrict__ nrm2,
-                               const int* __restrict__ active, float* __restrict__ out) {
-  const int pb = blockIdx.y;
-  const bool on = !active || active[pb];
-  const double inv = on && nrm2[2 * pb] > 0.0 ? 1.0 / sqrt(nrm2[2 * pb]) : 0.0;
-  const long long o = (long long)pb * g.len + g.G;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.npts;
-       t += (long long)gridDim.x * blockDim.x)
-    out[o + t] = (float)(r[o + t] * inv);
-}
-
 // flag |= some problem of the batch is still running.
 // Device side of the mixed-precision refinement loop (one graph per solve):
 // mix[p] = {inner iterations so far, status (0 running, 1 converged, 2 out
@@ -676,13 +652,6 @@ void launch_outer_accumulate(int* mix, int nb, const DevState* st, cudaStream_t 
 }
 void launch_sum_partials(const double* part, int nb, int nv, int nblk, double* out, cudaStream_t s) {
   k_sum_partials<<<nb, kBlock, 0, s>>>(part, nv, nblk, out);
-}
-void launch_axpy_mixed(const GridDesc& g, double* x, const float* d, const double* scale, cudaStream_t s) {
-  k_axpy_mixed<<<dim3(grid_for(g.npts, 1024), g.nb), kBlock, 0, s>>>(g, x, d, scale);
-}
-void launch_scale_to_f32(const GridDesc& g, const double* r, const double* nrm2, const int* active, float* out,
-                         cudaStream_t s) {
-  k_scale_to_f32<<<dim3(grid_for(g.npts, 1024), g.nb), kBlock, 0, s>>>(g, r, nrm2, active, out);
 }
 void launch_any_running(const DevState* st, int nb, int* flag, cudaStream_t s) {
   k_any_running<<<1, kBlock, 0, s>>>(st, nb, flag);
