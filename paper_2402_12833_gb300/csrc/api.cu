@@ -218,6 +218,7 @@ struct mg_hierarchy {
   Solver<double> s64;
   Solver<float> s32;
   double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *nrm = nullptr, *part_mix = nullptr;
+  int* xnz = nullptr;        // per problem: the packed FP64 iterate may be nonzero
   double* stage = nullptr;   // 2 n doubles: staging for host b and x
   // mixed precision as one graph (refinement loop on the device)
   int* mix = nullptr;        // per problem: inner iterations, status, active
@@ -431,7 +432,10 @@ void enqueue_prologue(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle 
                       cudaStream_t s) {
   const Level& L = h->lev[h->levels - 1];
   // a solve from a zero iterate has r = b, written by its start kernel
-  if (!S.zero_start) LAUNCH(h, K_RESIDUAL, s, launch_residual<T>(L.g, st_of<T>(L), S.b, S.x, S.r, S.part_res, s));
+  // the FP64 iterate was packed with its nonzero flag (a zero x0 skips the stencil)
+  const int* xnz = std::is_same<T, double>::value ? h->xnz : nullptr;
+  if (!S.zero_start)
+    LAUNCH(h, K_RESIDUAL, s, launch_residual<T>(L.g, st_of<T>(L), S.b, S.x, S.r, S.part_res, s, xnz));
   // a batch decides its loop condition from all problems (enqueue_any)
   LAUNCH(h, K_INIT, s, launch_init(S.state, h->nb, S.part_res, stream_blocks(L.g), S.res_hist, S.hist_cap, cond,
                                    use_cond && h->nb == 1, s));
@@ -467,7 +471,7 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
                                          s));
   LAUNCH(h, K_ORTH, s, launch_orth_update<T>(L.g, S.win, S.Z, S.AZ, S.r, C, S.part_G, S.state, s));
   LAUNCH(h, K_ALPHA, s, launch_small_alpha(S.state, h->nb, S.part_G, stream_blocks(L.g), S.part_zaz,
-                                          stream_blocks(L.g), stream_blocks(L.g), C, S.alpha_hist,
+                                          spmm_blocks<T>(L.g, C), spmm_blocks<T>(L.g, C), C, S.alpha_hist,
                                           (long long)S.hist_cap * C, S.small_scratch, S.counters, s));
   LAUNCH(h, K_UPDATE, s, launch_update_xr<T>(L.g, S.win, S.x, S.r, C, S.part_r, S.state, s));
   LAUNCH(h, K_CHECK, s, launch_check(S.state, h->nb, S.part_r, stream_blocks(L.g), S.res_hist, S.hist_cap, cond,
@@ -823,6 +827,11 @@ static mpcg_status setup_impl(const mg_operator* ops, int nb, int levels, const 
   const size_t nn = (size_t)n0 * n0;
   if ((st = h->mem.get(&h->L0, nn * nb, s)) != MPCG_OK) return fail(st);
   if ((st = h->mem.get(&h->info, nb, s)) != MPCG_OK) return fail(st);
+  if ((st = h->mem.get(&h->xnz, nb, s)) != MPCG_OK) return fail(st);
+  {
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device) == cudaSuccess) set_sm_count(nsm);
+  }
   if ((st = h->mem.get(&h->rdiag0, (size_t)n0 * nb, s)) != MPCG_OK) return fail(st);
   for (int b = 0; b < nb; ++b) {
     launch_dense_from_stencil(h->lev[0].g, h->lev[0].st64 + (size_t)b * h->lev[0].g.len, h->L0 + nn * b, s);
@@ -879,7 +888,8 @@ static mpcg_status solve_fp64(mg_hierarchy* h, const double* b, double* x, doubl
   CKS(ensure_hist(h, S, maxit));
   for (int p = 0; p < nb; ++p) {
     LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, b + (size_t)p * gf.n, gf.n, S.b + (size_t)p * gf.len, 1, s));
-    LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, x + (size_t)p * gf.n, gf.n, S.x + (size_t)p * gf.len, 1, s));
+    CK(cudaMemsetAsync(h->xnz + p, 0, sizeof(int), s));
+    LAUNCH(h, K_PACK, s, launch_pack_flag(gf, x + (size_t)p * gf.n, S.x + (size_t)p * gf.len, h->xnz + p, s));
   }
   LAUNCH(h, K_AUX, s, launch_set_params(S.state, nb, rtol, maxit, S.m, S.C, h->opt.drop_delta, h->opt.pinv_tau, s));
   std::vector<int> kd;
@@ -971,7 +981,7 @@ static bool build_mixed_graph(mg_hierarchy* h, double rtol, int maxit) {
   if (ok) {
     h->mg_head = 0;
     h->prof.target = &h->mg_head;
-    LAUNCH(h, K_RESIDUAL, cs, launch_residual<double>(gf, L.st64, h->b64, h->x64, h->r64, h->part_mix, cs));
+    LAUNCH(h, K_RESIDUAL, cs, launch_residual<double>(gf, L.st64, h->b64, h->x64, h->r64, h->part_mix, cs, h->xnz));
     LAUNCH(h, K_AUX, cs, launch_sum_partials(h->part_mix, nb, 2, stream_blocks(gf), h->nrm, cs));
     LAUNCH(h, K_AUX, cs, launch_outer_check(h->mix, h->active, nb, h->nrm, rtol, maxit, h->opt.max_outer, h->outer,
                                             S.state, h->opt.inner_rtol, S.m, S.C, h->opt.inner_drop_delta,
@@ -987,7 +997,7 @@ static bool build_mixed_graph(mg_hierarchy* h, double rtol, int maxit) {
       h->mg_tail = 0;
       h->prof.target = &h->mg_tail;
       LAUNCH(h, K_AUX, cs, launch_outer_accumulate(h->mix, nb, S.state, cs));
-      LAUNCH(h, K_AUX, cs, launch_axpy_mixed(gf, h->x64, S.x, h->nrm, cs));
+      LAUNCH(h, K_AUX, cs, launch_axpy_mixed(gf, h->x64, S.x, h->nrm, h->xnz, cs));
     }
     h->prof.target = nullptr;
     ok = (cudaStreamEndCapture(cs, &tmp) == cudaSuccess) && ok;
@@ -1043,7 +1053,8 @@ static mpcg_status solve_mixed_graph(mg_hierarchy* h, const double* b, double* x
   }
   for (int p = 0; p < nb; ++p) {
     LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, b + (size_t)p * gf.n, gf.n, h->b64 + (size_t)p * gf.len, 1, s));
-    LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, x + (size_t)p * gf.n, gf.n, h->x64 + (size_t)p * gf.len, 1, s));
+    CK(cudaMemsetAsync(h->xnz + p, 0, sizeof(int), s));
+    LAUNCH(h, K_PACK, s, launch_pack_flag(gf, x + (size_t)p * gf.n, h->x64 + (size_t)p * gf.len, h->xnz + p, s));
   }
   CK(cudaGraphLaunch(h->mexec, s));
   for (int p = 0; p < nb; ++p)
@@ -1085,7 +1096,8 @@ static mpcg_status solve_mixed(mg_hierarchy* h, const double* b, double* x, doub
   const int nb = h->nb;
   for (int p = 0; p < nb; ++p) {
     LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, b + (size_t)p * gf.n, gf.n, h->b64 + (size_t)p * gf.len, 1, s));
-    LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, x + (size_t)p * gf.n, gf.n, h->x64 + (size_t)p * gf.len, 1, s));
+    CK(cudaMemsetAsync(h->xnz + p, 0, sizeof(int), s));
+    LAUNCH(h, K_PACK, s, launch_pack_flag(gf, x + (size_t)p * gf.n, h->x64 + (size_t)p * gf.len, h->xnz + p, s));
   }
   // every problem refines on its own true FP64 residual; the problems run
   // their FP32 inner solves together, converged ones with a zero right-hand
@@ -1093,7 +1105,7 @@ static mpcg_status solve_mixed(mg_hierarchy* h, const double* b, double* x, doub
   std::vector<int> total(nb, 0), nhist(nb, 0), status(nb, 0), act(nb, 1);
   std::vector<double> nrm(2 * (size_t)nb), inner(maxit + 1);
   for (int outer = 0; outer <= h->opt.max_outer; ++outer) {
-    LAUNCH(h, K_RESIDUAL, s, launch_residual<double>(gf, L.st64, h->b64, h->x64, h->r64, h->part_mix, s));
+    LAUNCH(h, K_RESIDUAL, s, launch_residual<double>(gf, L.st64, h->b64, h->x64, h->r64, h->part_mix, s, h->xnz));
     LAUNCH(h, K_AUX, s, launch_sum_partials(h->part_mix, nb, 2, stream_blocks(gf), h->nrm, s));
     CK(cudaMemcpyAsync(nrm.data(), h->nrm, 2 * sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1145,7 +1157,7 @@ static mpcg_status solve_mixed(mg_hierarchy* h, const double* b, double* x, doub
         act[p] = 0;
       }
     }
-    LAUNCH(h, K_AUX, s, launch_axpy_mixed(gf, h->x64, S.x, h->nrm, s));
+    LAUNCH(h, K_AUX, s, launch_axpy_mixed(gf, h->x64, S.x, h->nrm, h->xnz, s));
   }
   for (int p = 0; p < nb; ++p)
     LAUNCH(h, K_PACK, s, launch_unpack<double, double>(gf, h->x64 + (size_t)p * gf.len, x + (size_t)p * gf.n, gf.n, 1, s));

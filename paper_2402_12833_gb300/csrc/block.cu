@@ -234,9 +234,11 @@ __global__ void __launch_bounds__(kBlock) k_start_inner(GridDesc g, const double
 
 // End of an inner solve: x64 += |r64| d32 (nrm2[2p] = |r64|^2).
 __global__ void __launch_bounds__(kBlock) k_axpy_mixed(GridDesc g, double* __restrict__ x,
-                                                       const float* __restrict__ d, const double* __restrict__ nrm2) {
+                                                       const float* __restrict__ d, const double* __restrict__ nrm2,
+                                                       int* xnz) {
   const int pb = blockIdx.y;
   const double sc = sqrt(nrm2[2 * pb]);
+  if (xnz && blockIdx.x == 0 && threadIdx.x == 0) xnz[pb] = 1;   // x may be nonzero from here on
   const long long o = (long long)pb * g.len + g.G;
   const long long ngroups = g.npts / 4;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
@@ -318,8 +320,9 @@ void launch_start_inner(const GridDesc& g, const double* r64, const double* nrm2
                         float* r32, double* part, cudaStream_t s) {
   k_start_inner<<<dim3(stream_blocks(g), g.nb), kBlock, 0, s>>>(g, r64, nrm2, active, b32, r32, part);
 }
-void launch_axpy_mixed(const GridDesc& g, double* x, const float* d, const double* scale, cudaStream_t s) {
-  k_axpy_mixed<<<dim3(stream_blocks(g), g.nb), kBlock, 0, s>>>(g, x, d, scale);
+void launch_axpy_mixed(const GridDesc& g, double* x, const float* d, const double* scale, int* xnz,
+                       cudaStream_t s) {
+  k_axpy_mixed<<<dim3(stream_blocks(g), g.nb), kBlock, 0, s>>>(g, x, d, scale, xnz);
 }
 
 template void launch_gram_window<double>(const GridDesc&, Window<double>, const double*, int, int, double*,

@@ -33,6 +33,13 @@ inline int grid_for(long long work, int cap) {
 // compact interior <-> padded layout (ncols columns; compact leading dim ld)
 template <typename TI, typename TO>
 void launch_pack(const GridDesc& g, const TI* src, long long ld, TO* dst, int ncols, cudaStream_t s);
+// pack of one FP64 column; *nz = 1 when it has a nonzero entry (zero it first)
+void launch_pack_flag(const GridDesc& g, const double* src, double* dst, int* nz, cudaStream_t s);
+// SM count used to size one-wave launches (set at hierarchy setup)
+void set_sm_count(int n);
+// blocks (and zaz partial slots) of launch_spmm on grid g with C columns
+template <typename T>
+int spmm_blocks(const GridDesc& g, int C);
 template <typename TI, typename TO>
 void launch_unpack(const GridDesc& g, const TI* src, TO* dst, long long ld, int ncols, cudaStream_t s);
 
@@ -41,10 +48,11 @@ void launch_unpack(const GridDesc& g, const TI* src, TO* dst, long long ld, int 
 template <typename T>
 void launch_spmm(const GridDesc& g, const T* st, const T* X, T* Y, int C, double* zaz,
                  const DevState* state, cudaStream_t s);
-// r = b - A x; partials [||r||^2, ||b||^2]
+// r = b - A x; partials [||r||^2, ||b||^2].  xnz (may be null): per problem,
+// 0 when x is known to be zero (then r = b without reading the stencil)
 template <typename T>
 void launch_residual(const GridDesc& g, const T* st, const T* b, const T* x, T* r, double* part,
-                     cudaStream_t s);
+                     cudaStream_t s, const int* xnz = nullptr);
 // coarse = P^T fine
 template <typename T>
 void launch_restrict(const GridDesc& gf, const GridDesc& gc, const T* rf, T* rc,
@@ -145,8 +153,8 @@ void launch_outer_check(int* mix, int* active, int nb, const double* nrm, double
                         cudaGraphConditionalHandle cond, cudaStream_t s);
 void launch_outer_accumulate(int* mix, int nb, const DevState* st, cudaStream_t s);
 void launch_sum_partials(const double* part, int nb, int nv, int nblk, double* out, cudaStream_t s);
-// x64 += scale * d (padded, FP32 d); scale read from device
-void launch_axpy_mixed(const GridDesc& g, double* x, const float* d, const double* scale,
+// x64 += scale * d (padded, FP32 d); scale read from device; xnz[p] = 1
+void launch_axpy_mixed(const GridDesc& g, double* x, const float* d, const double* scale, int* xnz,
                        cudaStream_t s);
 // start of an inner FP32 solve from a zero iterate: b32 = r32 = r64 / ||r64||
 // (device norm-squared) and the residual partials of ||r32||^2, ||b32||^2

@@ -18,6 +18,24 @@
 
 namespace mpcg {
 
+static_assert(kMaxCols <= 12, "MPCG_SMALL_C_SWITCH covers up to 12 columns");
+#define MPCG_SMALL_C_SWITCH(C, BODY)                                                             \
+  switch (C) {                                                                                   \
+    case 1: { constexpr int CC = 1; BODY; } break;                                               \
+    case 2: { constexpr int CC = 2; BODY; } break;                                               \
+    case 3: { constexpr int CC = 3; BODY; } break;                                               \
+    case 4: { constexpr int CC = 4; BODY; } break;                                               \
+    case 5: { constexpr int CC = 5; BODY; } break;                                               \
+    case 6: { constexpr int CC = 6; BODY; } break;                                               \
+    case 7: { constexpr int CC = 7; BODY; } break;                                               \
+    case 8: { constexpr int CC = 8; BODY; } break;                                               \
+    case 9: { constexpr int CC = 9; BODY; } break;                                               \
+    case 10: { constexpr int CC = 10; BODY; } break;                                             \
+    case 11: { constexpr int CC = 11; BODY; } break;                                             \
+    case 12: { constexpr int CC = 12; BODY; } break;                                             \
+    default: break;                                                                              \
+  }
+
 namespace {
 
 // out[v] = sum_b part[v * stride + b], b < nblk: one warp per value, lanes
@@ -165,55 +183,6 @@ __device__ void warp_jacobi_pinv(double* A, double* V, int na, double tau, doubl
   __syncwarp();
 }
 
-// Inverse of the SPD na x na matrix A (ld kPad) through its Cholesky factor,
-// into Ah.  A is overwritten.  Returns false if a pivot is not positive or
-// the inverse does not certify lambda_min > tau * na (see the file comment).
-__device__ bool warp_chol_inverse(double* A, double* X, int na, double tau, double* Ah, double* dinv) {
-  const int lane = threadIdx.x & 31;
-  bool ok = true;
-  for (int k = 0; k < na; ++k) {
-    const double piv = A[k * kPad + k];
-    if (!(piv > 0.0)) { ok = false; break; }
-    const double li = rsqrt(piv);
-    __syncwarp();
-    if (lane == 0) { A[k * kPad + k] = piv * li; dinv[k] = li; }
-    for (int i = k + 1 + lane; i < na; i += 32) A[i * kPad + k] *= li;
-    __syncwarp();
-    const int mm = na - k - 1;
-    for (int e = lane; e < mm * mm; e += 32) {
-      const int i = k + 1 + e / mm, j = k + 1 + e % mm;
-      if (j <= i) A[i * kPad + j] -= A[i * kPad + k] * A[j * kPad + k];
-    }
-    __syncwarp();
-  }
-  if (!ok) return false;
-  // X = L^{-1}: lane j owns column j
-  if (lane < na) {
-    const int j = lane;
-    for (int i = 0; i < na; ++i) X[i * kPad + j] = 0.0;
-    X[j * kPad + j] = dinv[j];
-    for (int i = j + 1; i < na; ++i) {
-      double s = 0.0;
-      for (int k = j; k < i; ++k) s += A[i * kPad + k] * X[k * kPad + j];
-      X[i * kPad + j] = -s * dinv[i];
-    }
-  }
-  __syncwarp();
-  double tr = 0.0;
-  for (int e = lane; e < na * na; e += 32) {
-    const int a = e / na, b = e % na;
-    const int k0 = a > b ? a : b;
-    double s = 0.0;
-    for (int k = k0; k < na; ++k) s += X[k * kPad + a] * X[k * kPad + b];
-    Ah[a * kPad + b] = s;
-    if (a == b) tr += s;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-  __syncwarp();
-  return tr > 0.0 && 1.0 / tr > tau * na;
-}
-
 __global__ void k_set_params(DevState* st, double rtol, int maxit, int m, int C, double delta, double tau) {
   st += blockIdx.x;
   st->rtol = rtol;
@@ -276,10 +245,27 @@ __global__ void k_small_beta(DevState* st, const double* part_W, int nchunks, in
   }
 }
 
-__global__ void k_small_alpha(DevState* st, const double* part_G, int nblk_G, const double* part_zaz, int nblk_zaz,
-                              int zaz_stride, int C, double* alpha_hist, long long ahist_stride, double* scratch,
-                              unsigned* counter) {
-  const int NG = C * (C + 1) / 2;
+// Position of G entry (a, b), a <= b, in the packed upper triangle of the
+// reduced Gram values ((0,0), (0,1), ..., (0,C-1), (1,1), ...).
+__device__ __forceinline__ int tri_index(int a, int b, int C) { return a * C - a * (a - 1) / 2 + (b - a); }
+
+// alpha = G^+ g after the grid reduction of G = sym(P^T A P), g = P^T r and
+// the z^T A z of the new block; G^+ also goes to the window ring.  One warp,
+// C columns known at compile time.  GB300 issues one FP64 warp instruction
+// per 64 cycles per SM sub-partition whatever the active lanes, so the
+// factorisation keeps one row per lane in registers and every step is a
+// handful of warp-wide instructions: the drop rule and the scaling are one
+// pass over the lanes; the Cholesky factor of D G D (right-looking, lane i
+// holds row i); the columns of L^{-1} by forward substitution (lane j holds
+// column j), whose squares give trace((D G D)^{-1}) for the cut test; and
+// row i of (D G D)^{-1} = L^{-T} (L^{-1} e_i) by backward substitution.
+template <int C>
+__global__ void __launch_bounds__(kBlock) k_small_alpha(DevState* st, const double* part_G, int nblk_G,
+                                                        const double* part_zaz, int nblk_zaz, int zaz_stride,
+                                                        double* alpha_hist, long long ahist_stride, double* scratch,
+                                                        unsigned* counter) {
+  constexpr int NG = C * (C + 1) / 2;
+  constexpr unsigned kFull = 0xffffffffu;
   const int pb = blockIdx.y;
   st += pb;
   part_G += (long long)pb * (NG + C) * nblk_G;
@@ -288,69 +274,160 @@ __global__ void k_small_alpha(DevState* st, const double* part_G, int nblk_G, co
   scratch += (long long)pb * kSmallScratch + kSmallScratchAlpha;
   counter += 2 * pb + 1;
   if (st->done) return;
-  __shared__ double red[kMaxCols * (kMaxCols + 1) / 2 + 2 * kMaxCols];
-  __shared__ double G[kPad * kPad], Gp[kPad * kPad], A[kPad * kPad], X[kPad * kPad], Ah[kPad * kPad];
-  __shared__ double dsc[kPad], rc[kPad], rs[kPad], lam[kPad];
-  __shared__ int act[kPad], map[kPad], rp[kPad], rq[kPad];
-  __shared__ int nact_sh;
+  __shared__ double red[NG + 2 * C];
+  __shared__ double Lsm[C][C];
+  __shared__ double dsm[C];
+  __shared__ int map[C];
+  // workspace of the Jacobi eigenvalue fallback
+  __shared__ double A[kPad * kPad], V[kPad * kPad], Ah[kPad * kPad];
+  __shared__ double rc[kPad], rs[kPad], lam[kPad];
+  __shared__ int rp[kPad], rq[kPad];
   if (!reduce_values_grid(part_G, NG + C, nblk_G, nblk_G, part_zaz, C, nblk_zaz, zaz_stride, scratch, counter))
     return;
   for (int e = threadIdx.x; e < NG + 2 * C; e += blockDim.x) red[e] = __ldcg(scratch + e);
   __syncthreads();
   if (threadIdx.x >= 32) return;
   const int lane = threadIdx.x;
+  // column-drop rule on the diagonal (the partials hold p_a ap_b + p_b ap_a)
+  double pap = 0.0, gv = 0.0;
+  bool act = false, bad = false;
+  if (lane < C) {
+    pap = 0.5 * red[tri_index(lane, lane, C)];
+    const double zaz = red[NG + C + lane];
+    gv = red[NG + lane];
+    bad = !isfinite(pap) || !isfinite(zaz);
+    act = pap > st->delta * zaz && pap > 0.0;
+  }
+  const unsigned amask = __ballot_sync(kFull, act);
+  const int na = __popc(amask);
+  bad = __any_sync(kFull, bad);
+  if (lane < C) map[lane] = 0;
+  __syncwarp();
+  if (act) map[__popc(amask & ((1u << lane) - 1u))] = lane;
+  const double dsc = act ? rsqrt(pap) : 0.0;
+  if (lane < C) dsm[lane] = dsc;
+  __syncwarp();
   if (lane == 0) {
-    // G = sym(P^T A P): the partials hold p_a ap_b + p_b ap_a for a <= b
-    int k = 0, na = 0, bad = 0;
-    for (int a = 0; a < C; ++a)
-      for (int b = a; b < C; ++b) {
-        const double v = 0.5 * red[k++];
-        G[a * kPad + b] = v;
-        G[b * kPad + a] = v;
-      }
-    for (int a = 0; a < C; ++a) {
-      const double pap = G[a * kPad + a], zaz = red[NG + C + a];
-      if (!isfinite(pap) || !isfinite(zaz)) bad = 1;
-      act[a] = (pap > st->delta * zaz && pap > 0.0) ? 1 : 0;   // column-drop rule
-      if (act[a]) map[na++] = a;
-      else st->dropped_total += 1;
-    }
-    nact_sh = na;
+    st->dropped_total += C - na;
     if (bad || na == 0) st->done = 3;
   }
-  __syncwarp();
-  const int na = nact_sh;
-  for (int e = lane; e < kPad * kPad; e += 32) Gp[e] = 0.0;
-  if (lane < na) dsc[lane] = rsqrt(G[map[lane] * kPad + map[lane]]);
-  __syncwarp();
+  const int ci = na > 0 ? map[lane < na ? lane : 0] : 0;
+  const double di = __shfl_sync(kFull, dsc, ci);
+  double Z[C];   // row `lane` of (D G D)^+ over the active positions
+#pragma unroll
+  for (int j = 0; j < C; ++j) Z[j] = 0.0;
   if (na > 0) {
-    for (int e = lane; e < kPad * kPad; e += 32) {
-      const int i = e / kPad, j = e % kPad;
-      A[e] = (i < na && j < na) ? dsc[i] * G[map[i] * kPad + map[j]] * dsc[j] : 0.0;
+    // row `lane` of D G D (G = 0.5 red; scaling by 0.5 is exact)
+    double Ar[C];
+    const double hdi = 0.5 * di;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int cj = map[j < na ? j : 0];
+      const double dj = __shfl_sync(kFull, dsc, cj);
+      const int lo = ci < cj ? ci : cj, hi = ci < cj ? cj : ci;
+      Ar[j] = (lane < na && j < na) ? hdi * red[tri_index(lo, hi, C)] * dj : 0.0;
     }
-    __syncwarp();
-    const bool ok = warp_chol_inverse(A, X, na, st->tau, Ah, lam);
-    if (!ok) {
-      for (int e = lane; e < kPad * kPad; e += 32) {
-        const int i = e / kPad, j = e % kPad;
-        A[e] = (i < na && j < na) ? dsc[i] * G[map[i] * kPad + map[j]] * dsc[j] : 0.0;
+    // Cholesky D G D = L L^T; dinv[k] = 1 / L_kk
+    double dinv[C];
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      dinv[k] = 0.0;
+      if (k < na && ok) {
+        const double piv = __shfl_sync(kFull, Ar[k], k);
+        if (!(piv > 0.0)) {
+          ok = false;
+        } else {
+          const double li = rsqrt(piv);
+          dinv[k] = li;
+          Ar[k] *= li;   // L_ik; lane k: L_kk = piv / sqrt(piv)
+#pragma unroll
+          for (int j = k + 1; j < C; ++j)
+            if (j < na) Ar[j] = fma(-Ar[k], __shfl_sync(kFull, Ar[k], j), Ar[j]);
+        }
+      }
+    }
+    if (ok) {
+      if (lane < na) {
+#pragma unroll
+        for (int j = 0; j < C; ++j) Lsm[lane][j] = Ar[j];
       }
       __syncwarp();
-      warp_jacobi_pinv(A, X, na, st->tau, Ah, rc, rs, rp, rq, lam);
+      // column `lane` of L^{-1}
+      double X[C];
+#pragma unroll
+      for (int k = 0; k < C; ++k) {
+        X[k] = 0.0;
+        if (k < na) {
+          double s = k == lane ? 1.0 : 0.0;
+#pragma unroll
+          for (int m = 0; m < k; ++m) s = fma(-Lsm[k][m], X[m], s);
+          X[k] = s * dinv[k];
+        }
+      }
+      // every eigenvalue passes the cut when 1 / trace(inverse) > tau * n
+      // (unit diagonal: lambda_max <= n, lambda_min >= 1 / trace(inverse))
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < C; ++k) t = fma(X[k], X[k], t);
+      if (lane >= na) t = 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+      ok = t > 0.0 && t * (st->tau * na) < 1.0;
+      if (ok) {   // row `lane` of the inverse: L^{-T} times column `lane` of L^{-1}
+#pragma unroll
+        for (int k = C - 1; k >= 0; --k) {
+          if (k < na) {
+            double s = X[k];
+#pragma unroll
+            for (int m = k + 1; m < C; ++m)
+              if (m < na) s = fma(-Lsm[m][k], Z[m], s);
+            Z[k] = s * dinv[k];
+          }
+        }
+      }
     }
-    for (int e = lane; e < na * na; e += 32) {
-      const int i = e / na, j = e % na;
-      Gp[map[i] * kPad + map[j]] = dsc[i] * Ah[i * kPad + j] * dsc[j];
+    if (!ok) {   // Jacobi eigenvalue pseudo-inverse of D G D
+      for (int e = lane; e < kPad * kPad; e += 32) {
+        const int i = e / kPad, j = e % kPad;
+        double v = 0.0;
+        if (i < na && j < na) {
+          const int a = map[i], b = map[j];
+          v = (0.5 * dsm[a]) * red[tri_index(a < b ? a : b, a < b ? b : a, C)] * dsm[b];
+        }
+        A[e] = v;
+      }
+      __syncwarp();
+      warp_jacobi_pinv(A, V, na, st->tau, Ah, rc, rs, rp, rq, lam);
+#pragma unroll
+      for (int j = 0; j < C; ++j) Z[j] = (lane < na && j < na) ? Ah[lane * kPad + j] : 0.0;
     }
-    __syncwarp();
   }
+  // G^+ = D (D G D)^+ D on the active columns (zero rows and columns for
+  // dropped ones) into the window ring; alpha = G^+ g
   const int ns = (st->newest + 1) % st->m;
-  for (int e = lane; e < C * C; e += 32) st->gpinv[ns][e / C][e % C] = Gp[(e / C) * kPad + e % C];
-  if (lane < C) {
-    double s = 0.0;
-    for (int b = 0; b < C; ++b) s += Gp[lane * kPad + b] * red[NG + b];
-    st->alpha[lane] = s;
-    if (alpha_hist) alpha_hist[(long long)st->k * C + lane] = s;
+  for (int e = lane; e < C * C; e += 32) st->gpinv[ns][e / C][e % C] = 0.0;
+  __syncwarp();
+  double al = 0.0;
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const int cj = map[j < na ? j : 0];
+    const double dj = __shfl_sync(kFull, dsc, cj);
+    const double gj = __shfl_sync(kFull, gv, cj);
+    if (lane < na && j < na) {
+      const double v = di * Z[j] * dj;
+      st->gpinv[ns][ci][cj] = v;
+      al = fma(v, gj, al);
+    }
+  }
+  __syncwarp();
+  if (lane < C && !act) {
+    st->alpha[lane] = 0.0;
+    if (alpha_hist) alpha_hist[(long long)st->k * C + lane] = 0.0;
+  }
+  if (lane < na) {
+    st->alpha[ci] = al;
+    if (alpha_hist) alpha_hist[(long long)st->k * C + ci] = al;
   }
   __syncwarp();
   if (lane == 0) {
@@ -612,8 +689,9 @@ void launch_small_beta(DevState* st, int nb, const double* part_W, int nchunks, 
 void launch_small_alpha(DevState* st, int nb, const double* part_G, int nblk_G, const double* part_zaz, int nblk_zaz,
                         int zaz_stride, int C, double* alpha_hist, long long ahist_stride, double* scratch,
                         unsigned* counter, cudaStream_t s) {
-  k_small_alpha<<<dim3(kSmallGrid, nb), kBlock, 0, s>>>(st, part_G, nblk_G, part_zaz, nblk_zaz, zaz_stride, C,
-                                                        alpha_hist, ahist_stride, scratch, counter);
+  MPCG_SMALL_C_SWITCH(C, (k_small_alpha<CC><<<dim3(kSmallGrid, nb), kBlock, 0, s>>>(
+                             st, part_G, nblk_G, part_zaz, nblk_zaz, zaz_stride, alpha_hist, ahist_stride, scratch,
+                             counter)));
 }
 void launch_check(DevState* st, int nb, const double* part_r, int nblk, double* res_hist, long long hist_stride,
                   cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {

@@ -29,6 +29,20 @@ __global__ void k_pack(GridDesc g, const TI* __restrict__ src, long long ld, TO*
   }
 }
 
+// Pack of one FP64 column that also records whether it has a nonzero entry
+// (nz = 1; the caller zeroes nz first).  Bit patterns are tested (no FP64
+// arithmetic); -0.0 counts as nonzero.
+__global__ void k_pack_flag(GridDesc g, const double* __restrict__ src, double* __restrict__ dst, int* nz) {
+  const long long n = g.n;
+  bool any = false;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const double v = src[t];
+    any |= __double_as_longlong(v) != 0;
+    dst[padded_index(g, t)] = v;
+  }
+  if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) *nz = 1;
+}
+
 template <typename TI, typename TO>
 __global__ void k_unpack(GridDesc g, const TI* __restrict__ src, TO* __restrict__ dst, long long ld, int ncols) {
   const long long n = g.n;
@@ -118,8 +132,11 @@ __device__ __forceinline__ void stencil_group(const T* __restrict__ st, long lon
   }
 }
 
+// The FP32 3D instances with up to 6 columns run three blocks per SM (at most
+// 85 registers) in one wave of resident blocks (spmm_blocks): measured faster
+// than two blocks per SM over two waves, whose loads wait longer.
 template <typename T, int DIM, int C, bool ZAZ>
-__global__ void __launch_bounds__(kBlock) k_spmm(GridDesc g, const T* __restrict__ st, const T* __restrict__ X,
+__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && DIM == 3 && C <= 6) ? 3 : 1) k_spmm(GridDesc g, const T* __restrict__ st, const T* __restrict__ X,
                                                  T* __restrict__ Y, double* zaz, const DevState* state) {
   const int pb = blockIdx.y;
   if (state && state[pb].done) return;
@@ -152,11 +169,16 @@ __global__ void __launch_bounds__(kBlock) k_spmm(GridDesc g, const T* __restrict
   if (ZAZ) block_sum_store<T, ZAZ ? C : 1>(zacc, zaz + (long long)pb * C * gridDim.x, gridDim.x, blockIdx.x);
 }
 
+// r = b - A x with the partials of |r|^2 and |b|^2.  xnz (may be null) flags
+// per problem whether x can be nonzero; for a zero iterate A x = 0 exactly
+// and the stencil is not read (r = b, the same values bit for bit).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBlock) k_residual(GridDesc g, const T* __restrict__ st, const T* __restrict__ b,
-                                                     const T* __restrict__ xv, T* __restrict__ r, double* part) {
+                                                     const T* __restrict__ xv, T* __restrict__ r, double* part,
+                                                     const int* __restrict__ xnz) {
   constexpr int W = Vec<T>::W;
   const int pb = blockIdx.y;
+  const bool zero_x = xnz && xnz[pb] == 0;
   const long long bo = (long long)pb * g.len;
   T sums[2] = {0, 0};
   const long long ngroups = g.npts / W;
@@ -166,7 +188,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(GridDesc g, const T* __rest
     T acc[1][W];
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[0][w] = 0;
-    stencil_group<T, DIM, 1>(st, g.cp, xv, idx, g.px, g.pxy, acc);
+    if (!zero_x) stencil_group<T, DIM, 1>(st, g.cp, xv, idx, g.px, g.pxy, acc);
     T bv[W], rv[W];
     Vec<T>::load(b + idx, bv);
 #pragma unroll
@@ -720,9 +742,10 @@ __global__ void __launch_bounds__(kBlock) k_vspmm(GridDesc g, const T* __restric
 template <typename T, bool NORMS>
 __global__ void __launch_bounds__(kBlock, 3) k_vres(GridDesc g, const T* __restrict__ st, const T* __restrict__ b,
                                                     const T* __restrict__ xv, T* __restrict__ r, double* part,
-                                                    const DevState* state) {
+                                                    const DevState* state, const int* __restrict__ xnz) {
   const int pb = blockIdx.y;
   if (state && state[pb].done) return;
+  const bool zero_x = xnz && xnz[pb] == 0;   // zero iterate: r = b
   constexpr int W = Vec<T>::W;
   const long long bo = (long long)pb * g.len;
   const long long cs = g.cstride;
@@ -735,22 +758,24 @@ __global__ void __launch_bounds__(kBlock, 3) k_vres(GridDesc g, const T* __restr
     T acc[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[w] = 0;
+    if (!zero_x) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const long long ro = row_offset<3>(k, g.px, g.pxy);
+      for (int k = 0; k < 9; ++k) {
+        const long long ro = row_offset<3>(k, g.px, g.pxy);
 #pragma unroll
-      for (int bb = 0; bb < 3; ++bb) {
-        const T* sp = st + (long long)(bb * 27 + 3 * k) * g.cp + idx0 + a * cs;
-        T a0[W], a1[W], a2[W], e[W + 2];
-        Vec<T>::load(sp, a0);
-        Vec<T>::load(sp + g.cp, a1);
-        Vec<T>::load(sp + 2 * g.cp, a2);
-        load_row<T>(xv + idx0 + bb * cs + ro, e);
+        for (int bb = 0; bb < 3; ++bb) {
+          const T* sp = st + (long long)(bb * 27 + 3 * k) * g.cp + idx0 + a * cs;
+          T a0[W], a1[W], a2[W], e[W + 2];
+          Vec<T>::load(sp, a0);
+          Vec<T>::load(sp + g.cp, a1);
+          Vec<T>::load(sp + 2 * g.cp, a2);
+          load_row<T>(xv + idx0 + bb * cs + ro, e);
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-          acc[w] = fma(a0[w], e[w], acc[w]);
-          acc[w] = fma(a1[w], e[w + 1], acc[w]);
-          acc[w] = fma(a2[w], e[w + 2], acc[w]);
+          for (int w = 0; w < W; ++w) {
+            acc[w] = fma(a0[w], e[w], acc[w]);
+            acc[w] = fma(a1[w], e[w + 1], acc[w]);
+            acc[w] = fma(a2[w], e[w + 2], acc[w]);
+          }
         }
       }
     }
@@ -815,6 +840,26 @@ template <typename TI, typename TO>
 void launch_pack(const GridDesc& g, const TI* src, long long ld, TO* dst, int ncols, cudaStream_t s) {
   k_pack<TI, TO><<<grid_for(g.n * ncols, 4096), kBlock, 0, s>>>(g, src, ld, dst, ncols);
 }
+void launch_pack_flag(const GridDesc& g, const double* src, double* dst, int* nz, cudaStream_t s) {
+  k_pack_flag<<<grid_for(g.n, 4096), kBlock, 0, s>>>(g, src, dst, nz);
+}
+
+int g_sm_count = 0;
+void set_sm_count(int n) { g_sm_count = n; }
+
+template <typename T>
+int spmm_blocks(const GridDesc& g, int C) {
+  const int nb = stream_blocks(g);
+  if (sizeof(T) != 4 || g.dim != 3 || g.ncomp != 1 || C > 6 || g_sm_count <= 0) return nb;
+  const long long groups = g.npts / 2;
+  const long long need = (groups + kBlock * 16 - 1) / (kBlock * 16);
+  long long w = 3LL * g_sm_count;   // one wave at three blocks per SM
+  if (w < need) w = need;
+  return (int)(w < nb ? w : nb);
+}
+template int spmm_blocks<double>(const GridDesc&, int);
+template int spmm_blocks<float>(const GridDesc&, int);
+
 template <typename TI, typename TO>
 void launch_unpack(const GridDesc& g, const TI* src, TO* dst, long long ld, int ncols, cudaStream_t s) {
   k_unpack<TI, TO><<<grid_for(g.n * ncols, 4096), kBlock, 0, s>>>(g, src, dst, ld, ncols);
@@ -829,7 +874,7 @@ template void launch_unpack<float, float>(const GridDesc&, const float*, float*,
 template <typename T, int DIM>
 static void spmm_dim(const GridDesc& g, const T* st, const T* X, T* Y, int C, double* zaz, const DevState* state,
                      cudaStream_t s) {
-  const dim3 grid(stream_blocks(g), g.nb);
+  const dim3 grid(spmm_blocks<T>(g, C), g.nb);
 #define MPCG_SPMM_CASE(CC)                                                                      \
   case CC:                                                                                      \
     if (zaz) k_spmm<T, DIM, CC, true><<<grid, kBlock, 0, s>>>(g, st, X, Y, zaz, state);         \
@@ -874,16 +919,17 @@ template void launch_spmm<float>(const GridDesc&, const float*, const float*, fl
                                  const DevState*, cudaStream_t);
 
 template <typename T>
-void launch_residual(const GridDesc& g, const T* st, const T* b, const T* x, T* r, double* part, cudaStream_t s) {
+void launch_residual(const GridDesc& g, const T* st, const T* b, const T* x, T* r, double* part, cudaStream_t s,
+                     const int* xnz) {
   const dim3 grid(stream_blocks(g), g.nb);
-  if (g.ncomp == 3) k_vres<T, true><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part, nullptr);
-  else if (g.dim == 3) k_residual<T, 3><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part);
-  else k_residual<T, 2><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part);
+  if (g.ncomp == 3) k_vres<T, true><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part, nullptr, xnz);
+  else if (g.dim == 3) k_residual<T, 3><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part, xnz);
+  else k_residual<T, 2><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part, xnz);
 }
 template void launch_residual<double>(const GridDesc&, const double*, const double*, const double*, double*,
-                                      double*, cudaStream_t);
+                                      double*, cudaStream_t, const int*);
 template void launch_residual<float>(const GridDesc&, const float*, const float*, const float*, float*, double*,
-                                     cudaStream_t);
+                                     cudaStream_t, const int*);
 
 template <typename T>
 void launch_restrict(const GridDesc& gf, const GridDesc& gc, const T* rf, T* rc, const DevState* state,
@@ -909,7 +955,7 @@ template <typename T>
 void launch_vres(const GridDesc& g, const T* st, const T* r, const T* x, T* t, const DevState* state,
                  cudaStream_t s) {
   k_vres<T, false><<<dim3(blocks_for(3 * (g.cstride / vw<T>())), g.nb), kBlock, 0, s>>>(g, st, r, x, t, nullptr,
-                                                                                        state);
+                                                                                        state, nullptr);
 }
 template void launch_vres<double>(const GridDesc&, const double*, const double*, const double*, double*,
                                   const DevState*, cudaStream_t);
