@@ -399,68 +399,72 @@ __global__ void __launch_bounds__(kBlock) k_prolong(GridDesc gc, GridDesc gf, co
 // and (g >> m) + 1 with weights 1 - f/s and f/s, f = g mod s (exact binary
 // fractions); coarse parents outside the grid are pad entries (zero).  One
 // launch writes columns 0 .. J-1 of Z (column J is the fine smoothing),
-// equal to successive two-grid prolongation up to the summation order.
+// equal to successive two-grid prolongation up to the summation order.  The
+// grid count is a template parameter, so that every column's ratio s and
+// weights fold to constants (the kernel is bound by instruction issue).
 template <typename T>
 struct CoarseSrc {
   const T* v[kMaxLevels];      // grid j's correction (padded, problem 0)
   GridDesc g[kMaxLevels];
 };
 
-template <typename T, int DIM>
-__global__ void __launch_bounds__(kBlock) k_prolong_all(GridDesc gf, CoarseSrc<T> src, int J, T* __restrict__ Z,
+template <typename T, int DIM, int JJ>
+__global__ void __launch_bounds__(kBlock) k_prolong_all(GridDesc gf, CoarseSrc<T> src, T* __restrict__ Z,
                                                         const DevState* state) {
   const int pb = blockIdx.y;
   if (state && state[pb].done) return;
   constexpr int W = Vec<T>::W;
-  constexpr int NR = W / 2 + 2;   // coarse x values a group needs at s = 2
+  constexpr int NR = 3;   // coarse x values a group of W <= 4 fine points needs at s >= 2
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= gf.npts / W) return;
   const long long t0 = q * W;
   int x0, y, z, a;
   decode(gf, t0, x0, y, z, a);
   const long long idf = (long long)pb * gf.len + gf.G + t0;
-  const bool rowpad = y >= gf.ny || (DIM == 3 && z >= gf.nz);
-  for (int j = 0; j < J; ++j) {
+  if (y >= gf.ny || (DIM == 3 && z >= gf.nz)) {   // pad row
     T o[W];
-    if (rowpad) {
 #pragma unroll
-      for (int w = 0; w < W; ++w) o[w] = 0;
-    } else {
-      const GridDesc& gc = src.g[j];
-      const int m = J - j;
-      const int sm1 = (1 << m) - 1;
-      const T inv_s = (T)1 / (T)(1 << m);
-      const int gy = y + gf.loy, gz = z + gf.loz;
-      const int cy0 = (gy >> m) - gc.loy, cz0 = DIM == 3 ? (gz >> m) - gc.loz : 0;
-      const T wy1 = (T)(gy & sm1) * inv_s, wz1 = DIM == 3 ? (T)(gz & sm1) * inv_s : (T)0;
-      const int gx0 = x0 + gf.lox;
-      const int X0 = gx0 >> m;
-      const T* base = src.v[j] + (long long)pb * gc.len + gc.G + a * gc.cstride + (X0 - gc.lox);
-      T row[NR];
+    for (int w = 0; w < W; ++w) o[w] = 0;
 #pragma unroll
-      for (int k = 0; k < NR; ++k) row[k] = 0;
+    for (int j = 0; j < JJ; ++j) Vec<T>::store(Z + (long long)j * gf.cp + idf, o);
+    return;
+  }
+  const int gy = y + gf.loy, gz = DIM == 3 ? z + gf.loz : 0, gx0 = x0 + gf.lox;
 #pragma unroll
-      for (int kz = 0; kz < (DIM == 3 ? 2 : 1); ++kz) {
-        const T wz = DIM == 3 ? (kz ? wz1 : (T)1 - wz1) : (T)1;
+  for (int j = 0; j < JJ; ++j) {
+    // grid j sits m = JJ - j levels below: s = 2^m fine intervals per coarse one
+    const int m = JJ - j, s = 1 << m, sm1 = s - 1;
+    const T inv_s = (T)1 / (T)s;
+    const GridDesc& gc = src.g[j];
+    const int cy0 = (gy >> m) - gc.loy, cz0 = DIM == 3 ? (gz >> m) - gc.loz : 0;
+    const T wy1 = (T)(gy & sm1) * inv_s, wz1 = DIM == 3 ? (T)(gz & sm1) * inv_s : (T)0;
+    const int X0 = gx0 >> m;
+    const T* base = src.v[j] + (long long)pb * gc.len + gc.G + (long long)a * gc.cstride + (X0 - gc.lox);
+    T row[NR];
 #pragma unroll
-        for (int ky = 0; ky < 2; ++ky) {
-          const T wgt = wz * (ky ? wy1 : (T)1 - wy1);
-          const T* rp = base + gc.px * (long long)(cy0 + ky) + (DIM == 3 ? gc.pxy * (cz0 + kz) : 0);
+    for (int k = 0; k < NR; ++k) row[k] = 0;
 #pragma unroll
-          for (int k = 0; k < NR; ++k) row[k] = fma(wgt, rp[k], row[k]);
-        }
+    for (int kz = 0; kz < (DIM == 3 ? 2 : 1); ++kz) {
+      const T wz = DIM == 3 ? (kz ? wz1 : (T)1 - wz1) : (T)1;
+#pragma unroll
+      for (int ky = 0; ky < 2; ++ky) {
+        const T wgt = wz * (ky ? wy1 : (T)1 - wy1);
+        const T* rp = base + gc.px * (long long)(cy0 + ky) + (DIM == 3 ? gc.pxy * (long long)(cz0 + kz) : 0);
+#pragma unroll
+        for (int k = 0; k < NR; ++k) row[k] = fma(wgt, rp[k], row[k]);
       }
+    }
+    // along x: fine node gx0 + w = X0 s + t sits in coarse interval k = t / s
+    // at fraction (t mod s) / s; k = 2 only for s = 2, t = 4 (fraction 0)
+    const T d0 = row[1] - row[0], d1 = row[2] - row[1];
+    const int f0 = gx0 & sm1;
+    T o[W];
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        const int gx = gx0 + w;
-        const int k = (gx >> m) - X0;
-        const T wx1 = (T)(gx & sm1) * inv_s;
-        T v = row[0];
-#pragma unroll
-        for (int kk = 0; kk < NR - 1; ++kk)
-          if (kk == k) v = fma(wx1, row[kk + 1] - row[kk], row[kk]);
-        o[w] = x0 + w < gf.nx ? v : (T)0;
-      }
+    for (int w = 0; w < W; ++w) {
+      const int t = f0 + w, k = t >> m;
+      const T f = (T)(t & sm1) * inv_s;
+      const T v = k == 0 ? fma(f, d0, row[0]) : (k == 1 ? fma(f, d1, row[1]) : row[2]);
+      o[w] = x0 + w < gf.nx ? v : (T)0;
     }
     Vec<T>::store(Z + (long long)j * gf.cp + idf, o);
   }
@@ -1047,8 +1051,19 @@ void launch_prolong_all(const GridDesc& gf, const T* const* coarse, const GridDe
     src.g[j] = gcs[j];
   }
   const dim3 grid(blocks_for(gf.npts / vw<T>()), gf.nb);
-  if (gf.dim == 3) k_prolong_all<T, 3><<<grid, kBlock, 0, s>>>(gf, src, J, Z, state);
-  else k_prolong_all<T, 2><<<grid, kBlock, 0, s>>>(gf, src, J, Z, state);
+  static_assert(kMaxLevels <= 12, "the switch below covers up to 11 coarse grids");
+#define MPCG_PROLONG_CASE(JJ)                                                                   \
+  case JJ:                                                                                      \
+    if (gf.dim == 3) k_prolong_all<T, 3, JJ><<<grid, kBlock, 0, s>>>(gf, src, Z, state);       \
+    else k_prolong_all<T, 2, JJ><<<grid, kBlock, 0, s>>>(gf, src, Z, state);                   \
+    break;
+  switch (J) {
+    MPCG_PROLONG_CASE(1) MPCG_PROLONG_CASE(2) MPCG_PROLONG_CASE(3) MPCG_PROLONG_CASE(4) MPCG_PROLONG_CASE(5)
+    MPCG_PROLONG_CASE(6) MPCG_PROLONG_CASE(7) MPCG_PROLONG_CASE(8) MPCG_PROLONG_CASE(9) MPCG_PROLONG_CASE(10)
+    MPCG_PROLONG_CASE(11)
+    default: break;
+  }
+#undef MPCG_PROLONG_CASE
 }
 template void launch_prolong_all<double>(const GridDesc&, const double* const*, const GridDesc*, int, double*,
                                          const DevState*, cudaStream_t);
