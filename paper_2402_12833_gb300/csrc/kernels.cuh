@@ -70,11 +70,6 @@ void launch_vres(const GridDesc& g, const T* st, const T* r, const T* x, T* t, c
 template <typename T>
 void launch_vblock(const GridDesc& g, const T* dinv, const T* t, const T* sin, T* out, const DevState* state,
                    cudaStream_t s);
-// fine[c] = P coarse[c] for c < ncols (column stride: grid len)
-template <typename T>
-void launch_prolong(const GridDesc& gc, const GridDesc& gf, const T* coarse, T* fine, int ncols,
-                    const DevState* state, cudaStream_t s);
-// coarse stencil = P^T A P (FP64)
 // out = Zc[0] + ... + Zc[ncols-1] (columns cp apart).
 template <typename T>
 void launch_sum_columns(const GridDesc& g, const T* Zc, int ncols, T* out, const DevState* state, cudaStream_t s);
@@ -89,6 +84,7 @@ void launch_coarse_tail(int jt, const GridDesc* g, const T* const* st, const T* 
 template <typename T>
 void launch_prolong_all(const GridDesc& gf, const T* const* coarse, const GridDesc* gcs, int J, T* Z,
                         const DevState* state, cudaStream_t s);
+// coarse stencil = P^T A P (FP64)
 void launch_galerkin(const GridDesc& gf, const GridDesc& gc, const double* stf, double* stc,
                      cudaStream_t s);
 // dinv = omega / centre coefficient (0 at pads)

@@ -311,86 +311,6 @@ __global__ void __launch_bounds__(kBlock, 4) k_jacobi(GridDesc g, const T* __res
   if (active) Vec<T>::store(out + idx, o);
 }
 
-// Prolongation P: bilinear / trilinear interpolation from the coarse grid.
-// Fine unknown i of an axis is global node g = i + lo; even g sits on coarse
-// node g/2, odd g takes half of coarse nodes (g-1)/2 and (g+1)/2 (coarse
-// unknown index = global - lo).  A group of W fine points starting at x0
-// (a multiple of 4, so even) reads coarse values x0/2 - lo .. x0/2 - lo + W/2
-// of each contributing coarse row:
-//   lo = 1: fine x0 + 2k = (c[k] + c[k+1]) / 2, fine x0 + 2k + 1 = c[k+1]
-//   lo = 0: fine x0 + 2k = c[k],               fine x0 + 2k + 1 = (c[k] + c[k+1]) / 2
-// Parents outside the grid are pad entries of the coarse layout (zero);
-// fine pad entries are written as zero.
-template <typename T, int DIM>
-__global__ void __launch_bounds__(kBlock) k_prolong(GridDesc gc, GridDesc gf, const T* __restrict__ coarse,
-                                                    T* __restrict__ fine, int ncols, const DevState* state) {
-  const int pb = blockIdx.y;
-  if (state && state[pb].done) return;
-  constexpr int W = Vec<T>::W;
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= gf.npts / W) return;
-  const long long t0 = q * W;
-  int x0, y, z, a;
-  decode(gf, t0, x0, y, z, a);
-  const long long idf = (long long)pb * gf.len + gf.G + t0;
-  const bool rowpad = y >= gf.ny || (DIM == 3 && z >= gf.nz);
-  // per axis: parents (c0, c1) with weights (w0, w1)
-  auto par = [](int i, int lo, int& c0, int& c1, T& w0, T& w1) {
-    const int g = i + lo;
-    if ((g & 1) == 0) { c0 = c1 = (g >> 1) - lo; w0 = (T)1; w1 = (T)0; }
-    else { c0 = ((g - 1) >> 1) - lo; c1 = c0 + 1; w0 = w1 = (T)0.5; }
-  };
-  int cy0, cy1, cz0 = 0, cz1 = 0;
-  T wy0, wy1, wz0 = 1, wz1 = 0;
-  par(y, gf.loy, cy0, cy1, wy0, wy1);
-  if (DIM == 3) par(z, gf.loz, cz0, cz1, wz0, wz1);
-  const long long pc = gc.px, ppc = gc.pxy;
-  const int cxb = (x0 >> 1) - gf.lox;
-  for (int c = 0; c < ncols; ++c) {
-    T o[W];
-    if (rowpad) {
-#pragma unroll
-      for (int w = 0; w < W; ++w) o[w] = 0;
-      Vec<T>::store(fine + (long long)c * gf.cp + idf, o);
-      continue;
-    }
-    const T* C0 = coarse + (long long)c * gc.cp + (long long)pb * gc.len + gc.G + a * gc.cstride;
-    T row[W / 2 + 1];
-#pragma unroll
-    for (int k = 0; k <= W / 2; ++k) row[k] = 0;
-#pragma unroll
-    for (int kz = 0; kz < (DIM == 3 ? 2 : 1); ++kz) {
-      const int czz = kz ? cz1 : cz0;
-      const T wz = kz ? wz1 : wz0;
-#pragma unroll
-      for (int ky = 0; ky < 2; ++ky) {
-        const int cyy = ky ? cy1 : cy0;
-        const T wgt = wz * (ky ? wy1 : wy0);
-        const T* rp = C0 + pc * cyy + (DIM == 3 ? ppc * czz : 0) + cxb;
-#pragma unroll
-        for (int k = 0; k <= W / 2; ++k) row[k] = fma(wgt, rp[k], row[k]);
-      }
-    }
-    if (gf.lox) {
-#pragma unroll
-      for (int k = 0; k < W / 2; ++k) {
-        o[2 * k] = (T)0.5 * (row[k] + row[k + 1]);
-        o[2 * k + 1] = row[k + 1];
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < W / 2; ++k) {
-        o[2 * k] = row[k];
-        o[2 * k + 1] = (T)0.5 * (row[k] + row[k + 1]);
-      }
-    }
-#pragma unroll
-    for (int w = 0; w < W; ++w)
-      if (x0 + w >= gf.nx) o[w] = 0;
-    Vec<T>::store(fine + (long long)c * gf.cp + idf, o);
-  }
-}
-
 // Composite prolongation P_J ... P_{j+1} of every coarse grid's correction
 // straight to the fine grid (Section 2.1 allows the composite transfers to be
 // formed explicitly): the nested Q1 spaces make it the multilinear
@@ -981,17 +901,6 @@ template void launch_jacobi<double>(const GridDesc&, const double*, const double
 template void launch_jacobi<float>(const GridDesc&, const float*, const float*, const float*, const float*, float*,
                                    int, const DevState*, cudaStream_t);
 
-template <typename T>
-void launch_prolong(const GridDesc& gc, const GridDesc& gf, const T* coarse, T* fine, int ncols,
-                    const DevState* state, cudaStream_t s) {
-  const dim3 grid(blocks_for(gf.npts / vw<T>()), gf.nb);
-  if (gf.dim == 3) k_prolong<T, 3><<<grid, kBlock, 0, s>>>(gc, gf, coarse, fine, ncols, state);
-  else k_prolong<T, 2><<<grid, kBlock, 0, s>>>(gc, gf, coarse, fine, ncols, state);
-}
-template void launch_prolong<double>(const GridDesc&, const GridDesc&, const double*, double*, int,
-                                     const DevState*, cudaStream_t);
-template void launch_prolong<float>(const GridDesc&, const GridDesc&, const float*, float*, int, const DevState*,
-                                    cudaStream_t);
 
 // out = sum of the ncols columns of Zc (the additive MG correction B r of
 // Eq. 3 as a single search direction), columns added in order.
