@@ -106,7 +106,7 @@ def level_dofs(nodes, dim, levels):
     return [((nodes - 1) // 2 ** (levels - 1 - j) - 1) ** dim for j in range(levels)]
 
 
-def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops, S=27, vector=False):
+def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops, S=27, vector=False, s_fine=None):
     """Dominant kernel class by total time; achieved = algorithmic bytes
     (or flops) summed over its launches / summed CUDA-event durations.
 
@@ -143,7 +143,8 @@ def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops, S=27, vector=False
                 jj -= 1
             jsub = (jsub + 1) % 3
         elif cls == "jacobi":
-            b, f = (S + 3) * w * ns[jj], (2 * S + 4) * ns[jj]
+            Sj = s_fine if (s_fine is not None and jj == J) else S   # matrix-free fine grid: kappa, not stencil
+            b, f = (Sj + 3) * w * ns[jj], (2 * S + 4) * ns[jj]
             jj -= 1
         elif cls == "restrict":
             b, f = (ns[jr] + ns[jr - 1]) * w, 2 * 27 * ns[jr - 1]
@@ -151,7 +152,7 @@ def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops, S=27, vector=False
         elif cls == "prolong":   # composite: write J fine columns, read every coarse correction once
             b, f = (J * ns[J] + sum(ns[:J])) * w, 2 * 8 * J * ns[J]
         elif cls in ("orth_update", "gram_window", "spmm", "update_xr"):
-            b, f = kernel_work(cls, ns[J], C, cnt, w, S)
+            b, f = kernel_work(cls, ns[J], C, cnt, w, s_fine if (s_fine is not None and cls == "spmm") else S)
         if cls == dom:
             if b is not None:
                 bytes_sum += b
@@ -381,6 +382,27 @@ def bench_ours(args):
     m1_ms = max_over_ranks(_timed(m1_step, args.steps, args.warmup, stream))
     Hm1.close()
 
+    # the same solve with the matrix-free fine operator (element coefficients
+    # kappa = 1 of this Poisson problem; the FP32 fine kernels rebuild the rows)
+    Hmf = M.Hierarchy(st, DIM, NODES, prob.levels, m=M_WINDOW, precision=M.MPCG_MIXED, stream=sptr, use_graph=ug)
+    M.mg_attach_q1_kappa(Hmf.h, torch.ones((NODES - 1) ** DIM, dtype=torch.float64, device="cuda"))
+    mf = {}
+
+    def mf_step():
+        x.zero_()
+        mf["st"], mf["k"], _, _ = Hmf.solve(b, x, rtol=RTOL, maxit=MAXIT, histories=False)
+
+    mf_ms = max_over_ranks(_timed(mf_step, args.steps, args.warmup, stream))
+    Axm = torch.empty_like(b)
+    M.mg_apply_operator(Hmf.h, prob.levels - 1, x, Axm, 1)
+    mf["true_res"] = float(torch.linalg.norm(b - Axm) / torch.linalg.norm(b))
+    x.zero_()
+    _, _, _, trace_mf = M.mpcg_solve_profiled(Hmf.h, b, x, RTOL, MAXIT)
+    _, mf["roofline"], _, tot_mf = roofline(trace_mf, level_dofs(NODES, DIM, prob.levels), prob.levels, M_WINDOW, 4,
+                                            peaks, FP64_PEAK_TFLOPS, s_fine=1)
+    mf["class_ms"] = {c: round(v, 4) for c, v in tot_mf.items()}
+    Hmf.close()
+
     # per-kernel durations from a live profiled solve (CUDA events on the solve stream)
     prof = {}
     for key, w in (("mixed", 4), ("fp64", 8)):
@@ -434,6 +456,11 @@ def bench_ours(args):
             "iterations": mx["iters"], "true_rel_residual": mx["true_rel_residual"],
             "rel_diff_vs_fp64_solution": mix_vs_fp64,
             "m1": {"value": world * n / (m1_ms * 1e-3), "ms_per_step": m1_ms, "iterations": int(m1["k"])},
+            "matrix_free": {"value": world * n / (mf_ms * 1e-3), "ms_per_step": mf_ms, "iterations": int(mf["k"]),
+                            "true_rel_residual": mf["true_res"], "roofline": mf["roofline"],
+                            "kernel_ms_per_solve": mf["class_ms"],
+                            "operator": "fine grid rebuilt from the element coefficients (kappa = 1) in the FP32 "
+                                        "SpMM and Jacobi kernels; stored stencils elsewhere"},
             "roofline": prof["mixed"]["roofline"],
             "fp64": {"value": res["fp64"]["value"], "unit": "DOFs/s", "ms_per_step": res["fp64"]["ms_per_step"],
                      "iterations": res["fp64"]["iters"], "true_rel_residual": res["fp64"]["true_rel_residual"],

@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT, "libmpcg.so")
-SOURCES = ["api.cu", "stencil.cu", "block.cu", "small.cu", "learned.cu", "learned_tc.cu", "batch.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "stencil.cu", "block.cu", "small.cu", "matfree.cu", "learned.cu", "learned_tc.cu", "batch.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

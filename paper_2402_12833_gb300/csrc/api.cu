@@ -53,6 +53,7 @@ struct Level {
   float* st32 = nullptr;
   double* dinv64 = nullptr;
   float* dinv32 = nullptr;
+  float* kq32 = nullptr;   // fine grid: -(h/12) kappa per element (matrix-free FP32 operator), or null
 };
 
 struct Alloc {
@@ -199,6 +200,7 @@ struct Profiler {
 struct mg_hierarchy {
   int device = 0;
   int dim = 2, levels = 1;
+  int nodes = 0;               // fine-grid nodes per side, boundary included
   int nb = 1;                  // problems in the batch (same grid, own operators)
   int* active = nullptr;       // mixed path: problems still refining
   mpcg_options opt;
@@ -337,6 +339,12 @@ void enqueue_smooth(mg_hierarchy* h, Solver<T>& S, int j, const T* rr, T* out, c
     }
     return;
   }
+  if constexpr (std::is_same<T, float>::value) {
+    if (nu == 2 && L.kq32) {   // fine grid with the matrix-free operator
+      LAUNCH(h, K_JACOBI, s, launch_jacobi_mf(L.g, L.kq32, di, rr, out, state, s));
+      return;
+    }
+  }
   if (nu == 1) {
     LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, nullptr, out, 0, state, s));
   } else if (nu == 2) {
@@ -465,7 +473,14 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
            launch_net_infer<T>(L.g, 1, S.r, L.g.len, h->net_c, h->net_wtc, S.state, nullptr,
                                S.Z + (size_t)(C - 1) * L.g.len, h->net_err, s));
   }
-  LAUNCH(h, K_SPMM, s, launch_spmm<T>(L.g, st_of<T>(L), S.Z, S.AZ, C, S.part_zaz, S.state, s));
+  bool mf = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (L.kq32 && C <= 8) {   // fine operator rebuilt from the element coefficients
+      LAUNCH(h, K_SPMM, s, launch_spmm_mf(L.g, L.kq32, S.Z, S.AZ, C, spmm_blocks<T>(L.g, C), S.part_zaz, S.state, s));
+      mf = true;
+    }
+  }
+  if (!mf) LAUNCH(h, K_SPMM, s, launch_spmm<T>(L.g, st_of<T>(L), S.Z, S.AZ, C, S.part_zaz, S.state, s));
   LAUNCH(h, K_GRAM, s, launch_gram_window<T>(L.g, S.win, S.Z, C, S.m, S.part_W, S.state, s));
   LAUNCH(h, K_BETA, s, launch_small_beta(S.state, h->nb, S.part_W, gram_chunks(L.g), C, S.small_scratch, S.counters,
                                          s));
@@ -779,6 +794,7 @@ static mpcg_status setup_impl(const mg_operator* ops, int nb, int levels, const 
   h->dim = A->dim;
   h->levels = levels;
   h->nb = nb;
+  h->nodes = A->nodes;
   h->opt = opt;
   h->stream = (cudaStream_t)opt.stream;
   h->n0 = (int)n0;
@@ -1430,6 +1446,52 @@ mpcg_status mg_learned_detach(mg_hierarchy* h) {
     h->net_on = false;
     CKS(rebuild_solvers(h));
   }
+  return MPCG_OK;
+}
+
+mpcg_status mg_attach_q1_kappa(mg_hierarchy* h, const double* kappa_dev) {
+  g_err.clear();
+  CKS(check_single(h));
+  Level& L = h->lev[h->levels - 1];
+  if (!kappa_dev || L.g.dim != 3 || L.g.ncomp != 1) {
+    set_err("mg_attach_q1_kappa: 3D scalar hierarchies and a device kappa array only");
+    return MPCG_ERR_ARG;
+  }
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = h->stream;
+  CKS(build_f32(h));
+  const int nodes = h->nodes;   // elements per side: nodes - 1
+  float* k32 = nullptr;
+  double* k64 = nullptr;
+  unsigned long long* chk = nullptr;
+  CKS(h->mem.get(&k32, L.g.len, s));
+  CK(cudaMalloc(&k64, sizeof(double) * L.g.len));
+  CK(cudaMalloc(&chk, 2 * sizeof(unsigned long long)));
+  CK(cudaMemsetAsync(k64, 0, sizeof(double) * L.g.len, s));
+  double dmax = 0.0, amax = 0.0;
+  const mpcg_status st = place_kappa(L.g, kappa_dev, nodes - 1, 1.0 / (nodes - 1), k32, k64, chk, L.st64, &dmax,
+                                     &amax, s);
+  cudaFree(k64);
+  cudaFree(chk);
+  CKS(st);
+  CK(cudaGetLastError());
+  if (!(dmax <= 1e-10 * amax)) {
+    set_err("mg_attach_q1_kappa: the stored fine operator is not the Q1 diffusion operator of this kappa "
+            "(largest coefficient difference %.3e of %.3e)", dmax, amax);
+    return MPCG_ERR_ARG;
+  }
+  L.kq32 = k32;
+  h->s32.drop_graph();
+  drop_mixed_graph_fwd(h);
+  return MPCG_OK;
+}
+
+mpcg_status mg_detach_q1_kappa(mg_hierarchy* h) {
+  g_err.clear();
+  CKS(check_single(h));
+  h->lev[h->levels - 1].kq32 = nullptr;
+  h->s32.drop_graph();
+  drop_mixed_graph_fwd(h);
   return MPCG_OK;
 }
 

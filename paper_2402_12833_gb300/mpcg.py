@@ -87,6 +87,8 @@ _SIGS = {
     "mg_learned_num_params": (C.c_int, []),
     "mg_learned_attach": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "mg_learned_detach": (C.c_int, [C.c_void_p]),
+    "mg_attach_q1_kappa": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mg_detach_q1_kappa": (C.c_int, [C.c_void_p]),
     "mg_learned_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mg_learned_train": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                    C.POINTER(mg_train_opts), C.c_void_p, C.c_void_p]),
@@ -237,6 +239,17 @@ def mg_learned_attach(h: int, params) -> None:
 
 def mg_learned_detach(h: int) -> None:
     _check(load().mg_learned_detach(h))
+
+
+def mg_attach_q1_kappa(h: int, kappa_dev) -> None:
+    """Matrix-free FP32 fine operator from the element coefficients (device
+    tensor of (nodes - 1)^3 float64, x fastest); checked against the stored
+    fine stencil."""
+    _check(load().mg_attach_q1_kappa(h, _ptr(kappa_dev)))
+
+
+def mg_detach_q1_kappa(h: int) -> None:
+    _check(load().mg_detach_q1_kappa(h))
 
 
 def mg_learned_forward(h: int, rhat_dev, y_dev, nimg: int = 1) -> None:
