@@ -181,8 +181,8 @@ def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops, S=27, vector=False
 def measured_traffic(key: str):
     """DRAM bytes per launch of a kernel class, from the ncu summaries under
     profiles/ (lines "traffic: key=<leg>:<class> bytes_per_launch=<B>
-    source=<file> sha256=<hash>").  None unless the kernel's source file is
-    unchanged since the counters were taken."""
+    source=<file>[,<file>] sha256=<hash>[,<hash>]").  None unless the
+    kernels' source files are unchanged since the counters were taken."""
     import glob
     import hashlib
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
@@ -193,12 +193,14 @@ def measured_traffic(key: str):
                 kv = dict(t.split("=", 1) for t in line.split()[1:])
                 if kv.get("key") != key:
                     continue
-                src = os.path.join(ROOT, "paper_2402_12833_gb300", "csrc", kv["source"])
-                if not os.path.exists(src):
-                    return None
-                with open(src, "rb") as g:
-                    if hashlib.sha256(g.read()).hexdigest() != kv["sha256"]:
+                # source=a.cu[,b.cu] sha256=h_a[,h_b]: every listed file unchanged
+                for name, digest in zip(kv["source"].split(","), kv["sha256"].split(",")):
+                    src = os.path.join(ROOT, "paper_2402_12833_gb300", "csrc", name)
+                    if not os.path.exists(src):
                         return None
+                    with open(src, "rb") as g:
+                        if hashlib.sha256(g.read()).hexdigest() != digest:
+                            return None
                 return float(kv["bytes_per_launch"])
     return None
 
@@ -310,6 +312,8 @@ def bench_ours(args):
                               use_graph=ug),
          "fp64": M.Hierarchy(st, DIM, NODES, prob.levels, m=M_WINDOW, precision=M.MPCG_FP64, stream=sptr,
                              use_graph=ug)}
+    if args.matrix_free:   # the matrix-free fine operator (element coefficients kappa = 1) in the mixed solve
+        M.mg_attach_q1_kappa(H["mixed"].h, torch.ones((NODES - 1) ** DIM, dtype=torch.float64, device="cuda"))
     b = torch.from_numpy(prob.b).cuda()
     x = torch.zeros_like(b)
     peaks = load_peaks()
@@ -400,6 +404,8 @@ def bench_ours(args):
     _, _, _, trace_mf = M.mpcg_solve_profiled(Hmf.h, b, x, RTOL, MAXIT)
     _, mf["roofline"], _, tot_mf = roofline(trace_mf, level_dofs(NODES, DIM, prob.levels), prob.levels, M_WINDOW, 4,
                                             peaks, FP64_PEAK_TFLOPS, s_fine=1)
+    if mf["roofline"] is not None:
+        mf["roofline"]["traffic"] = measured_traffic(f"poisson3d_mixed_mf:{mf['roofline']['kernel']}")
     mf["class_ms"] = {c: round(v, 4) for c, v in tot_mf.items()}
     Hmf.close()
 
@@ -835,6 +841,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--matrix-free", action="store_true",
+                    help="with --only mixed: the matrix-free fine operator in the timed solve")
     ap.add_argument("--direct", action="store_true",
                     help="launch kernels directly instead of one graph per solve (for ncu launch lists)")
     ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
