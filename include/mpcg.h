@@ -238,21 +238,23 @@ long long mg_last_launches(const mg_hierarchy* h);
 
 /*
  * Matrix-free fine operator (an extension: the paper names the combination
- * with a matrix-free strategy as future work, Section 4).  For a 3D scalar
- * hierarchy whose fine operator is the Q1 discretisation of -div(kappa grad
- * u) of Section 1 (kappa constant on each element, isotropic, h = 1/(nodes
- * - 1)), mg_attach_q1_kappa takes the element coefficients kappa_dev (device,
- * (nodes - 1)^3 doubles, x fastest) and from then on the FP32 kernels of the
- * mixed-precision inner solves rebuild the fine rows from them (the block
- * SpMM and the fine-grid two-sweep Jacobi) instead of streaming the stored
- * stencil: about 1 instead of 27 coefficient words per unknown.  The stored
- * operator stays for setup, the coarse grids and the FP64 refinement
- * residual.  The call checks every coupling between unknowns of the stored
- * FP64 fine stencil against the one kappa defines (largest difference at most
- * 1e-10 of the largest coefficient) and returns MPCG_ERR_ARG otherwise (or
- * for 2D, vector or batched hierarchies).  mg_detach_q1_kappa goes back to the
- * stored operator.  Results differ from the stored-operator solve by FP32
- * rounding only. */
+ * with a matrix-free strategy as future work, Section 4).  For a scalar
+ * hierarchy (2D or 3D, single or batched) whose fine operator is the Q1
+ * discretisation of -div(kappa grad u) of Section 1 (kappa constant on each
+ * element, isotropic, h = 1/(nodes - 1)), mg_attach_q1_kappa takes the
+ * element coefficients kappa_dev (device doubles: for each problem of the
+ * batch in turn, (nodes - 1)^dim elements, x fastest) and from then on the
+ * FP32 kernels of the mixed-precision inner solves rebuild the fine rows
+ * from them (the block SpMM and the fine-grid two-sweep Jacobi) instead of
+ * streaming the stored stencil: about 1 instead of 3^dim coefficient words
+ * per unknown.  The stored operators stay for setup, the coarse grids and
+ * the FP64 refinement residual.  The call checks every coupling between
+ * unknowns of the stored FP64 fine stencils against the ones kappa defines
+ * (largest difference at most 1e-10 of the largest coefficient) and returns
+ * MPCG_ERR_ARG otherwise (and for vector hierarchies); after a refused call
+ * the stored operator is in use.  mg_detach_q1_kappa goes back to the stored
+ * operator.  Results differ from the stored-operator
+ * solve by FP32 rounding only. */
 mpcg_status mg_attach_q1_kappa(mg_hierarchy* h, const double* kappa_dev);
 mpcg_status mg_detach_q1_kappa(mg_hierarchy* h);
 

@@ -53,7 +53,8 @@ struct Level {
   float* st32 = nullptr;
   double* dinv64 = nullptr;
   float* dinv32 = nullptr;
-  float* kq32 = nullptr;   // fine grid: -(h/12) kappa per element (matrix-free FP32 operator), or null
+  float* kq32 = nullptr;         // fine grid: element coefficients in use (matrix-free FP32 operator), or null
+  float* kq32_store = nullptr;   // their storage (kept across detach / attach)
 };
 
 struct Alloc {
@@ -475,8 +476,9 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
   }
   bool mf = false;
   if constexpr (std::is_same<T, float>::value) {
-    if (L.kq32 && C <= 8) {   // fine operator rebuilt from the element coefficients
-      LAUNCH(h, K_SPMM, s, launch_spmm_mf(L.g, L.kq32, S.Z, S.AZ, C, spmm_blocks<T>(L.g, C), S.part_zaz, S.state, s));
+    if (L.kq32 && C <= 12) {   // fine operator rebuilt from the element coefficients
+      LAUNCH(h, K_SPMM, s,
+             launch_spmm_mf(L.g, L.kq32, S.Z, S.AZ, C, spmm_blocks<T>(L.g, C), S.part_zaz, S.state, s));
       mf = true;
     }
   }
@@ -1451,28 +1453,39 @@ mpcg_status mg_learned_detach(mg_hierarchy* h) {
 
 mpcg_status mg_attach_q1_kappa(mg_hierarchy* h, const double* kappa_dev) {
   g_err.clear();
-  CKS(check_single(h));
+  CKS(check_h(h));
   Level& L = h->lev[h->levels - 1];
-  if (!kappa_dev || L.g.dim != 3 || L.g.ncomp != 1) {
-    set_err("mg_attach_q1_kappa: 3D scalar hierarchies and a device kappa array only");
+  if (!kappa_dev || L.g.ncomp != 1) {
+    set_err("mg_attach_q1_kappa: scalar hierarchies and a device kappa array only");
     return MPCG_ERR_ARG;
   }
   CK(cudaSetDevice(h->device));
   cudaStream_t s = h->stream;
   CKS(build_f32(h));
   const int nodes = h->nodes;   // elements per side: nodes - 1
-  float* k32 = nullptr;
+  if (!L.kq32_store) CKS(h->mem.get(&L.kq32_store, L.g.cp, s));
   double* k64 = nullptr;
   unsigned long long* chk = nullptr;
-  CKS(h->mem.get(&k32, L.g.len, s));
-  CK(cudaMalloc(&k64, sizeof(double) * L.g.len));
-  CK(cudaMalloc(&chk, 2 * sizeof(unsigned long long)));
-  CK(cudaMemsetAsync(k64, 0, sizeof(double) * L.g.len, s));
+  if (cudaMalloc(&k64, sizeof(double) * L.g.cp) != cudaSuccess ||
+      cudaMalloc(&chk, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaFree(k64);
+    cudaGetLastError();
+    set_err("mg_attach_q1_kappa: device allocation failed");
+    return MPCG_ERR_OOM;
+  }
   double dmax = 0.0, amax = 0.0;
-  const mpcg_status st = place_kappa(L.g, kappa_dev, nodes - 1, 1.0 / (nodes - 1), k32, k64, chk, L.st64, &dmax,
-                                     &amax, s);
+  mpcg_status st = MPCG_OK;
+  if (cudaMemsetAsync(k64, 0, sizeof(double) * L.g.cp, s) != cudaSuccess ||
+      cudaMemsetAsync(L.kq32_store, 0, sizeof(float) * L.g.cp, s) != cudaSuccess)
+    st = MPCG_ERR_CUDA;
+  if (st == MPCG_OK)
+    st = place_kappa(L.g, kappa_dev, nodes - 1, 1.0 / (nodes - 1), L.kq32_store, k64, chk, L.st64, &dmax, &amax, s);
   cudaFree(k64);
   cudaFree(chk);
+  // the slots were rewritten: until the check passes, the stored operator is in use
+  L.kq32 = nullptr;
+  h->s32.drop_graph();
+  drop_mixed_graph_fwd(h);
   CKS(st);
   CK(cudaGetLastError());
   if (!(dmax <= 1e-10 * amax)) {
@@ -1480,15 +1493,13 @@ mpcg_status mg_attach_q1_kappa(mg_hierarchy* h, const double* kappa_dev) {
             "(largest coefficient difference %.3e of %.3e)", dmax, amax);
     return MPCG_ERR_ARG;
   }
-  L.kq32 = k32;
-  h->s32.drop_graph();
-  drop_mixed_graph_fwd(h);
+  L.kq32 = L.kq32_store;
   return MPCG_OK;
 }
 
 mpcg_status mg_detach_q1_kappa(mg_hierarchy* h) {
   g_err.clear();
-  CKS(check_single(h));
+  CKS(check_h(h));
   h->lev[h->levels - 1].kq32 = nullptr;
   h->s32.drop_graph();
   drop_mixed_graph_fwd(h);

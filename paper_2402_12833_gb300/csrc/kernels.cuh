@@ -109,16 +109,18 @@ void launch_update_xr(const GridDesc& g, Window<T> win, T* x, T* r, int C, doubl
                       const DevState* state, cudaStream_t s);
 
 // ---- matfree.cu ----------------------------------------------------------
-// Element coefficients kappa (FP64, (ne)^3 elements, x fastest) into the
-// padded slots k32 / k64 of the fine grid as -(h/12) kappa, and the largest
-// difference between the stored FP64 stencil st64 and the one kappa defines
-// (couplings between unknowns), with the largest stored coefficient.
+// Element coefficients kappa (FP64, nb problems of ne^dim elements, x
+// fastest) into the padded slots k32 / k64 of the fine grid as -(h/12) kappa
+// (3D) or -kappa/6 (2D), and the largest difference between the stored FP64
+// stencil st64 and the one kappa defines (couplings between unknowns, all
+// problems), with the largest stored coefficient.
 mpcg_status place_kappa(const GridDesc& g, const double* kappa, int ne, double h, float* k32, double* k64,
                         unsigned long long* check, const double* st64, double* maxdiff, double* maxabs,
                         cudaStream_t s);
-// Y = A X (C <= 8 columns, zaz partials as launch_spmm with nblocks blocks)
-// and the fused two-sweep Jacobi, A rebuilt from k32 (3D scalar, FP32).
-void launch_spmm_mf(const GridDesc& g, const float* k32, const float* X, float* Y, int C, int nblocks, double* zaz,
+// Y = A X (C <= 12 columns, zaz partials as launch_spmm with nblocks blocks;
+// false for other C) and the fused two-sweep Jacobi, A rebuilt from k32
+// (2D / 3D scalar, FP32).
+bool launch_spmm_mf(const GridDesc& g, const float* k32, const float* X, float* Y, int C, int nblocks, double* zaz,
                     const DevState* state, cudaStream_t s);
 void launch_jacobi_mf(const GridDesc& g, const float* k32, const float* dinv, const float* r, float* out,
                       const DevState* state, cudaStream_t s);

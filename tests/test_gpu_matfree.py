@@ -3,10 +3,13 @@ from the element coefficients) against the stored-operator path and the
 FP64 oracle, through the C ABI.
 
 The attach call must accept exactly the operators its kappa defines; solves
-with it must reach the FP64 tolerance by the true residual, agree with the
-stored-operator mixed solve in iteration count (+-1: FP32 rounding of the
-rebuilt coefficients only) and with the FP64 oracle solution as the mixed
-path does.
+with it must reach the FP64 tolerance by the true residual and agree with the
+FP64 oracle solution as the mixed path does.  Their iteration counts follow
+the FP32 rounding of the rebuilt coefficients: within 10 % of the
+stored-operator solve (on high-contrast 2D fields the count of the FP32
+inner solves moves by several iterations under rounding-level changes, as
+the oracle's own counts do under 1e-15 perturbations of the right-hand
+side; the 3D cases stay within one).
 """
 import numpy as np
 import pytest
@@ -42,6 +45,10 @@ def _hier(M, prob, **opts):
                        dofs_per_node=1, faces=prob.faces, **opts)
 
 
+def _close(k1, k0):
+    return abs(k1 - k0) <= max(1, k0 // 10)
+
+
 def _solve(H, prob, rtol=1e-8):
     b = torch.from_numpy(prob.b).cuda()
     x = torch.zeros_like(b)
@@ -54,6 +61,9 @@ CASES = {
     "kappa3d_33": lambda: pb.diffusion_macro(3, 33, 9, rhs="normal", rhs_seed=3),
     "poisson3d_33": lambda: pb.poisson_random(3, 33, 2),
     "kappa3d_17_free_faces": lambda: pb.diffusion_faces(3, 17, 0x15, rhs_seed=8, kappa_seed=12),
+    "kappa2d_65": lambda: pb.diffusion_macro(2, 65, 3, rhs="normal", rhs_seed=4),
+    "poisson2d_129": lambda: pb.poisson_random(2, 129, 1),
+    "kappa2d_65_free_faces": lambda: pb.diffusion_faces(2, 65, 0x5, rhs_seed=2, kappa_seed=7),
 }
 
 
@@ -65,7 +75,9 @@ def test_matrix_free_solve_matches_stored_and_oracle(M, name):
     M.mg_attach_q1_kappa(H.h, _kappa(prob))
     st1, k1, x1 = _solve(H, prob)
     assert st0 == st1 == M.MPCG_OK
-    assert abs(k1 - k0) <= 1, (k0, k1)
+    assert _close(k1, k0), (k0, k1)
+    if prob.dim == 3:
+        assert abs(k1 - k0) <= 1, (k0, k1)
     O = omg.Hierarchy(prob.dim, None, prob.stencil, prob.levels, nodes=prob.nodes, faces=prob.faces)
     tr = np.linalg.norm(prob.b - O.A[-1] @ x1) / np.linalg.norm(prob.b)
     assert tr <= 1e-8, tr
@@ -87,10 +99,15 @@ def test_attach_rejects_other_operators(M):
     flat = torch.ones_like(_kappa(prob))               # the Poisson operator, not this one
     with pytest.raises(M.MpcgError):
         M.mg_attach_q1_kappa(H.h, flat)
-    p2 = pb.diffusion_macro(2, 33, 3)                  # 2D: not provided
+    p2 = pb.diffusion_macro(2, 33, 3)                  # 2D: the Poisson kappa is not this operator's
     H2 = M.Hierarchy(torch.from_numpy(p2.stencil).cuda(), 2, 33, p2.levels, precision=M.MPCG_MIXED)
     with pytest.raises(M.MpcgError):
         M.mg_attach_q1_kappa(H2.h, torch.ones((32 * 32,), dtype=torch.float64, device="cuda"))
+    pe = pb.elasticity_cantilever(nodes=9)              # vector problems: not provided
+    He = M.Hierarchy(torch.from_numpy(pe.stencil).cuda(), 3, 9, pe.levels, dofs_per_node=3, faces=pe.faces,
+                     precision=M.MPCG_MIXED)
+    with pytest.raises(M.MpcgError):
+        M.mg_attach_q1_kappa(He.h, torch.ones((8 ** 3,), dtype=torch.float64, device="cuda"))
     # the rejected attach left the stored path in place
     st, k, x = _solve(H, prob)
     assert st == M.MPCG_OK
@@ -132,3 +149,46 @@ def test_full_size_poisson_129_matrix_free(M):
                     c = {0: 8.0 / 3, 1: 0.0, 2: -1.0 / 6, 3: -1.0 / 12}[nd] * h
                     acc += c * X[q]
         assert abs(axh[z, y, xx] - acc) <= 1e-12 * (1.0 + abs(acc)), (z, y, xx)
+
+
+def test_batched_matrix_free_matches_single_solves(M):
+    """A batch of 2D problems with their own kappa: with the coefficients
+    attached, every problem reaches the tolerance by its true residual in
+    about the iteration count of its stored-operator solve."""
+    probs = [pb.diffusion_macro(2, 65, 20 + i, rhs="normal", rhs_seed=30 + i) for i in range(3)]
+    sts = [torch.from_numpy(np.ascontiguousarray(p.stencil)).cuda() for p in probs]
+    B = M.BatchedHierarchy(sts, 2, 65, probs[0].levels, precision=M.MPCG_MIXED)
+    b = torch.from_numpy(np.stack([p.b for p in probs])).cuda()
+    x = torch.zeros_like(b)
+    st0, it0 = B.solve(b, x, rtol=1e-8, maxit=2000)
+    kap = torch.from_numpy(np.concatenate([p.kappa.reshape(-1) for p in probs])).cuda()
+    M.mg_attach_q1_kappa(B.h, kap)
+    x.zero_()
+    st1, it1 = B.solve(b, x, rtol=1e-8, maxit=2000)
+    assert st0 == st1 == M.MPCG_OK
+    assert all(_close(a, b) for a, b in zip(it1, it0)), (it0, it1)
+    for i, p in enumerate(probs):
+        O = omg.Hierarchy(2, None, p.stencil, p.levels, nodes=65)
+        xi = x[i].cpu().numpy()
+        assert np.linalg.norm(p.b - O.A[-1] @ xi) / np.linalg.norm(p.b) <= 1e-8
+    # one wrong coefficient field in the batch is refused
+    bad = kap.clone()
+    bad[64 * 64 + 5] *= 3.0
+    with pytest.raises(M.MpcgError):
+        M.mg_attach_q1_kappa(B.h, bad)
+
+
+def test_learned_column_with_matrix_free_operator(M):
+    """The learned column (ten columns) over the matrix-free fine operator:
+    the solve converges as over the stored operator."""
+    prob = pb.diffusion_macro(2, 65, 3, rhs="normal", rhs_seed=4)
+    H = _hier(M, prob)
+    rng = np.random.default_rng(0)
+    params = (0.05 * rng.standard_normal(M.mg_learned_num_params())).astype(np.float32)
+    M.mg_learned_attach(H.h, params)
+    st0, k0, _ = _solve(H, prob)
+    M.mg_attach_q1_kappa(H.h, _kappa(prob))
+    st1, k1, x1 = _solve(H, prob)
+    assert st0 == st1 == M.MPCG_OK and _close(k1, k0), (k0, k1)
+    O = omg.Hierarchy(2, None, prob.stencil, prob.levels, nodes=prob.nodes)
+    assert np.linalg.norm(prob.b - O.A[-1] @ x1) / np.linalg.norm(prob.b) <= 1e-8
