@@ -531,9 +531,10 @@ def bench_batched(args):
     for i in mine:
         by.setdefault(sizes[i], []).append(i)
     classes, bs, xs, ns = [], [], [], 0
-    streams = []
+    streams, kappas = [], []
     for nodes in sorted(by):
         ps = [pb.batch_problem(i, nodes) for i in by[nodes]]
+        kappas.append(torch.from_numpy(np.concatenate([p.kappa.reshape(-1) for p in ps])).cuda())
         strm = torch.cuda.Stream()
         streams.append(strm)
         classes.append(M.BatchedHierarchy([torch.from_numpy(p.stencil).cuda() for p in ps], 2, nodes, ps[0].levels,
@@ -556,6 +557,13 @@ def bench_batched(args):
     ms = multi.max_over_ranks(_timed(step, args.steps, max(1, args.warmup // 3), torch.cuda.current_stream()),
                               device="cuda")
     launches = sum(M.mg_last_launches(c.h) for c in classes)
+    its_stored = its
+    # the same batch with the matrix-free fine operators (each problem's kappa)
+    for c, k in zip(classes, kappas):
+        M.mg_attach_q1_kappa(c.h, k)
+    ms_mf = multi.max_over_ranks(_timed(step, args.steps, max(1, args.warmup // 3), torch.cuda.current_stream()),
+                                 device="cuda")
+    its_mf, its = its, its_stored
     ns_all = multi.sum_over_ranks(ns, device="cuda")
     if world > 1:
         dist.destroy_process_group()
@@ -570,7 +578,9 @@ def bench_batched(args):
                    "problems_per_side_rank0": {str(k): len(v) for k, v in sorted(by.items())},
                    "total_dofs": int(ns_all)},
         "max_iterations_per_side": {str(k): int(i.max()) for k, i in zip(sorted(by), its)},
-        "gpu_launches_per_step": launches}))
+        "gpu_launches_per_step": launches,
+        "matrix_free": {"value": ns_all / (ms_mf * 1e-3), "ms_per_step": ms_mf,
+                        "max_iterations_per_side": {str(k): int(i.max()) for k, i in zip(sorted(by), its_mf)}}}))
     return 0
 
 
@@ -797,10 +807,13 @@ def bench_learned(args):
     st = torch.from_numpy(prob.stencil).cuda()
     b = torch.from_numpy(prob.b).cuda()
     out = {}
-    for key in ("plain", "learned"):
+    kap = torch.from_numpy(np.ascontiguousarray(prob.kappa).reshape(-1)).cuda()
+    for key in ("plain", "learned", "plain_matrix_free", "learned_matrix_free"):
         H = M.Hierarchy(st, 2, 1025, prob.levels, m=M_WINDOW, precision=M.MPCG_MIXED)
-        if key == "learned":
+        if key.startswith("learned"):
             M.mg_learned_attach(H.h, params)
+        if key.endswith("matrix_free"):   # fine operator rebuilt from the element coefficients
+            M.mg_attach_q1_kappa(H.h, kap)
         x = torch.zeros_like(b)
         res = {}
 
@@ -811,7 +824,7 @@ def bench_learned(args):
         ms = _timed(step, args.steps, 1, torch.cuda.current_stream())
         out[key] = {"ms_per_solve": ms, "iterations": int(res["k"]), "status": int(res["st"]),
                     "dofs_per_s": prob.n / (ms * 1e-3)}
-        if key == "learned":   # live CUDA-event time of the fused tensor-core network kernel
+        if key == "learned":  # live CUDA-event time of the fused tensor-core network kernel
             x.zero_()
             _, _, _, trace = M.mpcg_solve_profiled(H.h, b, x, RTOL, 50000)
             net = [t for c, t in trace if c == "net"]
@@ -825,6 +838,7 @@ def bench_learned(args):
                                "f = 1, MPCG m=5, mixed precision, rtol 1e-8; network 2-16-16-16-1 trained on 4096 "
                                "pairs from 129^2 problems (kappa seeds 1000-1015)"},
         "plain": out["plain"], "learned": out["learned"],
+        "plain_matrix_free": out["plain_matrix_free"], "learned_matrix_free": out["learned_matrix_free"],
         "training": {"pairs": len(R), "epochs": args.epochs, "loss_first": float(loss[0]),
                      "loss_last": float(loss[-1]), "pair_generation_s": gen_s, "train_s": train_s}}))
     return 0
