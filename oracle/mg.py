@@ -52,6 +52,7 @@ class Hierarchy:
         flags = [((faces >> (2 * a)) & 1, (faces >> (2 * a + 1)) & 1) for a in range(dim)]
         lo = [f[0] for f in flags]
         hi = [f[1] for f in flags]
+        self.lo = lo                                 # global coordinate of unknown 0 per axis
         if nodes is None:
             if faces != 0x3F:
                 raise ValueError("give nodes when some faces are not Dirichlet")
