@@ -52,6 +52,7 @@ typedef enum {
 } mpcg_status;
 
 enum { MPCG_FORMAT_STENCIL = 0 };
+enum { MPCG_SMOOTHER_JACOBI = 0, MPCG_SMOOTHER_SSOR = 1 };
 enum { MPCG_FP64 = 0, MPCG_MIXED = 1 };
 
 /* Largest supported number of columns (grids, plus an appended column) and
@@ -103,7 +104,8 @@ typedef struct {
  * values: m = 5 (Section 3 uses the last 5 blocks), nu = 2, omega = 2/3,
  * pinv_tau = 1e-12, drop_delta = 1e-10, precision MPCG_FP64,
  * inner_rtol = 3e-3, inner pinv_tau = 1e-6, inner drop_delta = 1e-5,
- * use_graph = 1, sum_columns = 0.  The FP32
+ * use_graph = 1, sum_columns = 0, smoother = MPCG_SMOOTHER_JACOBI,
+ * ssor_omega = 1, vcycle = 0.  The FP32
  * inner solves converge in fewer total iterations when restarted often (the
  * FP64 refinement renews the residual and the search space), hence the
  * loose inner tolerance. */
@@ -124,6 +126,14 @@ typedef struct {
                             as a single search direction (additive MG as one
                             preconditioner; with m = 1 this is additive-MG PCG,
                             the paper's comparison method); 0: one column per grid */
+  int smoother;          /* MPCG_SMOOTHER_JACOBI (damped Jacobi, omega, Eq. 2) or
+                            MPCG_SMOOTHER_SSOR: nu multicoloured SSOR steps (relaxation
+                            ssor_omega) from zero per grid -- Section 3's smoother */
+  double ssor_omega;     /* SSOR relaxation, 0 < ssor_omega < 2 (default 1: symmetric
+                            Gauss-Seidel) */
+  int vcycle;            /* 1: the multiplicative V(nu, nu) cycle with SSOR as the single
+                            preconditioned direction (with m = 1: the MG(V)-PCG method
+                            Section 3 compares against); scalar problems, SSOR only */
   void* stream;          /* cudaStream_t */
 } mpcg_options;
 
@@ -204,8 +214,9 @@ mpcg_status mg_apply_operator(mg_hierarchy* h, int level, const double* X_dev,
 
 /*
  * Z = [z^0 | ... | z^J] (Section 2.2): the additive multigrid correction of
- * every grid for the fine residual r, coarse grid first.  Z_dev is a
- * column-major n x levels device array.
+ * every grid for the fine residual r, coarse grid first (with the options'
+ * smoother).  Z_dev is a column-major n x levels device array.  With
+ * vcycle = 1 it is one column instead, the V-cycle B_V r.
  */
 mpcg_status mg_corrections(mg_hierarchy* h, const double* r_dev, double* Z_dev);
 

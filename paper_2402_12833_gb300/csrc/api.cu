@@ -265,7 +265,7 @@ mpcg_status build_solver(mg_hierarchy* h, Solver<T>& S) {
   cudaStream_t s = h->stream;
   const int J = h->levels - 1;
   const GridDesc& gf = h->lev[J].g;
-  S.C = h->opt.sum_columns ? 1 : h->levels + (h->net_on ? 1 : 0);
+  S.C = (h->opt.sum_columns || h->opt.vcycle) ? 1 : h->levels + (h->net_on ? 1 : 0);
   S.m = h->opt.m;
   // the FP32 solver only runs the inner solves of the refinement, which
   // start from zero with r = b written by launch_start_inner
@@ -288,7 +288,7 @@ mpcg_status build_solver(mg_hierarchy* h, Solver<T>& S) {
       CKS(S.mem.get(&S.rlev[j], g.cp, s));
       CKS(S.mem.get(&S.zc[j], (size_t)(j + 1) * g.cp, s));
     }
-    if (h->opt.nu > 2 || (g.ncomp > 1 && h->opt.nu > 1)) {
+    if (h->opt.nu > 2 || (g.ncomp > 1 && h->opt.nu > 1) || h->opt.vcycle) {   // V-cycle: defects
       CKS(S.mem.get(&S.tmp[j], g.cp, s));
       CKS(S.mem.get(&S.tmp2[j], g.cp, s));
     }
@@ -321,6 +321,20 @@ mpcg_status ensure_hist(mg_hierarchy* h, Solver<T>& S, int maxit) {
 }
 
 // nu damped-Jacobi sweeps from zero on grid j: rr -> out.
+// k multicoloured SSOR steps on grid j for the right-hand side rr, in place
+// on x (a forward sweep over the 2^dim colours, then a backward one).
+template <typename T>
+void enqueue_ssor_steps(mg_hierarchy* h, int j, const T* rr, T* x, int k, const DevState* state, cudaStream_t s) {
+  const Level& L = h->lev[j];
+  const int K = 1 << L.g.dim;
+  for (int step = 0; step < k; ++step) {
+    for (int c = 0; c < K; ++c)
+      LAUNCH(h, K_JACOBI, s, launch_gs_colour<T>(L.g, st_of<T>(L), rr, x, c, h->opt.ssor_omega, state, s));
+    for (int c = K - 1; c >= 0; --c)
+      LAUNCH(h, K_JACOBI, s, launch_gs_colour<T>(L.g, st_of<T>(L), rr, x, c, h->opt.ssor_omega, state, s));
+  }
+}
+
 template <typename T>
 void enqueue_smooth(mg_hierarchy* h, Solver<T>& S, int j, const T* rr, T* out, const DevState* state,
                     cudaStream_t s) {
@@ -328,6 +342,11 @@ void enqueue_smooth(mg_hierarchy* h, Solver<T>& S, int j, const T* rr, T* out, c
   const T* st = st_of<T>(L);
   const T* di = dinv_of<T>(L);
   const int nu = h->opt.nu;
+  if (h->opt.smoother == MPCG_SMOOTHER_SSOR) {   // nu SSOR steps from zero
+    cudaMemsetAsync(out, 0, sizeof(T) * L.g.cp, s);
+    enqueue_ssor_steps<T>(h, j, rr, out, nu, state, s);
+    return;
+  }
   if (L.g.ncomp > 1) {
     // block Jacobi: s = D^-1 r, then nu - 1 sweeps t = r - A s, s += D^-1 t
     // (the update is pointwise, so it runs in place)
@@ -389,7 +408,7 @@ void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState*
   // go through one single-block launch: their restrictions, smoothings and
   // the coarse solve are latency-bound as separate launches
   int jt = -1;
-  if (h->lev[0].g.ncomp == 1 && h->opt.nu == 2)
+  if (h->lev[0].g.ncomp == 1 && h->opt.nu == 2 && h->opt.smoother == MPCG_SMOOTHER_JACOBI)
     for (int j = 0; j < J; ++j)
       if (h->lev[j].g.npts <= kTailPoints) jt = j;
   const T* rj = r;
@@ -433,6 +452,33 @@ void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState*
   cudaStreamWaitEvent(s, h->ev_fine, 0);
 }
 
+// The multiplicative V(nu, nu) cycle from zero for the right-hand side r,
+// into out (Section 3's MG(V) preconditioner): on every grid from the
+// finest down, nu SSOR steps, the defect and its restriction; the exact
+// coarse solve; on the way up the prolongated correction and nu SSOR
+// steps.  Grid j < J keeps its right-hand side in rlev[j], its
+// iterate in zc[j] and its defect in tmp[j].
+template <typename T>
+void enqueue_vcycle(mg_hierarchy* h, Solver<T>& S, const T* r, T* out, const DevState* state, cudaStream_t s) {
+  const int J = h->levels - 1;
+  const int nu = h->opt.nu;
+  auto rhs = [&](int j) -> const T* { return j == J ? r : S.rlev[j]; };
+  auto it = [&](int j) -> T* { return j == J ? out : S.zc[j]; };
+  for (int j = J; j >= 1; --j) {
+    const Level& L = h->lev[j];
+    cudaMemsetAsync(it(j), 0, sizeof(T) * L.g.cp, s);
+    enqueue_ssor_steps<T>(h, j, rhs(j), it(j), nu, state, s);
+    LAUNCH(h, K_RESIDUAL, s, launch_defect<T>(L.g, st_of<T>(L), rhs(j), it(j), S.tmp[j], state, s));
+    LAUNCH(h, K_RESTRICT, s, launch_restrict<T>(L.g, h->lev[j - 1].g, S.tmp[j], S.rlev[j - 1], state, s));
+  }
+  LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->A0inv, S.rlev[0], it(0), state, s));
+  for (int j = 1; j <= J; ++j) {
+    const Level& L = h->lev[j];
+    LAUNCH(h, K_PROLONG, s, launch_prolong_add<T>(h->lev[j - 1].g, L.g, it(j - 1), it(j), state, s));
+    enqueue_ssor_steps<T>(h, j, rhs(j), it(j), nu, state, s);
+  }
+}
+
 template <typename T>
 void enqueue_any(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
 
@@ -463,7 +509,9 @@ template <typename T>
 void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
   const Level& L = h->lev[h->levels - 1];
   const int C = S.C;
-  if (h->opt.sum_columns) {   // additive MG as one preconditioner: Z = B r (Eq. 3)
+  if (h->opt.vcycle) {   // the multiplicative MG(V) preconditioner as the single direction
+    enqueue_vcycle<T>(h, S, S.r, S.Z, S.state, s);
+  } else if (h->opt.sum_columns) {   // additive MG as one preconditioner: Z = B r (Eq. 3)
     enqueue_mg<T>(h, S, S.r, S.Zmg, S.state, s);
     LAUNCH(h, K_AUX, s, launch_sum_columns<T>(L.g, S.Zmg, h->levels, S.Z, S.state, s));
   } else {
@@ -684,13 +732,16 @@ mpcg_status mpcg_default_options(mpcg_options* opt) {
   opt->max_outer = 20;
   opt->use_graph = 1;
   opt->sum_columns = 0;
+  opt->smoother = MPCG_SMOOTHER_JACOBI;
+  opt->ssor_omega = 1.0;
+  opt->vcycle = 0;
   opt->stream = nullptr;
   return MPCG_OK;
 }
 
 int mg_num_levels(const mg_hierarchy* h) { return h ? h->levels : -1; }
 int mg_num_columns(const mg_hierarchy* h) {
-  return h ? (h->opt.sum_columns ? 1 : h->levels + (h->net_on ? 1 : 0)) : -1;
+  return h ? ((h->opt.sum_columns || h->opt.vcycle) ? 1 : h->levels + (h->net_on ? 1 : 0)) : -1;
 }
 long long mg_level_size(const mg_hierarchy* h, int level) {
   if (!h || level < 0 || level >= h->levels) return -1;
@@ -781,9 +832,21 @@ static mpcg_status setup_impl(const mg_operator* ops, int nb, int levels, const 
   else mpcg_default_options(&opt);
   if (opt.m < 1 || opt.m > MPCG_MAX_WINDOW || opt.nu < 1 || !(opt.omega > 0.0) || opt.pinv_tau < 0.0 ||
       opt.drop_delta < 0.0 || (opt.precision != MPCG_FP64 && opt.precision != MPCG_MIXED) || opt.max_outer < 1 ||
-      (opt.sum_columns != 0 && opt.sum_columns != 1)) {
-    set_err("invalid options (m in 1..%d, nu >= 1, omega > 0, tau/delta >= 0, max_outer >= 1, sum_columns 0/1)",
+      (opt.sum_columns != 0 && opt.sum_columns != 1) || (opt.vcycle != 0 && opt.vcycle != 1) ||
+      (opt.sum_columns && opt.vcycle) ||
+      (opt.smoother != MPCG_SMOOTHER_JACOBI && opt.smoother != MPCG_SMOOTHER_SSOR) ||
+      !(opt.ssor_omega > 0.0 && opt.ssor_omega < 2.0)) {
+    set_err("invalid options (m in 1..%d, nu >= 1, omega > 0, tau/delta >= 0, max_outer >= 1, sum_columns 0/1, "
+            "vcycle 0/1 and not with sum_columns, smoother JACOBI/SSOR, 0 < ssor_omega < 2)",
             MPCG_MAX_WINDOW);
+    return MPCG_ERR_ARG;
+  }
+  if ((opt.smoother == MPCG_SMOOTHER_SSOR || opt.vcycle) && ncomp != 1) {
+    set_err("the SSOR smoother and the V-cycle are provided for scalar problems");
+    return MPCG_ERR_ARG;
+  }
+  if (opt.vcycle && opt.smoother != MPCG_SMOOTHER_SSOR) {
+    set_err("the V-cycle smooths with SSOR (smoother = MPCG_SMOOTHER_SSOR)");
     return MPCG_ERR_ARG;
   }
   const long long n0 = make_grid_nodes(A->dim, (q >> (levels - 1)) + 1, faces, ncomp).n;
@@ -1322,10 +1385,15 @@ mpcg_status mg_corrections(mg_hierarchy* h, const double* r, double* Z) {
   cudaStream_t s = h->stream;
   Solver<double>& S = h->s64;
   const GridDesc& gf = h->lev[h->levels - 1].g;
-  double* Zc = h->opt.sum_columns ? S.Zmg : S.Z;   // the per-grid columns
   launch_pack<double, double>(gf, r, gf.n, S.r, 1, s);
-  enqueue_mg<double>(h, S, S.r, Zc, nullptr, s);
-  launch_unpack<double, double>(gf, Zc, Z, gf.n, h->levels, s);
+  if (h->opt.vcycle) {   // one column: the V-cycle B_V r
+    enqueue_vcycle<double>(h, S, S.r, S.Z, nullptr, s);
+    launch_unpack<double, double>(gf, S.Z, Z, gf.n, 1, s);
+  } else {
+    double* Zc = h->opt.sum_columns ? S.Zmg : S.Z;   // the per-grid columns
+    enqueue_mg<double>(h, S, S.r, Zc, nullptr, s);
+    launch_unpack<double, double>(gf, Zc, Z, gf.n, h->levels, s);
+  }
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
   return MPCG_OK;
@@ -1416,8 +1484,8 @@ mpcg_status mg_learned_attach(mg_hierarchy* h, const float* params, int nparams)
     set_err("params must hold mg_learned_num_params() = %d floats", kNetParams);
     return MPCG_ERR_ARG;
   }
-  if (h->levels + 1 > MPCG_MAX_COLS || h->opt.sum_columns) {
-    set_err("too many grids for an extra column, or the columns are summed into one");
+  if (h->levels + 1 > MPCG_MAX_COLS || h->opt.sum_columns || h->opt.vcycle) {
+    set_err("too many grids for an extra column, or the columns are summed into one / a V-cycle");
     return MPCG_ERR_ARG;
   }
   CK(cudaSetDevice(h->device));

@@ -84,6 +84,20 @@ void launch_coarse_tail(int jt, const GridDesc* g, const T* const* st, const T* 
 template <typename T>
 void launch_prolong_all(const GridDesc& gf, const T* const* coarse, const GridDesc* gcs, int J, T* Z,
                         const DevState* state, cudaStream_t s);
+// Multicoloured SSOR: one Gauss-Seidel update of the unknowns of `colour`
+// (bit a = parity of the global coordinate on axis a), in place on x, scalar
+// grids; d = b - A x; fine += P coarse (two grids).
+template <typename T>
+void launch_gs_colour(const GridDesc& g, const T* st, const T* b, T* x, int colour, double omega, const DevState* state,
+                      cudaStream_t s);
+template <typename T>
+void launch_defect(const GridDesc& g, const T* st, const T* b, const T* x, T* d, const DevState* state,
+                   cudaStream_t s);
+template <typename T>
+void launch_prolong_add(const GridDesc& gc, const GridDesc& gf, const T* coarse, T* fine, const DevState* state,
+                        cudaStream_t s);
+template <typename T>
+void launch_add_to(const GridDesc& g, const T* src, T* dst, const DevState* state, cudaStream_t s);
 // coarse stencil = P^T A P (FP64)
 void launch_galerkin(const GridDesc& gf, const GridDesc& gc, const double* stf, double* stc,
                      cudaStream_t s);

@@ -311,6 +311,103 @@ __global__ void __launch_bounds__(kBlock, 4) k_jacobi(GridDesc g, const T* __res
   if (active) Vec<T>::store(out + idx, o);
 }
 
+// Multicoloured SSOR (Section 3's smoother; the colouring is a reading):
+// one Gauss-Seidel update of every unknown of colour `colour` (parity of the
+// global node coordinates, bit a for axis a), in place:
+// x_i += omega (b_i - sum_s a_is x_(i+s)) / a_ii.  No two unknowns of a
+// colour are coupled by the stencil, so the colour updates at once.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBlock) k_gs_colour(GridDesc g, const T* __restrict__ st, const T* __restrict__ b,
+                                                      T* __restrict__ x, int colour, T omega, const DevState* state) {
+  const int pb = blockIdx.y;
+  if (state && state[pb].done) return;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= g.npts) return;
+  int px_, py_, pz_, a;
+  decode(g, t, px_, py_, pz_, a);
+  if (!interior(g, px_, py_, pz_)) return;
+  const int c = ((px_ + g.lox) & 1) | (((py_ + g.loy) & 1) << 1) | (DIM == 3 ? (((pz_ + g.loz) & 1) << 2) : 0);
+  if (c != colour) return;
+  constexpr int S = DIM == 3 ? 27 : 9;
+  const long long i = (long long)pb * g.len + g.G + t;
+  T acc = 0;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = DIM == 3 ? s / 9 - 1 : 0;
+    acc = fma(st[(long long)s * g.cp + i], x[i + dx + (long long)dy * g.px + (long long)dz * g.pxy], acc);
+  }
+  const T diag = st[(long long)(S / 2) * g.cp + i];
+  x[i] += omega * (b[i] - acc) / diag;
+}
+
+// d = b - A x over the padded box (zero rows at pads), no norms.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBlock) k_defect(GridDesc g, const T* __restrict__ st, const T* __restrict__ b,
+                                                   const T* __restrict__ x, T* __restrict__ d, const DevState* state) {
+  const int pb = blockIdx.y;
+  if (state && state[pb].done) return;
+  constexpr int W = Vec<T>::W;
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= g.npts / W) return;
+  const long long idx = (long long)pb * g.len + g.G + q * W;
+  T acc[1][W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) acc[0][w] = 0;
+  stencil_group<T, DIM, 1>(st, g.cp, x, idx, g.px, g.pxy, acc);
+  T bv[W], o[W];
+  Vec<T>::load_keep(b + idx, bv);
+#pragma unroll
+  for (int w = 0; w < W; ++w) o[w] = bv[w] - acc[0][w];
+  Vec<T>::store(d + idx, o);
+}
+
+// fine += P coarse (two grids, Section 2.1's interpolation): fine global
+// node g sits on coarse node g/2 (even g) or between (g-1)/2 and (g+1)/2.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBlock) k_prolong_add(GridDesc gc, GridDesc gf, const T* __restrict__ coarse,
+                                                        T* __restrict__ fine, const DevState* state) {
+  const int pb = blockIdx.y;
+  if (state && state[pb].done) return;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= gf.npts) return;
+  int x, y, z, a;
+  decode(gf, t, x, y, z, a);
+  if (!interior(gf, x, y, z)) return;
+  const int gx = x + gf.lox, gy = y + gf.loy, gz = DIM == 3 ? z + gf.loz : 0;
+  const T* cb = coarse + (long long)pb * gc.len + gc.G + (long long)a * gc.cstride;
+  T v = 0;
+#pragma unroll
+  for (int kz = 0; kz < (DIM == 3 ? 2 : 1); ++kz) {
+    if (DIM == 3 && kz == 1 && !(gz & 1)) continue;
+    const int cz = DIM == 3 ? (gz >> 1) + kz - gc.loz : 0;
+#pragma unroll
+    for (int ky = 0; ky < 2; ++ky) {
+      if (ky == 1 && !(gy & 1)) continue;
+      const int cy = (gy >> 1) + ky - gc.loy;
+#pragma unroll
+      for (int kx = 0; kx < 2; ++kx) {
+        if (kx == 1 && !(gx & 1)) continue;
+        const int cx = (gx >> 1) + kx - gc.lox;
+        const T w = (T)((gx & 1) ? 0.5 : 1.0) * (T)((gy & 1) ? 0.5 : 1.0) * (T)((DIM == 3 && (gz & 1)) ? 0.5 : 1.0);
+        v = fma(w, cb[cx + (long long)cy * gc.px + (DIM == 3 ? (long long)cz * gc.pxy : 0)], v);
+      }
+    }
+  }
+  fine[(long long)pb * gf.len + gf.G + t] += v;
+}
+
+// dst += src over the padded box.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_add_to(GridDesc g, const T* __restrict__ src, T* __restrict__ dst,
+                                                   const DevState* state) {
+  const int pb = blockIdx.y;
+  if (state && state[pb].done) return;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= g.npts) return;
+  const long long i = (long long)pb * g.len + g.G + t;
+  dst[i] += src[i];
+}
+
 // Composite prolongation P_J ... P_{j+1} of every coarse grid's correction
 // straight to the fine grid (Section 2.1 allows the composite transfers to be
 // formed explicitly): the nested Q1 spaces make it the multilinear
@@ -950,6 +1047,49 @@ template void launch_coarse_tail<double>(int, const GridDesc*, const double* con
 template void launch_coarse_tail<float>(int, const GridDesc*, const float* const*, const float* const*,
                                         float* const*, float* const*, const float*, const double*, const DevState*,
                                         cudaStream_t);
+
+template <typename T>
+void launch_gs_colour(const GridDesc& g, const T* st, const T* b, T* x, int colour, double omega, const DevState* state,
+                      cudaStream_t s) {
+  const dim3 grid(blocks_for(g.npts), g.nb);
+  if (g.dim == 3) k_gs_colour<T, 3><<<grid, kBlock, 0, s>>>(g, st, b, x, colour, (T)omega, state);
+  else k_gs_colour<T, 2><<<grid, kBlock, 0, s>>>(g, st, b, x, colour, (T)omega, state);
+}
+template void launch_gs_colour<double>(const GridDesc&, const double*, const double*, double*, int, double,
+                                       const DevState*, cudaStream_t);
+template void launch_gs_colour<float>(const GridDesc&, const float*, const float*, float*, int, double,
+                                      const DevState*, cudaStream_t);
+
+template <typename T>
+void launch_defect(const GridDesc& g, const T* st, const T* b, const T* x, T* d, const DevState* state,
+                   cudaStream_t s) {
+  const dim3 grid(blocks_for(g.npts / vw<T>()), g.nb);
+  if (g.dim == 3) k_defect<T, 3><<<grid, kBlock, 0, s>>>(g, st, b, x, d, state);
+  else k_defect<T, 2><<<grid, kBlock, 0, s>>>(g, st, b, x, d, state);
+}
+template void launch_defect<double>(const GridDesc&, const double*, const double*, const double*, double*,
+                                    const DevState*, cudaStream_t);
+template void launch_defect<float>(const GridDesc&, const float*, const float*, const float*, float*,
+                                   const DevState*, cudaStream_t);
+
+template <typename T>
+void launch_prolong_add(const GridDesc& gc, const GridDesc& gf, const T* coarse, T* fine, const DevState* state,
+                        cudaStream_t s) {
+  const dim3 grid(blocks_for(gf.npts), gf.nb);
+  if (gf.dim == 3) k_prolong_add<T, 3><<<grid, kBlock, 0, s>>>(gc, gf, coarse, fine, state);
+  else k_prolong_add<T, 2><<<grid, kBlock, 0, s>>>(gc, gf, coarse, fine, state);
+}
+template void launch_prolong_add<double>(const GridDesc&, const GridDesc&, const double*, double*, const DevState*,
+                                         cudaStream_t);
+template void launch_prolong_add<float>(const GridDesc&, const GridDesc&, const float*, float*, const DevState*,
+                                        cudaStream_t);
+
+template <typename T>
+void launch_add_to(const GridDesc& g, const T* src, T* dst, const DevState* state, cudaStream_t s) {
+  k_add_to<T><<<dim3(blocks_for(g.npts), g.nb), kBlock, 0, s>>>(g, src, dst, state);
+}
+template void launch_add_to<double>(const GridDesc&, const double*, double*, const DevState*, cudaStream_t);
+template void launch_add_to<float>(const GridDesc&, const float*, float*, const DevState*, cudaStream_t);
 
 template <typename T>
 void launch_prolong_all(const GridDesc& gf, const T* const* coarse, const GridDesc* gcs, int J, T* Z,

@@ -24,6 +24,8 @@ MPCG_ERR_BREAKDOWN = -4
 MPCG_ERR_TIMEOUT = -5
 MPCG_ERR_OOM = -6
 MPCG_FORMAT_STENCIL = 0
+MPCG_SMOOTHER_JACOBI = 0
+MPCG_SMOOTHER_SSOR = 1
 MPCG_FP64 = 0
 MPCG_MIXED = 1
 MPCG_MAX_COLS = 12
@@ -48,7 +50,8 @@ class mpcg_options(C.Structure):
     _fields_ = [("m", C.c_int), ("nu", C.c_int), ("omega", C.c_double), ("pinv_tau", C.c_double),
                 ("drop_delta", C.c_double), ("precision", C.c_int), ("inner_rtol", C.c_double),
                 ("inner_pinv_tau", C.c_double), ("inner_drop_delta", C.c_double), ("max_outer", C.c_int),
-                ("use_graph", C.c_int), ("sum_columns", C.c_int), ("stream", C.c_void_p)]
+                ("use_graph", C.c_int), ("sum_columns", C.c_int), ("smoother", C.c_int), ("ssor_omega", C.c_double),
+                ("vcycle", C.c_int), ("stream", C.c_void_p)]
 
 
 class mg_train_opts(C.Structure):
