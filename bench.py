@@ -721,11 +721,15 @@ def bench_example1(args):
     elements, 4 grids (20 x 20 coarsest), k_xx = 10^-n (n = 0..7), k_yy = 1,
     f = 1, zero Dirichlet data, FP64, rtol 1e-8: iterations and time of
     additive MG-MPCG (one column per grid, m = 5 and m = 1) and additive MG-PCG
-    (the summed correction B r as a single direction, m = 1), with the
-    oracle's iteration counts beside them."""
+    (the summed correction B r as a single direction, m = 1) with the damped
+    Jacobi smoother, and the paper's comparison with SSOR: additive MG-MPCG
+    (m = 5) and MG-PCG with 6 SSOR steps per grid, and PCG preconditioned by
+    the multiplicative V(3,3) cycle; the oracle's iteration counts beside them."""
     import torch
     from oracle import mg as omg
     from oracle import mpcg as ompcg
+    from oracle import pcg as opcg
+    from oracle import ssor as oss
     from paper_2402_12833_gb300 import build as _build
     from paper_2402_12833_gb300 import mpcg as M
     from paper_2402_12833_gb300 import problems as pb
@@ -739,7 +743,11 @@ def bench_example1(args):
         b = torch.from_numpy(prob.b).cuda()
         x = torch.zeros_like(b)
         row = {"kxx": kxx}
-        for key, opts in (("mpcg_m5", dict(m=5)), ("mpcg_m1", dict(m=1)), ("pcg", dict(m=1, sum_columns=1))):
+        ssor = dict(smoother=M.MPCG_SMOOTHER_SSOR)
+        series = (("mpcg_m5", dict(m=5)), ("mpcg_m1", dict(m=1)), ("pcg", dict(m=1, sum_columns=1)),
+                  ("ssor_mpcg_m5", dict(ssor, nu=6, m=5)), ("ssor_pcg", dict(ssor, nu=6, m=1, sum_columns=1)),
+                  ("v33_pcg", dict(ssor, nu=3, m=1, vcycle=1)))
+        for key, opts in series:
             H = M.Hierarchy(st, 2, prob.nodes, prob.levels, **opts)
             res = {}
 
@@ -751,15 +759,23 @@ def bench_example1(args):
             row[key] = {"iterations": int(res["k"]), "ms": ms, "status": int(res["st"])}
             H.close()
         O = omg.Hierarchy(2, prob.n1, prob.stencil, prob.levels)
+        A, Ss = O.A[-1], oss.level_smoothers(O)
         row["oracle_iterations"] = {
-            "mpcg_m5": ompcg.mpcg(O.A[-1], prob.b, O.mg_columns, m=5, rtol=RTOL, maxit=20000).iters,
-            "pcg": ompcg.mpcg(O.A[-1], prob.b, lambda r: O.additive_mg(r)[:, None], m=1, rtol=RTOL,
-                              maxit=20000).iters}
+            "mpcg_m5": ompcg.mpcg(A, prob.b, O.mg_columns, m=5, rtol=RTOL, maxit=20000).iters,
+            "pcg": ompcg.mpcg(A, prob.b, lambda r: O.additive_mg(r)[:, None], m=1, rtol=RTOL,
+                              maxit=20000).iters,
+            "ssor_mpcg_m5": ompcg.mpcg(A, prob.b, lambda r: oss.additive_columns(O, Ss, r, 6), m=5, rtol=RTOL,
+                                       maxit=20000).iters,
+            "ssor_pcg": opcg.pcg(A, prob.b, lambda r: oss.additive_columns(O, Ss, r, 6).sum(axis=1), rtol=RTOL,
+                                 maxit=20000)[1],
+            "v33_pcg": opcg.pcg(A, prob.b, lambda r: oss.vcycle(O, Ss, r, 3), rtol=RTOL, maxit=20000)[1]}
         rows.append(row)
     print(json.dumps({"metric": "iterations to 1e-8 rel. residual", "workload": "example1",
                       "config": {"workload": "Section 3 Example 1: (0,1)^2, 160x160 Q1 elements, 4 grids (20x20 "
-                                             "coarsest), K = diag(k_xx, 1), f = 1, zero Dirichlet, damped Jacobi "
-                                             "nu=2 w=2/3, FP64, rtol 1e-8"},
+                                             "coarsest), K = diag(k_xx, 1), f = 1, zero Dirichlet, FP64, rtol 1e-8; "
+                                             "mpcg_m5/mpcg_m1/pcg: damped Jacobi nu=2 w=2/3; ssor_*: 6 "
+                                             "multicoloured SSOR steps per grid (w=1); v33_pcg: V(3,3) SSOR "
+                                             "cycle, exact coarsest solve"},
                       "rows": rows}))
     return 0
 
