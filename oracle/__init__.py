@@ -13,4 +13,6 @@ Modules
   mg         - the additive MG level corrections (Eq. 2, Eq. 3) as columns
   mpcg       - Algorithm 1 with the truncated window, pseudo-inverse, drop rule
   pcg        - textbook additive-MG PCG, used only as an independent pin
+  ssor       - multicoloured SSOR and the multiplicative V-cycle (Section 3's comparison)
+  amg        - an algebraic hierarchy by smoothed aggregation (Section 2.1's agglomeration)
 """
