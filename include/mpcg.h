@@ -190,6 +190,80 @@ mpcg_status mpcg_solve(mg_hierarchy* h, const double* b, double* x, double rtol,
 mpcg_status mg_hierarchy_setup_batched(const mg_operator* ops, int nprob, int levels, const mpcg_options* opt,
                                        mg_hierarchy** out);
 int mg_num_problems(const mg_hierarchy* h);
+
+/*
+ * Algebraic hierarchies (Section 2.1: the nested spaces may come from
+ * agglomeration rather than nested meshes; Section 3, Example 2 builds them
+ * algebraically).  The grids are built from the fine matrix alone by
+ * smoothed aggregation (Vanek, Mandel and Brezina, 1996):
+ *   strength   j != i strongly influences i when -a_ij > 0 and
+ *              -a_ij >= theta max_{k != i}(-a_ik); i and j are coupled when
+ *              either influences the other (positive couplings are weak)
+ *   aggregates in index order, an unknown whose strong neighbours are all
+ *              free starts an aggregate with them; each remaining unknown
+ *              joins the aggregate of its first strong neighbour (ascending
+ *              column) placed that way; unknowns without strong neighbours
+ *              stay outside every aggregate
+ *   transfers  T[i, a] = 1/sqrt(|a|); P = (I - (w/rho) D^-1 A) T with rho =
+ *              max_i sum_j |a_ij| / a_ii; R = P^T; A_c = P^T A P
+ * until a grid has at most coarse_size unknowns, max_levels grids exist, or
+ * an aggregation does not reduce the count.  The setup runs on the host (C++,
+ * once per matrix); the solve is the same additive MG-MPCG as for stencil
+ * hierarchies, with damped Jacobi (nu sweeps from zero, Eq. 2) on every grid
+ * >= 1, the exact coarse solve (at most 1024 unknowns), and every operator
+ * and transfer applied by the device in sliced ELLPACK form.  Grid indices
+ * follow the paper: 0 is the coarsest, mg_num_levels() - 1 the input matrix.
+ * Single problems, scalar unknowns; the SSOR smoother, the V-cycle, the
+ * learned column and the matrix-free operator are not provided for them.
+ */
+typedef struct {
+  int n;                 /* rows = columns, >= 1 */
+  const int* rowptr;     /* n + 1 offsets into col/val, rowptr[0] = 0 (host) */
+  const int* col;        /* column of each entry, ascending within a row (host) */
+  const double* val;     /* value of each entry (host) */
+} mg_csr;
+
+typedef struct {
+  double theta;          /* strength threshold in [0, 1]; default 0.4 */
+  double w;              /* prolongator smoothing weight in [0, 2]; 0 = plain aggregation; default 4/3 */
+  int max_levels;        /* grids including the finest, 1..MPCG_MAX_COLS; default MPCG_MAX_COLS */
+  int coarse_size;       /* stop at <= this many unknowns, 1..1024; default 256 */
+} mg_amg_options;
+
+enum { MPCG_AMG_A = 0, MPCG_AMG_P = 1 };
+
+mpcg_status mg_amg_default_options(mg_amg_options* amg);
+
+/*
+ * Build an algebraic hierarchy for the symmetric positive definite matrix A
+ * (host CSR, read during the call only; the matrix must be square with
+ * ascending columns, positive diagonal entries and symmetric to 1e-12
+ * relative).  amg and opt may be NULL for the defaults; opt->smoother must
+ * be MPCG_SMOOTHER_JACOBI and opt->vcycle 0.  On success *out owns device
+ * memory until mg_hierarchy_destroy; mpcg_solve, mg_corrections,
+ * mg_apply_operator and mg_level_size work on it as on a stencil hierarchy
+ * (vectors of A.n unknowns in the matrix's order).
+ * Errors: MPCG_ERR_ARG (bad matrix or options, coarsest grid above 1024
+ * unknowns), MPCG_ERR_NOT_SPD (coarsest Cholesky failed), MPCG_ERR_OOM,
+ * MPCG_ERR_CUDA.
+ */
+mpcg_status mg_hierarchy_setup_algebraic(const mg_csr* A, const mg_amg_options* amg, const mpcg_options* opt,
+                                         mg_hierarchy** out);
+
+/*
+ * The built hierarchy, for inspection (host copies kept by the handle).
+ * mg_amg_aggregates: for grid level >= 1, agg[i] = the unknown of grid
+ * level - 1 (the aggregate) that unknown i of grid `level` belongs to, or -1;
+ * agg holds mg_level_size(h, level) ints.
+ * mg_amg_nnz: entries of A_level (which = MPCG_AMG_A) or of P_level (grid
+ * level - 1 -> level, which = MPCG_AMG_P, level >= 1); -1 on bad arguments.
+ * mg_amg_get: that matrix in CSR form into host arrays of rows + 1, nnz and
+ * nnz entries (rows = mg_level_size(h, level)).
+ * Errors: MPCG_ERR_ARG (not an algebraic hierarchy, bad level or pointer).
+ */
+mpcg_status mg_amg_aggregates(const mg_hierarchy* h, int level, int* agg);
+long long mg_amg_nnz(const mg_hierarchy* h, int level, int which);
+mpcg_status mg_amg_get(const mg_hierarchy* h, int level, int which, int* rowptr, int* col, double* val);
 /*
  * Problems of uneven size: one batched hierarchy per grid size (nclass of
  * them, preferably each with its own stream in its options), solved
@@ -222,7 +296,7 @@ mpcg_status mg_corrections(mg_hierarchy* h, const double* r_dev, double* Z_dev);
 
 /* Copy grid `level`'s Galerkin operator in the stencil format above into
  * planes_dev (3^dim * n_level doubles, device). */
-mpcg_status mg_get_operator(mg_hierarchy* h, int level, double* planes_dev);
+mpcg_status mg_get_operator(mg_hierarchy* h, int level, double* planes_dev);   /* stencil hierarchies */
 
 /*
  * Measurement support (not part of the method).  Kernel launches are grouped

@@ -17,8 +17,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT, "libmpcg.so")
-SOURCES = ["api.cu", "stencil.cu", "block.cu", "small.cu", "matfree.cu", "learned.cu", "learned_tc.cu", "batch.cu",
-           "noalloc.cu"]
+SOURCES = ["api.cu", "stencil.cu", "block.cu", "small.cu", "matfree.cu", "ell.cu", "learned.cu", "learned_tc.cu",
+           "batch.cu", "noalloc.cu", "amg_setup.cpp"]
+# host-only units: no fused multiply-add contraction, so the hierarchy built on
+# the host rounds the same way on every machine
+HOST_FLAGS = ["-Xcompiler", "-ffp-contract=off"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -44,10 +47,11 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(SRC, src)
-        o = os.path.join(OUT, src.replace(".cu", ".o"))
+        o = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            cmd = [nvcc(), *ARCH, *FLAGS, *(extra or []), "-c", s, "-o", o]
+            host = HOST_FLAGS if src.endswith(".cpp") else []
+            cmd = [nvcc(), *ARCH, *FLAGS, *host, *(extra or []), "-c", s, "-o", o]
             jobs.append(cmd)
     def run(cmd):
         if verbose:

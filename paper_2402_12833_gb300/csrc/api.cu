@@ -9,10 +9,12 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <type_traits>
 #include <vector>
 
+#include "amg.h"
 #include "kernels.cuh"
 
 using namespace mpcg;
@@ -45,6 +47,24 @@ void set_err(const char* fmt, ...) {
     if (s_ != MPCG_OK) return s_;              \
   } while (0)
 
+// A sparse matrix of an algebraic hierarchy in device memory (EllDev layout);
+// the FP32 values exist once the mixed-precision solver is built.
+struct EllLevel {
+  int rows = 0, cols = 0, nslices = 0;
+  int* sptr = nullptr;
+  int* col = nullptr;
+  double* v64 = nullptr;
+  float* v32 = nullptr;
+  long long nent = 0;   // stored entries, padding included
+};
+
+template <typename T>
+EllDev<T> ell_of(const EllLevel& E);
+template <>
+EllDev<double> ell_of<double>(const EllLevel& E) { return {E.rows, E.cols, E.nslices, E.sptr, E.col, E.v64}; }
+template <>
+EllDev<float> ell_of<float>(const EllLevel& E) { return {E.rows, E.cols, E.nslices, E.sptr, E.col, E.v32}; }
+
 struct Level {
   GridDesc g;
   int nplanes = 0;   // stencil planes: ncomp * 3^dim
@@ -55,6 +75,8 @@ struct Level {
   float* dinv32 = nullptr;
   float* kq32 = nullptr;         // fine grid: element coefficients in use (matrix-free FP32 operator), or null
   float* kq32_store = nullptr;   // their storage (kept across detach / attach)
+  // algebraic hierarchies: the grid's operator, P_j (grid j-1 -> j) and R_j = P_j^T
+  EllLevel eA, eP, eR;
 };
 
 struct Alloc {
@@ -242,6 +264,11 @@ struct mg_hierarchy {
   int* net_err = nullptr;      // set by the tensor-core inference kernel on a timed-out wait
   unsigned char* net_wtc = nullptr;   // weights packed for the tensor-core kernel
   Alloc net_mem;
+  // algebraic hierarchy (flat grids, ELL operators); host copies of its
+  // matrices by grid index: A[j], P[j] (j >= 1), aggregates of grid j (j >= 1)
+  bool algebraic = false;
+  std::vector<mpcg::amg::Csr> amgA, amgP;
+  std::vector<std::vector<int>> amgAgg;
 };
 
 namespace {
@@ -342,6 +369,25 @@ void enqueue_smooth(mg_hierarchy* h, Solver<T>& S, int j, const T* rr, T* out, c
   const T* st = st_of<T>(L);
   const T* di = dinv_of<T>(L);
   const int nu = h->opt.nu;
+  if (h->algebraic) {   // damped Jacobi with the grid's sparse operator
+    const EllDev<T> E = ell_of<T>(L.eA);
+    const long long G = L.g.G;
+    if (nu <= 2) {
+      LAUNCH(h, K_JACOBI, s, launch_ell_jacobi<T>(E, di + G, rr + G, nullptr, out + G, nu - 1, state, s));
+      return;
+    }
+    T* a = S.tmp[j];
+    T* b = S.tmp2[j];
+    LAUNCH(h, K_JACOBI, s, launch_ell_jacobi<T>(E, di + G, rr + G, nullptr, a + G, 1, state, s));
+    for (int k = 3; k <= nu; ++k) {
+      T* o = k == nu ? out : b;
+      LAUNCH(h, K_JACOBI, s, launch_ell_jacobi<T>(E, di + G, rr + G, a + G, o + G, 2, state, s));
+      T* t = a;
+      a = b;
+      b = t;
+    }
+    return;
+  }
   if (h->opt.smoother == MPCG_SMOOTHER_SSOR) {   // nu SSOR steps from zero
     cudaMemsetAsync(out, 0, sizeof(T) * L.g.cp, s);
     enqueue_ssor_steps<T>(h, j, rr, out, nu, state, s);
@@ -391,7 +437,14 @@ void enqueue_smooth(mg_hierarchy* h, Solver<T>& S, int j, const T* rr, T* out, c
 // solve and the prolongation chain.  Under graph capture the side streams
 // become parallel graph branches.
 template <typename T>
+void enqueue_mg_algebraic(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState* state, cudaStream_t s);
+
+template <typename T>
 void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState* state, cudaStream_t s) {
+  if (h->algebraic) {
+    enqueue_mg_algebraic<T>(h, S, r, Z, state, s);
+    return;
+  }
   const int J = h->levels - 1;
   if (J == 0) {
     LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->A0inv, r, Z, state, s));
@@ -452,6 +505,65 @@ void enqueue_mg(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState*
   cudaStreamWaitEvent(s, h->ev_fine, 0);
 }
 
+// The additive corrections on an algebraic hierarchy, with the branch
+// structure of the structured one: the fine smoothing and each coarse grid's
+// smoothing on side streams, the restriction chain R_j = P_j^T and the coarse
+// solve on the main stream.  The prolongation is a cascade: P_k lifts all k
+// columns that have reached grid k-1 (the corrections of grids 0 .. k-1) in
+// one block SpMM, so every P_k is read once per iteration; grid j's buffer
+// zc[j] holds columns 0 .. j, column j being its own smoothed correction.
+template <typename T>
+void enqueue_mg_algebraic(mg_hierarchy* h, Solver<T>& S, const T* r, T* Z, const DevState* state, cudaStream_t s) {
+  const int J = h->levels - 1;
+  if (J == 0) {
+    LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->A0inv, r, Z, state, s));
+    return;
+  }
+  cudaStream_t s2 = h->prof.on ? s : h->side[0];
+  cudaEventRecord(h->ev_fork, s);
+  cudaStreamWaitEvent(s2, h->ev_fork, 0);
+  enqueue_smooth<T>(h, S, J, r, Z + (size_t)J * h->lev[J].g.cp, state, s2);
+  cudaEventRecord(h->ev_fine, s2);
+  const T* rj = r;
+  for (int j = J; j >= 1; --j) {
+    const GridDesc& gf = h->lev[j].g;
+    const GridDesc& gc = h->lev[j - 1].g;
+    LAUNCH(h, K_RESTRICT, s,
+           launch_ell_spmm<T>(ell_of<T>(h->lev[j].eR), rj + gf.G, gf.cp, S.rlev[j - 1] + gc.G, gc.cp, 1, nullptr, 0,
+                              state, s));
+    rj = S.rlev[j - 1];
+    if (j - 1 >= 1) {
+      cudaStream_t s3 = h->prof.on ? s : h->side[j - 1];
+      cudaEventRecord(h->ev_r[j - 1], s);
+      cudaStreamWaitEvent(s3, h->ev_r[j - 1], 0);
+      enqueue_smooth<T>(h, S, j - 1, S.rlev[j - 1], S.zc[j - 1] + (size_t)(j - 1) * gc.cp, state, s3);
+      cudaEventRecord(h->ev_sm[j - 1], s3);
+    }
+  }
+  LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->A0inv, S.rlev[0], S.zc[0], state, s));
+  for (int k = 1; k <= J; ++k) {
+    if (k - 1 >= 1) cudaStreamWaitEvent(s, h->ev_sm[k - 1], 0);
+    const GridDesc& gc = h->lev[k - 1].g;
+    const GridDesc& gk = h->lev[k].g;
+    T* dst = k < J ? S.zc[k] : Z;
+    LAUNCH(h, K_PROLONG, s,
+           launch_ell_spmm<T>(ell_of<T>(h->lev[k].eP), S.zc[k - 1] + gc.G, gc.cp, dst + gk.G, gk.cp, k, nullptr, 0,
+                              state, s));
+  }
+  cudaStreamWaitEvent(s, h->ev_fine, 0);
+}
+
+// r = b - A x on the fine grid (stored stencil or sparse operator).
+template <typename T>
+void launch_fine_residual(mg_hierarchy* h, const T* b, const T* x, T* r, double* part, cudaStream_t s,
+                          const int* xnz) {
+  const Level& L = h->lev[h->levels - 1];
+  if (h->algebraic)
+    launch_ell_residual<T>(ell_of<T>(L.eA), b + L.g.G, x + L.g.G, r + L.g.G, part, stream_blocks(L.g), s, xnz);
+  else
+    launch_residual<T>(L.g, st_of<T>(L), b, x, r, part, s, xnz);
+}
+
 // The multiplicative V(nu, nu) cycle from zero for the right-hand side r,
 // into out (Section 3's MG(V) preconditioner): on every grid from the
 // finest down, nu SSOR steps, the defect and its restriction; the exact
@@ -489,8 +601,7 @@ void enqueue_prologue(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle 
   // a solve from a zero iterate has r = b, written by its start kernel
   // the FP64 iterate was packed with its nonzero flag (a zero x0 skips the stencil)
   const int* xnz = std::is_same<T, double>::value ? h->xnz : nullptr;
-  if (!S.zero_start)
-    LAUNCH(h, K_RESIDUAL, s, launch_residual<T>(L.g, st_of<T>(L), S.b, S.x, S.r, S.part_res, s, xnz));
+  if (!S.zero_start) LAUNCH(h, K_RESIDUAL, s, launch_fine_residual<T>(h, S.b, S.x, S.r, S.part_res, s, xnz));
   // a batch decides its loop condition from all problems (enqueue_any)
   LAUNCH(h, K_INIT, s, launch_init(S.state, h->nb, S.part_res, stream_blocks(L.g), S.res_hist, S.hist_cap, cond,
                                    use_cond && h->nb == 1, s));
@@ -523,8 +634,14 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
                                S.Z + (size_t)(C - 1) * L.g.len, h->net_err, s));
   }
   bool mf = false;
+  if (h->algebraic) {
+    LAUNCH(h, K_SPMM, s,
+           launch_ell_spmm<T>(ell_of<T>(L.eA), S.Z + L.g.G, L.g.cp, S.AZ + L.g.G, L.g.cp, C, S.part_zaz,
+                              spmm_blocks<T>(L.g, C), S.state, s));
+    mf = true;
+  }
   if constexpr (std::is_same<T, float>::value) {
-    if (L.kq32 && C <= 12) {   // fine operator rebuilt from the element coefficients
+    if (!mf && L.kq32 && C <= 12) {   // fine operator rebuilt from the element coefficients
       LAUNCH(h, K_SPMM, s,
              launch_spmm_mf(L.g, L.kq32, S.Z, S.AZ, C, spmm_blocks<T>(L.g, C), S.part_zaz, S.state, s));
       mf = true;
@@ -669,6 +786,16 @@ mpcg_status build_f32(mg_hierarchy* h) {
   cudaStream_t s = h->stream;
   for (int j = 0; j < h->levels; ++j) {
     Level& L = h->lev[j];
+    if (h->algebraic) {
+      for (EllLevel* E : {&L.eA, &L.eP, &L.eR}) {
+        if (!E->v64) continue;
+        CKS(h->mem.get(&E->v32, (size_t)E->nent, s));
+        launch_convert_f32(E->v64, E->v32, E->nent, s);
+      }
+      CKS(h->mem.get(&L.dinv32, (size_t)L.g.cp, s));
+      launch_convert_f32(L.dinv64, L.dinv32, L.g.cp, s);
+      continue;
+    }
     CKS(h->mem.get(&L.st32, (size_t)L.nplanes * L.g.cp, s));
     CKS(h->mem.get(&L.dinv32, (size_t)L.ndinv * L.g.cp, s));
     launch_convert_f32(L.st64, L.st32, (long long)L.nplanes * L.g.cp, s);
@@ -685,6 +812,82 @@ mpcg_status build_f32(mg_hierarchy* h) {
   CKS(h->mem.get(&h->outer, 1, s));
   CK(cudaGetLastError());
   h->have32 = true;
+  return MPCG_OK;
+}
+
+// Sliced ELLPACK (EllDev layout) of a host CSR matrix, uploaded to the device.
+mpcg_status upload_ell(mg_hierarchy* h, const mpcg::amg::Csr& M, EllLevel& E, cudaStream_t s) {
+  E.rows = M.rows;
+  E.cols = M.cols;
+  E.nslices = (M.rows + 31) / 32;
+  std::vector<int> sptr((size_t)E.nslices + 1, 0);
+  long long total = 0;
+  for (int sl = 0; sl < E.nslices; ++sl) {
+    int w = 0;
+    for (int r = 32 * sl; r < 32 * sl + 32 && r < M.rows; ++r) w = std::max(w, M.ptr[r + 1] - M.ptr[r]);
+    total += 32LL * w;
+    if (total >= (1LL << 31)) {
+      set_err("sparse matrix too large for 32-bit entry offsets");
+      return MPCG_ERR_ARG;
+    }
+    sptr[(size_t)sl + 1] = (int)total;
+  }
+  E.nent = total;
+  std::vector<int> col((size_t)total, 0);
+  std::vector<double> val((size_t)total, 0.0);
+  for (int sl = 0; sl < E.nslices; ++sl)
+    for (int r = 32 * sl; r < 32 * sl + 32 && r < M.rows; ++r)
+      for (int e = M.ptr[r]; e < M.ptr[r + 1]; ++e) {
+        const size_t k = (size_t)sptr[sl] + 32 * (size_t)(e - M.ptr[r]) + (size_t)(r - 32 * sl);
+        col[k] = M.col[e];
+        val[k] = M.val[e];
+      }
+  CKS(h->mem.get(&E.sptr, sptr.size(), s));
+  CKS(h->mem.get(&E.col, col.size(), s));
+  CKS(h->mem.get(&E.v64, val.size(), s));
+  if (cudaMemcpyAsync(E.sptr, sptr.data(), sizeof(int) * sptr.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(E.col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(E.v64, val.data(), sizeof(double) * val.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    set_err("upload of a sparse operator failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return MPCG_ERR_CUDA;
+  }
+  return MPCG_OK;
+}
+
+mpcg_status check_options(const mpcg_options& opt) {
+  if (opt.m < 1 || opt.m > MPCG_MAX_WINDOW || opt.nu < 1 || !(opt.omega > 0.0) || opt.pinv_tau < 0.0 ||
+      opt.drop_delta < 0.0 || (opt.precision != MPCG_FP64 && opt.precision != MPCG_MIXED) || opt.max_outer < 1 ||
+      (opt.sum_columns != 0 && opt.sum_columns != 1) || (opt.vcycle != 0 && opt.vcycle != 1) ||
+      (opt.sum_columns && opt.vcycle) ||
+      (opt.smoother != MPCG_SMOOTHER_JACOBI && opt.smoother != MPCG_SMOOTHER_SSOR) ||
+      !(opt.ssor_omega > 0.0 && opt.ssor_omega < 2.0)) {
+    set_err("invalid options (m in 1..%d, nu >= 1, omega > 0, tau/delta >= 0, max_outer >= 1, sum_columns 0/1, "
+            "vcycle 0/1 and not with sum_columns, smoother JACOBI/SSOR, 0 < ssor_omega < 2)",
+            MPCG_MAX_WINDOW);
+    return MPCG_ERR_ARG;
+  }
+  return MPCG_OK;
+}
+
+// Side streams of the MG branches, their fork/join events and the capture stream.
+mpcg_status create_streams(mg_hierarchy* h) {
+  bool ev_ok = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&h->ev_fine, cudaEventDisableTiming) == cudaSuccess &&
+               cudaStreamCreateWithFlags(&h->side[0], cudaStreamNonBlocking) == cudaSuccess;
+  for (int j = 1; j < h->levels && ev_ok; ++j)
+    ev_ok = cudaStreamCreateWithFlags(&h->side[j], cudaStreamNonBlocking) == cudaSuccess;
+  for (int j = 0; j < kMaxLevels && ev_ok; ++j)
+    ev_ok = cudaEventCreateWithFlags(&h->ev_r[j], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&h->ev_sm[j], cudaEventDisableTiming) == cudaSuccess;
+  if (!ev_ok) {
+    set_err("creating streams/events failed");
+    return MPCG_ERR_CUDA;
+  }
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    set_err("cudaStreamCreateWithFlags failed");
+    return MPCG_ERR_CUDA;
+  }
   return MPCG_OK;
 }
 
@@ -830,17 +1033,7 @@ static mpcg_status setup_impl(const mg_operator* ops, int nb, int levels, const 
   mpcg_options opt;
   if (opt_in) opt = *opt_in;
   else mpcg_default_options(&opt);
-  if (opt.m < 1 || opt.m > MPCG_MAX_WINDOW || opt.nu < 1 || !(opt.omega > 0.0) || opt.pinv_tau < 0.0 ||
-      opt.drop_delta < 0.0 || (opt.precision != MPCG_FP64 && opt.precision != MPCG_MIXED) || opt.max_outer < 1 ||
-      (opt.sum_columns != 0 && opt.sum_columns != 1) || (opt.vcycle != 0 && opt.vcycle != 1) ||
-      (opt.sum_columns && opt.vcycle) ||
-      (opt.smoother != MPCG_SMOOTHER_JACOBI && opt.smoother != MPCG_SMOOTHER_SSOR) ||
-      !(opt.ssor_omega > 0.0 && opt.ssor_omega < 2.0)) {
-    set_err("invalid options (m in 1..%d, nu >= 1, omega > 0, tau/delta >= 0, max_outer >= 1, sum_columns 0/1, "
-            "vcycle 0/1 and not with sum_columns, smoother JACOBI/SSOR, 0 < ssor_omega < 2)",
-            MPCG_MAX_WINDOW);
-    return MPCG_ERR_ARG;
-  }
+  CKS(check_options(opt));
   if ((opt.smoother == MPCG_SMOOTHER_SSOR || opt.vcycle) && ncomp != 1) {
     set_err("the SSOR smoother and the V-cycle are provided for scalar problems");
     return MPCG_ERR_ARG;
@@ -868,22 +1061,7 @@ static mpcg_status setup_impl(const mg_operator* ops, int nb, int levels, const 
     mg_hierarchy_destroy(h);
     return s;
   };
-  bool ev_ok = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
-               cudaEventCreateWithFlags(&h->ev_fine, cudaEventDisableTiming) == cudaSuccess &&
-               cudaStreamCreateWithFlags(&h->side[0], cudaStreamNonBlocking) == cudaSuccess;
-  for (int j = 1; j < levels && ev_ok; ++j)
-    ev_ok = cudaStreamCreateWithFlags(&h->side[j], cudaStreamNonBlocking) == cudaSuccess;
-  for (int j = 0; j < kMaxLevels && ev_ok; ++j)
-    ev_ok = cudaEventCreateWithFlags(&h->ev_r[j], cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&h->ev_sm[j], cudaEventDisableTiming) == cudaSuccess;
-  if (!ev_ok) {
-    set_err("creating streams/events failed");
-    return fail(MPCG_ERR_CUDA);
-  }
-  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
-    set_err("cudaStreamCreateWithFlags failed");
-    return fail(MPCG_ERR_CUDA);
-  }
+  if ((st = create_streams(h)) != MPCG_OK) return fail(st);
   const int S = (A->dim == 3 ? 27 : 9) * ncomp;
   cudaStream_t s = h->stream;
   for (int j = 0; j < levels; ++j) {
@@ -959,6 +1137,205 @@ mpcg_status mg_hierarchy_setup_batched(const mg_operator* ops, int nprob, int le
 }
 
 int mg_num_problems(const mg_hierarchy* h) { return h ? h->nb : -1; }
+
+mpcg_status mg_amg_default_options(mg_amg_options* amg) {
+  if (!amg) {
+    set_err("NULL options");
+    return MPCG_ERR_ARG;
+  }
+  amg->theta = 0.4;
+  amg->w = 4.0 / 3.0;
+  amg->max_levels = MPCG_MAX_COLS;
+  amg->coarse_size = 256;
+  return MPCG_OK;
+}
+
+mpcg_status mg_hierarchy_setup_algebraic(const mg_csr* A, const mg_amg_options* amg_in, const mpcg_options* opt_in,
+                                         mg_hierarchy** out) {
+  g_err.clear();
+  if (!out) {
+    set_err("out pointer is NULL");
+    return MPCG_ERR_ARG;
+  }
+  *out = nullptr;
+  if (!A) {
+    set_err("matrix is NULL");
+    return MPCG_ERR_ARG;
+  }
+  mg_amg_options amg;
+  if (amg_in) amg = *amg_in;
+  else mg_amg_default_options(&amg);
+  if (!(amg.theta >= 0.0 && amg.theta <= 1.0) || !(amg.w >= 0.0 && amg.w <= 2.0) || amg.max_levels < 1 ||
+      amg.max_levels > MPCG_MAX_COLS || amg.max_levels > kMaxLevels || amg.coarse_size < 1 ||
+      amg.coarse_size > 1024) {
+    set_err("invalid algebraic options (theta in [0, 1], w in [0, 2], max_levels 1..%d, coarse_size 1..1024)",
+            MPCG_MAX_COLS);
+    return MPCG_ERR_ARG;
+  }
+  mpcg_options opt;
+  if (opt_in) opt = *opt_in;
+  else mpcg_default_options(&opt);
+  CKS(check_options(opt));
+  if (opt.smoother != MPCG_SMOOTHER_JACOBI || opt.vcycle) {
+    set_err("algebraic hierarchies smooth with damped Jacobi (no SSOR, no V-cycle)");
+    return MPCG_ERR_ARG;
+  }
+  std::string err;
+  if (!mpcg::amg::check_input(A->n, A->rowptr, A->col, A->val, err)) {
+    set_err("%s", err.c_str());
+    return MPCG_ERR_ARG;
+  }
+  mpcg::amg::Csr fine;
+  fine.rows = fine.cols = A->n;
+  const long long nnz = A->rowptr[A->n];
+  fine.ptr.assign(A->rowptr, A->rowptr + A->n + 1);
+  fine.col.assign(A->col, A->col + nnz);
+  fine.val.assign(A->val, A->val + nnz);
+  mpcg::amg::Levels H;
+  mpcg::amg::build(fine, {amg.theta, amg.w, amg.max_levels, amg.coarse_size}, H);
+  const int levels = (int)H.A.size();
+  const int n0 = H.A.back().rows;
+  if (n0 > 1024) {
+    set_err("coarsest grid has %d unknowns (> 1024): raise max_levels or lower theta", n0);
+    return MPCG_ERR_ARG;
+  }
+  mg_hierarchy* h = new mg_hierarchy();
+  cudaGetDevice(&h->device);
+  h->algebraic = true;
+  h->dim = 0;
+  h->levels = levels;
+  h->nb = 1;
+  h->nodes = 0;
+  h->opt = opt;
+  h->stream = (cudaStream_t)opt.stream;
+  h->n0 = n0;
+  mpcg_status st = MPCG_OK;
+  auto fail = [&](mpcg_status e) {
+    mg_hierarchy_destroy(h);
+    return e;
+  };
+  if ((st = create_streams(h)) != MPCG_OK) return fail(st);
+  {
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device) == cudaSuccess) set_sm_count(nsm);
+  }
+  cudaStream_t s = h->stream;
+  // grid j of the paper's numbering is entry levels - 1 - j of the fine-first lists
+  h->amgA.resize(levels);
+  h->amgP.resize(levels);
+  h->amgAgg.resize(levels);
+  for (int j = 0; j < levels; ++j) {
+    const int l = levels - 1 - j;
+    h->amgA[j] = std::move(H.A[l]);
+    if (j >= 1) {
+      h->amgP[j] = std::move(H.P[l]);
+      h->amgAgg[j] = std::move(H.agg[l]);
+    }
+  }
+  for (int j = 0; j < levels; ++j) {
+    Level& L = h->lev[j];
+    const mpcg::amg::Csr& Aj = h->amgA[j];
+    L.g = make_grid_flat(Aj.rows, 1);
+    L.nplanes = 0;
+    L.ndinv = 1;
+    if ((st = upload_ell(h, Aj, L.eA, s)) != MPCG_OK) return fail(st);
+    if (j >= 1) {
+      mpcg::amg::Csr Rt;
+      mpcg::amg::transpose(h->amgP[j], Rt);
+      if ((st = upload_ell(h, h->amgP[j], L.eP, s)) != MPCG_OK) return fail(st);
+      if ((st = upload_ell(h, Rt, L.eR, s)) != MPCG_OK) return fail(st);
+    }
+    // damped inverse diagonal omega / a_ii in the flat padded layout
+    std::vector<double> dv((size_t)L.g.len, 0.0);
+    for (int i = 0; i < Aj.rows; ++i)
+      for (int e = Aj.ptr[i]; e < Aj.ptr[i + 1]; ++e)
+        if (Aj.col[e] == i) dv[(size_t)L.g.G + i] = opt.omega / Aj.val[e];
+    if ((st = h->mem.get(&L.dinv64, (size_t)L.g.cp, s)) != MPCG_OK) return fail(st);
+    if (cudaMemcpyAsync(L.dinv64, dv.data(), sizeof(double) * dv.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      set_err("upload of the inverse diagonal failed: %s", cudaGetErrorString(cudaGetLastError()));
+      return fail(MPCG_ERR_CUDA);
+    }
+  }
+  // dense coarsest operator -> Cholesky -> inverse (as for stencil hierarchies)
+  const size_t nn = (size_t)n0 * n0;
+  if ((st = h->mem.get(&h->L0, nn, s)) != MPCG_OK) return fail(st);
+  if ((st = h->mem.get(&h->info, 1, s)) != MPCG_OK) return fail(st);
+  if ((st = h->mem.get(&h->xnz, 1, s)) != MPCG_OK) return fail(st);
+  if ((st = h->mem.get(&h->rdiag0, (size_t)n0, s)) != MPCG_OK) return fail(st);
+  {
+    const mpcg::amg::Csr& A0 = h->amgA[0];
+    std::vector<double> dense(nn, 0.0);
+    for (int i = 0; i < n0; ++i)
+      for (int e = A0.ptr[i]; e < A0.ptr[i + 1]; ++e) dense[(size_t)i * n0 + A0.col[e]] = A0.val[e];
+    if (cudaMemcpyAsync(h->L0, dense.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      set_err("upload of the coarsest operator failed");
+      return fail(MPCG_ERR_CUDA);
+    }
+    launch_cholesky(h->L0, h->rdiag0, n0, h->info, s);
+    int info = 0;
+    if (cudaMemcpyAsync(&info, h->info, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      set_err("setup kernels failed: %s", cudaGetErrorString(cudaGetLastError()));
+      return fail(MPCG_ERR_CUDA);
+    }
+    if (info != 0) {
+      set_err("coarsest operator is not positive definite (Cholesky pivot %d)", info);
+      return fail(MPCG_ERR_NOT_SPD);
+    }
+    double* X = nullptr;
+    if ((st = h->mem.get(&h->A0inv, nn, s)) != MPCG_OK) return fail(st);
+    if ((st = h->mem.get(&X, nn, s)) != MPCG_OK) return fail(st);
+    launch_coarse_inverse(h->L0, h->rdiag0, X, h->A0inv, n0, s);
+  }
+  if ((st = build_solver<double>(h, h->s64)) != MPCG_OK) return fail(st);
+  if (opt.precision == MPCG_MIXED) {
+    if ((st = build_f32(h)) != MPCG_OK) return fail(st);
+    if ((st = build_solver<float>(h, h->s32)) != MPCG_OK) return fail(st);
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    set_err("setup failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return fail(MPCG_ERR_CUDA);
+  }
+  *out = h;
+  return MPCG_OK;
+}
+
+static const mpcg::amg::Csr* amg_matrix(const mg_hierarchy* h, int level, int which) {
+  if (!h || !h->algebraic || level < 0 || level >= h->levels) return nullptr;
+  if (which == MPCG_AMG_A) return &h->amgA[level];
+  if (which == MPCG_AMG_P && level >= 1) return &h->amgP[level];
+  return nullptr;
+}
+
+mpcg_status mg_amg_aggregates(const mg_hierarchy* h, int level, int* agg) {
+  g_err.clear();
+  if (!h || !h->algebraic || level < 1 || level >= h->levels || !agg) {
+    set_err("need an algebraic hierarchy, a grid level >= 1 and an output array");
+    return MPCG_ERR_ARG;
+  }
+  const std::vector<int>& a = h->amgAgg[level];
+  std::copy(a.begin(), a.end(), agg);
+  return MPCG_OK;
+}
+
+long long mg_amg_nnz(const mg_hierarchy* h, int level, int which) {
+  const mpcg::amg::Csr* M = amg_matrix(h, level, which);
+  return M ? M->nnz() : -1;
+}
+
+mpcg_status mg_amg_get(const mg_hierarchy* h, int level, int which, int* rowptr, int* col, double* val) {
+  g_err.clear();
+  const mpcg::amg::Csr* M = amg_matrix(h, level, which);
+  if (!M || !rowptr || !col || !val) {
+    set_err("need an algebraic hierarchy, a valid level/matrix and output arrays");
+    return MPCG_ERR_ARG;
+  }
+  std::copy(M->ptr.begin(), M->ptr.end(), rowptr);
+  std::copy(M->col.begin(), M->col.end(), col);
+  std::copy(M->val.begin(), M->val.end(), val);
+  return MPCG_OK;
+}
 
 static mpcg_status solve_fp64(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, int* iters_out,
                               double* res_hist, double* alpha_hist) {
@@ -1062,7 +1439,7 @@ static bool build_mixed_graph(mg_hierarchy* h, double rtol, int maxit) {
   if (ok) {
     h->mg_head = 0;
     h->prof.target = &h->mg_head;
-    LAUNCH(h, K_RESIDUAL, cs, launch_residual<double>(gf, L.st64, h->b64, h->x64, h->r64, h->part_mix, cs, h->xnz));
+    LAUNCH(h, K_RESIDUAL, cs, launch_fine_residual<double>(h, h->b64, h->x64, h->r64, h->part_mix, cs, h->xnz));
     LAUNCH(h, K_AUX, cs, launch_sum_partials(h->part_mix, nb, 2, stream_blocks(gf), h->nrm, cs));
     LAUNCH(h, K_AUX, cs, launch_outer_check(h->mix, h->active, nb, h->nrm, rtol, maxit, h->opt.max_outer, h->outer,
                                             S.state, h->opt.inner_rtol, S.m, S.C, h->opt.inner_drop_delta,
@@ -1186,7 +1563,7 @@ static mpcg_status solve_mixed(mg_hierarchy* h, const double* b, double* x, doub
   std::vector<int> total(nb, 0), nhist(nb, 0), status(nb, 0), act(nb, 1);
   std::vector<double> nrm(2 * (size_t)nb), inner(maxit + 1);
   for (int outer = 0; outer <= h->opt.max_outer; ++outer) {
-    LAUNCH(h, K_RESIDUAL, s, launch_residual<double>(gf, L.st64, h->b64, h->x64, h->r64, h->part_mix, s, h->xnz));
+    LAUNCH(h, K_RESIDUAL, s, launch_fine_residual<double>(h, h->b64, h->x64, h->r64, h->part_mix, s, h->xnz));
     LAUNCH(h, K_AUX, s, launch_sum_partials(h->part_mix, nb, 2, stream_blocks(gf), h->nrm, s));
     CK(cudaMemcpyAsync(nrm.data(), h->nrm, 2 * sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1363,7 +1740,11 @@ mpcg_status mg_apply_operator(mg_hierarchy* h, int level, const double* X, doubl
   for (int c0 = 0; c0 < ncols; c0 += chunk) {
     const int nc = ncols - c0 < chunk ? ncols - c0 : chunk;
     launch_pack<double, double>(L.g, X + (size_t)c0 * L.g.n, L.g.n, xp, nc, s);
-    launch_spmm<double>(L.g, L.st64, xp, yp, nc, nullptr, nullptr, s);
+    if (h->algebraic)
+      launch_ell_spmm<double>(ell_of<double>(L.eA), xp + L.g.G, L.g.len, yp + L.g.G, L.g.len, nc, nullptr, 0, nullptr,
+                              s);
+    else
+      launch_spmm<double>(L.g, L.st64, xp, yp, nc, nullptr, nullptr, s);
     launch_unpack<double, double>(L.g, yp, Y + (size_t)c0 * L.g.n, L.g.n, nc, s);
   }
   cudaError_t e = cudaStreamSynchronize(s);
@@ -1404,6 +1785,10 @@ mpcg_status mg_get_operator(mg_hierarchy* h, int level, double* planes) {
   CKS(check_single(h));
   if (level < 0 || level >= h->levels || !planes) {
     set_err("bad level or pointer");
+    return MPCG_ERR_ARG;
+  }
+  if (h->algebraic) {
+    set_err("an algebraic hierarchy has no stencil planes (mg_amg_get returns its matrices)");
     return MPCG_ERR_ARG;
   }
   CK(cudaSetDevice(h->device));
@@ -1523,8 +1908,8 @@ mpcg_status mg_attach_q1_kappa(mg_hierarchy* h, const double* kappa_dev) {
   g_err.clear();
   CKS(check_h(h));
   Level& L = h->lev[h->levels - 1];
-  if (!kappa_dev || L.g.ncomp != 1) {
-    set_err("mg_attach_q1_kappa: scalar hierarchies and a device kappa array only");
+  if (!kappa_dev || L.g.ncomp != 1 || h->algebraic) {
+    set_err("mg_attach_q1_kappa: scalar stencil hierarchies and a device kappa array only");
     return MPCG_ERR_ARG;
   }
   CK(cudaSetDevice(h->device));

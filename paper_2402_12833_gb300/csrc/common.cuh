@@ -129,6 +129,53 @@ inline GridDesc make_grid_nodes(int dim, int nodes, unsigned faces, int ncomp, i
   return g;
 }
 
+// Unstructured ("flat") grid of n unknowns for an algebraic hierarchy:
+// unknown i lives at G + i of a box of npts = n rounded up to 32 entries,
+// the tail of the box and the guards being zero, so the block kernels (which
+// only read G, npts, len, cp and nb) run on it unchanged.  It is described as
+// one row (nx = n, ny = nz = 1, dim = 1) so that padded_index() maps i to G + i.
+inline GridDesc make_grid_flat(long long n, int nb = 1) {
+  GridDesc g;
+  g.nb = nb;
+  g.dim = 1;
+  g.ncomp = 1;
+  g.nx = (int)n;
+  g.ny = 1;
+  g.nz = 1;
+  g.lox = g.loy = g.loz = 0;
+  g.px = (int)((n + 31) / 32 * 32);
+  g.py = 1;
+  g.pz = 1;
+  g.pxy = g.px;
+  g.cstride = g.px;
+  g.dvx = make_fastdiv(g.px);
+  g.dvy = make_fastdiv(1);
+  g.dvz = make_fastdiv(1);
+  g.n1 = g.nx;
+  g.p = g.px;
+  g.lp = -1;
+  g.G = 32;
+  g.npts = g.px;
+  g.len = (2 * g.G + g.npts + 31) / 32 * 32;
+  g.n = n;
+  g.cp = (long long)nb * g.len;
+  return g;
+}
+
+// A sparse matrix of an algebraic hierarchy on the device, in sliced
+// ELLPACK form with slices of 32 rows (one warp): slice s holds
+// w_s = (sptr[s+1] - sptr[s]) / 32 entries per row, stored slot-major
+// (entry k of row 32 s + l at sptr[s] + 32 k + l) so that a warp reads each
+// slot of its 32 rows in one coalesced load.  Rows shorter than w_s, and the
+// rows past `rows` in the last slice, are padded with column 0 and value 0.
+template <typename T>
+struct EllDev {
+  int rows, cols, nslices;
+  const int* sptr;
+  const int* col;
+  const T* val;
+};
+
 // All-Dirichlet scalar grid with n1 unknowns per side.
 inline GridDesc make_grid(int dim, int n1, int nb = 1) { return make_grid_nodes(dim, n1 + 2, 0x3Fu, 1, nb); }
 

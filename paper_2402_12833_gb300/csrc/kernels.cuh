@@ -29,6 +29,22 @@ inline int grid_for(long long work, int cap) {
   return (int)(b < cap ? b : cap);
 }
 
+// ---- ell.cu (algebraic hierarchies; vectors offset by G) -----------------
+// Y[:, c] = A X[:, c], c < C <= 12 (column pitches ldx, ldy); zaz (may be
+// null) receives per-block partials of X_c^T Y_c, value-major with stride
+// nblocks.  nblocks <= 0: one thread per row.
+template <typename T>
+void launch_ell_spmm(const EllDev<T>& A, const T* X, long long ldx, T* Y, long long ldy, int C, double* zaz,
+                     int nblocks, const DevState* state, cudaStream_t s);
+// r = b - A x, partials [|r|^2, |b|^2] over nblocks blocks; xnz as launch_residual
+template <typename T>
+void launch_ell_residual(const EllDev<T>& A, const T* b, const T* x, T* r, double* part, int nblocks,
+                         cudaStream_t s, const int* xnz = nullptr);
+// damped Jacobi (dinv = omega / a_ii), modes as launch_jacobi
+template <typename T>
+void launch_ell_jacobi(const EllDev<T>& A, const T* dinv, const T* g, const T* sin, T* out, int mode,
+                       const DevState* state, cudaStream_t s);
+
 // ---- stencil.cu ----------------------------------------------------------
 // compact interior <-> padded layout (ncols columns; compact leading dim ld)
 template <typename TI, typename TO>

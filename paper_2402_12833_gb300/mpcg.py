@@ -30,6 +30,8 @@ MPCG_FP64 = 0
 MPCG_MIXED = 1
 MPCG_MAX_COLS = 12
 MPCG_MAX_WINDOW = 16
+MPCG_AMG_A = 0
+MPCG_AMG_P = 1
 
 
 class MpcgError(RuntimeError):
@@ -52,6 +54,14 @@ class mpcg_options(C.Structure):
                 ("inner_pinv_tau", C.c_double), ("inner_drop_delta", C.c_double), ("max_outer", C.c_int),
                 ("use_graph", C.c_int), ("sum_columns", C.c_int), ("smoother", C.c_int), ("ssor_omega", C.c_double),
                 ("vcycle", C.c_int), ("stream", C.c_void_p)]
+
+
+class mg_csr(C.Structure):
+    _fields_ = [("n", C.c_int), ("rowptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class mg_amg_options(C.Structure):
+    _fields_ = [("theta", C.c_double), ("w", C.c_double), ("max_levels", C.c_int), ("coarse_size", C.c_int)]
 
 
 class mg_train_opts(C.Structure):
@@ -85,6 +95,12 @@ _SIGS = {
     "mg_hierarchy_setup_batched": (C.c_int, [C.POINTER(mg_operator), C.c_int, C.c_int, C.POINTER(mpcg_options),
                                              C.POINTER(C.c_void_p)]),
     "mg_num_problems": (C.c_int, [C.c_void_p]),
+    "mg_amg_default_options": (C.c_int, [C.POINTER(mg_amg_options)]),
+    "mg_hierarchy_setup_algebraic": (C.c_int, [C.POINTER(mg_csr), C.POINTER(mg_amg_options),
+                                               C.POINTER(mpcg_options), C.POINTER(C.c_void_p)]),
+    "mg_amg_aggregates": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "mg_amg_nnz": (C.c_longlong, [C.c_void_p, C.c_int, C.c_int]),
+    "mg_amg_get": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mpcg_solve_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p),
                                      C.POINTER(C.c_void_p), C.c_double, C.c_int, C.POINTER(C.c_void_p)]),
     "mg_learned_num_params": (C.c_int, []),
@@ -329,6 +345,79 @@ def mpcg_solve_batched(classes, bs, xs, rtol=1e-8, maxit=500):
     st = load().mpcg_solve_batched(hs, n, bp, xp, rtol, maxit, ip)
     _check(st, allow=(MPCG_OK, MPCG_NOT_CONVERGED))
     return st, its
+
+
+def mg_amg_default_options(**overrides) -> mg_amg_options:
+    o = mg_amg_options()
+    _check(load().mg_amg_default_options(C.byref(o)))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def mg_hierarchy_setup_algebraic(indptr, indices, data, amg: mg_amg_options | None = None,
+                                 options: mpcg_options | None = None) -> int:
+    """Algebraic hierarchy of the host CSR matrix (indptr, indices, data)."""
+    rp = np.ascontiguousarray(indptr, dtype=np.int32)
+    ci = np.ascontiguousarray(indices, dtype=np.int32)
+    va = np.ascontiguousarray(data, dtype=np.float64)
+    A = mg_csr(len(rp) - 1, rp.ctypes.data, ci.ctypes.data, va.ctypes.data)
+    h = C.c_void_p()
+    a = amg if amg is not None else mg_amg_default_options()
+    opt = options if options is not None else mpcg_default_options()
+    _check(load().mg_hierarchy_setup_algebraic(C.byref(A), C.byref(a), C.byref(opt), C.byref(h)))
+    return h.value
+
+
+def mg_amg_aggregates(h: int, level: int) -> np.ndarray:
+    out = np.empty(mg_level_size(h, level), dtype=np.int32)
+    _check(load().mg_amg_aggregates(h, level, out.ctypes.data))
+    return out
+
+
+def mg_amg_nnz(h: int, level: int, which: int) -> int:
+    return load().mg_amg_nnz(h, level, which)
+
+
+def mg_amg_get(h: int, level: int, which: int):
+    """(indptr, indices, data) of A_level or P_level as numpy arrays."""
+    nnz = mg_amg_nnz(h, level, which)
+    if nnz < 0:
+        raise MpcgError(MPCG_ERR_ARG, "bad level or matrix")
+    rp = np.empty(mg_level_size(h, level) + 1, dtype=np.int32)
+    ci = np.empty(nnz, dtype=np.int32)
+    va = np.empty(nnz, dtype=np.float64)
+    _check(load().mg_amg_get(h, level, which, rp.ctypes.data, ci.ctypes.data, va.ctypes.data))
+    return rp, ci, va
+
+
+class AlgebraicHierarchy:
+    """Owning wrapper of an algebraic hierarchy handle built from a host CSR
+    matrix (anything with indptr / indices / data, e.g. scipy.sparse.csr_matrix)."""
+
+    def __init__(self, A, theta=None, w=None, max_levels=None, coarse_size=None, **options):
+        amg = {k: v for k, v in dict(theta=theta, w=w, max_levels=max_levels, coarse_size=coarse_size).items()
+               if v is not None}
+        self.amg = mg_amg_default_options(**amg)
+        self.options = mpcg_default_options(**options)
+        self.h = mg_hierarchy_setup_algebraic(A.indptr, A.indices, A.data, self.amg, self.options)
+        self.levels = mg_num_levels(self.h)
+
+    def solve(self, b, x, rtol=1e-8, maxit=500, histories=True):
+        return mpcg_solve(self.h, b, x, rtol, maxit, histories)
+
+    def close(self):
+        if self.h:
+            mg_hierarchy_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Hierarchy:

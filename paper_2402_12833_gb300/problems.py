@@ -350,6 +350,93 @@ def example1(kxx: float, nodes: int = 161, levels: int = 4) -> Problem:
     return anisotropic_2d(nodes, kxx, 1.0, levels)
 
 
+def stencil_csr(prob: Problem):
+    """The operator of a scalar stencil problem as a scipy CSR matrix (rows
+    and columns over the unknowns, x fastest; sorted columns, the couplings
+    to nodes outside the grid of unknowns left out), the input format of the
+    algebraic hierarchy."""
+    import scipy.sparse as sp
+    if prob.ncomp != 1:
+        raise ValueError("scalar problems only")
+    shape = prob.shape
+    dim = prob.dim
+    n = int(np.prod(shape))
+    idx = np.arange(n)
+    coords = [(idx // int(np.prod(shape[:a]))) % shape[a] for a in range(dim)]
+    rows, cols, vals = [], [], []
+    for s_, off in enumerate(_offsets(dim)):
+        ok = np.ones(n, dtype=bool)
+        col = np.zeros(n, dtype=np.int64)
+        stride = 1
+        for a in range(dim):
+            c = coords[a] + off[a]
+            ok &= (c >= 0) & (c < shape[a])
+            col += c * stride
+            stride *= shape[a]
+        v = prob.stencil[s_]
+        keep = ok & (v != 0.0)
+        rows.append(idx[keep])
+        cols.append(col[keep])
+        vals.append(v[keep])
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    A.sort_indices()
+    return A
+
+
+def fracture_kappa(nodes: int, kf: float, km: float = 1.0, delta: float = 1e-4, nfrac: int = 24,
+                   seed: int = 11) -> np.ndarray:
+    """Element coefficients of a seeded fracture network in the matrix of
+    permeability km (the stand-in for Example 2, whose network is not
+    published): nfrac straight fractures of thickness delta, centre uniform
+    in [0.05, 0.95]^2, length uniform in [0.15, 0.5], direction uniform in
+    [0, pi) (five uniforms per fracture, in that order).  Every element a
+    fracture crosses (sampled at h/4 along it) takes the element-averaged
+    permeability of a layer of thickness delta: arithmetic along a
+    conducting fracture (kf >= km), km + (delta/h)(kf - km), harmonic across
+    a blocking one, h / ((h - delta)/km + delta/kf)."""
+    ne = nodes - 1
+    h = 1.0 / ne
+    kap = np.full((ne, ne), km)
+    keff = km + (delta / h) * (kf - km) if kf >= km else h / ((h - delta) / km + delta / kf)
+    u = uniform(seed, 5 * nfrac).reshape(nfrac, 5)
+    for cx, cy, ul, ua, _ in u:
+        cx, cy = 0.05 + 0.9 * cx, 0.05 + 0.9 * cy
+        length, ang = 0.15 + 0.35 * ul, math.pi * ua
+        m = int(math.ceil(length / (h / 4))) + 1
+        t = np.linspace(-length / 2, length / 2, m)
+        x, y = cx + t * math.cos(ang), cy + t * math.sin(ang)
+        ok = (x >= 0) & (x < 1) & (y >= 0) & (y < 1)
+        ix = np.minimum((x[ok] / h).astype(np.int64), ne - 1)
+        iy = np.minimum((y[ok] / h).astype(np.int64), ne - 1)
+        kap[iy, ix] = keff
+    return kap
+
+
+def fracture_network(kf: float, nodes: int = 545, km: float = 1.0, delta: float = 1e-4, nfrac: int = 24,
+                     seed: int = 11) -> Problem:
+    """Example 2's boundary value problem on a seeded network: -div(kappa
+    grad p) = 0 on (0,1)^2, p = 1 on the right edge (its nodes eliminated),
+    inflow flux g_N = 1 on the left edge, g_N = 0 on top and bottom.  The
+    right-hand side is the consistent Neumann load (h per left-edge node, h/2
+    at its two corners) plus the Dirichlet lift: the full operator has zero
+    row sums, so -A_{I,D} 1 equals the row sums of the reduced operator.
+    545 nodes per side give 545 x 544 = 296,480 unknowns (Example 2 has about
+    3e5)."""
+    kap = fracture_kappa(nodes, kf, km, delta, nfrac, seed)
+    faces = 0x2                                   # the high x face (x = 1) is Dirichlet
+    st = assemble_diffusion(2, nodes, kappa=kap, faces=faces)
+    nx, ny = grid_shape(2, nodes, faces)
+    h = 1.0 / (nodes - 1)
+    g = np.zeros((ny, nx))
+    g[:, 0] = h
+    g[0, 0] = g[-1, 0] = h / 2
+    b = g.reshape(-1) + st.sum(axis=0)
+    levels = 1                                    # the deepest uniform hierarchy (>= 2 elements per side)
+    while (nodes - 1) % (1 << levels) == 0 and ((nodes - 1) >> levels) >= 2:
+        levels += 1
+    return Problem(2, nodes, levels, st, b, name=f"fracture_{nodes}_kf{kf:g}", kappa=kap, faces=faces)
+
+
 def net_init_params(seed: int = 7, chans=(2, 16, 16, 16, 1)) -> np.ndarray:
     """Initial weights of the learned column's 3x3 network, layer by layer
     W[co][ci][ky][kx]: Kaiming-uniform draws U(-b, b), b = sqrt(6 / (9 ci)),
