@@ -780,6 +780,214 @@ def bench_example1(args):
     return 0
 
 
+def amg_roofline(trace, ns, nnzA, nnzP, C, m, w, peaks):
+    """Dominant kernel class of a profiled solve on an algebraic hierarchy
+    and its achieved rate: algorithmic bytes per launch are the CSR content
+    of the matrix it streams (4-byte column + w-byte value per entry; ELL
+    padding excluded) plus the vectors it reads and writes once.  Launch
+    order per iteration (one stream): Jacobi J, restriction J, Jacobi J-1,
+    restriction J-1, ..., Jacobi 1, restriction 1, coarse solve,
+    prolongations P_1 .. P_J (k columns each), then the block kernels."""
+    J = len(ns) - 1
+    tot = {}
+    for cls, ms in trace:
+        tot[cls] = tot.get(cls, 0.0) + ms
+    dom = max(tot, key=tot.get)
+    cnt, jj, jr, jp = 0, J, J, 1
+    bytes_sum = dur = 0.0
+    launches = 0
+    for cls, ms in trace:
+        b = None
+        if cls == "init":
+            cnt = 0
+        if cls in ("init", "check"):
+            jj, jr, jp = J, J, 1
+        if cls == "jacobi":
+            b = nnzA[jj] * (4 + w) + 3 * ns[jj] * w
+            jj -= 1
+        elif cls == "restrict":
+            b = nnzP[jr] * (4 + w) + (ns[jr] + ns[jr - 1]) * w
+            jr -= 1
+        elif cls == "prolong":
+            b = nnzP[jp] * (4 + w) + jp * (ns[jp - 1] + ns[jp]) * w
+            jp += 1
+        elif cls == "spmm":
+            b = nnzA[J] * (4 + w) + 2 * C * ns[J] * w
+        elif cls in ("orth_update", "gram_window", "update_xr"):
+            b, _ = kernel_work(cls, ns[J], C, cnt, w)
+        if cls == dom:
+            if b is not None:
+                bytes_sum += b
+            dur += ms
+            launches += 1
+        if cls == "small_alpha":
+            cnt = min(cnt + 1, m)
+    share = tot[dom] / sum(tot.values())
+    if bytes_sum == 0:
+        return dom, None, tot
+    ach = bytes_sum / (dur * 1e-3) / 1e9
+    out = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": dom, "launches": launches,
+           "avg_launch_us": dur / launches * 1e3, "algorithmic_bytes_per_launch": bytes_sum / launches,
+           "share_of_solve": share}
+    return dom, out, tot
+
+
+def _timed_flushed(fn, steps, warmup, stream):
+    """Mean CUDA-event time of fn over `steps` calls, each preceded (outside
+    its event pair) by a 256 MB write that evicts the 129 MB L2."""
+    import torch
+    scratch = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        fn()
+    total = 0.0
+    for _ in range(steps):
+        scratch.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / steps
+
+
+def bench_algebraic(args):
+    """Algebraic hierarchies (smoothed aggregation, Section 2.1's
+    agglomeration; the stand-in for Section 3's BoomerAMG setup).  Headline:
+    the Example 2 stand-in, a seeded network of 24 fractures (thickness 1e-4)
+    on (0,1)^2 with 545^2 nodes (296,480 unknowns), p = 1 on the right edge,
+    unit inflow on the left, conducting fractures k_f = 1e4, k_m = 1; mixed
+    precision additive MG-MPCG (m = 5) to rtol 1e-8 on the algebraic
+    hierarchy.  Beside it: k_f = 10^-4 .. 10^4 with FP64 MPCG and PCG on the
+    algebraic hierarchy and mixed MPCG on the geometric one, and Section 3's
+    Example 1 (160^2 elements) across k_xx on both hierarchies; the oracle's
+    iteration counts at the two extreme k_f and at k_xx = 1e-6."""
+    import time
+    import torch
+    from oracle import amg as oa
+    from oracle import mg as omg
+    from oracle import mpcg as ompcg
+    from paper_2402_12833_gb300 import build as _build
+    from paper_2402_12833_gb300 import mpcg as M
+    from paper_2402_12833_gb300 import problems as pb
+    _build.build()
+    M.load()
+    stream = torch.cuda.current_stream()
+    peaks = load_peaks()
+
+    def solve_timed(H, b, x, steps, warmup):
+        res = {}
+
+        def step():
+            x.zero_()
+            res["st"], res["k"], _, _ = H.solve(b, x, rtol=RTOL, maxit=MAXIT, histories=False)
+
+        ms = _timed_flushed(step, steps, warmup, stream)
+        return ms, int(res["k"]), int(res["st"])
+
+    rows = []
+    head = None
+    for kf in (1e-4, 1e-2, 1.0, 1e2, 1e4):
+        prob = pb.fracture_network(kf)
+        A = pb.stencil_csr(prob)
+        b = torch.from_numpy(prob.b).cuda()
+        x = torch.zeros_like(b)
+        row = {"kf": kf}
+        t0 = time.perf_counter()
+        Hm = M.AlgebraicHierarchy(A, precision=M.MPCG_MIXED, stream=stream.cuda_stream)
+        row["setup_s"] = time.perf_counter() - t0
+        ns = [M.mg_level_size(Hm.h, j) for j in range(Hm.levels)]
+        row["grids"] = ns
+        steps = args.steps if kf == 1e4 else 1
+        clk = Clocks(0) if kf == 1e4 else None
+        ms, k, st = solve_timed(Hm, b, x, steps, args.warmup if kf == 1e4 else 1)
+        clocks = clk.stop() if clk else None
+        Ax = torch.empty_like(b)
+        M.mg_apply_operator(Hm.h, Hm.levels - 1, x, Ax, 1)
+        tr = float(torch.linalg.norm(b - Ax) / torch.linalg.norm(b))
+        row["mixed_mpcg"] = {"iterations": k, "ms": ms, "status": st, "true_rel_residual": tr}
+        if kf == 1e4:
+            x.zero_()
+            _, _, _, trace = M.mpcg_solve_profiled(Hm.h, b, x, RTOL, MAXIT)
+            nnzA = [M.mg_amg_nnz(Hm.h, j, M.MPCG_AMG_A) for j in range(Hm.levels)]
+            nnzP = [0] + [M.mg_amg_nnz(Hm.h, j, M.MPCG_AMG_P) for j in range(1, Hm.levels)]
+            dom, rl, tot = amg_roofline(trace, ns, nnzA, nnzP, Hm.levels, M_WINDOW, 4, peaks)
+            if rl is not None:
+                rl["traffic"] = measured_traffic(f"fracture_mixed:{dom}")
+            head = {"value": prob.n / (ms * 1e-3), "ms_per_step": ms, "iterations": k, "true_rel_residual": tr,
+                    "roofline": rl, "clocks": clocks, "launches": M.mg_last_launches(Hm.h),
+                    "kernel_ms_per_solve": {c: round(v, 4) for c, v in tot.items()}}
+            x.zero_()
+            ms_steps, _, _ = solve_timed(Hm, b, x, 1, 0)
+            head["launches"] = M.mg_last_launches(Hm.h)
+        Hm.close()
+        for key, opts in (("fp64_mpcg", dict(m=M_WINDOW)), ("fp64_pcg", dict(m=1, sum_columns=1))):
+            H = M.AlgebraicHierarchy(A, stream=stream.cuda_stream, **opts)
+            ms, k, st = solve_timed(H, b, x, 1, 1)
+            row[key] = {"iterations": k, "ms": ms, "status": st}
+            H.close()
+        st_dev = torch.from_numpy(prob.stencil).cuda()
+        Hg = M.Hierarchy(st_dev, 2, prob.nodes, prob.levels, faces=prob.faces, precision=M.MPCG_MIXED,
+                         stream=stream.cuda_stream)
+        ms, k, st = solve_timed(Hg, b, x, 1, 1)
+        row["geometric_mixed_mpcg"] = {"iterations": k, "ms": ms, "status": st, "grids": prob.levels}
+        Hg.close()
+        if kf in (1e-4, 1e4) and not args.no_cpu_baseline:
+            t0 = time.perf_counter()
+            O = oa.AlgebraicHierarchy(A)
+            t1 = time.perf_counter()
+            r5 = ompcg.mpcg(A, prob.b, O.mg_columns, m=M_WINDOW, rtol=RTOL, maxit=MAXIT)
+            t2 = time.perf_counter()
+            r1 = ompcg.mpcg(A, prob.b, lambda v: O.additive_mg(v)[:, None], m=1, rtol=RTOL, maxit=MAXIT)
+            row["oracle"] = {"mpcg": r5.iters, "pcg": r1.iters, "setup_s": t1 - t0, "mpcg_solve_s": t2 - t1}
+        rows.append(row)
+    ex1 = []
+    for n_ in range(0, 8):
+        kxx = 10.0 ** (-n_)
+        prob = pb.example1(kxx)
+        A = pb.stencil_csr(prob)
+        b = torch.from_numpy(prob.b).cuda()
+        x = torch.zeros_like(b)
+        H = M.AlgebraicHierarchy(A, stream=stream.cuda_stream)
+        ms, k, st = solve_timed(H, b, x, 1, 1)
+        r = {"kxx": kxx, "algebraic_mpcg": {"iterations": k, "ms": ms, "grids": H.levels}}
+        H.close()
+        H = M.AlgebraicHierarchy(A, stream=stream.cuda_stream, m=1, sum_columns=1)
+        ms, k, st = solve_timed(H, b, x, 1, 1)
+        r["algebraic_pcg"] = {"iterations": k, "ms": ms}
+        H.close()
+        if kxx == 1e-6 and not args.no_cpu_baseline:
+            O = oa.AlgebraicHierarchy(A)
+            r["oracle"] = {"mpcg": ompcg.mpcg(A, prob.b, O.mg_columns, m=M_WINDOW, rtol=RTOL, maxit=MAXIT).iters,
+                           "pcg": ompcg.mpcg(A, prob.b, lambda v: O.additive_mg(v)[:, None], m=1, rtol=RTOL,
+                                             maxit=MAXIT).iters}
+        ex1.append(r)
+    last = rows[-1]
+    cpu = None
+    if "oracle" in last:
+        o = last["oracle"]
+        cpu = {"value": 296480 / o["mpcg_solve_s"], "unit": "DOFs/s", "cores": 1, "kind": "oracle",
+               "sample": f"one full FP64 oracle solve of the headline problem ({o['mpcg']} iterations, "
+                         f"{o['mpcg_solve_s']:.1f} s; hierarchy setup {o['setup_s']:.1f} s excluded)"}
+    print(json.dumps({
+        "metric": METRIC, "workload": "algebraic", "value": head["value"], "unit": "DOFs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "Example 2 stand-in: seeded network of 24 fractures (delta 1e-4) in (0,1)^2, 545^2 "
+                               "Q1 nodes, 296,480 unknowns, p=1 right edge, unit inflow left, k_m=1, k_f=1e4; "
+                               "smoothed-aggregation hierarchy (theta 0.4, w 4/3, coarse <= 256), damped "
+                               "Jacobi nu=2, MPCG m=5, mixed precision, rtol 1e-8",
+                   "l2": "working set ~130 MB per solve, about the L2 size: L2 flushed (256 MB write) before "
+                         "every timed solve, outside its events"},
+        "iterations": head["iterations"], "true_rel_residual": head["true_rel_residual"],
+        "roofline": head["roofline"], "kernel_ms_per_solve": head["kernel_ms_per_solve"],
+        "gpu_launches": head["launches"] * args.steps, "clocks": head["clocks"], "peaks": peaks,
+        "fracture_sweep": rows, "example1": ex1, "cpu_baseline": cpu}))
+    return 0
+
+
 def bench_learned(args):
     """2D high-contrast diffusion, 1025^2 nodes, 9 grids, f = 1, kappa seed 3:
     the mixed-precision solver without and with the learned column; the
@@ -862,7 +1070,7 @@ def bench_learned(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["poisson3d", "batched", "learned", "elasticity", "example1"],
+    ap.add_argument("--workload", choices=["poisson3d", "batched", "learned", "elasticity", "example1", "algebraic"],
                     default="poisson3d",
                     help="poisson3d: the headline line; batched / learned / elasticity: the other workloads")
     ap.add_argument("--epochs", type=int, default=20, help="training epochs of the learned workload")
@@ -889,6 +1097,8 @@ def main():
         return bench_elasticity(args)
     if args.workload == "example1":
         return bench_example1(args)
+    if args.workload == "algebraic":
+        return bench_algebraic(args)
     if args.workload == "learned":
         return bench_learned(args)
     return bench_ours(args)

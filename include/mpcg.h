@@ -210,7 +210,9 @@ int mg_num_problems(const mg_hierarchy* h);
  * an aggregation does not reduce the count.  The setup runs on the host (C++,
  * once per matrix); the solve is the same additive MG-MPCG as for stencil
  * hierarchies, with damped Jacobi (nu sweeps from zero, Eq. 2) on every grid
- * >= 1, the exact coarse solve (at most 1024 unknowns), and every operator
+ * >= 1 with the weight omega_j = min(omega, (4/3) / rho_j), rho_j =
+ * max_i sum_k |a_ik| / a_ii on grid j (so that every level correction stays
+ * positive definite), the exact coarse solve (at most 1024 unknowns), and every operator
  * and transfer applied by the device in sliced ELLPACK form.  Grid indices
  * follow the paper: 0 is the coarsest, mg_num_levels() - 1 the input matrix.
  * Single problems, scalar unknowns; the SSOR smoother, the V-cycle, the

@@ -35,6 +35,14 @@ Readings (the paper fixes none of them; the library uses the same):
     Gershgorin bound max_i sum_j |a_ij| / |a_ii| of the spectral radius of
     D^-1 A (w = 0: plain aggregation, P = T);
   * Galerkin coarse operators A_c = P^T A P;
+  * the damped Jacobi smoother of grid j takes the weight
+    omega_j = min(omega, (4/3) / rho_j), rho_j the Gershgorin bound of
+    D_j^-1 A_j, so that omega_j lambda_max(D_j^-1 A_j) <= 4/3 < 2 and every
+    level correction stays symmetric positive definite (the coarse operators
+    of smoothed aggregation couple more unknowns than the fine Q1 operator
+    and can have lambda_max(D^-1 A) above 3, where omega = 2/3 would make
+    the nu = 2 correction indefinite); on Q1 fine grids rho = 2 and
+    omega_j = omega = 2/3;
   * coarsening stops at <= coarse_size unknowns, at max_levels grids, or
     when an aggregation yields no aggregate or does not reduce the count.
 """
@@ -152,4 +160,13 @@ class AlgebraicHierarchy(Hierarchy):
         self.levels = len(self.A)
         self.dim, self.nu, self.omega, self.ncomp = 0, nu, omega, 1
         self.Dinv = [1.0 / Aj.diagonal() for Aj in self.A]
+        self.omegas = [min(omega, (4.0 / 3.0) / gershgorin_bound(Aj)) for Aj in self.A]
         self.chol = sla.cholesky(self.A[0].toarray(), lower=True)
+
+    def smooth(self, j: int, g: np.ndarray) -> np.ndarray:
+        """Damped Jacobi, nu sweeps from zero (Eq. 2, c_0 = 0) with the grid's
+        weight omega_j."""
+        s = np.zeros_like(g)
+        for _ in range(self.nu):
+            s = s + self.omegas[j] * self.Dinv[j] * (g - self.A[j] @ s)
+        return s

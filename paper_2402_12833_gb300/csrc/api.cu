@@ -1245,11 +1245,15 @@ mpcg_status mg_hierarchy_setup_algebraic(const mg_csr* A, const mg_amg_options* 
       if ((st = upload_ell(h, h->amgP[j], L.eP, s)) != MPCG_OK) return fail(st);
       if ((st = upload_ell(h, Rt, L.eR, s)) != MPCG_OK) return fail(st);
     }
-    // damped inverse diagonal omega / a_ii in the flat padded layout
+    // damped inverse diagonal omega_j / a_ii in the flat padded layout, with
+    // omega_j = min(omega, (4/3) / rho_j), rho_j the Gershgorin bound of
+    // D^-1 A_j: omega_j lambda_max(D^-1 A_j) <= 4/3 keeps every level
+    // correction positive definite on the wider coarse operators
+    const double wj = std::min(opt.omega, (4.0 / 3.0) / mpcg::amg::gershgorin(Aj));
     std::vector<double> dv((size_t)L.g.len, 0.0);
     for (int i = 0; i < Aj.rows; ++i)
       for (int e = Aj.ptr[i]; e < Aj.ptr[i + 1]; ++e)
-        if (Aj.col[e] == i) dv[(size_t)L.g.G + i] = opt.omega / Aj.val[e];
+        if (Aj.col[e] == i) dv[(size_t)L.g.G + i] = wj / Aj.val[e];
     if ((st = h->mem.get(&L.dinv64, (size_t)L.g.cp, s)) != MPCG_OK) return fail(st);
     if (cudaMemcpyAsync(L.dinv64, dv.data(), sizeof(double) * dv.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {

@@ -102,24 +102,32 @@ def test_columns_and_operators_match_oracle(M, name):
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_solves_match_oracle(M, name):
-    """Additive MG-MPCG (m = 5) and additive MG-PCG (summed column) in FP64."""
+    """Additive MG-MPCG (m = 5) and additive MG-PCG (summed column) in FP64.
+
+    The solution bar is 1e-10 relative, or ten times the oracle's own drift
+    when b is perturbed by 1e-15 relative noise, whichever is larger: on the
+    strongly anisotropic Example 1 operator (k_xx = 1e-6) two oracle solves
+    that differ only in the rounding of b already end 2e-10 .. 4e-10 apart,
+    while on the other cases they agree to ~1e-13."""
     prob, A, amg = _case(name)
     O = _oracle(A, amg)
     b = torch.from_numpy(prob.b).cuda()
+    bp = prob.b * (1.0 + 1e-15 * np.random.default_rng(1).standard_normal(prob.b.shape))
     runs = {
-        "mpcg": (dict(m=5), lambda: ompcg.mpcg(A, prob.b, O.mg_columns, rtol=1e-8, maxit=3000)),
+        "mpcg": (dict(m=5), lambda rhs: ompcg.mpcg(A, rhs, O.mg_columns, rtol=1e-8, maxit=3000)),
         "pcg": (dict(m=1, sum_columns=1),
-                lambda: ompcg.mpcg(A, prob.b, lambda v: O.additive_mg(v)[:, None], m=1, rtol=1e-8, maxit=3000)),
+                lambda rhs: ompcg.mpcg(A, rhs, lambda v: O.additive_mg(v)[:, None], m=1, rtol=1e-8, maxit=3000)),
     }
     for key, (opts, ref) in runs.items():
         H = _gpu(M, A, amg, **opts)
         x = torch.zeros_like(b)
         st, k, _, _ = H.solve(b, x, rtol=1e-8, maxit=3000)
-        res = ref()
+        res = ref(prob.b)
+        drift = np.linalg.norm(ref(bp).x - res.x) / np.linalg.norm(res.x)
         assert st == M.MPCG_OK, key
         assert abs(k - res.iters) <= 1, (key, k, res.iters)
         err = np.linalg.norm(x.cpu().numpy() - res.x) / np.linalg.norm(res.x)
-        assert err <= 1e-10, (key, err)
+        assert err <= max(1e-10, 10 * drift), (key, err, drift)
 
 
 def test_pcg_collapse_is_textbook_pcg(M):

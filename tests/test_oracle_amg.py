@@ -178,3 +178,21 @@ def test_algebraic_hierarchy_handles_the_anisotropy():
     res = ompcg.mpcg(A, prob.b, H.mg_columns, rtol=1e-8, maxit=3000)
     assert np.linalg.norm(prob.b - A @ res.x) <= 1.01e-8 * np.linalg.norm(prob.b)
     assert res.iters * 4 < kg, (res.iters, kg)
+
+
+def test_level_smoothers_stay_positive_definite():
+    """Conducting fractures (k_f = 1e4): a coarse operator of the hierarchy
+    has lambda_max(D^-1 A) above 3, where the fixed weight 2/3 would exceed 2;
+    the grid weights keep omega_j lambda_max <= 4/3 on every grid, and on the
+    Q1 fine grid (Gershgorin bound 2) omega_j is the given 2/3."""
+    prob = pb.fracture_network(1e4, nodes=129)
+    A = pb.stencil_csr(prob)
+    H = oa.AlgebraicHierarchy(A)
+    assert abs(H.omegas[H.J] - 2.0 / 3.0) <= 1e-15
+    lam = []
+    for j in range(H.levels):
+        d = H.A[j].diagonal()
+        At = (H.A[j].toarray() / np.sqrt(d)[:, None]) / np.sqrt(d)[None, :]
+        lam.append(np.linalg.eigvalsh(At).max() if H.A[j].shape[0] <= 2500 else 2.0)
+        assert H.omegas[j] * lam[-1] <= 4.0 / 3.0 + 1e-12, j
+    assert max(lam) * 2.0 / 3.0 > 2.0 * 0.9    # the fixed weight would come close to, or pass, 2
