@@ -833,9 +833,10 @@ def amg_roofline(trace, ns, nnzA, nnzP, C, m, w, peaks):
     return dom, out, tot
 
 
-def _timed_flushed(fn, steps, warmup, stream):
+def _timed_flushed(fn, steps, warmup, stream, nvtx=False):
     """Mean CUDA-event time of fn over `steps` calls, each preceded (outside
-    its event pair) by a 256 MB write that evicts the 129 MB L2."""
+    its event pair) by a 256 MB write that evicts the 129 MB L2; with nvtx
+    every timed call sits in an NVTX range "timed_step"."""
     import torch
     scratch = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
     for _ in range(warmup):
@@ -845,10 +846,14 @@ def _timed_flushed(fn, steps, warmup, stream):
         scratch.fill_(1.0)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if nvtx:
+            torch.cuda.nvtx.range_push("timed_step")
         e0.record(stream)
         fn()
         e1.record(stream)
         torch.cuda.synchronize()
+        if nvtx:
+            torch.cuda.nvtx.range_pop()
         total += e0.elapsed_time(e1)
     return total / steps
 
@@ -877,32 +882,33 @@ def bench_algebraic(args):
     stream = torch.cuda.current_stream()
     peaks = load_peaks()
 
-    def solve_timed(H, b, x, steps, warmup):
+    def solve_timed(H, b, x, steps, warmup, nvtx=False):
         res = {}
 
         def step():
             x.zero_()
             res["st"], res["k"], _, _ = H.solve(b, x, rtol=RTOL, maxit=MAXIT, histories=False)
 
-        ms = _timed_flushed(step, steps, warmup, stream)
+        ms = _timed_flushed(step, steps, warmup, stream, nvtx)
         return ms, int(res["k"]), int(res["st"])
 
     rows = []
     head = None
-    for kf in (1e-4, 1e-2, 1.0, 1e2, 1e4):
+    for kf in ((1e4,) if args.headline_only else (1e-4, 1e-2, 1.0, 1e2, 1e4)):
         prob = pb.fracture_network(kf)
         A = pb.stencil_csr(prob)
         b = torch.from_numpy(prob.b).cuda()
         x = torch.zeros_like(b)
         row = {"kf": kf}
         t0 = time.perf_counter()
-        Hm = M.AlgebraicHierarchy(A, precision=M.MPCG_MIXED, stream=stream.cuda_stream)
+        Hm = M.AlgebraicHierarchy(A, precision=M.MPCG_MIXED, stream=stream.cuda_stream,
+                                  use_graph=0 if args.direct else 1)
         row["setup_s"] = time.perf_counter() - t0
         ns = [M.mg_level_size(Hm.h, j) for j in range(Hm.levels)]
         row["grids"] = ns
         steps = args.steps if kf == 1e4 else 1
         clk = Clocks(0) if kf == 1e4 else None
-        ms, k, st = solve_timed(Hm, b, x, steps, args.warmup if kf == 1e4 else 1)
+        ms, k, st = solve_timed(Hm, b, x, steps, args.warmup if kf == 1e4 else 1, nvtx=kf == 1e4)
         clocks = clk.stop() if clk else None
         Ax = torch.empty_like(b)
         M.mg_apply_operator(Hm.h, Hm.levels - 1, x, Ax, 1)
@@ -923,6 +929,9 @@ def bench_algebraic(args):
             ms_steps, _, _ = solve_timed(Hm, b, x, 1, 0)
             head["launches"] = M.mg_last_launches(Hm.h)
         Hm.close()
+        if args.headline_only:
+            rows.append(row)
+            continue
         for key, opts in (("fp64_mpcg", dict(m=M_WINDOW)), ("fp64_pcg", dict(m=1, sum_columns=1))):
             H = M.AlgebraicHierarchy(A, stream=stream.cuda_stream, **opts)
             ms, k, st = solve_timed(H, b, x, 1, 1)
@@ -944,7 +953,7 @@ def bench_algebraic(args):
             row["oracle"] = {"mpcg": r5.iters, "pcg": r1.iters, "setup_s": t1 - t0, "mpcg_solve_s": t2 - t1}
         rows.append(row)
     ex1 = []
-    for n_ in range(0, 8):
+    for n_ in (() if args.headline_only else range(0, 8)):
         kxx = 10.0 ** (-n_)
         prob = pb.example1(kxx)
         A = pb.stencil_csr(prob)
@@ -1079,6 +1088,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="algebraic workload: the headline solve only (no sweeps, no oracle)")
     ap.add_argument("--matrix-free", action="store_true",
                     help="with --only mixed: the matrix-free fine operator in the timed solve")
     ap.add_argument("--direct", action="store_true",

@@ -50,7 +50,7 @@ void set_err(const char* fmt, ...) {
 // A sparse matrix of an algebraic hierarchy in device memory (EllDev layout);
 // the FP32 values exist once the mixed-precision solver is built.
 struct EllLevel {
-  int rows = 0, cols = 0, nslices = 0;
+  int rows = 0, cols = 0, nslices = 0, lg = 0;
   int* sptr = nullptr;
   int* col = nullptr;
   double* v64 = nullptr;
@@ -61,9 +61,9 @@ struct EllLevel {
 template <typename T>
 EllDev<T> ell_of(const EllLevel& E);
 template <>
-EllDev<double> ell_of<double>(const EllLevel& E) { return {E.rows, E.cols, E.nslices, E.sptr, E.col, E.v64}; }
+EllDev<double> ell_of<double>(const EllLevel& E) { return {E.rows, E.cols, E.nslices, E.lg, E.sptr, E.col, E.v64}; }
 template <>
-EllDev<float> ell_of<float>(const EllLevel& E) { return {E.rows, E.cols, E.nslices, E.sptr, E.col, E.v32}; }
+EllDev<float> ell_of<float>(const EllLevel& E) { return {E.rows, E.cols, E.nslices, E.lg, E.sptr, E.col, E.v32}; }
 
 struct Level {
   GridDesc g;
@@ -816,15 +816,21 @@ mpcg_status build_f32(mg_hierarchy* h) {
 }
 
 // Sliced ELLPACK (EllDev layout) of a host CSR matrix, uploaded to the device.
+// Lanes per row: the largest power of two g <= 32 with g <= (mean row
+// length) / 6, so that every lane still takes about six entries or more.
 mpcg_status upload_ell(mg_hierarchy* h, const mpcg::amg::Csr& M, EllLevel& E, cudaStream_t s) {
   E.rows = M.rows;
   E.cols = M.cols;
-  E.nslices = (M.rows + 31) / 32;
+  const double mean = M.rows ? (double)M.nnz() / M.rows : 0.0;
+  E.lg = 0;
+  while (E.lg < 5 && (double)(2 << E.lg) <= mean / 6.0) ++E.lg;
+  const int g = 1 << E.lg, rps = 32 >> E.lg;   // lanes per row, rows per slice
+  E.nslices = (M.rows + rps - 1) / rps;
   std::vector<int> sptr((size_t)E.nslices + 1, 0);
   long long total = 0;
   for (int sl = 0; sl < E.nslices; ++sl) {
     int w = 0;
-    for (int r = 32 * sl; r < 32 * sl + 32 && r < M.rows; ++r) w = std::max(w, M.ptr[r + 1] - M.ptr[r]);
+    for (int r = rps * sl; r < rps * sl + rps && r < M.rows; ++r) w = std::max(w, (M.ptr[r + 1] - M.ptr[r] + g - 1) / g);
     total += 32LL * w;
     if (total >= (1LL << 31)) {
       set_err("sparse matrix too large for 32-bit entry offsets");
@@ -836,9 +842,10 @@ mpcg_status upload_ell(mg_hierarchy* h, const mpcg::amg::Csr& M, EllLevel& E, cu
   std::vector<int> col((size_t)total, 0);
   std::vector<double> val((size_t)total, 0.0);
   for (int sl = 0; sl < E.nslices; ++sl)
-    for (int r = 32 * sl; r < 32 * sl + 32 && r < M.rows; ++r)
+    for (int r = rps * sl; r < rps * sl + rps && r < M.rows; ++r)
       for (int e = M.ptr[r]; e < M.ptr[r + 1]; ++e) {
-        const size_t k = (size_t)sptr[sl] + 32 * (size_t)(e - M.ptr[r]) + (size_t)(r - 32 * sl);
+        const int idx = e - M.ptr[r];   // entry idx of the row: slot idx / g of lane (r - rps sl) g + idx mod g
+        const size_t k = (size_t)sptr[sl] + 32 * (size_t)(idx / g) + (size_t)((r - rps * sl) * g + idx % g);
         col[k] = M.col[e];
         val[k] = M.val[e];
       }

@@ -163,14 +163,18 @@ inline GridDesc make_grid_flat(long long n, int nb = 1) {
 }
 
 // A sparse matrix of an algebraic hierarchy on the device, in sliced
-// ELLPACK form with slices of 32 rows (one warp): slice s holds
-// w_s = (sptr[s+1] - sptr[s]) / 32 entries per row, stored slot-major
-// (entry k of row 32 s + l at sptr[s] + 32 k + l) so that a warp reads each
-// slot of its 32 rows in one coalesced load.  Rows shorter than w_s, and the
-// rows past `rows` in the last slice, are padded with column 0 and value 0.
+// ELLPACK form with one warp per slice and g = 2^lg lanes per row: slice s
+// holds the 32/g rows s*32/g ... s*32/g + 32/g - 1; lane l serves row
+// l / g of the slice and takes entries q, q + g, q + 2g, ... of it
+// (q = l mod g).  Slot k of lane l is stored at sptr[s] + 32 k + l, so a
+// warp reads each slot of its rows in one coalesced load; the slice has
+// (sptr[s+1] - sptr[s]) / 32 slots.  Missing entries, and the rows past
+// `rows` in the last slice, are padded with column 0 and value 0.  g = 1
+// suits short rows (one thread per row); long rows (restrictions, the wider
+// coarse operators) take several lanes and a shuffle reduction.
 template <typename T>
 struct EllDev {
-  int rows, cols, nslices;
+  int rows, cols, nslices, lg;
   const int* sptr;
   const int* col;
   const T* val;

@@ -5,10 +5,11 @@
 // (prolongation) of Section 2.1.  Vectors are flat padded arrays (unknown i
 // at G + i); every launcher takes pointers already offset by G.
 //
-// One thread computes one row; the 32 rows of a slice are one warp, so the
-// column and value loads of a slot are coalesced and the slot count of the
-// warp is uniform.  The gathered X entries come through L1/L2: the matrices
-// of a grid hierarchy couple nearby unknowns.
+// A warp computes one slice: g lanes per row accumulate every g-th entry and
+// a shuffle reduction over the g lanes finishes the row, so the column and
+// value loads of a slot are coalesced and the slot count of the warp is
+// uniform.  The gathered X entries come through L1/L2: the matrices of a
+// grid hierarchy couple nearby unknowns.
 #include "kernels.cuh"
 #include "vec.cuh"
 
@@ -21,6 +22,13 @@ __device__ __forceinline__ T ldv(const T* p) {
   return __ldg(p);
 }
 
+// sum over the g = 2^lg lanes of a row group (all 32 lanes take part)
+template <typename T>
+__device__ __forceinline__ T group_sum(T v, int lg) {
+  for (int o = 1; o < (1 << lg); o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Y[:, c] = A X[:, c] for C columns (column pitches ldx, ldy); with ZAZ the
 // per-block partials of X[:, c]^T Y[:, c] (value-major, stride gridDim.x).
 template <typename T, int C, bool ZAZ>
@@ -31,9 +39,10 @@ __global__ void __launch_bounds__(kBlock) k_ell_spmm(EllDev<T> A, const T* __res
   T zacc[ZAZ ? C : 1];
 #pragma unroll
   for (int c = 0; c < (ZAZ ? C : 1); ++c) zacc[c] = 0;
-  const long long nr = (long long)A.nslices * 32;
-  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nr; r += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(r >> 5), lane = (int)(r & 31);
+  const long long nt = (long long)A.nslices * 32;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nt; t += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(t >> 5), lane = (int)(t & 31);
+    const long long r = ((long long)s << (5 - A.lg)) + (lane >> A.lg);
     const int b = A.sptr[s];
     const int w = (A.sptr[s + 1] - b) >> 5;
     T acc[C];
@@ -46,7 +55,9 @@ __global__ void __launch_bounds__(kBlock) k_ell_spmm(EllDev<T> A, const T* __res
 #pragma unroll
       for (int c = 0; c < C; ++c) acc[c] = fma(v, X[c * ldx + j], acc[c]);
     }
-    if (r < A.rows) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = group_sum(acc[c], A.lg);
+    if (r < A.rows && (lane & ((1 << A.lg) - 1)) == 0) {
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         Y[c * ldy + r] = acc[c];
@@ -65,9 +76,10 @@ __global__ void __launch_bounds__(kBlock) k_ell_residual(EllDev<T> A, const T* _
                                                          double* part, const int* __restrict__ xnz) {
   const bool zero_x = xnz && xnz[0] == 0;
   T sums[2] = {0, 0};
-  const long long nr = (long long)A.nslices * 32;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nr; q += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(q >> 5), lane = (int)(q & 31);
+  const long long nt = (long long)A.nslices * 32;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nt; t += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(t >> 5), lane = (int)(t & 31);
+    const long long q = ((long long)s << (5 - A.lg)) + (lane >> A.lg);
     T acc = 0;
     if (!zero_x) {
       const int e0 = A.sptr[s];
@@ -76,8 +88,9 @@ __global__ void __launch_bounds__(kBlock) k_ell_residual(EllDev<T> A, const T* _
         const int e = e0 + 32 * k + lane;
         acc = fma(ldv(A.val + e), x[ldv(A.col + e)], acc);
       }
+      acc = group_sum(acc, A.lg);
     }
-    if (q < A.rows) {
+    if (q < A.rows && (lane & ((1 << A.lg) - 1)) == 0) {
       const T bv = b[q];
       const T rv = bv - acc;
       r[q] = rv;
@@ -97,9 +110,10 @@ __global__ void __launch_bounds__(kBlock) k_ell_jacobi(EllDev<T> A, const T* __r
                                                        const T* __restrict__ g, const T* __restrict__ sin,
                                                        T* __restrict__ out, int mode, const DevState* state) {
   if (state && state[0].done) return;
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= (long long)A.nslices * 32) return;
-  const int s = (int)(q >> 5), lane = (int)(q & 31);
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)A.nslices * 32) return;   // whole warps: the grid covers the slices in units of 32 threads
+  const int s = (int)(t >> 5), lane = (int)(t & 31);
+  const long long q = ((long long)s << (5 - A.lg)) + (lane >> A.lg);
   T acc = 0;
   if (mode != 0) {
     const int e0 = A.sptr[s];
@@ -110,8 +124,9 @@ __global__ void __launch_bounds__(kBlock) k_ell_jacobi(EllDev<T> A, const T* __r
       const T xj = mode == 1 ? dinv[j] * g[j] : sin[j];
       acc = fma(ldv(A.val + e), xj, acc);
     }
+    acc = group_sum(acc, A.lg);
   }
-  if (q >= A.rows) return;
+  if (q >= A.rows || (lane & ((1 << A.lg) - 1)) != 0) return;
   const T d = dinv[q], gv = g[q];
   if (mode == 0) out[q] = d * gv;
   else if (mode == 1) out[q] = d * gv + d * (gv - acc);
