@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(kBlock) k_ell_spmm(EllDev<T> A, const T* __res
     T acc[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) acc[c] = 0;
+#pragma unroll 4   // four slots' loads in flight: the short coarse rows are latency-bound
     for (int k = 0; k < w; ++k) {
       const int e = b + 32 * k + lane;
       const int j = ldv(A.col + e);
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(kBlock) k_ell_residual(EllDev<T> A, const T* _
     if (!zero_x) {
       const int e0 = A.sptr[s];
       const int w = (A.sptr[s + 1] - e0) >> 5;
+#pragma unroll 4
       for (int k = 0; k < w; ++k) {
         const int e = e0 + 32 * k + lane;
         acc = fma(ldv(A.val + e), x[ldv(A.col + e)], acc);
@@ -118,6 +120,7 @@ __global__ void __launch_bounds__(kBlock) k_ell_jacobi(EllDev<T> A, const T* __r
   if (mode != 0) {
     const int e0 = A.sptr[s];
     const int w = (A.sptr[s + 1] - e0) >> 5;
+#pragma unroll 4
     for (int k = 0; k < w; ++k) {
       const int e = e0 + 32 * k + lane;
       const int j = ldv(A.col + e);
