@@ -42,12 +42,38 @@ CASES = {
     "fracture_129_blocking": lambda: (pb.fracture_network(1e-4, nodes=129), dict()),
     "fracture_129_conducting": lambda: (pb.fracture_network(1e4, nodes=129), dict()),
     "plain_aggregation_65": lambda: (pb.diffusion_macro(2, 65, 5, rhs="normal", rhs_seed=3), dict(w=0.0)),
+    "isolated_unknowns": lambda: (_with_isolated(pb.diffusion_macro(2, 33, 4, rhs="normal", rhs_seed=5)),
+                                  dict(coarse_size=30)),
 }
+
+
+class _Csr:
+    """A problem given directly as a CSR matrix (no stencil)."""
+
+    def __init__(self, A, b):
+        self.A, self.b = A, b
+
+
+def _with_isolated(prob):
+    """The problem's matrix with 40 decoupled unknowns (diagonal-only rows,
+    in no aggregate) interleaved at every 25th position."""
+    A0 = pb.stencil_csr(prob)
+    n0 = A0.shape[0]
+    iso = np.arange(0, 40) * 25
+    keep = np.setdiff1d(np.arange(n0 + 40), iso)
+    E = sp.csr_matrix((np.ones(n0), (keep, np.arange(n0))), shape=(n0 + 40, n0))
+    D = sp.csr_matrix((2.0 + iso / 1000.0, (iso, iso)), shape=(n0 + 40, n0 + 40))
+    A = sp.csr_matrix(E @ A0 @ E.T + D)
+    b = np.zeros(n0 + 40)
+    b[keep] = prob.b
+    b[iso] = 1.0
+    return _Csr(A, b)
 
 
 def _case(name):
     prob, amg = CASES[name]()
-    A = pb.stencil_csr(prob)
+    A = prob.A if isinstance(prob, _Csr) else pb.stencil_csr(prob)
+    A.sort_indices()
     return prob, A, amg
 
 
@@ -261,3 +287,11 @@ def test_full_size_fracture_network(M):
         idx = rng.integers(0, A.shape[0], 200)
         for j in range(O.levels):
             assert np.abs(got[idx, j] - ref[idx, j]).max() <= 1e-12 * np.abs(ref[:, j]).max(), (kf, j)
+
+
+def test_isolated_unknowns_are_outside_every_aggregate(M):
+    prob, A, amg = _case("isolated_unknowns")
+    H = _gpu(M, A, amg)
+    agg = M.mg_amg_aggregates(H.h, H.levels - 1)
+    iso = np.arange(0, 40) * 25
+    assert np.all(agg[iso] == -1) and np.all(np.delete(agg, iso) >= 0)

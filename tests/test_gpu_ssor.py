@@ -127,3 +127,25 @@ def test_options_are_checked(M):
     with pytest.raises(M.MpcgError):
         M.Hierarchy(torch.from_numpy(pe.stencil).cuda(), 3, 9, pe.levels, dofs_per_node=3, faces=pe.faces,
                     smoother=M.MPCG_SMOOTHER_SSOR)
+
+
+@pytest.mark.parametrize("omega", [0.8, 1.4])
+def test_ssor_relaxation_factor(M, omega):
+    """SSOR with omega != 1 (under- and over-relaxed) against the oracle:
+    the level corrections and the V(3,3) cycle to 1e-12."""
+    prob = CASES["kappa2d_33"]()
+    H = _hier(M, prob, nu=6, ssor_omega=omega)
+    O = omg.Hierarchy(prob.dim, None, prob.stencil, prob.levels, nodes=prob.nodes, faces=prob.faces)
+    Ss = oss.level_smoothers(O, omega)
+    r = np.random.default_rng(7).standard_normal(prob.n)
+    Z = torch.zeros((prob.levels, prob.n), dtype=torch.float64, device="cuda")
+    M.mg_corrections(H.h, torch.from_numpy(r).cuda(), Z)
+    ref = oss.additive_columns(O, Ss, r, 6)
+    got = Z.cpu().numpy().T
+    for j in range(prob.levels):
+        assert np.abs(got[:, j] - ref[:, j]).max() <= 1e-12 * np.abs(ref[:, j]).max(), j
+    Hv = _hier(M, prob, nu=3, vcycle=1, m=1, ssor_omega=omega)
+    Zv = torch.zeros((1, prob.n), dtype=torch.float64, device="cuda")
+    M.mg_corrections(Hv.h, torch.from_numpy(r).cuda(), Zv)
+    refv = oss.vcycle(O, Ss, r, 3)
+    assert np.abs(Zv.cpu().numpy()[0] - refv).max() <= 1e-12 * np.abs(refv).max()
