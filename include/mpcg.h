@@ -266,6 +266,24 @@ mpcg_status mg_hierarchy_setup_algebraic(const mg_csr* A, const mg_amg_options* 
 mpcg_status mg_amg_aggregates(const mg_hierarchy* h, int level, int* agg);
 long long mg_amg_nnz(const mg_hierarchy* h, int level, int which);
 mpcg_status mg_amg_get(const mg_hierarchy* h, int level, int which, int* rowptr, int* col, double* val);
+
+/*
+ * The same smoothed-aggregation setup on the host alone (no device memory,
+ * no CUDA call): for inspecting a hierarchy before building a solver.
+ * mg_amg_setup_host checks A and amg as mg_hierarchy_setup_algebraic does
+ * (amg may be NULL) and builds every grid; the inspection calls take the
+ * same arguments as their mg_amg_* counterparts (grid 0 is the coarsest).
+ * mg_amg_host_size returns -1 and the others MPCG_ERR_ARG on bad arguments.
+ * The handle owns host memory until mg_amg_host_destroy.
+ */
+typedef struct mg_amg_host mg_amg_host;
+mpcg_status mg_amg_setup_host(const mg_csr* A, const mg_amg_options* amg, mg_amg_host** out);
+int mg_amg_host_levels(const mg_amg_host* a);
+long long mg_amg_host_size(const mg_amg_host* a, int level);
+long long mg_amg_host_nnz(const mg_amg_host* a, int level, int which);
+mpcg_status mg_amg_host_aggregates(const mg_amg_host* a, int level, int* agg);
+mpcg_status mg_amg_host_get(const mg_amg_host* a, int level, int which, int* rowptr, int* col, double* val);
+void mg_amg_host_destroy(mg_amg_host* a);
 /*
  * Problems of uneven size: one batched hierarchy per grid size (nclass of
  * them, preferably each with its own stream in its options), solved

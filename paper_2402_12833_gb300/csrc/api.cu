@@ -350,15 +350,25 @@ mpcg_status ensure_hist(mg_hierarchy* h, Solver<T>& S, int maxit) {
 // nu damped-Jacobi sweeps from zero on grid j: rr -> out.
 // k multicoloured SSOR steps on grid j for the right-hand side rr, in place
 // on x (a forward sweep over the 2^dim colours, then a backward one).
+// With omega = 1 a colour updated twice in a row (the turn of each step,
+// K-1 then K-1, and colour 0 between steps) gets an exactly zero second
+// update: unknowns of one colour do not couple, so the first update already
+// zeroed the colour's residual; those launches are skipped (the result moves
+// by rounding only).
 template <typename T>
 void enqueue_ssor_steps(mg_hierarchy* h, int j, const T* rr, T* x, int k, const DevState* state, cudaStream_t s) {
   const Level& L = h->lev[j];
   const int K = 1 << L.g.dim;
+  const bool skip_repeat = h->opt.ssor_omega == 1.0;
+  int last = -1;
+  auto update = [&](int c) {
+    if (skip_repeat && c == last) return;
+    LAUNCH(h, K_JACOBI, s, launch_gs_colour<T>(L.g, st_of<T>(L), rr, x, c, h->opt.ssor_omega, state, s));
+    last = c;
+  };
   for (int step = 0; step < k; ++step) {
-    for (int c = 0; c < K; ++c)
-      LAUNCH(h, K_JACOBI, s, launch_gs_colour<T>(L.g, st_of<T>(L), rr, x, c, h->opt.ssor_omega, state, s));
-    for (int c = K - 1; c >= 0; --c)
-      LAUNCH(h, K_JACOBI, s, launch_gs_colour<T>(L.g, st_of<T>(L), rr, x, c, h->opt.ssor_omega, state, s));
+    for (int c = 0; c < K; ++c) update(c);
+    for (int c = K - 1; c >= 0; --c) update(c);
   }
 }
 
@@ -1157,14 +1167,9 @@ mpcg_status mg_amg_default_options(mg_amg_options* amg) {
   return MPCG_OK;
 }
 
-mpcg_status mg_hierarchy_setup_algebraic(const mg_csr* A, const mg_amg_options* amg_in, const mpcg_options* opt_in,
-                                         mg_hierarchy** out) {
-  g_err.clear();
-  if (!out) {
-    set_err("out pointer is NULL");
-    return MPCG_ERR_ARG;
-  }
-  *out = nullptr;
+// Checks the matrix and the algebraic options, then builds the grids on the
+// host (finest first); the coarsest grid must hold at most 1024 unknowns.
+static mpcg_status amg_build_checked(const mg_csr* A, const mg_amg_options* amg_in, mpcg::amg::Levels& H) {
   if (!A) {
     set_err("matrix is NULL");
     return MPCG_ERR_ARG;
@@ -1179,14 +1184,6 @@ mpcg_status mg_hierarchy_setup_algebraic(const mg_csr* A, const mg_amg_options* 
             MPCG_MAX_COLS);
     return MPCG_ERR_ARG;
   }
-  mpcg_options opt;
-  if (opt_in) opt = *opt_in;
-  else mpcg_default_options(&opt);
-  CKS(check_options(opt));
-  if (opt.smoother != MPCG_SMOOTHER_JACOBI || opt.vcycle) {
-    set_err("algebraic hierarchies smooth with damped Jacobi (no SSOR, no V-cycle)");
-    return MPCG_ERR_ARG;
-  }
   std::string err;
   if (!mpcg::amg::check_input(A->n, A->rowptr, A->col, A->val, err)) {
     set_err("%s", err.c_str());
@@ -1198,14 +1195,34 @@ mpcg_status mg_hierarchy_setup_algebraic(const mg_csr* A, const mg_amg_options* 
   fine.ptr.assign(A->rowptr, A->rowptr + A->n + 1);
   fine.col.assign(A->col, A->col + nnz);
   fine.val.assign(A->val, A->val + nnz);
-  mpcg::amg::Levels H;
   mpcg::amg::build(fine, {amg.theta, amg.w, amg.max_levels, amg.coarse_size}, H);
-  const int levels = (int)H.A.size();
-  const int n0 = H.A.back().rows;
-  if (n0 > 1024) {
-    set_err("coarsest grid has %d unknowns (> 1024): raise max_levels or lower theta", n0);
+  if (H.A.back().rows > 1024) {
+    set_err("coarsest grid has %d unknowns (> 1024): raise max_levels or lower theta", H.A.back().rows);
     return MPCG_ERR_ARG;
   }
+  return MPCG_OK;
+}
+
+mpcg_status mg_hierarchy_setup_algebraic(const mg_csr* A, const mg_amg_options* amg_in, const mpcg_options* opt_in,
+                                         mg_hierarchy** out) {
+  g_err.clear();
+  if (!out) {
+    set_err("out pointer is NULL");
+    return MPCG_ERR_ARG;
+  }
+  *out = nullptr;
+  mpcg_options opt;
+  if (opt_in) opt = *opt_in;
+  else mpcg_default_options(&opt);
+  CKS(check_options(opt));
+  if (opt.smoother != MPCG_SMOOTHER_JACOBI || opt.vcycle) {
+    set_err("algebraic hierarchies smooth with damped Jacobi (no SSOR, no V-cycle)");
+    return MPCG_ERR_ARG;
+  }
+  mpcg::amg::Levels H;
+  CKS(amg_build_checked(A, amg_in, H));
+  const int levels = (int)H.A.size();
+  const int n0 = H.A.back().rows;
   mg_hierarchy* h = new mg_hierarchy();
   cudaGetDevice(&h->device);
   h->algebraic = true;
@@ -1347,6 +1364,86 @@ mpcg_status mg_amg_get(const mg_hierarchy* h, int level, int which, int* rowptr,
   std::copy(M->val.begin(), M->val.end(), val);
   return MPCG_OK;
 }
+
+}  // extern "C"
+
+// Host-only hierarchy: the grids of the paper's numbering (0 coarsest).
+struct mg_amg_host {
+  std::vector<mpcg::amg::Csr> A, P;
+  std::vector<std::vector<int>> agg;
+};
+
+extern "C" {
+
+mpcg_status mg_amg_setup_host(const mg_csr* A, const mg_amg_options* amg, mg_amg_host** out) {
+  g_err.clear();
+  if (!out) {
+    set_err("out pointer is NULL");
+    return MPCG_ERR_ARG;
+  }
+  *out = nullptr;
+  mpcg::amg::Levels H;
+  CKS(amg_build_checked(A, amg, H));
+  const int levels = (int)H.A.size();
+  mg_amg_host* a = new mg_amg_host();
+  a->A.resize(levels);
+  a->P.resize(levels);
+  a->agg.resize(levels);
+  for (int j = 0; j < levels; ++j) {
+    const int l = levels - 1 - j;
+    a->A[j] = std::move(H.A[l]);
+    if (j >= 1) {
+      a->P[j] = std::move(H.P[l]);
+      a->agg[j] = std::move(H.agg[l]);
+    }
+  }
+  *out = a;
+  return MPCG_OK;
+}
+
+int mg_amg_host_levels(const mg_amg_host* a) { return a ? (int)a->A.size() : -1; }
+
+long long mg_amg_host_size(const mg_amg_host* a, int level) {
+  if (!a || level < 0 || level >= (int)a->A.size()) return -1;
+  return a->A[level].rows;
+}
+
+static const mpcg::amg::Csr* host_matrix(const mg_amg_host* a, int level, int which) {
+  if (!a || level < 0 || level >= (int)a->A.size()) return nullptr;
+  if (which == MPCG_AMG_A) return &a->A[level];
+  if (which == MPCG_AMG_P && level >= 1) return &a->P[level];
+  return nullptr;
+}
+
+long long mg_amg_host_nnz(const mg_amg_host* a, int level, int which) {
+  const mpcg::amg::Csr* M = host_matrix(a, level, which);
+  return M ? M->nnz() : -1;
+}
+
+mpcg_status mg_amg_host_aggregates(const mg_amg_host* a, int level, int* agg) {
+  g_err.clear();
+  if (!a || level < 1 || level >= (int)a->A.size() || !agg) {
+    set_err("need a host hierarchy, a grid level >= 1 and an output array");
+    return MPCG_ERR_ARG;
+  }
+  std::copy(a->agg[level].begin(), a->agg[level].end(), agg);
+  return MPCG_OK;
+}
+
+mpcg_status mg_amg_host_get(const mg_amg_host* a, int level, int which, int* rowptr, int* col, double* val) {
+  g_err.clear();
+  const mpcg::amg::Csr* M = host_matrix(a, level, which);
+  if (!M || !rowptr || !col || !val) {
+    set_err("need a host hierarchy, a valid level/matrix and output arrays");
+    return MPCG_ERR_ARG;
+  }
+  std::copy(M->ptr.begin(), M->ptr.end(), rowptr);
+  std::copy(M->col.begin(), M->col.end(), col);
+  std::copy(M->val.begin(), M->val.end(), val);
+  return MPCG_OK;
+}
+
+void mg_amg_host_destroy(mg_amg_host* a) { delete a; }
 
 static mpcg_status solve_fp64(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, int* iters_out,
                               double* res_hist, double* alpha_hist) {

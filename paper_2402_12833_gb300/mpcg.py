@@ -101,6 +101,13 @@ _SIGS = {
     "mg_amg_aggregates": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "mg_amg_nnz": (C.c_longlong, [C.c_void_p, C.c_int, C.c_int]),
     "mg_amg_get": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mg_amg_setup_host": (C.c_int, [C.POINTER(mg_csr), C.POINTER(mg_amg_options), C.POINTER(C.c_void_p)]),
+    "mg_amg_host_levels": (C.c_int, [C.c_void_p]),
+    "mg_amg_host_size": (C.c_longlong, [C.c_void_p, C.c_int]),
+    "mg_amg_host_nnz": (C.c_longlong, [C.c_void_p, C.c_int, C.c_int]),
+    "mg_amg_host_aggregates": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "mg_amg_host_get": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mg_amg_host_destroy": (None, [C.c_void_p]),
     "mpcg_solve_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p),
                                      C.POINTER(C.c_void_p), C.c_double, C.c_int, C.POINTER(C.c_void_p)]),
     "mg_learned_num_params": (C.c_int, []),
@@ -391,6 +398,53 @@ def mg_amg_get(h: int, level: int, which: int):
     va = np.empty(nnz, dtype=np.float64)
     _check(load().mg_amg_get(h, level, which, rp.ctypes.data, ci.ctypes.data, va.ctypes.data))
     return rp, ci, va
+
+
+class AmgHost:
+    """The smoothed-aggregation grids built on the host only (no device):
+    levels, sizes, aggregates and the CSR matrices of every grid."""
+
+    def __init__(self, A, theta=None, w=None, max_levels=None, coarse_size=None):
+        amg = {k: v for k, v in dict(theta=theta, w=w, max_levels=max_levels, coarse_size=coarse_size).items()
+               if v is not None}
+        rp = np.ascontiguousarray(A.indptr, dtype=np.int32)
+        ci = np.ascontiguousarray(A.indices, dtype=np.int32)
+        va = np.ascontiguousarray(A.data, dtype=np.float64)
+        M = mg_csr(len(rp) - 1, rp.ctypes.data, ci.ctypes.data, va.ctypes.data)
+        h = C.c_void_p()
+        _check(load().mg_amg_setup_host(C.byref(M), C.byref(mg_amg_default_options(**amg)), C.byref(h)))
+        self.h = h.value
+        self.levels = load().mg_amg_host_levels(self.h)
+
+    def size(self, level: int) -> int:
+        return load().mg_amg_host_size(self.h, level)
+
+    def aggregates(self, level: int) -> np.ndarray:
+        out = np.empty(self.size(level), dtype=np.int32)
+        _check(load().mg_amg_host_aggregates(self.h, level, out.ctypes.data))
+        return out
+
+    def get(self, level: int, which: int):
+        """(indptr, indices, data) of A_level (MPCG_AMG_A) or P_level (MPCG_AMG_P)."""
+        nnz = load().mg_amg_host_nnz(self.h, level, which)
+        if nnz < 0:
+            raise MpcgError(MPCG_ERR_ARG, "bad level or matrix")
+        rp = np.empty(self.size(level) + 1, dtype=np.int32)
+        ci = np.empty(nnz, dtype=np.int32)
+        va = np.empty(nnz, dtype=np.float64)
+        _check(load().mg_amg_host_get(self.h, level, which, rp.ctypes.data, ci.ctypes.data, va.ctypes.data))
+        return rp, ci, va
+
+    def close(self):
+        if self.h:
+            load().mg_amg_host_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class AlgebraicHierarchy:
