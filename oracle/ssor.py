@@ -1,7 +1,11 @@
 """SSOR smoothing and the multiplicative V-cycle, the paper's comparison
 setup (Section 3: symmetric successive over-relaxation as the smoother, 3
 pre- and 3 post-smoothing steps in the multiplicative MG, 6 steps on each
-level for the additive MG; the multiplicative MG preconditions CG).
+level for the additive MG; the multiplicative MG preconditions CG).  The
+V-cycle also takes damped-Jacobi smoothers (class Jacobi): the colouring
+of the SSOR reading needs grid coordinates, which an algebraic hierarchy
+does not have; Jacobi is self-adjoint, so V(nu, nu) with it stays a
+symmetric preconditioner.
 
 This is test infrastructure: only tests/, the package's smoke entry point
 and bench.py's CPU baseline may use it; the CUDA path shares nothing with it.
@@ -66,6 +70,28 @@ class SSOR:
             self.sweep(b, x, fwd)
             self.sweep(b, x, fwd[::-1])
         return x
+
+
+class Jacobi:
+    """Damped Jacobi on one grid as a smoother with a starting iterate:
+    k sweeps x <- x + w D^-1 (b - A x), in place (Eq. 2's smoother)."""
+
+    def __init__(self, A: sp.spmatrix, dinv: np.ndarray, w: float):
+        self.A = sp.csr_matrix(A)
+        self.dinv = dinv
+        self.w = w
+
+    def steps(self, b: np.ndarray, x: np.ndarray, k: int) -> np.ndarray:
+        for _ in range(k):
+            x += self.w * self.dinv * (b - self.A @ x)
+        return x
+
+
+def jacobi_smoothers(H):
+    """The damped-Jacobi smoother of every grid of H with the grid's weight
+    (H.omegas where the hierarchy sets one per grid, else H.omega)."""
+    ws = getattr(H, "omegas", None) or [H.omega] * H.levels
+    return [Jacobi(H.A[j], H.Dinv[j], ws[j]) for j in range(H.levels)]
 
 
 def level_smoothers(H, omega: float = 1.0):

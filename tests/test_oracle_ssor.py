@@ -147,3 +147,28 @@ def test_vcycle_pcg_solves_tiny_problems_and_beats_additive_pcg():
     assert np.linalg.norm(xv - xd) <= 1e-8 * np.linalg.norm(xd)
     assert np.linalg.norm(xa - xd) <= 1e-8 * np.linalg.norm(xd)
     assert kv < ka, (kv, ka)
+
+
+def test_jacobi_vcycle_is_the_two_grid_error_propagation():
+    """Two grids, V(nu, nu) with damped Jacobi: B_V = (I - E) A^-1 with the
+    error propagation E = (I - W A)^nu (I - P A_c^-1 P^T A) (I - W A)^nu,
+    W = w D^-1 (the product form, formed densely); B_V is symmetric."""
+    from oracle import amg as oa
+    prob = pb.example1(1e-2, nodes=17, levels=2)
+    A = omg.Hierarchy(2, None, prob.stencil, 2, nodes=17).A[-1]
+    H = oa.AlgebraicHierarchy(A, max_levels=2, coarse_size=8)
+    assert H.levels == 2
+    Sm = oss.jacobi_smoothers(H)
+    n = A.shape[0]
+    Ad = A.toarray()
+    W = H.omegas[1] * np.diag(1.0 / np.diag(Ad))
+    P = H.P[1].toarray()
+    Ac = P.T @ Ad @ P
+    S = np.eye(n) - W @ Ad
+    nu = 3
+    E = np.linalg.matrix_power(S, nu) @ (np.eye(n) - P @ np.linalg.solve(Ac, P.T @ Ad)) @ np.linalg.matrix_power(S, nu)
+    B = (np.eye(n) - E) @ np.linalg.inv(Ad)
+    Bv = np.stack([oss.vcycle(H, Sm, e, nu) for e in np.eye(n)], axis=1)
+    assert np.abs(Bv - B).max() <= 1e-11 * np.abs(B).max()
+    assert np.abs(Bv - Bv.T).max() <= 1e-11 * np.abs(Bv).max()
+    assert np.linalg.eigvalsh(0.5 * (Bv + Bv.T)).min() > 0
