@@ -866,8 +866,8 @@ def bench_algebraic(args):
     unit inflow on the left, conducting fractures k_f = 1e4, k_m = 1; mixed
     precision additive MG-MPCG (m = 5) to rtol 1e-8 on the algebraic
     hierarchy.  Beside it: k_f = 10^-4 .. 10^4 with FP64 MPCG (m = 5 and the
-    longest window, m = 16) and PCG on the algebraic hierarchy and mixed MPCG
-    on the geometric one, and Section 3's
+    longest window, m = 16), PCG and MG(V)-PCG (V(3,3) with damped Jacobi) on
+    the algebraic hierarchy and mixed MPCG on the geometric one, and Section 3's
     Example 1 (160^2 elements) across k_xx on both hierarchies; the oracle's
     iteration counts at the two extreme k_f and at k_xx = 1e-6."""
     import time
@@ -875,6 +875,8 @@ def bench_algebraic(args):
     from oracle import amg as oa
     from oracle import mg as omg
     from oracle import mpcg as ompcg
+    from oracle import pcg as opcg
+    from oracle import ssor as oss
     from paper_2402_12833_gb300 import build as _build
     from paper_2402_12833_gb300 import mpcg as M
     from paper_2402_12833_gb300 import problems as pb
@@ -934,7 +936,7 @@ def bench_algebraic(args):
             rows.append(row)
             continue
         for key, opts in (("fp64_mpcg", dict(m=M_WINDOW)), ("fp64_mpcg_m16", dict(m=16)),
-                          ("fp64_pcg", dict(m=1, sum_columns=1))):
+                          ("fp64_pcg", dict(m=1, sum_columns=1)), ("fp64_vpcg", dict(m=1, vcycle=1, nu=3))):
             H = M.AlgebraicHierarchy(A, stream=stream.cuda_stream, **opts)
             ms, k, st = solve_timed(H, b, x, 1, 1)
             row[key] = {"iterations": k, "ms": ms, "status": st}
@@ -953,8 +955,11 @@ def bench_algebraic(args):
             t2 = time.perf_counter()
             r1 = ompcg.mpcg(A, prob.b, lambda v: O.additive_mg(v)[:, None], m=1, rtol=RTOL, maxit=MAXIT)
             r16 = ompcg.mpcg(A, prob.b, O.mg_columns, m=16, rtol=RTOL, maxit=MAXIT)
-            row["oracle"] = {"mpcg": r5.iters, "mpcg_m16": r16.iters, "pcg": r1.iters, "setup_s": t1 - t0,
-                             "mpcg_solve_s": t2 - t1}
+            O3 = oa.AlgebraicHierarchy(A, nu=3)
+            Sm = oss.jacobi_smoothers(O3)
+            rv = opcg.pcg(A, prob.b, lambda v: oss.vcycle(O3, Sm, v, 3), rtol=RTOL, maxit=MAXIT)
+            row["oracle"] = {"mpcg": r5.iters, "mpcg_m16": r16.iters, "pcg": r1.iters, "vpcg": rv[1],
+                             "setup_s": t1 - t0, "mpcg_solve_s": t2 - t1}
         rows.append(row)
     ex1 = []
     for n_ in (() if args.headline_only else range(0, 8)):
@@ -970,6 +975,10 @@ def bench_algebraic(args):
         H = M.AlgebraicHierarchy(A, stream=stream.cuda_stream, m=1, sum_columns=1)
         ms, k, st = solve_timed(H, b, x, 1, 1)
         r["algebraic_pcg"] = {"iterations": k, "ms": ms}
+        H.close()
+        H = M.AlgebraicHierarchy(A, stream=stream.cuda_stream, m=1, vcycle=1, nu=3)
+        ms, k, st = solve_timed(H, b, x, 1, 1)
+        r["algebraic_vpcg"] = {"iterations": k, "ms": ms}
         H.close()
         if kxx == 1e-6 and not args.no_cpu_baseline:
             O = oa.AlgebraicHierarchy(A)

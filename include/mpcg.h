@@ -131,9 +131,12 @@ typedef struct {
                             ssor_omega) from zero per grid -- Section 3's smoother */
   double ssor_omega;     /* SSOR relaxation, 0 < ssor_omega < 2 (default 1: symmetric
                             Gauss-Seidel) */
-  int vcycle;            /* 1: the multiplicative V(nu, nu) cycle with SSOR as the single
+  int vcycle;            /* 1: the multiplicative V(nu, nu) cycle as the single
                             preconditioned direction (with m = 1: the MG(V)-PCG method
-                            Section 3 compares against); scalar problems, SSOR only */
+                            Section 3 compares against), smoothing with the chosen
+                            smoother (nu SSOR steps, or nu damped-Jacobi sweeps, the
+                            post-smoothing continuing from the corrected iterate);
+                            scalar problems; not with sum_columns */
   void* stream;          /* cudaStream_t */
 } mpcg_options;
 
@@ -215,8 +218,10 @@ int mg_num_problems(const mg_hierarchy* h);
  * positive definite), the exact coarse solve (at most 1024 unknowns), and every operator
  * and transfer applied by the device in sliced ELLPACK form.  Grid indices
  * follow the paper: 0 is the coarsest, mg_num_levels() - 1 the input matrix.
- * Single problems, scalar unknowns; the SSOR smoother, the V-cycle, the
- * learned column and the matrix-free operator are not provided for them.
+ * Single problems, scalar unknowns; the V-cycle (vcycle = 1) smooths with
+ * damped Jacobi there; the SSOR smoother (its colouring needs grid
+ * coordinates), the learned column and the matrix-free operator are not
+ * provided for them.
  */
 typedef struct {
   int n;                 /* rows = columns, >= 1 */
@@ -241,7 +246,7 @@ mpcg_status mg_amg_default_options(mg_amg_options* amg);
  * (host CSR, read during the call only; the matrix must be square with
  * ascending columns, positive diagonal entries and symmetric to 1e-12
  * relative).  amg and opt may be NULL for the defaults; opt->smoother must
- * be MPCG_SMOOTHER_JACOBI and opt->vcycle 0.  On success *out owns device
+ * be MPCG_SMOOTHER_JACOBI.  On success *out owns device
  * memory until mg_hierarchy_destroy; mpcg_solve, mg_corrections,
  * mg_apply_operator and mg_level_size work on it as on a stencil hierarchy
  * (vectors of A.n unknowns in the matrix's order).

@@ -574,12 +574,56 @@ void launch_fine_residual(mg_hierarchy* h, const T* b, const T* x, T* r, double*
     launch_residual<T>(L.g, st_of<T>(L), b, x, r, part, s, xnz);
 }
 
+// One damped-Jacobi sweep on grid j (stored stencil or sparse operator),
+// modes as launch_jacobi: 0 xout = dinv g, 1 two sweeps from zero,
+// 2 xout = xin + dinv (g - A xin).
+template <typename T>
+void jacobi_sweep(mg_hierarchy* h, int j, const T* g, const T* xin, T* xout, int mode, const DevState* state,
+                  cudaStream_t s) {
+  const Level& L = h->lev[j];
+  if (h->algebraic) {
+    const long long G = L.g.G;
+    LAUNCH(h, K_JACOBI, s,
+           launch_ell_jacobi<T>(ell_of<T>(L.eA), dinv_of<T>(L) + G, g + G, xin ? xin + G : nullptr, xout + G, mode,
+                                state, s));
+  } else {
+    LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st_of<T>(L), dinv_of<T>(L), g, xin, xout, mode, state, s));
+  }
+}
+
+// k smoothing steps of the V-cycle on grid j for the right-hand side g, in
+// place on x, from zero when `zero` (x need not be cleared then): SSOR
+// steps, or damped-Jacobi sweeps alternating between x and tmp2[j] (the
+// last one lands in x).
+template <typename T>
+void enqueue_vsmooth(mg_hierarchy* h, Solver<T>& S, int j, const T* g, T* x, int k, bool zero, const DevState* state,
+                     cudaStream_t s) {
+  const Level& L = h->lev[j];
+  if (h->opt.smoother == MPCG_SMOOTHER_SSOR) {
+    if (zero) cudaMemsetAsync(x, 0, sizeof(T) * L.g.cp, s);
+    enqueue_ssor_steps<T>(h, j, g, x, k, state, s);
+    return;
+  }
+  int left = k;
+  if (zero) {
+    jacobi_sweep<T>(h, j, g, nullptr, x, k >= 2 ? 1 : 0, state, s);
+    left -= k >= 2 ? 2 : 1;
+  }
+  T* cur = x;
+  for (; left > 0; --left) {
+    T* dst = cur == x ? S.tmp2[j] : x;
+    jacobi_sweep<T>(h, j, g, cur, dst, 2, state, s);
+    cur = dst;
+  }
+  if (cur != x) cudaMemcpyAsync(x, cur, sizeof(T) * L.g.cp, cudaMemcpyDeviceToDevice, s);
+}
+
 // The multiplicative V(nu, nu) cycle from zero for the right-hand side r,
 // into out (Section 3's MG(V) preconditioner): on every grid from the
-// finest down, nu SSOR steps, the defect and its restriction; the exact
-// coarse solve; on the way up the prolongated correction and nu SSOR
-// steps.  Grid j < J keeps its right-hand side in rlev[j], its
-// iterate in zc[j] and its defect in tmp[j].
+// finest down, nu smoothing steps (SSOR, or damped Jacobi), the defect and
+// its restriction; the exact coarse solve; on the way up the prolongated
+// correction and nu smoothing steps.  Grid j < J keeps its right-hand side
+// in rlev[j], its iterate in zc[j] and its defect in tmp[j].
 template <typename T>
 void enqueue_vcycle(mg_hierarchy* h, Solver<T>& S, const T* r, T* out, const DevState* state, cudaStream_t s) {
   const int J = h->levels - 1;
@@ -588,16 +632,30 @@ void enqueue_vcycle(mg_hierarchy* h, Solver<T>& S, const T* r, T* out, const Dev
   auto it = [&](int j) -> T* { return j == J ? out : S.zc[j]; };
   for (int j = J; j >= 1; --j) {
     const Level& L = h->lev[j];
-    cudaMemsetAsync(it(j), 0, sizeof(T) * L.g.cp, s);
-    enqueue_ssor_steps<T>(h, j, rhs(j), it(j), nu, state, s);
-    LAUNCH(h, K_RESIDUAL, s, launch_defect<T>(L.g, st_of<T>(L), rhs(j), it(j), S.tmp[j], state, s));
-    LAUNCH(h, K_RESTRICT, s, launch_restrict<T>(L.g, h->lev[j - 1].g, S.tmp[j], S.rlev[j - 1], state, s));
+    const GridDesc& gc = h->lev[j - 1].g;
+    enqueue_vsmooth<T>(h, S, j, rhs(j), it(j), nu, true, state, s);
+    if (h->algebraic) {
+      const long long G = L.g.G;
+      LAUNCH(h, K_RESIDUAL, s,
+             launch_ell_defect<T>(ell_of<T>(L.eA), rhs(j) + G, it(j) + G, S.tmp[j] + G, state, s));
+      LAUNCH(h, K_RESTRICT, s,
+             launch_ell_spmm<T>(ell_of<T>(L.eR), S.tmp[j] + G, L.g.cp, S.rlev[j - 1] + gc.G, gc.cp, 1, nullptr, 0,
+                                state, s));
+    } else {
+      LAUNCH(h, K_RESIDUAL, s, launch_defect<T>(L.g, st_of<T>(L), rhs(j), it(j), S.tmp[j], state, s));
+      LAUNCH(h, K_RESTRICT, s, launch_restrict<T>(L.g, gc, S.tmp[j], S.rlev[j - 1], state, s));
+    }
   }
   LAUNCH(h, K_COARSE, s, launch_coarse_solve<T>(h->lev[0].g, h->A0inv, S.rlev[0], it(0), state, s));
   for (int j = 1; j <= J; ++j) {
     const Level& L = h->lev[j];
-    LAUNCH(h, K_PROLONG, s, launch_prolong_add<T>(h->lev[j - 1].g, L.g, it(j - 1), it(j), state, s));
-    enqueue_ssor_steps<T>(h, j, rhs(j), it(j), nu, state, s);
+    const GridDesc& gc = h->lev[j - 1].g;
+    if (h->algebraic)
+      LAUNCH(h, K_PROLONG, s,
+             launch_ell_spmv_add<T>(ell_of<T>(L.eP), it(j - 1) + gc.G, it(j) + L.g.G, state, s));
+    else
+      LAUNCH(h, K_PROLONG, s, launch_prolong_add<T>(gc, L.g, it(j - 1), it(j), state, s));
+    enqueue_vsmooth<T>(h, S, j, rhs(j), it(j), nu, false, state, s);
   }
 }
 
@@ -1055,10 +1113,6 @@ static mpcg_status setup_impl(const mg_operator* ops, int nb, int levels, const 
     set_err("the SSOR smoother and the V-cycle are provided for scalar problems");
     return MPCG_ERR_ARG;
   }
-  if (opt.vcycle && opt.smoother != MPCG_SMOOTHER_SSOR) {
-    set_err("the V-cycle smooths with SSOR (smoother = MPCG_SMOOTHER_SSOR)");
-    return MPCG_ERR_ARG;
-  }
   const long long n0 = make_grid_nodes(A->dim, (q >> (levels - 1)) + 1, faces, ncomp).n;
   if (n0 > 1024) {
     set_err("coarsest grid has %lld unknowns (> 1024); use more levels", n0);
@@ -1215,8 +1269,8 @@ mpcg_status mg_hierarchy_setup_algebraic(const mg_csr* A, const mg_amg_options* 
   if (opt_in) opt = *opt_in;
   else mpcg_default_options(&opt);
   CKS(check_options(opt));
-  if (opt.smoother != MPCG_SMOOTHER_JACOBI || opt.vcycle) {
-    set_err("algebraic hierarchies smooth with damped Jacobi (no SSOR, no V-cycle)");
+  if (opt.smoother != MPCG_SMOOTHER_JACOBI) {
+    set_err("algebraic hierarchies smooth with damped Jacobi (the SSOR colouring needs grid coordinates)");
     return MPCG_ERR_ARG;
   }
   mpcg::amg::Levels H;

@@ -29,9 +29,10 @@ __device__ __forceinline__ T group_sum(T v, int lg) {
   return v;
 }
 
-// Y[:, c] = A X[:, c] for C columns (column pitches ldx, ldy); with ZAZ the
-// per-block partials of X[:, c]^T Y[:, c] (value-major, stride gridDim.x).
-template <typename T, int C, bool ZAZ>
+// Y[:, c] = A X[:, c] (ADD: Y[:, c] += A X[:, c]) for C columns (column
+// pitches ldx, ldy); with ZAZ the per-block partials of X[:, c]^T Y[:, c]
+// (value-major, stride gridDim.x).
+template <typename T, int C, bool ZAZ, bool ADD = false>
 __global__ void __launch_bounds__(kBlock) k_ell_spmm(EllDev<T> A, const T* __restrict__ X, long long ldx,
                                                      T* __restrict__ Y, long long ldy, double* zaz,
                                                      const DevState* state) {
@@ -61,7 +62,8 @@ __global__ void __launch_bounds__(kBlock) k_ell_spmm(EllDev<T> A, const T* __res
     if (r < A.rows && (lane & ((1 << A.lg) - 1)) == 0) {
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        Y[c * ldy + r] = acc[c];
+        if (ADD) Y[c * ldy + r] += acc[c];
+        else Y[c * ldy + r] = acc[c];
         if (ZAZ) zacc[c] = fma(X[c * ldx + r], acc[c], zacc[c]);
       }
     }
@@ -69,9 +71,10 @@ __global__ void __launch_bounds__(kBlock) k_ell_spmm(EllDev<T> A, const T* __res
   if (ZAZ) block_sum_store<T, ZAZ ? C : 1>(zacc, zaz, gridDim.x, blockIdx.x);
 }
 
-// r = b - A x with the partials of |r|^2 and |b|^2; a zero iterate (xnz[0]
-// == 0) gives r = b without reading the matrix.
-template <typename T>
+// r = b - A x with the partials of |r|^2 and |b|^2 (NORMS; without them it
+// is the defect of the V-cycle); a zero iterate (xnz[0] == 0) gives r = b
+// without reading the matrix.
+template <typename T, bool NORMS = true>
 __global__ void __launch_bounds__(kBlock) k_ell_residual(EllDev<T> A, const T* __restrict__ b,
                                                          const T* __restrict__ x, T* __restrict__ r,
                                                          double* part, const int* __restrict__ xnz) {
@@ -100,7 +103,7 @@ __global__ void __launch_bounds__(kBlock) k_ell_residual(EllDev<T> A, const T* _
       sums[1] = fma(bv, bv, sums[1]);
     }
   }
-  block_sum_store<T, 2>(sums, part, gridDim.x, blockIdx.x);
+  if (NORMS) block_sum_store<T, 2>(sums, part, gridDim.x, blockIdx.x);
 }
 
 // Damped Jacobi with dinv = omega / a_ii: mode 0: out = dinv g; mode 1: two
@@ -169,6 +172,24 @@ void launch_ell_residual(const EllDev<T>& A, const T* b, const T* x, T* r, doubl
                          const int* xnz) {
   k_ell_residual<T><<<nblocks, kBlock, 0, s>>>(A, b, x, r, part, xnz);
 }
+
+template <typename T>
+void launch_ell_defect(const EllDev<T>& A, const T* b, const T* x, T* d, const DevState* state, cudaStream_t s) {
+  (void)state;   // every problem of an algebraic hierarchy is the single problem 0
+  k_ell_residual<T, false><<<ell_threads_blocks(A), kBlock, 0, s>>>(A, b, x, d, nullptr, nullptr);
+}
+template void launch_ell_defect<double>(const EllDev<double>&, const double*, const double*, double*, const DevState*,
+                                        cudaStream_t);
+template void launch_ell_defect<float>(const EllDev<float>&, const float*, const float*, float*, const DevState*,
+                                       cudaStream_t);
+
+template <typename T>
+void launch_ell_spmv_add(const EllDev<T>& A, const T* X, T* Y, const DevState* state, cudaStream_t s) {
+  k_ell_spmm<T, 1, false, true><<<ell_threads_blocks(A), kBlock, 0, s>>>(A, X, 0, Y, 0, nullptr, state);
+}
+template void launch_ell_spmv_add<double>(const EllDev<double>&, const double*, double*, const DevState*,
+                                          cudaStream_t);
+template void launch_ell_spmv_add<float>(const EllDev<float>&, const float*, float*, const DevState*, cudaStream_t);
 template void launch_ell_residual<double>(const EllDev<double>&, const double*, const double*, double*, double*, int,
                                           cudaStream_t, const int*);
 template void launch_ell_residual<float>(const EllDev<float>&, const float*, const float*, float*, double*, int,

@@ -40,6 +40,12 @@ void launch_ell_spmm(const EllDev<T>& A, const T* X, long long ldx, T* Y, long l
 template <typename T>
 void launch_ell_residual(const EllDev<T>& A, const T* b, const T* x, T* r, double* part, int nblocks,
                          cudaStream_t s, const int* xnz = nullptr);
+// d = b - A x without norms (V-cycle defect)
+template <typename T>
+void launch_ell_defect(const EllDev<T>& A, const T* b, const T* x, T* d, const DevState* state, cudaStream_t s);
+// Y += A X, one column (V-cycle prolongation of the coarse correction)
+template <typename T>
+void launch_ell_spmv_add(const EllDev<T>& A, const T* X, T* Y, const DevState* state, cudaStream_t s);
 // damped Jacobi (dinv = omega / a_ii), modes as launch_jacobi
 template <typename T>
 void launch_ell_jacobi(const EllDev<T>& A, const T* dinv, const T* g, const T* sin, T* out, int mode,

@@ -18,6 +18,7 @@ torch = pytest.importorskip("torch")
 from oracle import amg as oa
 from oracle import mpcg as ompcg
 from oracle import pcg as opcg
+from oracle import ssor as oss
 from paper_2402_12833_gb300 import problems as pb
 
 pytestmark = pytest.mark.gpu
@@ -295,3 +296,25 @@ def test_isolated_unknowns_are_outside_every_aggregate(M):
     agg = M.mg_amg_aggregates(H.h, H.levels - 1)
     iso = np.arange(0, 40) * 25
     assert np.all(agg[iso] == -1) and np.all(np.delete(agg, iso) >= 0)
+
+
+@pytest.mark.parametrize("name", ["example1_1e-6_81", "fracture_129_conducting", "isolated_unknowns"])
+@pytest.mark.parametrize("nu", [2, 3])
+def test_jacobi_vcycle_matches_oracle(M, name, nu):
+    """MG(V)-PCG on the algebraic hierarchy: the V(nu, nu) cycle with the
+    grids' damped-Jacobi weights to 1e-12 and the PCG solve (counts +-1)."""
+    prob, A, amg = _case(name)
+    O = _oracle(A, amg)
+    H = _gpu(M, A, amg, nu=nu, vcycle=1, m=1)
+    Sm = oss.jacobi_smoothers(O)
+    r = np.random.default_rng(nu).standard_normal(A.shape[0])
+    Z = torch.zeros((1, A.shape[0]), dtype=torch.float64, device="cuda")
+    M.mg_corrections(H.h, torch.from_numpy(r).cuda(), Z)
+    ref = oss.vcycle(O, Sm, r, nu)
+    assert np.abs(Z.cpu().numpy()[0] - ref).max() <= 1e-12 * np.abs(ref).max()
+    b = torch.from_numpy(prob.b).cuda()
+    x = torch.zeros_like(b)
+    st, k, _, _ = H.solve(b, x, rtol=1e-8, maxit=3000)
+    xr, kr, _ = opcg.pcg(A, prob.b, lambda v: oss.vcycle(O, Sm, v, nu), rtol=1e-8, maxit=3000)
+    assert st == M.MPCG_OK and abs(k - kr) <= 1, (k, kr)
+    assert np.linalg.norm(A @ x.cpu().numpy() - prob.b) <= 1e-8 * np.linalg.norm(prob.b)

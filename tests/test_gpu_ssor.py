@@ -119,7 +119,7 @@ def test_mixed_precision_vcycle_reaches_tolerance(M):
 def test_options_are_checked(M):
     prob = CASES["kappa2d_33"]()
     st = torch.from_numpy(prob.stencil).cuda()
-    for bad in (dict(vcycle=1), dict(smoother=2), dict(smoother=1, ssor_omega=2.0),
+    for bad in (dict(vcycle=1, sum_columns=1), dict(smoother=2), dict(smoother=1, ssor_omega=2.0),
                 dict(smoother=1, vcycle=1, sum_columns=1)):
         with pytest.raises(M.MpcgError):
             M.Hierarchy(st, 2, 33, prob.levels, **bad)
@@ -149,3 +149,26 @@ def test_ssor_relaxation_factor(M, omega):
     M.mg_corrections(Hv.h, torch.from_numpy(r).cuda(), Zv)
     refv = oss.vcycle(O, Ss, r, 3)
     assert np.abs(Zv.cpu().numpy()[0] - refv).max() <= 1e-12 * np.abs(refv).max()
+
+
+@pytest.mark.parametrize("name", ["kappa2d_33", "kappa3d_17", "example1_1e-3"])
+def test_jacobi_vcycle_matches_oracle(M, name):
+    """The V(nu, nu) cycle with damped-Jacobi smoothing (nu = 3, odd: the
+    post-smoothing ends in the ping-pong buffer and is copied back) and the
+    MG(V)-PCG solve against the oracle."""
+    prob = CASES[name]()
+    st = torch.from_numpy(np.ascontiguousarray(prob.stencil)).cuda()
+    H = M.Hierarchy(st, prob.dim, prob.nodes, prob.levels, faces=prob.faces, nu=3, vcycle=1, m=1)
+    O = omg.Hierarchy(prob.dim, None, prob.stencil, prob.levels, nodes=prob.nodes, faces=prob.faces)
+    Sm = oss.jacobi_smoothers(O)
+    r = np.random.default_rng(3).standard_normal(prob.n)
+    Z = torch.zeros((1, prob.n), dtype=torch.float64, device="cuda")
+    M.mg_corrections(H.h, torch.from_numpy(r).cuda(), Z)
+    ref = oss.vcycle(O, Sm, r, 3)
+    assert np.abs(Z.cpu().numpy()[0] - ref).max() <= 1e-12 * np.abs(ref).max()
+    b = torch.from_numpy(prob.b).cuda()
+    x = torch.zeros_like(b)
+    st_, k, _, _ = H.solve(b, x, rtol=1e-8, maxit=2000)
+    xr, kr, _ = opcg.pcg(O.A[-1], prob.b, lambda v: oss.vcycle(O, Sm, v, 3), rtol=1e-8, maxit=2000)
+    assert st_ == M.MPCG_OK and abs(k - kr) <= 1, (k, kr)
+    assert np.linalg.norm(x.cpu().numpy() - xr) <= 1e-10 * np.linalg.norm(xr)
