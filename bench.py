@@ -431,11 +431,16 @@ def bench_ours(args):
         xh[:] = 0.0
         M.mpcg_solve(H["mixed"].h, bh, xh, RTOL, MAXIT, histories=False)
     barrier()
-    t0 = time.perf_counter()
+    # each step times the API call alone (H2D of b and x0, the solve, D2H of
+    # x); resetting x0 to zero in the pinned host buffer is input preparation
+    # and stays outside
+    e2e_total = 0.0
     for _ in range(args.steps):
         xh[:] = 0.0
+        t0 = time.perf_counter()
         M.mpcg_solve(H["mixed"].h, bh, xh, RTOL, MAXIT, histories=False)
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+        e2e_total += time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_total / args.steps)
     barrier()
 
     cpu = None
