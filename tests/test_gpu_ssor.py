@@ -35,6 +35,9 @@ CASES = {
     "kappa2d_33_faces": lambda: pb.diffusion_faces(2, 33, 0x9, rhs_seed=3, kappa_seed=4),
     "kappa3d_17": lambda: pb.diffusion_macro(3, 17, 4, rhs="normal", rhs_seed=6),
     "example1_1e-3": lambda: pb.example1(1e-3, nodes=41, levels=3),
+    # larger fine grids (16,384 and 32,768 padded points)
+    "kappa2d_129": lambda: pb.diffusion_macro(2, 129, 6, rhs="normal", rhs_seed=8),
+    "kappa3d_33": lambda: pb.diffusion_macro(3, 33, 7, rhs="normal", rhs_seed=9),
 }
 
 
