@@ -224,7 +224,7 @@ int mg_num_problems(const mg_hierarchy* h);
  * provided for them.
  */
 typedef struct {
-  int n;                 /* rows = columns, >= 1 */
+  int n;                 /* rows = columns, 1 .. 2^30 */
   const int* rowptr;     /* n + 1 offsets into col/val, rowptr[0] = 0 (host) */
   const int* col;        /* column of each entry, ascending within a row (host) */
   const double* val;     /* value of each entry (host) */

@@ -1238,6 +1238,10 @@ static mpcg_status amg_build_checked(const mg_csr* A, const mg_amg_options* amg_
             MPCG_MAX_COLS);
     return MPCG_ERR_ARG;
   }
+  if (A->n > (1 << 30)) {
+    set_err("matrix: at most 2^30 rows (the flat grid pitch is a 32-bit int)");
+    return MPCG_ERR_ARG;
+  }
   std::string err;
   if (!mpcg::amg::check_input(A->n, A->rowptr, A->col, A->val, err)) {
     set_err("%s", err.c_str());
