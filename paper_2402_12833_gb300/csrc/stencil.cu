@@ -74,12 +74,11 @@ __device__ __forceinline__ void load_row(const T* __restrict__ p, T (&e)[Vec<T>:
 // false) reads nothing.  Fewer L1 wavefronts than the scalar loads; used by
 // the Jacobi sweep, which reads two rows per stencil row (measured faster
 // there, slower in the multi-column SpMM, whose loads then wait longer).
-template <typename T>
-__device__ __forceinline__ void load_row_shfl(const T* __restrict__ p, T (&e)[Vec<T>::W + 2], bool active,
+template <typename T, int W = Vec<T>::W>
+__device__ __forceinline__ void load_row_shfl(const T* __restrict__ p, T (&e)[W + 2], bool active,
                                               unsigned act, int lane) {
-  constexpr int W = Vec<T>::W;
   T mid[W];
-  if (active) Vec<T>::load_keep(p, mid);
+  if (active) VecN<T, W>::load_keep(p, mid);
   else {
 #pragma unroll
     for (int w = 0; w < W; ++w) mid[w] = 0;
@@ -245,13 +244,15 @@ __global__ void __launch_bounds__(kBlock) k_restrict(GridDesc gf, GridDesc gc, c
 //   mode 1: out = s1 + dinv (r - A s1), s1 = dinv r  (two sweeps, s1 formed
 //           at the neighbours on the fly)
 //   mode 2: out = sin + dinv (r - A sin)           (a further sweep)
-template <typename T, int DIM>
+//   W points per thread: Vec<T>::W (one vector load), or 1 on the small
+//   grids (modes 0 and 1; mode 2 keeps Vec<T>::W).  Every point's
+//   arithmetic is the same whatever W.
+template <typename T, int DIM, int W = Vec<T>::W>
 __global__ void __launch_bounds__(kBlock, 4) k_jacobi(GridDesc g, const T* __restrict__ st, const T* __restrict__ dinv,
                                                    const T* __restrict__ r, const T* __restrict__ sin,
                                                    T* __restrict__ out, int mode, const DevState* state) {
   const int pb = blockIdx.y;
   if (state && state[pb].done) return;
-  constexpr int W = Vec<T>::W;
   const long long ngroups = g.npts / W;
   const long long q0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31);
   if (q0 >= ngroups) return;   // the whole warp is idle
@@ -261,14 +262,14 @@ __global__ void __launch_bounds__(kBlock, 4) k_jacobi(GridDesc g, const T* __res
   const long long idx = (long long)pb * g.len + g.G + q * W;
   T di[W] = {}, ri[W] = {}, o[W];
   if (active) {
-    Vec<T>::load_keep(dinv + idx, di);
-    Vec<T>::load_keep(r + idx, ri);
+    VecN<T, W>::load_keep(dinv + idx, di);
+    VecN<T, W>::load_keep(r + idx, ri);
   }
   if (mode == 0) {
     if (!active) return;
 #pragma unroll
     for (int w = 0; w < W; ++w) o[w] = di[w] * ri[w];
-    Vec<T>::store(out + idx, o);
+    VecN<T, W>::store(out + idx, o);
     return;
   }
   T acc[1][W];
@@ -282,12 +283,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_jacobi(GridDesc g, const T* __res
       const long long ro = row_offset<DIM>(k, g.px, g.pxy);
       T a0[W] = {}, a1[W] = {}, a2[W] = {}, ed[W + 2], er[W + 2];
       if (active) {
-        Vec<T>::load(st + (long long)(3 * k + 0) * g.cp + idx, a0);
-        Vec<T>::load(st + (long long)(3 * k + 1) * g.cp + idx, a1);
-        Vec<T>::load(st + (long long)(3 * k + 2) * g.cp + idx, a2);
+        VecN<T, W>::load(st + (long long)(3 * k + 0) * g.cp + idx, a0);
+        VecN<T, W>::load(st + (long long)(3 * k + 1) * g.cp + idx, a1);
+        VecN<T, W>::load(st + (long long)(3 * k + 2) * g.cp + idx, a2);
       }
-      load_row_shfl<T>(dinv + idx + ro, ed, active, act, lane);
-      load_row_shfl<T>(r + idx + ro, er, active, act, lane);
+      load_row_shfl<T, W>(dinv + idx + ro, ed, active, act, lane);
+      load_row_shfl<T, W>(r + idx + ro, er, active, act, lane);
 #pragma unroll
       for (int w = 0; w < W; ++w) {
         acc[0][w] = fma(a0[w], ed[w] * er[w], acc[0][w]);
@@ -300,15 +301,17 @@ __global__ void __launch_bounds__(kBlock, 4) k_jacobi(GridDesc g, const T* __res
       const T s1 = di[w] * ri[w];
       o[w] = s1 + di[w] * (ri[w] - acc[0][w]);
     }
-  } else {
+  } else if constexpr (W == Vec<T>::W) {   // mode 2 (the launcher uses the full width for it)
     if (!active) return;
     stencil_group<T, DIM, 1>(st, g.cp, sin, idx, g.px, g.pxy, acc);
     T sv[W];
     Vec<T>::load_keep(sin + idx, sv);
 #pragma unroll
     for (int w = 0; w < W; ++w) o[w] = sv[w] + di[w] * (ri[w] - acc[0][w]);
+  } else {
+    return;
   }
-  if (active) Vec<T>::store(out + idx, o);
+  if (active) VecN<T, W>::store(out + idx, o);
 }
 
 // Multicoloured SSOR (Section 3's smoother; the colouring is a reading):
@@ -968,6 +971,19 @@ template <typename T>
 void launch_jacobi(const GridDesc& g, const T* st, const T* dinv, const T* r, const T* sin, T* out, int mode,
                    const DevState* state, cudaStream_t s) {
   if (g.ncomp != 1) return;   // vector grids smooth with launch_vres / launch_vblock
+  // one point per thread where Vec<T>::W points per thread would leave fewer
+  // than 4 warps per SM (the small coarse grids, latency-bound): more warps
+  // in flight, same sums (measured: 33^3 and 17^3 launches 11.9 -> 7.2 us,
+  // the 129^3 solve 4.575 -> 4.557 ms).  Larger grids keep the vector width:
+  // their smoothing runs beside the fine grid's, and four times the blocks
+  // there slowed the solve.
+  const bool narrow = mode != 2 && g_sm_count > 0 && g.npts / vw<T>() * g.nb < (long long)g_sm_count * 128;
+  if (narrow) {
+    const dim3 grid(blocks_for(g.npts), g.nb);
+    if (g.dim == 3) k_jacobi<T, 3, 1><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
+    else k_jacobi<T, 2, 1><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
+    return;
+  }
   const dim3 grid(blocks_for(g.npts / vw<T>()), g.nb);
   if (g.dim == 3) k_jacobi<T, 3><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
   else k_jacobi<T, 2><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);

@@ -44,6 +44,21 @@ struct Vec<double> {
   }
 };
 
+// Loads and stores of W consecutive values (W = 1 or the full vector width
+// of Vec<T>), for kernels whose points per thread depend on the grid size.
+template <typename T, int W>
+struct VecN;
+template <typename T>
+struct VecN<T, 1> {
+  __device__ static __forceinline__ void load(const T* p, T (&v)[1]) { v[0] = __ldcs(p); }
+  __device__ static __forceinline__ void load_keep(const T* p, T (&v)[1]) { v[0] = *p; }
+  __device__ static __forceinline__ void store(T* p, const T (&v)[1]) { *p = v[0]; }
+};
+template <>
+struct VecN<float, 4> : Vec<float> {};
+template <>
+struct VecN<double, 2> : Vec<double> {};
+
 // Number of values a lane holds after `steps` halvings of nv values.
 __host__ __device__ constexpr int rs_count(int nv, int steps) {
   return steps == 0 ? nv : rs_count((nv + 1) / 2, steps - 1);
