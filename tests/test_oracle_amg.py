@@ -196,3 +196,67 @@ def test_level_smoothers_stay_positive_definite():
         lam.append(np.linalg.eigvalsh(At).max() if H.A[j].shape[0] <= 2500 else 2.0)
         assert H.omegas[j] * lam[-1] <= 4.0 / 3.0 + 1e-12, j
     assert max(lam) * 2.0 / 3.0 > 2.0 * 0.9    # the fixed weight would come close to, or pass, 2
+
+
+# ---------------------------------------------------------------- planted mistakes
+# Each plants a plausible mistake in the oracle (on the CPU) and shows that a
+# pin above fails.
+
+def test_planted_smoothing_sign_fails_energy_pin(monkeypatch):
+    def plus(A, T, w=4.0 / 3.0):          # P = T + s D^-1 A T (wrong sign)
+        T = sp.csr_matrix(T)
+        A = sp.csr_matrix(A)
+        s = w / oa.gershgorin_bound(A)
+        return sp.csr_matrix(T + sp.diags(s / A.diagonal()) @ (A @ T))
+    monkeypatch.setattr(oa, "smoothed_prolongator", plus)
+    with pytest.raises(AssertionError):
+        test_smoothed_prolongator_keeps_constants_and_lowers_energy()
+
+
+def test_planted_unsymmetrised_strength_fails_hand_pin(monkeypatch):
+    real = oa.strength
+
+    def directed(A, theta):               # forgets the symmetrisation
+        A = sp.csr_matrix(A)
+        n = A.shape[0]
+        rows = np.repeat(np.arange(n), np.diff(A.indptr))
+        c = np.where(rows != A.indices, -A.data, -np.inf)
+        m = np.full(n, -np.inf)
+        np.maximum.at(m, rows, c)
+        keep = (c > 0.0) & (c >= theta * m[rows])
+        S = sp.csr_matrix((np.ones(int(keep.sum()), dtype=bool), (rows[keep], A.indices[keep])), shape=(n, n))
+        S.sort_indices()
+        return S
+    monkeypatch.setattr(oa, "strength", directed)
+    with pytest.raises(AssertionError):
+        test_strength_hand_examples()
+    monkeypatch.setattr(oa, "strength", real)
+
+
+def test_planted_missing_second_pass_fails_path_pin(monkeypatch):
+    def one_pass(S):
+        n = S.shape[0]
+        nbrs = [S.indices[S.indptr[i]:S.indptr[i + 1]] for i in range(n)]
+        agg = np.full(n, -1, dtype=np.int64)
+        na = 0
+        for i in range(n):
+            N = nbrs[i]
+            if len(N) == 0 or agg[i] >= 0 or np.any(agg[N] >= 0):
+                continue
+            agg[i] = na
+            agg[N] = na
+            na += 1
+        return agg, na
+    monkeypatch.setattr(oa, "aggregate", one_pass)
+    with pytest.raises(AssertionError):
+        test_aggregation_of_paths()
+
+
+def test_planted_unnormalised_tentative_fails_orthonormality_pin(monkeypatch):
+    def ones(agg, na):                    # T[i, a] = 1 instead of 1/sqrt(|a|)
+        n = agg.shape[0]
+        inside = agg >= 0
+        return sp.csr_matrix((np.ones(int(inside.sum())), (np.arange(n)[inside], agg[inside])), shape=(n, na))
+    monkeypatch.setattr(oa, "tentative", ones)
+    with pytest.raises(AssertionError):
+        test_tentative_prolongator()

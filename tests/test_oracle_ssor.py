@@ -172,3 +172,28 @@ def test_jacobi_vcycle_is_the_two_grid_error_propagation():
     assert np.abs(Bv - B).max() <= 1e-11 * np.abs(B).max()
     assert np.abs(Bv - Bv.T).max() <= 1e-11 * np.abs(Bv).max()
     assert np.linalg.eigvalsh(0.5 * (Bv + Bv.T)).min() > 0
+
+
+# ---------------------------------------------------------------- planted mistakes
+# Plants in the oracle (on the CPU) that a pin above must catch.
+
+def test_planted_forward_only_steps_fail_symmetry_pin(monkeypatch):
+    def forward_twice(self, b, x, k):     # the "backward" sweep repeats the forward order
+        fwd = list(range(self.K))
+        for _ in range(k):
+            self.sweep(b, x, fwd)
+            self.sweep(b, x, fwd)
+        return x
+    monkeypatch.setattr(oss.SSOR, "steps", forward_twice)
+    with pytest.raises(AssertionError):
+        test_ssor_steps_and_vcycle_are_symmetric(list(TINY)[0])
+
+
+def test_planted_relaxation_squared_fails_splitting_pin(monkeypatch):
+    def sweep_w2(self, b, x, order):      # omega^2 instead of omega in the update
+        for c in order:
+            i = self.idx[c]
+            x[i] += self.omega ** 2 * (self.dinv[c] @ (b[i] - self.rows[c] @ x))
+    monkeypatch.setattr(oss.SSOR, "sweep", sweep_w2)
+    with pytest.raises(AssertionError):
+        test_one_step_from_zero_is_the_ssor_splitting("kappa2d_9", 1.3)
