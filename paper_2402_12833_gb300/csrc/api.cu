@@ -181,8 +181,6 @@ struct Profiler {
     pending.push_back({cls, used});
     used += 2;
   }
-  // launches beyond the first inside one LAUNCH (a multi-kernel step)
-  void extra(long long k) { *(target ? target : &live) += k; }
   void end(cudaStream_t s) {
     if (on) cudaEventRecord(pool[pending.back().second + 1], s);
   }
