@@ -237,7 +237,7 @@ typedef struct {
   int coarse_size;       /* stop at <= this many unknowns, 1..1024; default 256 */
 } mg_amg_options;
 
-enum { MPCG_AMG_A = 0, MPCG_AMG_P = 1 };
+enum { MPCG_AMG_A = 0, MPCG_AMG_P = 1, MPCG_AMG_R = 2 };
 
 mpcg_status mg_amg_default_options(mg_amg_options* amg);
 
@@ -288,6 +288,20 @@ long long mg_amg_host_size(const mg_amg_host* a, int level);
 long long mg_amg_host_nnz(const mg_amg_host* a, int level, int which);
 mpcg_status mg_amg_host_aggregates(const mg_amg_host* a, int level, int* agg);
 mpcg_status mg_amg_host_get(const mg_amg_host* a, int level, int which, int* rowptr, int* col, double* val);
+/*
+ * The sliced-ELLPACK form the device applies (one warp per slice of 32 / g
+ * rows, g = 2^lg lanes per row: the largest power of two <= 32 with
+ * g <= mean row length / 6; slot k of lane l of slice s at
+ * sptr[s] + 32 k + l, lane l serving row l / g of the slice and its entries
+ * l mod g, l mod g + g, ...; padding column 0, value 0) of A_level, P_level
+ * or R_level = P_level^T (which = MPCG_AMG_R, level >= 1).
+ * mg_amg_host_ell_entries returns the stored entries (padding included), or
+ * -1; mg_amg_host_ell writes lg, the slice count, nslices + 1 offsets and
+ * that many columns and values.
+ */
+long long mg_amg_host_ell_entries(const mg_amg_host* a, int level, int which);
+mpcg_status mg_amg_host_ell(const mg_amg_host* a, int level, int which, int* lg, int* nslices, int* sptr, int* col,
+                            double* val);
 void mg_amg_host_destroy(mg_amg_host* a);
 /*
  * Problems of uneven size: one batched hierarchy per grid size (nclass of

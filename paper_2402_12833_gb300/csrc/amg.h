@@ -57,5 +57,17 @@ void multiply(const Csr& A, const Csr& B, Csr& C);
 void smoothed_prolongator(const Csr& A, const Csr& T, double w, Csr& P);
 void build(const Csr& A, const Params& p, Levels& out);
 
+// Sliced ELLPACK of a CSR matrix, the layout the device kernels read (one
+// warp per slice, g = 2^lg lanes per row, slot k of lane l of slice s at
+// sptr[s] + 32 k + l; padding: column 0, value 0).  Lanes per row: the
+// largest power of two g <= 32 with g <= (mean row length) / 6.  Returns
+// false when the stored entries would not fit 32-bit offsets.
+struct Ell {
+  int rows = 0, cols = 0, nslices = 0, lg = 0;
+  std::vector<int> sptr, col;
+  std::vector<double> val;
+};
+bool ell_layout(const Csr& M, Ell& E);
+
 }  // namespace amg
 }  // namespace mpcg

@@ -290,5 +290,35 @@ void build(const Csr& A, const Params& p, Levels& out) {
   }
 }
 
+bool ell_layout(const Csr& M, Ell& E) {
+  E.rows = M.rows;
+  E.cols = M.cols;
+  const double mean = M.rows ? (double)M.nnz() / M.rows : 0.0;
+  E.lg = 0;
+  while (E.lg < 5 && (double)(2 << E.lg) <= mean / 6.0) ++E.lg;
+  const int g = 1 << E.lg, rps = 32 >> E.lg;   // lanes per row, rows per slice
+  E.nslices = (M.rows + rps - 1) / rps;
+  E.sptr.assign((size_t)E.nslices + 1, 0);
+  long long total = 0;
+  for (int sl = 0; sl < E.nslices; ++sl) {
+    int w = 0;
+    for (int r = rps * sl; r < rps * sl + rps && r < M.rows; ++r) w = std::max(w, (M.ptr[r + 1] - M.ptr[r] + g - 1) / g);
+    total += 32LL * w;
+    if (total >= (1LL << 31)) return false;
+    E.sptr[(size_t)sl + 1] = (int)total;
+  }
+  E.col.assign((size_t)total, 0);
+  E.val.assign((size_t)total, 0.0);
+  for (int sl = 0; sl < E.nslices; ++sl)
+    for (int r = rps * sl; r < rps * sl + rps && r < M.rows; ++r)
+      for (int e = M.ptr[r]; e < M.ptr[r + 1]; ++e) {
+        const int idx = e - M.ptr[r];   // entry idx of the row: slot idx / g of lane (r - rps sl) g + idx mod g
+        const size_t k = (size_t)E.sptr[sl] + 32 * (size_t)(idx / g) + (size_t)((r - rps * sl) * g + idx % g);
+        E.col[k] = M.col[e];
+        E.val[k] = M.val[e];
+      }
+  return true;
+}
+
 }  // namespace amg
 }  // namespace mpcg

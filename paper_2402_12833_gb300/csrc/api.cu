@@ -881,46 +881,26 @@ mpcg_status build_f32(mg_hierarchy* h) {
   return MPCG_OK;
 }
 
-// Sliced ELLPACK (EllDev layout) of a host CSR matrix, uploaded to the device.
-// Lanes per row: the largest power of two g <= 32 with g <= (mean row
-// length) / 6, so that every lane still takes about six entries or more.
+// Sliced ELLPACK (EllDev layout, amg::ell_layout) of a host CSR matrix,
+// uploaded to the device.
 mpcg_status upload_ell(mg_hierarchy* h, const mpcg::amg::Csr& M, EllLevel& E, cudaStream_t s) {
-  E.rows = M.rows;
-  E.cols = M.cols;
-  const double mean = M.rows ? (double)M.nnz() / M.rows : 0.0;
-  E.lg = 0;
-  while (E.lg < 5 && (double)(2 << E.lg) <= mean / 6.0) ++E.lg;
-  const int g = 1 << E.lg, rps = 32 >> E.lg;   // lanes per row, rows per slice
-  E.nslices = (M.rows + rps - 1) / rps;
-  std::vector<int> sptr((size_t)E.nslices + 1, 0);
-  long long total = 0;
-  for (int sl = 0; sl < E.nslices; ++sl) {
-    int w = 0;
-    for (int r = rps * sl; r < rps * sl + rps && r < M.rows; ++r) w = std::max(w, (M.ptr[r + 1] - M.ptr[r] + g - 1) / g);
-    total += 32LL * w;
-    if (total >= (1LL << 31)) {
-      set_err("sparse matrix too large for 32-bit entry offsets");
-      return MPCG_ERR_ARG;
-    }
-    sptr[(size_t)sl + 1] = (int)total;
+  mpcg::amg::Ell L;
+  if (!mpcg::amg::ell_layout(M, L)) {
+    set_err("sparse matrix too large for 32-bit entry offsets");
+    return MPCG_ERR_ARG;
   }
-  E.nent = total;
-  std::vector<int> col((size_t)total, 0);
-  std::vector<double> val((size_t)total, 0.0);
-  for (int sl = 0; sl < E.nslices; ++sl)
-    for (int r = rps * sl; r < rps * sl + rps && r < M.rows; ++r)
-      for (int e = M.ptr[r]; e < M.ptr[r + 1]; ++e) {
-        const int idx = e - M.ptr[r];   // entry idx of the row: slot idx / g of lane (r - rps sl) g + idx mod g
-        const size_t k = (size_t)sptr[sl] + 32 * (size_t)(idx / g) + (size_t)((r - rps * sl) * g + idx % g);
-        col[k] = M.col[e];
-        val[k] = M.val[e];
-      }
-  CKS(h->mem.get(&E.sptr, sptr.size(), s));
-  CKS(h->mem.get(&E.col, col.size(), s));
-  CKS(h->mem.get(&E.v64, val.size(), s));
-  if (cudaMemcpyAsync(E.sptr, sptr.data(), sizeof(int) * sptr.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(E.col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(E.v64, val.data(), sizeof(double) * val.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+  E.rows = L.rows;
+  E.cols = L.cols;
+  E.nslices = L.nslices;
+  E.lg = L.lg;
+  E.nent = (long long)L.col.size();
+  CKS(h->mem.get(&E.sptr, L.sptr.size(), s));
+  CKS(h->mem.get(&E.col, L.col.size(), s));
+  CKS(h->mem.get(&E.v64, L.val.size(), s));
+  if (cudaMemcpyAsync(E.sptr, L.sptr.data(), sizeof(int) * L.sptr.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(E.col, L.col.data(), sizeof(int) * L.col.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(E.v64, L.val.data(), sizeof(double) * L.val.size(), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     set_err("upload of a sparse operator failed: %s", cudaGetErrorString(cudaGetLastError()));
     return MPCG_ERR_CUDA;
@@ -1496,6 +1476,41 @@ mpcg_status mg_amg_host_get(const mg_amg_host* a, int level, int which, int* row
   std::copy(M->ptr.begin(), M->ptr.end(), rowptr);
   std::copy(M->col.begin(), M->col.end(), col);
   std::copy(M->val.begin(), M->val.end(), val);
+  return MPCG_OK;
+}
+
+static bool host_ell(const mg_amg_host* a, int level, int which, mpcg::amg::Ell& E) {
+  mpcg::amg::Csr Rt;
+  const mpcg::amg::Csr* M = nullptr;
+  if (which == MPCG_AMG_R) {
+    const mpcg::amg::Csr* P = host_matrix(a, level, MPCG_AMG_P);
+    if (!P) return false;
+    mpcg::amg::transpose(*P, Rt);
+    M = &Rt;
+  } else {
+    M = host_matrix(a, level, which);
+  }
+  return M && mpcg::amg::ell_layout(*M, E);
+}
+
+long long mg_amg_host_ell_entries(const mg_amg_host* a, int level, int which) {
+  mpcg::amg::Ell E;
+  return host_ell(a, level, which, E) ? (long long)E.col.size() : -1;
+}
+
+mpcg_status mg_amg_host_ell(const mg_amg_host* a, int level, int which, int* lg, int* nslices, int* sptr, int* col,
+                            double* val) {
+  g_err.clear();
+  mpcg::amg::Ell E;
+  if (!lg || !nslices || !sptr || !col || !val || !host_ell(a, level, which, E)) {
+    set_err("need a host hierarchy, a valid level/matrix and output arrays");
+    return MPCG_ERR_ARG;
+  }
+  *lg = E.lg;
+  *nslices = E.nslices;
+  std::copy(E.sptr.begin(), E.sptr.end(), sptr);
+  std::copy(E.col.begin(), E.col.end(), col);
+  std::copy(E.val.begin(), E.val.end(), val);
   return MPCG_OK;
 }
 

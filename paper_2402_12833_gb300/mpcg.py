@@ -32,6 +32,7 @@ MPCG_MAX_COLS = 12
 MPCG_MAX_WINDOW = 16
 MPCG_AMG_A = 0
 MPCG_AMG_P = 1
+MPCG_AMG_R = 2
 
 
 class MpcgError(RuntimeError):
@@ -108,6 +109,9 @@ _SIGS = {
     "mg_amg_host_aggregates": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "mg_amg_host_get": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mg_amg_host_destroy": (None, [C.c_void_p]),
+    "mg_amg_host_ell_entries": (C.c_longlong, [C.c_void_p, C.c_int, C.c_int]),
+    "mg_amg_host_ell": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_void_p,
+                                  C.c_void_p, C.c_void_p]),
     "mpcg_solve_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p),
                                      C.POINTER(C.c_void_p), C.c_double, C.c_int, C.POINTER(C.c_void_p)]),
     "mg_learned_num_params": (C.c_int, []),
@@ -434,6 +438,22 @@ class AmgHost:
         va = np.empty(nnz, dtype=np.float64)
         _check(load().mg_amg_host_get(self.h, level, which, rp.ctypes.data, ci.ctypes.data, va.ctypes.data))
         return rp, ci, va
+
+    def ell(self, level: int, which: int):
+        """(lg, sptr, col, val): the sliced-ELLPACK arrays the device reads for
+        A_level, P_level or R_level (MPCG_AMG_R)."""
+        ne = load().mg_amg_host_ell_entries(self.h, level, which)
+        if ne < 0:
+            raise MpcgError(MPCG_ERR_ARG, "bad level or matrix")
+        rows = {MPCG_AMG_A: self.size(level), MPCG_AMG_P: self.size(level),
+                MPCG_AMG_R: self.size(level - 1) if level >= 1 else 0}[which]
+        lg, ns = C.c_int(), C.c_int()
+        sptr = np.empty(rows + 2, dtype=np.int32)     # >= nslices + 1 for any lane count
+        col = np.empty(ne, dtype=np.int32)
+        val = np.empty(ne, dtype=np.float64)
+        _check(load().mg_amg_host_ell(self.h, level, which, C.byref(lg), C.byref(ns), sptr.ctypes.data,
+                                      col.ctypes.data, val.ctypes.data))
+        return lg.value, sptr[:ns.value + 1].copy(), col, val
 
     def close(self):
         if self.h:
