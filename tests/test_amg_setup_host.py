@@ -77,3 +77,25 @@ def test_host_setup_refuses_bad_input(M):
     with pytest.raises(M.MpcgError):
         H.aggregates(0)
     assert M.load().mg_amg_host_size(H.h, 5) == -1
+
+
+def test_device_setup_refuses_bad_requests_before_any_cuda_call(M):
+    """mg_hierarchy_setup_algebraic checks options and the matrix before it
+    touches a device, so its refusals hold on a machine without a GPU."""
+    A = pb.stencil_csr(pb.example1(1.0, nodes=33, levels=2))
+    cases = [
+        (A, {}, dict(smoother=M.MPCG_SMOOTHER_SSOR)),   # SSOR needs grid coordinates
+        (A, dict(theta=2.0), {}),
+        (A, dict(coarse_size=5000), {}),
+        (A, {}, dict(m=0)),
+        (A, {}, dict(vcycle=1, sum_columns=1)),
+    ]
+    for mat, amg, opts in cases:
+        with pytest.raises(M.MpcgError) as e:
+            M.AlgebraicHierarchy(mat, **amg, **opts)
+        assert e.value.status == M.MPCG_ERR_ARG
+    bad = A.tolil()
+    bad[1, 0] = 5.0 * bad[1, 0]
+    with pytest.raises(M.MpcgError) as e:
+        M.AlgebraicHierarchy(bad.tocsr())
+    assert e.value.status == M.MPCG_ERR_ARG and "symmetric" in str(e.value)
