@@ -361,6 +361,19 @@ mpcg_status mpcg_solve_profiled(mg_hierarchy* h, const double* b, double* x, dou
 long long mg_last_launches(const mg_hierarchy* h);
 
 /*
+ * Counters of the last solve on h for problem `problem` of the batch (0 for
+ * a single problem), read from the device after the call (synchronises the
+ * hierarchy's stream).  out[0] = x updates, out[1] = termination (0 running,
+ * 1 converged, 2 maxit, 3 breakdown), out[2] = search columns removed by the
+ * drop rule of the singular-Gram remark (Section 2.2) summed over all blocks,
+ * out[3] = blocks whose pseudo-inverse (P^T A P)^+ took the eigenvalue path
+ * (the Cholesky certificate that every eigenvalue passes the cutoff failed).
+ * FP64 path: the whole solve; MPCG_MIXED: the last FP32 inner solve.
+ * Errors: MPCG_ERR_ARG (NULL h or out, problem out of range), MPCG_ERR_CUDA.
+ */
+mpcg_status mg_last_solve_counters(const mg_hierarchy* h, int problem, int* out4);
+
+/*
  * Matrix-free fine operator (an extension: the paper names the combination
  * with a matrix-free strategy as future work, Section 4).  For a scalar
  * hierarchy (2D or 3D, single or batched) whose fine operator is the Q1
@@ -434,9 +447,13 @@ void mg_hierarchy_destroy(mg_hierarchy* h);
  * device memory is fully reserved by another framework's pool allocator, or
  * a latency-critical loop that must not call cudaMalloc/cudaFree because
  * cudaFree synchronises the whole device.  It computes what
- * mg_apply_operator computes on the finest grid, without needing a hierarchy.
+ * mg_apply_operator computes on the finest grid of a scalar hierarchy whose
+ * six faces are all Dirichlet (dofs_per_node = 1, dirichlet_face_mask 0x3F),
+ * without needing a hierarchy.
+ *   nodes       nodes per side, boundary included; nodes - 1 in [2, 32768]
+ *               (any value, as mg_hierarchy_setup accepts)
  *   values_dev  3^dim * n doubles (device), X_dev, Y_dev column-major
- *               n x ncols (device), n = (nodes-2)^dim
+ *               n x ncols (device), n = (nodes-2)^dim interior nodes
  *   stream      cudaStream_t; the work is only enqueued on it (the call does
  *               not synchronise), so synchronise before reading Y.
  * Scratch: one static device array of 2^21 doubles (16 MiB) that every GPU
@@ -445,11 +462,14 @@ void mg_hierarchy_destroy(mg_hierarchy* h);
  * larger requests return MPCG_ERR_ARG with a message naming both sizes
  * (e.g. 3D grids up to 33^3 nodes with 12 columns, 2D grids up to 257^2
  * nodes with 11 columns).
- * The first call on a device looks up the array's device address and must
- * happen with that device current; make that first call before any stream
- * capture.  All calls share the one array, and it keeps the last call's
- * contents (the call clears it first): calls whose work overlaps on the GPU
- * (different streams or host threads without ordering) race on it.
+ * The array's device address is looked up with cudaGetSymbolAddress on the
+ * first call made in each CUDA context (with that context current) and
+ * cached under the context's unique ID; a device reset or another context
+ * yields a new ID and therefore a fresh lookup.  Make the first call in a
+ * context before any stream capture.  All calls share the one array, and it
+ * keeps the last call's contents (the call clears it first): calls whose work
+ * overlaps on the GPU (different streams or host threads without ordering)
+ * race on it.  A successful call clears mpcg_last_error().
  */
 mpcg_status mg_stencil_apply_noalloc(int dim, int nodes, const double* values_dev, const double* X_dev,
                                      double* Y_dev, int ncols, void* stream);

@@ -1878,6 +1878,28 @@ const char* mpcg_kernel_class_name(int cls) {
 
 long long mg_last_launches(const mg_hierarchy* h) { return h ? h->last_launches : -1; }
 
+mpcg_status mg_last_solve_counters(const mg_hierarchy* h, int problem, int* out4) {
+  g_err.clear();
+  if (!h || !out4 || problem < 0 || problem >= h->nb) {
+    set_err("mg_last_solve_counters: NULL argument or problem index out of range");
+    return MPCG_ERR_ARG;
+  }
+  const DevState* st = h->opt.precision == MPCG_MIXED ? h->s32.state : h->s64.state;
+  if (!st) {
+    out4[0] = out4[1] = out4[2] = out4[3] = 0;
+    return MPCG_OK;
+  }
+  CK(cudaSetDevice(h->device));
+  DevState d;
+  CK(cudaMemcpyAsync(&d, st + problem, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  out4[0] = d.k;
+  out4[1] = d.done;
+  out4[2] = d.dropped_total;
+  out4[3] = d.pinv_fallbacks;
+  return MPCG_OK;
+}
+
 mpcg_status mpcg_solve_profiled(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, int* iters_out,
                                 double* class_ms, long long* class_launches, int* trace_cls, float* trace_ms,
                                 long long trace_cap, long long* trace_len) {

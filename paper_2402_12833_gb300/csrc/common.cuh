@@ -205,7 +205,8 @@ struct DevState {
   int maxit;
   int ncols;      // active column count C of this solver
   int m;          // window length
-  int dropped_total;
+  int dropped_total;   // search columns dropped by the drop rule, summed over blocks
+  int pinv_fallbacks;  // blocks whose Gram took the eigenvalue pseudo-inverse
   double rtol;
   double bnorm;
   double rnorm;

@@ -207,12 +207,15 @@ __global__ void k_init(DevState* st, const double* part_res, int nblk, double* r
     st->count = 0;
     st->newest = st->m - 1;
     st->dropped_total = 0;
+    st->pinv_fallbacks = 0;
     st->rnorm = sqrt(v[0]);
     st->bnorm = sqrt(v[1]);
     int done = 0;
-    if (st->bnorm == 0.0 || st->rnorm <= st->rtol * st->bnorm) done = 1;
+    // a non-finite b or x_0 is a breakdown, tested first: with b infinite,
+    // ||r|| <= rtol ||b|| reads inf <= inf and would pass as converged
+    if (!isfinite(st->rnorm) || !isfinite(st->bnorm)) done = 3;
+    else if (st->bnorm == 0.0 || st->rnorm <= st->rtol * st->bnorm) done = 1;
     else if (st->maxit <= 0) done = 2;
-    else if (!isfinite(st->rnorm)) done = 3;
     st->done = done;
     if (res_hist) res_hist[0] = st->bnorm > 0.0 ? st->rnorm / st->bnorm : 0.0;
     if (use_cond) cudaGraphSetConditional(cond, done == 0 ? 1u : 0u);
@@ -388,6 +391,7 @@ __global__ void __launch_bounds__(kBlock) k_small_alpha(DevState* st, const doub
       }
     }
     if (!ok) {   // Jacobi eigenvalue pseudo-inverse of D G D
+      if (lane == 0) st->pinv_fallbacks += 1;
       for (int e = lane; e < kPad * kPad; e += 32) {
         const int i = e / kPad, j = e % kPad;
         double v = 0.0;

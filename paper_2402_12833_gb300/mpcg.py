@@ -91,6 +91,7 @@ _SIGS = {
                                       C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_longlong, C.POINTER(C.c_longlong)]),
     "mg_last_launches": (C.c_longlong, [C.c_void_p]),
+    "mg_last_solve_counters": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "mg_stencil_apply_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                            C.c_void_p]),
     "mg_hierarchy_setup_batched": (C.c_int, [C.POINTER(mg_operator), C.c_int, C.c_int, C.POINTER(mpcg_options),
@@ -226,6 +227,14 @@ def mpcg_solve_profiled(h: int, b, x, rtol: float = 1e-8, maxit: int = 500, trac
 
 def mg_last_launches(h: int) -> int:
     return load().mg_last_launches(h)
+
+
+def mg_last_solve_counters(h: int, problem: int = 0) -> dict:
+    """Counters of the last solve: x updates, termination code, dropped
+    columns, eigenvalue pseudo-inverse blocks."""
+    out = np.zeros(4, dtype=np.int32)
+    _check(load().mg_last_solve_counters(h, problem, out.ctypes.data))
+    return {"iters": int(out[0]), "done": int(out[1]), "dropped": int(out[2]), "pinv_fallbacks": int(out[3])}
 
 
 def mg_num_levels(h: int) -> int:

@@ -64,6 +64,12 @@ def normal(seed: int, count: int) -> np.ndarray:
     return out[:count]
 
 
+def perturbed(v: np.ndarray, seed: int, rel: float) -> np.ndarray:
+    """``v`` with every entry scaled by (1 + rel * g), g a seeded N(0,1) draw
+    (seed stream offset so that it never repeats a right-hand side's draw)."""
+    return v * (1.0 + rel * normal(7_000_000 + seed, v.size))
+
+
 # ---------------------------------------------------------------------------
 # grids
 # ---------------------------------------------------------------------------

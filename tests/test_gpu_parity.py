@@ -119,11 +119,15 @@ def test_solve_matches_oracle(M, name, m):
         # the drop rule and the pseudo-inverse cutoff are discontinuous in the
         # data: with a 10-block window on high contrast the Gram matrices sit
         # near the thresholds and rounding decides drops, so the oracle itself
-        # moves between 58 and 62 iterations under 1e-15 relative changes of b
-        # (and differs between CPU platforms).  The count is held to 10 % of
-        # the oracle's; the solutions agree to 1e-9 (their spread under the
-        # same perturbations is ~1e-10) and the true residual meets rtol.
-        assert abs(k - ref.iters) <= max(1, int(np.ceil(0.1 * ref.iters))), (k, ref.iters)
+        # moves by several iterations under 1e-15 relative changes of b
+        # (tests/test_oracle_pins.py pins that spread on the CPU).  The GPU
+        # count must lie within the oracle's own spread over eight such
+        # perturbations (widened by one); the solutions agree to 1e-9 (their
+        # spread under the same perturbations is ~1e-10) and the true
+        # residual meets rtol.
+        spread = [ompcg.mpcg(O.A[-1], pb.perturbed(prob.b, s, 1e-15), O.mg_columns, m=m, rtol=1e-8,
+                             maxit=800).iters for s in range(8)] + [ref.iters]
+        assert min(spread) - 1 <= k <= max(spread) + 1, (k, spread)
         assert np.linalg.norm(x - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
         tr = np.linalg.norm(prob.b - O.A[-1] @ x) / np.linalg.norm(prob.b)
         assert tr <= 1.01e-8
@@ -286,5 +290,154 @@ def test_example1_hierarchy_and_solve_match_oracle(M, kxx):
     st, k, rh, ah = H.solve(b, x, rtol=1e-8, maxit=3000)
     ref = ompcg.mpcg(O.A[-1], prob.b, O.mg_columns, m=5, rtol=1e-8, maxit=3000)
     assert st == M.MPCG_OK and ref.converged
-    assert abs(k - ref.iters) <= max(1, int(np.ceil(0.05 * ref.iters))), (k, ref.iters)
+    assert abs(k - ref.iters) <= 1, (k, ref.iters)
     assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+
+
+# -- the branches of the drop rule and the scaled pseudo-inverse (Section 2.2,
+# the remark on a singular P^T A P) and the breakdown exits
+
+def _eig_cut_margin(ref, tau):
+    """Over the oracle's blocks: (blocks whose Cholesky certificate
+    trace((DGD)^-1) * tau * n_active < 1 fails, eigenvalues cut, smallest
+    distance in decades between an eigenvalue of D G D and the cutoff
+    tau * lambda_max)."""
+    fails = cuts = 0
+    margin = np.inf
+    for P, AP in ref.blocks:
+        G = P.T @ AP
+        G = 0.5 * (G + G.T)
+        act = np.where(np.diag(G) > 0)[0]
+        d = 1.0 / np.sqrt(np.diag(G)[act])
+        Gh = d[:, None] * G[np.ix_(act, act)] * d[None, :]
+        lam = np.linalg.eigvalsh(Gh)
+        fails += int(np.trace(np.linalg.inv(Gh)) * tau * act.size >= 1.0)
+        thr = tau * lam.max()
+        cuts += int((lam <= thr).sum())
+        margin = min(margin, float(np.min(np.abs(np.log10(lam / thr)))))
+    return fails, cuts, margin
+
+
+@pytest.mark.parametrize("name,tau,expect_cuts", [("poisson2d_65", 0.03, False), ("poisson3d_17", 0.3, True),
+                                                  ("kappa3d_17", 0.7, True)])
+def test_eigenvalue_pseudo_inverse_branch_matches_oracle(M, name, tau, expect_cuts):
+    """A raised cutoff tau makes the Cholesky certificate in the alpha kernel
+    fail, so the Jacobi eigenvalue pseudo-inverse runs on the GPU; with
+    expect_cuts some eigenvalues of D G D fall below tau * lambda_max and are
+    removed.  Every eigenvalue sits at least 5 % away from the cutoff, so
+    rounding cannot change which are kept."""
+    prob = PROBS[name]()
+    H = _hier(M, prob, pinv_tau=tau)
+    O = _oracle(prob)
+    b = torch.from_numpy(prob.b).cuda()
+    x = torch.zeros_like(b)
+    st, k, rh, ah = H.solve(b, x, rtol=1e-8, maxit=400)
+    cnt = M.mg_last_solve_counters(H.h)
+    ref = ompcg.mpcg(O.A[-1], prob.b, O.mg_columns, rtol=1e-8, maxit=400, tau=tau, keep_blocks=True)
+    fails, cuts, margin = _eig_cut_margin(ref, tau)
+    assert margin > np.log10(1.05), margin
+    assert fails >= 1 and (cuts >= 1) == expect_cuts, (fails, cuts)
+    assert st == M.MPCG_OK and ref.converged
+    assert cnt["pinv_fallbacks"] >= 1 and cnt["iters"] == k, cnt
+    assert abs(k - ref.iters) <= 1, (k, ref.iters)
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
+    kk = min(k, ref.iters)
+    A = np.array(ref.alpha_hist[:kk])
+    assert np.allclose(ah[:kk], A, rtol=1e-7, atol=1e-10 * np.abs(A).max())
+
+
+def test_default_cutoff_never_takes_the_eigenvalue_branch(M):
+    """At the default tau = 1e-12 the certified Cholesky path serves every
+    block of a well-conditioned solve (the counter sees no fallback)."""
+    prob = PROBS["poisson2d_65"]()
+    H = _hier(M, prob)
+    b = torch.from_numpy(prob.b).cuda()
+    H.solve(b, torch.zeros_like(b))
+    cnt = M.mg_last_solve_counters(H.h)
+    assert cnt["pinv_fallbacks"] == 0 and cnt["dropped"] == 0 and cnt["done"] == 1, cnt
+
+
+def test_zero_network_column_is_dropped_every_block(M):
+    """A learned column from an all-zero network is identically zero: the drop
+    rule removes it from every block, and the solve equals the plain one and
+    the oracle's run with a zero extra column."""
+    prob = PROBS["kappa2d_33_normal"]()
+    H = _hier(M, prob)
+    O = _oracle(prob)
+    b = torch.from_numpy(prob.b).cuda()
+    x0 = torch.zeros_like(b)
+    st0, k0, _, _ = H.solve(b, x0, rtol=1e-8, maxit=400)
+    plain = M.mg_last_solve_counters(H.h)
+    M.mg_learned_attach(H.h, np.zeros(M.mg_learned_num_params(), dtype=np.float32))
+    x = torch.zeros_like(b)
+    st, k, rh, ah = H.solve(b, x, rtol=1e-8, maxit=400)
+    cnt = M.mg_last_solve_counters(H.h)
+    ref = ompcg.mpcg(O.A[-1], prob.b, O.mg_columns, rtol=1e-8, maxit=400, extra_column=lambda r: np.zeros_like(r))
+    assert st == st0 == M.MPCG_OK and ref.converged
+    assert all(prob.levels in d for d in ref.dropped)
+    assert cnt["dropped"] == plain["dropped"] + k, (cnt, plain, k)
+    assert k == k0 and abs(k - ref.iters) <= 1, (k, k0, ref.iters)
+    assert np.all(ah[:, -1] == 0.0)
+    assert np.linalg.norm(x.cpu().numpy() - x0.cpu().numpy()) <= 1e-12 * np.linalg.norm(x0.cpu().numpy())
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_every_column_dropped_is_a_breakdown(M, precision):
+    """drop_delta = 2 removes every column of the first block (its squared
+    A-norms equal those before orthogonalisation): the oracle's first block
+    keeps nothing and its iterate never moves; the library stops with
+    MPCG_ERR_BREAKDOWN instead of looping."""
+    prob = PROBS["poisson2d_65"]()
+    prec = M.MPCG_FP64 if precision == "fp64" else M.MPCG_MIXED
+    H = _hier(M, prob, drop_delta=2.0, inner_drop_delta=2.0, precision=prec)
+    b = torch.from_numpy(prob.b).cuda()
+    x = torch.zeros_like(b)
+    with pytest.raises(M.MpcgError) as e:
+        H.solve(b, x, rtol=1e-8, maxit=50)
+    assert e.value.status == M.MPCG_ERR_BREAKDOWN
+    cnt = M.mg_last_solve_counters(H.h)
+    assert cnt["done"] == 3 and cnt["dropped"] == prob.levels, cnt
+    O = _oracle(prob)
+    ref = ompcg.mpcg(O.A[-1], prob.b, O.mg_columns, rtol=1e-8, maxit=3, delta=2.0)
+    assert ref.dropped[0] == list(range(prob.levels)) and not np.any(ref.x)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("where", ["b_nan", "b_inf", "x0_nan"])
+def test_non_finite_input_is_a_breakdown(M, precision, where):
+    """A NaN or infinity in b or x_0 (made on the host) ends the solve with
+    MPCG_ERR_BREAKDOWN; the hierarchy stays usable for the next solve."""
+    prob = PROBS["kappa2d_65"]()
+    prec = M.MPCG_FP64 if precision == "fp64" else M.MPCG_MIXED
+    H = _hier(M, prob, precision=prec)
+    b = prob.b.copy()
+    x0 = np.zeros(prob.n)
+    bad = {"b_nan": np.nan, "b_inf": np.inf, "x0_nan": np.nan}[where]
+    (x0 if where.startswith("x0") else b)[prob.n // 3] = bad
+    bd, xd = torch.from_numpy(b).cuda(), torch.from_numpy(x0).cuda()
+    with pytest.raises(M.MpcgError) as e:
+        H.solve(bd, xd, rtol=1e-8, maxit=100)
+    assert e.value.status == M.MPCG_ERR_BREAKDOWN
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    st, k, _, _ = H.solve(torch.from_numpy(prob.b).cuda(), x, rtol=1e-8, maxit=2000)
+    assert st == M.MPCG_OK and torch.isfinite(x).all()
+
+
+def test_full_size_fp64_solve_matches_oracle(M):
+    """The 3D Poisson workload at full size (129^3 nodes, 2,048,383 unknowns,
+    6 grids, N(0,1) right-hand side seed 2, m = 5) in the FP64 path, with
+    the graph-launched solve the benchmark times: iteration count +-1 and
+    the solution to 1e-10 relative against the oracle."""
+    prob = pb.poisson_random(3, 129, 2)
+    H = _hier(M, prob, m=5, precision=M.MPCG_FP64)
+    b = torch.from_numpy(prob.b).cuda()
+    x = torch.zeros_like(b)
+    st, k, rh, ah = H.solve(b, x, rtol=1e-8, maxit=200, histories=False)
+    xg = x.cpu().numpy()
+    H.close()
+    O = _oracle(prob)
+    ref = ompcg.mpcg(O.A[-1], prob.b, O.mg_columns, m=5, rtol=1e-8, maxit=200)
+    assert st == M.MPCG_OK and ref.converged
+    assert abs(k - ref.iters) <= 1, (k, ref.iters)
+    assert np.linalg.norm(xg - ref.x) <= 1e-10 * np.linalg.norm(ref.x)

@@ -53,9 +53,15 @@ def _reference(M, prob, X):
     return Yd.cpu().numpy()
 
 
-@pytest.mark.parametrize("dim,nodes,ncols", [(3, 17, 5), (2, 65, 12), (3, 33, 3)])
+@pytest.mark.parametrize("dim,nodes,ncols", [(3, 17, 5), (2, 65, 12), (3, 33, 3), (2, 161, 4), (3, 13, 2)])
 def test_noalloc_matches_allocating_entry_point_twice(lib, dim, nodes, ncols):
-    prob = pb.diffusion_macro(dim, nodes, 21, rhs="normal", rhs_seed=4)
+    # 161 and 13 nodes: element counts that are not powers of two (Example 1's
+    # 160 x 160 elements; 12 = 3 * 2^2), which the hierarchy accepts as well
+    if (nodes - 1) & (nodes - 2):
+        st = pb.assemble_diffusion(dim, nodes)
+        prob = pb.Problem(dim, nodes, 4 if nodes == 161 else 2, st, pb.normal(4, (nodes - 2) ** dim), name="odd")
+    else:
+        prob = pb.diffusion_macro(dim, nodes, 21, rhs="normal", rhs_seed=4)
     for call in range(2):
         X = pb.normal(500 + call, ncols * prob.n).reshape(ncols, prob.n)
         got = _call(lib, prob, X)
@@ -81,3 +87,7 @@ def test_noalloc_rejects_grids_beyond_the_scratch(lib):
                                            ctypes.c_void_p(X.data_ptr()), 1, None)
     assert status == lib.MPCG_ERR_ARG
     assert "scratch" in lib.mpcg_last_error()
+    # a good call afterwards clears the message
+    small = pb.poisson_random(2, 17, 2)
+    _call(lib, small, pb.normal(3, small.n).reshape(1, small.n))
+    assert lib.mpcg_last_error() == ""
