@@ -422,6 +422,27 @@ mpcg_status mg_learned_detach(mg_hierarchy* h);
 /* y = N(rhat, c) for nimg images on h's fine grid (device, n floats each,
  * rhat already scaled); needs attached weights. */
 mpcg_status mg_learned_forward(mg_hierarchy* h, const float* rhat_dev, float* y_dev, int nimg);
+/* mg_learned_forward that also copies the activations out for inspection
+ * (the tensor-core inference kernel): acts_dev (device, may be NULL) gets
+ * 4 * nimg * n * 16 floats, [layer][image][point][channel], points
+ * lexicographic (x fastest); layer 0 holds the two bfloat16 input channels
+ * (zero-padded to 16), layers 1-3 the bfloat16 outputs of the first three
+ * convolutions after ReLU. */
+mpcg_status mg_learned_forward_acts(mg_hierarchy* h, const float* rhat_dev, float* y_dev, float* acts_dev,
+                                   int nimg);
+/*
+ * One forward and backward pass of the training kernels (no weight update)
+ * on nimg (1..MPCG_MAX_COLS) pairs (rhat_i, e_i) of problem h (device, n
+ * floats each): grad (host or device, mg_learned_num_params() doubles) gets
+ * the gradient of the mean A-angle loss with respect to params (host or
+ * device floats, the FP32 master weights; the forward uses their bfloat16
+ * rounding); loss (host, may be NULL) the mean loss; acts_dev (device, may
+ * be NULL) the training forward's activations in the layout of
+ * mg_learned_forward_acts; y_dev (device, may be NULL) the outputs.
+ * Errors: MPCG_ERR_ARG, MPCG_ERR_OOM, MPCG_ERR_CUDA.
+ */
+mpcg_status mg_learned_grad(mg_hierarchy* h, const float* params, const float* rhat_dev, const float* e_dev,
+                            int nimg, double* grad, float* acts_dev, float* y_dev, double* loss);
 /*
  * Train the network on the GPU: pairs (rhat_i, e_i) of scaled residuals and
  * the matching errors (device, npairs x n floats, compact layout) belonging to

@@ -2160,7 +2160,8 @@ mpcg_status mg_detach_q1_kappa(mg_hierarchy* h) {
   return MPCG_OK;
 }
 
-mpcg_status mg_learned_forward(mg_hierarchy* h, const float* rhat_dev, float* y_dev, int nimg) {
+mpcg_status mg_learned_forward_acts(mg_hierarchy* h, const float* rhat_dev, float* y_dev, float* acts_dev,
+                                   int nimg) {
   g_err.clear();
   CKS(check_h(h));
   CKS(net_check_grid(h));
@@ -2176,7 +2177,8 @@ mpcg_status mg_learned_forward(mg_hierarchy* h, const float* rhat_dev, float* y_
   mpcg_status st = MPCG_OK;
   if ((st = tmp.get(&r, (size_t)nimg * g.len, s)) == MPCG_OK && (st = tmp.get(&y, (size_t)nimg * g.len, s)) == MPCG_OK) {
     launch_pack<float, float>(g, rhat_dev, g.n, r, nimg, s);
-    launch_net_infer<float>(g, nimg, r, g.len, h->net_c, h->net_wtc, nullptr, y, (float*)nullptr, h->net_err, s);
+    launch_net_infer<float>(g, nimg, r, g.len, h->net_c, h->net_wtc, nullptr, y, (float*)nullptr, h->net_err, s,
+                            acts_dev);
     launch_unpack<float, float>(g, y, y_dev, g.n, nimg, s);
     int err = 0;
     if (cudaMemcpyAsync(&err, h->net_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -2189,6 +2191,102 @@ mpcg_status mg_learned_forward(mg_hierarchy* h, const float* rhat_dev, float* y_
     }
   }
   tmp.release();
+  return st;
+}
+
+mpcg_status mg_learned_forward(mg_hierarchy* h, const float* rhat_dev, float* y_dev, int nimg) {
+  return mg_learned_forward_acts(h, rhat_dev, y_dev, nullptr, nimg);
+}
+
+mpcg_status mg_learned_grad(mg_hierarchy* h, const float* params, const float* rhat_dev, const float* e_dev,
+                            int nimg, double* grad, float* acts_dev, float* y_dev, double* loss) {
+  g_err.clear();
+  CKS(check_h(h));
+  CKS(net_check_grid(h));
+  if (!params || !rhat_dev || !e_dev || !grad || nimg < 1 || nimg > MPCG_MAX_COLS) {
+    set_err("mg_learned_grad: params, rhat, e and grad are required and nimg must be in 1..%d", MPCG_MAX_COLS);
+    return MPCG_ERR_ARG;
+  }
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = h->stream;
+  const GridDesc g = h->lev[h->levels - 1].g;
+  if (g.p > 1024) {
+    set_err("training grids are limited to 1025 nodes per side");
+    return MPCG_ERR_ARG;
+  }
+  CKS(build_f32(h));
+  CKS(net_prepare(h));
+  net_prepare_attributes(g);
+  Alloc mem;
+  mpcg_status st = MPCG_OK;
+  auto get = [&](auto** p, size_t n) {
+    if (st == MPCG_OK) st = mem.get(p, n, s);
+  };
+  const int B = nimg;
+  const size_t L = g.len;
+  const int nw = net_wgrad_blocks(g, B);
+  float *rb, *eb, *aeb, *y, *ay, *dy, *master, *wq;
+  double *dots, *coef, *lsum, *gd;
+  NetActs a;
+  NetGrads gr;
+  get(&rb, B * L);
+  get(&eb, B * L);
+  get(&aeb, B * L);
+  get(&y, B * L);
+  get(&ay, B * L);
+  get(&dy, B * L);
+  get(&a.a0, B * L * kNetIn);
+  get(&a.a1, B * L * kNetC1);
+  get(&a.a2, B * L * kNetW);
+  get(&a.a3, B * L * kNetW);
+  get(&gr.d1, B * L * kNetW);
+  get(&gr.d2, B * L * kNetW);
+  get(&gr.d3, B * L * kNetW);
+  get(&gr.part[0], (size_t)kNetC1 * kNetIn * 9 * nw);
+  get(&gr.part[1], (size_t)kNetW * kNetC1 * 9 * nw);
+  get(&gr.part[2], (size_t)kNetW * kNetW * 9 * nw);
+  get(&gr.part[3], (size_t)kNetW * 9 * nw);
+  get(&master, kNetParams);
+  get(&wq, kNetParams);
+  get(&dots, 3 * 64 * B);
+  get(&coef, 2 * B);
+  get(&lsum, 1);
+  get(&gd, kNetParams);
+  double** parts_dev = nullptr;
+  int* nblk_dev = nullptr;
+  get(&parts_dev, 4);
+  get(&nblk_dev, 4);
+  if (st != MPCG_OK) {
+    mem.release();
+    return st;
+  }
+  const int nblk_h[4] = {nw, nw, nw, nw};
+  cudaMemcpyAsync(parts_dev, gr.part, sizeof(gr.part), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(nblk_dev, nblk_h, sizeof(nblk_h), cudaMemcpyHostToDevice, s);
+  copy_floats(master, params, kNetParams, s);
+  launch_round_bf16(master, wq, kNetParams, s);
+  launch_pack<float, float>(g, rhat_dev, g.n, rb, B, s);
+  launch_pack<float, float>(g, e_dev, g.n, eb, B, s);
+  const float* st32 = h->lev[h->levels - 1].st32;
+  launch_spmm<float>(g, st32, eb, aeb, B, nullptr, nullptr, s);
+  cudaMemsetAsync(lsum, 0, sizeof(double), s);
+  launch_net_forward<float>(g, B, rb, L, h->net_c, wq, nullptr, a, y, (float*)nullptr, s);
+  launch_spmm<float>(g, st32, y, ay, B, nullptr, nullptr, s);
+  launch_net_loss_grad(g, B, y, ay, eb, aeb, dots, coef, lsum, dy, s);
+  launch_net_backward(g, B, wq, a, dy, gr, s);
+  launch_net_grad_sum(parts_dev, nblk_dev, gd, s);
+  if (acts_dev) launch_net_acts_export(g, B, a, acts_dev, s);
+  if (y_dev) launch_unpack<float, float>(g, y, y_dev, g.n, B, s);
+  double lh = 0.0;
+  if (cudaMemcpyAsync(grad, gd, sizeof(double) * kNetParams,
+                      is_device_pointer(grad) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&lh, lsum, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    set_err("mg_learned_grad: %s", cudaGetErrorString(cudaGetLastError()));
+    st = MPCG_ERR_CUDA;
+  }
+  if (loss) *loss = lh;
+  mem.release();
   return st;
 }
 

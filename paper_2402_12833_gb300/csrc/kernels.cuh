@@ -238,10 +238,11 @@ void launch_net_forward(const GridDesc& g, int B, const T* r, long long r_ld, co
                         const DevState* state, NetActs acts, float* y, T* z, cudaStream_t s);
 // Fused tensor-core inference (all four layers per output tile); wtc holds
 // the weights packed by launch_net_pack_tc (net_tc_weight_bytes() bytes);
-// err is set to 1 if a bounded wait on the MMA completion runs out.
+// err is set to 1 if a bounded wait on the MMA completion runs out; acts
+// (may be null) receives the activations [4][B][n1*n1][16] as floats.
 template <typename T>
 void launch_net_infer(const GridDesc& g, int B, const T* r, long long r_ld, const float* c, const void* wtc,
-                      const DevState* state, float* y, T* z, int* err, cudaStream_t s);
+                      const DevState* state, float* y, T* z, int* err, cudaStream_t s, float* acts = nullptr);
 void launch_net_pack_tc(const float* wq, void* wtc, cudaStream_t s);
 int net_tc_weight_bytes();
 void net_infer_prepare_attributes();
@@ -252,6 +253,11 @@ void launch_net_loss_grad(const GridDesc& g, int B, const float* y, const float*
 void launch_net_adam(const double* const* parts_dev, const int* nblk_dev, float* master, float* m, float* v, float* wq,
                      int step, float lr, float b1, float b2, float eps, cudaStream_t s);
 void launch_round_bf16(const float* src, float* dst, int n, cudaStream_t s);
+// grad[i] = sum of the weight-gradient partials of parameter i (all layers)
+void launch_net_grad_sum(const double* const* parts_dev, const int* nblk_dev, double* grad, cudaStream_t s);
+// activations a0..a3 of the training forward ([B][len][C] bfloat16, padded)
+// to the compact float layout [4][B][n1*n1][16] (a0 zero-padded to 16)
+void launch_net_acts_export(const GridDesc& g, int B, NetActs acts, float* out, cudaStream_t s);
 void launch_net_coef(const GridDesc& g, const double* dinv, double omega, float* c, double* part, cudaStream_t s);
 void net_prepare_attributes(const GridDesc& g);
 

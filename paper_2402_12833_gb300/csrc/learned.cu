@@ -284,6 +284,35 @@ __global__ void k_net_adam(const double* const* parts, const int* nblk, int npar
   wq[i] = __bfloat162float(__float2bfloat16_rn(w));
 }
 
+__global__ void k_net_grad_sum(const double* const* parts, const int* nblk, int nparams, double* grad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nparams) return;
+  int layer = 0, off = i;
+  const int sizes[4] = {kNetC1 * kNetIn * 9, kNetW * kNetW * 9, kNetW * kNetW * 9, kNetW * 9};
+  while (off >= sizes[layer]) off -= sizes[layer], ++layer;
+  double gsum = 0.0;
+  const double* p = parts[layer] + (long long)off * nblk[layer];
+  for (int k = 0; k < nblk[layer]; ++k) gsum += p[k];
+  grad[i] = gsum;
+}
+
+__global__ void k_net_acts_export(GridDesc g, int B, NetActs a, float* out) {
+  const long long nn = (long long)g.n1 * g.n1;
+  const long long total = 4LL * B * nn;
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total;
+       u += (long long)gridDim.x * blockDim.x) {
+    const int L = (int)(u / (B * nn));
+    const int b = (int)((u / nn) % B);
+    const long long q = u % nn;
+    const long long t = (q / g.n1) * g.p + q % g.n1;
+    const long long base = (long long)b * g.len + g.G + t;
+    float* o = out + u * 16;
+    const int C = L == 0 ? kNetIn : 16;
+    const __nv_bfloat16* src = L == 0 ? a.a0 : L == 1 ? a.a1 : L == 2 ? a.a2 : a.a3;
+    for (int ch = 0; ch < 16; ++ch) o[ch] = ch < C ? __bfloat162float(src[base * C + ch]) : 0.f;
+  }
+}
+
 __global__ void k_round_bf16(const float* src, float* dst, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = __bfloat162float(__float2bfloat16_rn(src[i]));
@@ -381,6 +410,14 @@ void launch_net_adam(const double* const* parts_dev, const int* nblk_dev, float*
                      int step, float lr, float b1, float b2, float eps, cudaStream_t s) {
   k_net_adam<<<(kNetParams + kBlock - 1) / kBlock, kBlock, 0, s>>>(parts_dev, nblk_dev, kNetParams, master, m, v, wq,
                                                                    step, lr, b1, b2, eps);
+}
+
+void launch_net_grad_sum(const double* const* parts_dev, const int* nblk_dev, double* grad, cudaStream_t s) {
+  k_net_grad_sum<<<(kNetParams + kBlock - 1) / kBlock, kBlock, 0, s>>>(parts_dev, nblk_dev, kNetParams, grad);
+}
+
+void launch_net_acts_export(const GridDesc& g, int B, NetActs acts, float* out, cudaStream_t s) {
+  k_net_acts_export<<<grid_for(4LL * B * g.n1 * g.n1, 4096), kBlock, 0, s>>>(g, B, acts, out);
 }
 
 void launch_round_bf16(const float* src, float* dst, int n, cudaStream_t s) {

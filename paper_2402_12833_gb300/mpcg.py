@@ -121,6 +121,9 @@ _SIGS = {
     "mg_attach_q1_kappa": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mg_detach_q1_kappa": (C.c_int, [C.c_void_p]),
     "mg_learned_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "mg_learned_forward_acts": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "mg_learned_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]),
     "mg_learned_train": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                    C.POINTER(mg_train_opts), C.c_void_p, C.c_void_p]),
 }
@@ -293,6 +296,23 @@ def mg_detach_q1_kappa(h: int) -> None:
 
 def mg_learned_forward(h: int, rhat_dev, y_dev, nimg: int = 1) -> None:
     _check(load().mg_learned_forward(h, _ptr(rhat_dev), _ptr(y_dev), nimg))
+
+
+def mg_learned_forward_acts(h: int, rhat_dev, y_dev, acts_dev, nimg: int = 1) -> None:
+    """Forward pass that also fills acts_dev ([4][nimg][n][16] floats)."""
+    _check(load().mg_learned_forward_acts(h, _ptr(rhat_dev), _ptr(y_dev), _ptr(acts_dev), nimg))
+
+
+def mg_learned_grad(h: int, params: np.ndarray, rhat_dev, e_dev, nimg: int, acts_dev=None, y_dev=None):
+    """One forward + backward pass of the training kernels; returns
+    (gradient as float64 array, mean loss)."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    grad = np.zeros(mg_learned_num_params())
+    loss = C.c_double(0.0)
+    _check(load().mg_learned_grad(h, p.ctypes.data, _ptr(rhat_dev), _ptr(e_dev), nimg, grad.ctypes.data,
+                                  _ptr(acts_dev) if acts_dev is not None else None,
+                                  _ptr(y_dev) if y_dev is not None else None, C.byref(loss)))
+    return grad, loss.value
 
 
 def mg_learned_train(handles, pair_prob, rhat_dev, e_dev, params: np.ndarray, epochs: int = 10, batch: int = 8,
