@@ -53,7 +53,19 @@ typedef enum {
 
 enum { MPCG_FORMAT_STENCIL = 0 };
 enum { MPCG_SMOOTHER_JACOBI = 0, MPCG_SMOOTHER_SSOR = 1 };
-enum { MPCG_FP64 = 0, MPCG_MIXED = 1 };
+/* Arithmetic of the solve:
+ *   MPCG_FP64     FP64 vectors and FP64 arithmetic throughout;
+ *   MPCG_MIXED    FP32 bulk with FP64 reductions, pseudo-inverse, coarse
+ *                 Cholesky and iterative refinement on the FP64 residual;
+ *   MPCG_FP64_DW  FP64 data (b, x, operators) with the bulk in double-word
+ *                 arithmetic: every vector entry is a pair of floats
+ *                 hi + lo (about 48 significant bits, 8 bytes) computed on
+ *                 the FP32 pipe, which GB300 issues 64 times faster than
+ *                 FP64; reductions, pseudo-inverse and coarse solve in FP64.
+ *                 Results agree with MPCG_FP64 to ~1e-13 relative per step;
+ *                 magnitudes must stay within float's exponent range (the
+ *                 low word of values below ~1e-30 is flushed). */
+enum { MPCG_FP64 = 0, MPCG_MIXED = 1, MPCG_FP64_DW = 2 };
 
 /* Largest supported number of columns (grids, plus an appended column) and
  * window length. */
@@ -115,7 +127,7 @@ typedef struct {
   double omega;          /* Jacobi damping */
   double pinv_tau;       /* eigenvalue cutoff of the scaled pseudo-inverse (FP64 path) */
   double drop_delta;     /* column-drop threshold on A-norm^2 ratios (FP64 path) */
-  int precision;         /* MPCG_FP64, or MPCG_MIXED (FP32 bulk, FP64 reductions + refinement) */
+  int precision;         /* MPCG_FP64, MPCG_MIXED or MPCG_FP64_DW (see above) */
   double inner_rtol;     /* MPCG_MIXED: relative tolerance of each FP32 inner solve */
   double inner_pinv_tau; /* MPCG_MIXED: cutoff used inside the FP32 inner solve */
   double inner_drop_delta;

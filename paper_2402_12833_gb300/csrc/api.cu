@@ -55,6 +55,7 @@ struct EllLevel {
   int* col = nullptr;
   double* v64 = nullptr;
   float* v32 = nullptr;
+  dw* vdw = nullptr;   // double-word values (MPCG_FP64_DW)
   long long nent = 0;   // stored entries, padding included
 };
 
@@ -64,6 +65,8 @@ template <>
 EllDev<double> ell_of<double>(const EllLevel& E) { return {E.rows, E.cols, E.nslices, E.lg, E.sptr, E.col, E.v64}; }
 template <>
 EllDev<float> ell_of<float>(const EllLevel& E) { return {E.rows, E.cols, E.nslices, E.lg, E.sptr, E.col, E.v32}; }
+template <>
+EllDev<dw> ell_of<dw>(const EllLevel& E) { return {E.rows, E.cols, E.nslices, E.lg, E.sptr, E.col, E.vdw}; }
 
 struct Level {
   GridDesc g;
@@ -73,6 +76,8 @@ struct Level {
   float* st32 = nullptr;
   double* dinv64 = nullptr;
   float* dinv32 = nullptr;
+  dw* stdw = nullptr;            // double-word copies (MPCG_FP64_DW)
+  dw* dinvdw = nullptr;
   float* kq32 = nullptr;         // fine grid: element coefficients in use (matrix-free FP32 operator), or null
   float* kq32_store = nullptr;   // their storage (kept across detach / attach)
   // algebraic hierarchies: the grid's operator, P_j (grid j-1 -> j) and R_j = P_j^T
@@ -240,6 +245,8 @@ struct mg_hierarchy {
   Alloc mem;
   Solver<double> s64;
   Solver<float> s32;
+  Solver<dw> sdw;            // FP64 data, double-word arithmetic (MPCG_FP64_DW)
+  bool havedw = false;
   double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *nrm = nullptr, *part_mix = nullptr;
   int* xnz = nullptr;        // per problem: the packed FP64 iterate may be nonzero
   double* stage = nullptr;   // 2 n doubles: staging for host b and x
@@ -277,12 +284,16 @@ template <>
 const double* st_of<double>(const Level& L) { return L.st64; }
 template <>
 const float* st_of<float>(const Level& L) { return L.st32; }
+template <>
+const dw* st_of<dw>(const Level& L) { return L.stdw; }
 template <typename T>
 const T* dinv_of(const Level& L);
 template <>
 const double* dinv_of<double>(const Level& L) { return L.dinv64; }
 template <>
 const float* dinv_of<float>(const Level& L) { return L.dinv32; }
+template <>
+const dw* dinv_of<dw>(const Level& L) { return L.dinvdw; }
 
 template <typename T>
 mpcg_status build_solver(mg_hierarchy* h, Solver<T>& S) {
@@ -666,7 +677,7 @@ void enqueue_prologue(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle 
   const Level& L = h->lev[h->levels - 1];
   // a solve from a zero iterate has r = b, written by its start kernel
   // the FP64 iterate was packed with its nonzero flag (a zero x0 skips the stencil)
-  const int* xnz = std::is_same<T, double>::value ? h->xnz : nullptr;
+  const int* xnz = std::is_same<T, float>::value ? nullptr : h->xnz;
   if (!S.zero_start) LAUNCH(h, K_RESIDUAL, s, launch_fine_residual<T>(h, S.b, S.x, S.r, S.part_res, s, xnz));
   // a batch decides its loop condition from all problems (enqueue_any)
   LAUNCH(h, K_INIT, s, launch_init(S.state, h->nb, S.part_res, stream_blocks(L.g), S.res_hist, S.hist_cap, cond,
@@ -881,6 +892,33 @@ mpcg_status build_f32(mg_hierarchy* h) {
   return MPCG_OK;
 }
 
+// Double-word copies of the operators (MPCG_FP64_DW): stencils and sparse
+// values split from the FP64 ones, inverse diagonals recomputed from them.
+mpcg_status build_dw(mg_hierarchy* h) {
+  if (h->havedw) return MPCG_OK;
+  cudaStream_t s = h->stream;
+  for (int j = 0; j < h->levels; ++j) {
+    Level& L = h->lev[j];
+    if (h->algebraic) {
+      for (EllLevel* E : {&L.eA, &L.eP, &L.eR}) {
+        if (!E->v64) continue;
+        CKS(h->mem.get(&E->vdw, (size_t)E->nent, s));
+        launch_convert_dw(E->v64, E->vdw, E->nent, s);
+      }
+      CKS(h->mem.get(&L.dinvdw, (size_t)L.g.cp, s));
+      launch_convert_dw(L.dinv64, L.dinvdw, L.g.cp, s);
+      continue;
+    }
+    CKS(h->mem.get(&L.stdw, (size_t)L.nplanes * L.g.cp, s));
+    CKS(h->mem.get(&L.dinvdw, (size_t)L.ndinv * L.g.cp, s));
+    launch_convert_dw(L.st64, L.stdw, (long long)L.nplanes * L.g.cp, s);
+    launch_convert_dw(L.dinv64, L.dinvdw, (long long)L.ndinv * L.g.cp, s);
+  }
+  CK(cudaGetLastError());
+  h->havedw = true;
+  return MPCG_OK;
+}
+
 // Sliced ELLPACK (EllDev layout, amg::ell_layout) of a host CSR matrix,
 // uploaded to the device.
 mpcg_status upload_ell(mg_hierarchy* h, const mpcg::amg::Csr& M, EllLevel& E, cudaStream_t s) {
@@ -910,7 +948,7 @@ mpcg_status upload_ell(mg_hierarchy* h, const mpcg::amg::Csr& M, EllLevel& E, cu
 
 mpcg_status check_options(const mpcg_options& opt) {
   if (opt.m < 1 || opt.m > MPCG_MAX_WINDOW || opt.nu < 1 || !(opt.omega > 0.0) || opt.pinv_tau < 0.0 ||
-      opt.drop_delta < 0.0 || (opt.precision != MPCG_FP64 && opt.precision != MPCG_MIXED) || opt.max_outer < 1 ||
+      opt.drop_delta < 0.0 || (opt.precision != MPCG_FP64 && opt.precision != MPCG_MIXED && opt.precision != MPCG_FP64_DW) || opt.max_outer < 1 ||
       (opt.sum_columns != 0 && opt.sum_columns != 1) || (opt.vcycle != 0 && opt.vcycle != 1) ||
       (opt.sum_columns && opt.vcycle) ||
       (opt.smoother != MPCG_SMOOTHER_JACOBI && opt.smoother != MPCG_SMOOTHER_SSOR) ||
@@ -1012,6 +1050,7 @@ void mg_hierarchy_destroy(mg_hierarchy* h) {
   if (h->mgraph) cudaGraphDestroy(h->mgraph);
   h->s64.release();
   h->s32.release();
+  h->sdw.release();
   h->mem.release();
   h->prof.release();
   h->net_mem.release();
@@ -1167,6 +1206,10 @@ static mpcg_status setup_impl(const mg_operator* ops, int nb, int levels, const 
   if (opt.precision == MPCG_MIXED) {
     if ((st = build_f32(h)) != MPCG_OK) return fail(st);
     if ((st = build_solver<float>(h, h->s32)) != MPCG_OK) return fail(st);
+  }
+  if (opt.precision == MPCG_FP64_DW) {
+    if ((st = build_dw(h)) != MPCG_OK) return fail(st);
+    if ((st = build_solver<dw>(h, h->sdw)) != MPCG_OK) return fail(st);
   }
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     set_err("setup failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1357,6 +1400,10 @@ mpcg_status mg_hierarchy_setup_algebraic(const mg_csr* A, const mg_amg_options* 
     if ((st = build_f32(h)) != MPCG_OK) return fail(st);
     if ((st = build_solver<float>(h, h->s32)) != MPCG_OK) return fail(st);
   }
+  if (opt.precision == MPCG_FP64_DW) {
+    if ((st = build_dw(h)) != MPCG_OK) return fail(st);
+    if ((st = build_solver<dw>(h, h->sdw)) != MPCG_OK) return fail(st);
+  }
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     set_err("setup failed: %s", cudaGetErrorString(cudaGetLastError()));
     return fail(MPCG_ERR_CUDA);
@@ -1516,23 +1563,28 @@ mpcg_status mg_amg_host_ell(const mg_amg_host* a, int level, int which, int* lg,
 
 void mg_amg_host_destroy(mg_amg_host* a) { delete a; }
 
-static mpcg_status solve_fp64(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, int* iters_out,
-                              double* res_hist, double* alpha_hist) {
-  Solver<double>& S = h->s64;
+}  // extern "C"
+
+// The FP64-data solve: T = double (FP64 arithmetic) or dw (double-word
+// arithmetic on the FP32 pipe; b and x0 are split into pairs on entry and x
+// is assembled back into doubles).
+template <typename T>
+static mpcg_status solve_fp64(mg_hierarchy* h, Solver<T>& S, const double* b, double* x, double rtol, int maxit,
+                              int* iters_out, double* res_hist, double* alpha_hist) {
   cudaStream_t s = h->stream;
   const GridDesc& gf = h->lev[h->levels - 1].g;
   const int nb = h->nb;
   CKS(ensure_hist(h, S, maxit));
   for (int p = 0; p < nb; ++p) {
-    LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, b + (size_t)p * gf.n, gf.n, S.b + (size_t)p * gf.len, 1, s));
+    LAUNCH(h, K_PACK, s, launch_pack<double, T>(gf, b + (size_t)p * gf.n, gf.n, S.b + (size_t)p * gf.len, 1, s));
     CK(cudaMemsetAsync(h->xnz + p, 0, sizeof(int), s));
-    LAUNCH(h, K_PACK, s, launch_pack_flag(gf, x + (size_t)p * gf.n, S.x + (size_t)p * gf.len, h->xnz + p, s));
+    LAUNCH(h, K_PACK, s, launch_pack_flag<T>(gf, x + (size_t)p * gf.n, S.x + (size_t)p * gf.len, h->xnz + p, s));
   }
   LAUNCH(h, K_AUX, s, launch_set_params(S.state, nb, rtol, maxit, S.m, S.C, h->opt.drop_delta, h->opt.pinv_tau, s));
   std::vector<int> kd;
-  CKS(run_solver<double>(h, S, kd));
+  CKS(run_solver<T>(h, S, kd));
   for (int p = 0; p < nb; ++p) {
-    LAUNCH(h, K_PACK, s, launch_unpack<double, double>(gf, S.x + (size_t)p * gf.len, x + (size_t)p * gf.n, gf.n, 1, s));
+    LAUNCH(h, K_PACK, s, launch_unpack<T, double>(gf, S.x + (size_t)p * gf.len, x + (size_t)p * gf.n, gf.n, 1, s));
     const int k = kd[2 * p];
     if (res_hist)
       CK(cudaMemcpyAsync(res_hist + (size_t)p * (maxit + 1), S.res_hist + (size_t)p * S.hist_cap,
@@ -1554,6 +1606,8 @@ static mpcg_status solve_fp64(mg_hierarchy* h, const double* b, double* x, doubl
   }
   return result;
 }
+
+extern "C" {
 
 // The mixed-precision solve as one CUDA graph: an outer conditional while
 // node (FP64 residual, device-side decision, scaling, FP32 inner solve,
@@ -1851,8 +1905,10 @@ mpcg_status mpcg_solve(mg_hierarchy* h, const double* b, double* x, double rtol,
     st = MPCG_OK;
     if (h->opt.use_graph && !h->force_direct && !res_hist) st = solve_mixed_graph(h, bd, xd, rtol, maxit, iters_out, &fallback);
     if (fallback) st = solve_mixed(h, bd, xd, rtol, maxit, iters_out, res_hist);
+  } else if (h->opt.precision == MPCG_FP64_DW) {
+    st = solve_fp64<dw>(h, h->sdw, bd, xd, rtol, maxit, iters_out, res_hist, alpha_hist);
   } else {
-    st = solve_fp64(h, bd, xd, rtol, maxit, iters_out, res_hist, alpha_hist);
+    st = solve_fp64<double>(h, h->s64, bd, xd, rtol, maxit, iters_out, res_hist, alpha_hist);
   }
   h->prof.flush();
   h->last_launches = h->prof.live;
@@ -1884,7 +1940,9 @@ mpcg_status mg_last_solve_counters(const mg_hierarchy* h, int problem, int* out4
     set_err("mg_last_solve_counters: NULL argument or problem index out of range");
     return MPCG_ERR_ARG;
   }
-  const DevState* st = h->opt.precision == MPCG_MIXED ? h->s32.state : h->s64.state;
+  const DevState* st = h->opt.precision == MPCG_MIXED    ? h->s32.state
+                        : h->opt.precision == MPCG_FP64_DW ? h->sdw.state
+                                                           : h->s64.state;
   if (!st) {
     out4[0] = out4[1] = out4[2] = out4[3] = 0;
     return MPCG_OK;
@@ -2048,11 +2106,13 @@ void drop_mixed_graph_fwd(mg_hierarchy* h);
 mpcg_status rebuild_solvers(mg_hierarchy* h) {
   CK(cudaStreamSynchronize(h->stream));
   drop_mixed_graph_fwd(h);
-  const bool had32 = h->s32.built;
+  const bool had32 = h->s32.built, haddw = h->sdw.built;
   h->s64.release();
   h->s32.release();
+  h->sdw.release();
   CKS(build_solver<double>(h, h->s64));
   if (had32) CKS(build_solver<float>(h, h->s32));
+  if (haddw) CKS(build_solver<dw>(h, h->sdw));
   return MPCG_OK;
 }
 

@@ -23,7 +23,7 @@ namespace {
 // block jj = b % m and on the contiguous point chunk b / m, so that the
 // blocks running together read the same chunk of Z (L2 reuse).
 template <typename T, int C>
-__global__ void __launch_bounds__(kBlock, 3) k_gram_window(GridDesc g, Window<T> win, const T* __restrict__ Z,
+__global__ void __launch_bounds__(kBlock, kIsDw<T> ? 1 : 3) k_gram_window(GridDesc g, Window<T> win, const T* __restrict__ Z,
                                                         double* part, int nchunks, const DevState* state) {
   const int pb = blockIdx.y;
   state += pb;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_gram_window(GridDesc g, Window<T>
 }
 
 template <typename T, int C>
-__global__ void __launch_bounds__(kBlock, 2) k_orth_update(GridDesc g, Window<T> win, const T* __restrict__ Z,
+__global__ void __launch_bounds__(kBlock, kIsDw<T> ? 1 : 2) k_orth_update(GridDesc g, Window<T> win, const T* __restrict__ Z,
                                                         const T* __restrict__ AZ, const T* __restrict__ r,
                                                         double* part, const DevState* state) {
   const int pb = blockIdx.y;
@@ -337,5 +337,11 @@ template void launch_update_xr<double>(const GridDesc&, Window<double>, double*,
                                        const DevState*, cudaStream_t);
 template void launch_update_xr<float>(const GridDesc&, Window<float>, float*, float*, int, double*,
                                       const DevState*, cudaStream_t);
+template void launch_gram_window<dw>(const GridDesc&, Window<dw>, const dw*, int, int, double*, const DevState*,
+                                     cudaStream_t);
+template void launch_orth_update<dw>(const GridDesc&, Window<dw>, const dw*, const dw*, const dw*, int, double*,
+                                     const DevState*, cudaStream_t);
+template void launch_update_xr<dw>(const GridDesc&, Window<dw>, dw*, dw*, int, double*, const DevState*,
+                                   cudaStream_t);
 
 }  // namespace mpcg

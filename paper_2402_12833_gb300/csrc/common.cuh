@@ -30,6 +30,7 @@
 #include <stdint.h>
 
 #include "../../include/mpcg.h"
+#include "dw.cuh"
 
 namespace mpcg {
 

@@ -205,4 +205,14 @@ template void launch_ell_jacobi<double>(const EllDev<double>&, const double*, co
 template void launch_ell_jacobi<float>(const EllDev<float>&, const float*, const float*, const float*, float*, int,
                                        const DevState*, cudaStream_t);
 
+// double-word instances (MPCG_FP64_DW)
+template void launch_ell_spmm<dw>(const EllDev<dw>&, const dw*, long long, dw*, long long, int, double*, int,
+                                  const DevState*, cudaStream_t);
+template void launch_ell_defect<dw>(const EllDev<dw>&, const dw*, const dw*, dw*, const DevState*, cudaStream_t);
+template void launch_ell_spmv_add<dw>(const EllDev<dw>&, const dw*, dw*, const DevState*, cudaStream_t);
+template void launch_ell_residual<dw>(const EllDev<dw>&, const dw*, const dw*, dw*, double*, int, cudaStream_t,
+                                      const int*);
+template void launch_ell_jacobi<dw>(const EllDev<dw>&, const dw*, const dw*, const dw*, dw*, int, const DevState*,
+                                    cudaStream_t);
+
 }  // namespace mpcg

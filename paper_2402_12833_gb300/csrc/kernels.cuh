@@ -56,7 +56,8 @@ void launch_ell_jacobi(const EllDev<T>& A, const T* dinv, const T* g, const T* s
 template <typename TI, typename TO>
 void launch_pack(const GridDesc& g, const TI* src, long long ld, TO* dst, int ncols, cudaStream_t s);
 // pack of one FP64 column; *nz = 1 when it has a nonzero entry (zero it first)
-void launch_pack_flag(const GridDesc& g, const double* src, double* dst, int* nz, cudaStream_t s);
+template <typename TO>
+void launch_pack_flag(const GridDesc& g, const double* src, TO* dst, int* nz, cudaStream_t s);
 // SM count used to size one-wave launches (set at hierarchy setup)
 void set_sm_count(int n);
 // blocks (and zaz partial slots) of launch_spmm on grid g with C columns
@@ -127,6 +128,8 @@ void launch_galerkin(const GridDesc& gf, const GridDesc& gc, const double* stf, 
 template <typename T>
 void launch_dinv(const GridDesc& g, const double* st, T* dinv, double omega, cudaStream_t s);
 void launch_convert_f32(const double* src, float* dst, long long count, cudaStream_t s);
+// double -> double-word pairs (dw.cuh), element by element
+void launch_convert_dw(const double* src, dw* dst, long long count, cudaStream_t s);
 
 // ---- block.cu --------------------------------------------------------------
 // W partials: rows jj*C+a (window block jj, newest first), cols b:

@@ -341,6 +341,8 @@ template void launch_net_infer<double>(const GridDesc&, int, const double*, long
                                        const DevState*, float*, double*, int*, cudaStream_t, float*);
 template void launch_net_infer<float>(const GridDesc&, int, const float*, long long, const float*, const void*,
                                       const DevState*, float*, float*, int*, cudaStream_t, float*);
+template void launch_net_infer<dw>(const GridDesc&, int, const dw*, long long, const float*, const void*,
+                                   const DevState*, float*, dw*, int*, cudaStream_t, float*);
 
 void net_infer_prepare_attributes() {
   cudaFuncSetAttribute(k_net_infer_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);

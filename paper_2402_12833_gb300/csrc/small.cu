@@ -720,6 +720,7 @@ template void launch_coarse_solve<double>(const GridDesc&, const double*, const 
                                           cudaStream_t);
 template void launch_coarse_solve<float>(const GridDesc&, const double*, const float*, float*, const DevState*,
                                          cudaStream_t);
+template void launch_coarse_solve<dw>(const GridDesc&, const double*, const dw*, dw*, const DevState*, cudaStream_t);
 void launch_mix_init(int* mix, int* active, int nb, int* outer, cudaStream_t s) {
   k_mix_init<<<1, kBlock, 0, s>>>(mix, active, nb, outer);
 }

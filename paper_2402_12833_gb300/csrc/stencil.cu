@@ -32,13 +32,14 @@ __global__ void k_pack(GridDesc g, const TI* __restrict__ src, long long ld, TO*
 // Pack of one FP64 column that also records whether it has a nonzero entry
 // (nz = 1; the caller zeroes nz first).  Bit patterns are tested (no FP64
 // arithmetic); -0.0 counts as nonzero.
-__global__ void k_pack_flag(GridDesc g, const double* __restrict__ src, double* __restrict__ dst, int* nz) {
+template <typename TO>
+__global__ void k_pack_flag(GridDesc g, const double* __restrict__ src, TO* __restrict__ dst, int* nz) {
   const long long n = g.n;
   bool any = false;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const double v = src[t];
     any |= __double_as_longlong(v) != 0;
-    dst[padded_index(g, t)] = v;
+    dst[padded_index(g, t)] = (TO)v;
   }
   if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) *nz = 1;
 }
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(kBlock) k_restrict(GridDesc gf, GridDesc gc, c
     for (int ey = -1; ey <= 1; ++ey) {
 #pragma unroll
       for (int ex = -1; ex <= 1; ++ex) {
-        const T w = (T)((ex ? 0.5 : 1.0) * (ey ? 0.5 : 1.0) * (ez ? 0.5 : 1.0));
+        const T w = (T)((ex ? 0.5f : 1.f) * (ey ? 0.5f : 1.f) * (ez ? 0.5f : 1.f));
         acc = fma(w, rf[idf + ex + pf * ey + pp * ez], acc);
       }
     }
@@ -454,7 +455,7 @@ __global__ void __launch_bounds__(kBlock) k_prolong_all(GridDesc gf, CoarseSrc<T
   for (int j = 0; j < JJ; ++j) {
     // grid j sits m = JJ - j levels below: s = 2^m fine intervals per coarse one
     const int m = JJ - j, s = 1 << m, sm1 = s - 1;
-    const T inv_s = (T)1 / (T)s;
+    const T inv_s = (T)(1.f / (float)s);   // exact: s is a power of two
     const GridDesc& gc = src.g[j];
     const int cy0 = (gy >> m) - gc.loy, cz0 = DIM == 3 ? (gz >> m) - gc.loz : 0;
     const T wy1 = (T)(gy & sm1) * inv_s, wz1 = DIM == 3 ? (T)(gz & sm1) * inv_s : (T)0;
@@ -528,7 +529,7 @@ __global__ void __launch_bounds__(1024) k_coarse_tail(TailArgs<T> a, const DevSt
         for (int ez = (DIM == 3 ? -1 : 0); ez <= (DIM == 3 ? 1 : 0); ++ez)
           for (int ey = -1; ey <= 1; ++ey)
             for (int ex = -1; ex <= 1; ++ex) {
-              const T w = (T)((ex ? 0.5 : 1.0) * (ey ? 0.5 : 1.0) * (ez ? 0.5 : 1.0));
+              const T w = (T)((ex ? 0.5f : 1.f) * (ey ? 0.5f : 1.f) * (ez ? 0.5f : 1.f));
               acc = fma(w, rf[idf + ex + pf * ey + pp * ez], acc);
             }
       }
@@ -864,12 +865,17 @@ template <typename TI, typename TO>
 void launch_pack(const GridDesc& g, const TI* src, long long ld, TO* dst, int ncols, cudaStream_t s) {
   k_pack<TI, TO><<<grid_for(g.n * ncols, 4096), kBlock, 0, s>>>(g, src, ld, dst, ncols);
 }
-void launch_pack_flag(const GridDesc& g, const double* src, double* dst, int* nz, cudaStream_t s) {
-  k_pack_flag<<<grid_for(g.n, 4096), kBlock, 0, s>>>(g, src, dst, nz);
+template <typename TO>
+void launch_pack_flag(const GridDesc& g, const double* src, TO* dst, int* nz, cudaStream_t s) {
+  k_pack_flag<TO><<<grid_for(g.n, 4096), kBlock, 0, s>>>(g, src, dst, nz);
 }
 
+#ifndef MPCG_STENCIL_DW
 int g_sm_count = 0;
 void set_sm_count(int n) { g_sm_count = n; }
+#else
+extern int g_sm_count;
+#endif
 
 template <typename T>
 int spmm_blocks(const GridDesc& g, int C) {
@@ -881,19 +887,23 @@ int spmm_blocks(const GridDesc& g, int C) {
   if (w < need) w = need;
   return (int)(w < nb ? w : nb);
 }
+#ifndef MPCG_STENCIL_DW
 template int spmm_blocks<double>(const GridDesc&, int);
 template int spmm_blocks<float>(const GridDesc&, int);
+#endif
 
 template <typename TI, typename TO>
 void launch_unpack(const GridDesc& g, const TI* src, TO* dst, long long ld, int ncols, cudaStream_t s) {
   k_unpack<TI, TO><<<grid_for(g.n * ncols, 4096), kBlock, 0, s>>>(g, src, dst, ld, ncols);
 }
+#ifndef MPCG_STENCIL_DW
 template void launch_pack<double, double>(const GridDesc&, const double*, long long, double*, int, cudaStream_t);
 template void launch_pack<double, float>(const GridDesc&, const double*, long long, float*, int, cudaStream_t);
 template void launch_unpack<double, double>(const GridDesc&, const double*, double*, long long, int, cudaStream_t);
 template void launch_unpack<float, double>(const GridDesc&, const float*, double*, long long, int, cudaStream_t);
 template void launch_pack<float, float>(const GridDesc&, const float*, long long, float*, int, cudaStream_t);
 template void launch_unpack<float, float>(const GridDesc&, const float*, float*, long long, int, cudaStream_t);
+#endif
 
 template <typename T, int DIM>
 static void spmm_dim(const GridDesc& g, const T* st, const T* X, T* Y, int C, double* zaz, const DevState* state,
@@ -937,10 +947,12 @@ void launch_spmm(const GridDesc& g, const T* st, const T* X, T* Y, int C, double
   else if (g.dim == 3) spmm_dim<T, 3>(g, st, X, Y, C, zaz, state, s);
   else spmm_dim<T, 2>(g, st, X, Y, C, zaz, state, s);
 }
+#ifndef MPCG_STENCIL_DW
 template void launch_spmm<double>(const GridDesc&, const double*, const double*, double*, int, double*,
                                   const DevState*, cudaStream_t);
 template void launch_spmm<float>(const GridDesc&, const float*, const float*, float*, int, double*,
                                  const DevState*, cudaStream_t);
+#endif
 
 template <typename T>
 void launch_residual(const GridDesc& g, const T* st, const T* b, const T* x, T* r, double* part, cudaStream_t s,
@@ -950,10 +962,12 @@ void launch_residual(const GridDesc& g, const T* st, const T* b, const T* x, T* 
   else if (g.dim == 3) k_residual<T, 3><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part, xnz);
   else k_residual<T, 2><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part, xnz);
 }
+#ifndef MPCG_STENCIL_DW
 template void launch_residual<double>(const GridDesc&, const double*, const double*, const double*, double*,
                                       double*, cudaStream_t, const int*);
 template void launch_residual<float>(const GridDesc&, const float*, const float*, const float*, float*, double*,
                                      cudaStream_t, const int*);
+#endif
 
 template <typename T>
 void launch_restrict(const GridDesc& gf, const GridDesc& gc, const T* rf, T* rc, const DevState* state,
@@ -962,10 +976,12 @@ void launch_restrict(const GridDesc& gf, const GridDesc& gc, const T* rf, T* rc,
   if (gc.dim == 3) k_restrict<T, 3><<<grid, kBlock, 0, s>>>(gf, gc, rf, rc, state);
   else k_restrict<T, 2><<<grid, kBlock, 0, s>>>(gf, gc, rf, rc, state);
 }
+#ifndef MPCG_STENCIL_DW
 template void launch_restrict<double>(const GridDesc&, const GridDesc&, const double*, double*, const DevState*,
                                       cudaStream_t);
 template void launch_restrict<float>(const GridDesc&, const GridDesc&, const float*, float*, const DevState*,
                                      cudaStream_t);
+#endif
 
 template <typename T>
 void launch_jacobi(const GridDesc& g, const T* st, const T* dinv, const T* r, const T* sin, T* out, int mode,
@@ -994,25 +1010,31 @@ void launch_vres(const GridDesc& g, const T* st, const T* r, const T* x, T* t, c
   k_vres<T, false><<<dim3(blocks_for(3 * (g.cstride / vw<T>())), g.nb), kBlock, 0, s>>>(g, st, r, x, t, nullptr,
                                                                                         state, nullptr);
 }
+#ifndef MPCG_STENCIL_DW
 template void launch_vres<double>(const GridDesc&, const double*, const double*, const double*, double*,
                                   const DevState*, cudaStream_t);
 template void launch_vres<float>(const GridDesc&, const float*, const float*, const float*, float*,
                                  const DevState*, cudaStream_t);
+#endif
 
 template <typename T>
 void launch_vblock(const GridDesc& g, const T* dinv, const T* t, const T* sin, T* out, const DevState* state,
                    cudaStream_t s) {
   k_vblock<T><<<dim3(blocks_for(g.cstride / vw<T>()), g.nb), kBlock, 0, s>>>(g, dinv, t, sin, out, state);
 }
+#ifndef MPCG_STENCIL_DW
 template void launch_vblock<double>(const GridDesc&, const double*, const double*, const double*, double*,
                                     const DevState*, cudaStream_t);
 template void launch_vblock<float>(const GridDesc&, const float*, const float*, const float*, float*,
                                    const DevState*, cudaStream_t);
+#endif
 
+#ifndef MPCG_STENCIL_DW
 template void launch_jacobi<double>(const GridDesc&, const double*, const double*, const double*, const double*,
                                     double*, int, const DevState*, cudaStream_t);
 template void launch_jacobi<float>(const GridDesc&, const float*, const float*, const float*, const float*, float*,
                                    int, const DevState*, cudaStream_t);
+#endif
 
 
 // out = sum of the ncols columns of Zc (the additive MG correction B r of
@@ -1035,8 +1057,10 @@ template <typename T>
 void launch_sum_columns(const GridDesc& g, const T* Zc, int ncols, T* out, const DevState* state, cudaStream_t s) {
   k_sum_columns<T><<<dim3(stream_blocks(g), g.nb), kBlock, 0, s>>>(g, Zc, ncols, out, state);
 }
+#ifndef MPCG_STENCIL_DW
 template void launch_sum_columns<double>(const GridDesc&, const double*, int, double*, const DevState*, cudaStream_t);
 template void launch_sum_columns<float>(const GridDesc&, const float*, int, float*, const DevState*, cudaStream_t);
+#endif
 
 template <typename T>
 void launch_coarse_tail(int jt, const GridDesc* g, const T* const* st, const T* const* dinv, T* const* r,
@@ -1057,12 +1081,14 @@ void launch_coarse_tail(int jt, const GridDesc* g, const T* const* st, const T* 
   if (g[0].dim == 3) k_coarse_tail<T, 3><<<grid, 1024, smem, s>>>(a, state);
   else k_coarse_tail<T, 2><<<grid, 1024, smem, s>>>(a, state);
 }
+#ifndef MPCG_STENCIL_DW
 template void launch_coarse_tail<double>(int, const GridDesc*, const double* const*, const double* const*,
                                          double* const*, double* const*, const double*, const double*,
                                          const DevState*, cudaStream_t);
 template void launch_coarse_tail<float>(int, const GridDesc*, const float* const*, const float* const*,
                                         float* const*, float* const*, const float*, const double*, const DevState*,
                                         cudaStream_t);
+#endif
 
 template <typename T>
 void launch_gs_colour(const GridDesc& g, const T* st, const T* b, T* x, int colour, double omega, const DevState* state,
@@ -1071,10 +1097,12 @@ void launch_gs_colour(const GridDesc& g, const T* st, const T* b, T* x, int colo
   if (g.dim == 3) k_gs_colour<T, 3><<<grid, kBlock, 0, s>>>(g, st, b, x, colour, (T)omega, state);
   else k_gs_colour<T, 2><<<grid, kBlock, 0, s>>>(g, st, b, x, colour, (T)omega, state);
 }
+#ifndef MPCG_STENCIL_DW
 template void launch_gs_colour<double>(const GridDesc&, const double*, const double*, double*, int, double,
                                        const DevState*, cudaStream_t);
 template void launch_gs_colour<float>(const GridDesc&, const float*, const float*, float*, int, double,
                                       const DevState*, cudaStream_t);
+#endif
 
 template <typename T>
 void launch_defect(const GridDesc& g, const T* st, const T* b, const T* x, T* d, const DevState* state,
@@ -1083,10 +1111,12 @@ void launch_defect(const GridDesc& g, const T* st, const T* b, const T* x, T* d,
   if (g.dim == 3) k_defect<T, 3><<<grid, kBlock, 0, s>>>(g, st, b, x, d, state);
   else k_defect<T, 2><<<grid, kBlock, 0, s>>>(g, st, b, x, d, state);
 }
+#ifndef MPCG_STENCIL_DW
 template void launch_defect<double>(const GridDesc&, const double*, const double*, const double*, double*,
                                     const DevState*, cudaStream_t);
 template void launch_defect<float>(const GridDesc&, const float*, const float*, const float*, float*,
                                    const DevState*, cudaStream_t);
+#endif
 
 template <typename T>
 void launch_prolong_add(const GridDesc& gc, const GridDesc& gf, const T* coarse, T* fine, const DevState* state,
@@ -1095,17 +1125,21 @@ void launch_prolong_add(const GridDesc& gc, const GridDesc& gf, const T* coarse,
   if (gf.dim == 3) k_prolong_add<T, 3><<<grid, kBlock, 0, s>>>(gc, gf, coarse, fine, state);
   else k_prolong_add<T, 2><<<grid, kBlock, 0, s>>>(gc, gf, coarse, fine, state);
 }
+#ifndef MPCG_STENCIL_DW
 template void launch_prolong_add<double>(const GridDesc&, const GridDesc&, const double*, double*, const DevState*,
                                          cudaStream_t);
 template void launch_prolong_add<float>(const GridDesc&, const GridDesc&, const float*, float*, const DevState*,
                                         cudaStream_t);
+#endif
 
 template <typename T>
 void launch_add_to(const GridDesc& g, const T* src, T* dst, const DevState* state, cudaStream_t s) {
   k_add_to<T><<<dim3(blocks_for(g.npts), g.nb), kBlock, 0, s>>>(g, src, dst, state);
 }
+#ifndef MPCG_STENCIL_DW
 template void launch_add_to<double>(const GridDesc&, const double*, double*, const DevState*, cudaStream_t);
 template void launch_add_to<float>(const GridDesc&, const float*, float*, const DevState*, cudaStream_t);
+#endif
 
 template <typename T>
 void launch_prolong_all(const GridDesc& gf, const T* const* coarse, const GridDesc* gcs, int J, T* Z,
@@ -1130,26 +1164,80 @@ void launch_prolong_all(const GridDesc& gf, const T* const* coarse, const GridDe
   }
 #undef MPCG_PROLONG_CASE
 }
+#ifndef MPCG_STENCIL_DW
 template void launch_prolong_all<double>(const GridDesc&, const double* const*, const GridDesc*, int, double*,
                                          const DevState*, cudaStream_t);
 template void launch_prolong_all<float>(const GridDesc&, const float* const*, const GridDesc*, int, float*,
                                         const DevState*, cudaStream_t);
+#endif
 
+#ifndef MPCG_STENCIL_DW
 void launch_galerkin(const GridDesc& gf, const GridDesc& gc, const double* stf, double* stc, cudaStream_t s) {
   const dim3 grid(blocks_for(gc.npts), gc.nb);
   if (gc.dim == 3) k_galerkin<3><<<grid, kBlock, 0, s>>>(gf, gc, stf, stc);
   else k_galerkin<2><<<grid, kBlock, 0, s>>>(gf, gc, stf, stc);
 }
+#endif
 
 template <typename T>
 void launch_dinv(const GridDesc& g, const double* st, T* dinv, double omega, cudaStream_t s) {
   k_dinv<T><<<dim3(blocks_for(g.npts), g.nb), kBlock, 0, s>>>(g, st, dinv, omega);
 }
+#ifndef MPCG_STENCIL_DW
 template void launch_dinv<double>(const GridDesc&, const double*, double*, double, cudaStream_t);
 template void launch_dinv<float>(const GridDesc&, const double*, float*, double, cudaStream_t);
+#endif
 
+#ifndef MPCG_STENCIL_DW
 void launch_convert_f32(const double* src, float* dst, long long count, cudaStream_t s) {
   k_convert_f32<<<grid_for(count, 4096), kBlock, 0, s>>>(src, dst, count);
 }
+#endif
+
+#ifndef MPCG_STENCIL_DW
+template void launch_pack_flag<double>(const GridDesc&, const double*, double*, int*, cudaStream_t);
+#else
+// The double-word instances (FP64 data, double-FP32 arithmetic), compiled in
+// their own translation unit (stencil_dw.cu) to keep the build parallel.
+template void launch_pack<double, dw>(const GridDesc&, const double*, long long, dw*, int, cudaStream_t);
+template void launch_unpack<dw, double>(const GridDesc&, const dw*, double*, long long, int, cudaStream_t);
+template void launch_pack_flag<dw>(const GridDesc&, const double*, dw*, int*, cudaStream_t);
+template int spmm_blocks<dw>(const GridDesc&, int);
+template void launch_spmm<dw>(const GridDesc&, const dw*, const dw*, dw*, int, double*, const DevState*,
+                              cudaStream_t);
+template void launch_residual<dw>(const GridDesc&, const dw*, const dw*, const dw*, dw*, double*, cudaStream_t,
+                                  const int*);
+template void launch_restrict<dw>(const GridDesc&, const GridDesc&, const dw*, dw*, const DevState*, cudaStream_t);
+template void launch_jacobi<dw>(const GridDesc&, const dw*, const dw*, const dw*, const dw*, dw*, int,
+                                const DevState*, cudaStream_t);
+template void launch_vres<dw>(const GridDesc&, const dw*, const dw*, const dw*, dw*, const DevState*, cudaStream_t);
+template void launch_vblock<dw>(const GridDesc&, const dw*, const dw*, const dw*, dw*, const DevState*,
+                                cudaStream_t);
+template void launch_sum_columns<dw>(const GridDesc&, const dw*, int, dw*, const DevState*, cudaStream_t);
+template void launch_coarse_tail<dw>(int, const GridDesc*, const dw* const*, const dw* const*, dw* const*,
+                                     dw* const*, const dw*, const double*, const DevState*, cudaStream_t);
+template void launch_gs_colour<dw>(const GridDesc&, const dw*, const dw*, dw*, int, double, const DevState*,
+                                   cudaStream_t);
+template void launch_defect<dw>(const GridDesc&, const dw*, const dw*, const dw*, dw*, const DevState*,
+                                cudaStream_t);
+template void launch_prolong_add<dw>(const GridDesc&, const GridDesc&, const dw*, dw*, const DevState*,
+                                     cudaStream_t);
+template void launch_add_to<dw>(const GridDesc&, const dw*, dw*, const DevState*, cudaStream_t);
+template void launch_prolong_all<dw>(const GridDesc&, const dw* const*, const GridDesc*, int, dw*,
+                                     const DevState*, cudaStream_t);
+template void launch_dinv<dw>(const GridDesc&, const double*, dw*, double, cudaStream_t);
+
+namespace {
+__global__ void k_convert_dw(const double* __restrict__ src, dw* __restrict__ dst, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = dw_from_double(src[i]);
+}
+}  // namespace
+
+void launch_convert_dw(const double* src, dw* dst, long long count, cudaStream_t s) {
+  k_convert_dw<<<grid_for(count, 4096), kBlock, 0, s>>>(src, dst, count);
+}
+#endif
 
 }  // namespace mpcg

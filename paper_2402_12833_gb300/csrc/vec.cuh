@@ -4,6 +4,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dw.cuh"
 
 namespace mpcg {
 
@@ -44,6 +45,23 @@ struct Vec<double> {
   }
 };
 
+// double-word pairs: two per 16-byte vector, like doubles
+template <>
+struct Vec<dw> {
+  static constexpr int W = 2;
+  __device__ static __forceinline__ void load(const dw* p, dw (&v)[2]) {
+    const float4 q = __ldcs(reinterpret_cast<const float4*>(p));
+    v[0] = dw(q.x, q.y); v[1] = dw(q.z, q.w);
+  }
+  __device__ static __forceinline__ void load_keep(const dw* p, dw (&v)[2]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = dw(q.x, q.y); v[1] = dw(q.z, q.w);
+  }
+  __device__ static __forceinline__ void store(dw* p, const dw (&v)[2]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+  }
+};
+
 // Loads and stores of W consecutive values (W = 1 or the full vector width
 // of Vec<T>), for kernels whose points per thread depend on the grid size.
 template <typename T, int W>
@@ -58,6 +76,8 @@ template <>
 struct VecN<float, 4> : Vec<float> {};
 template <>
 struct VecN<double, 2> : Vec<double> {};
+template <>
+struct VecN<dw, 2> : Vec<dw> {};
 
 // Number of values a lane holds after `steps` halvings of nv values.
 __host__ __device__ constexpr int rs_count(int nv, int steps) {

@@ -28,6 +28,7 @@ MPCG_SMOOTHER_JACOBI = 0
 MPCG_SMOOTHER_SSOR = 1
 MPCG_FP64 = 0
 MPCG_MIXED = 1
+MPCG_FP64_DW = 2   # FP64 data, double-word (2 x FP32) arithmetic
 MPCG_MAX_COLS = 12
 MPCG_MAX_WINDOW = 16
 MPCG_AMG_A = 0
