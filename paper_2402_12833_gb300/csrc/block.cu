@@ -35,32 +35,66 @@ __global__ void __launch_bounds__(kBlock, kIsDw<T> ? 1 : 3) k_gram_window(GridDe
   const long long bo = (long long)pb * g.len + g.G;
   const T* AP = win.AP[slot] + bo;
   const T* Zb = Z + bo;
-  constexpr int W = Vec<T>::W;
-  const long long ngroups = g.npts / W;
+  // double-word: one point per thread and step (register pressure); the
+  // group count per chunk follows the chunking of the vector width
+  constexpr int VW = Vec<T>::W;
+  constexpr int W = kIsDw<T> ? 1 : VW;
+  const long long ngroups = g.npts / VW;
   const long long per = (ngroups + nchunks - 1) / nchunks;
-  const long long g0 = (long long)chunk * per;
-  const long long g1 = g0 + per < ngroups ? g0 + per : ngroups;
+  const long long g0 = (long long)chunk * per * (VW / W);
+  const long long g1 = (g0 + per * (VW / W)) < ngroups * (VW / W) ? g0 + per * (VW / W) : ngroups * (VW / W);
   // the chunk count keeps every thread at <= 16 vector groups (64 points in
   // FP32) before its partial sums enter the reduction
-  T acc[C * C];
+  typename Acc<T>::type acc[C * C];
 #pragma unroll
-  for (int e = 0; e < C * C; ++e) acc[e] = 0;
-  for (long long q = g0 + threadIdx.x; q < g1; q += blockDim.x) {
+  for (int e = 0; e < C * C; ++e) acc[e] = Acc<T>::of(T(0));
+  auto load_point = [&](long long q, T (&z)[C][W], T (&ap)[C][W]) {
     const long long i = q * W;
-    T z[C][W], ap[C][W];
 #pragma unroll
-    for (int b = 0; b < C; ++b) Vec<T>::load_keep(Zb + (long long)b * g.cp + i, z[b]);
+    for (int b = 0; b < C; ++b) VecN<T, W>::load_keep(Zb + (long long)b * g.cp + i, z[b]);
 #pragma unroll
-    for (int a = 0; a < C; ++a) Vec<T>::load(AP + (long long)a * g.cp + i, ap[a]);
+    for (int a = 0; a < C; ++a) VecN<T, W>::load(AP + (long long)a * g.cp + i, ap[a]);
+  };
+  auto accumulate = [&](const T (&z)[C][W], const T (&ap)[C][W]) {
 #pragma unroll
     for (int a = 0; a < C; ++a)
 #pragma unroll
       for (int b = 0; b < C; ++b)
 #pragma unroll
-        for (int w = 0; w < W; ++w) acc[a * C + b] = fma(ap[a][w], z[b][w], acc[a * C + b]);
+        for (int w = 0; w < W; ++w) mac(acc[a * C + b], ap[a][w], z[b][w]);
+  };
+  if constexpr (kIsDw<T>) {
+    // the double-word sums leave few warps per SM: the next point's loads
+    // are issued before the current point's products (software pipelining)
+    long long q = g0 + threadIdx.x;
+    T z[C][W], ap[C][W];
+    if (q < g1) load_point(q, z, ap);
+    while (q < g1) {
+      const long long qn = q + blockDim.x;
+      T zn[C][W], apn[C][W];
+      if (qn < g1) load_point(qn, zn, apn);
+      accumulate(z, ap);
+#pragma unroll
+      for (int b = 0; b < C; ++b)
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          z[b][w] = zn[b][w];
+          ap[b][w] = apn[b][w];
+        }
+      q = qn;
+    }
+  } else {
+    for (long long q = g0 + threadIdx.x; q < g1; q += blockDim.x) {
+      T z[C][W], ap[C][W];
+      load_point(q, z, ap);
+      accumulate(z, ap);
+    }
   }
+  T fin[C * C];
+#pragma unroll
+  for (int e = 0; e < C * C; ++e) fin[e] = Acc<T>::value(acc[e]);
   double* pj = part + ((long long)pb * m + jj) * C * C * nchunks;
-  block_sum_store<T, C * C>(acc, pj, nchunks, chunk);
+  block_sum_store<T, C * C>(fin, pj, nchunks, chunk);
 }
 
 template <typename T, int C>
@@ -91,30 +125,36 @@ __global__ void __launch_bounds__(kBlock, kIsDw<T> ? 1 : 2) k_orth_update(GridDe
   const T* Zb = Z + bo;
   const T* AZb = AZ + bo;
   const T* rb = r + bo;
-  constexpr int W = Vec<T>::W;
+  constexpr int W = kIsDw<T> ? 1 : Vec<T>::W;   // double-word: one point per thread (registers)
   constexpr int NG = C * (C + 1) / 2;
-  T acc[NG + C];
+  using A = typename Acc<T>::type;
+  A acc[NG + C];
 #pragma unroll
-  for (int i = 0; i < NG + C; ++i) acc[i] = 0;
+  for (int i = 0; i < NG + C; ++i) acc[i] = Acc<T>::of(T(0));
   const long long ngroups = g.npts / W;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
        q += (long long)gridDim.x * blockDim.x) {
     const long long i = q * W;
-    T p[C][W], ap[C][W];
+    A pacc[C][W], apacc[C][W];
 #pragma unroll
     for (int b = 0; b < C; ++b) {
-      Vec<T>::load(Zb + (long long)b * g.cp + i, p[b]);
-      Vec<T>::load(AZb + (long long)b * g.cp + i, ap[b]);
+      T zv[W], azv[W];
+      VecN<T, W>::load(Zb + (long long)b * g.cp + i, zv);
+      VecN<T, W>::load(AZb + (long long)b * g.cp + i, azv);
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        pacc[b][w] = Acc<T>::of(zv[w]);
+        apacc[b][w] = Acc<T>::of(azv[w]);
+      }
     }
-    for (int jj = 0; jj < cnt; ++jj) {
-      const T* Pj = pp[jj];
-      const T* APj = app[jj];
-      T pa[C][W], apa[C][W];
+    auto load_block = [&](int jj, T (&pa)[C][W], T (&apa)[C][W]) {
 #pragma unroll
       for (int a = 0; a < C; ++a) {
-        Vec<T>::load(Pj + (long long)a * g.cp + i, pa[a]);
-        Vec<T>::load(APj + (long long)a * g.cp + i, apa[a]);
+        VecN<T, W>::load(pp[jj] + (long long)a * g.cp + i, pa[a]);
+        VecN<T, W>::load(app[jj] + (long long)a * g.cp + i, apa[a]);
       }
+    };
+    auto apply_block = [&](int jj, const T (&pa)[C][W], const T (&apa)[C][W]) {
 #pragma unroll
       for (int a = 0; a < C; ++a)
 #pragma unroll
@@ -122,32 +162,67 @@ __global__ void __launch_bounds__(kBlock, kIsDw<T> ? 1 : 2) k_orth_update(GridDe
           const T bt = beta[jj][a][b];
 #pragma unroll
           for (int w = 0; w < W; ++w) {
-            p[b][w] = fma(-pa[a][w], bt, p[b][w]);
-            ap[b][w] = fma(-apa[a][w], bt, ap[b][w]);
+            mac(pacc[b][w], -pa[a][w], bt);
+            mac(apacc[b][w], -apa[a][w], bt);
           }
         }
+    };
+    if constexpr (kIsDw<T>) {
+      // few warps per SM in double-word: block jj + 1 is loaded while
+      // block jj's products run (software pipelining)
+      T pa[C][W], apa[C][W];
+      if (cnt > 0) load_block(0, pa, apa);
+      for (int jj = 0; jj < cnt; ++jj) {
+        T pn[C][W], apn[C][W];
+        if (jj + 1 < cnt) load_block(jj + 1, pn, apn);
+        apply_block(jj, pa, apa);
+#pragma unroll
+        for (int a = 0; a < C; ++a)
+#pragma unroll
+          for (int w = 0; w < W; ++w) {
+            pa[a][w] = pn[a][w];
+            apa[a][w] = apn[a][w];
+          }
+      }
+    } else {
+      for (int jj = 0; jj < cnt; ++jj) {
+        T pa[C][W], apa[C][W];
+        load_block(jj, pa, apa);
+        apply_block(jj, pa, apa);
+      }
     }
+    T p[C][W], ap[C][W];
+#pragma unroll
+    for (int b = 0; b < C; ++b)
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        p[b][w] = Acc<T>::value(pacc[b][w]);
+        ap[b][w] = Acc<T>::value(apacc[b][w]);
+      }
     T rv[W];
-    Vec<T>::load(rb + i, rv);
+    VecN<T, W>::load(rb + i, rv);
     int k = 0;
 #pragma unroll
     for (int a = 0; a < C; ++a) {
-      Vec<T>::store(Pn + (long long)a * g.cp + i, p[a]);
-      Vec<T>::store(APn + (long long)a * g.cp + i, ap[a]);
+      VecN<T, W>::store(Pn + (long long)a * g.cp + i, p[a]);
+      VecN<T, W>::store(APn + (long long)a * g.cp + i, ap[a]);
 #pragma unroll
       for (int b = a; b < C; ++b) {
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-          acc[k] = fma(p[a][w], ap[b][w], acc[k]);
-          acc[k] = fma(p[b][w], ap[a][w], acc[k]);
+          mac(acc[k], p[a][w], ap[b][w]);
+          mac(acc[k], p[b][w], ap[a][w]);
         }
         ++k;
       }
 #pragma unroll
-      for (int w = 0; w < W; ++w) acc[NG + a] = fma(p[a][w], rv[w], acc[NG + a]);
+      for (int w = 0; w < W; ++w) mac(acc[NG + a], p[a][w], rv[w]);
     }
   }
-  block_sum_store<T, NG + C>(acc, part + (long long)pb * (NG + C) * gridDim.x, gridDim.x, blockIdx.x);
+  T fin[NG + C];
+#pragma unroll
+  for (int i = 0; i < NG + C; ++i) fin[i] = Acc<T>::value(acc[i]);
+  block_sum_store<T, NG + C>(fin, part + (long long)pb * (NG + C) * gridDim.x, gridDim.x, blockIdx.x);
 }
 
 template <typename T, int C>
