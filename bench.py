@@ -164,7 +164,7 @@ def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops, S=27, vector=False
     share = tot[dom] / sum(tot.values())
     if bytes_sum == 0:
         return dom, None, share, tot
-    if w == 8:   # FP64 arithmetic on GB300 runs far below the HBM roofline: ALU bound
+    if w == 8 and fp64_alu_peak_tflops:   # FP64 arithmetic on GB300 runs far below the HBM roofline: ALU bound
         ach = flops_sum / (dur * 1e-3) / 1e12
         out = {"bound": "alu", "achieved": ach, "peak": fp64_alu_peak_tflops, "unit": "TFLOP/s",
                "frac": ach / fp64_alu_peak_tflops, "traffic": None,
@@ -178,31 +178,78 @@ def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops, S=27, vector=False
     return dom, out, share, tot
 
 
-def measured_traffic(key: str):
-    """DRAM bytes per launch of a kernel class, from the ncu summaries under
-    profiles/ (lines "traffic: key=<leg>:<class> bytes_per_launch=<B>
-    source=<file>[,<file>] sha256=<hash>[,<hash>]").  None unless the
-    kernels' source files are unchanged since the counters were taken."""
+def profile_value(kind: str, key: str, field: str):
+    """A figure recorded from an ncu capture in the summaries under profiles/
+    (lines "<kind>: key=<key> <field>=<value> ... source=<file>[,<file>]
+    sha256=<hash>[,<hash>]").  None unless every listed kernel source file is
+    unchanged since the counters were taken."""
     import glob
     import hashlib
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         with open(path) as f:
             for line in f:
-                if not line.startswith("traffic: "):
+                if not line.startswith(kind + ": "):
                     continue
                 kv = dict(t.split("=", 1) for t in line.split()[1:])
                 if kv.get("key") != key:
                     continue
-                # source=a.cu[,b.cu] sha256=h_a[,h_b]: every listed file unchanged
-                for name, digest in zip(kv["source"].split(","), kv["sha256"].split(",")):
-                    src = os.path.join(ROOT, "paper_2402_12833_gb300", "csrc", name)
-                    if not os.path.exists(src):
-                        return None
-                    with open(src, "rb") as g:
-                        if hashlib.sha256(g.read()).hexdigest() != digest:
-                            return None
-                return float(kv["bytes_per_launch"])
+                # source=a.cu[,b.cu] sha256=h_a[,h_b] (one digest per file) or
+                # sha256=h (one digest of the files' contents in order):
+                # every listed file unchanged, else look further
+                names, digests = kv["source"].split(","), kv["sha256"].split(",")
+                paths = [os.path.join(ROOT, "paper_2402_12833_gb300", "csrc", nm) for nm in names]
+                if not all(os.path.exists(q) for q in paths):
+                    continue
+                blobs = []
+                for q in paths:
+                    with open(q, "rb") as g:
+                        blobs.append(g.read())
+                if len(digests) == len(names):
+                    ok = all(hashlib.sha256(bl).hexdigest() == dg for bl, dg in zip(blobs, digests))
+                else:
+                    ok = hashlib.sha256(b"".join(blobs)).hexdigest() == digests[0]
+                if ok:
+                    return float(kv[field])
     return None
+
+
+def measured_traffic(key: str):
+    """DRAM bytes per launch of a kernel class ("traffic:" lines, key
+    <leg>:<class>)."""
+    return profile_value("traffic", key, "bytes_per_launch")
+
+
+def bmin_per_iteration(iters: int, n: int, C: int, m: int, w: int, S: int) -> float:
+    """Algorithmic bytes of one MPCG iteration on the fine grid, the B_min of
+    the survey's measurement section: read the stored window (P_j, A P_j),
+    write the new block (P, A P), read and write x and r, read the operator
+    once -- (2 cnt C + 2 C + 4) w + S w per unknown, with cnt the blocks in
+    the window at that iteration (min(k - 1, m) for update k), averaged over
+    the solve.  Coarse grids (at most 1/7 of the fine chain in 3D) are left
+    out, so the fraction errs low."""
+    tot = 0.0
+    for k in range(1, iters + 1):
+        cnt = min(k - 1, m)
+        tot += ((2 * cnt * C + 2 * C + 4) * w + S * w) * n
+    return tot / iters
+
+
+def per_iteration(key: str, ms_per_step: float, iters: int, n: int, C: int, m: int, w: int, S: int, peaks):
+    """Per-iteration HBM figures of one solve: the iteration time (the timed
+    solve / its x updates, so per-solve work counts against it), the
+    algorithmic B_min bandwidth and, where a committed ncu capture of one
+    steady-state iteration of this leg exists for the current kernels, the
+    measured DRAM bandwidth (dram__bytes_read + write of that iteration's
+    launches / the iteration time)."""
+    t = ms_per_step / iters * 1e-3
+    bmin = bmin_per_iteration(iters, n, C, m, w, S)
+    dram = profile_value("iteration", key, "dram_bytes")
+    out = {"ms": t * 1e3, "iterations": iters, "bmin_bytes": bmin, "bmin_GBps": bmin / t / 1e9,
+           "bmin_frac": bmin / t / 1e9 / peaks["hbm_gbs"], "dram_bytes": dram,
+           "dram_GBps": dram / t / 1e9 if dram else None,
+           "dram_frac": dram / t / 1e9 / peaks["hbm_gbs"] if dram else None,
+           "peak_GBps": peaks["hbm_gbs"], "peak_source": peaks["source"]}
+    return out
 
 
 def load_peaks():
@@ -238,6 +285,64 @@ for rep in range({warmup} + {steps}):
 print(json.dumps({{"setup_s": t1 - t0, "solve_s": sum(times) / len(times), "iters": res.iters, "n": prob.n,
                   "res": res.res_hist[-1], "steps": len(times)}}))
 """
+
+
+def usable_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def host_mem_available_gb() -> float:
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    return 0.0
+
+
+ORACLE_GB_PER_PROCESS = 5.0   # one 129^3 oracle solve peaks at 4.1 GB resident; with margin
+
+
+def oracle_baselines(n: int):
+    """The FP64 oracle as it stands on the host cores, started after every GPU
+    measurement so that it does not compete for them: one process on one
+    core (one full solve), then one process per usable core, each solving the
+    same workload at once (host throughput = processes x n / slowest solve;
+    capped by the memory available).  Returns (all-cores, single-core)."""
+    cmd, env = oracle_cmd(0, 1)
+    single = None
+    out = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode == 0:
+        o = json.loads(out.stdout.strip().splitlines()[-1])
+        single = {"value": o["n"] / o["solve_s"], "unit": "DOFs/s", "cores": 1, "kind": "oracle",
+                  "sample": f"one full FP64 solve of the workload ({o['iters']} iterations, {o['solve_s']:.1f} s; "
+                            f"hierarchy setup {o['setup_s']:.1f} s excluded)", "iters": o["iters"]}
+    else:
+        return ({"value": None, "unit": "DOFs/s", "cores": 1, "kind": "oracle",
+                 "sample": "failed: " + out.stderr[-300:]}, None)
+    cores = usable_cores()
+    nproc = max(1, min(cores, int(host_mem_available_gb() // ORACLE_GB_PER_PROCESS)))
+    procs = [subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+             for _ in range(nproc)]
+    times, iters = [], None
+    for p in procs:
+        o_out, o_err = p.communicate(timeout=3600)
+        if p.returncode != 0:
+            return single, single
+        o = json.loads(o_out.strip().splitlines()[-1])
+        times.append(o["solve_s"])
+        iters = o["iters"]
+    allc = {"value": nproc * n / max(times), "unit": "DOFs/s", "cores": nproc, "kind": "oracle",
+            "sample": f"{nproc} single-threaded oracle processes ({cores} usable cores), each one full FP64 solve "
+                      f"of the workload at the same time ({iters} iterations; slowest {max(times):.1f} s, "
+                      f"fastest {min(times):.1f} s; setup excluded)", "iters": iters,
+            "single_core": single}
+    return allc, single
 
 
 def oracle_cmd(warmup: int, steps: int, seed: int = RHS_SEED):
@@ -284,11 +389,6 @@ def bench_ours(args):
     import torch.distributed as dist
 
     rank, world, local = _rank()
-    # the CPU baseline runs in a fresh process started before any CUDA work
-    oracle_proc = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cmd, env = oracle_cmd(0, 1)
-        oracle_proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -308,10 +408,10 @@ def bench_ours(args):
     sptr = stream.cuda_stream
     st = torch.from_numpy(prob.stencil).cuda()
     ug = 0 if args.direct else 1
-    H = {"mixed": M.Hierarchy(st, DIM, NODES, prob.levels, m=M_WINDOW, precision=M.MPCG_MIXED, stream=sptr,
-                              use_graph=ug),
-         "fp64": M.Hierarchy(st, DIM, NODES, prob.levels, m=M_WINDOW, precision=M.MPCG_FP64, stream=sptr,
-                             use_graph=ug)}
+    legs = ("fp64", "fp64_dw", "mixed") if args.only is None else (args.only,)
+    precs = {"mixed": M.MPCG_MIXED, "fp64": M.MPCG_FP64, "fp64_dw": M.MPCG_FP64_DW}
+    H = {k: M.Hierarchy(st, DIM, NODES, prob.levels, m=M_WINDOW, precision=precs[k], stream=sptr, use_graph=ug)
+         for k in legs}
     if args.matrix_free:   # the matrix-free fine operator (element coefficients kappa = 1) in the mixed solve
         M.mg_attach_q1_kappa(H["mixed"].h, torch.ones((NODES - 1) ** DIM, dtype=torch.float64, device="cuda"))
     b = torch.from_numpy(prob.b).cuda()
@@ -328,8 +428,7 @@ def bench_ours(args):
 
     res = {}
     clocks = None
-    keys = ("fp64", "mixed") if args.only is None else (args.only,)
-    for key in keys:
+    for key in legs:
         h = H[key]
         for _ in range(args.warmup):
             x.zero_()
@@ -360,7 +459,7 @@ def bench_ours(args):
         true_res = float(torch.linalg.norm(b - Ax) / torch.linalg.norm(b))
         res[key] = {"ms_per_step": ms, "value": world * n / (ms * 1e-3), "iters": iters[-1],
                     "launches_per_step": launches, "true_rel_residual": true_res,
-                    "x": x.detach().clone() if key == "fp64" else None}
+                    "x": x.detach().clone() if key in ("fp64", "fp64_dw") else None}
 
     if args.only is not None:
         r = res[args.only]
@@ -369,8 +468,6 @@ def bench_ours(args):
                               "ms_per_step": r["ms_per_step"], "iterations": r["iters"],
                               "true_rel_residual": r["true_rel_residual"], "launches_per_step": r["launches_per_step"],
                               "clocks": clocks}))
-        if oracle_proc is not None:
-            oracle_proc.kill()
         for h in H.values():
             h.close()
         return 0
@@ -411,11 +508,13 @@ def bench_ours(args):
 
     # per-kernel durations from a live profiled solve (CUDA events on the solve stream)
     prof = {}
-    for key, w in (("mixed", 4), ("fp64", 8)):
+    for key, w in (("mixed", 4), ("fp64", 8), ("fp64_dw", 8)):
         x.zero_()
         _, k, classes, trace = M.mpcg_solve_profiled(H[key].h, b, x, RTOL, MAXIT)
+        # FP64 arithmetic is bound by the FP64 pipe; the double-word kernels
+        # are reported against the HBM roofline they aim at
         dom, rl, share, tot = roofline(trace, level_dofs(NODES, DIM, prob.levels), prob.levels, M_WINDOW, w, peaks,
-                                       FP64_PEAK_TFLOPS)
+                                       FP64_PEAK_TFLOPS if key == "fp64" else None)
         if rl is not None:
             rl["traffic"] = measured_traffic(f"poisson3d_{key}:{dom}")
         prof[key] = {"roofline": rl, "class_ms": {c: round(v, 4) for c, v in tot.items()}}
@@ -423,6 +522,11 @@ def bench_ours(args):
     x.zero_()
     H["mixed"].solve(b, x, rtol=RTOL, maxit=MAXIT, histories=False)
     mix_vs_fp64 = float(torch.linalg.norm(x - res["fp64"]["x"]) / torch.linalg.norm(res["fp64"]["x"]))
+    dw_vs_fp64 = float(torch.linalg.norm(res["fp64_dw"]["x"] - res["fp64"]["x"]) / torch.linalg.norm(res["fp64"]["x"]))
+    piter = {}
+    for key, w in (("mixed", 4), ("fp64", 8), ("fp64_dw", 8)):
+        piter[key] = per_iteration(f"poisson3d_{key}", res[key]["ms_per_step"], res[key]["iters"], n, prob.levels,
+                                   M_WINDOW, w, 27, peaks)
 
     # end to end through the C ABI with pinned host buffers
     bh = torch.from_numpy(prob.b).pin_memory().numpy()
@@ -443,17 +547,11 @@ def bench_ours(args):
     e2e_s = max_over_ranks(e2e_total / args.steps)
     barrier()
 
+    for h in H.values():
+        h.close()
     cpu = None
-    if oracle_proc is not None:
-        out, err = oracle_proc.communicate(timeout=1800)
-        if oracle_proc.returncode == 0:
-            o = json.loads(out.strip().splitlines()[-1])
-            cpu = {"value": o["n"] / o["solve_s"], "unit": "DOFs/s", "cores": 1, "kind": "oracle",
-                   "sample": f"one full FP64 solve of the same workload ({o['iters']} iterations, "
-                             f"{o['solve_s']:.1f} s; hierarchy setup {o['setup_s']:.1f} s excluded)",
-                   "iters": o["iters"]}
-        else:
-            cpu = {"value": None, "unit": "DOFs/s", "cores": 1, "kind": "oracle", "sample": "failed: " + err[-300:]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, _ = oracle_baselines(n)
 
     if rank == 0:
         mx = res["mixed"]
@@ -473,10 +571,19 @@ def bench_ours(args):
                             "operator": "fine grid rebuilt from the element coefficients (kappa = 1) in the FP32 "
                                         "SpMM and Jacobi kernels; stored stencils elsewhere"},
             "roofline": prof["mixed"]["roofline"],
+            "per_iteration": piter["mixed"],
             "fp64": {"value": res["fp64"]["value"], "unit": "DOFs/s", "ms_per_step": res["fp64"]["ms_per_step"],
                      "iterations": res["fp64"]["iters"], "true_rel_residual": res["fp64"]["true_rel_residual"],
-                     "roofline": prof["fp64"]["roofline"]},
-            "kernel_ms_per_solve": {"mixed": prof["mixed"]["class_ms"], "fp64": prof["fp64"]["class_ms"]},
+                     "roofline": prof["fp64"]["roofline"], "per_iteration": piter["fp64"]},
+            "fp64_dw": {"value": res["fp64_dw"]["value"], "unit": "DOFs/s",
+                        "ms_per_step": res["fp64_dw"]["ms_per_step"], "iterations": res["fp64_dw"]["iters"],
+                        "true_rel_residual": res["fp64_dw"]["true_rel_residual"],
+                        "rel_diff_vs_fp64_solution": dw_vs_fp64, "roofline": prof["fp64_dw"]["roofline"],
+                        "per_iteration": piter["fp64_dw"],
+                        "arithmetic": "FP64 data; vectors and stencils as float pairs hi + lo (~48-bit "
+                                      "significand) on the FP32 pipe; FP64 reductions, pseudo-inverse, coarse solve"},
+            "kernel_ms_per_solve": {"mixed": prof["mixed"]["class_ms"], "fp64": prof["fp64"]["class_ms"],
+                                    "fp64_dw": prof["fp64_dw"]["class_ms"]},
             "e2e": {"value": world * n / e2e_s, "unit": "DOFs/s", "h2d_bytes_per_step": 2 * 8 * n,
                     "d2h_bytes_per_step": 8 * n},
             "gpu_launches": mx["launches_per_step"] * args.steps,
@@ -485,8 +592,6 @@ def bench_ours(args):
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
-    for h in H.values():
-        h.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -1112,9 +1217,16 @@ def main():
                     help="with --only mixed: the matrix-free fine operator in the timed solve")
     ap.add_argument("--direct", action="store_true",
                     help="launch kernels directly instead of one graph per solve (for ncu launch lists)")
-    ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
+    ap.add_argument("--only", choices=["mixed", "fp64", "fp64_dw"], default=None,
                     help="time one precision only and print its figures (profiling runs)")
+    ap.add_argument("--nodes", type=int, default=None,
+                    help="with --only: nodes per side of the 3D Poisson grid (smaller cases for profiling)")
     args = ap.parse_args()
+    if args.nodes is not None:
+        if args.only is None:
+            ap.error("--nodes goes with --only")
+        global NODES
+        NODES = args.nodes
     if args.warmup < 3 and args.impl == "ours":
         print("note: warmup raised to 3", file=sys.stderr)
         args.warmup = 3
