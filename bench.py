@@ -18,6 +18,7 @@ no collective on the data path); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import faulthandler
 import json
 import os
 import statistics
@@ -1152,6 +1153,7 @@ def bench_learned(args):
             owner.append(i)
         hs.append(H)
     gen_s = time.perf_counter() - t0
+    print(f"learned workload: {len(R)} training pairs in {gen_s:.1f} s", file=sys.stderr, flush=True)
     params = pb.net_init_params(7)
     t0 = time.perf_counter()
     loss = [float("nan")]
@@ -1159,13 +1161,18 @@ def bench_learned(args):
         loss = M.mg_learned_train([h.h for h in hs], owner, torch.stack(R).contiguous(),
                                   torch.stack(E).contiguous(), params, epochs=args.epochs, batch=8, lr=1e-3)
     train_s = time.perf_counter() - t0
+    print(f"learned workload: trained {args.epochs} epochs in {train_s:.1f} s", file=sys.stderr, flush=True)
     prob = pb.diffusion_macro(2, 1025, 3)
     st = torch.from_numpy(prob.stencil).cuda()
     b = torch.from_numpy(prob.b).cuda()
     out = {}
     kap = torch.from_numpy(np.ascontiguousarray(prob.kappa).reshape(-1)).cuda()
-    for key in ("plain", "learned", "plain_matrix_free", "learned_matrix_free"):
-        H = M.Hierarchy(st, 2, 1025, prob.levels, m=M_WINDOW, precision=M.MPCG_MIXED)
+    legs = {"plain": M.MPCG_MIXED, "learned": M.MPCG_MIXED, "plain_matrix_free": M.MPCG_MIXED,
+            "learned_matrix_free": M.MPCG_MIXED, "plain_fp64": M.MPCG_FP64, "plain_fp64_dw": M.MPCG_FP64_DW,
+            "learned_fp64_dw": M.MPCG_FP64_DW}
+    for key, prec in legs.items():
+        print(f"learned workload: leg {key}", file=sys.stderr, flush=True)
+        H = M.Hierarchy(st, 2, 1025, prob.levels, m=M_WINDOW, precision=prec)
         if key.startswith("learned"):
             M.mg_learned_attach(H.h, params)
         if key.endswith("matrix_free"):   # fine operator rebuilt from the element coefficients
@@ -1178,8 +1185,11 @@ def bench_learned(args):
             res["st"], res["k"], _, _ = H.solve(b, x, rtol=RTOL, maxit=50000, histories=False)
 
         ms = _timed(step, args.steps, 1, torch.cuda.current_stream())
+        Ax = torch.empty_like(b)
+        M.mg_apply_operator(H.h, prob.levels - 1, x, Ax, 1)
         out[key] = {"ms_per_solve": ms, "iterations": int(res["k"]), "status": int(res["st"]),
-                    "dofs_per_s": prob.n / (ms * 1e-3)}
+                    "dofs_per_s": prob.n / (ms * 1e-3),
+                    "true_rel_residual": float(torch.linalg.norm(b - Ax) / torch.linalg.norm(b))}
         if key == "learned":  # live CUDA-event time of the fused tensor-core network kernel
             x.zero_()
             _, _, _, trace = M.mpcg_solve_profiled(H.h, b, x, RTOL, 50000)
@@ -1195,12 +1205,18 @@ def bench_learned(args):
                                "pairs from 129^2 problems (kappa seeds 1000-1015)"},
         "plain": out["plain"], "learned": out["learned"],
         "plain_matrix_free": out["plain_matrix_free"], "learned_matrix_free": out["learned_matrix_free"],
+        "plain_fp64": out["plain_fp64"], "plain_fp64_dw": out["plain_fp64_dw"],
+        "learned_fp64_dw": out["learned_fp64_dw"],
+        # wall time of the plain FP64 solve over that of mixed precision + the learned column
+        "speedup_learned_mixed_vs_plain_fp64": out["plain_fp64"]["ms_per_solve"] / out["learned"]["ms_per_solve"],
+        "speedup_learned_mixed_vs_plain_mixed": out["plain"]["ms_per_solve"] / out["learned"]["ms_per_solve"],
         "training": {"pairs": len(R), "epochs": args.epochs, "loss_first": float(loss[0]),
                      "loss_last": float(loss[-1]), "pair_generation_s": gen_s, "train_s": train_s}}))
     return 0
 
 
 def main():
+    faulthandler.enable()   # a native crash prints the Python stack of the call that made it
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", choices=["poisson3d", "batched", "learned", "elasticity", "example1", "algebraic"],
                     default="poisson3d",

@@ -347,6 +347,7 @@ template void launch_net_infer<dw>(const GridDesc&, int, const dw*, long long, c
 void net_infer_prepare_attributes() {
   cudaFuncSetAttribute(k_net_infer_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   cudaFuncSetAttribute(k_net_infer_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  cudaFuncSetAttribute(k_net_infer_tc<dw>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
 }
 
 }  // namespace mpcg
