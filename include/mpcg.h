@@ -507,6 +507,50 @@ void mg_hierarchy_destroy(mg_hierarchy* h);
 mpcg_status mg_stencil_apply_noalloc(int dim, int nodes, const double* values_dev, const double* X_dev,
                                      double* Y_dev, int ncols, void* stream);
 
+/*
+ * Autotuner of the launch shapes (the paper has no counterpart; the
+ * kernels' grid shapes otherwise follow fixed rules measured on GB300).
+ * Tunables, each keyed by (tunable, arithmetic, grid points incl. padding,
+ * problems in the batch, columns):
+ *   MG_TUNE_STREAM_BLOCKS  blocks of the streaming block kernels (A-
+ *                          orthogonalisation, update, residual) on a grid;
+ *   MG_TUNE_SPMM_BLOCKS    blocks of the block SpMM;
+ *   MG_TUNE_GRAM_CHUNKS    point chunks per window block of the window Gram;
+ *   MG_TUNE_JACOBI_NARROW  1: one point per thread in the Jacobi sweep of a
+ *                          grid, 0: a 16-byte vector per thread.
+ * Every tuned value is clamped at launch to the range the solver's buffers
+ * reserve and to at most 64 FP32 points per thread per partial sum, so no
+ * table content can make a launch unsafe or change the accuracy bound.
+ *
+ * mg_autotune(h, cache_path, timed): for h's finest grid in h's arithmetic
+ * (and the Jacobi switch of every scalar grid), times each candidate shape
+ * on profiled solves of a fixed random right-hand side (CUDA events around
+ * every launch; the best of two solves after a warm-up) and keeps the shape
+ * whose kernel classes took least time.  With cache_path (may be NULL) a
+ * cache written on this device that holds every key is loaded instead of
+ * timing, and the table is written there afterwards.  Changes results only
+ * at rounding level (reduction partitions follow the shapes).  Shapes apply
+ * to every hierarchy of the process with the same keys; graphs captured
+ * before are rebuilt on their next solve.  *timed (may be NULL) gets the
+ * number of candidates timed (0 when the cache served).  Synchronises.
+ * Errors: MPCG_ERR_ARG (NULL h, unwritable cache), MPCG_ERR_CUDA, or a
+ * failed timed solve's status.
+ *
+ * mg_autotune_load / mg_autotune_save (host only): the JSON cache, tagged
+ * with a device name and SM count; a file for another device is refused and
+ * loads nothing.  mg_autotune_lookup returns a stored value or -1;
+ * mg_autotune_set stores one (clamped at launch like any other);
+ * mg_autotune_clear empties the table (the fixed rules apply again).
+ */
+enum { MG_TUNE_STREAM_BLOCKS = 0, MG_TUNE_SPMM_BLOCKS = 1, MG_TUNE_GRAM_CHUNKS = 2, MG_TUNE_JACOBI_NARROW = 3 };
+enum { MG_TUNE_ANY = -1, MG_TUNE_F32 = 0, MG_TUNE_F64 = 1, MG_TUNE_DW = 2 };
+mpcg_status mg_autotune(mg_hierarchy* h, const char* cache_path, int* timed);
+mpcg_status mg_autotune_load(const char* cache_path, const char* device_name, int sm_count, int* entries);
+mpcg_status mg_autotune_save(const char* cache_path, const char* device_name, int sm_count);
+int mg_autotune_lookup(int tunable, int kind, long long npts, int nb, int ncols);
+void mg_autotune_set(int tunable, int kind, long long npts, int nb, int ncols, int value);
+void mg_autotune_clear(void);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char* mpcg_last_error(void);
 

@@ -16,6 +16,7 @@
 
 #include "amg.h"
 #include "kernels.cuh"
+#include "tune.h"
 
 using namespace mpcg;
 
@@ -330,11 +331,14 @@ mpcg_status build_solver(mg_hierarchy* h, Solver<T>& S) {
     }
   }
   CKS(S.mem.get(&S.state, nb, s));
-  CKS(S.mem.get(&S.part_res, nb * 2 * stream_blocks(gf), s));
-  CKS(S.mem.get(&S.part_zaz, nb * C * stream_blocks(gf), s));
-  CKS(S.mem.get(&S.part_W, nb * S.m * C * C * gram_chunks(gf), s));
-  CKS(S.mem.get(&S.part_G, nb * (C * (C + 1) / 2 + C) * stream_blocks(gf), s));
-  CKS(S.mem.get(&S.part_r, nb * stream_blocks(gf), s));
+  // partial-sum slots for the most blocks a tuned launch shape may take
+  // (the autotuner can change the shapes after the buffers exist)
+  const size_t sbc = (size_t)stream_blocks_cap(gf), gcc = (size_t)gram_chunks_cap(gf);
+  CKS(S.mem.get(&S.part_res, nb * 2 * sbc, s));
+  CKS(S.mem.get(&S.part_zaz, nb * C * sbc, s));
+  CKS(S.mem.get(&S.part_W, nb * S.m * C * C * gcc, s));
+  CKS(S.mem.get(&S.part_G, nb * (C * (C + 1) / 2 + C) * sbc, s));
+  CKS(S.mem.get(&S.part_r, nb * sbc, s));
   CKS(S.mem.get(&S.small_scratch, nb * kSmallScratch, s));
   CKS(S.mem.get(&S.counters, 2 * nb, s));
   CKS(S.mem.get(&S.flag, 1, s));
@@ -883,7 +887,7 @@ mpcg_status build_f32(mg_hierarchy* h) {
   CKS(h->mem.get(&h->x64, gf.cp, s));
   CKS(h->mem.get(&h->r64, gf.cp, s));
   CKS(h->mem.get(&h->nrm, 2 * (size_t)h->nb + 2, s));
-  CKS(h->mem.get(&h->part_mix, 2 * (size_t)h->nb * stream_blocks(gf), s));
+  CKS(h->mem.get(&h->part_mix, 2 * (size_t)h->nb * stream_blocks_cap(gf), s));
   CKS(h->mem.get(&h->active, h->nb, s));
   CKS(h->mem.get(&h->mix, 3 * (size_t)h->nb, s));
   CKS(h->mem.get(&h->outer, 1, s));
@@ -1927,6 +1931,193 @@ mpcg_status mpcg_solve(mg_hierarchy* h, const double* b, double* x, double rtol,
   }
   return st;
 }
+
+// ---------------------------------------------------------------------------
+// Autotuner: launch shapes timed per kernel class on this hierarchy's grids
+// and arithmetic (see tune.h for the table and its JSON cache).
+
+static void drop_all_graphs(mg_hierarchy* h) {
+  cudaStreamSynchronize(h->stream);
+  h->s64.drop_graph();
+  h->s32.drop_graph();
+  h->sdw.drop_graph();
+  drop_mixed_graph(h);
+}
+
+mpcg_status mg_autotune(mg_hierarchy* h, const char* cache_path, int* timed_out) {
+  g_err.clear();
+  CKS(check_h(h));
+  if (timed_out) *timed_out = 0;
+  CK(cudaSetDevice(h->device));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, h->device));
+  const int sms = prop.multiProcessorCount;
+  const int J = h->levels - 1;
+  const GridDesc gf = h->lev[J].g;
+  const int nb = h->nb;
+  const int prec = h->opt.precision;
+  const int kind = prec == MPCG_MIXED ? tune::kF32 : (prec == MPCG_FP64_DW ? tune::kDW : tune::kF64);
+  const int C = prec == MPCG_MIXED ? h->s32.C : (prec == MPCG_FP64_DW ? h->sdw.C : h->s64.C);
+  struct Tunable {
+    int fn, kind;
+    long long npts;
+    int C, dflt, lo, hi;
+    std::vector<int> metric;   // kernel classes whose time decides
+  };
+  std::vector<Tunable> keys;
+  keys.push_back({tune::kStream, tune::kAny, gf.npts, 0, stream_blocks_default(gf), stream_blocks_min(gf),
+                  stream_blocks_cap(gf), {K_ORTH, K_UPDATE, K_RESIDUAL, K_INIT, K_CHECK}});
+  keys.push_back({tune::kGram, tune::kAny, gf.npts, 0, gram_chunks_default(gf), gram_chunks_min(gf),
+                  gram_chunks_cap(gf), {K_GRAM, K_BETA}});
+  {
+    int d = 0;
+    if (kind == tune::kF32) d = spmm_blocks<float>(gf, C);
+    else if (kind == tune::kDW) d = spmm_blocks<dw>(gf, C);
+    else d = spmm_blocks<double>(gf, C);
+    keys.push_back({tune::kSpmm, kind, gf.npts, C, d, stream_blocks_min(gf), stream_blocks_cap(gf), {K_SPMM, K_ALPHA}});
+  }
+  if (!h->algebraic && h->opt.smoother == MPCG_SMOOTHER_JACOBI)
+    for (int j = 1; j <= J; ++j) {
+      const GridDesc& g = h->lev[j].g;
+      if (g.ncomp != 1) continue;
+      const bool rule = g.npts / (kind == tune::kF32 ? 4 : 2) * g.nb < (long long)sms * 128;
+      keys.push_back({tune::kJacobi, kind, g.npts, 0, rule ? 1 : 0, 0, 1, {K_JACOBI}});
+    }
+  // a cache written on this device that holds every key: no timing
+  if (cache_path && tune::load(cache_path, prop.name, sms) >= 0) {
+    bool all = true;
+    for (const Tunable& k : keys) {
+      int v;
+      all = all && tune::find(k.fn, k.kind, k.npts, nb, k.C, &v);
+    }
+    if (all) {
+      drop_all_graphs(h);
+      return MPCG_OK;
+    }
+  }
+  // time the candidates on profiled solves of a fixed right-hand side
+  Alloc mem;
+  cudaStream_t s = h->stream;
+  double *b = nullptr, *x = nullptr;
+  const size_t n = (size_t)gf.n * nb;
+  mpcg_status st = mem.get(&b, n, s);
+  if (st == MPCG_OK) st = mem.get(&x, n, s);
+  if (st != MPCG_OK) {
+    mem.release();
+    return st;
+  }
+  {
+    std::vector<double> hb(n);
+    unsigned long long z = 0x2545F4914F6CDD1DULL;
+    for (size_t i = 0; i < n; ++i) {   // splitmix64 -> uniform in [-1, 1)
+      z += 0x9E3779B97F4A7C15ULL;
+      unsigned long long t = z;
+      t = (t ^ (t >> 30)) * 0xBF58476D1CE4E5B9ULL;
+      t = (t ^ (t >> 27)) * 0x94D049BB133111EBULL;
+      t ^= t >> 31;
+      hb[i] = (double)(t >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    }
+    if (cudaMemcpyAsync(b, hb.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      mem.release();
+      set_err("mg_autotune: upload of the right-hand side failed");
+      return MPCG_ERR_CUDA;
+    }
+  }
+  int timed = 0;
+  auto measure = [&](const Tunable& k, double* out) -> mpcg_status {
+    drop_all_graphs(h);
+    double best = 1e300;
+    for (int rep = 0; rep < 3; ++rep) {
+      double ms[K_COUNT] = {};
+      int it = 0;
+      if (cudaMemsetAsync(x, 0, sizeof(double) * n, s) != cudaSuccess) return MPCG_ERR_CUDA;
+      const mpcg_status r = mpcg_solve_profiled(h, b, x, 1e-8, 500, &it, ms, nullptr, nullptr, nullptr, 0, nullptr);
+      if (r != MPCG_OK && r != MPCG_NOT_CONVERGED) return r;
+      double t = 0.0;
+      for (int c : k.metric) t += ms[c];
+      if (rep > 0 && t < best) best = t;   // the first solve is a warm-up
+    }
+    ++timed;
+    *out = best;
+    return MPCG_OK;
+  };
+  for (const Tunable& k : keys) {
+    std::vector<int> cand = {k.dflt};
+    if (k.fn == tune::kJacobi) {
+      cand = {0, 1};
+    } else if (k.fn == tune::kGram) {
+      for (int f : {k.dflt / 2, 2 * k.dflt, 4 * k.dflt}) cand.push_back(f);
+    } else {
+      for (int f : {1, 2, 3, 4, 6, 8}) cand.push_back(f * sms);
+    }
+    int best_v = k.dflt;
+    double best_t = 1e300;
+    std::vector<int> seen;
+    for (int v : cand) {
+      if (v < k.lo || v > k.hi || std::find(seen.begin(), seen.end(), v) != seen.end()) continue;
+      seen.push_back(v);
+      tune::set(k.fn, k.kind, k.npts, nb, k.C, v);
+      double t = 0.0;
+      st = measure(k, &t);
+      if (st != MPCG_OK) break;
+      if (t < best_t) {
+        best_t = t;
+        best_v = v;
+      }
+    }
+    tune::set(k.fn, k.kind, k.npts, nb, k.C, best_v);
+    if (st != MPCG_OK) break;
+  }
+  drop_all_graphs(h);
+  mem.release();
+  if (timed_out) *timed_out = timed;
+  if (st != MPCG_OK) {
+    set_err("mg_autotune: a timed solve failed: %s", g_err.c_str());
+    return st;
+  }
+  if (cache_path && !tune::save(cache_path, prop.name, sms)) {
+    set_err("mg_autotune: cannot write the cache file %s", cache_path);
+    return MPCG_ERR_ARG;
+  }
+  return MPCG_OK;
+}
+
+mpcg_status mg_autotune_load(const char* cache_path, const char* device_name, int sm_count, int* entries) {
+  g_err.clear();
+  if (!cache_path || !device_name) {
+    set_err("mg_autotune_load: NULL path or device name");
+    return MPCG_ERR_ARG;
+  }
+  const int r = tune::load(cache_path, device_name, sm_count);
+  if (r < 0) {
+    set_err(r == -1 ? "mg_autotune_load: no such file" : r == -2 ? "mg_autotune_load: malformed cache file"
+                                                               : "mg_autotune_load: cache written for another device");
+    return MPCG_ERR_ARG;
+  }
+  if (entries) *entries = r;
+  return MPCG_OK;
+}
+
+mpcg_status mg_autotune_save(const char* cache_path, const char* device_name, int sm_count) {
+  g_err.clear();
+  if (!cache_path || !device_name || !tune::save(cache_path, device_name, sm_count)) {
+    set_err("mg_autotune_save: cannot write the cache file");
+    return MPCG_ERR_ARG;
+  }
+  return MPCG_OK;
+}
+
+int mg_autotune_lookup(int tunable, int kind, long long npts, int nb, int ncols) {
+  int v = -1;
+  return tune::find(tunable, kind, npts, nb, ncols, &v) ? v : -1;
+}
+
+void mg_autotune_set(int tunable, int kind, long long npts, int nb, int ncols, int value) {
+  if (tunable >= 0 && tunable < tune::kNumTunables) tune::set(tunable, kind, npts, nb, ncols, value);
+}
+
+void mg_autotune_clear(void) { tune::clear(); }
 
 const char* mpcg_kernel_class_name(int cls) {
   return cls >= 0 && cls < K_COUNT ? kClassNames[cls] : "";

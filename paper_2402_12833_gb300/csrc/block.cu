@@ -13,6 +13,7 @@
 // order.  In the FP32 path each thread sums at most 64 points in FP32 and the
 // warp adds its 32 lanes in FP32; everything above the warp is FP64.
 #include "kernels.cuh"
+#include "tune.h"
 #include "vec.cuh"
 
 namespace mpcg {
@@ -352,22 +353,55 @@ __global__ void __launch_bounds__(kBlock) k_axpy_mixed(GridDesc g, double* __res
     default: break;                                                                              \
   }
 
-int gram_chunks(const GridDesc& g) {
+int gram_chunks_default(const GridDesc& g) {
   // 8 vector groups (32 points in FP32, 16 in FP64) per thread and chunk
   const long long groups = g.npts / 4;
   long long c = (groups + kBlock * 8 - 1) / (kBlock * 8);
   if (c < 1) c = 1;
   return (int)(c < kGramChunksMax ? c : kGramChunksMax);
 }
+// at most 16 vector groups (64 FP32 points) per thread and chunk
+int gram_chunks_min(const GridDesc& g) { return (gram_chunks_default(g) + 1) / 2; }
+int gram_chunks_cap(const GridDesc& g) {
+  const long long c = 4LL * gram_chunks_default(g);
+  return (int)(c < kGramChunksMax ? c : kGramChunksMax);
+}
+int gram_chunks(const GridDesc& g) {
+  const int v = tune::lookup(tune::kGram, tune::kAny, g.npts, g.nb, 0, gram_chunks_default(g));
+  const int lo = gram_chunks_min(g), hi = gram_chunks_cap(g);
+  return v < lo ? lo : (v > hi ? hi : v);
+}
 
-int stream_blocks(const GridDesc& g) {
+int stream_blocks_min(const GridDesc& g) {
   const long long groups = g.npts / 2;
   long long need = (groups + kBlock * 16 - 1) / (kBlock * 16);   // <= 64 points per thread
+  if (need < 1) need = 1;
+  return (int)(need < kStreamBlocksMax ? need : kStreamBlocksMax);
+}
+int stream_blocks_default(const GridDesc& g) {
+  const long long groups = g.npts / 2;
+  long long need = stream_blocks_min(g);
   long long fill = (groups + kBlock - 1) / kBlock;                // no idle threads
   long long nb = kStreamBlocks < fill ? kStreamBlocks : fill;
   if (need > nb) nb = need;
   if (nb < 1) nb = 1;
   return (int)(nb < kStreamBlocksMax ? nb : kStreamBlocksMax);
+}
+// the most blocks the tuner may choose (and the reduction buffers reserve):
+// eight per SM, without idle threads
+int stream_blocks_cap(const GridDesc& g) {
+  const long long groups = g.npts / 2;
+  const long long fill = (groups + kBlock - 1) / kBlock;
+  long long c = 8LL * (sm_count() > 0 ? sm_count() : 152);
+  if (c > fill) c = fill;
+  const long long d = stream_blocks_default(g);
+  if (c < d) c = d;
+  return (int)(c < kStreamBlocksMax ? c : kStreamBlocksMax);
+}
+int stream_blocks(const GridDesc& g) {
+  const int v = tune::lookup(tune::kStream, tune::kAny, g.npts, g.nb, 0, stream_blocks_default(g));
+  const int lo = stream_blocks_min(g), hi = stream_blocks_cap(g);
+  return v < lo ? lo : (v > hi ? hi : v);
 }
 
 template <typename T>

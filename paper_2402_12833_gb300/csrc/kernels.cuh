@@ -17,8 +17,28 @@ constexpr int kGramChunksMax = 4096;
 
 // Grid sizes of the streaming block kernels and of the window Gram kernel;
 // both keep every thread at <= 64 points per FP32 partial sum.
+// Launch shapes: the fixed rules, unless the autotuner's table (tune.h) holds
+// a value for the grid, clamped to the range the reduction buffers reserve
+// (stream_blocks_cap / gram_chunks_cap) and to the accuracy limit of at most
+// 64 FP32 points per thread before the partial sums leave the thread.
 int stream_blocks(const GridDesc& g);
 int gram_chunks(const GridDesc& g);
+int stream_blocks_default(const GridDesc& g);
+int gram_chunks_default(const GridDesc& g);
+int stream_blocks_min(const GridDesc& g);
+int stream_blocks_cap(const GridDesc& g);
+int gram_chunks_min(const GridDesc& g);
+int gram_chunks_cap(const GridDesc& g);
+// number of SMs (set at hierarchy setup; 0 before)
+int sm_count();
+template <typename T>
+constexpr int kind_of();
+template <>
+constexpr int kind_of<float>() { return 0; }
+template <>
+constexpr int kind_of<double>() { return 1; }
+template <>
+constexpr int kind_of<dw>() { return 2; }
 
 // Sets the calling thread's message returned by mpcg_last_error().
 void set_error_message(const char* msg);

@@ -11,6 +11,7 @@
 // test.  blockIdx.y selects the problem of a batch (offset b * len; columns
 // and stencil planes are cp = nb * len apart).
 #include "kernels.cuh"
+#include "tune.h"
 #include "vec.cuh"
 
 namespace mpcg {
@@ -873,6 +874,7 @@ void launch_pack_flag(const GridDesc& g, const double* src, TO* dst, int* nz, cu
 #ifndef MPCG_STENCIL_DW
 int g_sm_count = 0;
 void set_sm_count(int n) { g_sm_count = n; }
+int sm_count() { return g_sm_count; }
 #else
 extern int g_sm_count;
 #endif
@@ -880,12 +882,19 @@ extern int g_sm_count;
 template <typename T>
 int spmm_blocks(const GridDesc& g, int C) {
   const int nb = stream_blocks(g);
-  if (sizeof(T) != 4 || g.dim != 3 || g.ncomp != 1 || C > 6 || g_sm_count <= 0) return nb;
-  const long long groups = g.npts / 2;
-  const long long need = (groups + kBlock * 16 - 1) / (kBlock * 16);
-  long long w = 3LL * g_sm_count;   // one wave at three blocks per SM
-  if (w < need) w = need;
-  return (int)(w < nb ? w : nb);
+  int dflt = nb;
+  if (sizeof(T) == 4 && g.dim == 3 && g.ncomp == 1 && C <= 6 && g_sm_count > 0) {
+    const long long groups = g.npts / 2;
+    const long long need = (groups + kBlock * 16 - 1) / (kBlock * 16);
+    long long w = 3LL * g_sm_count;   // one wave at three blocks per SM
+    if (w < need) w = need;
+    dflt = (int)(w < nb ? w : nb);
+  }
+  // tuned: between the 64-points-per-thread minimum and the partial-sum
+  // slots the solver reserves (stream_blocks_cap)
+  const int v = tune::lookup(tune::kSpmm, kind_of<T>(), g.npts, g.nb, C, dflt);
+  const int lo = stream_blocks_min(g), hi = stream_blocks_cap(g);
+  return v < lo ? lo : (v > hi ? hi : v);
 }
 #ifndef MPCG_STENCIL_DW
 template int spmm_blocks<double>(const GridDesc&, int);
@@ -993,7 +1002,8 @@ void launch_jacobi(const GridDesc& g, const T* st, const T* dinv, const T* r, co
   // the 129^3 solve 4.575 -> 4.557 ms).  Larger grids keep the vector width:
   // their smoothing runs beside the fine grid's, and four times the blocks
   // there slowed the solve.
-  const bool narrow = mode != 2 && g_sm_count > 0 && g.npts / vw<T>() * g.nb < (long long)g_sm_count * 128;
+  const bool narrow_rule = g_sm_count > 0 && g.npts / vw<T>() * g.nb < (long long)g_sm_count * 128;
+  const bool narrow = mode != 2 && tune::lookup(tune::kJacobi, kind_of<T>(), g.npts, g.nb, 0, narrow_rule ? 1 : 0) != 0;
   if (narrow) {
     const dim3 grid(blocks_for(g.npts), g.nb);
     if (g.dim == 3) k_jacobi<T, 3, 1><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);

@@ -122,6 +122,12 @@ _SIGS = {
     "mg_attach_q1_kappa": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mg_detach_q1_kappa": (C.c_int, [C.c_void_p]),
     "mg_learned_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "mg_autotune": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_int)]),
+    "mg_autotune_load": (C.c_int, [C.c_char_p, C.c_char_p, C.c_int, C.POINTER(C.c_int)]),
+    "mg_autotune_save": (C.c_int, [C.c_char_p, C.c_char_p, C.c_int]),
+    "mg_autotune_lookup": (C.c_int, [C.c_int, C.c_int, C.c_longlong, C.c_int, C.c_int]),
+    "mg_autotune_set": (None, [C.c_int, C.c_int, C.c_longlong, C.c_int, C.c_int, C.c_int]),
+    "mg_autotune_clear": (None, []),
     "mg_learned_forward_acts": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mg_learned_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
@@ -297,6 +303,40 @@ def mg_detach_q1_kappa(h: int) -> None:
 
 def mg_learned_forward(h: int, rhat_dev, y_dev, nimg: int = 1) -> None:
     _check(load().mg_learned_forward(h, _ptr(rhat_dev), _ptr(y_dev), nimg))
+
+
+MG_TUNE_STREAM_BLOCKS, MG_TUNE_SPMM_BLOCKS, MG_TUNE_GRAM_CHUNKS, MG_TUNE_JACOBI_NARROW = 0, 1, 2, 3
+MG_TUNE_ANY, MG_TUNE_F32, MG_TUNE_F64, MG_TUNE_DW = -1, 0, 1, 2
+
+
+def mg_autotune(h: int, cache_path: str | None = None) -> int:
+    """Tune the launch shapes for h (see mpcg.h); returns the number of
+    candidates timed (0 when the cache served)."""
+    timed = C.c_int(0)
+    _check(load().mg_autotune(h, cache_path.encode() if cache_path else None, C.byref(timed)))
+    return timed.value
+
+
+def mg_autotune_load(path: str, device: str, sm_count: int) -> int:
+    n = C.c_int(0)
+    _check(load().mg_autotune_load(path.encode(), device.encode(), sm_count, C.byref(n)))
+    return n.value
+
+
+def mg_autotune_save(path: str, device: str, sm_count: int) -> None:
+    _check(load().mg_autotune_save(path.encode(), device.encode(), sm_count))
+
+
+def mg_autotune_lookup(tunable: int, kind: int, npts: int, nb: int, ncols: int) -> int:
+    return load().mg_autotune_lookup(tunable, kind, npts, nb, ncols)
+
+
+def mg_autotune_set(tunable: int, kind: int, npts: int, nb: int, ncols: int, value: int) -> None:
+    load().mg_autotune_set(tunable, kind, npts, nb, ncols, value)
+
+
+def mg_autotune_clear() -> None:
+    load().mg_autotune_clear()
 
 
 def mg_learned_forward_acts(h: int, rhat_dev, y_dev, acts_dev, nimg: int = 1) -> None:
