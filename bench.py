@@ -427,6 +427,18 @@ def bench_ours(args):
         from paper_2402_12833_gb300.multi import max_over_ranks as mor
         return mor(v, device="cuda")
 
+    # launch shapes: the fixed rules first (timed below for comparison), then
+    # the autotuner's choice for every leg, which the timed region uses
+    fixed_ms = {}
+    if not args.no_autotune:
+        for key in legs:
+            hk = H[key]
+            for _ in range(args.warmup):
+                x.zero_()
+                hk.solve(b, x, rtol=RTOL, maxit=MAXIT, histories=False)
+            fixed_ms[key] = _timed(lambda: (x.zero_(), hk.solve(b, x, rtol=RTOL, maxit=MAXIT, histories=False)),
+                                   args.steps, 0, stream)
+        tuned = {key: M.mg_autotune(H[key].h) for key in legs}
     res = {}
     clocks = None
     for key in legs:
@@ -573,6 +585,9 @@ def bench_ours(args):
                                         "SpMM and Jacobi kernels; stored stencils elsewhere"},
             "roofline": prof["mixed"]["roofline"],
             "per_iteration": piter["mixed"],
+            "autotune": None if args.no_autotune else {
+                "candidates_timed": tuned, "fixed_rules_ms_per_step": fixed_ms,
+                "note": "every leg timed with the autotuner's launch shapes; the fixed rules' times beside"},
             "fp64": {"value": res["fp64"]["value"], "unit": "DOFs/s", "ms_per_step": res["fp64"]["ms_per_step"],
                      "iterations": res["fp64"]["iters"], "true_rel_residual": res["fp64"]["true_rel_residual"],
                      "roofline": prof["fp64"]["roofline"], "per_iteration": piter["fp64"]},
@@ -1235,6 +1250,8 @@ def main():
                     help="launch kernels directly instead of one graph per solve (for ncu launch lists)")
     ap.add_argument("--only", choices=["mixed", "fp64", "fp64_dw"], default=None,
                     help="time one precision only and print its figures (profiling runs)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the fixed launch-shape rules only (no autotuning)")
     ap.add_argument("--nodes", type=int, default=None,
                     help="with --only: nodes per side of the 3D Poisson grid (smaller cases for profiling)")
     args = ap.parse_args()

@@ -524,9 +524,10 @@ mpcg_status mg_stencil_apply_noalloc(int dim, int nodes, const double* values_de
  *
  * mg_autotune(h, cache_path, timed): for h's finest grid in h's arithmetic
  * (and the Jacobi switch of every scalar grid), times each candidate shape
- * on profiled solves of a fixed random right-hand side (CUDA events around
- * every launch; the best of two solves after a warm-up) and keeps the shape
- * whose kernel classes took least time.  With cache_path (may be NULL) a
+ * on whole solves of a fixed random right-hand side as they run (graph
+ * launch, concurrent multigrid branches; CUDA events around batches of five
+ * solves, the best of three batches after a warm-up batch), one shape at a
+ * time against the best found so far, and keeps the fastest.  With cache_path (may be NULL) a
  * cache written on this device that holds every key is loaded instead of
  * timing, and the table is written there afterwards.  Changes results only
  * at rounding level (reduction partitions follow the shapes).  Shapes apply
