@@ -2485,7 +2485,7 @@ mpcg_status mg_learned_grad(mg_hierarchy* h, const float* params, const float* r
   }
   CKS(build_f32(h));
   CKS(net_prepare(h));
-  net_prepare_attributes(g);
+  net_train_tc_prepare_attributes();
   Alloc mem;
   mpcg_status st = MPCG_OK;
   auto get = [&](auto** p, size_t n) {
@@ -2493,7 +2493,7 @@ mpcg_status mg_learned_grad(mg_hierarchy* h, const float* params, const float* r
   };
   const int B = nimg;
   const size_t L = g.len;
-  const int nw = net_wgrad_blocks(g, B);
+  const int nw = net_wgrad_tc_blocks(g, B);
   float *rb, *eb, *aeb, *y, *ay, *dy, *master, *wq;
   double *dots, *coef, *lsum, *gd;
   NetActs a;
@@ -2521,17 +2521,17 @@ mpcg_status mg_learned_grad(mg_hierarchy* h, const float* params, const float* r
   get(&coef, 2 * B);
   get(&lsum, 1);
   get(&gd, kNetParams);
+  unsigned char* wtc = nullptr;
+  int* terr = nullptr;
+  get(&wtc, (size_t)net_tc_weight_bytes());
+  get(&terr, 1);
   double** parts_dev = nullptr;
-  int* nblk_dev = nullptr;
   get(&parts_dev, 4);
-  get(&nblk_dev, 4);
   if (st != MPCG_OK) {
     mem.release();
     return st;
   }
-  const int nblk_h[4] = {nw, nw, nw, nw};
   cudaMemcpyAsync(parts_dev, gr.part, sizeof(gr.part), cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(nblk_dev, nblk_h, sizeof(nblk_h), cudaMemcpyHostToDevice, s);
   copy_floats(master, params, kNetParams, s);
   launch_round_bf16(master, wq, kNetParams, s);
   launch_pack<float, float>(g, rhat_dev, g.n, rb, B, s);
@@ -2539,20 +2539,26 @@ mpcg_status mg_learned_grad(mg_hierarchy* h, const float* params, const float* r
   const float* st32 = h->lev[h->levels - 1].st32;
   launch_spmm<float>(g, st32, eb, aeb, B, nullptr, nullptr, s);
   cudaMemsetAsync(lsum, 0, sizeof(double), s);
-  launch_net_forward<float>(g, B, rb, L, h->net_c, wq, nullptr, a, y, (float*)nullptr, s);
+  launch_net_pack_tc(wq, wtc, s);
+  launch_net_infer<float>(g, B, rb, L, h->net_c, wtc, nullptr, y, (float*)nullptr, terr, s, nullptr, a);
   launch_spmm<float>(g, st32, y, ay, B, nullptr, nullptr, s);
   launch_net_loss_grad(g, B, y, ay, eb, aeb, dots, coef, lsum, dy, s);
-  launch_net_backward(g, B, wq, a, dy, gr, s);
-  launch_net_grad_sum(parts_dev, nblk_dev, gd, s);
+  launch_net_backward(g, B, wq, a, dy, gr, terr, s);
+  launch_net_grad_sum(parts_dev, nw, gd, s);
   if (acts_dev) launch_net_acts_export(g, B, a, acts_dev, s);
   if (y_dev) launch_unpack<float, float>(g, y, y_dev, g.n, B, s);
   double lh = 0.0;
+  int terr_h = 0;
   if (cudaMemcpyAsync(grad, gd, sizeof(double) * kNetParams,
                       is_device_pointer(grad) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(&lh, lsum, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&terr_h, terr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
     set_err("mg_learned_grad: %s", cudaGetErrorString(cudaGetLastError()));
     st = MPCG_ERR_CUDA;
+  } else if (terr_h) {
+    set_err("mg_learned_grad: a tensor-core wait timed out");
+    st = MPCG_ERR_TIMEOUT;
   }
   if (loss) *loss = lh;
   mem.release();
@@ -2597,7 +2603,7 @@ mpcg_status mg_learned_train(mg_hierarchy* const* hs, int nprob, const int* pair
     CKS(build_f32(hs[i]));
     CKS(net_prepare(hs[i]));
   }
-  net_prepare_attributes(g);
+  net_train_tc_prepare_attributes();
   Alloc mem;
   mpcg_status st = MPCG_OK;
   auto get = [&](auto** p, size_t n) {
@@ -2608,7 +2614,7 @@ mpcg_status mg_learned_train(mg_hierarchy* const* hs, int nprob, const int* pair
   NetActs a;
   NetGrads gr;
   const size_t L = g.len;
-  const int nw = net_wgrad_blocks(g, B);
+  const int nw = net_wgrad_tc_blocks(g, B);
   get(&R, (size_t)npairs * L);
   get(&E, (size_t)npairs * L);
   get(&AE, (size_t)npairs * L);
@@ -2636,17 +2642,17 @@ mpcg_status mg_learned_train(mg_hierarchy* const* hs, int nprob, const int* pair
   get(&dots, 3 * 64 * B);
   get(&coef, 2 * B);
   get(&loss, 1);
+  unsigned char* wtc = nullptr;
+  int* terr = nullptr;
+  get(&wtc, (size_t)net_tc_weight_bytes());
+  get(&terr, 1);
   double** parts_dev = nullptr;
-  int* nblk_dev = nullptr;
   get(&parts_dev, 4);
-  get(&nblk_dev, 4);
   if (st != MPCG_OK) {
     mem.release();
     return st;
   }
-  int nblk_h[4] = {nw, nw, nw, nw};
   cudaMemcpyAsync(parts_dev, gr.part, sizeof(gr.part), cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(nblk_dev, nblk_h, sizeof(nblk_h), cudaMemcpyHostToDevice, s);
   copy_floats(master, params, kNetParams, s);
   launch_round_bf16(master, wq, kNetParams, s);
   // training set in the padded layout, and A e per pair (FP32 operators)
@@ -2684,19 +2690,28 @@ mpcg_status mg_learned_train(mg_hierarchy* const* hs, int nprob, const int* pair
       }
       mg_hierarchy* hp = hs[pair_prob[bt[0]]];
       const float* c = hp->net_c;
-      launch_net_forward<float>(g, nb, rb, L, c, wq, nullptr, a, y, (float*)nullptr, s);
+      launch_net_pack_tc(wq, wtc, s);
+      launch_net_infer<float>(g, nb, rb, L, c, wtc, nullptr, y, (float*)nullptr, terr, s, nullptr, a);
       launch_spmm<float>(g, hp->lev[hp->levels - 1].st32, y, ay, nb, nullptr, nullptr, s);
       launch_net_loss_grad(g, nb, y, ay, eb, aeb, dots, coef, loss, dy, s);
-      launch_net_backward(g, nb, wq, a, dy, gr, s);
+      launch_net_backward(g, nb, wq, a, dy, gr, terr, s);
       ++step;
-      launch_net_adam(parts_dev, nblk_dev, master, m, v, wq, step, (float)opts->lr, (float)opts->beta1,
+      // a short last batch of a problem launches fewer blocks than nw
+      launch_net_adam(parts_dev, net_wgrad_tc_blocks(g, nb), master, m, v, wq, step, (float)opts->lr, (float)opts->beta1,
                       (float)opts->beta2, (float)opts->eps, s);
     }
     double lh = 0.0;
+    int terr_h = 0;
     if (cudaMemcpyAsync(&lh, loss, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&terr_h, terr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
       set_err("training step failed: %s", cudaGetErrorString(cudaGetLastError()));
       st = MPCG_ERR_CUDA;
+      break;
+    }
+    if (terr_h) {
+      set_err("training: a tensor-core wait timed out");
+      st = MPCG_ERR_TIMEOUT;
       break;
     }
     if (loss_hist) loss_hist[ep] = lh / (double)batches.size();

@@ -251,37 +251,43 @@ struct NetGrads {  // data gradients [B][len][16] float; weight-gradient partial
   double* part[4];
 };
 
-int net_blocks(const GridDesc& g, int B);
-int net_wgrad_blocks(const GridDesc& g, int B);
-size_t net_wgrad_smem(const GridDesc& g);
-// y = N(r s, c) with s = 1/||r|| from state (or 1 without state); writes y
-// (float, may be null) and/or z = ||r|| y (T, may be null); 2D grids.
-template <typename T>
-void launch_net_forward(const GridDesc& g, int B, const T* r, long long r_ld, const float* c, const float* wq,
-                        const DevState* state, NetActs acts, float* y, T* z, cudaStream_t s);
 // Fused tensor-core inference (all four layers per output tile); wtc holds
 // the weights packed by launch_net_pack_tc (net_tc_weight_bytes() bytes);
 // err is set to 1 if a bounded wait on the MMA completion runs out; acts
-// (may be null) receives the activations [4][B][n1*n1][16] as floats.
+// (may be null) receives the activations [4][B][n1*n1][16] as floats; keep
+// (pointers may be null) receives them in the padded bfloat16 layout of
+// NetActs (the training forward pass).
 template <typename T>
 void launch_net_infer(const GridDesc& g, int B, const T* r, long long r_ld, const float* c, const void* wtc,
-                      const DevState* state, float* y, T* z, int* err, cudaStream_t s, float* acts = nullptr);
+                      const DevState* state, float* y, T* z, int* err, cudaStream_t s, float* acts = nullptr,
+                      NetActs keep = NetActs{nullptr, nullptr, nullptr, nullptr});
+// Tensor-core training kernels (learned_train_tc.cu): the weight gradient of
+// layer `layer` (0..3) into part (value-major, stride net_wgrad_tc_blocks)
+// and the masked data gradient through a layer with cout outputs (1 or 16).
+void launch_net_wgrad_tc(const GridDesc& g, int B, int layer, const float* dOut, const __nv_bfloat16* act,
+                         double* part, int* err, cudaStream_t s);
+void launch_net_dgrad_tc(const GridDesc& g, int B, int cout, const float* dOut, const float* W,
+                         const __nv_bfloat16* act_in, float* dIn, int* err, cudaStream_t s);
+int net_wgrad_tc_blocks(const GridDesc& g, int B);
+void net_train_tc_prepare_attributes();
+
 void launch_net_pack_tc(const float* wq, void* wtc, cudaStream_t s);
 int net_tc_weight_bytes();
 void net_infer_prepare_attributes();
 void launch_net_backward(const GridDesc& g, int B, const float* wq, NetActs acts, const float* dy, NetGrads gr,
-                         cudaStream_t s);
+                         int* err, cudaStream_t s);
 void launch_net_loss_grad(const GridDesc& g, int B, const float* y, const float* Ay, const float* e,
                           const float* Ae, double* part, double* coef, double* loss_sum, float* dy, cudaStream_t s);
-void launch_net_adam(const double* const* parts_dev, const int* nblk_dev, float* master, float* m, float* v, float* wq,
+// the weight-gradient partials of every layer are nblk per parameter (the
+// block count of the last backward pass: net_wgrad_tc_blocks of its batch)
+void launch_net_adam(const double* const* parts_dev, int nblk, float* master, float* m, float* v, float* wq,
                      int step, float lr, float b1, float b2, float eps, cudaStream_t s);
 void launch_round_bf16(const float* src, float* dst, int n, cudaStream_t s);
 // grad[i] = sum of the weight-gradient partials of parameter i (all layers)
-void launch_net_grad_sum(const double* const* parts_dev, const int* nblk_dev, double* grad, cudaStream_t s);
+void launch_net_grad_sum(const double* const* parts_dev, int nblk, double* grad, cudaStream_t s);
 // activations a0..a3 of the training forward ([B][len][C] bfloat16, padded)
 // to the compact float layout [4][B][n1*n1][16] (a0 zero-padded to 16)
 void launch_net_acts_export(const GridDesc& g, int B, NetActs acts, float* out, cudaStream_t s);
 void launch_net_coef(const GridDesc& g, const double* dinv, double omega, float* c, double* part, cudaStream_t s);
-void net_prepare_attributes(const GridDesc& g);
 
 }  // namespace mpcg

@@ -164,12 +164,15 @@ __device__ __forceinline__ void issue_row(uint32_t tmem, int col0, uint32_t act_
 // y: optional float output, z: optional output ||r|| y (type T), acts:
 // optional copy of the bfloat16 activations as floats for inspection,
 // [4][B][n1 * n1][16] compact (layer 0 = the two input channels, zero-padded
-// to 16; layers 1-3 = the outputs of the first three convolutions).
+// to 16; layers 1-3 = the outputs of the first three convolutions); keep:
+// optional bfloat16 activations in the padded training layout ([B][len][C],
+// interior points only; the pads stay as the caller zeroed them), the forward
+// pass of training.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 2)
     k_net_infer_tc(GridDesc g, const T* __restrict__ r, long long r_ld, const float* __restrict__ c,
                    const uint4* __restrict__ wtc, const DevState* state, float* __restrict__ y, T* __restrict__ z,
-                   int* err, float* __restrict__ acts) {
+                   int* err, float* __restrict__ acts, NetActs keep) {
   if (state && state->done) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
@@ -217,6 +220,15 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int off = (yy * kXS + tid + 1) * 16;
       *reinterpret_cast<uint4*>(smem + kOffAct0 + off) = make_uint4(pack_bf16x2(v0[yy], v1[yy]), 0, 0, 0);
       *reinterpret_cast<uint4*>(smem + kOffAct0 + kPlane + off) = make_uint4(0, 0, 0, 0);
+    }
+    if (keep.a0 && tid >= kHalo && tid < kHalo + kTW && gxx < n1) {
+      for (int yy = kHalo; yy < kHalo + kTH; ++yy) {
+        const int gy = gy0 + yy;
+        if (gy >= n1) break;
+        const long long o = (long long)b * g.len + g.G + gxx + p * gy;
+        keep.a0[o * 2 + 0] = __float2bfloat16_rn(v0[yy]);
+        keep.a0[o * 2 + 1] = __float2bfloat16_rn(v1[yy]);
+      }
     }
     if (acts && tid >= kHalo && tid < kHalo + kTW && gxx < n1) {
       const long long nn = (long long)n1 * n1;
@@ -277,6 +289,12 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int off = ((row - L - 1) * kXS + x + 1) * 16;   // in place: slot of input row row - 1
         *reinterpret_cast<uint4*>(act + off) = make_uint4(q[0], q[1], q[2], q[3]);
         *reinterpret_cast<uint4*>(act + kPlane + off) = make_uint4(q[4], q[5], q[6], q[7]);
+        __nv_bfloat16* kept = L == 0 ? keep.a1 : (L == 1 ? keep.a2 : keep.a3);
+        if (kept && inside && x >= kHalo && x < kHalo + kTW && row >= kHalo && row < kHalo + kTH) {
+          uint4* o = reinterpret_cast<uint4*>(kept + ((long long)b * g.len + g.G + gx + p * gy) * 16);
+          o[0] = make_uint4(q[0], q[1], q[2], q[3]);
+          o[1] = make_uint4(q[4], q[5], q[6], q[7]);
+        }
         if (acts && inside && x >= kHalo && x < kHalo + kTW && row >= kHalo && row < kHalo + kTH) {
           const long long nn = (long long)n1 * n1;
           float* o = acts + ((((long long)(L + 1) * gridDim.z + b) * nn) + (long long)gy * n1 + gx) * 16;
@@ -332,17 +350,17 @@ void launch_net_pack_tc(const float* wq, void* wtc, cudaStream_t s) {
 
 template <typename T>
 void launch_net_infer(const GridDesc& g, int B, const T* r, long long r_ld, const float* c, const void* wtc,
-                      const DevState* state, float* y, T* z, int* err, cudaStream_t s, float* acts) {
+                      const DevState* state, float* y, T* z, int* err, cudaStream_t s, float* acts, NetActs keep) {
   const dim3 grid((unsigned)((g.n1 + kTW - 1) / kTW), (unsigned)((g.n1 + kTH - 1) / kTH), (unsigned)B);
   k_net_infer_tc<T><<<grid, kThreads, kSmemBytes, s>>>(g, r, r_ld, c, reinterpret_cast<const uint4*>(wtc), state, y,
-                                                        z, err, acts);
+                                                        z, err, acts, keep);
 }
 template void launch_net_infer<double>(const GridDesc&, int, const double*, long long, const float*, const void*,
-                                       const DevState*, float*, double*, int*, cudaStream_t, float*);
+                                       const DevState*, float*, double*, int*, cudaStream_t, float*, NetActs);
 template void launch_net_infer<float>(const GridDesc&, int, const float*, long long, const float*, const void*,
-                                      const DevState*, float*, float*, int*, cudaStream_t, float*);
+                                      const DevState*, float*, float*, int*, cudaStream_t, float*, NetActs);
 template void launch_net_infer<dw>(const GridDesc&, int, const dw*, long long, const float*, const void*,
-                                   const DevState*, float*, dw*, int*, cudaStream_t, float*);
+                                   const DevState*, float*, dw*, int*, cudaStream_t, float*, NetActs);
 
 void net_infer_prepare_attributes() {
   cudaFuncSetAttribute(k_net_infer_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);

@@ -7,7 +7,10 @@ exact convolution, except where the FP32 accumulation bound leaves the
 rounding undecided (a counted one-ulp flip, which must then be one of the
 two neighbours).  Weight gradients are checked element by element against
 the oracle's backward pass run on the GPU's own activations, within the FP32
-accumulation bound of each entry's absolute sum.  The solver with the network attached is compared with the oracle
+accumulation bound of each entry's absolute sum.  Training runs on the
+tensor cores: the forward pass is the fused inference kernel keeping its
+activations, the weight and data gradients are tcgen05 GEMMs whose FP32
+gradients enter as bfloat16 hi + lo pairs (16 significant bits).  The solver with the network attached is compared with the oracle
 MPCG using the same network as its extra column; training on solver-made
 (residual, error) pairs must lower the loss on those pairs and on pairs of
 held-out coefficient fields, and the trained column must keep the solver
@@ -189,14 +192,15 @@ def test_weight_gradients_match_oracle(M, nodes, B):
     assert np.linalg.norm(g_gpu - g_ind) <= 3e-2 * np.linalg.norm(g_ind)
 
 
-def test_training_step_applies_the_gradient(M):
+@pytest.mark.parametrize("B,batch", [(4, 4), (3, 4)])
+def test_training_step_applies_the_gradient(M, B, batch):
     """With beta1 = 0 and eps >> |g| the first Adam step of mg_learned_train
     is -lr g / (|g| + eps): the step on one batch recovers the gradient that
-    mg_learned_grad returns for that batch (FP32 update arithmetic)."""
+    mg_learned_grad returns for that batch (FP32 update arithmetic), also for
+    a batch shorter than the batch size (fewer weight-gradient partials)."""
     prob = pb.diffusion_macro(2, 33, 22, rhs="normal", rhs_seed=1)
     H = _hier(M, prob)
     theta = OL.init_params(5)
-    B = 4
     R = np.stack([pb.normal(40 + k, prob.n) for k in range(B)])
     R /= np.linalg.norm(R, axis=1, keepdims=True)
     E = np.stack([pb.normal(50 + k, prob.n) for k in range(B)])
@@ -205,7 +209,7 @@ def test_training_step_applies_the_gradient(M):
     g_ref, _ = M.mg_learned_grad(H.h, theta, Rd, Ed, B)
     params = theta.copy()
     lr = eps = 1e3
-    M.mg_learned_train([H.h], [0] * B, Rd, Ed, params, epochs=1, batch=B, lr=lr, beta1=0.0, beta2=0.999, eps=eps)
+    M.mg_learned_train([H.h], [0] * B, Rd, Ed, params, epochs=1, batch=batch, lr=lr, beta1=0.0, beta2=0.999, eps=eps)
     step = params.astype(np.float64) - theta.astype(np.float64)
     g32 = g_ref.astype(np.float32).astype(np.float64)
     want = -lr * g32 / (np.abs(g32) + eps)
