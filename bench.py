@@ -1230,10 +1230,48 @@ def bench_learned(args):
     return 0
 
 
+def bench_net_kernels(args):
+    """Throughput of the learned column's tensor-core kernels on their own:
+    inference (mg_learned_forward, 4 images of the 1025^2 field) and one
+    training forward + backward pass (mg_learned_grad, 8 pairs of a 257^2
+    field; --nodes sets the training grid).  Also the driver of the ncu
+    captures of these kernels."""
+    import numpy as np
+    import torch
+    from paper_2402_12833_gb300 import build as _build
+    from paper_2402_12833_gb300 import mpcg as M
+    from paper_2402_12833_gb300 import problems as pb
+    _build.build()
+    M.load()
+    out = {}
+    theta = pb.net_init_params(7)
+    for key, nodes, nimg in (("inference", 1025, 4), ("training_pass", args.nodes or 257, 8)):
+        prob = pb.diffusion_macro(2, nodes, 21)
+        H = M.Hierarchy(torch.from_numpy(prob.stencil).cuda(), 2, nodes, prob.levels)
+        R = np.stack([pb.normal(40 + k, prob.n) for k in range(nimg)])
+        R /= np.linalg.norm(R, axis=1, keepdims=True)
+        Rd = torch.from_numpy(R.astype(np.float32)).cuda()
+        if key == "inference":
+            M.mg_learned_attach(H.h, theta)
+            Y = torch.zeros_like(Rd)
+            fn = lambda: M.mg_learned_forward(H.h, Rd, Y, nimg)
+        else:
+            Ed = torch.from_numpy(np.stack([pb.normal(50 + k, prob.n) for k in range(nimg)]).astype(np.float32)).cuda()
+            fn = lambda: M.mg_learned_grad(H.h, theta, Rd, Ed, nimg)
+        ms = _timed(fn, args.steps, args.warmup, torch.cuda.current_stream())
+        out[key] = {"grid": f"{nodes}^2", "images": nimg, "ms_per_call": ms, "us_per_image": 1e3 * ms / nimg}
+        H.close()
+    print(json.dumps({"metric": "learned-column kernel throughput", "workload": "net_kernels", "unit": "us/image",
+                      "inference": out["inference"], "training_pass": out["training_pass"],
+                      "note": "each call is synchronous through the C ABI (includes its host round trip)"}))
+    return 0
+
+
 def main():
     faulthandler.enable()   # a native crash prints the Python stack of the call that made it
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["poisson3d", "batched", "learned", "elasticity", "example1", "algebraic"],
+    ap.add_argument("--workload", choices=["poisson3d", "batched", "learned", "elasticity", "example1", "algebraic",
+                                           "net_kernels"],
                     default="poisson3d",
                     help="poisson3d: the headline line; batched / learned / elasticity: the other workloads")
     ap.add_argument("--epochs", type=int, default=20, help="training epochs of the learned workload")
@@ -1256,11 +1294,11 @@ def main():
                     help="with --only: nodes per side of the 3D Poisson grid (smaller cases for profiling)")
     args = ap.parse_args()
     if args.nodes is not None:
-        if args.only is None:
-            ap.error("--nodes goes with --only")
+        if args.only is None and args.workload != "net_kernels":
+            ap.error("--nodes goes with --only or --workload net_kernels")
         global NODES
         NODES = args.nodes
-    if args.warmup < 3 and args.impl == "ours":
+    if args.warmup < 3 and args.impl == "ours" and args.only is None and args.workload != "net_kernels":
         print("note: warmup raised to 3", file=sys.stderr)
         args.warmup = 3
     if args.impl == "reference":
@@ -1275,6 +1313,8 @@ def main():
         return bench_algebraic(args)
     if args.workload == "learned":
         return bench_learned(args)
+    if args.workload == "net_kernels":
+        return bench_net_kernels(args)
     return bench_ours(args)
 
 
