@@ -26,6 +26,9 @@ from __future__ import annotations
 import numpy as np
 
 CHANS = (2, 16, 16, 16, 1)
+# the 3D vector-valued network of the elasticity problem: the three
+# displacement components of r / ||r|| in, three out, 3x3x3 convolutions
+CHANS3 = (3, 16, 16, 16, 3)
 
 
 def n_params() -> int:
@@ -160,5 +163,126 @@ def batch_grad(theta, pairs, n1, emulate=True):
         y = y.reshape(-1)
         L, dy = angle_loss(y, e, A @ y, A @ e)
         gsum += backward(cache, dy.reshape(n1, n1))
+        Lsum += L
+    return Lsum / len(pairs), gsum / len(pairs)
+
+
+# ---------------------------------------------------------------------------
+# 3D network for vector problems (3D elasticity): the same architecture with
+# 3x3x3 convolutions, channels 3 -> 16 -> 16 -> 16 -> 3, on the grid of
+# unknown nodes (zero padding outside it, i.e. at clamped nodes and beyond
+# the free faces).  Weights W[co][ci][kz][ky][kx] multiply the input at
+# (x + kx - 1, y + ky - 1, z + kz - 1); the input is r / ||r|| per component
+# (no coefficient channel: the material is homogeneous).  Unknown
+# i = a + 3 * node, node = x + nx (y + ny z) maps to image[a, z, y, x].
+
+def n_params3() -> int:
+    return sum(CHANS3[i + 1] * CHANS3[i] * 27 for i in range(4))
+
+
+def unpack3(theta: np.ndarray) -> list:
+    out, k = [], 0
+    for i in range(4):
+        sz = CHANS3[i + 1] * CHANS3[i] * 27
+        out.append(theta[k:k + sz].reshape(CHANS3[i + 1], CHANS3[i], 3, 3, 3))
+        k += sz
+    return out
+
+
+def init_params3(seed: int = 7) -> np.ndarray:
+    from paper_2402_12833_gb300.problems import net_init_params
+    return net_init_params(seed, CHANS3, taps=27)
+
+
+def to_image3(v: np.ndarray, shape) -> np.ndarray:
+    """Vector of 3 components per node -> (3, Z, Y, X)."""
+    Z, Y, X = shape
+    return np.asarray(v).reshape(Z, Y, X, 3).transpose(3, 0, 1, 2)
+
+
+def from_image3(img: np.ndarray) -> np.ndarray:
+    return np.ascontiguousarray(img.transpose(1, 2, 3, 0)).reshape(-1)
+
+
+def conv3(x: np.ndarray, W: np.ndarray) -> np.ndarray:
+    """Zero-padded 3x3x3 correlation: x (cin, Z, Y, X), W (cout, cin, 3, 3, 3)."""
+    cin, Z, Y, X = x.shape
+    xp = np.zeros((cin, Z + 2, Y + 2, X + 2), dtype=np.float64)
+    xp[:, 1:-1, 1:-1, 1:-1] = x
+    out = np.zeros((W.shape[0], Z, Y, X))
+    for kz in range(3):
+        for ky in range(3):
+            for kx in range(3):
+                patch = xp[:, kz:kz + Z, ky:ky + Y, kx:kx + X]
+                out += np.einsum("oc,czyx->ozyx", W[:, :, kz, ky, kx].astype(np.float64), patch)
+    return out
+
+
+def conv3_transpose(d: np.ndarray, W: np.ndarray) -> np.ndarray:
+    """Adjoint of ``conv3`` with respect to its input."""
+    cout, Z, Y, X = d.shape
+    out = np.zeros((W.shape[1], Z + 2, Y + 2, X + 2))
+    for kz in range(3):
+        for ky in range(3):
+            for kx in range(3):
+                out[:, kz:kz + Z, ky:ky + Y, kx:kx + X] += np.einsum("oc,ozyx->czyx",
+                                                                     W[:, :, kz, ky, kx].astype(np.float64), d)
+    return out[:, 1:-1, 1:-1, 1:-1]
+
+
+def conv3_wgrad(d: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """d L / d W for out = conv3(x, W), given d = d L / d out."""
+    cin, Z, Y, X = x.shape
+    xp = np.zeros((cin, Z + 2, Y + 2, X + 2))
+    xp[:, 1:-1, 1:-1, 1:-1] = x
+    g = np.zeros((d.shape[0], cin, 3, 3, 3))
+    for kz in range(3):
+        for ky in range(3):
+            for kx in range(3):
+                g[:, :, kz, ky, kx] = np.einsum("ozyx,czyx->oc", d, xp[:, kz:kz + Z, ky:ky + Y, kx:kx + X])
+    return g
+
+
+def forward3(theta: np.ndarray, rhat: np.ndarray, emulate: bool = True):
+    """y = N(rhat) for rhat of shape (3, Z, Y, X); returns (y, cache)."""
+    Ws = unpack3(theta)
+    rnd = bf16 if emulate else (lambda v: np.asarray(v, dtype=np.float64))
+    Wq = [rnd(W) for W in Ws]
+    x = rnd(np.asarray(rhat, dtype=np.float32 if emulate else np.float64))
+    acts = [x]
+    for i in range(4):
+        z = conv3(x, Wq[i])
+        if i < 3:
+            z = np.maximum(z, 0.0)
+            x = rnd(z.astype(np.float32) if emulate else z)
+            acts.append(x)
+        else:
+            x = z
+    return x, (Wq, acts)
+
+
+def backward3(cache, dy: np.ndarray) -> np.ndarray:
+    """Gradient of the loss w.r.t. the packed 3D parameters, given dL/dy of
+    shape (3, Z, Y, X) (the rounding to bfloat16 passed straight through)."""
+    Wq, acts = cache
+    d = np.asarray(dy, dtype=np.float64)
+    grads = [None] * 4
+    for i in range(3, -1, -1):
+        grads[i] = conv3_wgrad(d, acts[i])
+        if i > 0:
+            d = conv3_transpose(d, Wq[i]) * (acts[i] > 0)
+    return np.concatenate([g.reshape(-1) for g in grads])
+
+
+def batch_grad3(theta, pairs, shape, emulate=True):
+    """Mean loss and gradient over pairs [(rhat, e, A)] of vectors (3 unknowns
+    per node) on a grid of unknown nodes of the given (Z, Y, X) shape."""
+    gsum = np.zeros(n_params3())
+    Lsum = 0.0
+    for rhat, e, A in pairs:
+        y, cache = forward3(theta, to_image3(rhat, shape), emulate)
+        yv = from_image3(y)
+        L, dy = angle_loss(yv, e, A @ yv, A @ e)
+        gsum += backward3(cache, to_image3(dy, shape))
         Lsum += L
     return Lsum / len(pairs), gsum / len(pairs)

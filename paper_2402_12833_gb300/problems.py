@@ -443,14 +443,15 @@ def fracture_network(kf: float, nodes: int = 545, km: float = 1.0, delta: float 
     return Problem(2, nodes, levels, st, b, name=f"fracture_{nodes}_kf{kf:g}", kappa=kap, faces=faces)
 
 
-def net_init_params(seed: int = 7, chans=(2, 16, 16, 16, 1)) -> np.ndarray:
-    """Initial weights of the learned column's 3x3 network, layer by layer
-    W[co][ci][ky][kx]: Kaiming-uniform draws U(-b, b), b = sqrt(6 / (9 ci)),
-    from the splitmix64 uniforms above (float32)."""
+def net_init_params(seed: int = 7, chans=(2, 16, 16, 16, 1), taps: int = 9) -> np.ndarray:
+    """Initial weights of the learned column's network, layer by layer
+    W[co][ci][taps]: Kaiming-uniform draws U(-b, b), b = sqrt(6 / (taps ci)),
+    from the splitmix64 uniforms above (float32); taps = 9 for the 3x3
+    network of 2D problems, 27 for the 3x3x3 one of 3D vector problems."""
     parts = []
     for i in range(len(chans) - 1):
-        b = np.sqrt(6.0 / (chans[i] * 9))
-        u = uniform(seed * 1000 + i, chans[i + 1] * chans[i] * 9)
+        b = np.sqrt(6.0 / (chans[i] * taps))
+        u = uniform(seed * 1000 + i, chans[i + 1] * chans[i] * taps)
         parts.append((2.0 * u - 1.0) * b)
     return np.concatenate(parts).astype(np.float32)
 
