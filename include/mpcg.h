@@ -418,6 +418,15 @@ mpcg_status mg_detach_q1_kappa(mg_hierarchy* h);
  * (zero weight, or a dropped column, when it does not help).
  * Parameters: mg_learned_num_params() floats, layer by layer, each layer
  * W[co][ci][ky][kx] (tap (ky, kx) multiplies the input at (x+kx-1, y+ky-1)).
+ *
+ * Single 3D vector problems (3 unknowns per node, e.g. linear elasticity)
+ * take a 3x3x3 network instead: channels 3 -> 16 -> 16 -> 16 -> 3 (ReLU after
+ * the first three, zero padding outside the unknown grid, no bias, no
+ * coefficient channel; bfloat16 weights and activations, FP32 accumulation)
+ * maps the three displacement components of r/||r|| to the three components
+ * of y.  Parameters: mg_learned_num_params_of(h) = 16416 floats, layer by
+ * layer, each W[co][ci][kz][ky][kx] (tap (kz, ky, kx) multiplies the input
+ * at (x+kx-1, y+ky-1, z+kz-1)).  Training batches hold 1..8 pairs.
  */
 typedef struct {
   int epochs;        /* passes over the training pairs */
@@ -426,9 +435,13 @@ typedef struct {
   unsigned long long seed;        /* shuffling */
 } mg_train_opts;
 
+/* Parameter count of the 2D network. */
 int mg_learned_num_params(void);
-/* Attach weights (host or device floats); mpcg_solve then uses
- * mg_num_levels()+1 columns.  Errors: MPCG_ERR_ARG (3D grid, wrong count). */
+/* Parameter count of h's network (the 2D or the 3D vector one); -1 for NULL. */
+int mg_learned_num_params_of(const mg_hierarchy* h);
+/* Attach weights (host or device floats, mg_learned_num_params_of(h) of
+ * them); mpcg_solve then uses mg_num_levels()+1 columns.  Errors:
+ * MPCG_ERR_ARG (scalar 3D or batched problem, wrong count). */
 mpcg_status mg_learned_attach(mg_hierarchy* h, const float* params, int nparams);
 mpcg_status mg_learned_detach(mg_hierarchy* h);
 /* y = N(rhat, c) for nimg images on h's fine grid (device, n floats each,
@@ -439,13 +452,15 @@ mpcg_status mg_learned_forward(mg_hierarchy* h, const float* rhat_dev, float* y_
  * 4 * nimg * n * 16 floats, [layer][image][point][channel], points
  * lexicographic (x fastest); layer 0 holds the two bfloat16 input channels
  * (zero-padded to 16), layers 1-3 the bfloat16 outputs of the first three
- * convolutions after ReLU. */
+ * convolutions after ReLU.  3D vector problems: points are the grid nodes
+ * (n / 3 of them), layer 0 holds the three input components. */
 mpcg_status mg_learned_forward_acts(mg_hierarchy* h, const float* rhat_dev, float* y_dev, float* acts_dev,
                                    int nimg);
 /*
  * One forward and backward pass of the training kernels (no weight update)
- * on nimg (1..MPCG_MAX_COLS) pairs (rhat_i, e_i) of problem h (device, n
- * floats each): grad (host or device, mg_learned_num_params() doubles) gets
+ * on nimg (1..MPCG_MAX_COLS; 1..8 for 3D vector problems) pairs (rhat_i,
+ * e_i) of problem h (device, n floats each): grad (host or device,
+ * mg_learned_num_params_of(h) doubles) gets
  * the gradient of the mean A-angle loss with respect to params (host or
  * device floats, the FP32 master weights; the forward uses their bfloat16
  * rounding); loss (host, may be NULL) the mean loss; acts_dev (device, may

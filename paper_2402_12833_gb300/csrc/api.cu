@@ -710,9 +710,14 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
     enqueue_mg<T>(h, S, S.r, S.Z, S.state, s);
   }
   if (h->net_on) {
-    LAUNCH(h, K_NET, s,
-           launch_net_infer<T>(L.g, 1, S.r, L.g.len, h->net_c, h->net_wtc, S.state, nullptr,
-                               S.Z + (size_t)(C - 1) * L.g.len, h->net_err, s));
+    if (L.g.ncomp == 3)   // the 3D vector network, one launch per layer
+      LAUNCH(h, K_NET, s,
+             launch_net3_forward<T>(L.g, 1, S.r, L.g.len, h->net_wq, S.state, h->net_acts, nullptr,
+                                    S.Z + (size_t)(C - 1) * L.g.cp, h->net_err, s));
+    else
+      LAUNCH(h, K_NET, s,
+             launch_net_infer<T>(L.g, 1, S.r, L.g.len, h->net_c, h->net_wtc, S.state, nullptr,
+                                 S.Z + (size_t)(C - 1) * L.g.len, h->net_err, s));
   }
   bool mf = false;
   if (h->algebraic) {
@@ -2273,10 +2278,19 @@ mpcg_status mg_get_operator(mg_hierarchy* h, int level, double* planes) {
 // Learned search column (an extension beyond the paper).
 namespace {
 
+// the 3x3x3 network of 3D vector problems, else the 3x3 one of 2D problems
+bool net3_of(const mg_hierarchy* h) {
+  const GridDesc& g = h->lev[h->levels - 1].g;
+  return h->dim == 3 && g.ncomp == 3 && h->nb == 1 && !h->algebraic;
+}
+int net_params_of(const mg_hierarchy* h) { return net3_of(h) ? kNet3Params : kNetParams; }
+
 mpcg_status net_check_grid(const mg_hierarchy* h) {
   const GridDesc& g = h->lev[h->levels - 1].g;
+  if (net3_of(h)) return MPCG_OK;
   if (h->dim != 2 || h->nb != 1 || g.ncomp != 1 || g.nx != g.ny || g.px != g.py || g.lp < 0) {
-    set_err("the learned column is implemented for single (unbatched) scalar 2D problems with Dirichlet faces");
+    set_err("the learned column is implemented for single (unbatched) scalar 2D problems with Dirichlet faces "
+            "and for single 3D vector problems (3 unknowns per node)");
     return MPCG_ERR_ARG;
   }
   return MPCG_OK;
@@ -2284,9 +2298,21 @@ mpcg_status net_check_grid(const mg_hierarchy* h) {
 
 // Coefficient channel and inference buffers of hierarchy h.
 mpcg_status net_prepare(mg_hierarchy* h) {
-  if (h->net_c) return MPCG_OK;
+  if (h->net_wq) return MPCG_OK;
   cudaStream_t s = h->stream;
   const Level& L = h->lev[h->levels - 1];
+  if (net3_of(h)) {   // the 3D network: activations on the node box, no coefficient channel
+    const size_t alen = (size_t)net3_act_len(L.g);
+    CKS(h->net_mem.get(&h->net_wq, kNet3Params, s));
+    CKS(h->net_mem.get(&h->net_acts.a0, alen * 16, s));
+    CKS(h->net_mem.get(&h->net_acts.a1, alen * 16, s));
+    CKS(h->net_mem.get(&h->net_acts.a2, alen * 16, s));
+    CKS(h->net_mem.get(&h->net_acts.a3, alen * 16, s));
+    CKS(h->net_mem.get(&h->net_err, 1, s));
+    net3_prepare_attributes();
+    CK(cudaGetLastError());
+    return MPCG_OK;
+  }
   double* part = nullptr;
   CKS(h->net_mem.get(&h->net_c, L.g.len, s));
   CKS(h->net_mem.get(&part, 256, s));
@@ -2310,6 +2336,83 @@ mpcg_status copy_floats(float* dst, const float* src, int n, cudaStream_t s) {
   return MPCG_OK;
 }
 
+// Buffers of one training batch of up to B images on grid g: inputs, A e,
+// the network's outputs and activations, the data gradients, the
+// weight-gradient partials (2D: the 3x3 network; net3: the 3x3x3 one).
+struct NetBatch {
+  bool net3 = false;
+  int np = 0;
+  float *rb = nullptr, *eb = nullptr, *aeb = nullptr, *y = nullptr, *ay = nullptr, *dy = nullptr, *d4 = nullptr;
+  double *dots = nullptr, *coef = nullptr;
+  NetActs a = {};
+  NetGrads gr = {};
+  unsigned char* wtc = nullptr;
+  int* terr = nullptr;
+  double** parts_dev = nullptr;
+};
+
+int net_batch_blocks(const NetBatch& nb, const GridDesc& g, int nimg) {
+  return nb.net3 ? net3_wgrad_blocks(g, nimg) : net_wgrad_tc_blocks(g, nimg);
+}
+
+mpcg_status net_batch_alloc(bool net3, const GridDesc& g, int B, Alloc& mem, cudaStream_t s, NetBatch& nb) {
+  nb.net3 = net3;
+  nb.np = net3 ? kNet3Params : kNetParams;
+  mpcg_status st = MPCG_OK;
+  auto get = [&](auto** p, size_t n) {
+    if (st == MPCG_OK) st = mem.get(p, n, s);
+  };
+  const size_t L = g.len;
+  const size_t A = net3 ? (size_t)net3_act_len(g) : L;   // points of one activation image
+  const int nw = net_batch_blocks(nb, g, B);
+  get(&nb.rb, B * L);
+  get(&nb.eb, B * L);
+  get(&nb.aeb, B * L);
+  get(&nb.y, B * L);
+  get(&nb.ay, B * L);
+  get(&nb.dy, B * L);
+  get(&nb.a.a0, B * A * (net3 ? 16 : kNetIn));
+  get(&nb.a.a1, B * A * 16);
+  get(&nb.a.a2, B * A * 16);
+  get(&nb.a.a3, B * A * 16);
+  get(&nb.gr.d1, B * A * 16);
+  get(&nb.gr.d2, B * A * 16);
+  get(&nb.gr.d3, B * A * 16);
+  if (net3) get(&nb.d4, B * A * 16);
+  const size_t lsz[4] = {net3 ? 16 * 3 * 27u : (size_t)kNetC1 * kNetIn * 9, net3 ? 16 * 16 * 27u : (size_t)kNetW * kNetC1 * 9,
+                         net3 ? 16 * 16 * 27u : (size_t)kNetW * kNetW * 9, net3 ? 3 * 16 * 27u : (size_t)kNetW * 9};
+  for (int l = 0; l < 4; ++l) get(&nb.gr.part[l], lsz[l] * nw);
+  get(&nb.dots, 3 * 64 * B);
+  get(&nb.coef, 2 * B);
+  if (!net3) get(&nb.wtc, (size_t)net_tc_weight_bytes());
+  get(&nb.terr, 1);
+  get(&nb.parts_dev, 4);
+  if (st != MPCG_OK) return st;
+  if (net3) net3_prepare_attributes();
+  else net_train_tc_prepare_attributes();
+  CK(cudaMemcpyAsync(nb.parts_dev, nb.gr.part, sizeof(nb.gr.part), cudaMemcpyHostToDevice, s));
+  return MPCG_OK;
+}
+
+// One forward and backward pass on nimg images already in nb.rb / eb / aeb:
+// y, A y, the loss (added to loss_sum), dL/dy and the weight-gradient
+// partials.  c: the 2D network's coefficient channel; st32: the FP32 fine
+// operator.
+void net_batch_step(NetBatch& nb, const GridDesc& g, int nimg, const float* c, const float* st32, const float* wq,
+                    double* loss_sum, cudaStream_t s) {
+  if (nb.net3) {
+    launch_net3_forward<float>(g, nimg, nb.rb, g.len, wq, nullptr, nb.a, nb.y, (float*)nullptr, nb.terr, s);
+  } else {
+    launch_net_pack_tc(wq, nb.wtc, s);
+    launch_net_infer<float>(g, nimg, nb.rb, g.len, c, nb.wtc, nullptr, nb.y, (float*)nullptr, nb.terr, s, nullptr,
+                            nb.a);
+  }
+  launch_spmm<float>(g, st32, nb.y, nb.ay, nimg, nullptr, nullptr, s);
+  launch_net_loss_grad(g, nimg, nb.y, nb.ay, nb.eb, nb.aeb, nb.dots, nb.coef, loss_sum, nb.dy, s);
+  if (nb.net3) launch_net3_backward(g, nimg, wq, nb.a, nb.dy, nb.gr, nb.d4, nb.terr, s);
+  else launch_net_backward(g, nimg, wq, nb.a, nb.dy, nb.gr, nb.terr, s);
+}
+
 // Rebuild the solvers after the column count changed.
 void drop_mixed_graph_fwd(mg_hierarchy* h);
 mpcg_status rebuild_solvers(mg_hierarchy* h) {
@@ -2331,26 +2434,29 @@ extern "C" {
 
 int mg_learned_num_params(void) { return kNetParams; }
 
+int mg_learned_num_params_of(const mg_hierarchy* h) { return h ? net_params_of(h) : -1; }
+
 mpcg_status mg_learned_attach(mg_hierarchy* h, const float* params, int nparams) {
   g_err.clear();
   CKS(check_h(h));
   CKS(net_check_grid(h));
-  if (!params || nparams != kNetParams) {
-    set_err("params must hold mg_learned_num_params() = %d floats", kNetParams);
+  const int np = net_params_of(h);
+  if (!params || nparams != np) {
+    set_err("params must hold mg_learned_num_params_of(h) = %d floats", np);
     return MPCG_ERR_ARG;
   }
-  if (h->levels + 1 > MPCG_MAX_COLS || h->opt.sum_columns || h->opt.vcycle) {
+  if (h->levels + 1 > (net3_of(h) ? kMaxVecCols : MPCG_MAX_COLS) || h->opt.sum_columns || h->opt.vcycle) {
     set_err("too many grids for an extra column, or the columns are summed into one / a V-cycle");
     return MPCG_ERR_ARG;
   }
   CK(cudaSetDevice(h->device));
   CKS(net_prepare(h));
   float* tmp = nullptr;
-  CK(cudaMalloc(&tmp, sizeof(float) * kNetParams));
-  mpcg_status st = copy_floats(tmp, params, kNetParams, h->stream);
+  CK(cudaMalloc(&tmp, sizeof(float) * np));
+  mpcg_status st = copy_floats(tmp, params, np, h->stream);
   if (st == MPCG_OK) {
-    launch_round_bf16(tmp, h->net_wq, kNetParams, h->stream);
-    launch_net_pack_tc(h->net_wq, h->net_wtc, h->stream);
+    launch_round_bf16(tmp, h->net_wq, np, h->stream);
+    if (!net3_of(h)) launch_net_pack_tc(h->net_wq, h->net_wtc, h->stream);
   }
   cudaStreamSynchronize(h->stream);
   cudaFree(tmp);
@@ -2444,10 +2550,22 @@ mpcg_status mg_learned_forward_acts(mg_hierarchy* h, const float* rhat_dev, floa
   Alloc tmp;
   float *r = nullptr, *y = nullptr;
   mpcg_status st = MPCG_OK;
-  if ((st = tmp.get(&r, (size_t)nimg * g.len, s)) == MPCG_OK && (st = tmp.get(&y, (size_t)nimg * g.len, s)) == MPCG_OK) {
+  NetActs a3 = {};
+  if (net3_of(h)) {   // activations for nimg images
+    const size_t A = (size_t)net3_act_len(g) * nimg * 16;
+    for (__nv_bfloat16** p : {&a3.a0, &a3.a1, &a3.a2, &a3.a3})
+      if (st == MPCG_OK) st = tmp.get(p, A, s);
+  }
+  if (st == MPCG_OK && (st = tmp.get(&r, (size_t)nimg * g.len, s)) == MPCG_OK &&
+      (st = tmp.get(&y, (size_t)nimg * g.len, s)) == MPCG_OK) {
     launch_pack<float, float>(g, rhat_dev, g.n, r, nimg, s);
-    launch_net_infer<float>(g, nimg, r, g.len, h->net_c, h->net_wtc, nullptr, y, (float*)nullptr, h->net_err, s,
-                            acts_dev);
+    if (net3_of(h)) {
+      launch_net3_forward<float>(g, nimg, r, g.len, h->net_wq, nullptr, a3, y, (float*)nullptr, h->net_err, s);
+      if (acts_dev) launch_net3_acts_export(g, nimg, a3, acts_dev, s);
+    } else {
+      launch_net_infer<float>(g, nimg, r, g.len, h->net_c, h->net_wtc, nullptr, y, (float*)nullptr, h->net_err, s,
+                              acts_dev);
+    }
     launch_unpack<float, float>(g, y, y_dev, g.n, nimg, s);
     int err = 0;
     if (cudaMemcpyAsync(&err, h->net_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -2472,87 +2590,54 @@ mpcg_status mg_learned_grad(mg_hierarchy* h, const float* params, const float* r
   g_err.clear();
   CKS(check_h(h));
   CKS(net_check_grid(h));
-  if (!params || !rhat_dev || !e_dev || !grad || nimg < 1 || nimg > MPCG_MAX_COLS) {
-    set_err("mg_learned_grad: params, rhat, e and grad are required and nimg must be in 1..%d", MPCG_MAX_COLS);
+  const bool net3 = net3_of(h);
+  const int maxb = net3 ? kMaxVecCols : MPCG_MAX_COLS;
+  if (!params || !rhat_dev || !e_dev || !grad || nimg < 1 || nimg > maxb) {
+    set_err("mg_learned_grad: params, rhat, e and grad are required and nimg must be in 1..%d", maxb);
     return MPCG_ERR_ARG;
   }
   CK(cudaSetDevice(h->device));
   cudaStream_t s = h->stream;
   const GridDesc g = h->lev[h->levels - 1].g;
-  if (g.p > 1024) {
+  if (!net3 && g.p > 1024) {
     set_err("training grids are limited to 1025 nodes per side");
     return MPCG_ERR_ARG;
   }
   CKS(build_f32(h));
   CKS(net_prepare(h));
-  net_train_tc_prepare_attributes();
   Alloc mem;
-  mpcg_status st = MPCG_OK;
-  auto get = [&](auto** p, size_t n) {
-    if (st == MPCG_OK) st = mem.get(p, n, s);
-  };
-  const int B = nimg;
-  const size_t L = g.len;
-  const int nw = net_wgrad_tc_blocks(g, B);
-  float *rb, *eb, *aeb, *y, *ay, *dy, *master, *wq;
-  double *dots, *coef, *lsum, *gd;
-  NetActs a;
-  NetGrads gr;
-  get(&rb, B * L);
-  get(&eb, B * L);
-  get(&aeb, B * L);
-  get(&y, B * L);
-  get(&ay, B * L);
-  get(&dy, B * L);
-  get(&a.a0, B * L * kNetIn);
-  get(&a.a1, B * L * kNetC1);
-  get(&a.a2, B * L * kNetW);
-  get(&a.a3, B * L * kNetW);
-  get(&gr.d1, B * L * kNetW);
-  get(&gr.d2, B * L * kNetW);
-  get(&gr.d3, B * L * kNetW);
-  get(&gr.part[0], (size_t)kNetC1 * kNetIn * 9 * nw);
-  get(&gr.part[1], (size_t)kNetW * kNetC1 * 9 * nw);
-  get(&gr.part[2], (size_t)kNetW * kNetW * 9 * nw);
-  get(&gr.part[3], (size_t)kNetW * 9 * nw);
-  get(&master, kNetParams);
-  get(&wq, kNetParams);
-  get(&dots, 3 * 64 * B);
-  get(&coef, 2 * B);
-  get(&lsum, 1);
-  get(&gd, kNetParams);
-  unsigned char* wtc = nullptr;
-  int* terr = nullptr;
-  get(&wtc, (size_t)net_tc_weight_bytes());
-  get(&terr, 1);
-  double** parts_dev = nullptr;
-  get(&parts_dev, 4);
+  NetBatch nbt;
+  mpcg_status st = net_batch_alloc(net3, g, nimg, mem, s, nbt);
+  double *lsum = nullptr, *gd = nullptr;
+  float *master = nullptr, *wq = nullptr;
+  if (st == MPCG_OK) st = mem.get(&lsum, 1, s);
+  if (st == MPCG_OK) st = mem.get(&gd, nbt.np, s);
+  if (st == MPCG_OK) st = mem.get(&master, nbt.np, s);
+  if (st == MPCG_OK) st = mem.get(&wq, nbt.np, s);
   if (st != MPCG_OK) {
     mem.release();
     return st;
   }
-  cudaMemcpyAsync(parts_dev, gr.part, sizeof(gr.part), cudaMemcpyHostToDevice, s);
-  copy_floats(master, params, kNetParams, s);
-  launch_round_bf16(master, wq, kNetParams, s);
-  launch_pack<float, float>(g, rhat_dev, g.n, rb, B, s);
-  launch_pack<float, float>(g, e_dev, g.n, eb, B, s);
+  copy_floats(master, params, nbt.np, s);
+  launch_round_bf16(master, wq, nbt.np, s);
+  launch_pack<float, float>(g, rhat_dev, g.n, nbt.rb, nimg, s);
+  launch_pack<float, float>(g, e_dev, g.n, nbt.eb, nimg, s);
   const float* st32 = h->lev[h->levels - 1].st32;
-  launch_spmm<float>(g, st32, eb, aeb, B, nullptr, nullptr, s);
+  launch_spmm<float>(g, st32, nbt.eb, nbt.aeb, nimg, nullptr, nullptr, s);
   cudaMemsetAsync(lsum, 0, sizeof(double), s);
-  launch_net_pack_tc(wq, wtc, s);
-  launch_net_infer<float>(g, B, rb, L, h->net_c, wtc, nullptr, y, (float*)nullptr, terr, s, nullptr, a);
-  launch_spmm<float>(g, st32, y, ay, B, nullptr, nullptr, s);
-  launch_net_loss_grad(g, B, y, ay, eb, aeb, dots, coef, lsum, dy, s);
-  launch_net_backward(g, B, wq, a, dy, gr, terr, s);
-  launch_net_grad_sum(parts_dev, nw, gd, s);
-  if (acts_dev) launch_net_acts_export(g, B, a, acts_dev, s);
-  if (y_dev) launch_unpack<float, float>(g, y, y_dev, g.n, B, s);
+  net_batch_step(nbt, g, nimg, h->net_c, st32, wq, lsum, s);
+  launch_net_grad_sum(nbt.parts_dev, net_batch_blocks(nbt, g, nimg), net3 ? 1 : 0, gd, s);
+  if (acts_dev) {
+    if (net3) launch_net3_acts_export(g, nimg, nbt.a, acts_dev, s);
+    else launch_net_acts_export(g, nimg, nbt.a, acts_dev, s);
+  }
+  if (y_dev) launch_unpack<float, float>(g, nbt.y, y_dev, g.n, nimg, s);
   double lh = 0.0;
   int terr_h = 0;
-  if (cudaMemcpyAsync(grad, gd, sizeof(double) * kNetParams,
+  if (cudaMemcpyAsync(grad, gd, sizeof(double) * nbt.np,
                       is_device_pointer(grad) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(&lh, lsum, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemcpyAsync(&terr_h, terr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&terr_h, nbt.terr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
     set_err("mg_learned_grad: %s", cudaGetErrorString(cudaGetLastError()));
     st = MPCG_ERR_CUDA;
@@ -2573,16 +2658,21 @@ mpcg_status mg_learned_train(mg_hierarchy* const* hs, int nprob, const int* pair
     set_err("mg_learned_train: bad arguments");
     return MPCG_ERR_ARG;
   }
+  CKS(check_h(hs[0]));
+  const bool net3 = net3_of(hs[0]);
   const int B = opts->batch;
-  if (B < 1 || B > MPCG_MAX_COLS || opts->epochs < 0) {
-    set_err("batch must be in 1..%d and epochs >= 0", MPCG_MAX_COLS);
+  const int maxb = net3 ? kMaxVecCols : MPCG_MAX_COLS;
+  if (B < 1 || B > maxb || opts->epochs < 0) {
+    set_err("batch must be in 1..%d and epochs >= 0", maxb);
     return MPCG_ERR_ARG;
   }
   for (int i = 0; i < nprob; ++i) {
     CKS(check_h(hs[i]));
     CKS(net_check_grid(hs[i]));
-    if (hs[i]->lev[hs[i]->levels - 1].g.n1 != hs[0]->lev[hs[0]->levels - 1].g.n1) {
-      set_err("all training problems must share the fine grid size");
+    const GridDesc& gi = hs[i]->lev[hs[i]->levels - 1].g;
+    const GridDesc& g0 = hs[0]->lev[hs[0]->levels - 1].g;
+    if (net3_of(hs[i]) != net3 || gi.nx != g0.nx || gi.ny != g0.ny || gi.nz != g0.nz || gi.ncomp != g0.ncomp) {
+      set_err("all training problems must share the fine grid");
       return MPCG_ERR_ARG;
     }
   }
@@ -2595,7 +2685,7 @@ mpcg_status mg_learned_train(mg_hierarchy* const* hs, int nprob, const int* pair
   CK(cudaSetDevice(h0->device));
   cudaStream_t s = h0->stream;
   const GridDesc g = h0->lev[h0->levels - 1].g;
-  if (g.p > 1024) {
+  if (!net3 && g.p > 1024) {
     set_err("training grids are limited to 1025 nodes per side");
     return MPCG_ERR_ARG;
   }
@@ -2603,58 +2693,29 @@ mpcg_status mg_learned_train(mg_hierarchy* const* hs, int nprob, const int* pair
     CKS(build_f32(hs[i]));
     CKS(net_prepare(hs[i]));
   }
-  net_train_tc_prepare_attributes();
   Alloc mem;
-  mpcg_status st = MPCG_OK;
+  NetBatch nbt;
+  mpcg_status st = net_batch_alloc(net3, g, B, mem, s, nbt);
   auto get = [&](auto** p, size_t n) {
     if (st == MPCG_OK) st = mem.get(p, n, s);
   };
-  float *R, *E, *AE, *rb, *eb, *aeb, *y, *ay, *dy, *master, *m, *v, *wq;
-  double *dots, *coef, *loss;
-  NetActs a;
-  NetGrads gr;
+  float *R, *E, *AE, *master, *m, *v, *wq;
+  double* loss;
   const size_t L = g.len;
-  const int nw = net_wgrad_tc_blocks(g, B);
   get(&R, (size_t)npairs * L);
   get(&E, (size_t)npairs * L);
   get(&AE, (size_t)npairs * L);
-  get(&rb, B * L);
-  get(&eb, B * L);
-  get(&aeb, B * L);
-  get(&y, B * L);
-  get(&ay, B * L);
-  get(&dy, B * L);
-  get(&a.a0, B * L * kNetIn);
-  get(&a.a1, B * L * kNetC1);
-  get(&a.a2, B * L * kNetW);
-  get(&a.a3, B * L * kNetW);
-  get(&gr.d1, B * L * kNetW);
-  get(&gr.d2, B * L * kNetW);
-  get(&gr.d3, B * L * kNetW);
-  get(&gr.part[0], (size_t)kNetC1 * kNetIn * 9 * nw);
-  get(&gr.part[1], (size_t)kNetW * kNetC1 * 9 * nw);
-  get(&gr.part[2], (size_t)kNetW * kNetW * 9 * nw);
-  get(&gr.part[3], (size_t)kNetW * 9 * nw);
-  get(&master, kNetParams);
-  get(&m, kNetParams);
-  get(&v, kNetParams);
-  get(&wq, kNetParams);
-  get(&dots, 3 * 64 * B);
-  get(&coef, 2 * B);
+  get(&master, nbt.np);
+  get(&m, nbt.np);
+  get(&v, nbt.np);
+  get(&wq, nbt.np);
   get(&loss, 1);
-  unsigned char* wtc = nullptr;
-  int* terr = nullptr;
-  get(&wtc, (size_t)net_tc_weight_bytes());
-  get(&terr, 1);
-  double** parts_dev = nullptr;
-  get(&parts_dev, 4);
   if (st != MPCG_OK) {
     mem.release();
     return st;
   }
-  cudaMemcpyAsync(parts_dev, gr.part, sizeof(gr.part), cudaMemcpyHostToDevice, s);
-  copy_floats(master, params, kNetParams, s);
-  launch_round_bf16(master, wq, kNetParams, s);
+  copy_floats(master, params, nbt.np, s);
+  launch_round_bf16(master, wq, nbt.np, s);
   // training set in the padded layout, and A e per pair (FP32 operators)
   launch_pack<float, float>(g, rhat_dev, g.n, R, npairs, s);
   launch_pack<float, float>(g, e_dev, g.n, E, npairs, s);
@@ -2684,26 +2745,21 @@ mpcg_status mg_learned_train(mg_hierarchy* const* hs, int nprob, const int* pair
     for (auto& bt : batches) {
       const int nb = (int)bt.size();
       for (int k = 0; k < nb; ++k) {
-        cudaMemcpyAsync(rb + k * L, R + (size_t)bt[k] * L, sizeof(float) * L, cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(eb + k * L, E + (size_t)bt[k] * L, sizeof(float) * L, cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(aeb + k * L, AE + (size_t)bt[k] * L, sizeof(float) * L, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(nbt.rb + k * L, R + (size_t)bt[k] * L, sizeof(float) * L, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(nbt.eb + k * L, E + (size_t)bt[k] * L, sizeof(float) * L, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(nbt.aeb + k * L, AE + (size_t)bt[k] * L, sizeof(float) * L, cudaMemcpyDeviceToDevice, s);
       }
       mg_hierarchy* hp = hs[pair_prob[bt[0]]];
-      const float* c = hp->net_c;
-      launch_net_pack_tc(wq, wtc, s);
-      launch_net_infer<float>(g, nb, rb, L, c, wtc, nullptr, y, (float*)nullptr, terr, s, nullptr, a);
-      launch_spmm<float>(g, hp->lev[hp->levels - 1].st32, y, ay, nb, nullptr, nullptr, s);
-      launch_net_loss_grad(g, nb, y, ay, eb, aeb, dots, coef, loss, dy, s);
-      launch_net_backward(g, nb, wq, a, dy, gr, terr, s);
+      net_batch_step(nbt, g, nb, hp->net_c, hp->lev[hp->levels - 1].st32, wq, loss, s);
       ++step;
-      // a short last batch of a problem launches fewer blocks than nw
-      launch_net_adam(parts_dev, net_wgrad_tc_blocks(g, nb), master, m, v, wq, step, (float)opts->lr, (float)opts->beta1,
-                      (float)opts->beta2, (float)opts->eps, s);
+      // a short last batch of a problem launches fewer blocks
+      launch_net_adam(nbt.parts_dev, net_batch_blocks(nbt, g, nb), net3 ? 1 : 0, master, m, v, wq, step,
+                      (float)opts->lr, (float)opts->beta1, (float)opts->beta2, (float)opts->eps, s);
     }
     double lh = 0.0;
     int terr_h = 0;
     if (cudaMemcpyAsync(&lh, loss, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(&terr_h, terr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&terr_h, nbt.terr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
       set_err("training step failed: %s", cudaGetErrorString(cudaGetLastError()));
       st = MPCG_ERR_CUDA;
@@ -2717,7 +2773,7 @@ mpcg_status mg_learned_train(mg_hierarchy* const* hs, int nprob, const int* pair
     if (loss_hist) loss_hist[ep] = lh / (double)batches.size();
   }
   if (st == MPCG_OK) {
-    cudaMemcpyAsync(params, master, sizeof(float) * kNetParams,
+    cudaMemcpyAsync(params, master, sizeof(float) * nbt.np,
                     is_device_pointer(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) st = MPCG_ERR_CUDA;
   }

@@ -242,6 +242,12 @@ constexpr int kNetOff2 = kNetOff1 + kNetC1 * kNetIn * 9;
 constexpr int kNetOff3 = kNetOff2 + kNetW * kNetC1 * 9;
 constexpr int kNetOff4 = kNetOff3 + kNetW * kNetW * 9;
 constexpr int kNetParams = kNetOff4 + kNetW * 9;
+// the 3x3x3 network of 3D vector problems: channels 3 -> 16 -> 16 -> 16 -> 3
+constexpr int kNet3Off1 = 0;
+constexpr int kNet3Off2 = kNet3Off1 + 16 * 3 * 27;
+constexpr int kNet3Off3 = kNet3Off2 + 16 * 16 * 27;
+constexpr int kNet3Off4 = kNet3Off3 + 16 * 16 * 27;
+constexpr int kNet3Params = kNet3Off4 + 3 * 16 * 27;
 
 struct NetActs {   // [B][len][C] bfloat16, zero pads
   __nv_bfloat16 *a0, *a1, *a2, *a3;
@@ -270,6 +276,21 @@ void launch_net_dgrad_tc(const GridDesc& g, int B, int cout, const float* dOut, 
                          const __nv_bfloat16* act_in, float* dIn, int* err, cudaStream_t s);
 int net_wgrad_tc_blocks(const GridDesc& g, int B);
 void net_train_tc_prepare_attributes();
+// The 3x3x3 network of 3D vector problems (learned3_tc.cu): activations are
+// [B][net3_act_len(g)][16] bfloat16 on the node box; partials of the weight
+// gradient are net3_wgrad_blocks per parameter; d4 is scratch of the size of
+// one activation set in FP32.
+long long net3_act_len(const GridDesc& g);
+int net3_wgrad_blocks(const GridDesc& g, int B);
+void net3_prepare_attributes();
+template <typename T>
+void launch_net3_forward(const GridDesc& g, int B, const T* r, long long r_ld, const float* wq, const DevState* state,
+                         NetActs acts, float* y, T* z, int* err, cudaStream_t s);
+void launch_net3_backward(const GridDesc& g, int B, const float* wq, NetActs acts, const float* dy, NetGrads gr,
+                          float* d4, int* err, cudaStream_t s);
+// activations of the 3D network to the compact float layout
+// [4][B][unknown nodes][16], nodes x fastest
+void launch_net3_acts_export(const GridDesc& g, int B, NetActs acts, float* out, cudaStream_t s);
 
 void launch_net_pack_tc(const float* wq, void* wtc, cudaStream_t s);
 int net_tc_weight_bytes();
@@ -280,11 +301,12 @@ void launch_net_loss_grad(const GridDesc& g, int B, const float* y, const float*
                           const float* Ae, double* part, double* coef, double* loss_sum, float* dy, cudaStream_t s);
 // the weight-gradient partials of every layer are nblk per parameter (the
 // block count of the last backward pass: net_wgrad_tc_blocks of its batch)
-void launch_net_adam(const double* const* parts_dev, int nblk, float* master, float* m, float* v, float* wq,
+// net3: the 3D network's layer sizes and parameter count
+void launch_net_adam(const double* const* parts_dev, int nblk, int net3, float* master, float* m, float* v, float* wq,
                      int step, float lr, float b1, float b2, float eps, cudaStream_t s);
 void launch_round_bf16(const float* src, float* dst, int n, cudaStream_t s);
 // grad[i] = sum of the weight-gradient partials of parameter i (all layers)
-void launch_net_grad_sum(const double* const* parts_dev, int nblk, double* grad, cudaStream_t s);
+void launch_net_grad_sum(const double* const* parts_dev, int nblk, int net3, double* grad, cudaStream_t s);
 // activations a0..a3 of the training forward ([B][len][C] bfloat16, padded)
 // to the compact float layout [4][B][n1*n1][16] (a0 zero-padded to 16)
 void launch_net_acts_export(const GridDesc& g, int B, NetActs acts, float* out, cudaStream_t s);

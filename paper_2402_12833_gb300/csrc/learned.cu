@@ -75,12 +75,19 @@ __global__ void k_net_dy(GridDesc g, int B, const float* __restrict__ Ay, const 
 // Reduce the weight-gradient partials of all layers and take one Adam step
 // (Kingma & Ba 2015, bias-corrected) on the FP32 master weights; also writes
 // the bfloat16-rounded copy used by the forward pass.
-__global__ void k_net_adam(const double* const* parts, int nblk, int nparams, float* master, float* m,
+// layer sizes of the 2D (3x3) and 3D (3x3x3, 3 -> 16 -> 16 -> 16 -> 3) networks
+__device__ __forceinline__ int net_layer_size(int net3, int layer) {
+  if (net3) return layer == 0 || layer == 3 ? 3 * 16 * 27 : 16 * 16 * 27;
+  return layer == 0 ? kNetC1 * kNetIn * 9 : (layer == 3 ? kNetW * 9 : kNetW * kNetW * 9);
+}
+
+__global__ void k_net_adam(const double* const* parts, int nblk, int nparams, int net3, float* master, float* m,
                            float* v, float* wq, int step, float lr, float b1, float b2, float eps) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nparams) return;
   int layer = 0, off = i;
-  const int sizes[4] = {kNetC1 * kNetIn * 9, kNetW * kNetW * 9, kNetW * kNetW * 9, kNetW * 9};
+  const int sizes[4] = {net_layer_size(net3, 0), net_layer_size(net3, 1), net_layer_size(net3, 2),
+                        net_layer_size(net3, 3)};
   while (off >= sizes[layer]) off -= sizes[layer], ++layer;
   double gsum = 0.0;
   const double* p = parts[layer] + (long long)off * nblk;
@@ -97,11 +104,12 @@ __global__ void k_net_adam(const double* const* parts, int nblk, int nparams, fl
   wq[i] = __bfloat162float(__float2bfloat16_rn(w));
 }
 
-__global__ void k_net_grad_sum(const double* const* parts, int nblk, int nparams, double* grad) {
+__global__ void k_net_grad_sum(const double* const* parts, int nblk, int nparams, int net3, double* grad) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nparams) return;
   int layer = 0, off = i;
-  const int sizes[4] = {kNetC1 * kNetIn * 9, kNetW * kNetW * 9, kNetW * kNetW * 9, kNetW * 9};
+  const int sizes[4] = {net_layer_size(net3, 0), net_layer_size(net3, 1), net_layer_size(net3, 2),
+                        net_layer_size(net3, 3)};
   while (off >= sizes[layer]) off -= sizes[layer], ++layer;
   double gsum = 0.0;
   const double* p = parts[layer] + (long long)off * nblk;
@@ -181,14 +189,16 @@ void launch_net_loss_grad(const GridDesc& g, int B, const float* y, const float*
   k_net_dy<<<grid_for((long long)B * g.len, 4096), kBlock, 0, s>>>(g, B, Ay, Ae, coef, dy);
 }
 
-void launch_net_adam(const double* const* parts_dev, int nblk, float* master, float* m, float* v, float* wq,
+void launch_net_adam(const double* const* parts_dev, int nblk, int net3, float* master, float* m, float* v, float* wq,
                      int step, float lr, float b1, float b2, float eps, cudaStream_t s) {
-  k_net_adam<<<(kNetParams + kBlock - 1) / kBlock, kBlock, 0, s>>>(parts_dev, nblk, kNetParams, master, m, v, wq,
+  const int np = net3 ? kNet3Params : kNetParams;
+  k_net_adam<<<(np + kBlock - 1) / kBlock, kBlock, 0, s>>>(parts_dev, nblk, np, net3, master, m, v, wq,
                                                                    step, lr, b1, b2, eps);
 }
 
-void launch_net_grad_sum(const double* const* parts_dev, int nblk, double* grad, cudaStream_t s) {
-  k_net_grad_sum<<<(kNetParams + kBlock - 1) / kBlock, kBlock, 0, s>>>(parts_dev, nblk, kNetParams, grad);
+void launch_net_grad_sum(const double* const* parts_dev, int nblk, int net3, double* grad, cudaStream_t s) {
+  const int np = net3 ? kNet3Params : kNetParams;
+  k_net_grad_sum<<<(np + kBlock - 1) / kBlock, kBlock, 0, s>>>(parts_dev, nblk, np, net3, grad);
 }
 
 void launch_net_acts_export(const GridDesc& g, int B, NetActs acts, float* out, cudaStream_t s) {

@@ -1,0 +1,492 @@
+// The learned column of 3D vector problems (3D elasticity) on the
+// fifth-generation tensor cores: a 3x3x3 convolutional network with channels
+// 3 -> 16 -> 16 -> 16 -> 3 (ReLU after the first three, zero padding, no
+// bias) maps the three displacement components of r / ||r|| to y; the solver
+// appends z = ||r|| y (all three components) as one MPCG column.
+//
+// Activations live on the node box of the vector grid (node t = x + px (y +
+// py z), the same box as each displacement component) as 16 bfloat16
+// channels per node, [B][act_len][16] with the grid's zero guards in front;
+// nodes outside the unknown grid (pads) hold zeros, the zero padding of the
+// convolutions.
+//
+// One launch per layer (the 3D halo of a fused four-layer tile would cost
+// more than the round trip of 32 bytes per node): a CTA owns R = 4 rows of
+// up to 128 nodes at one z and stages the 3 x (R + 2) input rows around them
+// (x from -1 to 128) as K-major bfloat16 planes.  Per output row and tap
+// (dx, dy, dz) the A operand is a staged row shifted by the tap (SBO = 128 B,
+// LBO = one plane), B the tap's 16 x 16 weight tile, D 16 FP32 columns of
+// TMEM per row: 27 tcgen05.mma (kind::f16, M = 128 nodes, N = 16, K = 16)
+// per row in the forward pass; the data gradient (the transposed
+// convolution, masked by the ReLU pattern of the layer input) takes its FP32
+// input as bfloat16 hi + lo planes, 54 MMAs per row.  The weight gradient is
+// the pixel-reduction GEMM of the 2D network with 27 taps: A = dOut^T (hi
+// rows 0-15, lo rows 16-31), B = the im2col of the layer input (27 taps x 16
+// channels = 432 rows, three MMAs of N = 144 per K step), accumulated in 432
+// TMEM columns over a CTA's run of 64-node chunks.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+#include "tc.cuh"
+
+namespace mpcg {
+
+namespace {
+
+constexpr int kT3 = 128;                       // threads: TMEM lanes 0..127 = nodes of a row tile
+constexpr int kR3 = 4;                         // output rows per CTA
+constexpr int kXS3 = 130;                      // staged nodes per row: x = -1 .. 128
+constexpr int kRows3 = 3 * (kR3 + 2);          // staged rows (z - 1 .. z + 1) x (y0 - 1 .. y0 + R)
+constexpr int kPlane3 = kRows3 * kXS3 * 16;    // bytes of one 8-channel plane
+constexpr int kW3Bytes = 27 * 512;             // 27 weight tiles of 16 x 16 bf16
+constexpr long long kWait3 = 1LL << 22;
+
+__device__ __forceinline__ int canon16(int row, int k) {
+  return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+__host__ __device__ __forceinline__ long long act_len3(const GridDesc& g) {
+  return (2 * g.G + g.cstride + 31) / 32 * 32;
+}
+
+__device__ __forceinline__ bool inside3(const GridDesc& g, int x, int y, int z) {
+  return x >= 0 && y >= 0 && z >= 0 && x < g.nx && y < g.ny && z < g.nz;
+}
+
+// smem byte layout of the conv kernel: NPL planes, the weight tiles, the
+// row barriers, the TMEM slot
+template <int NPL>
+struct Conv3Smem {
+  static constexpr int kWOff = NPL * kPlane3;
+  static constexpr int kBarOff = kWOff + kW3Bytes;
+  static constexpr int kBytes = kBarOff + 8 * kR3 + 16;
+};
+
+// MODE 0: forward, out = relu?(sum W in(p + off)), in bfloat16 activations;
+//         LAST: 3 FP32 outputs to a vector-layout array (y, or z = s y).
+// MODE 1: data gradient, dIn = mask(act_in > 0) sum W^T dOut(p - off), dOut
+//         FP32 [B][act_len][16] (zero beyond the layer's outputs).
+template <int MODE, bool RELU, bool LAST, typename T>
+__global__ void __launch_bounds__(kT3, 1)
+    k_net3_conv_tc(GridDesc g, int B, const void* __restrict__ in, const float* __restrict__ W, int cin, int cout,
+                   const __nv_bfloat16* __restrict__ act_in, void* __restrict__ out, float* __restrict__ yv,
+                   T* __restrict__ zv, const DevState* state, int* err) {
+  constexpr int NPL = MODE == 0 ? 2 : 4;
+  using S = Conv3Smem<NPL>;
+  if (state && state->done) return;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::kBarOff);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S::kBarOff + 8 * kR3);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int x0 = blockIdx.x * 128, y0 = blockIdx.y * kR3;
+  const int z = blockIdx.z % g.pz, b = blockIdx.z / g.pz;
+  const long long alen = act_len3(g);
+  const long long abase = (long long)b * alen + g.G;
+  const long long px = g.px, pxy = g.pxy;
+
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), 64);
+  if (tid < kR3) tc::mbar_init(tc::smem_u32(bar + tid));
+  if (tid == 0) tc::mbar_init_fence();
+  // weight tiles: forward row n = co, column k = ci; gradient row n = ci, k = co
+  for (int e = tid; e < 27 * 256; e += kT3) {
+    const int t = e / 256, n = (e / 16) % 16, k = e % 16;
+    const int co = MODE == 0 ? n : k, ci = MODE == 0 ? k : n;
+    const float w = (co < cout && ci < cin) ? W[(co * cin + ci) * 27 + t] : 0.f;
+    *reinterpret_cast<__nv_bfloat16*>(smem + S::kWOff + t * 512 + canon16(n, k)) = __float2bfloat16_rn(w);
+  }
+  // staged rows: slot (dz, sy) = dz * (R + 2) + sy holds node row (y0 - 1 + sy, z - 1 + dz)
+  for (int e = tid; e < kRows3 * kXS3; e += kT3) {
+    const int row = e / kXS3, xs = e % kXS3;
+    const int dz = row / (kR3 + 2), sy = row % (kR3 + 2);
+    const int x = x0 - 1 + xs, y = y0 - 1 + sy, zz = z - 1 + dz;
+    const bool in_grid = inside3(g, x, y, zz);
+    const long long node = abase + x + px * y + pxy * zz;
+    const int off = (row * kXS3 + xs) * 16;
+    if (MODE == 0) {
+      uint4 p0 = make_uint4(0, 0, 0, 0), p1 = make_uint4(0, 0, 0, 0);
+      if (in_grid) {
+        const uint4* src = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(in) + node * 16);
+        p0 = src[0];
+        p1 = src[1];
+      }
+      *reinterpret_cast<uint4*>(smem + off) = p0;
+      *reinterpret_cast<uint4*>(smem + kPlane3 + off) = p1;
+    } else {
+      float hi[16], lo[16];
+      const float* src = static_cast<const float*>(in) + node * 16;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) tc::split_bf16(in_grid ? src[c] : 0.f, hi[c], lo[c]);
+#pragma unroll
+      for (int pl = 0; pl < 4; ++pl) {
+        const float* v = pl < 2 ? hi + 8 * pl : lo + 8 * (pl - 2);
+        *reinterpret_cast<uint4*>(smem + pl * kPlane3 + off) =
+            make_uint4(tc::pack_bf16x2(v[0], v[1]), tc::pack_bf16x2(v[2], v[3]), tc::pack_bf16x2(v[4], v[5]),
+                       tc::pack_bf16x2(v[6], v[7]));
+      }
+    }
+  }
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = tc::idesc_bf16(128, 16);
+  if (tid == 0) {
+    const uint32_t s0 = tc::smem_u32(smem), w0 = tc::smem_u32(smem + S::kWOff);
+    for (int r = 0; r < kR3; ++r) {
+      for (int t = 0; t < 27; ++t) {
+        const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
+        // forward: input at (x + kx - 1, y + ky - 1, z + kz - 1);
+        // gradient: dOut at (x - kx + 1, y - ky + 1, z - kz + 1)
+        const int sz = MODE == 0 ? kz : 2 - kz, sy = MODE == 0 ? r + ky : r + 2 - ky, sx = MODE == 0 ? kx : 2 - kx;
+        const uint32_t a = s0 + (uint32_t)(((sz * (kR3 + 2) + sy) * kXS3 + sx) * 16);
+        const uint64_t bdesc = tc::sdesc(w0 + t * 512, 128, 256);
+        tc::mma_bf16(tmem + 16 * r, tc::sdesc(a, kPlane3, 128), bdesc, idesc, t > 0 ? 1u : 0u);
+        if (MODE == 1) tc::mma_bf16(tmem + 16 * r, tc::sdesc(a + 2 * kPlane3, kPlane3, 128), bdesc, idesc, 1u);
+      }
+      tc::mma_commit(tc::smem_u32(bar + r));
+    }
+  }
+  bool failed = false;
+  const int x = x0 + tid;
+  const double zs = (LAST && state) ? state->rnorm : 1.0;
+  for (int r = 0; r < kR3; ++r) {
+    const bool ok = tc::mbar_wait(tc::smem_u32(bar + r), 0u, kWait3);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    tc::fence_after();
+    float v[16];
+    tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * r, v);
+    const int y = y0 + r;
+    if (!inside3(g, x, y, z)) continue;   // pads keep their zeros
+    const long long t = x + px * y + pxy * z;
+    const long long node = abase + t;
+    if (MODE == 1) {
+      const uint4* m = reinterpret_cast<const uint4*>(act_in + node * 16);
+      const uint4 m0 = m[0], m1 = m[1];
+      const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+      float o[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const unsigned short hb = (unsigned short)(c & 1 ? mw[c >> 1] >> 16 : mw[c >> 1] & 0xFFFFu);
+        o[c] = (c < cin && __bfloat162float(__ushort_as_bfloat16(hb)) > 0.f) ? v[c] : 0.f;
+      }
+      float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + node * 16);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dst[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    } else if (LAST) {
+      // components a = 0..2 of node t in the vector layout of the grid
+      const long long vb = (long long)b * g.len + g.G + t;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (yv) yv[vb + a * g.cstride] = v[a];
+        if (zv) zv[vb + a * g.cstride] = (T)(zs * (double)v[a]);
+      }
+    } else {
+      uint32_t q[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float a0 = RELU ? fmaxf(v[2 * k], 0.f) : v[2 * k];
+        const float a1 = RELU ? fmaxf(v[2 * k + 1], 0.f) : v[2 * k + 1];
+        q[k] = tc::pack_bf16x2(2 * k < cout ? a0 : 0.f, 2 * k + 1 < cout ? a1 : 0.f);
+      }
+      uint4* dst = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out) + node * 16);
+      dst[0] = make_uint4(q[0], q[1], q[2], q[3]);
+      dst[1] = make_uint4(q[4], q[5], q[6], q[7]);
+    }
+  }
+  if (failed) {
+    if (tid == 0) atomicExch(err, 1);
+    for (int r = 0; r < kR3; ++r) tc::mbar_wait(tc::smem_u32(bar + r), 0u, kWait3);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 64);
+}
+
+// Network input: channels 0..2 = bf16(r_a * s), s = 1 / ||r|| from the
+// solver state (or 1), channels 3..15 zero; grid nodes only.
+template <typename T>
+__global__ void k_net3_input(GridDesc g, int B, const T* __restrict__ r, long long r_ld, const DevState* state,
+                             __nv_bfloat16* __restrict__ a0) {
+  if (state && state->done) return;
+  const float s = state ? (float)(state->rnorm > 0.0 ? 1.0 / state->rnorm : 0.0) : 1.f;
+  const long long alen = act_len3(g);
+  const long long total = (long long)B * g.cstride;
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total;
+       u += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(u / g.cstride);
+    const long long t = u - (long long)b * g.cstride;
+    const int x = (int)(t % g.px), y = (int)((t / g.px) % g.py), z = (int)(t / g.pxy);
+    if (!inside3(g, x, y, z)) continue;
+    const T* rb = r + (long long)b * r_ld + g.G + t;
+    float v[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a] = (float)rb[a * g.cstride] * s;
+    uint4* dst = reinterpret_cast<uint4*>(a0 + ((long long)b * alen + g.G + t) * 16);
+    dst[0] = make_uint4(tc::pack_bf16x2(v[0], v[1]), tc::pack_bf16x2(v[2], 0.f), 0u, 0u);
+    dst[1] = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+// dOut of the last layer: the vector-layout dL/dy to [B][act_len][16] FP32
+// (channels 0..2).
+__global__ void k_net3_dy_channels(GridDesc g, int B, const float* __restrict__ dy, float* __restrict__ d) {
+  const long long alen = act_len3(g);
+  const long long total = (long long)B * g.cstride;
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total;
+       u += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(u / g.cstride);
+    const long long t = u - (long long)b * g.cstride;
+    const int x = (int)(t % g.px), y = (int)((t / g.px) % g.py), z = (int)(t / g.pxy);
+    if (!inside3(g, x, y, z)) continue;
+    float4* dst = reinterpret_cast<float4*>(d + ((long long)b * alen + g.G + t) * 16);
+    const float* src = dy + (long long)b * g.len + g.G + t;
+    dst[0] = make_float4(src[0], src[g.cstride], src[2 * g.cstride], 0.f);
+  }
+}
+
+// Weight gradient, 27 taps: see the file comment.
+constexpr int kWChunk3 = 64;
+constexpr int kWA3 = 128 * kWChunk3 * 2;      // 16 KB
+constexpr int kWB3 = 432 * kWChunk3 * 2;      // 54 KB
+constexpr int kWStage3 = kWA3 + kWB3;
+constexpr int kWSmem3 = 2 * kWStage3 + 64;    // 140 KB: one CTA per SM (its 512 TMEM columns)
+
+__device__ __forceinline__ int toff64(int row, int k) {
+  return (row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+__global__ void __launch_bounds__(kT3, 1)
+    k_net3_wgrad_tc(GridDesc g, int cin, int cout, int chunks_per_block, int blocks_per_image,
+                    const float* __restrict__ dOut, const __nv_bfloat16* __restrict__ act, double* part, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kWStage3);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * kWStage3 + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = blockIdx.x / blocks_per_image, blk = blockIdx.x % blocks_per_image;
+  const long long nchunks = (g.cstride + kWChunk3 - 1) / kWChunk3;
+  const long long c0 = (long long)blk * chunks_per_block;
+  long long c1 = c0 + chunks_per_block;
+  if (c1 > nchunks) c1 = nchunks;
+  const int n = c0 < c1 ? (int)(c1 - c0) : 0;
+  const long long alen = act_len3(g);
+  const long long abase = (long long)b * alen + g.G;
+
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), 512);
+  if (tid < 2) tc::mbar_init(tc::smem_u32(bar + tid));
+  if (tid == 0) tc::mbar_init_fence();
+  for (int i = tid; i < 2 * kWA3 / 16; i += kT3) {
+    const int st = i / (kWA3 / 16), j = i % (kWA3 / 16);
+    reinterpret_cast<uint4*>(smem + st * kWStage3)[j] = make_uint4(0, 0, 0, 0);
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = tc::idesc_bf16(128, 144);
+  bool failed = false;
+  for (int i = 0; i < n && !failed; ++i) {
+    const int st = i & 1;
+    unsigned char* A = smem + st * kWStage3;
+    unsigned char* Bt = A + kWA3;
+    if (i >= 2) {
+      const bool ok = tc::mbar_wait(tc::smem_u32(bar + st), (uint32_t)(((i - 2) >> 1) & 1), kWait3);
+      failed = __syncthreads_or(!ok);
+      if (failed) break;
+      tc::fence_after();
+    }
+    const long long t0 = (c0 + i) * kWChunk3;
+    // A: dOut^T, hi rows co, lo rows 16 + co (16 channels, zero beyond cout)
+    for (int item = tid; item < 2 * 8; item += kT3) {
+      const int cg = item / 8, pg = item % 8;
+#pragma unroll 1
+      for (int c = 0; c < 8; ++c) {
+        const int co = cg * 8 + c;
+        float hi[8], lo[8];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const long long t = t0 + pg * 8 + kk;
+          const float d = (t < g.cstride && co < cout) ? dOut[(abase + t) * 16 + co] : 0.f;
+          tc::split_bf16(d, hi[kk], lo[kk]);
+        }
+        *reinterpret_cast<uint4*>(A + toff64(co, pg * 8)) =
+            make_uint4(tc::pack_bf16x2(hi[0], hi[1]), tc::pack_bf16x2(hi[2], hi[3]), tc::pack_bf16x2(hi[4], hi[5]),
+                       tc::pack_bf16x2(hi[6], hi[7]));
+        *reinterpret_cast<uint4*>(A + toff64(16 + co, pg * 8)) =
+            make_uint4(tc::pack_bf16x2(lo[0], lo[1]), tc::pack_bf16x2(lo[2], lo[3]), tc::pack_bf16x2(lo[4], lo[5]),
+                       tc::pack_bf16x2(lo[6], lo[7]));
+      }
+    }
+    // B: im2col rows (tap, ci), 27 taps x 2 channel halves x 8 point groups
+    for (int item = tid; item < 27 * 2 * 8; item += kT3) {
+      const int tap = item / 16, half = (item / 8) % 2, pg = item % 8;
+      const int kz = tap / 9, ky = (tap / 3) % 3, kx = tap % 3;
+      const long long off = (kx - 1) + (long long)(ky - 1) * g.px + (long long)(kz - 1) * g.pxy;
+      uint32_t w[8][4];
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const long long t = t0 + pg * 8 + kk;
+        if (t >= g.cstride) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) w[kk][j] = 0u;
+        } else {
+          const uint4 v = *reinterpret_cast<const uint4*>(act + (abase + t + off) * 16 + half * 8);
+          w[kk][0] = v.x; w[kk][1] = v.y; w[kk][2] = v.z; w[kk][3] = v.w;
+        }
+      }
+#pragma unroll
+      for (int ci = 0; ci < 8; ++ci) {
+        const unsigned sel = (ci & 1) ? 0x7632u : 0x5410u;
+        const int wi = ci >> 1;
+        *reinterpret_cast<uint4*>(Bt + toff64(tap * 16 + half * 8 + ci, pg * 8)) =
+            make_uint4(__byte_perm(w[0][wi], w[1][wi], sel), __byte_perm(w[2][wi], w[3][wi], sel),
+                       __byte_perm(w[4][wi], w[5][wi], sel), __byte_perm(w[6][wi], w[7][wi], sel));
+      }
+    }
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (tid == 0) {
+      const uint32_t a_addr = tc::smem_u32(A), b_addr = tc::smem_u32(Bt);
+#pragma unroll
+      for (int ks = 0; ks < kWChunk3 / 16; ++ks)
+#pragma unroll
+        for (int part3 = 0; part3 < 3; ++part3)   // taps 9 part3 .. 9 part3 + 8: B rows from 144 part3
+          tc::mma_bf16(tmem + 144 * part3, tc::sdesc(a_addr + ks * 256, 128, 1024),
+                       tc::sdesc(b_addr + part3 * 18 * 1024 + ks * 256, 128, 1024), idesc, (i > 0 || ks > 0) ? 1u : 0u);
+      tc::mma_commit(tc::smem_u32(bar + st));
+    }
+  }
+  bool drained = true;
+  if (n > 0) {
+    const int last = n - 1;
+    drained = tc::mbar_wait(tc::smem_u32(bar + (last & 1)), (uint32_t)((last >> 1) & 1), kWait3);
+    if (!drained && n > 1) tc::mbar_wait(tc::smem_u32(bar + ((last - 1) & 1)), (uint32_t)(((last - 1) >> 1) & 1), kWait3);
+  }
+  failed = __syncthreads_or(failed || !drained);
+  tc::fence_after();
+  if (failed) {
+    if (tid == 0) atomicExch(err, 1);
+  } else if (warp == 0) {
+#pragma unroll 1
+    for (int j = 0; j < 432 / 16; ++j) {
+      float v[16];
+      if (n > 0) tc::tmem_ld16(tmem + 16 * j, v);
+      else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const float lo = __shfl_down_sync(0xffffffffu, v[c], 16);
+        const int ncol = 16 * j + c, tap = ncol / 16, ci = ncol % 16, co = lane;
+        if (lane < cout && ci < cin)
+          part[(long long)((co * cin + ci) * 27 + tap) * gridDim.x + blockIdx.x] = (double)v[c] + (double)lo;
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+constexpr int kWCpb3 = 16;   // 64-node chunks per CTA
+
+__global__ void k_net3_acts_export(GridDesc g, int B, NetActs a, float* out) {
+  const long long alen = act_len3(g);
+  const long long nn = (long long)g.nx * g.ny * g.nz;
+  const long long total = 4LL * B * nn;
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total;
+       u += (long long)gridDim.x * blockDim.x) {
+    const int L = (int)(u / (B * nn));
+    const int b = (int)((u / nn) % B);
+    const long long q = u % nn;
+    const int x = (int)(q % g.nx), y = (int)((q / g.nx) % g.ny), z = (int)(q / ((long long)g.nx * g.ny));
+    const long long node = (long long)b * alen + g.G + x + g.px * (long long)y + g.pxy * (long long)z;
+    const __nv_bfloat16* src = L == 0 ? a.a0 : L == 1 ? a.a1 : L == 2 ? a.a2 : a.a3;
+    float* o = out + u * 16;
+    for (int c = 0; c < 16; ++c) o[c] = __bfloat162float(src[node * 16 + c]);
+  }
+}
+
+}  // namespace
+
+void launch_net3_acts_export(const GridDesc& g, int B, NetActs acts, float* out, cudaStream_t s) {
+  k_net3_acts_export<<<grid_for(4LL * B * g.nx * g.ny * g.nz, 4096), kBlock, 0, s>>>(g, B, acts, out);
+}
+
+long long net3_act_len(const GridDesc& g) { return act_len3(g); }
+
+int net3_wgrad_blocks(const GridDesc& g, int B) {
+  const long long nchunks = (g.cstride + kWChunk3 - 1) / kWChunk3;
+  return B * (int)((nchunks + kWCpb3 - 1) / kWCpb3);
+}
+
+void net3_prepare_attributes() {
+  cudaFuncSetAttribute(k_net3_conv_tc<0, true, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       Conv3Smem<2>::kBytes);
+  cudaFuncSetAttribute(k_net3_conv_tc<0, false, true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       Conv3Smem<2>::kBytes);
+  cudaFuncSetAttribute(k_net3_conv_tc<0, false, true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       Conv3Smem<2>::kBytes);
+  cudaFuncSetAttribute(k_net3_conv_tc<0, false, true, dw>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       Conv3Smem<2>::kBytes);
+  cudaFuncSetAttribute(k_net3_conv_tc<1, false, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       Conv3Smem<4>::kBytes);
+  cudaFuncSetAttribute(k_net3_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmem3);
+}
+
+// Forward pass of nimg images: r (type T, vector layout, image stride r_ld,
+// scaled by 1 / ||r|| from state when given) -> acts.a0..a3 (bfloat16) and
+// y (float, vector layout, may be null) and/or z = ||r|| y (T, may be null).
+template <typename T>
+void launch_net3_forward(const GridDesc& g, int B, const T* r, long long r_ld, const float* wq, const DevState* state,
+                         NetActs acts, float* y, T* z, int* err, cudaStream_t s) {
+  const long long total = (long long)B * g.cstride;
+  k_net3_input<T><<<grid_for(total, 4096), kBlock, 0, s>>>(g, B, r, r_ld, state, acts.a0);
+  const dim3 grid((unsigned)((g.px + 127) / 128), (unsigned)((g.py + kR3 - 1) / kR3), (unsigned)(g.pz * B));
+  const int sm2 = Conv3Smem<2>::kBytes;
+  k_net3_conv_tc<0, true, false, float><<<grid, kT3, sm2, s>>>(g, B, acts.a0, wq + kNet3Off1, 3, 16, nullptr,
+                                                               acts.a1, nullptr, nullptr, state, err);
+  k_net3_conv_tc<0, true, false, float><<<grid, kT3, sm2, s>>>(g, B, acts.a1, wq + kNet3Off2, 16, 16, nullptr,
+                                                               acts.a2, nullptr, nullptr, state, err);
+  k_net3_conv_tc<0, true, false, float><<<grid, kT3, sm2, s>>>(g, B, acts.a2, wq + kNet3Off3, 16, 16, nullptr,
+                                                               acts.a3, nullptr, nullptr, state, err);
+  k_net3_conv_tc<0, false, true, T><<<grid, kT3, sm2, s>>>(g, B, acts.a3, wq + kNet3Off4, 16, 3, nullptr, nullptr,
+                                                           y, z, state, err);
+}
+template void launch_net3_forward<float>(const GridDesc&, int, const float*, long long, const float*, const DevState*,
+                                         NetActs, float*, float*, int*, cudaStream_t);
+template void launch_net3_forward<double>(const GridDesc&, int, const double*, long long, const float*,
+                                          const DevState*, NetActs, float*, double*, int*, cudaStream_t);
+template void launch_net3_forward<dw>(const GridDesc&, int, const dw*, long long, const float*, const DevState*,
+                                      NetActs, float*, dw*, int*, cudaStream_t);
+
+// Backward pass: dy (vector layout) -> weight-gradient partials per layer
+// (stride net3_wgrad_blocks) and the data gradients d3, d2, d1 ([B][act_len][16]).
+void launch_net3_backward(const GridDesc& g, int B, const float* wq, NetActs acts, const float* dy, NetGrads gr,
+                          float* d4, int* err, cudaStream_t s) {
+  const long long total = (long long)B * g.cstride;
+  k_net3_dy_channels<<<grid_for(total, 4096), kBlock, 0, s>>>(g, B, dy, d4);
+  const long long nchunks = (g.cstride + kWChunk3 - 1) / kWChunk3;
+  const int bpi = (int)((nchunks + kWCpb3 - 1) / kWCpb3);
+  const dim3 wgrid((unsigned)(B * bpi));
+  const dim3 grid((unsigned)((g.px + 127) / 128), (unsigned)((g.py + kR3 - 1) / kR3), (unsigned)(g.pz * B));
+  const int sm4 = Conv3Smem<4>::kBytes;
+  k_net3_wgrad_tc<<<wgrid, kT3, kWSmem3, s>>>(g, 16, 3, kWCpb3, bpi, d4, acts.a3, gr.part[3], err);
+  k_net3_conv_tc<1, false, false, float><<<grid, kT3, sm4, s>>>(g, B, d4, wq + kNet3Off4, 16, 3, acts.a3, gr.d3,
+                                                                nullptr, nullptr, nullptr, err);
+  k_net3_wgrad_tc<<<wgrid, kT3, kWSmem3, s>>>(g, 16, 16, kWCpb3, bpi, gr.d3, acts.a2, gr.part[2], err);
+  k_net3_conv_tc<1, false, false, float><<<grid, kT3, sm4, s>>>(g, B, gr.d3, wq + kNet3Off3, 16, 16, acts.a2, gr.d2,
+                                                                nullptr, nullptr, nullptr, err);
+  k_net3_wgrad_tc<<<wgrid, kT3, kWSmem3, s>>>(g, 16, 16, kWCpb3, bpi, gr.d2, acts.a1, gr.part[1], err);
+  k_net3_conv_tc<1, false, false, float><<<grid, kT3, sm4, s>>>(g, B, gr.d2, wq + kNet3Off2, 16, 16, acts.a1, gr.d1,
+                                                                nullptr, nullptr, nullptr, err);
+  k_net3_wgrad_tc<<<wgrid, kT3, kWSmem3, s>>>(g, 3, 16, kWCpb3, bpi, gr.d1, acts.a0, gr.part[0], err);
+}
+
+}  // namespace mpcg

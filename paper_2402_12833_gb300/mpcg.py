@@ -117,6 +117,7 @@ _SIGS = {
     "mpcg_solve_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p),
                                      C.POINTER(C.c_void_p), C.c_double, C.c_int, C.POINTER(C.c_void_p)]),
     "mg_learned_num_params": (C.c_int, []),
+    "mg_learned_num_params_of": (C.c_int, [C.c_void_p]),
     "mg_learned_attach": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "mg_learned_detach": (C.c_int, [C.c_void_p]),
     "mg_attach_q1_kappa": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -281,9 +282,14 @@ def mg_learned_num_params() -> int:
     return load().mg_learned_num_params()
 
 
+def mg_learned_num_params_of(h: int) -> int:
+    """Parameter count of h's network (2D scalar or 3D vector problem)."""
+    return load().mg_learned_num_params_of(h)
+
+
 def mg_learned_attach(h: int, params) -> None:
     p = np.ascontiguousarray(params, dtype=np.float32) if isinstance(params, np.ndarray) else params
-    _check(load().mg_learned_attach(h, _ptr(p), mg_learned_num_params()))
+    _check(load().mg_learned_attach(h, _ptr(p), mg_learned_num_params_of(h)))
 
 
 def mg_learned_detach(h: int) -> None:
@@ -348,7 +354,7 @@ def mg_learned_grad(h: int, params: np.ndarray, rhat_dev, e_dev, nimg: int, acts
     """One forward + backward pass of the training kernels; returns
     (gradient as float64 array, mean loss)."""
     p = np.ascontiguousarray(params, dtype=np.float32)
-    grad = np.zeros(mg_learned_num_params())
+    grad = np.zeros(mg_learned_num_params_of(h))
     loss = C.c_double(0.0)
     _check(load().mg_learned_grad(h, p.ctypes.data, _ptr(rhat_dev), _ptr(e_dev), nimg, grad.ctypes.data,
                                   _ptr(acts_dev) if acts_dev is not None else None,
