@@ -816,6 +816,7 @@ def bench_elasticity(args):
         if oracle_proc is not None:
             oracle_proc.kill()
         return 0
+    learned = elasticity_learned(M, pb, prob, st, b, stream, args)
     cpu = None
     if oracle_proc is not None:
         o_out, o_err = oracle_proc.communicate(timeout=1800)
@@ -836,10 +837,66 @@ def bench_elasticity(args):
                                "Cholesky), 3x3 block Jacobi nu=2 w=2/3, MPCG m=5, rtol 1e-8",
                    "l2": "working set ~0.7 GB per solve > 129 MB L2 (no flush needed)"},
         "iterations": mx["iterations"], "true_rel_residual": mx["true_rel_residual"], "roofline": mx["roofline"],
-        "fp64": out["fp64"], "m1": m1, "kernel_ms_per_solve": mx["kernel_ms_per_solve"],
+        "fp64": out["fp64"], "m1": m1, "learned": learned, "kernel_ms_per_solve": mx["kernel_ms_per_solve"],
         "gpu_launches": mx["launches_per_step"] * args.steps, "clocks": clocks, "peaks": peaks,
         "cpu_baseline": cpu}))
     return 0
+
+
+def elasticity_learned(M, pb, prob, st, b, stream, args):
+    """The learned column on the elasticity workload: the 3x3x3 network is
+    trained on the GPU on (residual, error) pairs that the FP64 solver makes
+    for the same body under two other loads, (1, 0, 0) and (0, 1, 1) (the
+    first 24 iterates of each), then the mixed-precision solve of the
+    workload's load (0, 0, -1) runs with the trained column."""
+    import torch
+    t0 = time.perf_counter()
+    R, E = [], []
+    H = M.Hierarchy(st, 3, prob.nodes, prob.levels, dofs_per_node=3, faces=prob.faces, m=M_WINDOW)
+    Ax = torch.empty_like(b)
+    for force in ((1.0, 0.0, 0.0), (0.0, 1.0, 1.0)):
+        bf = torch.from_numpy(pb.elasticity_body_force(prob.nodes, force)).cuda()
+        xs = torch.zeros_like(bf)
+        H.solve(bf, xs, rtol=1e-13, maxit=MAXIT, histories=False)
+        for k in range(1, 25):
+            xk = torch.zeros_like(bf)
+            H.solve(bf, xk, rtol=1e-30, maxit=k, histories=False)
+            M.mg_apply_operator(H.h, prob.levels - 1, xk, Ax, 1)
+            r = bf - Ax
+            nr = torch.linalg.norm(r)
+            R.append((r / nr).float())
+            E.append(((xs - xk) / nr).float())
+    gen_s = time.perf_counter() - t0
+    params = pb.net_init_params(7, (3, 16, 16, 16, 3), taps=27)
+    epochs = 20
+    t0 = time.perf_counter()
+    loss = M.mg_learned_train([H.h], [0] * len(R), torch.stack(R).contiguous(), torch.stack(E).contiguous(), params,
+                              epochs=epochs, batch=8, lr=1e-3)
+    train_s = time.perf_counter() - t0
+    H.close()
+    H = M.Hierarchy(st, 3, prob.nodes, prob.levels, dofs_per_node=3, faces=prob.faces, m=M_WINDOW,
+                    precision=M.MPCG_MIXED, stream=stream.cuda_stream)
+    M.mg_learned_attach(H.h, params)
+    x = torch.zeros_like(b)
+    res = {}
+
+    def step():
+        x.zero_()
+        res["st"], res["k"], _, _ = H.solve(b, x, rtol=RTOL, maxit=MAXIT, histories=False)
+
+    ms = _timed(step, args.steps, args.warmup, stream)
+    M.mg_apply_operator(H.h, prob.levels - 1, x, Ax, 1)
+    out = {"value": prob.n / (ms * 1e-3), "ms_per_step": ms, "iterations": int(res["k"]), "status": int(res["st"]),
+           "true_rel_residual": float(torch.linalg.norm(b - Ax) / torch.linalg.norm(b)),
+           "training": {"pairs": len(R), "epochs": epochs, "loss_first": float(loss[0]),
+                        "loss_last": float(loss[-1]), "pair_generation_s": gen_s, "train_s": train_s}}
+    x.zero_()
+    _, _, _, trace = M.mpcg_solve_profiled(H.h, b, x, RTOL, MAXIT)
+    net = [t for c, t in trace if c == "net"]
+    if net:   # the four layer launches of one application, CUDA-event time
+        out["net_us_per_application"] = 1e3 * sum(net) / len(net)
+    H.close()
+    return out
 
 
 def bench_example1(args):
@@ -1245,25 +1302,35 @@ def bench_net_kernels(args):
     M.load()
     out = {}
     theta = pb.net_init_params(7)
-    for key, nodes, nimg in (("inference", 1025, 4), ("training_pass", args.nodes or 257, 8)):
-        prob = pb.diffusion_macro(2, nodes, 21)
-        H = M.Hierarchy(torch.from_numpy(prob.stencil).cuda(), 2, nodes, prob.levels)
+    theta3 = pb.net_init_params(7, (3, 16, 16, 16, 3), taps=27)
+    cases = (("inference", 2, 1025, 4), ("training_pass", 2, args.nodes or 257, 8),
+             ("inference3", 3, 65, 4), ("training_pass3", 3, args.nodes3 or 65, 8))
+    for key, dim, nodes, nimg in cases:
+        if dim == 2:
+            prob = pb.diffusion_macro(2, nodes, 21)
+            H = M.Hierarchy(torch.from_numpy(prob.stencil).cuda(), 2, nodes, prob.levels)
+            th = theta
+        else:   # the 3x3x3 network of the elasticity cantilever
+            prob = pb.elasticity_cantilever(nodes)
+            H = M.Hierarchy(torch.from_numpy(prob.stencil).cuda(), 3, nodes, prob.levels, dofs_per_node=3,
+                            faces=prob.faces)
+            th = theta3
         R = np.stack([pb.normal(40 + k, prob.n) for k in range(nimg)])
         R /= np.linalg.norm(R, axis=1, keepdims=True)
         Rd = torch.from_numpy(R.astype(np.float32)).cuda()
-        if key == "inference":
-            M.mg_learned_attach(H.h, theta)
+        if key.startswith("inference"):
+            M.mg_learned_attach(H.h, th)
             Y = torch.zeros_like(Rd)
             fn = lambda: M.mg_learned_forward(H.h, Rd, Y, nimg)
         else:
             Ed = torch.from_numpy(np.stack([pb.normal(50 + k, prob.n) for k in range(nimg)]).astype(np.float32)).cuda()
-            fn = lambda: M.mg_learned_grad(H.h, theta, Rd, Ed, nimg)
+            fn = lambda: M.mg_learned_grad(H.h, th, Rd, Ed, nimg)
         ms = _timed(fn, args.steps, args.warmup, torch.cuda.current_stream())
-        out[key] = {"grid": f"{nodes}^2", "images": nimg, "ms_per_call": ms, "us_per_image": 1e3 * ms / nimg}
+        out[key] = {"grid": f"{nodes}^{dim}", "images": nimg, "ms_per_call": ms, "us_per_image": 1e3 * ms / nimg}
         H.close()
     print(json.dumps({"metric": "learned-column kernel throughput", "workload": "net_kernels", "unit": "us/image",
-                      "inference": out["inference"], "training_pass": out["training_pass"],
-                      "note": "each call is synchronous through the C ABI (includes its host round trip)"}))
+                      **out, "note": "each call is synchronous through the C ABI (includes its host round trip "
+                                     "and, for the 3D calls, the allocation of the activations)"}))
     return 0
 
 
@@ -1292,6 +1359,8 @@ def main():
                     help="time the fixed launch-shape rules only (no autotuning)")
     ap.add_argument("--nodes", type=int, default=None,
                     help="with --only: nodes per side of the 3D Poisson grid (smaller cases for profiling)")
+    ap.add_argument("--nodes3", type=int, default=None,
+                    help="with --workload net_kernels: nodes per side of the 3D training-pass grid")
     args = ap.parse_args()
     if args.nodes is not None:
         if args.only is None and args.workload != "net_kernels":

@@ -712,7 +712,7 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
   if (h->net_on) {
     if (L.g.ncomp == 3)   // the 3D vector network, one launch per layer
       LAUNCH(h, K_NET, s,
-             launch_net3_forward<T>(L.g, 1, S.r, L.g.len, h->net_wq, S.state, h->net_acts, nullptr,
+             launch_net3_forward<T>(L.g, 1, S.r, L.g.len, h->net_wtc, S.state, h->net_acts, nullptr,
                                     S.Z + (size_t)(C - 1) * L.g.cp, h->net_err, s));
     else
       LAUNCH(h, K_NET, s,
@@ -2309,6 +2309,7 @@ mpcg_status net_prepare(mg_hierarchy* h) {
     CKS(h->net_mem.get(&h->net_acts.a2, alen * 16, s));
     CKS(h->net_mem.get(&h->net_acts.a3, alen * 16, s));
     CKS(h->net_mem.get(&h->net_err, 1, s));
+    CKS(h->net_mem.get(&h->net_wtc, (size_t)net3_pack_bytes(), s));
     net3_prepare_attributes();
     CK(cudaGetLastError());
     return MPCG_OK;
@@ -2384,7 +2385,7 @@ mpcg_status net_batch_alloc(bool net3, const GridDesc& g, int B, Alloc& mem, cud
   for (int l = 0; l < 4; ++l) get(&nb.gr.part[l], lsz[l] * nw);
   get(&nb.dots, 3 * 64 * B);
   get(&nb.coef, 2 * B);
-  if (!net3) get(&nb.wtc, (size_t)net_tc_weight_bytes());
+  get(&nb.wtc, (size_t)(net3 ? net3_pack_bytes() : net_tc_weight_bytes()));
   get(&nb.terr, 1);
   get(&nb.parts_dev, 4);
   if (st != MPCG_OK) return st;
@@ -2401,7 +2402,8 @@ mpcg_status net_batch_alloc(bool net3, const GridDesc& g, int B, Alloc& mem, cud
 void net_batch_step(NetBatch& nb, const GridDesc& g, int nimg, const float* c, const float* st32, const float* wq,
                     double* loss_sum, cudaStream_t s) {
   if (nb.net3) {
-    launch_net3_forward<float>(g, nimg, nb.rb, g.len, wq, nullptr, nb.a, nb.y, (float*)nullptr, nb.terr, s);
+    launch_net3_pack(wq, nb.wtc, s);
+    launch_net3_forward<float>(g, nimg, nb.rb, g.len, nb.wtc, nullptr, nb.a, nb.y, (float*)nullptr, nb.terr, s);
   } else {
     launch_net_pack_tc(wq, nb.wtc, s);
     launch_net_infer<float>(g, nimg, nb.rb, g.len, c, nb.wtc, nullptr, nb.y, (float*)nullptr, nb.terr, s, nullptr,
@@ -2409,7 +2411,7 @@ void net_batch_step(NetBatch& nb, const GridDesc& g, int nimg, const float* c, c
   }
   launch_spmm<float>(g, st32, nb.y, nb.ay, nimg, nullptr, nullptr, s);
   launch_net_loss_grad(g, nimg, nb.y, nb.ay, nb.eb, nb.aeb, nb.dots, nb.coef, loss_sum, nb.dy, s);
-  if (nb.net3) launch_net3_backward(g, nimg, wq, nb.a, nb.dy, nb.gr, nb.d4, nb.terr, s);
+  if (nb.net3) launch_net3_backward(g, nimg, nb.wtc, nb.a, nb.dy, nb.gr, nb.d4, nb.terr, s);
   else launch_net_backward(g, nimg, wq, nb.a, nb.dy, nb.gr, nb.terr, s);
 }
 
@@ -2456,7 +2458,8 @@ mpcg_status mg_learned_attach(mg_hierarchy* h, const float* params, int nparams)
   mpcg_status st = copy_floats(tmp, params, np, h->stream);
   if (st == MPCG_OK) {
     launch_round_bf16(tmp, h->net_wq, np, h->stream);
-    if (!net3_of(h)) launch_net_pack_tc(h->net_wq, h->net_wtc, h->stream);
+    if (net3_of(h)) launch_net3_pack(h->net_wq, h->net_wtc, h->stream);
+    else launch_net_pack_tc(h->net_wq, h->net_wtc, h->stream);
   }
   cudaStreamSynchronize(h->stream);
   cudaFree(tmp);
@@ -2560,7 +2563,7 @@ mpcg_status mg_learned_forward_acts(mg_hierarchy* h, const float* rhat_dev, floa
       (st = tmp.get(&y, (size_t)nimg * g.len, s)) == MPCG_OK) {
     launch_pack<float, float>(g, rhat_dev, g.n, r, nimg, s);
     if (net3_of(h)) {
-      launch_net3_forward<float>(g, nimg, r, g.len, h->net_wq, nullptr, a3, y, (float*)nullptr, h->net_err, s);
+      launch_net3_forward<float>(g, nimg, r, g.len, h->net_wtc, nullptr, a3, y, (float*)nullptr, h->net_err, s);
       if (acts_dev) launch_net3_acts_export(g, nimg, a3, acts_dev, s);
     } else {
       launch_net_infer<float>(g, nimg, r, g.len, h->net_c, h->net_wtc, nullptr, y, (float*)nullptr, h->net_err, s,

@@ -283,11 +283,15 @@ void net_train_tc_prepare_attributes();
 long long net3_act_len(const GridDesc& g);
 int net3_wgrad_blocks(const GridDesc& g, int B);
 void net3_prepare_attributes();
+// bfloat16 tap tiles of all layers, forward and data-gradient orientation
+// (net3_pack_bytes() bytes), from the bfloat16-rounded weights wq
+int net3_pack_bytes();
+void launch_net3_pack(const float* wq, unsigned char* wp, cudaStream_t s);
 template <typename T>
-void launch_net3_forward(const GridDesc& g, int B, const T* r, long long r_ld, const float* wq, const DevState* state,
-                         NetActs acts, float* y, T* z, int* err, cudaStream_t s);
-void launch_net3_backward(const GridDesc& g, int B, const float* wq, NetActs acts, const float* dy, NetGrads gr,
-                          float* d4, int* err, cudaStream_t s);
+void launch_net3_forward(const GridDesc& g, int B, const T* r, long long r_ld, const unsigned char* wp,
+                         const DevState* state, NetActs acts, float* y, T* z, int* err, cudaStream_t s);
+void launch_net3_backward(const GridDesc& g, int B, const unsigned char* wp, NetActs acts, const float* dy,
+                          NetGrads gr, float* d4, int* err, cudaStream_t s);
 // activations of the 3D network to the compact float layout
 // [4][B][unknown nodes][16], nodes x fastest
 void launch_net3_acts_export(const GridDesc& g, int B, NetActs acts, float* out, cudaStream_t s);

@@ -67,11 +67,34 @@ struct Conv3Smem {
 //         LAST: 3 FP32 outputs to a vector-layout array (y, or z = s y).
 // MODE 1: data gradient, dIn = mask(act_in > 0) sum W^T dOut(p - off), dOut
 //         FP32 [B][act_len][16] (zero beyond the layer's outputs).
+// 16-byte asynchronous copy global -> shared; src_bytes 0 zero-fills
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Packed weights: for layer l and mode m (0 forward, 1 data gradient) the 27
+// tap tiles of 16 x 16 bfloat16 in the K-major layout of the B operand, at
+// byte (2 l + m) * kW3Bytes.  Forward row n = co, column k = ci; gradient
+// row n = ci, column k = co; zero beyond the layer's channels.
+__global__ void k_net3_pack(const float* __restrict__ wq, unsigned char* __restrict__ wp) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 8 * 27 * 256) return;
+  const int lm = e / (27 * 256), l = lm >> 1, mode = lm & 1;
+  const int t = (e / 256) % 27, n = (e / 16) % 16, k = e % 16;
+  const int cin = l == 0 ? 3 : 16, cout = l == 3 ? 3 : 16;
+  const int off = l == 0 ? kNet3Off1 : l == 1 ? kNet3Off2 : l == 2 ? kNet3Off3 : kNet3Off4;
+  const int co = mode == 0 ? n : k, ci = mode == 0 ? k : n;
+  const float w = (co < cout && ci < cin) ? wq[off + (co * cin + ci) * 27 + t] : 0.f;
+  *reinterpret_cast<__nv_bfloat16*>(wp + lm * kW3Bytes + t * 512 + canon16(n, k)) = __float2bfloat16_rn(w);
+}
+
 template <int MODE, bool RELU, bool LAST, typename T>
 __global__ void __launch_bounds__(kT3, 1)
-    k_net3_conv_tc(GridDesc g, int B, const void* __restrict__ in, const float* __restrict__ W, int cin, int cout,
-                   const __nv_bfloat16* __restrict__ act_in, void* __restrict__ out, float* __restrict__ yv,
-                   T* __restrict__ zv, const DevState* state, int* err) {
+    k_net3_conv_tc(GridDesc g, int B, const void* __restrict__ in, const unsigned char* __restrict__ wp, int cin,
+                   int cout, const __nv_bfloat16* __restrict__ act_in, void* __restrict__ out,
+                   float* __restrict__ yv, T* __restrict__ zv, const DevState* state, int* err) {
   constexpr int NPL = MODE == 0 ? 2 : 4;
   using S = Conv3Smem<NPL>;
   if (state && state->done) return;
@@ -88,44 +111,45 @@ __global__ void __launch_bounds__(kT3, 1)
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), 64);
   if (tid < kR3) tc::mbar_init(tc::smem_u32(bar + tid));
   if (tid == 0) tc::mbar_init_fence();
-  // weight tiles: forward row n = co, column k = ci; gradient row n = ci, k = co
-  for (int e = tid; e < 27 * 256; e += kT3) {
-    const int t = e / 256, n = (e / 16) % 16, k = e % 16;
-    const int co = MODE == 0 ? n : k, ci = MODE == 0 ? k : n;
-    const float w = (co < cout && ci < cin) ? W[(co * cin + ci) * 27 + t] : 0.f;
-    *reinterpret_cast<__nv_bfloat16*>(smem + S::kWOff + t * 512 + canon16(n, k)) = __float2bfloat16_rn(w);
-  }
+  // the layer's 27 packed weight tiles (13,824 bytes)
+  for (int e = tid; e < kW3Bytes / 16; e += kT3)
+    cp_async16(smem + S::kWOff + 16 * e, wp + 16 * e, 16);
   // staged rows: slot (dz, sy) = dz * (R + 2) + sy holds node row (y0 - 1 + sy, z - 1 + dz)
   for (int e = tid; e < kRows3 * kXS3; e += kT3) {
     const int row = e / kXS3, xs = e % kXS3;
     const int dz = row / (kR3 + 2), sy = row % (kR3 + 2);
     const int x = x0 - 1 + xs, y = y0 - 1 + sy, zz = z - 1 + dz;
     const bool in_grid = inside3(g, x, y, zz);
-    const long long node = abase + x + px * y + pxy * zz;
+    const long long node = in_grid ? abase + x + px * y + pxy * zz : abase;
     const int off = (row * kXS3 + xs) * 16;
-    if (MODE == 0) {
-      uint4 p0 = make_uint4(0, 0, 0, 0), p1 = make_uint4(0, 0, 0, 0);
-      if (in_grid) {
-        const uint4* src = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(in) + node * 16);
-        p0 = src[0];
-        p1 = src[1];
-      }
-      *reinterpret_cast<uint4*>(smem + off) = p0;
-      *reinterpret_cast<uint4*>(smem + kPlane3 + off) = p1;
+    if (MODE == 0) {   // two 16-byte halves (channels 0-7, 8-15), zero-filled off the grid
+      const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(in) + node * 16;
+      cp_async16(smem + off, src, in_grid ? 16 : 0);
+      cp_async16(smem + kPlane3 + off, src + 8, in_grid ? 16 : 0);
     } else {
-      float hi[16], lo[16];
-      const float* src = static_cast<const float*>(in) + node * 16;
+      float v[16];
+      const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(in) + node * 16);
 #pragma unroll
-      for (int c = 0; c < 16; ++c) tc::split_bf16(in_grid ? src[c] : 0.f, hi[c], lo[c]);
+      for (int q = 0; q < 4; ++q) {
+        const float4 f = in_grid ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[4 * q] = f.x;
+        v[4 * q + 1] = f.y;
+        v[4 * q + 2] = f.z;
+        v[4 * q + 3] = f.w;
+      }
+      float hi[16], lo[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) tc::split_bf16(v[c], hi[c], lo[c]);
 #pragma unroll
       for (int pl = 0; pl < 4; ++pl) {
-        const float* v = pl < 2 ? hi + 8 * pl : lo + 8 * (pl - 2);
+        const float* w = pl < 2 ? hi + 8 * pl : lo + 8 * (pl - 2);
         *reinterpret_cast<uint4*>(smem + pl * kPlane3 + off) =
-            make_uint4(tc::pack_bf16x2(v[0], v[1]), tc::pack_bf16x2(v[2], v[3]), tc::pack_bf16x2(v[4], v[5]),
-                       tc::pack_bf16x2(v[6], v[7]));
+            make_uint4(tc::pack_bf16x2(w[0], w[1]), tc::pack_bf16x2(w[2], w[3]), tc::pack_bf16x2(w[4], w[5]),
+                       tc::pack_bf16x2(w[6], w[7]));
       }
     }
   }
+  cp_async_wait_all();
   tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
@@ -300,25 +324,25 @@ __global__ void __launch_bounds__(kT3, 1)
       tc::fence_after();
     }
     const long long t0 = (c0 + i) * kWChunk3;
-    // A: dOut^T, hi rows co, lo rows 16 + co (16 channels, zero beyond cout)
-    for (int item = tid; item < 2 * 8; item += kT3) {
-      const int cg = item / 8, pg = item % 8;
-#pragma unroll 1
-      for (int c = 0; c < 8; ++c) {
-        const int co = cg * 8 + c;
-        float hi[8], lo[8];
+    // A: dOut^T, hi rows co, lo rows 16 + co (16 channels, zero beyond
+    // cout); thread = (point of the chunk, channel half)
+    {
+      const int pt = tid & (kWChunk3 - 1), h = tid / kWChunk3;
+      const long long t = t0 + pt;
+      float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f), f1 = f0;
+      if (t < g.cstride) {
+        const float4* src = reinterpret_cast<const float4*>(dOut + (abase + t) * 16 + 8 * h);
+        f0 = src[0];
+        f1 = src[1];
+      }
+      const float d[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-          const long long t = t0 + pg * 8 + kk;
-          const float d = (t < g.cstride && co < cout) ? dOut[(abase + t) * 16 + co] : 0.f;
-          tc::split_bf16(d, hi[kk], lo[kk]);
-        }
-        *reinterpret_cast<uint4*>(A + toff64(co, pg * 8)) =
-            make_uint4(tc::pack_bf16x2(hi[0], hi[1]), tc::pack_bf16x2(hi[2], hi[3]), tc::pack_bf16x2(hi[4], hi[5]),
-                       tc::pack_bf16x2(hi[6], hi[7]));
-        *reinterpret_cast<uint4*>(A + toff64(16 + co, pg * 8)) =
-            make_uint4(tc::pack_bf16x2(lo[0], lo[1]), tc::pack_bf16x2(lo[2], lo[3]), tc::pack_bf16x2(lo[4], lo[5]),
-                       tc::pack_bf16x2(lo[6], lo[7]));
+      for (int c = 0; c < 8; ++c) {
+        const int co = 8 * h + c;
+        float hi, lo;
+        tc::split_bf16(co < cout ? d[c] : 0.f, hi, lo);
+        *reinterpret_cast<__nv_bfloat16*>(A + toff64(co, pt)) = __float2bfloat16_rn(hi);
+        *reinterpret_cast<__nv_bfloat16*>(A + toff64(16 + co, pt)) = __float2bfloat16_rn(lo);
       }
     }
     // B: im2col rows (tap, ci), 27 taps x 2 channel halves x 8 point groups
@@ -426,6 +450,12 @@ int net3_wgrad_blocks(const GridDesc& g, int B) {
   return B * (int)((nchunks + kWCpb3 - 1) / kWCpb3);
 }
 
+int net3_pack_bytes() { return 8 * kW3Bytes; }
+
+void launch_net3_pack(const float* wq, unsigned char* wp, cudaStream_t s) {
+  k_net3_pack<<<(8 * 27 * 256 + kBlock - 1) / kBlock, kBlock, 0, s>>>(wq, wp);
+}
+
 void net3_prepare_attributes() {
   cudaFuncSetAttribute(k_net3_conv_tc<0, true, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        Conv3Smem<2>::kBytes);
@@ -442,34 +472,36 @@ void net3_prepare_attributes() {
 
 // Forward pass of nimg images: r (type T, vector layout, image stride r_ld,
 // scaled by 1 / ||r|| from state when given) -> acts.a0..a3 (bfloat16) and
-// y (float, vector layout, may be null) and/or z = ||r|| y (T, may be null).
+// y (float, vector layout, may be null) and/or z = ||r|| y (T, may be null);
+// wp: the weights packed by launch_net3_pack.
 template <typename T>
-void launch_net3_forward(const GridDesc& g, int B, const T* r, long long r_ld, const float* wq, const DevState* state,
-                         NetActs acts, float* y, T* z, int* err, cudaStream_t s) {
+void launch_net3_forward(const GridDesc& g, int B, const T* r, long long r_ld, const unsigned char* wp,
+                         const DevState* state, NetActs acts, float* y, T* z, int* err, cudaStream_t s) {
   const long long total = (long long)B * g.cstride;
   k_net3_input<T><<<grid_for(total, 4096), kBlock, 0, s>>>(g, B, r, r_ld, state, acts.a0);
   const dim3 grid((unsigned)((g.px + 127) / 128), (unsigned)((g.py + kR3 - 1) / kR3), (unsigned)(g.pz * B));
   const int sm2 = Conv3Smem<2>::kBytes;
-  k_net3_conv_tc<0, true, false, float><<<grid, kT3, sm2, s>>>(g, B, acts.a0, wq + kNet3Off1, 3, 16, nullptr,
-                                                               acts.a1, nullptr, nullptr, state, err);
-  k_net3_conv_tc<0, true, false, float><<<grid, kT3, sm2, s>>>(g, B, acts.a1, wq + kNet3Off2, 16, 16, nullptr,
-                                                               acts.a2, nullptr, nullptr, state, err);
-  k_net3_conv_tc<0, true, false, float><<<grid, kT3, sm2, s>>>(g, B, acts.a2, wq + kNet3Off3, 16, 16, nullptr,
-                                                               acts.a3, nullptr, nullptr, state, err);
-  k_net3_conv_tc<0, false, true, T><<<grid, kT3, sm2, s>>>(g, B, acts.a3, wq + kNet3Off4, 16, 3, nullptr, nullptr,
-                                                           y, z, state, err);
+  const unsigned char* w[4] = {wp, wp + 2 * kW3Bytes, wp + 4 * kW3Bytes, wp + 6 * kW3Bytes};
+  k_net3_conv_tc<0, true, false, float><<<grid, kT3, sm2, s>>>(g, B, acts.a0, w[0], 3, 16, nullptr, acts.a1,
+                                                               nullptr, nullptr, state, err);
+  k_net3_conv_tc<0, true, false, float><<<grid, kT3, sm2, s>>>(g, B, acts.a1, w[1], 16, 16, nullptr, acts.a2,
+                                                               nullptr, nullptr, state, err);
+  k_net3_conv_tc<0, true, false, float><<<grid, kT3, sm2, s>>>(g, B, acts.a2, w[2], 16, 16, nullptr, acts.a3,
+                                                               nullptr, nullptr, state, err);
+  k_net3_conv_tc<0, false, true, T><<<grid, kT3, sm2, s>>>(g, B, acts.a3, w[3], 16, 3, nullptr, nullptr, y, z,
+                                                           state, err);
 }
-template void launch_net3_forward<float>(const GridDesc&, int, const float*, long long, const float*, const DevState*,
-                                         NetActs, float*, float*, int*, cudaStream_t);
-template void launch_net3_forward<double>(const GridDesc&, int, const double*, long long, const float*,
+template void launch_net3_forward<float>(const GridDesc&, int, const float*, long long, const unsigned char*,
+                                         const DevState*, NetActs, float*, float*, int*, cudaStream_t);
+template void launch_net3_forward<double>(const GridDesc&, int, const double*, long long, const unsigned char*,
                                           const DevState*, NetActs, float*, double*, int*, cudaStream_t);
-template void launch_net3_forward<dw>(const GridDesc&, int, const dw*, long long, const float*, const DevState*,
-                                      NetActs, float*, dw*, int*, cudaStream_t);
+template void launch_net3_forward<dw>(const GridDesc&, int, const dw*, long long, const unsigned char*,
+                                      const DevState*, NetActs, float*, dw*, int*, cudaStream_t);
 
 // Backward pass: dy (vector layout) -> weight-gradient partials per layer
 // (stride net3_wgrad_blocks) and the data gradients d3, d2, d1 ([B][act_len][16]).
-void launch_net3_backward(const GridDesc& g, int B, const float* wq, NetActs acts, const float* dy, NetGrads gr,
-                          float* d4, int* err, cudaStream_t s) {
+void launch_net3_backward(const GridDesc& g, int B, const unsigned char* wp, NetActs acts, const float* dy,
+                          NetGrads gr, float* d4, int* err, cudaStream_t s) {
   const long long total = (long long)B * g.cstride;
   k_net3_dy_channels<<<grid_for(total, 4096), kBlock, 0, s>>>(g, B, dy, d4);
   const long long nchunks = (g.cstride + kWChunk3 - 1) / kWChunk3;
@@ -477,14 +509,15 @@ void launch_net3_backward(const GridDesc& g, int B, const float* wq, NetActs act
   const dim3 wgrid((unsigned)(B * bpi));
   const dim3 grid((unsigned)((g.px + 127) / 128), (unsigned)((g.py + kR3 - 1) / kR3), (unsigned)(g.pz * B));
   const int sm4 = Conv3Smem<4>::kBytes;
+  const unsigned char* wg[4] = {wp + kW3Bytes, wp + 3 * kW3Bytes, wp + 5 * kW3Bytes, wp + 7 * kW3Bytes};
   k_net3_wgrad_tc<<<wgrid, kT3, kWSmem3, s>>>(g, 16, 3, kWCpb3, bpi, d4, acts.a3, gr.part[3], err);
-  k_net3_conv_tc<1, false, false, float><<<grid, kT3, sm4, s>>>(g, B, d4, wq + kNet3Off4, 16, 3, acts.a3, gr.d3,
-                                                                nullptr, nullptr, nullptr, err);
+  k_net3_conv_tc<1, false, false, float><<<grid, kT3, sm4, s>>>(g, B, d4, wg[3], 16, 3, acts.a3, gr.d3, nullptr,
+                                                                nullptr, nullptr, err);
   k_net3_wgrad_tc<<<wgrid, kT3, kWSmem3, s>>>(g, 16, 16, kWCpb3, bpi, gr.d3, acts.a2, gr.part[2], err);
-  k_net3_conv_tc<1, false, false, float><<<grid, kT3, sm4, s>>>(g, B, gr.d3, wq + kNet3Off3, 16, 16, acts.a2, gr.d2,
+  k_net3_conv_tc<1, false, false, float><<<grid, kT3, sm4, s>>>(g, B, gr.d3, wg[2], 16, 16, acts.a2, gr.d2,
                                                                 nullptr, nullptr, nullptr, err);
   k_net3_wgrad_tc<<<wgrid, kT3, kWSmem3, s>>>(g, 16, 16, kWCpb3, bpi, gr.d2, acts.a1, gr.part[1], err);
-  k_net3_conv_tc<1, false, false, float><<<grid, kT3, sm4, s>>>(g, B, gr.d2, wq + kNet3Off2, 16, 16, acts.a1, gr.d1,
+  k_net3_conv_tc<1, false, false, float><<<grid, kT3, sm4, s>>>(g, B, gr.d2, wg[1], 16, 16, acts.a1, gr.d1,
                                                                 nullptr, nullptr, nullptr, err);
   k_net3_wgrad_tc<<<wgrid, kT3, kWSmem3, s>>>(g, 3, 16, kWCpb3, bpi, gr.d1, acts.a0, gr.part[0], err);
 }
