@@ -695,6 +695,34 @@ def bench_batched(args):
         dist.destroy_process_group()
     if rank != 0:
         return 0
+    # roofline of the dominant kernel class on one problem of the largest side
+    # solved alone: a batched launch skips its converged problems, so it has
+    # no fixed byte count
+    big = max(by)
+    p0 = pb.batch_problem(by[big][0], big)
+    H1 = M.Hierarchy(torch.from_numpy(p0.stencil).cuda(), 2, big, p0.levels, m=M_WINDOW, precision=M.MPCG_MIXED)
+    ns1 = [M.mg_level_size(H1.h, j) for j in range(p0.levels)]
+    b1 = torch.from_numpy(p0.b).cuda()
+    x1 = torch.zeros_like(b1)
+    _, _, _, trace = M.mpcg_solve_profiled(H1.h, b1, x1, RTOL, 20000)
+    _, rl, _, tot1 = roofline(trace, ns1, p0.levels, M_WINDOW, 4, load_peaks(), FP64_PEAK_TFLOPS, S=9)
+    if rl is not None:
+        rl["workload"] = f"problem {by[big][0]} ({big}^2 nodes) of the batch solved alone"
+    H1.close()
+    cpu = None
+    if not args.no_cpu_baseline:   # after the GPU legs, one core: the oracle on one problem of each side <= 257
+        sample = [(by[sd][0], sd) for sd in sorted(by) if sd <= 257]
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        code = BATCH_ORACLE.format(root=ROOT, sample=sample, m=M_WINDOW, rtol=RTOL)
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+        if r.returncode == 0:
+            o = json.loads(r.stdout.strip().splitlines()[-1])
+            cpu = {"value": o["n"] / o["solve_s"], "unit": "DOFs/s", "cores": 1, "kind": "oracle",
+                   "sample": f"FP64 oracle solves of problems {[i for i, _ in sample]} (sides "
+                             f"{[sd for _, sd in sample]}, {o['iters']} iterations, {o['solve_s']:.1f} s, setup "
+                             f"excluded); DOFs of the sample / its solve time"}
+        else:
+            cpu = {"value": None, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
     print(json.dumps({
         "metric": METRIC, "workload": "batched", "value": ns_all / (ms * 1e-3), "unit": "DOFs/s", "n_gpus": world,
         "scaling": "strong", "steps": args.steps, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32+f64",
@@ -704,10 +732,30 @@ def bench_batched(args):
                    "problems_per_side_rank0": {str(k): len(v) for k, v in sorted(by.items())},
                    "total_dofs": int(ns_all)},
         "max_iterations_per_side": {str(k): int(i.max()) for k, i in zip(sorted(by), its)},
-        "gpu_launches_per_step": launches,
+        "gpu_launches_per_step": launches, "one_graph_launch": True, "roofline": rl,
+        "kernel_ms_per_solve_of_roofline_problem": {c: round(v, 4) for c, v in tot1.items()},
+        "cpu_baseline": cpu,
         "matrix_free": {"value": ns_all / (ms_mf * 1e-3), "ms_per_step": ms_mf,
                         "max_iterations_per_side": {str(k): int(i.max()) for k, i in zip(sorted(by), its_mf)}}}))
     return 0
+
+
+BATCH_ORACLE = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from paper_2402_12833_gb300 import problems as pb
+from oracle import mg as omg, mpcg as ompcg
+n, t, its = 0, 0.0, []
+for idx, nodes in {sample!r}:
+    p = pb.batch_problem(idx, nodes)
+    H = omg.Hierarchy(2, p.n1, p.stencil, p.levels)
+    t0 = time.perf_counter()
+    res = ompcg.mpcg(H.A[-1], p.b, H.mg_columns, m={m}, rtol={rtol}, maxit=20000)
+    t += time.perf_counter() - t0
+    n += p.n
+    its.append(res.iters)
+print(json.dumps({{"n": n, "solve_s": t, "iters": its}}))
+"""
 
 
 ELAST_ORACLE = r"""

@@ -318,11 +318,29 @@ void mg_amg_host_destroy(mg_amg_host* a);
 /*
  * Problems of uneven size: one batched hierarchy per grid size (nclass of
  * them, preferably each with its own stream in its options), solved
- * concurrently.  b[c], x[c], iters[c] are the arguments of mpcg_solve for
- * class c (iters may be NULL).  Returns the worst status of all problems.
+ * concurrently: as one graph launch (mpcg_solve_batched_graph) when every
+ * class is a mixed-precision hierarchy with graphs enabled, else from one
+ * host thread per class.  b[c], x[c], iters[c] are the arguments of
+ * mpcg_solve for class c (iters may be NULL).  Returns the worst status of
+ * all problems.
  */
 mpcg_status mpcg_solve_batched(mg_hierarchy* const* hs, int nclass, const double* const* b, double* const* x,
                                double rtol, int maxit, int* const* iters);
+/*
+ * mpcg_solve_batched as ONE CUDA graph launch: every class's whole
+ * mixed-precision solve (refinement loop and inner MPCG loop as conditional
+ * while nodes, no host round trip) is a root branch of one graph, and the GPU
+ * runs the branches concurrently; inputs are packed and results unpacked on
+ * hs[0]'s stream around the launch.  The graph is built on the first call and
+ * reused while the classes, their graphs, rtol and maxit are unchanged (at
+ * most 8 such graphs are cached; destroying a hierarchy drops those holding
+ * it).  mpcg_solve_batched takes this path by itself when it applies.
+ * Errors: MPCG_ERR_ARG unless every class is a distinct MPCG_MIXED hierarchy
+ * with graphs enabled (use_graph) on one device; MPCG_ERR_CUDA if the graph
+ * cannot be built; per class as mpcg_solve (the worst status is returned).
+ */
+mpcg_status mpcg_solve_batched_graph(mg_hierarchy* const* hs, int nclass, const double* const* b,
+                                     double* const* x, double rtol, int maxit, int* const* iters);
 
 /* Number of grids and of search columns (grids + appended columns). */
 int mg_num_levels(const mg_hierarchy* h);

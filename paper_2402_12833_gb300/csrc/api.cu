@@ -10,6 +10,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -224,7 +226,15 @@ struct Profiler {
     (h)->prof.end((s));               \
   } while (0)
 
+// identity of a hierarchy for caches that outlive a call (never reused)
+static long long next_hierarchy_uid() {
+  static std::atomic<long long> n{0};
+  return ++n;
+}
+
 struct mg_hierarchy {
+  long long uid = next_hierarchy_uid();
+  long long graph_gen = 0;     // bumped whenever the mixed-precision graph is dropped
   int device = 0;
   int dim = 2, levels = 1;
   int nodes = 0;               // fine-grid nodes per side, boundary included
@@ -278,6 +288,43 @@ struct mg_hierarchy {
 };
 
 namespace {
+
+// Graphs that hold the mixed-precision solves of several hierarchies (the
+// size classes of a batch of uneven problems, mpcg_solve_batched_graph),
+// keyed by the classes' identities, graph generations and history
+// capacities, the tolerance and the iteration limit.
+struct ClassGraph {
+  std::vector<long long> uid, gen;
+  std::vector<int> hist;
+  double rtol = 0.0;
+  int maxit = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_class_graph_mu;
+std::vector<ClassGraph> g_class_graphs;
+constexpr size_t kMaxClassGraphs = 8;
+
+void destroy_class_graph(ClassGraph& e) {
+  if (e.exec) cudaGraphExecDestroy(e.exec);
+  if (e.graph) cudaGraphDestroy(e.graph);
+  e.exec = nullptr;
+  e.graph = nullptr;
+}
+
+// Drop every cached class graph that contains hierarchy `uid`.
+void purge_class_graphs(long long uid) {
+  std::lock_guard<std::mutex> lk(g_class_graph_mu);
+  for (size_t i = 0; i < g_class_graphs.size();) {
+    auto& u = g_class_graphs[i].uid;
+    if (std::find(u.begin(), u.end(), uid) != u.end()) {
+      destroy_class_graph(g_class_graphs[i]);
+      g_class_graphs.erase(g_class_graphs.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
 
 template <typename T>
 const T* st_of(const Level& L);
@@ -1055,6 +1102,7 @@ void mg_hierarchy_destroy(mg_hierarchy* h) {
   if (!h) return;
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
+  purge_class_graphs(h->uid);
   if (h->mexec) cudaGraphExecDestroy(h->mexec);
   if (h->mgraph) cudaGraphDestroy(h->mgraph);
   h->s64.release();
@@ -1629,6 +1677,7 @@ static void drop_mixed_graph(mg_hierarchy* h) {
   h->mgraph = nullptr;
   h->mg_rtol = -1.0;
   h->mg_maxit = h->mg_hist = -1;
+  ++h->graph_gen;
 }
 
 static cudaGraphNode_t add_while(cudaStream_t cs, cudaGraph_t g, cudaGraphConditionalHandle c, cudaGraph_t* body,
@@ -1650,22 +1699,22 @@ static cudaGraphNode_t add_while(cudaStream_t cs, cudaGraph_t g, cudaGraphCondit
   return node;
 }
 
-static bool build_mixed_graph(mg_hierarchy* h, double rtol, int maxit) {
-  drop_mixed_graph(h);
+// Capture h's whole mixed-precision solve (init, the refinement while node
+// and its body with the inner while node) into `graph` as a new root branch.
+// Several hierarchies captured into one graph run concurrently in one launch.
+static bool capture_mixed(mg_hierarchy* h, cudaGraph_t graph, double rtol, int maxit) {
   Solver<float>& S = h->s32;
   const int J = h->levels - 1;
   const Level& L = h->lev[J];
   const GridDesc& gf = L.g;
   const int nb = h->nb;
   cudaStream_t cs = h->cap_stream;
-  cudaGraph_t graph = nullptr, obody = nullptr, ibody = nullptr;
+  cudaGraph_t obody = nullptr, ibody = nullptr;
   cudaGraphConditionalHandle c_out, c_in;
-  bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
-  ok = ok && cudaGraphConditionalHandleCreate(&c_out, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  bool ok = cudaGraphConditionalHandleCreate(&c_out, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
   ok = ok && cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
                  cudaSuccess;
   if (!ok) {
-    if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
     return false;
   }
@@ -1713,10 +1762,19 @@ static bool build_mixed_graph(mg_hierarchy* h, double rtol, int maxit) {
     ok = (cudaStreamEndCapture(cs, &tmp) == cudaSuccess) && ok;
   }
   h->prof.target = nullptr;
+  if (!ok) cudaGetLastError();
+  return ok;
+}
+
+static bool build_mixed_graph(mg_hierarchy* h, double rtol, int maxit) {
+  drop_mixed_graph(h);
+  cudaGraph_t graph = nullptr;
+  bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
+  ok = ok && capture_mixed(h, graph, rtol, maxit);
   cudaGraphExec_t exec = nullptr;
   ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
   if (!ok) {
-    cudaGraphDestroy(graph);
+    if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
     return false;
   }
@@ -1724,7 +1782,7 @@ static bool build_mixed_graph(mg_hierarchy* h, double rtol, int maxit) {
   h->mexec = exec;
   h->mg_rtol = rtol;
   h->mg_maxit = maxit;
-  h->mg_hist = S.hist_cap;
+  h->mg_hist = h->s32.hist_cap;
   return true;
 }
 
@@ -1782,6 +1840,179 @@ static mpcg_status solve_mixed_graph(mg_hierarchy* h, const double* b, double* x
     }
   }
   return result;
+}
+
+// Whether mpcg_solve_batched_graph takes these classes: mixed precision,
+// graphs enabled, one device, no hierarchy twice.
+static bool classes_graph_eligible(mg_hierarchy* const* hs, int nclass) {
+  if (!hs || nclass < 1) return false;
+  for (int c = 0; c < nclass; ++c) {
+    const mg_hierarchy* h = hs[c];
+    if (!h || h->opt.precision != MPCG_MIXED || !h->opt.use_graph || h->force_direct || h->device != hs[0]->device)
+      return false;
+    for (int d = 0; d < c; ++d)
+      if (hs[d] == h) return false;
+  }
+  return true;
+}
+
+mpcg_status mpcg_solve_batched_graph(mg_hierarchy* const* hs, int nclass, const double* const* b,
+                                     double* const* x, double rtol, int maxit, int* const* iters) {
+  g_err.clear();
+  if (!hs || nclass < 1 || !b || !x) {
+    set_err("mpcg_solve_batched_graph: bad arguments");
+    return MPCG_ERR_ARG;
+  }
+  if (maxit < 0 || !(rtol >= 0.0)) {
+    set_err("maxit must be >= 0 and rtol >= 0");
+    return MPCG_ERR_ARG;
+  }
+  for (int c = 0; c < nclass; ++c) {
+    CKS(check_h(hs[c]));
+    if (!b[c] || !x[c]) {
+      set_err("b[%d] and x[%d] must not be NULL", c, c);
+      return MPCG_ERR_ARG;
+    }
+  }
+  if (!classes_graph_eligible(hs, nclass)) {
+    set_err("mpcg_solve_batched_graph: every class must be a distinct mixed-precision hierarchy with graphs "
+            "enabled, all on one device");
+    return MPCG_ERR_ARG;
+  }
+  CK(cudaSetDevice(hs[0]->device));
+  cudaStream_t s = hs[0]->stream;
+  for (int c = 0; c < nclass; ++c) {
+    mg_hierarchy* h = hs[c];
+    CKS(build_f32(h));
+    CKS(build_solver<float>(h, h->s32));
+    CKS(ensure_hist(h, h->s32, maxit));
+    if (h->stream != s) CK(cudaStreamSynchronize(h->stream));   // earlier work on the class's own stream
+  }
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_class_graph_mu);
+    for (auto& e : g_class_graphs) {
+      bool same = e.rtol == rtol && e.maxit == maxit && (int)e.uid.size() == nclass;
+      for (int c = 0; same && c < nclass; ++c)
+        same = e.uid[c] == hs[c]->uid && e.gen[c] == hs[c]->graph_gen && e.hist[c] == hs[c]->s32.hist_cap;
+      if (same) {
+        exec = e.exec;
+        break;
+      }
+    }
+  }
+  if (!exec) {
+    ClassGraph e;
+    e.rtol = rtol;
+    e.maxit = maxit;
+    bool ok = cudaGraphCreate(&e.graph, 0) == cudaSuccess;
+    for (int c = 0; c < nclass && ok; ++c) ok = capture_mixed(hs[c], e.graph, rtol, maxit);
+    ok = ok && cudaGraphInstantiate(&e.exec, e.graph, 0) == cudaSuccess;
+    if (!ok) {
+      destroy_class_graph(e);
+      cudaGetLastError();
+      set_err("mpcg_solve_batched_graph: the graph of the classes could not be built");
+      return MPCG_ERR_CUDA;
+    }
+    for (int c = 0; c < nclass; ++c) {
+      e.uid.push_back(hs[c]->uid);
+      e.gen.push_back(hs[c]->graph_gen);
+      e.hist.push_back(hs[c]->s32.hist_cap);
+    }
+    exec = e.exec;
+    std::lock_guard<std::mutex> lk(g_class_graph_mu);
+    if (g_class_graphs.size() >= kMaxClassGraphs) {
+      destroy_class_graph(g_class_graphs.front());
+      g_class_graphs.erase(g_class_graphs.begin());
+    }
+    g_class_graphs.push_back(e);
+  }
+  // inputs: pack every class's b and x0 (host arrays staged as in mpcg_solve)
+  std::vector<const double*> bd(nclass);
+  std::vector<double*> xd(nclass);
+  std::vector<char> xhost(nclass, 0);
+  for (int c = 0; c < nclass; ++c) {
+    mg_hierarchy* h = hs[c];
+    const GridDesc& gf = h->lev[h->levels - 1].g;
+    const size_t ntot = (size_t)gf.n * h->nb;
+    bd[c] = b[c];
+    xd[c] = x[c];
+    const bool bdev = is_device_pointer(b[c]), xdev = is_device_pointer(x[c]);
+    if (!bdev || !xdev) {
+      if (!h->stage) CKS(h->mem.get(&h->stage, 2 * ntot, s));
+      if (!bdev) {
+        CK(cudaMemcpyAsync(h->stage, b[c], sizeof(double) * ntot, cudaMemcpyHostToDevice, s));
+        bd[c] = h->stage;
+      }
+      if (!xdev) {
+        CK(cudaMemcpyAsync(h->stage + ntot, x[c], sizeof(double) * ntot, cudaMemcpyHostToDevice, s));
+        xd[c] = h->stage + ntot;
+        xhost[c] = 1;
+      }
+    }
+    h->prof.reset();
+    for (int p = 0; p < h->nb; ++p) {
+      LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, bd[c] + (size_t)p * gf.n, gf.n,
+                                                        h->b64 + (size_t)p * gf.len, 1, s));
+      CK(cudaMemsetAsync(h->xnz + p, 0, sizeof(int), s));
+      LAUNCH(h, K_PACK, s, launch_pack_flag(gf, xd[c] + (size_t)p * gf.n, h->x64 + (size_t)p * gf.len, h->xnz + p, s));
+    }
+  }
+  CK(cudaGraphLaunch(exec, s));
+  std::vector<std::vector<int>> mix(nclass);
+  std::vector<int> steps(nclass, 0), nerr(nclass, 0);
+  for (int c = 0; c < nclass; ++c) {
+    mg_hierarchy* h = hs[c];
+    const GridDesc& gf = h->lev[h->levels - 1].g;
+    for (int p = 0; p < h->nb; ++p)
+      LAUNCH(h, K_PACK, s, launch_unpack<double, double>(gf, h->x64 + (size_t)p * gf.len, xd[c] + (size_t)p * gf.n,
+                                                          gf.n, 1, s));
+    mix[c].resize(3 * (size_t)h->nb);
+    CK(cudaMemcpyAsync(mix[c].data(), h->mix, sizeof(int) * 3 * h->nb, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&steps[c], h->outer, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (h->net_on && h->net_err) CK(cudaMemcpyAsync(&nerr[c], h->net_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  mpcg_status worst = MPCG_OK;
+  std::string msg;
+  for (int c = 0; c < nclass; ++c) {
+    mg_hierarchy* h = hs[c];
+    const GridDesc& gf = h->lev[h->levels - 1].g;
+    long long kmax = 0;
+    for (int p = 0; p < h->nb; ++p) kmax = std::max<long long>(kmax, mix[c][3 * p]);
+    h->prof.live += 1 + (long long)steps[c] * (h->mg_head + h->mg_iprol + h->mg_tail) + kmax * h->mg_ibody;
+    h->prof.flush();
+    h->last_launches = h->prof.live;
+    mpcg_status st = MPCG_OK;
+    std::string cmsg;
+    for (int p = 0; p < h->nb; ++p) {
+      if (iters && iters[c]) iters[c][p] = mix[c][3 * p];
+      const int status = mix[c][3 * p + 1];
+      if (status == 3) {
+        if (st != MPCG_ERR_BREAKDOWN) cmsg = "breakdown in the FP32 inner solve of problem " + std::to_string(p);
+        st = MPCG_ERR_BREAKDOWN;
+      } else if (status != 1 && st == MPCG_OK) {
+        st = MPCG_NOT_CONVERGED;
+      }
+    }
+    if (nerr[c]) {
+      st = MPCG_ERR_TIMEOUT;
+      cmsg = "learned column: a tensor-core wait timed out";
+    }
+    if (xhost[c] && (st >= 0 || st == MPCG_ERR_BREAKDOWN))
+      CK(cudaMemcpyAsync(x[c], xd[c], sizeof(double) * (size_t)gf.n * h->nb, cudaMemcpyDeviceToHost, s));
+    if (st < 0 && (worst >= 0 || st < worst)) {
+      worst = st;
+      msg = "class " + std::to_string(c) + ": " + cmsg;
+    } else if (st == MPCG_NOT_CONVERGED && worst == MPCG_OK) {
+      worst = st;
+      msg = "class " + std::to_string(c) + " did not converge";
+    }
+  }
+  CK(cudaStreamSynchronize(s));
+  if (worst != MPCG_OK) set_err("%s", msg.c_str());
+  return worst;
 }
 
 static mpcg_status solve_mixed(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, int* iters_out,
@@ -2785,3 +3016,7 @@ mpcg_status mg_learned_train(mg_hierarchy* const* hs, int nprob, const int* pair
 }
 
 }  // extern "C"
+
+namespace mpcg {
+bool batched_graph_eligible(mg_hierarchy* const* hs, int nclass) { return classes_graph_eligible(hs, nclass); }
+}  // namespace mpcg

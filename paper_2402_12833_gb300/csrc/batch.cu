@@ -2,10 +2,12 @@
 //
 // Problems of one grid size form one batched hierarchy (mg_hierarchy_setup_batched),
 // whose every kernel processes the whole batch at once (the problem index is
-// blockIdx.y) inside one graph launch with a device-side loop that runs while
-// any problem of the batch is unconverged.  The size classes are independent:
-// this entry point drives them from one host thread each, so that their graph
-// launches execute concurrently on their own streams.
+// blockIdx.y) with a device-side loop that runs while any problem of the
+// batch is unconverged.  The size classes are independent: mixed-precision
+// classes with graphs run as branches of one CUDA graph (one launch for the
+// whole batch, mpcg_solve_batched_graph in api.cu); otherwise this entry
+// point drives them from one host thread each, so that their launches execute
+// concurrently on their own streams.
 #include <string>
 #include <thread>
 #include <vector>
@@ -18,6 +20,10 @@ extern "C" mpcg_status mpcg_solve_batched(mg_hierarchy* const* hs, int nclass, c
     mpcg::set_error_message("mpcg_solve_batched: bad arguments");
     return MPCG_ERR_ARG;
   }
+  // mixed-precision classes with graphs: every class's solve is a branch of
+  // one CUDA graph, one launch for the whole batch
+  if (nclass > 1 && mpcg::batched_graph_eligible(hs, nclass))
+    return mpcg_solve_batched_graph(hs, nclass, b, x, rtol, maxit, iters);
   std::vector<mpcg_status> st(nclass, MPCG_OK);
   std::vector<std::string> err(nclass);
   std::vector<std::thread> th;

@@ -42,6 +42,9 @@ constexpr int kind_of<dw>() { return 2; }
 
 // Sets the calling thread's message returned by mpcg_last_error().
 void set_error_message(const char* msg);
+// mpcg_solve_batched_graph takes these classes (mixed precision, graphs on,
+// one device, each hierarchy once)
+bool batched_graph_eligible(mg_hierarchy* const* hs, int nclass);
 
 inline int grid_for(long long work, int cap) {
   long long b = (work + kBlock - 1) / kBlock;

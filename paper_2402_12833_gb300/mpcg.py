@@ -116,6 +116,8 @@ _SIGS = {
                                   C.c_void_p, C.c_void_p]),
     "mpcg_solve_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p),
                                      C.POINTER(C.c_void_p), C.c_double, C.c_int, C.POINTER(C.c_void_p)]),
+    "mpcg_solve_batched_graph": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p),
+                                           C.POINTER(C.c_void_p), C.c_double, C.c_int, C.POINTER(C.c_void_p)]),
     "mg_learned_num_params": (C.c_int, []),
     "mg_learned_num_params_of": (C.c_int, [C.c_void_p]),
     "mg_learned_attach": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
@@ -420,16 +422,19 @@ class BatchedHierarchy:
             pass
 
 
-def mpcg_solve_batched(classes, bs, xs, rtol=1e-8, maxit=500):
+def mpcg_solve_batched(classes, bs, xs, rtol=1e-8, maxit=500, one_graph=None):
     """Solve every BatchedHierarchy in ``classes`` concurrently; returns
-    (status, [iterations per class])."""
+    (status, [iterations per class]).  one_graph=True calls
+    mpcg_solve_batched_graph (one graph launch, mixed precision only);
+    None lets the library choose."""
     n = len(classes)
     hs = (C.c_void_p * n)(*[c.h for c in classes])
     bp = (C.c_void_p * n)(*[_ptr(b) for b in bs])
     xp = (C.c_void_p * n)(*[_ptr(x) for x in xs])
     its = [np.zeros(c.nprob, dtype=np.int32) for c in classes]
     ip = (C.c_void_p * n)(*[i.ctypes.data for i in its])
-    st = load().mpcg_solve_batched(hs, n, bp, xp, rtol, maxit, ip)
+    fn = load().mpcg_solve_batched_graph if one_graph else load().mpcg_solve_batched
+    st = fn(hs, n, bp, xp, rtol, maxit, ip)
     _check(st, allow=(MPCG_OK, MPCG_NOT_CONVERGED))
     return st, its
 

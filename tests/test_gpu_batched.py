@@ -98,3 +98,85 @@ def test_uneven_batch_in_concurrent_classes(M):
         for i, p in enumerate(ps):
             assert it[i] > 0
             assert _true_res(p, X[i]) <= 1e-8
+
+
+def _classes(M, sizes, precision, first=0):
+    classes, bs, probs = [], [], []
+    for nodes, cnt in sizes.items():
+        ps = [pb.batch_problem(first + len(probs) * 7 + i, nodes) for i in range(cnt)]
+        probs.append(ps)
+        strm = torch.cuda.Stream()
+        classes.append(M.BatchedHierarchy([_dev(p.stencil) for p in ps], 2, nodes, ps[0].levels,
+                                          precision=precision, stream=strm.cuda_stream))
+        bs.append(_dev(np.stack([p.b for p in ps])))
+    torch.cuda.synchronize()
+    return classes, bs, probs
+
+
+def test_one_graph_batch_equals_per_class_solves(M):
+    """mpcg_solve_batched_graph (every class's mixed-precision solve a branch
+    of one CUDA graph, one launch) gives bitwise the per-class solves'
+    results and iteration counts, on a rebuilt graph and on the cached one,
+    with device and with host arrays."""
+    sizes = {33: 3, 65: 2, 129: 1}
+    classes, bs, probs = _classes(M, sizes, M.MPCG_MIXED)
+    ref_x, ref_it = [], []
+    for c, b in zip(classes, bs):
+        x = torch.zeros_like(b)
+        st, it = c.solve(b, x, rtol=1e-8, maxit=4000)
+        assert st == M.MPCG_OK
+        ref_x.append(x.cpu().numpy())
+        ref_it.append(np.array(it))
+    for call in range(2):   # the second call reuses the cached graph
+        xs = [torch.zeros_like(b) for b in bs]
+        st, its = M.mpcg_solve_batched(classes, bs, xs, rtol=1e-8, maxit=4000, one_graph=True)
+        assert st == M.MPCG_OK
+        for x, it, rx, ri in zip(xs, its, ref_x, ref_it):
+            assert np.array_equal(it, ri), (call, it, ri)
+            assert np.array_equal(x.cpu().numpy(), rx), call
+    # host arrays (staged through each class's buffers)
+    bh = [b.cpu().numpy() for b in bs]
+    xh = [np.zeros_like(b) for b in bh]
+    st, its = M.mpcg_solve_batched(classes, bh, xh, rtol=1e-8, maxit=4000, one_graph=True)
+    assert st == M.MPCG_OK
+    for x, rx in zip(xh, ref_x):
+        assert np.array_equal(x, rx)
+    for ps, x in zip(probs, ref_x):
+        for i, p in enumerate(ps):
+            assert _true_res(p, x[i]) <= 1e-8
+
+
+def test_one_graph_batch_after_a_class_is_replaced(M):
+    """A destroyed class drops the cached graphs that hold it; a new class
+    in its place gets a new graph (results equal its own solve)."""
+    classes, bs, _ = _classes(M, {33: 2, 65: 1}, M.MPCG_MIXED, first=40)
+    xs = [torch.zeros_like(b) for b in bs]
+    M.mpcg_solve_batched(classes, bs, xs, rtol=1e-8, maxit=4000, one_graph=True)
+    classes[1].close()
+    new, nbs, _ = _classes(M, {65: 2}, M.MPCG_MIXED, first=60)
+    classes[1], bs[1] = new[0], nbs[0]
+    xs = [torch.zeros_like(b) for b in bs]
+    st, its = M.mpcg_solve_batched(classes, bs, xs, rtol=1e-8, maxit=4000, one_graph=True)
+    assert st == M.MPCG_OK
+    x1 = torch.zeros_like(bs[1])
+    st1, it1 = classes[1].solve(bs[1], x1, rtol=1e-8, maxit=4000)
+    assert np.array_equal(np.array(it1), its[1]) and torch.equal(x1, xs[1])
+
+
+def test_one_graph_batch_refuses_other_precisions(M):
+    """The one-graph entry takes mixed-precision classes only; the general
+    entry point runs an FP64 class among them from host threads."""
+    classes, bs, probs = _classes(M, {33: 2}, M.MPCG_MIXED, first=80)
+    c64, b64, p64 = _classes(M, {65: 1}, M.MPCG_FP64, first=90)
+    allc, allb = classes + c64, bs + b64
+    xs = [torch.zeros_like(b) for b in allb]
+    with pytest.raises(M.MpcgError):
+        M.mpcg_solve_batched(allc, allb, xs, rtol=1e-8, maxit=4000, one_graph=True)
+    with pytest.raises(M.MpcgError):   # a class twice
+        M.mpcg_solve_batched(classes + classes, bs + bs, [xs[0], xs[0]], rtol=1e-8, maxit=4000, one_graph=True)
+    st, its = M.mpcg_solve_batched(allc, allb, xs, rtol=1e-8, maxit=4000)
+    assert st == M.MPCG_OK
+    for ps, x in zip(probs + p64, xs):
+        X = x.cpu().numpy()
+        for i, p in enumerate(ps):
+            assert _true_res(p, X[i]) <= 1e-8
