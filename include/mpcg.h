@@ -502,6 +502,19 @@ mpcg_status mg_learned_train(mg_hierarchy* const* hs, int nprob, const int* pair
                              const float* rhat_dev, const float* e_dev, const mg_train_opts* opts,
                              float* params, double* loss_hist);
 
+/*
+ * Failure-path check of the learned column's tensor-core kernels (no
+ * counterpart in the paper).  Every such kernel waits on mbarriers for its
+ * MMAs with a bounded number of polls; a wait that runs out makes the kernel
+ * let its issued MMAs finish (bounded), free its tensor memory and set an
+ * error flag that the calling entry point returns as MPCG_ERR_TIMEOUT (the
+ * CUDA context stays usable).  This sets the polls of the first waits on the
+ * current device: 0 gives up at once (the failure path runs on every CTA),
+ * 4194304 is the default.  Graphs captured earlier read the new value too.
+ * Errors: MPCG_ERR_ARG (polls < 0), MPCG_ERR_CUDA.
+ */
+mpcg_status mg_set_tensor_wait_limit(long long polls);
+
 /* Release everything the hierarchy owns.  NULL is ignored. */
 void mg_hierarchy_destroy(mg_hierarchy* h);
 

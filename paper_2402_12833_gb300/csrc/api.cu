@@ -1951,6 +1951,7 @@ mpcg_status mpcg_solve_batched_graph(mg_hierarchy* const* hs, int nclass, const 
       }
     }
     h->prof.reset();
+    if (h->net_on && h->net_err) CK(cudaMemsetAsync(h->net_err, 0, sizeof(int), s));
     for (int p = 0; p < h->nb; ++p) {
       LAUNCH(h, K_PACK, s, launch_pack<double, double>(gf, bd[c] + (size_t)p * gf.n, gf.n,
                                                         h->b64 + (size_t)p * gf.len, 1, s));
@@ -2139,6 +2140,7 @@ mpcg_status mpcg_solve(mg_hierarchy* h, const double* b, double* x, double rtol,
     }
   }
   h->prof.reset();
+  if (h->net_on && h->net_err) CK(cudaMemsetAsync(h->net_err, 0, sizeof(int), s));
   mpcg_status st;
   if (h->opt.precision == MPCG_MIXED) {
     bool fallback = true;
@@ -2669,6 +2671,18 @@ int mg_learned_num_params(void) { return kNetParams; }
 
 int mg_learned_num_params_of(const mg_hierarchy* h) { return h ? net_params_of(h) : -1; }
 
+mpcg_status mg_set_tensor_wait_limit(long long polls) {
+  g_err.clear();
+  if (polls < 0) {
+    set_err("polls must be >= 0");
+    return MPCG_ERR_ARG;
+  }
+  CK(set_wait_first_infer(polls));
+  CK(set_wait_first_train(polls));
+  CK(set_wait_first_net3(polls));
+  return MPCG_OK;
+}
+
 mpcg_status mg_learned_attach(mg_hierarchy* h, const float* params, int nparams) {
   g_err.clear();
   CKS(check_h(h));
@@ -2792,6 +2806,7 @@ mpcg_status mg_learned_forward_acts(mg_hierarchy* h, const float* rhat_dev, floa
   }
   if (st == MPCG_OK && (st = tmp.get(&r, (size_t)nimg * g.len, s)) == MPCG_OK &&
       (st = tmp.get(&y, (size_t)nimg * g.len, s)) == MPCG_OK) {
+    cudaMemsetAsync(h->net_err, 0, sizeof(int), s);
     launch_pack<float, float>(g, rhat_dev, g.n, r, nimg, s);
     if (net3_of(h)) {
       launch_net3_forward<float>(g, nimg, r, g.len, h->net_wtc, nullptr, a3, y, (float*)nullptr, h->net_err, s);

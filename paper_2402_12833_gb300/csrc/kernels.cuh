@@ -286,6 +286,11 @@ void net_train_tc_prepare_attributes();
 long long net3_act_len(const GridDesc& g);
 int net3_wgrad_blocks(const GridDesc& g, int B);
 void net3_prepare_attributes();
+// polls of the first bounded wait of each learned-column tensor-core kernel
+// (2D inference, 2D training, 3D network) on the current device
+cudaError_t set_wait_first_infer(long long polls);
+cudaError_t set_wait_first_train(long long polls);
+cudaError_t set_wait_first_net3(long long polls);
 // bfloat16 tap tiles of all layers, forward and data-gradient orientation
 // (net3_pack_bytes() bytes), from the bfloat16-rounded weights wq
 int net3_pack_bytes();

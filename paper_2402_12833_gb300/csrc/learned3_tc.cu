@@ -41,6 +41,9 @@ constexpr int kRows3 = 3 * (kR3 + 2);          // staged rows (z - 1 .. z + 1) x
 constexpr int kPlane3 = kRows3 * kXS3 * 16;    // bytes of one 8-channel plane
 constexpr int kW3Bytes = 27 * 512;             // 27 weight tiles of 16 x 16 bf16
 constexpr long long kWait3 = 1LL << 22;
+// polls of a first wait before a kernel gives up (set_wait_first_net3; the
+// drain after a give-up always uses kWait3)
+__constant__ long long c_wait_first3 = kWait3;
 
 __device__ __forceinline__ int canon16(int row, int k) {
   return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(kT3, 1)
   const int x = x0 + tid;
   const double zs = (LAST && state) ? state->rnorm : 1.0;
   for (int r = 0; r < kR3; ++r) {
-    const bool ok = tc::mbar_wait(tc::smem_u32(bar + r), 0u, kWait3);
+    const bool ok = tc::mbar_wait(tc::smem_u32(bar + r), 0u, c_wait_first3);
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
@@ -313,12 +316,13 @@ __global__ void __launch_bounds__(kT3, 1)
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = tc::idesc_bf16(128, 144);
   bool failed = false;
+  int issued = 0;   // chunks whose MMAs were issued
   for (int i = 0; i < n && !failed; ++i) {
     const int st = i & 1;
     unsigned char* A = smem + st * kWStage3;
     unsigned char* Bt = A + kWA3;
     if (i >= 2) {
-      const bool ok = tc::mbar_wait(tc::smem_u32(bar + st), (uint32_t)(((i - 2) >> 1) & 1), kWait3);
+      const bool ok = tc::mbar_wait(tc::smem_u32(bar + st), (uint32_t)(((i - 2) >> 1) & 1), c_wait_first3);
       failed = __syncthreads_or(!ok);
       if (failed) break;
       tc::fence_after();
@@ -385,12 +389,15 @@ __global__ void __launch_bounds__(kT3, 1)
                        tc::sdesc(b_addr + part3 * 18 * 1024 + ks * 256, 128, 1024), idesc, (i > 0 || ks > 0) ? 1u : 0u);
       tc::mma_commit(tc::smem_u32(bar + st));
     }
+    issued = i + 1;
   }
+  // every MMA issued has completed once the last issued commit has
   bool drained = true;
-  if (n > 0) {
-    const int last = n - 1;
+  if (issued > 0) {
+    const int last = issued - 1;
     drained = tc::mbar_wait(tc::smem_u32(bar + (last & 1)), (uint32_t)((last >> 1) & 1), kWait3);
-    if (!drained && n > 1) tc::mbar_wait(tc::smem_u32(bar + ((last - 1) & 1)), (uint32_t)(((last - 1) >> 1) & 1), kWait3);
+    if (!drained && issued > 1)
+      tc::mbar_wait(tc::smem_u32(bar + ((last - 1) & 1)), (uint32_t)(((last - 1) >> 1) & 1), kWait3);
   }
   failed = __syncthreads_or(failed || !drained);
   tc::fence_after();
@@ -448,6 +455,10 @@ long long net3_act_len(const GridDesc& g) { return act_len3(g); }
 int net3_wgrad_blocks(const GridDesc& g, int B) {
   const long long nchunks = (g.cstride + kWChunk3 - 1) / kWChunk3;
   return B * (int)((nchunks + kWCpb3 - 1) / kWCpb3);
+}
+
+cudaError_t set_wait_first_net3(long long polls) {
+  return cudaMemcpyToSymbol(c_wait_first3, &polls, sizeof(polls));
 }
 
 int net3_pack_bytes() { return 8 * kW3Bytes; }

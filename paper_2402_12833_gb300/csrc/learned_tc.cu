@@ -107,9 +107,13 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait; false if the phase did not complete within the limit
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long i = 0; i < kWaitLimit; ++i)
+// polls of a row's first wait before the kernel gives up (set_wait_first_infer;
+// the drain after a give-up always uses kWaitLimit)
+__constant__ long long c_wait_first = kWaitLimit;
+
+// bounded wait; false if the phase did not complete within `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit = kWaitLimit) {
+  for (long long i = 0; i < limit; ++i)
     if (mbar_try(bar, parity)) return true;
   return false;
 }
@@ -269,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     pending = (1u << nrows) - 1u;
     for (int i = 0; i < nrows; ++i) {
-      const bool ok = mbar_wait(bar0 + 8 * i, (parity >> i) & 1u);
+      const bool ok = mbar_wait(bar0 + 8 * i, (parity >> i) & 1u, c_wait_first);
       if (!ok) {
         failed = true;
         break;
@@ -361,6 +365,10 @@ template void launch_net_infer<float>(const GridDesc&, int, const float*, long l
                                       const DevState*, float*, float*, int*, cudaStream_t, float*, NetActs);
 template void launch_net_infer<dw>(const GridDesc&, int, const dw*, long long, const float*, const void*,
                                    const DevState*, float*, dw*, int*, cudaStream_t, float*, NetActs);
+
+cudaError_t set_wait_first_infer(long long polls) {
+  return cudaMemcpyToSymbol(c_wait_first, &polls, sizeof(polls));
+}
 
 void net_infer_prepare_attributes() {
   cudaFuncSetAttribute(k_net_infer_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);

@@ -44,6 +44,9 @@ constexpr int kStage = kABytes + kBBytes;
 constexpr int kWSmem = 80 * 1024;
 constexpr int kWTmemCols = 256;
 constexpr long long kWaitLimitW = 1LL << 22;
+// polls of a first wait before a kernel gives up (set_wait_first_train; the
+// drain after a give-up always uses kWaitLimitW)
+__constant__ long long c_wait_first_w = kWaitLimitW;
 
 // byte offset of element (row, k) in a tile of 64 K columns: core matrices
 // of 8 rows x 8 k (128 B), K-adjacent (LBO = 128 B), row groups 1024 B apart
@@ -83,13 +86,14 @@ __global__ void __launch_bounds__(kWT, 2)
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = tc::idesc_bf16(kM, kN);
   bool failed = false;
+  int issued = 0;   // chunks whose MMAs were issued
 
   for (int i = 0; i < n && !failed; ++i) {
     const int st = i & 1;
     unsigned char* A = smem + st * kStage;
     unsigned char* Bt = A + kABytes;
     if (i >= 2) {   // the MMAs of chunk i - 2 read this stage
-      const bool ok = tc::mbar_wait(tc::smem_u32(bar + st), (uint32_t)(((i - 2) >> 1) & 1), kWaitLimitW);
+      const bool ok = tc::mbar_wait(tc::smem_u32(bar + st), (uint32_t)(((i - 2) >> 1) & 1), c_wait_first_w);
       failed = __syncthreads_or(!ok);
       if (failed) break;
       tc::fence_after();
@@ -168,13 +172,14 @@ __global__ void __launch_bounds__(kWT, 2)
                      (i > 0 || ks > 0) ? 1u : 0u);
       tc::mma_commit(tc::smem_u32(bar + st));
     }
+    issued = i + 1;
   }
-  // every MMA issued has completed once the last commit has
+  // every MMA issued has completed once the last issued commit has
   bool drained = true;
-  if (n > 0) {
-    const int last = n - 1;
+  if (issued > 0) {
+    const int last = issued - 1;
     drained = tc::mbar_wait(tc::smem_u32(bar + (last & 1)), (uint32_t)((last >> 1) & 1), kWaitLimitW);
-    if (!drained && n > 1)
+    if (!drained && issued > 1)
       tc::mbar_wait(tc::smem_u32(bar + ((last - 1) & 1)), (uint32_t)(((last - 1) >> 1) & 1), kWaitLimitW);
   }
   failed = __syncthreads_or(failed || !drained);
@@ -291,7 +296,7 @@ __global__ void __launch_bounds__(kWT, 2)
   bool failed = false;
   const int x = x0 + tid;
   for (int r = 0; r < kDR; ++r) {
-    const bool ok = tc::mbar_wait(tc::smem_u32(bar + r), 0u, kWaitLimitW);
+    const bool ok = tc::mbar_wait(tc::smem_u32(bar + r), 0u, c_wait_first_w);
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
@@ -347,6 +352,10 @@ int net_wgrad_tc_blocks(const GridDesc& g, int B) {
   const long long nchunks = (g.npts + kChunk - 1) / kChunk;
   const int cpb = net_wgrad_tc_chunks_per_block();
   return B * (int)((nchunks + cpb - 1) / cpb);
+}
+
+cudaError_t set_wait_first_train(long long polls) {
+  return cudaMemcpyToSymbol(c_wait_first_w, &polls, sizeof(polls));
 }
 
 void net_train_tc_prepare_attributes() {

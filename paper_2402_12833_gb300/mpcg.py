@@ -119,6 +119,7 @@ _SIGS = {
     "mpcg_solve_batched_graph": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p),
                                            C.POINTER(C.c_void_p), C.c_double, C.c_int, C.POINTER(C.c_void_p)]),
     "mg_learned_num_params": (C.c_int, []),
+    "mg_set_tensor_wait_limit": (C.c_int, [C.c_longlong]),
     "mg_learned_num_params_of": (C.c_int, [C.c_void_p]),
     "mg_learned_attach": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "mg_learned_detach": (C.c_int, [C.c_void_p]),
@@ -292,6 +293,15 @@ def mg_learned_num_params_of(h: int) -> int:
 def mg_learned_attach(h: int, params) -> None:
     p = np.ascontiguousarray(params, dtype=np.float32) if isinstance(params, np.ndarray) else params
     _check(load().mg_learned_attach(h, _ptr(p), mg_learned_num_params_of(h)))
+
+
+MG_TENSOR_WAIT_DEFAULT = 1 << 22
+
+
+def mg_set_tensor_wait_limit(polls: int) -> None:
+    """Polls of the first bounded waits of the tensor-core kernels (0: give
+    up at once, exercising the timeout path)."""
+    _check(load().mg_set_tensor_wait_limit(polls))
 
 
 def mg_learned_detach(h: int) -> None:

@@ -342,3 +342,44 @@ def test_training_lowers_loss_on_held_out_fields(M):
     assert sum(k for _, k in gains) <= 0.96 * sum(k for k, _ in gains), gains
     for before, after in held:
         assert after < before - 0.01, held
+
+
+def test_tensor_core_wait_timeout_is_reported_and_recovers(M):
+    """With zero polls for the first bounded wait, every tensor-core kernel
+    gives up: the forward pass, the training pass and a solve with the column
+    (its graph built before the change) return MPCG_ERR_TIMEOUT after the
+    kernels let their MMAs finish and free tensor memory; with the default
+    limit back, the same calls give the earlier results bitwise."""
+    prob = pb.diffusion_macro(2, 65, 21, rhs="normal", rhs_seed=4)
+    H = _hier(M, prob)
+    theta = OL.init_params(7)
+    M.mg_learned_attach(H.h, theta)
+    R = np.stack([pb.normal(3 + k, prob.n) for k in range(2)])
+    R = torch.from_numpy((R / np.linalg.norm(R, axis=1, keepdims=True)).astype(np.float32)).cuda()
+    E = torch.from_numpy(np.stack([pb.normal(9 + k, prob.n) for k in range(2)]).astype(np.float32)).cuda()
+    b = torch.from_numpy(prob.b).cuda()
+    Y0 = torch.zeros_like(R)
+    M.mg_learned_forward(H.h, R, Y0, 2)
+    g0, l0 = M.mg_learned_grad(H.h, theta, R, E, 2)
+    x0 = torch.zeros_like(b)
+    st0, k0, _, _ = H.solve(b, x0, rtol=1e-8, maxit=800, histories=False)
+    try:
+        M.mg_set_tensor_wait_limit(0)
+        for call in (lambda: M.mg_learned_forward(H.h, R, torch.zeros_like(R), 2),
+                     lambda: M.mg_learned_grad(H.h, theta, R, E, 2),
+                     lambda: H.solve(b, torch.zeros_like(b), rtol=1e-8, maxit=800, histories=False)):
+            with pytest.raises(M.MpcgError) as ei:
+                call()
+            assert ei.value.status == M.MPCG_ERR_TIMEOUT, ei.value
+    finally:
+        M.mg_set_tensor_wait_limit(M.MG_TENSOR_WAIT_DEFAULT)
+    Y1 = torch.zeros_like(R)
+    M.mg_learned_forward(H.h, R, Y1, 2)
+    assert torch.equal(Y0, Y1)
+    g1, l1 = M.mg_learned_grad(H.h, theta, R, E, 2)
+    assert np.array_equal(g0, g1) and abs(l1 - l0) <= 1e-15
+    x1 = torch.zeros_like(b)
+    st1, k1, _, _ = H.solve(b, x1, rtol=1e-8, maxit=800, histories=False)
+    assert st1 == st0 == M.MPCG_OK and k1 == k0 and torch.equal(x0, x1)
+    with pytest.raises(M.MpcgError):
+        M.mg_set_tensor_wait_limit(-1)

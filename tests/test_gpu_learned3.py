@@ -402,3 +402,35 @@ def test_training3_lowers_loss(M):
         st, its[name], _, _ = H.solve(b, x, rtol=1e-8, maxit=1000, histories=False)
         assert st == M.MPCG_OK
     print("iterations: plain", k0, "with the column", its)
+
+
+def test_tensor_core_wait_timeout3_is_reported_and_recovers(M):
+    """The 3D network's kernels with zero polls for their first wait (the
+    weight-gradient CTAs own 16 chunks, so they give up inside their chunk
+    pipeline and drain the MMAs they issued): MPCG_ERR_TIMEOUT from the
+    forward and the training pass; the default limit restores the earlier
+    results bitwise."""
+    prob = pb.elasticity_cantilever(9)
+    H = _hier(M, prob)
+    theta = OL.init_params3(7)
+    M.mg_learned_attach(H.h, theta)
+    R = np.stack([pb.normal(3 + k, prob.n) for k in range(2)])
+    R = torch.from_numpy((R / np.linalg.norm(R, axis=1, keepdims=True)).astype(np.float32)).cuda()
+    E = torch.from_numpy(np.stack([pb.normal(9 + k, prob.n) for k in range(2)]).astype(np.float32)).cuda()
+    Y0 = torch.zeros_like(R)
+    M.mg_learned_forward(H.h, R, Y0, 2)
+    g0, _ = M.mg_learned_grad(H.h, theta, R, E, 2)
+    try:
+        M.mg_set_tensor_wait_limit(0)
+        for call in (lambda: M.mg_learned_forward(H.h, R, torch.zeros_like(R), 2),
+                     lambda: M.mg_learned_grad(H.h, theta, R, E, 2)):
+            with pytest.raises(M.MpcgError) as ei:
+                call()
+            assert ei.value.status == M.MPCG_ERR_TIMEOUT, ei.value
+    finally:
+        M.mg_set_tensor_wait_limit(M.MG_TENSOR_WAIT_DEFAULT)
+    Y1 = torch.zeros_like(R)
+    M.mg_learned_forward(H.h, R, Y1, 2)
+    assert torch.equal(Y0, Y1)
+    g1, _ = M.mg_learned_grad(H.h, theta, R, E, 2)
+    assert np.array_equal(g0, g1)
