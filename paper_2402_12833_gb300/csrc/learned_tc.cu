@@ -56,13 +56,14 @@ constexpr int kEH = kTH + 2 * kHalo;   // 16
 constexpr int kXS = kEW + 2;           // stored row length: x = -1 and x = 128 are zero columns
 constexpr int kNPix = kEH * kXS;       // pixels of one activation buffer
 constexpr int kPlane = kNPix * 16;     // bytes of one channel plane
-constexpr int kThreads = 128;          // four warps: TMEM lanes 0..127
+constexpr int kThreads = 256;          // eight warps: TMEM lanes 0..127, twice (channel halves)
 constexpr int kMaxRows = kEH - 2;      // rows computed by the first layer
-constexpr int kTmemCols = 256;         // one 16-column accumulator per row of a layer
+constexpr int kMaxSlots = kEH;         // input rows (slots) of the first layer: one mbarrier each
+constexpr int kTmemCols = 256;         // one 16-column accumulator per output row of a layer (224 used)
 constexpr long long kWaitLimit = 1LL << 22;
 
-static_assert(kEW == kThreads, "one thread per tile column");
-static_assert(kEH == 16 && kThreads == 128, "halo-column zeroing maps 16 rows x 2 sides x 2 planes (x 2 passes)");
+static_assert(2 * kEW == kThreads, "two threads per tile column: one per channel half");
+static_assert(kEH == 16 && kThreads >= 64, "halo-column zeroing maps 16 rows x 2 sides x 2 planes");
 
 // shared memory map (bytes): one activation buffer, updated in place
 constexpr int kActBytes = 2 * kPlane;                // two planes
@@ -70,12 +71,20 @@ constexpr int kWBytes = 4 * 9 * 16 * 16 * 2;         // four layers x nine taps 
 constexpr int kOffAct0 = 0;
 constexpr int kOffW = kOffAct0 + kActBytes;
 constexpr int kOffBar = kOffW + kWBytes;
-constexpr int kSmemBytes = kOffBar + 8 * kMaxRows + 16;
+constexpr int kSmemBytes = kOffBar + 8 * kMaxSlots + 16;
 
 // instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits
-// 17-22, M >> 4 at bits 24-28
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+// 17-22, M = 128 (>> 4 at bits 24-28)
+__host__ __device__ constexpr uint32_t idesc_n(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+// TMEM column of output row i of a layer: descending in i, so that the
+// three y-taps of one input row land in three consecutive 16-column blocks
+constexpr int kColTop = kMaxRows - 1;
+__host__ __device__ constexpr int col_of(int i) { return 16 * (kColTop - i); }
+static_assert(col_of(0) + 16 <= kTmemCols && col_of(kMaxRows - 1) == 0, "output blocks fit the TMEM allocation");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -118,18 +127,30 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
   return false;
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
       :
-      : "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 8 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // 16 consecutive FP32 columns of this thread's TMEM lane
@@ -151,14 +172,29 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// the nine MMAs of one activation row into TMEM columns col0 .. col0 + 15;
-// `slot` is the storage slot of input row `row`
-__device__ __forceinline__ void issue_row(uint32_t tmem, int col0, uint32_t act_in, uint32_t w_layer, int slot) {
+// The MMAs that read input slot s of a layer with nrows output rows.  Output
+// row i takes input slots i, i + 1, i + 2 (y-taps ky = 0, 1, 2), so slot s
+// feeds the outputs s - ky for ky in [lo, hi] (those in range).  For each
+// x-tap kx the A operand is slot s shifted by kx and the B operand stacks the
+// tiles of ky = lo .. hi along N (weights packed ky-fastest): block j lands
+// in output s - lo - j, whose columns follow those of s - lo.  Output s's
+// first contribution (kx = 0, ky = 0) initialises its block; everything else
+// accumulates.  Four MMAs per slot instead of nine per output row.
+__device__ __forceinline__ void issue_slot(uint32_t tmem, uint32_t act_in, uint32_t w_layer, int s, int nrows) {
+  const int lo = s - (nrows - 1) > 0 ? s - (nrows - 1) : 0;
+  const int hi = s < 2 ? s : 2;
 #pragma unroll
-  for (int t = 0; t < 9; ++t) {
-    const int dy = t / 3 - 1, dx = t % 3 - 1;
-    const uint32_t a = act_in + (uint32_t)(((slot + dy) * kXS + dx + 1) * 16);
-    mma_bf16(tmem + (uint32_t)col0, sdesc(a, kPlane, 128), sdesc(w_layer + t * 512, 128, 256), t > 0 ? 1u : 0u);
+  for (int kx = 0; kx < 3; ++kx) {
+    const uint64_t adesc = sdesc(act_in + (uint32_t)((s * kXS + kx) * 16), kPlane, 128);
+    int l = lo;
+    if (kx == 0 && lo == 0) {
+      mma_bf16(tmem + (uint32_t)col_of(s), adesc, sdesc(w_layer + (uint32_t)(kx * 3) * 512, 128, 256), idesc_n(16),
+               0u);
+      l = 1;
+    }
+    if (l <= hi)
+      mma_bf16(tmem + (uint32_t)col_of(s - l), adesc, sdesc(w_layer + (uint32_t)(kx * 3 + l) * 512, 128, 256),
+               idesc_n(16 * (hi - l + 1)), 1u);
   }
 }
 
@@ -180,8 +216,10 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (state && state->done) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 8 * kMaxRows);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 8 * kMaxSlots);
+  // thread = (tile column x, channel half h): the two threads of a column
+  // share the staging rows and split every TMEM row read (8 channels each)
+  const int tid = threadIdx.x, warp = tid >> 5, x = tid & (kEW - 1), h = tid / kEW;
   const int b = blockIdx.z;
   const int gx0 = blockIdx.x * kTW - kHalo, gy0 = blockIdx.y * kTH - kHalo;
   const int n1 = g.n1;
@@ -193,7 +231,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid < kMaxRows) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + tid)) : "memory");
+  if (tid < kMaxSlots) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + tid)) : "memory");
   if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   // zero the x = -1 and x = 128 columns of every slot and plane (the only
   // activation entries that no layer writes but later layers read)
@@ -208,40 +246,42 @@ __global__ void __launch_bounds__(kThreads, 2)
   {
     const float sc = state ? (float)(state->rnorm > 0.0 ? 1.0 / state->rnorm : 0.0) : 1.f;
     const T* rb = r + (long long)b * r_ld;
-    const int gxx = gx0 + tid;
+    const int gxx = gx0 + x;
     const bool colok = gxx >= 0 && gxx < n1;
-    float v0[kEH], v1[kEH];
+    constexpr int kHalfRows = kEH / 2;   // rows h * 8 .. h * 8 + 7 of the tile
+    const int y0 = h * kHalfRows;
+    float v0[kHalfRows], v1[kHalfRows];
 #pragma unroll
-    for (int yy = 0; yy < kEH; ++yy) {
-      const int gy = gy0 + yy;
+    for (int k = 0; k < kHalfRows; ++k) {
+      const int gy = gy0 + y0 + k;
       const bool ok = colok && gy >= 0 && gy < n1;
       const long long idx = g.G + gxx + p * gy;
-      v0[yy] = ok ? (float)rb[idx] * sc : 0.f;
-      v1[yy] = ok ? c[idx] : 0.f;
+      v0[k] = ok ? (float)rb[idx] * sc : 0.f;
+      v1[k] = ok ? c[idx] : 0.f;
     }
 #pragma unroll
-    for (int yy = 0; yy < kEH; ++yy) {
-      const int off = (yy * kXS + tid + 1) * 16;
-      *reinterpret_cast<uint4*>(smem + kOffAct0 + off) = make_uint4(pack_bf16x2(v0[yy], v1[yy]), 0, 0, 0);
+    for (int k = 0; k < kHalfRows; ++k) {
+      const int off = ((y0 + k) * kXS + x + 1) * 16;
+      *reinterpret_cast<uint4*>(smem + kOffAct0 + off) = make_uint4(pack_bf16x2(v0[k], v1[k]), 0, 0, 0);
       *reinterpret_cast<uint4*>(smem + kOffAct0 + kPlane + off) = make_uint4(0, 0, 0, 0);
     }
-    if (keep.a0 && tid >= kHalo && tid < kHalo + kTW && gxx < n1) {
-      for (int yy = kHalo; yy < kHalo + kTH; ++yy) {
-        const int gy = gy0 + yy;
-        if (gy >= n1) break;
+    if (keep.a0 && x >= kHalo && x < kHalo + kTW && gxx < n1) {
+      for (int k = 0; k < kHalfRows; ++k) {
+        const int yy = y0 + k, gy = gy0 + yy;
+        if (yy < kHalo || yy >= kHalo + kTH || gy >= n1) continue;
         const long long o = (long long)b * g.len + g.G + gxx + p * gy;
-        keep.a0[o * 2 + 0] = __float2bfloat16_rn(v0[yy]);
-        keep.a0[o * 2 + 1] = __float2bfloat16_rn(v1[yy]);
+        keep.a0[o * 2 + 0] = __float2bfloat16_rn(v0[k]);
+        keep.a0[o * 2 + 1] = __float2bfloat16_rn(v1[k]);
       }
     }
-    if (acts && tid >= kHalo && tid < kHalo + kTW && gxx < n1) {
+    if (acts && x >= kHalo && x < kHalo + kTW && gxx < n1) {
       const long long nn = (long long)n1 * n1;
-      for (int yy = kHalo; yy < kHalo + kTH; ++yy) {
-        const int gy = gy0 + yy;
-        if (gy >= n1) break;
+      for (int k = 0; k < kHalfRows; ++k) {
+        const int yy = y0 + k, gy = gy0 + yy;
+        if (yy < kHalo || yy >= kHalo + kTH || gy >= n1) continue;
         float* o = acts + (((long long)b * nn) + (long long)gy * n1 + gxx) * 16;
-        o[0] = __bfloat162float(__float2bfloat16_rn(v0[yy]));
-        o[1] = __bfloat162float(__float2bfloat16_rn(v1[yy]));
+        o[0] = __bfloat162float(__float2bfloat16_rn(v0[k]));
+        o[1] = __bfloat162float(__float2bfloat16_rn(v1[k]));
         for (int ch = 2; ch < 16; ++ch) o[ch] = 0.f;
       }
     }
@@ -254,62 +294,61 @@ __global__ void __launch_bounds__(kThreads, 2)
   const uint32_t bar0 = smem_u32(bar), w_addr = smem_u32(smem + kOffW);
   const uint32_t act_addr = smem_u32(smem + kOffAct0);
   unsigned char* act = smem + kOffAct0;
-  uint32_t parity = 0;            // bit i: phase of row barrier i to wait for next
-  uint32_t pending = 0;           // bit i: row barrier i has a commit not yet waited for
+  uint32_t phase = 0;             // bit s: parity of the commits issued to slot barrier s so far
   bool failed = false;
   const double zscale = state ? state->rnorm : 1.0;
-  const int x = tid;
   const int gx = gx0 + x;
 
   for (int L = 0; L < 4 && !failed; ++L) {
     const uint32_t wl = w_addr + L * 9 * 512;
-    const int r0 = L + 1, nrows = kEH - 2 * (L + 1);
+    const int r0 = L + 1, nrows = kEH - 2 * (L + 1), nslots = nrows + 2;
+    // input row q of layer L lives in slot q - L; output row r0 + i is
+    // written to slot i (its slot as an input of layer L + 1)
     if (tid == 0) {
       fence_after();
-      for (int i = 0; i < nrows; ++i) {
-        issue_row(tmem, 16 * i, act_addr, wl, r0 + i - L);
-        mma_commit(bar0 + 8 * i);
+      for (int sl = 0; sl < nslots; ++sl) {
+        issue_slot(tmem, act_addr, wl, sl, nrows);
+        mma_commit(bar0 + 8 * sl);
       }
     }
-    pending = (1u << nrows) - 1u;
     for (int i = 0; i < nrows; ++i) {
-      const bool ok = mbar_wait(bar0 + 8 * i, (parity >> i) & 1u, c_wait_first);
+      // output i is complete once the MMAs of slot i + 2 are (commits
+      // complete in issue order), and by then so are those reading slot i
+      const int sb = i + 2;
+      const bool ok = mbar_wait(bar0 + 8 * sb, (phase >> sb) & 1u, c_wait_first);
       if (!ok) {
         failed = true;
         break;
       }
-      parity ^= 1u << i;
-      pending &= ~(1u << i);
       fence_after();
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * i, v);
+      // warps w and w + 4 read the same 32 lanes: channels 8 h .. 8 h + 7
+      float v[8];
+      tmem_ld8(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(col_of(i) + 8 * h), v);
       const int row = r0 + i, gy = gy0 + row;
       const bool inside = gx >= 0 && gx < n1 && gy >= 0 && gy < n1;
       if (L < 3) {
-        uint32_t q[8];
+        uint32_t q[4];
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < 4; ++k)
           q[k] = inside ? pack_bf16x2(fmaxf(v[2 * k], 0.f), fmaxf(v[2 * k + 1], 0.f)) : 0u;
         const int off = ((row - L - 1) * kXS + x + 1) * 16;   // in place: slot of input row row - 1
-        *reinterpret_cast<uint4*>(act + off) = make_uint4(q[0], q[1], q[2], q[3]);
-        *reinterpret_cast<uint4*>(act + kPlane + off) = make_uint4(q[4], q[5], q[6], q[7]);
+        *reinterpret_cast<uint4*>(act + h * kPlane + off) = make_uint4(q[0], q[1], q[2], q[3]);
         __nv_bfloat16* kept = L == 0 ? keep.a1 : (L == 1 ? keep.a2 : keep.a3);
         if (kept && inside && x >= kHalo && x < kHalo + kTW && row >= kHalo && row < kHalo + kTH) {
           uint4* o = reinterpret_cast<uint4*>(kept + ((long long)b * g.len + g.G + gx + p * gy) * 16);
-          o[0] = make_uint4(q[0], q[1], q[2], q[3]);
-          o[1] = make_uint4(q[4], q[5], q[6], q[7]);
+          o[h] = make_uint4(q[0], q[1], q[2], q[3]);
         }
         if (acts && inside && x >= kHalo && x < kHalo + kTW && row >= kHalo && row < kHalo + kTH) {
           const long long nn = (long long)n1 * n1;
-          float* o = acts + ((((long long)(L + 1) * gridDim.z + b) * nn) + (long long)gy * n1 + gx) * 16;
+          float* o = acts + ((((long long)(L + 1) * gridDim.z + b) * nn) + (long long)gy * n1 + gx) * 16 + 8 * h;
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
+          for (int k = 0; k < 4; ++k) {
             const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&q[k]);
             o[2 * k] = __low2float(h2);
             o[2 * k + 1] = __high2float(h2);
           }
         }
-      } else if (inside && x >= kHalo && x < kHalo + kTW && row >= kHalo && row < kHalo + kTH) {
+      } else if (h == 0 && inside && x >= kHalo && x < kHalo + kTW && row >= kHalo && row < kHalo + kTH) {
         const long long o = (long long)b * g.len + g.G + gx + p * gy;
         if (y) y[o] = v[0];
         if (z) z[o] = (T)(zscale * (double)v[0]);
@@ -319,12 +358,13 @@ __global__ void __launch_bounds__(kThreads, 2)
     fence_async_smem();
     fence_before();
     failed = __syncthreads_or(failed);
-  }
-  if (failed) {
-    if (tid == 0) atomicExch(err, 1);
-    // let the MMAs still in flight finish (bounded) before freeing their memory
-    for (int i = 0; i < kMaxRows; ++i)
-      if ((pending >> i) & 1u) mbar_wait(bar0 + 8 * i, (parity >> i) & 1u);
+    if (failed) {
+      if (tid == 0) atomicExch(err, 1);
+      // the layer's last commit covers every MMA it issued: let them finish
+      // (bounded) before their memory is freed
+      mbar_wait(bar0 + 8 * (nslots - 1), (phase >> (nslots - 1)) & 1u);
+    }
+    phase ^= (1u << nslots) - 1u;
   }
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
@@ -340,7 +380,8 @@ __global__ void k_net_pack_tc(const float* __restrict__ wq, __nv_bfloat16* __res
     else if (L == 1) w = wq[kNetOff2 + (n * kNetC1 + k) * 9 + t];
     else if (L == 2) w = wq[kNetOff3 + (n * kNetW + k) * 9 + t];
     else { if (n == 0) w = wq[kNetOff4 + k * 9 + t]; }
-    wtc[((L * 9 + t) * 512 + canon(n, k)) / 2] = __float2bfloat16_rn(w);
+    // tap t = ky * 3 + kx of the weights goes to tile kx * 3 + ky (ky fastest)
+    wtc[((L * 9 + (t % 3) * 3 + t / 3) * 512 + canon(n, k)) / 2] = __float2bfloat16_rn(w);
   }
 }
 
