@@ -63,7 +63,7 @@ template <int NPL>
 struct Conv3Smem {
   static constexpr int kWOff = NPL * kPlane3;
   static constexpr int kBarOff = kWOff + kW3Bytes;
-  static constexpr int kBytes = kBarOff + 8 * kR3 + 16;
+  static constexpr int kBytes = kBarOff + 8 * (kR3 + 2) + 16;   // one mbarrier per staged y row
 };
 
 // MODE 0: forward, out = relu?(sum W in(p + off)), in bfloat16 activations;
@@ -79,7 +79,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // Packed weights: for layer l and mode m (0 forward, 1 data gradient) the 27
 // tap tiles of 16 x 16 bfloat16 in the K-major layout of the B operand, at
-// byte (2 l + m) * kW3Bytes.  Forward row n = co, column k = ci; gradient
+// byte (2 l + m) * kW3Bytes, ordered (kz, kx, ky) so that the three y-taps of
+// one (kz, kx) are consecutive.  Forward row n = co, column k = ci; gradient
 // row n = ci, column k = co; zero beyond the layer's channels.
 __global__ void k_net3_pack(const float* __restrict__ wq, unsigned char* __restrict__ wp) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -90,7 +91,9 @@ __global__ void k_net3_pack(const float* __restrict__ wq, unsigned char* __restr
   const int off = l == 0 ? kNet3Off1 : l == 1 ? kNet3Off2 : l == 2 ? kNet3Off3 : kNet3Off4;
   const int co = mode == 0 ? n : k, ci = mode == 0 ? k : n;
   const float w = (co < cout && ci < cin) ? wq[off + (co * cin + ci) * 27 + t] : 0.f;
-  *reinterpret_cast<__nv_bfloat16*>(wp + lm * kW3Bytes + t * 512 + canon16(n, k)) = __float2bfloat16_rn(w);
+  // tap t = kz * 9 + ky * 3 + kx goes to tile (kz * 3 + kx) * 3 + ky (ky fastest)
+  const int tp = ((t / 9) * 3 + t % 3) * 3 + (t / 3) % 3;
+  *reinterpret_cast<__nv_bfloat16*>(wp + lm * kW3Bytes + tp * 512 + canon16(n, k)) = __float2bfloat16_rn(w);
 }
 
 template <int MODE, bool RELU, bool LAST, typename T>
@@ -103,7 +106,7 @@ __global__ void __launch_bounds__(kT3, 1)
   if (state && state->done) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::kBarOff);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S::kBarOff + 8 * kR3);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S::kBarOff + 8 * (kR3 + 2));
   const int tid = threadIdx.x, warp = tid >> 5;
   const int x0 = blockIdx.x * 128, y0 = blockIdx.y * kR3;
   const int z = blockIdx.z % g.pz, b = blockIdx.z / g.pz;
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__(kT3, 1)
   const long long px = g.px, pxy = g.pxy;
 
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), 64);
-  if (tid < kR3) tc::mbar_init(tc::smem_u32(bar + tid));
+  if (tid < kR3 + 2) tc::mbar_init(tc::smem_u32(bar + tid));
   if (tid == 0) tc::mbar_init_fence();
   // the layer's 27 packed weight tiles (13,824 bytes)
   for (int e = tid; e < kW3Bytes / 16; e += kT3)
@@ -158,35 +161,61 @@ __global__ void __launch_bounds__(kT3, 1)
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t idesc = tc::idesc_bf16(128, 16);
+  // Output row r takes the staged rows sy = r .. r + 2; the MMAs go by
+  // staged row (sy outer, then sz, then the x shift sx), and the y-taps that
+  // one staged row feeds are stacked along N (weights packed y-tap-fastest)
+  // into the outputs' TMEM blocks: forward, ky = sy - r, block column
+  // 16 (R - 1 - r), descending in r; gradient, ky = r + 2 - sy, column 16 r.
+  // An output's first contribution (sy = r, sz = sx = 0, hi plane) sets its
+  // block; everything else accumulates.  Commit per staged row: output r is
+  // complete with the commit of sy = r + 2.
   if (tid == 0) {
     const uint32_t s0 = tc::smem_u32(smem), w0 = tc::smem_u32(smem + S::kWOff);
-    for (int r = 0; r < kR3; ++r) {
-      for (int t = 0; t < 27; ++t) {
-        const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
-        // forward: input at (x + kx - 1, y + ky - 1, z + kz - 1);
-        // gradient: dOut at (x - kx + 1, y - ky + 1, z - kz + 1)
-        const int sz = MODE == 0 ? kz : 2 - kz, sy = MODE == 0 ? r + ky : r + 2 - ky, sx = MODE == 0 ? kx : 2 - kx;
-        const uint32_t a = s0 + (uint32_t)(((sz * (kR3 + 2) + sy) * kXS3 + sx) * 16);
-        const uint64_t bdesc = tc::sdesc(w0 + t * 512, 128, 256);
-        tc::mma_bf16(tmem + 16 * r, tc::sdesc(a, kPlane3, 128), bdesc, idesc, t > 0 ? 1u : 0u);
-        if (MODE == 1) tc::mma_bf16(tmem + 16 * r, tc::sdesc(a + 2 * kPlane3, kPlane3, 128), bdesc, idesc, 1u);
+    for (int sy = 0; sy < kR3 + 2; ++sy) {
+      const int lo = MODE == 0 ? (sy - kR3 + 1 > 0 ? sy - kR3 + 1 : 0) : (2 - sy > 0 ? 2 - sy : 0);
+      const int hi = MODE == 0 ? (sy < 2 ? sy : 2) : (kR3 + 1 - sy < 2 ? kR3 + 1 - sy : 2);
+      for (int sz = 0; sz < 3; ++sz) {
+        for (int sx = 0; sx < 3; ++sx) {
+          const int kz = MODE == 0 ? sz : 2 - sz, kx = MODE == 0 ? sx : 2 - sx;
+          const uint32_t a = s0 + (uint32_t)(((sz * (kR3 + 2) + sy) * kXS3 + sx) * 16);
+          const uint32_t wt = w0 + (uint32_t)((kz * 3 + kx) * 3) * 512;   // the tile of ky = 0
+          // output block of tap ky (column of the output it feeds)
+          auto col = [&](int ky) { return MODE == 0 ? 16 * (kR3 - 1 - (sy - ky)) : 16 * (sy + ky - 2); };
+          int l = lo, h = hi;
+          if (sz == 0 && sx == 0 && sy < kR3) {   // output sy's first contribution
+            const int kf = MODE == 0 ? 0 : 2;
+            const uint64_t bf = tc::sdesc(wt + kf * 512, 128, 256);
+            tc::mma_bf16(tmem + col(kf), tc::sdesc(a, kPlane3, 128), bf, tc::idesc_bf16(128, 16), 0u);
+            if (MODE == 1)
+              tc::mma_bf16(tmem + col(kf), tc::sdesc(a + 2 * kPlane3, kPlane3, 128), bf, tc::idesc_bf16(128, 16), 1u);
+            if (MODE == 0) l = 1;
+            else h = 1;
+          }
+          if (l <= h) {
+            const uint64_t bd = tc::sdesc(wt + l * 512, 128, 256);
+            const uint32_t id = tc::idesc_bf16(128, 16 * (h - l + 1));
+            const uint32_t d = tmem + col(l);   // columns ascend with ky in both orientations
+            tc::mma_bf16(d, tc::sdesc(a, kPlane3, 128), bd, id, 1u);
+            if (MODE == 1) tc::mma_bf16(d, tc::sdesc(a + 2 * kPlane3, kPlane3, 128), bd, id, 1u);
+          }
+        }
       }
-      tc::mma_commit(tc::smem_u32(bar + r));
+      tc::mma_commit(tc::smem_u32(bar + sy));
     }
   }
   bool failed = false;
   const int x = x0 + tid;
   const double zs = (LAST && state) ? state->rnorm : 1.0;
   for (int r = 0; r < kR3; ++r) {
-    const bool ok = tc::mbar_wait(tc::smem_u32(bar + r), 0u, c_wait_first3);
+    const bool ok = tc::mbar_wait(tc::smem_u32(bar + r + 2), 0u, c_wait_first3);
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
     }
     tc::fence_after();
     float v[16];
-    tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * r, v);
+    const int col = MODE == 0 ? 16 * (kR3 - 1 - r) : 16 * r;
+    tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
     const int y = y0 + r;
     if (!inside3(g, x, y, z)) continue;   // pads keep their zeros
     const long long t = x + px * y + pxy * z;
@@ -227,7 +256,8 @@ __global__ void __launch_bounds__(kT3, 1)
   }
   if (failed) {
     if (tid == 0) atomicExch(err, 1);
-    for (int r = 0; r < kR3; ++r) tc::mbar_wait(tc::smem_u32(bar + r), 0u, kWait3);
+    // the last commit covers every MMA issued: let them finish (bounded)
+    tc::mbar_wait(tc::smem_u32(bar + kR3 + 1), 0u, kWait3);
   }
   tc::fence_before();
   __syncthreads();
