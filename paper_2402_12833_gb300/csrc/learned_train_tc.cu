@@ -216,16 +216,20 @@ __global__ void __launch_bounds__(kWT, 2)
 // A CTA owns R = 8 rows of 128 points of one image; the R + 2 rows of dOut
 // around them (x from -1 to 128) are staged once as four bfloat16 planes
 // (hi channels 0-7, hi 8-15, lo 0-7, lo 8-15; hi = bf16(d), lo = bf16(d - hi)).
-// For output row r and tap t the A operand is the staged row r + 2 - t/3
-// shifted by 2 - t%3 points (SBO = 128 B, LBO = one plane); two MMAs per tap
-// (hi planes, lo planes) against the tap's 16 x 16 weight tile accumulate in
-// 16 TMEM columns of the row; 18 MMAs per row, one commit per row.
+// Output row r takes the staged rows r .. r + 2 (tap ky = r + 2 - row) at
+// the x shift 2 - kx.  The MMAs go by staged row and shift: the A operand is
+// the staged row shifted (SBO = 128 B, LBO = one plane) and B stacks the
+// 16 x 16 weight tiles of the y-taps that row feeds along N (tiles packed
+// ky-fastest), into the outputs' 16-column TMEM blocks (column 16 r,
+// ascending with ky); hi planes and lo planes are two MMAs.  An output's
+// first contribution (its own staged row, shift 0, hi planes) sets its
+// block; one commit per staged row, output r complete with staged row r + 2.
 constexpr int kDR = 8;                   // output rows per CTA
 constexpr int kDXS = 130;                // stored points per row: x = -1 .. 128
 constexpr int kDPlane = (kDR + 2) * kDXS * 16;
 constexpr int kDWOff = 4 * kDPlane;      // weight tiles
 constexpr int kDBarOff = kDWOff + 9 * 512;
-constexpr int kDSmem = kDBarOff + 8 * kDR + 16;
+constexpr int kDSmem = kDBarOff + 8 * (kDR + 2) + 16;
 constexpr int kDTmemCols = 128;
 
 __device__ __forceinline__ int canon16(int row, int k) {
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(kWT, 2)
                    const __nv_bfloat16* __restrict__ act_in, float* __restrict__ dIn, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kDBarOff);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kDBarOff + 8 * kDR);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kDBarOff + 8 * (kDR + 2));
   const int tid = threadIdx.x, warp = tid >> 5;
   const int x0 = blockIdx.x * 128, y0 = blockIdx.y * kDR, b = blockIdx.z;
   const int n1 = g.n1;
@@ -246,13 +250,14 @@ __global__ void __launch_bounds__(kWT, 2)
   const long long base = (long long)b * g.len + g.G;
 
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kDTmemCols);
-  if (tid < kDR) tc::mbar_init(tc::smem_u32(bar + tid));
+  if (tid < kDR + 2) tc::mbar_init(tc::smem_u32(bar + tid));
   if (tid == 0) tc::mbar_init_fence();
-  // weight tiles: tile t, row n = ci, column k = co
+  // weight tiles: tap t = ky * 3 + kx at tile kx * 3 + ky, row n = ci, column k = co
   for (int e = tid; e < 9 * 256; e += kWT) {
     const int t = e / 256, ci = (e / 16) % 16, co = e % 16;
     const float w = co < COUT ? W[(co * 16 + ci) * 9 + t] : 0.f;
-    *reinterpret_cast<__nv_bfloat16*>(smem + kDWOff + t * 512 + canon16(ci, co)) = __float2bfloat16_rn(w);
+    *reinterpret_cast<__nv_bfloat16*>(smem + kDWOff + ((t % 3) * 3 + t / 3) * 512 + canon16(ci, co)) =
+        __float2bfloat16_rn(w);
   }
   // dOut rows y0 - 1 .. y0 + kDR, x0 - 1 .. x0 + 128 (zero outside the grid)
   for (int e = tid; e < (kDR + 2) * kDXS; e += kWT) {
@@ -279,24 +284,37 @@ __global__ void __launch_bounds__(kWT, 2)
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t idesc = tc::idesc_bf16(128, 16);
   if (tid == 0) {
     const uint32_t s0 = tc::smem_u32(smem), w0 = tc::smem_u32(smem + kDWOff);
-    for (int r = 0; r < kDR; ++r) {
+    for (int sr = 0; sr < kDR + 2; ++sr) {
+      const int lo = 2 - sr > 0 ? 2 - sr : 0, hi = kDR + 1 - sr < 2 ? kDR + 1 - sr : 2;
 #pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const uint32_t a = s0 + (uint32_t)(((r + 2 - t / 3) * kDXS + (2 - t % 3)) * 16);
-        const uint64_t bdesc = tc::sdesc(w0 + t * 512, 128, 256);
-        tc::mma_bf16(tmem + 16 * r, tc::sdesc(a, kDPlane, 128), bdesc, idesc, t > 0 ? 1u : 0u);
-        tc::mma_bf16(tmem + 16 * r, tc::sdesc(a + 2 * kDPlane, kDPlane, 128), bdesc, idesc, 1u);
+      for (int sx = 0; sx < 3; ++sx) {
+        const int kx = 2 - sx;
+        const uint32_t a = s0 + (uint32_t)((sr * kDXS + sx) * 16);
+        const uint64_t ah = tc::sdesc(a, kDPlane, 128), al = tc::sdesc(a + 2 * kDPlane, kDPlane, 128);
+        int h = hi;
+        if (sx == 0 && sr < kDR) {   // output sr's first contribution: tap ky = 2
+          const uint64_t bf = tc::sdesc(w0 + (kx * 3 + 2) * 512, 128, 256);
+          tc::mma_bf16(tmem + 16 * sr, ah, bf, tc::idesc_bf16(128, 16), 0u);
+          tc::mma_bf16(tmem + 16 * sr, al, bf, tc::idesc_bf16(128, 16), 1u);
+          h = 1;
+        }
+        if (lo <= h) {   // taps lo .. h into outputs sr + lo - 2 ..
+          const uint64_t bd = tc::sdesc(w0 + (kx * 3 + lo) * 512, 128, 256);
+          const uint32_t id = tc::idesc_bf16(128, 16 * (h - lo + 1));
+          const uint32_t d = tmem + (uint32_t)(16 * (sr + lo - 2));
+          tc::mma_bf16(d, ah, bd, id, 1u);
+          tc::mma_bf16(d, al, bd, id, 1u);
+        }
       }
-      tc::mma_commit(tc::smem_u32(bar + r));
+      tc::mma_commit(tc::smem_u32(bar + sr));
     }
   }
   bool failed = false;
   const int x = x0 + tid;
   for (int r = 0; r < kDR; ++r) {
-    const bool ok = tc::mbar_wait(tc::smem_u32(bar + r), 0u, c_wait_first_w);
+    const bool ok = tc::mbar_wait(tc::smem_u32(bar + r + 2), 0u, c_wait_first_w);
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
@@ -329,8 +347,9 @@ __global__ void __launch_bounds__(kWT, 2)
   }
   if (failed) {
     if (tid == 0) atomicExch(err, 1);
-    // the MMAs still in flight finish (bounded) before their memory is freed
-    for (int r = 0; r < kDR; ++r) tc::mbar_wait(tc::smem_u32(bar + r), 0u, kWaitLimitW);
+    // the last commit covers every MMA issued: let them finish (bounded)
+    // before their memory is freed
+    tc::mbar_wait(tc::smem_u32(bar + kDR + 1), 0u, kWaitLimitW);
   }
   tc::fence_before();
   __syncthreads();
