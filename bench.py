@@ -695,20 +695,27 @@ def bench_batched(args):
         dist.destroy_process_group()
     if rank != 0:
         return 0
-    # roofline of the dominant kernel class on one problem of the largest side
-    # solved alone: a batched launch skips its converged problems, so it has
-    # no fixed byte count
+    # roofline of the dominant kernel class of the largest size class, over
+    # its first five inner iterations: every problem of the class is still
+    # running there, so a launch moves the class's problem count times the
+    # per-problem algorithmic bytes (later launches skip converged problems)
     big = max(by)
+    ci = sorted(by).index(big)
+    cbig = classes[ci]
     p0 = pb.batch_problem(by[big][0], big)
-    H1 = M.Hierarchy(torch.from_numpy(p0.stencil).cuda(), 2, big, p0.levels, m=M_WINDOW, precision=M.MPCG_MIXED)
-    ns1 = [M.mg_level_size(H1.h, j) for j in range(p0.levels)]
-    b1 = torch.from_numpy(p0.b).cuda()
-    x1 = torch.zeros_like(b1)
-    _, _, _, trace = M.mpcg_solve_profiled(H1.h, b1, x1, RTOL, 20000)
-    _, rl, _, tot1 = roofline(trace, ns1, p0.levels, M_WINDOW, 4, load_peaks(), FP64_PEAK_TFLOPS, S=9)
+    ns1 = [M.mg_level_size(cbig.h, j) for j in range(p0.levels)]
+    M.mg_detach_q1_kappa(cbig.h)   # the stored stencils, as in the headline figure
+    xs[ci].zero_()
+    _, _, _, trace = M.mpcg_solve_profiled(cbig.h, bs[ci], xs[ci], RTOL, 20000)
+    checks = [i for i, (c, _) in enumerate(trace) if c == "check"]
+    head = trace[:checks[4] + 1] if len(checks) >= 5 else trace
+    nprob = len(by[big])
+    _, rl, _, tot1 = roofline(head, ns1, p0.levels, M_WINDOW, 4, load_peaks(), FP64_PEAK_TFLOPS, S=9)
     if rl is not None:
-        rl["workload"] = f"problem {by[big][0]} ({big}^2 nodes) of the batch solved alone"
-    H1.close()
+        for k in ("achieved", "frac", "algorithmic_bytes_per_launch"):
+            rl[k] *= nprob
+        rl["workload"] = (f"the {nprob} problems of {big}^2 nodes (the largest class), first five inner "
+                          f"iterations of the profiled class solve (every problem running)")
     cpu = None
     if not args.no_cpu_baseline:   # after the GPU legs, one core: the oracle on one problem of each side <= 257
         sample = [(by[sd][0], sd) for sd in sorted(by) if sd <= 257]
@@ -733,7 +740,7 @@ def bench_batched(args):
                    "total_dofs": int(ns_all)},
         "max_iterations_per_side": {str(k): int(i.max()) for k, i in zip(sorted(by), its)},
         "gpu_launches_per_step": launches, "one_graph_launch": True, "roofline": rl,
-        "kernel_ms_per_solve_of_roofline_problem": {c: round(v, 4) for c, v in tot1.items()},
+        "kernel_ms_first_five_iterations_of_largest_class": {c: round(v, 4) for c, v in tot1.items()},
         "cpu_baseline": cpu,
         "matrix_free": {"value": ns_all / (ms_mf * 1e-3), "ms_per_step": ms_mf,
                         "max_iterations_per_side": {str(k): int(i.max()) for k, i in zip(sorted(by), its_mf)}}}))

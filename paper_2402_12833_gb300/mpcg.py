@@ -223,20 +223,25 @@ def mpcg_kernel_class_name(cls: int) -> str:
 
 def mpcg_solve_profiled(h: int, b, x, rtol: float = 1e-8, maxit: int = 500, trace_cap: int = 1 << 16):
     """Solve with per-launch CUDA-event timing; returns (status, iterations,
-    {class name: (total ms, launches)}, [(class name, ms) per launch])."""
-    it = C.c_int(0)
+    {class name: (total ms, launches)}, [(class name, ms) per launch]).
+    iterations is an int, or an array with one count per problem for a
+    batched hierarchy."""
+    nprob = max(1, mg_num_problems(h))
+    it = np.zeros(nprob, dtype=np.int32)
     ms = np.zeros(MPCG_NUM_KERNEL_CLASSES)
     cnt = np.zeros(MPCG_NUM_KERNEL_CLASSES, dtype=np.int64)
     tc = np.zeros(trace_cap, dtype=np.int32)
     tm = np.zeros(trace_cap, dtype=np.float32)
     tl = C.c_longlong(0)
-    st = load().mpcg_solve_profiled(h, _ptr(b), _ptr(x), rtol, maxit, C.byref(it), ms.ctypes.data, cnt.ctypes.data,
-                                    tc.ctypes.data, tm.ctypes.data, trace_cap, C.byref(tl))
+    st = load().mpcg_solve_profiled(h, _ptr(b), _ptr(x), rtol, maxit, it.ctypes.data_as(C.POINTER(C.c_int)),
+                                    ms.ctypes.data, cnt.ctypes.data, tc.ctypes.data, tm.ctypes.data, trace_cap,
+                                    C.byref(tl))
     _check(st, allow=(MPCG_OK, MPCG_NOT_CONVERGED))
     names = [mpcg_kernel_class_name(i) for i in range(MPCG_NUM_KERNEL_CLASSES)]
     n = min(tl.value, trace_cap)
     trace = [(names[int(c)], float(t)) for c, t in zip(tc[:n], tm[:n])]
-    return st, it.value, {names[i]: (float(ms[i]), int(cnt[i])) for i in range(MPCG_NUM_KERNEL_CLASSES)}, trace
+    iters = int(it[0]) if nprob == 1 else it.copy()
+    return st, iters, {names[i]: (float(ms[i]), int(cnt[i])) for i in range(MPCG_NUM_KERNEL_CLASSES)}, trace
 
 
 def mg_last_launches(h: int) -> int:
