@@ -1251,8 +1251,11 @@ def bench_algebraic(args):
 def bench_learned(args):
     """2D high-contrast diffusion, 1025^2 nodes, 9 grids, f = 1, kappa seed 3:
     the mixed-precision solver without and with the learned column; the
-    network is trained on the GPU on 4096 (residual, error) pairs of 129^2
-    problems with kappa seeds 1000..1015 made by the solver itself."""
+    network is trained on the GPU on (residual, error) pairs made by the
+    solver itself: by default 4096 pairs of 129^2 problems with kappa seeds
+    1000..1015 (FP64 iterates 1..256); --train-nodes 1025 trains on pairs of
+    the evaluation size instead (--train-seeds problems, mixed-precision
+    iterates 1, 1 + stride, ... below 257)."""
     import numpy as np
     import torch
     from paper_2402_12833_gb300 import build as _build
@@ -1262,14 +1265,16 @@ def bench_learned(args):
     M.load()
     t0 = time.perf_counter()
     hs, R, E, owner = [], [], [], []
-    for i, sd in enumerate(range(1000, 1016) if args.epochs > 0 else ()):
-        prob = pb.diffusion_macro(2, 129, sd)
-        H = M.Hierarchy(torch.from_numpy(prob.stencil).cuda(), 2, 129, prob.levels, m=M_WINDOW)
+    tn = args.train_nodes
+    prec = M.MPCG_FP64 if tn <= 129 else M.MPCG_MIXED   # iterates of the evaluation size: the mixed solver
+    for i, sd in enumerate(range(1000, 1000 + args.train_seeds) if args.epochs > 0 else ()):
+        prob = pb.diffusion_macro(2, tn, sd)
+        H = M.Hierarchy(torch.from_numpy(prob.stencil).cuda(), 2, tn, prob.levels, m=M_WINDOW, precision=prec)
         b = torch.from_numpy(prob.b).cuda()
         xs = torch.zeros_like(b)
         H.solve(b, xs, rtol=1e-12, maxit=20000, histories=False)
         Ax = torch.empty_like(b)
-        for k in range(1, 257):
+        for k in range(1, 257, args.train_stride):
             x = torch.zeros_like(b)
             H.solve(b, x, rtol=1e-30, maxit=k, histories=False)
             M.mg_apply_operator(H.h, prob.levels - 1, x, Ax, 1)
@@ -1328,8 +1333,9 @@ def bench_learned(args):
         "metric": METRIC, "workload": "learned", "value": out["learned"]["dofs_per_s"], "unit": "DOFs/s",
         "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64+bf16", "data": "synthetic",
         "config": {"workload": "2D diffusion 1025^2, 9 grids, log10 kappa U[-2,4] on 16x16 macro cells (seed 3), "
-                               "f = 1, MPCG m=5, mixed precision, rtol 1e-8; network 2-16-16-16-1 trained on 4096 "
-                               "pairs from 129^2 problems (kappa seeds 1000-1015)"},
+                               "f = 1, MPCG m=5, mixed precision, rtol 1e-8; network 2-16-16-16-1 trained on "
+                               f"{len(R)} pairs from {args.train_nodes}^2 problems (kappa seeds 1000-"
+                               f"{999 + args.train_seeds})"},
         "plain": out["plain"], "learned": out["learned"],
         "plain_matrix_free": out["plain_matrix_free"], "learned_matrix_free": out["learned_matrix_free"],
         "plain_fp64": out["plain_fp64"], "plain_fp64_dw": out["plain_fp64_dw"],
@@ -1337,7 +1343,8 @@ def bench_learned(args):
         # wall time of the plain FP64 solve over that of mixed precision + the learned column
         "speedup_learned_mixed_vs_plain_fp64": out["plain_fp64"]["ms_per_solve"] / out["learned"]["ms_per_solve"],
         "speedup_learned_mixed_vs_plain_mixed": out["plain"]["ms_per_solve"] / out["learned"]["ms_per_solve"],
-        "training": {"pairs": len(R), "epochs": args.epochs, "loss_first": float(loss[0]),
+        "training": {"pairs": len(R), "grid": f"{args.train_nodes}^2", "problems": args.train_seeds,
+                     "iterate_stride": args.train_stride, "epochs": args.epochs, "loss_first": float(loss[0]),
                      "loss_last": float(loss[-1]), "pair_generation_s": gen_s, "train_s": train_s}}))
     return 0
 
@@ -1397,6 +1404,9 @@ def main():
                     default="poisson3d",
                     help="poisson3d: the headline line; batched / learned / elasticity: the other workloads")
     ap.add_argument("--epochs", type=int, default=20, help="training epochs of the learned workload")
+    ap.add_argument("--train-nodes", type=int, default=129, help="learned workload: nodes per side of the training problems")
+    ap.add_argument("--train-seeds", type=int, default=16, help="learned workload: number of training problems")
+    ap.add_argument("--train-stride", type=int, default=1, help="learned workload: stride of the iterates 1..256 used as pairs")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
