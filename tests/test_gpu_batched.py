@@ -180,3 +180,20 @@ def test_one_graph_batch_refuses_other_precisions(M):
         X = x.cpu().numpy()
         for i, p in enumerate(ps):
             assert _true_res(p, X[i]) <= 1e-8
+
+
+def test_profiled_solve_of_a_batch(M):
+    """mpcg_solve_profiled on a batched hierarchy (direct launches with
+    per-launch CUDA events) returns one iteration count per problem, those of
+    the graph-launched solve, and iterates that agree with it."""
+    classes, bs, _ = _classes(M, {65: 3}, M.MPCG_MIXED, first=120)
+    c, b = classes[0], bs[0]
+    x0 = torch.zeros_like(b)
+    st, it = c.solve(b, x0, rtol=1e-8, maxit=4000)
+    x1 = torch.zeros_like(b)
+    st1, it1, cls, trace = M.mpcg_solve_profiled(c.h, b, x1, 1e-8, 4000)
+    assert st1 == st == M.MPCG_OK
+    assert np.asarray(it1).shape == (3,)
+    assert np.all(np.abs(np.asarray(it1) - np.asarray(it)) <= 1), (it1, it)
+    assert torch.linalg.norm(x1 - x0) <= 1e-6 * torch.linalg.norm(x0)
+    assert sum(1 for k, _ in trace if k == "check") >= int(np.max(it))
