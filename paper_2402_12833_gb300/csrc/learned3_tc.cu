@@ -13,13 +13,14 @@
 // One launch per layer (the 3D halo of a fused four-layer tile would cost
 // more than the round trip of 32 bytes per node): a CTA owns R = 4 rows of
 // up to 128 nodes at one z and stages the 3 x (R + 2) input rows around them
-// (x from -1 to 128) as K-major bfloat16 planes.  Per output row and tap
-// (dx, dy, dz) the A operand is a staged row shifted by the tap (SBO = 128 B,
-// LBO = one plane), B the tap's 16 x 16 weight tile, D 16 FP32 columns of
-// TMEM per row: 27 tcgen05.mma (kind::f16, M = 128 nodes, N = 16, K = 16)
-// per row in the forward pass; the data gradient (the transposed
-// convolution, masked by the ReLU pattern of the layer input) takes its FP32
-// input as bfloat16 hi + lo planes, 54 MMAs per row.  The weight gradient is
+// (x from -1 to 128) as K-major bfloat16 planes.  The MMAs go by staged row:
+// per staged row, z plane and x shift the A operand is the staged row
+// shifted (SBO = 128 B, LBO = one plane) and B stacks the 16 x 16 weight
+// tiles of the y-taps that row feeds along N (16 to 48), into the 16 FP32
+// TMEM columns of each output row (tcgen05.mma kind::f16, M = 128 nodes,
+// K = 16): 57 MMAs per CTA in the forward pass; the data gradient (the
+// transposed convolution, masked by the ReLU pattern of the layer input)
+// takes its FP32 input as bfloat16 hi + lo planes, 114 MMAs per CTA.  The weight gradient is
 // the pixel-reduction GEMM of the 2D network with 27 taps: A = dOut^T (hi
 // rows 0-15, lo rows 16-31), B = the im2col of the layer input (27 taps x 16
 // channels = 432 rows, three MMAs of N = 144 per K step), accumulated in 432

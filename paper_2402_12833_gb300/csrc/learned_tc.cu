@@ -3,16 +3,20 @@
 // the first three, zero padding, bfloat16 weights and activations, FP32
 // accumulation) fused in one kernel per output tile.
 //
-// Each layer is an implicit GEMM: for one row of 128 tile pixels (M = 128)
-// and one tap (dy, dx) of the 3x3 stencil, D[pixel][co] += A[pixel][ci] *
-// B[co][ci] with A the input activations shifted by the tap and B the tap's
-// 16 x 16 weight slice (K = 16 input channels, N = 16 output channels), so a
-// row is nine tcgen05.mma (kind::f16, bf16 inputs, FP32 accumulator in tensor
-// memory).  One elected thread issues the MMAs; tcgen05.commit signals an
-// mbarrier; the four warps read the accumulator back with tcgen05.ld, apply
-// ReLU and the domain mask, round to bfloat16 and write the next layer's
-// activations to shared memory.  Layer 1 has two input channels (zero-padded
-// to 16), layer 4 one output channel (zero-padded weights, column 0 read).
+// Each layer is an implicit GEMM over rows of 128 tile pixels (M = 128,
+// K = 16 input channels): output row i takes the input rows i, i + 1, i + 2
+// (the y-taps), each shifted by the x-tap.  The MMAs go by input row: for
+// input row s and x-tap kx the A operand is row s shifted by kx, and the B
+// operand stacks the 16 x 16 weight tiles of the y-taps that row feeds along
+// N (16, 32 or 48), so the product lands in the TMEM blocks of up to three
+// output rows at once (tcgen05.mma kind::f16, bf16 inputs, FP32 accumulator
+// in tensor memory; see issue_slot).  One elected thread issues the MMAs
+// with one tcgen05.commit per input row; eight warps read the accumulators
+// back with tcgen05.ld (two warps per 32-lane quadrant, one per channel
+// half), apply ReLU and the domain mask, round to bfloat16 and write the
+// next layer's activations to shared memory.  Layer 1 has two input
+// channels (zero-padded to 16), layer 4 one output channel (zero-padded
+// weights, column 0 read).
 //
 // Tile: 120 x 8 output pixels with a 4-pixel halo (four layers of 3x3), i.e.
 // 128 x 16 activation pixels; layer l computes rows l .. 15 - l, so the halo
@@ -25,20 +29,16 @@
 // leading byte offset (LBO) steps between the two K halves, the stride byte
 // offset (SBO) between consecutive groups of 8 rows.  Activations are kept as
 // two planes (channels 0-7 and 8-15) of [row][x + 1] pixels x 16 bytes, so
-// the A operand of tap (dy, dx) for a row is simply the 128 consecutive
-// pixels starting at (row + dy, dx): SBO = 128 bytes, LBO = one plane.  The
-// weights are packed once per attach into the compact tile layout (LBO = 128,
-// SBO = 256 bytes).  The activations are updated in place: input row q of
-// layer L lives in slot q - L, and output row r is written to slot r - L - 1
-// (its slot as an input of layer L + 1) once row r's MMAs have completed --
-// by then every MMA that reads input row r - 1 (rows r - 2 .. r) is done, and
-// the commits complete in issue order.  This halves the shared memory, so two
-// CTAs share an SM and hide each other's latencies.
-// Per layer the issuing thread enqueues the MMAs of all
-// rows at once, each row into its own TMEM columns and signalling its own
-// mbarrier, and every warp drains the rows in order as they complete (a
-// warp reads only its own 32 TMEM lanes, so no block barrier is needed
-// between rows).
+// the A operand of input row s at x-tap kx is simply the 128 consecutive
+// pixels starting at (s, kx): SBO = 128 bytes, LBO = one plane.  The weights
+// are packed once per attach into compact tiles ordered y-tap-fastest
+// (LBO = 128, SBO = 256 bytes; consecutive tiles continue the N rows).  The
+// activations are updated in place: input row q of layer L lives in slot
+// q - L, and output row r is written to slot r - L - 1 (its slot as an input
+// of layer L + 1) once it is complete -- with the commit of input row r + 1,
+// by which time the MMAs reading slot r - L - 1 are done, since commits
+// complete in issue order.  This halves the shared memory, so two CTAs share
+// an SM and hide each other's latencies.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
