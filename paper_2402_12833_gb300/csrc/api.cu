@@ -785,6 +785,7 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
   LAUNCH(h, K_BETA, s, launch_small_beta(S.state, h->nb, S.part_W, gram_chunks(L.g), C, S.small_scratch, S.counters,
                                          s));
   LAUNCH(h, K_ORTH, s, launch_orth_update<T>(L.g, S.win, S.Z, S.AZ, S.r, C, S.part_G, S.state, s));
+  if constexpr (kIsDw<T>) LAUNCH(h, K_ORTH, s, launch_orth_gram_dw(L.g, S.win, S.r, C, S.part_G, S.state, s));
   LAUNCH(h, K_ALPHA, s, launch_small_alpha(S.state, h->nb, S.part_G, stream_blocks(L.g), S.part_zaz,
                                           spmm_blocks<T>(L.g, C), spmm_blocks<T>(L.g, C), C, S.alpha_hist,
                                           (long long)S.hist_cap * C, S.small_scratch, S.counters, s));

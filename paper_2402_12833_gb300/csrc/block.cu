@@ -23,8 +23,12 @@ namespace {
 // W_jj[a][b] = sum_i AP_slot(jj)[a][i] Z[b][i].  Block b works on window
 // block jj = b % m and on the contiguous point chunk b / m, so that the
 // blocks running together read the same chunk of Z (L2 reuse).
+// double-word Gram: two blocks per SM (128 registers) without the software
+// pipelining of the next point's loads (which needs 24 more registers)
+constexpr bool kGramDwPrefetch = false;
+
 template <typename T, int C>
-__global__ void __launch_bounds__(kBlock, kIsDw<T> ? 1 : 3) k_gram_window(GridDesc g, Window<T> win, const T* __restrict__ Z,
+__global__ void __launch_bounds__(kBlock, kIsDw<T> ? 2 : 3) k_gram_window(GridDesc g, Window<T> win, const T* __restrict__ Z,
                                                         double* part, int nchunks, const DevState* state) {
   const int pb = blockIdx.y;
   state += pb;
@@ -64,9 +68,9 @@ __global__ void __launch_bounds__(kBlock, kIsDw<T> ? 1 : 3) k_gram_window(GridDe
 #pragma unroll
         for (int w = 0; w < W; ++w) mac(acc[a * C + b], ap[a][w], z[b][w]);
   };
-  if constexpr (kIsDw<T>) {
-    // the double-word sums leave few warps per SM: the next point's loads
-    // are issued before the current point's products (software pipelining)
+  if constexpr (kIsDw<T> && kGramDwPrefetch) {
+    // the next point's loads are issued before the current point's products
+    // (software pipelining)
     long long q = g0 + threadIdx.x;
     T z[C][W], ap[C][W];
     if (q < g1) load_point(q, z, ap);
@@ -98,8 +102,36 @@ __global__ void __launch_bounds__(kBlock, kIsDw<T> ? 1 : 3) k_gram_window(GridDe
   block_sum_store<T, C * C>(fin, pj, nchunks, chunk);
 }
 
+// Gram partials of one point group: G = sym(P^T A P) (upper triangle,
+// p_a ap_b + p_b ap_a) and g = P^T r.
+template <typename T, int C, int W>
+__device__ __forceinline__ void gram_point(const T (&p)[C][W], const T (&ap)[C][W], const T* rp,
+                                           typename Acc<T>::type (&acc)[C * (C + 1) / 2 + C]) {
+  constexpr int NG = C * (C + 1) / 2;
+  T rv[W];
+  VecN<T, W>::load(rp, rv);
+  int k = 0;
+#pragma unroll
+  for (int a = 0; a < C; ++a) {
+#pragma unroll
+    for (int b = a; b < C; ++b) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        mac(acc[k], p[a][w], ap[b][w]);
+        mac(acc[k], p[b][w], ap[a][w]);
+      }
+      ++k;
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) mac(acc[NG + a], p[a][w], rv[w]);
+  }
+}
+
+// In double-word arithmetic the Gram partials of the new block go to a
+// second kernel (k_orth_gram_dw): without their 27 double-word accumulators
+// the orthogonalisation fits 128 registers and two blocks per SM.
 template <typename T, int C>
-__global__ void __launch_bounds__(kBlock, kIsDw<T> ? 1 : 2) k_orth_update(GridDesc g, Window<T> win, const T* __restrict__ Z,
+__global__ void __launch_bounds__(kBlock, 2) k_orth_update(GridDesc g, Window<T> win, const T* __restrict__ Z,
                                                         const T* __restrict__ AZ, const T* __restrict__ r,
                                                         double* part, const DevState* state) {
   const int pb = blockIdx.y;
@@ -127,11 +159,12 @@ __global__ void __launch_bounds__(kBlock, kIsDw<T> ? 1 : 2) k_orth_update(GridDe
   const T* AZb = AZ + bo;
   const T* rb = r + bo;
   constexpr int W = kIsDw<T> ? 1 : Vec<T>::W;   // double-word: one point per thread (registers)
+  constexpr bool kParts = !kIsDw<T>;             // Gram partials here, or in k_orth_gram_dw
   constexpr int NG = C * (C + 1) / 2;
   using A = typename Acc<T>::type;
-  A acc[NG + C];
+  A acc[kParts ? NG + C : 1];
 #pragma unroll
-  for (int i = 0; i < NG + C; ++i) acc[i] = Acc<T>::of(T(0));
+  for (int i = 0; i < (kParts ? NG + C : 1); ++i) acc[i] = Acc<T>::of(T(0));
   const long long ngroups = g.npts / W;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
        q += (long long)gridDim.x * blockDim.x) {
@@ -200,30 +233,51 @@ __global__ void __launch_bounds__(kBlock, kIsDw<T> ? 1 : 2) k_orth_update(GridDe
         p[b][w] = Acc<T>::value(pacc[b][w]);
         ap[b][w] = Acc<T>::value(apacc[b][w]);
       }
-    T rv[W];
-    VecN<T, W>::load(rb + i, rv);
-    int k = 0;
 #pragma unroll
     for (int a = 0; a < C; ++a) {
       VecN<T, W>::store(Pn + (long long)a * g.cp + i, p[a]);
       VecN<T, W>::store(APn + (long long)a * g.cp + i, ap[a]);
-#pragma unroll
-      for (int b = a; b < C; ++b) {
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-          mac(acc[k], p[a][w], ap[b][w]);
-          mac(acc[k], p[b][w], ap[a][w]);
-        }
-        ++k;
-      }
-#pragma unroll
-      for (int w = 0; w < W; ++w) mac(acc[NG + a], p[a][w], rv[w]);
     }
+    if constexpr (kParts) gram_point<T, C, W>(p, ap, rb + i, acc);
   }
-  T fin[NG + C];
+  if constexpr (kParts) {
+    T fin[NG + C];
 #pragma unroll
-  for (int i = 0; i < NG + C; ++i) fin[i] = Acc<T>::value(acc[i]);
-  block_sum_store<T, NG + C>(fin, part + (long long)pb * (NG + C) * gridDim.x, gridDim.x, blockIdx.x);
+    for (int i = 0; i < NG + C; ++i) fin[i] = Acc<T>::value(acc[i]);
+    block_sum_store<T, NG + C>(fin, part + (long long)pb * (NG + C) * gridDim.x, gridDim.x, blockIdx.x);
+  }
+}
+
+// The Gram partials of the new block, double-word: the same points per
+// thread and the same order as the fused FP32 / FP64 kernels (same grid).
+template <int C>
+__global__ void __launch_bounds__(kBlock, 2) k_orth_gram_dw(GridDesc g, Window<dw> win, const dw* __restrict__ r,
+                                                             double* part, const DevState* state) {
+  const int pb = blockIdx.y;
+  state += pb;
+  if (state->done) return;
+  const int ns = (state->newest + 1) % state->m;
+  const long long bo = (long long)pb * g.len + g.G;
+  const dw* Pn = win.P[ns] + bo;
+  const dw* APn = win.AP[ns] + bo;
+  constexpr int NG = C * (C + 1) / 2;
+  dwacc acc[NG + C];
+#pragma unroll
+  for (int i = 0; i < NG + C; ++i) acc[i] = dwacc_of(dw(0));
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.npts;
+       q += (long long)gridDim.x * blockDim.x) {
+    dw p[C][1], ap[C][1];
+#pragma unroll
+    for (int a = 0; a < C; ++a) {
+      VecN<dw, 1>::load(Pn + (long long)a * g.cp + q, p[a]);
+      VecN<dw, 1>::load(APn + (long long)a * g.cp + q, ap[a]);
+    }
+    gram_point<dw, C, 1>(p, ap, r + bo + q, acc);
+  }
+  dw fin[NG + C];
+#pragma unroll
+  for (int i = 0; i < NG + C; ++i) fin[i] = dwacc_value(acc[i]);
+  block_sum_store<dw, NG + C>(fin, part + (long long)pb * (NG + C) * gridDim.x, gridDim.x, blockIdx.x);
 }
 
 template <typename T, int C>
@@ -416,6 +470,12 @@ void launch_orth_update(const GridDesc& g, Window<T> win, const T* Z, const T* A
                         const DevState* state, cudaStream_t s) {
   const int nb = stream_blocks(g);
   MPCG_C_SWITCH(C, (k_orth_update<T, CC><<<dim3(nb, g.nb), kBlock, 0, s>>>(g, win, Z, AZ, r, part, state)));
+}
+
+void launch_orth_gram_dw(const GridDesc& g, Window<dw> win, const dw* r, int C, double* part, const DevState* state,
+                         cudaStream_t s) {
+  const int nb = stream_blocks(g);
+  MPCG_C_SWITCH(C, (k_orth_gram_dw<CC><<<dim3(nb, g.nb), kBlock, 0, s>>>(g, win, r, part, state)));
 }
 
 template <typename T>

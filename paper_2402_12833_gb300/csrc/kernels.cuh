@@ -165,6 +165,10 @@ void launch_gram_window(const GridDesc& g, Window<T> win, const T* Z, int C, int
 template <typename T>
 void launch_orth_update(const GridDesc& g, Window<T> win, const T* Z, const T* AZ, const T* r,
                         int C, double* part, const DevState* state, cudaStream_t s);
+// double-word: the Gram partials of the new block (launch_orth_update<dw>
+// leaves them to this kernel), same partial layout as the fused kernels
+void launch_orth_gram_dw(const GridDesc& g, Window<dw> win, const dw* r, int C, double* part,
+                         const DevState* state, cudaStream_t s);
 // x += P alpha, r -= AP alpha (newest block); partial of ||r||^2
 template <typename T>
 void launch_update_xr(const GridDesc& g, Window<T> win, T* x, T* r, int C, double* part,
