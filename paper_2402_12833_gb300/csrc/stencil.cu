@@ -137,7 +137,7 @@ __device__ __forceinline__ void stencil_group(const T* __restrict__ st, long lon
 // 85 registers) in one wave of resident blocks (spmm_blocks): measured faster
 // than two blocks per SM over two waves, whose loads wait longer.
 template <typename T, int DIM, int C, bool ZAZ>
-__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && DIM == 3 && C <= 6) ? 3 : 1) k_spmm(GridDesc g, const T* __restrict__ st, const T* __restrict__ X,
+__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && DIM == 3 && C <= 6) ? 3 : (kIsDw<T> ? 2 : 1)) k_spmm(GridDesc g, const T* __restrict__ st, const T* __restrict__ X,
                                                  T* __restrict__ Y, double* zaz, const DevState* state) {
   const int pb = blockIdx.y;
   if (state && state[pb].done) return;
