@@ -99,6 +99,8 @@ def kernel_work(cls: str, n: int, C: int, cnt: int, w: int, S: int = 27):
         return (S + 2 * C) * w * n, 2 * (S * C + C) * n
     if cls == "update_xr":        # read P, AP, x, r; write x, r
         return (2 * C + 4) * w * n, 2 * (2 * C + 1) * n
+    if cls == "orth_gram":        # double-word: read the new P, AP and r; sym Gram + P^T r
+        return (2 * C + 1) * w * n, 2 * (C * (C + 1) + C) * n
     return None, None
 
 
@@ -152,7 +154,7 @@ def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops, S=27, vector=False
             jr -= 1
         elif cls == "prolong":   # composite: write J fine columns, read every coarse correction once
             b, f = (J * ns[J] + sum(ns[:J])) * w, 2 * 8 * J * ns[J]
-        elif cls in ("orth_update", "gram_window", "spmm", "update_xr"):
+        elif cls in ("orth_update", "gram_window", "spmm", "update_xr", "orth_gram"):
             b, f = kernel_work(cls, ns[J], C, cnt, w, s_fine if (s_fine is not None and cls == "spmm") else S)
         if cls == dom:
             if b is not None:

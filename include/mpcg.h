@@ -371,7 +371,9 @@ mpcg_status mg_get_operator(mg_hierarchy* h, int level, double* planes_dev);   /
  * Measurement support (not part of the method).  Kernel launches are grouped
  * in MPCG_NUM_KERNEL_CLASSES classes named by mpcg_kernel_class_name():
  * pack, residual, init, restrict, coarse_solve, prolong, jacobi, spmm,
- * gram_window, small_beta, orth_update, small_alpha, update_xr, check, aux.
+ * gram_window, small_beta, orth_update, small_alpha, update_xr, check, aux,
+ * net (the learned column) and orth_gram (the Gram partials of the new block
+ * in double-word arithmetic, a kernel of its own there).
  *
  * mpcg_solve_profiled runs mpcg_solve with direct kernel launches (no graph)
  * and a CUDA event pair around every launch on the hierarchy's stream; it
@@ -383,7 +385,7 @@ mpcg_status mg_get_operator(mg_hierarchy* h, int level, double* planes_dev);   /
  * mg_last_launches returns how many kernels the last mpcg_solve or
  * mpcg_solve_profiled call on h executed (graph launches counted per node).
  */
-#define MPCG_NUM_KERNEL_CLASSES 16
+#define MPCG_NUM_KERNEL_CLASSES 17
 const char* mpcg_kernel_class_name(int cls);
 mpcg_status mpcg_solve_profiled(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit,
                                 int* iters_out, double* class_ms, long long* class_launches,

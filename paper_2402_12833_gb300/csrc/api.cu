@@ -157,11 +157,11 @@ struct Solver {
 
 enum KClass {
   K_PACK, K_RESIDUAL, K_INIT, K_RESTRICT, K_COARSE, K_PROLONG, K_JACOBI, K_SPMM, K_GRAM, K_BETA, K_ORTH,
-  K_ALPHA, K_UPDATE, K_CHECK, K_AUX, K_NET, K_COUNT
+  K_ALPHA, K_UPDATE, K_CHECK, K_AUX, K_NET, K_OGRAM, K_COUNT
 };
 const char* const kClassNames[K_COUNT] = {"pack", "residual", "init", "restrict", "coarse_solve", "prolong",
                                           "jacobi", "spmm", "gram_window", "small_beta", "orth_update",
-                                          "small_alpha", "update_xr", "check", "aux", "net"};
+                                          "small_alpha", "update_xr", "check", "aux", "net", "orth_gram"};
 
 // Launch accounting and optional per-launch CUDA-event timing (direct
 // launches only; never active while a graph is captured).
@@ -785,7 +785,7 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
   LAUNCH(h, K_BETA, s, launch_small_beta(S.state, h->nb, S.part_W, gram_chunks(L.g), C, S.small_scratch, S.counters,
                                          s));
   LAUNCH(h, K_ORTH, s, launch_orth_update<T>(L.g, S.win, S.Z, S.AZ, S.r, C, S.part_G, S.state, s));
-  if constexpr (kIsDw<T>) LAUNCH(h, K_ORTH, s, launch_orth_gram_dw(L.g, S.win, S.r, C, S.part_G, S.state, s));
+  if constexpr (kIsDw<T>) LAUNCH(h, K_OGRAM, s, launch_orth_gram_dw(L.g, S.win, S.r, C, S.part_G, S.state, s));
   LAUNCH(h, K_ALPHA, s, launch_small_alpha(S.state, h->nb, S.part_G, stream_blocks(L.g), S.part_zaz,
                                           spmm_blocks<T>(L.g, C), spmm_blocks<T>(L.g, C), C, S.alpha_hist,
                                           (long long)S.hist_cap * C, S.small_scratch, S.counters, s));

@@ -138,7 +138,7 @@ _SIGS = {
     "mg_learned_train": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                    C.POINTER(mg_train_opts), C.c_void_p, C.c_void_p]),
 }
-MPCG_NUM_KERNEL_CLASSES = 16
+MPCG_NUM_KERNEL_CLASSES = 17
 
 
 def load(path: str = LIB_PATH):
