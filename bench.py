@@ -223,8 +223,8 @@ def measured_traffic(key: str):
 
 
 def bmin_per_iteration(iters: int, n: int, C: int, m: int, w: int, S: int) -> float:
-    """Algorithmic bytes of one MPCG iteration on the fine grid, the B_min of
-    the survey's measurement section: read the stored window (P_j, A P_j),
+    """Algorithmic bytes of one MPCG iteration on the fine grid (B_min, the
+    least HBM traffic an iteration needs): read the stored window (P_j, A P_j),
     write the new block (P, A P), read and write x and r, read the operator
     once -- (2 cnt C + 2 C + 4) w + S w per unknown, with cnt the blocks in
     the window at that iteration (min(k - 1, m) for update k), averaged over
@@ -1355,8 +1355,9 @@ def bench_net_kernels(args):
     """Throughput of the learned column's tensor-core kernels on their own:
     inference (mg_learned_forward, 4 images of the 1025^2 field) and one
     training forward + backward pass (mg_learned_grad, 8 pairs of a 257^2
-    field; --nodes sets the training grid).  Also the driver of the ncu
-    captures of these kernels."""
+    field; --nodes sets the training grid), then the same for the 3D network
+    on the 65^3 elasticity grid (--nodes3 sets its training grid).  The ncu
+    captures of these kernels run this workload."""
     import numpy as np
     import torch
     from paper_2402_12833_gb300 import build as _build
