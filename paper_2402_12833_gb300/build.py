@@ -49,7 +49,11 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         s = os.path.join(SRC, src)
         o = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
         objs.append(o)
-        if force or _stale(o, [s] + headers):
+        # a translation unit that includes another .cu (stencil_dw.cu) depends on it
+        with open(s) as f:
+            inc = [os.path.join(SRC, ln.split('"')[1]) for ln in f
+                   if ln.startswith('#include "') and ln.split('"')[1].endswith(".cu")]
+        if force or _stale(o, [s] + headers + inc):
             host = HOST_FLAGS if src.endswith(".cpp") else []
             cmd = [nvcc(), *ARCH, *FLAGS, *host, *(extra or []), "-c", s, "-o", o]
             jobs.append(cmd)

@@ -470,8 +470,12 @@ void enqueue_smooth(mg_hierarchy* h, Solver<T>& S, int j, const T* rr, T* out, c
     T* t = S.tmp2[j];
     LAUNCH(h, K_JACOBI, s, launch_vblock<T>(L.g, di, rr, nullptr, sv, state, s));
     for (int k = 2; k <= nu; ++k) {
-      LAUNCH(h, K_JACOBI, s, launch_vres<T>(L.g, st, rr, sv, t, state, s));
-      LAUNCH(h, K_JACOBI, s, launch_vblock<T>(L.g, di, t, sv, k == nu ? out : sv, state, s));
+      if (k == nu) {   // the last sweep writes `out`, not s: one fused pass
+        LAUNCH(h, K_JACOBI, s, launch_vres_block<T>(L.g, st, rr, sv, di, out, state, s));
+      } else {
+        LAUNCH(h, K_JACOBI, s, launch_vres<T>(L.g, st, rr, sv, t, state, s));
+        LAUNCH(h, K_JACOBI, s, launch_vblock<T>(L.g, di, t, sv, sv, state, s));
+      }
     }
     return;
   }

@@ -113,6 +113,10 @@ void launch_jacobi(const GridDesc& g, const T* st, const T* dinv, const T* r, co
 template <typename T>
 void launch_vres(const GridDesc& g, const T* st, const T* r, const T* x, T* t, const DevState* state,
                  cudaStream_t s);
+// the last block-Jacobi sweep fused: out = x + dinv (r - A x), out != x
+template <typename T>
+void launch_vres_block(const GridDesc& g, const T* st, const T* r, const T* x, const T* dinv, T* out,
+                       const DevState* state, cudaStream_t s);
 template <typename T>
 void launch_vblock(const GridDesc& g, const T* dinv, const T* t, const T* sin, T* out, const DevState* state,
                    cudaStream_t s);

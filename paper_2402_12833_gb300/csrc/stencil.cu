@@ -854,6 +854,70 @@ __global__ void __launch_bounds__(kBlock) k_vblock(GridDesc g, const T* __restri
   }
 }
 
+// The last block-Jacobi sweep in one pass: t = b - A x for the three
+// components of a node group (the arithmetic of k_vres), then
+// out = x + dinv t (that of k_vblock); out must not alias x (x is read at
+// the neighbours).  Bitwise the results of k_vres followed by k_vblock.
+template <typename T>
+__global__ void __launch_bounds__(kBlock, 3) k_vres_block(GridDesc g, const T* __restrict__ st,
+                                                          const T* __restrict__ b, const T* __restrict__ xv,
+                                                          const T* __restrict__ dinv, T* __restrict__ out,
+                                                          const DevState* state) {
+  const int pb = blockIdx.y;
+  if (state && state[pb].done) return;
+  constexpr int W = Vec<T>::W;
+  const long long bo = (long long)pb * g.len;
+  const long long cs = g.cstride;
+  const long long ngroups = cs / W;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ngroups;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long idx0 = bo + g.G + q * W;
+    T tv[3][W];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T acc[W];
+#pragma unroll
+      for (int w = 0; w < W; ++w) acc[w] = 0;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const long long ro = row_offset<3>(k, g.px, g.pxy);
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+          const T* sp = st + (long long)(bb * 27 + 3 * k) * g.cp + idx0 + a * cs;
+          T a0[W], a1[W], a2[W], e[W + 2];
+          Vec<T>::load(sp, a0);
+          Vec<T>::load(sp + g.cp, a1);
+          Vec<T>::load(sp + 2 * g.cp, a2);
+          load_row<T>(xv + idx0 + bb * cs + ro, e);
+#pragma unroll
+          for (int w = 0; w < W; ++w) {
+            acc[w] = fma(a0[w], e[w], acc[w]);
+            acc[w] = fma(a1[w], e[w + 1], acc[w]);
+            acc[w] = fma(a2[w], e[w + 2], acc[w]);
+          }
+        }
+      }
+      T bv[W];
+      Vec<T>::load(b + idx0 + a * cs, bv);
+#pragma unroll
+      for (int w = 0; w < W; ++w) tv[a][w] = bv[w] - acc[w];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T o[W];
+      Vec<T>::load_keep(xv + idx0 + a * cs, o);
+#pragma unroll
+      for (int bb = 0; bb < 3; ++bb) {
+        T d[W];
+        Vec<T>::load_keep(dinv + (long long)bb * g.cp + idx0 + a * cs, d);
+#pragma unroll
+        for (int w = 0; w < W; ++w) o[w] = fma(d[w], tv[bb][w], o[w]);
+      }
+      Vec<T>::store(out + idx0 + a * cs, o);
+    }
+  }
+}
+
 inline int blocks_for(long long n) { return (int)((n + kBlock - 1) / kBlock); }
 
 template <typename T>
@@ -1025,6 +1089,18 @@ template void launch_vres<double>(const GridDesc&, const double*, const double*,
                                   const DevState*, cudaStream_t);
 template void launch_vres<float>(const GridDesc&, const float*, const float*, const float*, float*,
                                  const DevState*, cudaStream_t);
+#endif
+
+template <typename T>
+void launch_vres_block(const GridDesc& g, const T* st, const T* r, const T* x, const T* dinv, T* out,
+                       const DevState* state, cudaStream_t s) {
+  k_vres_block<T><<<dim3(blocks_for(g.cstride / vw<T>()), g.nb), kBlock, 0, s>>>(g, st, r, x, dinv, out, state);
+}
+#ifndef MPCG_STENCIL_DW
+template void launch_vres_block<double>(const GridDesc&, const double*, const double*, const double*,
+                                        const double*, double*, const DevState*, cudaStream_t);
+template void launch_vres_block<float>(const GridDesc&, const float*, const float*, const float*, const float*,
+                                       float*, const DevState*, cudaStream_t);
 #endif
 
 template <typename T>
@@ -1223,6 +1299,8 @@ template void launch_jacobi<dw>(const GridDesc&, const dw*, const dw*, const dw*
 template void launch_vres<dw>(const GridDesc&, const dw*, const dw*, const dw*, dw*, const DevState*, cudaStream_t);
 template void launch_vblock<dw>(const GridDesc&, const dw*, const dw*, const dw*, dw*, const DevState*,
                                 cudaStream_t);
+template void launch_vres_block<dw>(const GridDesc&, const dw*, const dw*, const dw*, const dw*, dw*,
+                                    const DevState*, cudaStream_t);
 template void launch_sum_columns<dw>(const GridDesc&, const dw*, int, dw*, const DevState*, cudaStream_t);
 template void launch_coarse_tail<dw>(int, const GridDesc*, const dw* const*, const dw* const*, dw* const*,
                                      dw* const*, const dw*, const double*, const DevState*, cudaStream_t);
