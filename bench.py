@@ -116,7 +116,8 @@ def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops, S=27, vector=False
     The grid of each multilevel launch follows the launch order of one MG
     chain: the smoothings of grids J, J-1, ..., 1 (nu = 2: one fused launch
     each; vector problems: the first sweep, then the second sweep's
-    residual and block update fused in one launch, per grid), the
+    residual and block update -- one launch on the fine grid, two on the
+    coarser ones), the
     restrictions from grids J, ..., 1, one composite prolongation."""
     J = len(ns) - 1
     jsub = 0
@@ -137,12 +138,20 @@ def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops, S=27, vector=False
         if cls in ("init", "check"):
             jj, jr, jp, jsub = J, J, 1, 0
         if cls == "jacobi" and vector:
+            fused = ns[jj] // 3 >= (1 << 17) * 0.9   # the fine grids whose last sweep is one launch
             if jsub == 0:     # s1 = D^-1 r: read r, 3 inverse-block planes; write s1
                 b, f = 5 * w * ns[jj], 2 * 3 * ns[jj]
-            else:             # fused last sweep s = s1 + D^-1 (r - A s1): read S planes, s1, r, 3 planes; write s
+            elif fused:       # s = s1 + D^-1 (r - A s1) in one launch: read S planes, s1, r, 3 planes; write s
                 b, f = (S + 6) * w * ns[jj], 2 * (S + 3) * ns[jj]
+            elif jsub == 1:   # t = r - A s1: read S planes, s1, r; write t
+                b, f = (S + 3) * w * ns[jj], 2 * S * ns[jj]
+            else:             # s = s1 + D^-1 t: read t, s1, 3 planes; write s
+                b, f = 6 * w * ns[jj], 2 * 3 * ns[jj]
+            if jsub == 2 or (jsub == 1 and fused):
                 jj -= 1
-            jsub = (jsub + 1) % 2
+                jsub = 0
+            else:
+                jsub += 1
         elif cls == "jacobi":
             Sj = s_fine if (s_fine is not None and jj == J) else S   # matrix-free fine grid: kappa, not stencil
             b, f = (Sj + 3) * w * ns[jj], (2 * S + 4) * ns[jj]

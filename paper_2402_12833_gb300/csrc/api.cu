@@ -469,12 +469,17 @@ void enqueue_smooth(mg_hierarchy* h, Solver<T>& S, int j, const T* rr, T* out, c
     T* sv = nu == 1 ? out : S.tmp[j];
     T* t = S.tmp2[j];
     LAUNCH(h, K_JACOBI, s, launch_vblock<T>(L.g, di, rr, nullptr, sv, state, s));
+    // the last sweep writes `out`, not s: one fused pass on grids of at
+    // least 2^17 nodes (the fine grid of the 65^3 problem); on smaller grids
+    // its three components per thread leave too few threads (measured
+    // 28-30 us against 17-19 us for the two launches)
+    const bool fuse = L.g.cstride >= (1LL << 17);
     for (int k = 2; k <= nu; ++k) {
-      if (k == nu) {   // the last sweep writes `out`, not s: one fused pass
+      if (k == nu && fuse) {
         LAUNCH(h, K_JACOBI, s, launch_vres_block<T>(L.g, st, rr, sv, di, out, state, s));
       } else {
         LAUNCH(h, K_JACOBI, s, launch_vres<T>(L.g, st, rr, sv, t, state, s));
-        LAUNCH(h, K_JACOBI, s, launch_vblock<T>(L.g, di, t, sv, sv, state, s));
+        LAUNCH(h, K_JACOBI, s, launch_vblock<T>(L.g, di, t, sv, k == nu ? out : sv, state, s));
       }
     }
     return;
