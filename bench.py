@@ -87,16 +87,29 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------- algorithmic bytes / flops
+# Stored stencil coefficients per unknown that a kernel streams: the full
+# stencil (3^dim taps, 81 for 3D elasticity), or for the FP32 scalar kernels
+# of the mixed precision its symmetric half (the diagonal and the couplings
+# to the later neighbours: 14 of 27 in 3D, 5 of 9 in 2D).
+def stencil_words(dim: int, w: int, vector: bool = False) -> int:
+    if vector:
+        return 81
+    full = 3 ** dim
+    return full // 2 + 1 if w == 4 else full
+
+
 def kernel_work(cls: str, n: int, C: int, cnt: int, w: int, S: int = 27):
     """Algorithmic HBM bytes and flops of one launch on the fine grid (per
     unknown figures x n; cnt = blocks in the window at that launch; S =
-    stencil coefficients per unknown: 27 for 3D scalar, 81 for elasticity)."""
+    stored stencil coefficients per unknown, stencil_words).  The flops
+    count the full stencil's products whatever is stored."""
     if cls == "orth_update":      # read Z, AZ, P_j, AP_j, r; write P, AP; sym Gram + P^T r
         return (2 * cnt * C + 4 * C + 1) * w * n, 2 * (2 * cnt * C * C + C * (C + 1) + C) * n
     if cls == "gram_window":      # read AP_j, Z
         return (cnt + 1) * C * w * n, 2 * cnt * C * C * n
     if cls == "spmm":             # read stencil, Z; write AZ (+ Z^T AZ)
-        return (S + 2 * C) * w * n, 2 * (S * C + C) * n
+        taps = 81 if S == 81 else (27 if S > 9 else 9)
+        return (S + 2 * C) * w * n, 2 * (taps * C + C) * n
     if cls == "update_xr":        # read P, AP, x, r; write x, r
         return (2 * C + 4) * w * n, 2 * (2 * C + 1) * n
     if cls == "orth_gram":        # double-word: read the new P, AP and r; sym Gram + P^T r
@@ -154,7 +167,8 @@ def roofline(trace, ns, C, m, w, peaks, fp64_alu_peak_tflops, S=27, vector=False
                 jsub += 1
         elif cls == "jacobi":
             Sj = s_fine if (s_fine is not None and jj == J) else S   # matrix-free fine grid: kappa, not stencil
-            b, f = (Sj + 3) * w * ns[jj], (2 * S + 4) * ns[jj]
+            taps = 27 if S > 9 else 9
+            b, f = (Sj + 3) * w * ns[jj], (2 * taps + 4) * ns[jj]
             jj -= 1
         elif cls == "restrict":
             b, f = (ns[jr] + ns[jr - 1]) * w, 2 * 27 * ns[jr - 1]
@@ -522,7 +536,7 @@ def bench_ours(args):
     x.zero_()
     _, _, _, trace_mf = M.mpcg_solve_profiled(Hmf.h, b, x, RTOL, MAXIT)
     _, mf["roofline"], _, tot_mf = roofline(trace_mf, level_dofs(NODES, DIM, prob.levels), prob.levels, M_WINDOW, 4,
-                                            peaks, FP64_PEAK_TFLOPS, s_fine=1)
+                                            peaks, FP64_PEAK_TFLOPS, S=stencil_words(DIM, 4), s_fine=1)
     if mf["roofline"] is not None:
         mf["roofline"]["traffic"] = measured_traffic(f"poisson3d_mixed_mf:{mf['roofline']['kernel']}")
     mf["class_ms"] = {c: round(v, 4) for c, v in tot_mf.items()}
@@ -536,7 +550,8 @@ def bench_ours(args):
         # FP64 arithmetic is bound by the FP64 pipe; the double-word kernels
         # are reported against the HBM roofline they aim at
         dom, rl, share, tot = roofline(trace, level_dofs(NODES, DIM, prob.levels), prob.levels, M_WINDOW, w, peaks,
-                                       FP64_PEAK_TFLOPS if key == "fp64" else None)
+                                       FP64_PEAK_TFLOPS if key == "fp64" else None,
+                                       S=stencil_words(DIM, 4 if key == "mixed" else 8))
         if rl is not None:
             rl["traffic"] = measured_traffic(f"poisson3d_{key}:{dom}")
         prof[key] = {"roofline": rl, "class_ms": {c: round(v, 4) for c, v in tot.items()}}
@@ -548,7 +563,7 @@ def bench_ours(args):
     piter = {}
     for key, w in (("mixed", 4), ("fp64", 8), ("fp64_dw", 8)):
         piter[key] = per_iteration(f"poisson3d_{key}", res[key]["ms_per_step"], res[key]["iters"], n, prob.levels,
-                                   M_WINDOW, w, 27, peaks)
+                                   M_WINDOW, w, stencil_words(DIM, w), peaks)
 
     # end to end through the C ABI with pinned host buffers
     bh = torch.from_numpy(prob.b).pin_memory().numpy()
@@ -719,7 +734,8 @@ def bench_batched(args):
     checks = [i for i, (c, _) in enumerate(trace) if c == "check"]
     head = trace[:checks[4] + 1] if len(checks) >= 5 else trace
     nprob = len(by[big])
-    _, rl, _, tot1 = roofline(head, ns1, p0.levels, M_WINDOW, 4, load_peaks(), FP64_PEAK_TFLOPS, S=9)
+    _, rl, _, tot1 = roofline(head, ns1, p0.levels, M_WINDOW, 4, load_peaks(), FP64_PEAK_TFLOPS,
+                              S=stencil_words(2, 4))
     if rl is not None:
         for k in ("achieved", "frac", "algorithmic_bytes_per_launch"):
             rl[k] *= nprob

@@ -363,6 +363,20 @@ mpcg_status mg_apply_operator(mg_hierarchy* h, int level, const double* X_dev,
  */
 mpcg_status mg_corrections(mg_hierarchy* h, const double* r_dev, double* Z_dev);
 
+/*
+ * The FP32 arithmetic of the mixed precision's inner solves, for testing it
+ * against FP64: mg_apply_operator and mg_corrections with the data rounded to
+ * FP32 on entry and the FP32 kernels of the inner iterations (on scalar
+ * grids, the stored stencil's symmetric half: the diagonal and the couplings
+ * to the lexicographically later neighbours, the others read transposed as
+ * A(i, i - s) = A(i - s, i)).  Same arguments and layouts as the FP64 calls;
+ * results are returned as doubles.  MPCG_ERR_ARG unless h is a single
+ * stencil hierarchy built with precision MPCG_MIXED.
+ */
+mpcg_status mg_apply_operator_f32(mg_hierarchy* h, int level, const double* X_dev,
+                                  double* Y_dev, int ncols);
+mpcg_status mg_corrections_f32(mg_hierarchy* h, const double* r_dev, double* Z_dev);
+
 /* Copy grid `level`'s Galerkin operator in the stencil format above into
  * planes_dev (3^dim * n_level doubles, device). */
 mpcg_status mg_get_operator(mg_hierarchy* h, int level, double* planes_dev);   /* stencil hierarchies */

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT, "libmpcg.so")
-SOURCES = ["api.cu", "stencil.cu", "stencil_dw.cu", "block.cu", "small.cu", "matfree.cu", "ell.cu", "learned.cu", "learned_tc.cu", "learned_train_tc.cu", "learned3_tc.cu",
+SOURCES = ["api.cu", "stencil.cu", "stencil_dw.cu", "stencil_sym.cu", "block.cu", "small.cu", "matfree.cu", "ell.cu", "learned.cu", "learned_tc.cu", "learned_train_tc.cu", "learned3_tc.cu",
            "batch.cu", "noalloc.cu", "amg_setup.cpp", "tune.cpp"]
 # host-only units: no fused multiply-add contraction, so the hierarchy built on
 # the host rounds the same way on every machine

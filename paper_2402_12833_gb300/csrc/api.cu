@@ -77,6 +77,7 @@ struct Level {
   int ndinv = 0;     // inverse-diagonal planes: ncomp
   double* st64 = nullptr;
   float* st32 = nullptr;
+  float* sth32 = nullptr;        // scalar grids: the symmetric half of st32 (FP32 SpMM and smoothing)
   double* dinv64 = nullptr;
   float* dinv32 = nullptr;
   dw* stdw = nullptr;            // double-word copies (MPCG_FP64_DW)
@@ -432,6 +433,20 @@ void enqueue_ssor_steps(mg_hierarchy* h, int j, const T* rr, T* x, int k, const 
   }
 }
 
+// Damped-Jacobi launch of a scalar stencil grid (modes as launch_jacobi):
+// FP32 reads the symmetric half where the grid has one.
+template <typename T>
+void jacobi_of(const Level& L, const T* st, const T* di, const T* rr, const T* sin, T* out, int mode,
+               const DevState* state, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (L.sth32) {
+      launch_jacobi_sym(L.g, L.sth32, di, rr, sin, out, mode, state, s);
+      return;
+    }
+  }
+  launch_jacobi<T>(L.g, st, di, rr, sin, out, mode, state, s);
+}
+
 template <typename T>
 void enqueue_smooth(mg_hierarchy* h, Solver<T>& S, int j, const T* rr, T* out, const DevState* state,
                     cudaStream_t s) {
@@ -491,16 +506,16 @@ void enqueue_smooth(mg_hierarchy* h, Solver<T>& S, int j, const T* rr, T* out, c
     }
   }
   if (nu == 1) {
-    LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, nullptr, out, 0, state, s));
+    LAUNCH(h, K_JACOBI, s, jacobi_of<T>(L, st, di, rr, nullptr, out, 0, state, s));
   } else if (nu == 2) {
-    LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, nullptr, out, 1, state, s));
+    LAUNCH(h, K_JACOBI, s, jacobi_of<T>(L, st, di, rr, nullptr, out, 1, state, s));
   } else {
     T* a = S.tmp[j];
     T* b = S.tmp2[j];
-    LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, nullptr, a, 1, state, s));
+    LAUNCH(h, K_JACOBI, s, jacobi_of<T>(L, st, di, rr, nullptr, a, 1, state, s));
     for (int k = 3; k <= nu; ++k) {
       T* o = k == nu ? out : b;
-      LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st, di, rr, a, o, 2, state, s));
+      LAUNCH(h, K_JACOBI, s, jacobi_of<T>(L, st, di, rr, a, o, 2, state, s));
       T* t = a;
       a = b;
       b = t;
@@ -656,7 +671,7 @@ void jacobi_sweep(mg_hierarchy* h, int j, const T* g, const T* xin, T* xout, int
            launch_ell_jacobi<T>(ell_of<T>(L.eA), dinv_of<T>(L) + G, g + G, xin ? xin + G : nullptr, xout + G, mode,
                                 state, s));
   } else {
-    LAUNCH(h, K_JACOBI, s, launch_jacobi<T>(L.g, st_of<T>(L), dinv_of<T>(L), g, xin, xout, mode, state, s));
+    LAUNCH(h, K_JACOBI, s, jacobi_of<T>(L, st_of<T>(L), dinv_of<T>(L), g, xin, xout, mode, state, s));
   }
 }
 
@@ -786,6 +801,9 @@ void enqueue_body(mg_hierarchy* h, Solver<T>& S, cudaGraphConditionalHandle cond
     if (!mf && L.kq32 && C <= 12) {   // fine operator rebuilt from the element coefficients
       LAUNCH(h, K_SPMM, s,
              launch_spmm_mf(L.g, L.kq32, S.Z, S.AZ, C, spmm_blocks<T>(L.g, C), S.part_zaz, S.state, s));
+      mf = true;
+    } else if (!mf && L.sth32) {   // the symmetric half of the stored stencil
+      LAUNCH(h, K_SPMM, s, launch_spmm_sym(L.g, L.sth32, S.Z, S.AZ, C, S.part_zaz, S.state, s));
       mf = true;
     }
   }
@@ -943,6 +961,10 @@ mpcg_status build_f32(mg_hierarchy* h) {
     CKS(h->mem.get(&L.dinv32, (size_t)L.ndinv * L.g.cp, s));
     launch_convert_f32(L.st64, L.st32, (long long)L.nplanes * L.g.cp, s);
     launch_convert_f32(L.dinv64, L.dinv32, (long long)L.ndinv * L.g.cp, s);
+    if (L.g.ncomp == 1) {   // the FP32 SpMM and Jacobi stream the symmetric half: 14 of 27 (5 of 9) planes
+      CKS(h->mem.get(&L.sth32, (size_t)sym_planes(L.g.dim) * L.g.cp, s));
+      launch_sym_half(L.g, L.st64, L.sth32, s);
+    }
   }
   const GridDesc& gf = h->lev[h->levels - 1].g;
   CKS(h->mem.get(&h->b64, gf.cp, s));
@@ -2490,6 +2512,70 @@ mpcg_status mg_corrections(mg_hierarchy* h, const double* r, double* Z) {
     double* Zc = h->opt.sum_columns ? S.Zmg : S.Z;   // the per-grid columns
     enqueue_mg<double>(h, S, S.r, Zc, nullptr, s);
     launch_unpack<double, double>(gf, Zc, Z, gf.n, h->levels, s);
+  }
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  return MPCG_OK;
+}
+
+mpcg_status mg_apply_operator_f32(mg_hierarchy* h, int level, const double* X, double* Y, int ncols) {
+  g_err.clear();
+  CKS(check_single(h));
+  if (level < 0 || level >= h->levels || ncols < 1 || !X || !Y) {
+    set_err("bad level, column count or pointer");
+    return MPCG_ERR_ARG;
+  }
+  if (h->algebraic || h->opt.precision != MPCG_MIXED) {
+    set_err("the FP32 operators exist on stencil hierarchies built with precision MPCG_MIXED");
+    return MPCG_ERR_ARG;
+  }
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = h->stream;
+  const Level& L = h->lev[level];
+  float *xp = nullptr, *yp = nullptr;
+  const int maxc = L.g.ncomp > 1 ? kMaxVecCols : kMaxCols;
+  const int chunk = ncols < maxc ? ncols : maxc;
+  CK(cudaMalloc(&xp, sizeof(float) * chunk * L.g.len));
+  CK(cudaMalloc(&yp, sizeof(float) * chunk * L.g.len));
+  cudaMemsetAsync(xp, 0, sizeof(float) * chunk * L.g.len, s);
+  for (int c0 = 0; c0 < ncols; c0 += chunk) {
+    const int nc = ncols - c0 < chunk ? ncols - c0 : chunk;
+    launch_pack<double, float>(L.g, X + (size_t)c0 * L.g.n, L.g.n, xp, nc, s);
+    if (L.sth32) launch_spmm_sym(L.g, L.sth32, xp, yp, nc, nullptr, nullptr, s);
+    else launch_spmm<float>(L.g, L.st32, xp, yp, nc, nullptr, nullptr, s);
+    launch_unpack<float, double>(L.g, yp, Y + (size_t)c0 * L.g.n, L.g.n, nc, s);
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(xp);
+  cudaFree(yp);
+  CK(e);
+  CK(cudaGetLastError());
+  return MPCG_OK;
+}
+
+mpcg_status mg_corrections_f32(mg_hierarchy* h, const double* r, double* Z) {
+  g_err.clear();
+  CKS(check_single(h));
+  if (!r || !Z) {
+    set_err("NULL pointer");
+    return MPCG_ERR_ARG;
+  }
+  if (h->algebraic || h->opt.precision != MPCG_MIXED) {
+    set_err("the FP32 operators exist on stencil hierarchies built with precision MPCG_MIXED");
+    return MPCG_ERR_ARG;
+  }
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = h->stream;
+  Solver<float>& S = h->s32;
+  const GridDesc& gf = h->lev[h->levels - 1].g;
+  launch_pack<double, float>(gf, r, gf.n, S.r, 1, s);
+  if (h->opt.vcycle) {
+    enqueue_vcycle<float>(h, S, S.r, S.Z, nullptr, s);
+    launch_unpack<float, double>(gf, S.Z, Z, gf.n, 1, s);
+  } else {
+    float* Zc = h->opt.sum_columns ? S.Zmg : S.Z;
+    enqueue_mg<float>(h, S, S.r, Zc, nullptr, s);
+    launch_unpack<float, double>(gf, Zc, Z, gf.n, h->levels, s);
   }
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());

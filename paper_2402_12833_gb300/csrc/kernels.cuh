@@ -108,6 +108,18 @@ void launch_restrict(const GridDesc& gf, const GridDesc& gc, const T* rf, T* rc,
 template <typename T>
 void launch_jacobi(const GridDesc& g, const T* st, const T* dinv, const T* r, const T* sin, T* out,
                    int mode, const DevState* state, cudaStream_t s);
+// ---- stencil_sym.cu: FP32 on the symmetric half of a scalar stencil ------
+// Planes of the half: 14 (3D) or 5 (2D), the diagonal and the couplings to
+// the lexicographically later neighbours, same pitch (cp) as the full planes.
+int sym_planes(int dim);
+// half (sym_planes(g.dim) * g.cp floats) from the full FP64 planes st;
+// couplings with a pad row or column stored as zero
+void launch_sym_half(const GridDesc& g, const double* st, float* half, cudaStream_t s);
+// launch_spmm<float> and launch_jacobi<float> (scalar grids) reading the half
+void launch_spmm_sym(const GridDesc& g, const float* half, const float* X, float* Y, int C, double* zaz,
+                     const DevState* state, cudaStream_t s);
+void launch_jacobi_sym(const GridDesc& g, const float* half, const float* dinv, const float* r, const float* sin,
+                       float* out, int mode, const DevState* state, cudaStream_t s);
 // Vector operators (3 unknowns per node): t = r - A x (one sweep's residual)
 // and the block-Jacobi update out = (sin or 0) + dinv t (in place allowed).
 template <typename T>

@@ -14,6 +14,15 @@
 #include "tune.h"
 #include "vec.cuh"
 
+// stencil.cu compiles the float / double instances; stencil_dw.cu
+// (MPCG_STENCIL_DW) the double-word ones and stencil_sym.cu
+// (MPCG_STENCIL_SYM) the FP32 kernels on the symmetric half of the stencil.
+#if defined(MPCG_STENCIL_DW) || defined(MPCG_STENCIL_SYM)
+#define MPCG_STENCIL_PLAIN 0
+#else
+#define MPCG_STENCIL_PLAIN 1
+#endif
+
 namespace mpcg {
 
 namespace {
@@ -104,9 +113,72 @@ __device__ __forceinline__ long long row_offset(int k, long long px, long long p
   return dy * px + dz * pxy;
 }
 
+// o[w] = p[w - 1] and o[w] = p[w + 1] for the W values of a group: one
+// aligned vector load (evict-first) and one scalar.
+template <typename T, int W>
+__device__ __forceinline__ void load_left(const T* __restrict__ p, T (&o)[W]) {
+  if constexpr (W > 1) {
+    T v[W];
+    VecN<T, W>::load(p, v);
+#pragma unroll
+    for (int w = 1; w < W; ++w) o[w] = v[w - 1];
+  }
+  o[0] = p[-1];
+}
+template <typename T, int W>
+__device__ __forceinline__ void load_right(const T* __restrict__ p, T (&o)[W]) {
+  if constexpr (W > 1) {
+    T v[W];
+    VecN<T, W>::load(p, v);
+#pragma unroll
+    for (int w = 0; w + 1 < W; ++w) o[w] = v[w + 1];
+  }
+  o[W - 1] = p[W];
+}
+
+// The three couplings a_j = A(i, i + (j - 1) + ro) of stencil row k (row
+// offset ro) for the W points i of the group at idx.
+//   SYM = false: the full stencil, plane 3k + j at the point itself.
+//   SYM = true: the symmetric half (launch_sym_half: plane p holds tap
+//   3^dim / 2 + p, the diagonal and the couplings to the later neighbours).
+//   A coupling to an earlier neighbour is read transposed, A(i, i - s) =
+//   A(i - s, i), from the mirrored tap's plane at the neighbour: rows before
+//   the centre row read the mirrored row's three planes at i + ro shifted by
+//   -1, 0, +1; the centre row reads its x-1 coupling from the x+1 plane at
+//   i - 1.  The later rows' planes are loaded with the default caching, since
+//   the groups behind read them again transposed.
+template <typename T, int DIM, int W, bool SYM>
+__device__ __forceinline__ void row_coeffs(const T* __restrict__ st, long long pitch, long long idx, long long ro,
+                                           int k, T (&a0)[W], T (&a1)[W], T (&a2)[W]) {
+  if constexpr (!SYM) {
+    VecN<T, W>::load(st + (long long)(3 * k + 0) * pitch + idx, a0);
+    VecN<T, W>::load(st + (long long)(3 * k + 1) * pitch + idx, a1);
+    VecN<T, W>::load(st + (long long)(3 * k + 2) * pitch + idx, a2);
+  } else {
+    constexpr int R = DIM == 3 ? 9 : 3, kc = R / 2, tc = 3 * kc + 1;
+    if (k > kc) {
+      VecN<T, W>::load_keep(st + (long long)(3 * k + 0 - tc) * pitch + idx, a0);
+      VecN<T, W>::load_keep(st + (long long)(3 * k + 1 - tc) * pitch + idx, a1);
+      VecN<T, W>::load_keep(st + (long long)(3 * k + 2 - tc) * pitch + idx, a2);
+    } else if (k == kc) {
+      VecN<T, W>::load(st + idx, a1);
+      VecN<T, W>::load_keep(st + pitch + idx, a2);
+#pragma unroll
+      for (int w = 1; w < W; ++w) a0[w] = a2[w - 1];
+      a0[0] = st[pitch + idx - 1];
+    } else {
+      const int km = R - 1 - k;
+      load_left<T, W>(st + (long long)(3 * km + 2 - tc) * pitch + idx + ro, a0);
+      VecN<T, W>::load(st + (long long)(3 * km + 1 - tc) * pitch + idx + ro, a1);
+      load_right<T, W>(st + (long long)(3 * km + 0 - tc) * pitch + idx + ro, a2);
+    }
+  }
+}
+
 // acc[c][w] += sum over the stencil of A(point w) * X_c(neighbour), C columns;
-// pitch = distance between stencil planes and between columns.
-template <typename T, int DIM, int C>
+// pitch = distance between stencil planes and between columns; SYM as
+// row_coeffs.
+template <typename T, int DIM, int C, bool SYM = false>
 __device__ __forceinline__ void stencil_group(const T* __restrict__ st, long long pitch, const T* __restrict__ X,
                                               long long idx, long long px, long long pxy,
                                               T (&acc)[C][Vec<T>::W]) {
@@ -116,9 +188,7 @@ __device__ __forceinline__ void stencil_group(const T* __restrict__ st, long lon
   for (int k = 0; k < R; ++k) {
     const long long ro = row_offset<DIM>(k, px, pxy);
     T a0[W], a1[W], a2[W];
-    Vec<T>::load(st + (long long)(3 * k + 0) * pitch + idx, a0);
-    Vec<T>::load(st + (long long)(3 * k + 1) * pitch + idx, a1);
-    Vec<T>::load(st + (long long)(3 * k + 2) * pitch + idx, a2);
+    row_coeffs<T, DIM, W, SYM>(st, pitch, idx, ro, k, a0, a1, a2);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       T e[W + 2];
@@ -136,7 +206,7 @@ __device__ __forceinline__ void stencil_group(const T* __restrict__ st, long lon
 // The FP32 3D instances with up to 6 columns run three blocks per SM (at most
 // 85 registers) in one wave of resident blocks (spmm_blocks): measured faster
 // than two blocks per SM over two waves, whose loads wait longer.
-template <typename T, int DIM, int C, bool ZAZ>
+template <typename T, int DIM, int C, bool ZAZ, bool SYM = false>
 __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && DIM == 3 && C <= 6) ? 3 : (kIsDw<T> ? 2 : 1)) k_spmm(GridDesc g, const T* __restrict__ st, const T* __restrict__ X,
                                                  T* __restrict__ Y, double* zaz, const DevState* state) {
   const int pb = blockIdx.y;
@@ -155,7 +225,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && DIM == 3 && C <= 6)
     for (int c = 0; c < C; ++c)
 #pragma unroll
       for (int w = 0; w < W; ++w) acc[c][w] = 0;
-    stencil_group<T, DIM, C>(st, g.cp, X, idx, g.px, g.pxy, acc);
+    stencil_group<T, DIM, C, SYM>(st, g.cp, X, idx, g.px, g.pxy, acc);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       Vec<T>::store(Y + (long long)c * g.cp + idx, acc[c]);
@@ -248,8 +318,9 @@ __global__ void __launch_bounds__(kBlock) k_restrict(GridDesc gf, GridDesc gc, c
 //   mode 2: out = sin + dinv (r - A sin)           (a further sweep)
 //   W points per thread: Vec<T>::W (one vector load), or 1 on the small
 //   grids (modes 0 and 1; mode 2 keeps Vec<T>::W).  Every point's
-//   arithmetic is the same whatever W.
-template <typename T, int DIM, int W = Vec<T>::W>
+//   arithmetic is the same whatever W.  SYM: st is the symmetric half
+//   (row_coeffs).
+template <typename T, int DIM, int W = Vec<T>::W, bool SYM = false>
 __global__ void __launch_bounds__(kBlock, 4) k_jacobi(GridDesc g, const T* __restrict__ st, const T* __restrict__ dinv,
                                                    const T* __restrict__ r, const T* __restrict__ sin,
                                                    T* __restrict__ out, int mode, const DevState* state) {
@@ -284,11 +355,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_jacobi(GridDesc g, const T* __res
     for (int k = 0; k < R; ++k) {
       const long long ro = row_offset<DIM>(k, g.px, g.pxy);
       T a0[W] = {}, a1[W] = {}, a2[W] = {}, ed[W + 2], er[W + 2];
-      if (active) {
-        VecN<T, W>::load(st + (long long)(3 * k + 0) * g.cp + idx, a0);
-        VecN<T, W>::load(st + (long long)(3 * k + 1) * g.cp + idx, a1);
-        VecN<T, W>::load(st + (long long)(3 * k + 2) * g.cp + idx, a2);
-      }
+      if (active) row_coeffs<T, DIM, W, SYM>(st, g.cp, idx, ro, k, a0, a1, a2);
       load_row_shfl<T, W>(dinv + idx + ro, ed, active, act, lane);
       load_row_shfl<T, W>(r + idx + ro, er, active, act, lane);
 #pragma unroll
@@ -305,7 +372,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_jacobi(GridDesc g, const T* __res
     }
   } else if constexpr (W == Vec<T>::W) {   // mode 2 (the launcher uses the full width for it)
     if (!active) return;
-    stencil_group<T, DIM, 1>(st, g.cp, sin, idx, g.px, g.pxy, acc);
+    stencil_group<T, DIM, 1, SYM>(st, g.cp, sin, idx, g.px, g.pxy, acc);
     T sv[W];
     Vec<T>::load_keep(sin + idx, sv);
 #pragma unroll
@@ -690,6 +757,31 @@ __global__ void k_convert_f32(const double* __restrict__ src, float* __restrict_
     dst[i] = (float)src[i];
 }
 
+// The symmetric half of a scalar FP64 stencil in FP32 (A is symmetric, so
+// A(i, i - s) = A(i - s, i) need not be stored twice): plane p = 0 .. S/2
+// (S = 3^dim taps) holds tap S/2 + p, the diagonal and the couplings to the
+// later neighbours (offset dx + dy px + dz pxy > 0).  A coupling whose row or
+// column is not an unknown (pad or guard entry, zero diagonal) is stored as
+// zero, so that the transposed reads leave the rows of pads at zero.  Every
+// entry of the cp-element planes (all problems, guards included) is written.
+template <int DIM>
+__global__ void k_sym_half(GridDesc g, const double* __restrict__ st, float* __restrict__ out) {
+  constexpr int S = DIM == 3 ? 27 : 9, tc = S / 2;
+  const double* diag = st + (long long)tc * g.cp;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.cp;
+       e += (long long)gridDim.x * blockDim.x) {
+    const bool row = diag[e] != 0.0;
+#pragma unroll
+    for (int p = 0; p <= tc; ++p) {
+      const int t = tc + p;
+      const long long off = (t % 3 - 1) + (long long)(t / 3 % 3 - 1) * g.px + (DIM == 3 ? (t / 9 - 1) * g.pxy : 0);
+      const long long nb = e + off;
+      const bool col = nb < g.cp && diag[nb] != 0.0;
+      out[(long long)p * g.cp + e] = row && col ? (float)st[(long long)t * g.cp + e] : 0.0f;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Vector unknowns (3D elasticity, three components per node).  Plane
 // b * 27 + s at the row of component a holds the coupling of unknown
@@ -935,7 +1027,7 @@ void launch_pack_flag(const GridDesc& g, const double* src, TO* dst, int* nz, cu
   k_pack_flag<TO><<<grid_for(g.n, 4096), kBlock, 0, s>>>(g, src, dst, nz);
 }
 
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 int g_sm_count = 0;
 void set_sm_count(int n) { g_sm_count = n; }
 int sm_count() { return g_sm_count; }
@@ -960,7 +1052,7 @@ int spmm_blocks(const GridDesc& g, int C) {
   const int lo = stream_blocks_min(g), hi = stream_blocks_cap(g);
   return v < lo ? lo : (v > hi ? hi : v);
 }
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template int spmm_blocks<double>(const GridDesc&, int);
 template int spmm_blocks<float>(const GridDesc&, int);
 #endif
@@ -969,7 +1061,7 @@ template <typename TI, typename TO>
 void launch_unpack(const GridDesc& g, const TI* src, TO* dst, long long ld, int ncols, cudaStream_t s) {
   k_unpack<TI, TO><<<grid_for(g.n * ncols, 4096), kBlock, 0, s>>>(g, src, dst, ld, ncols);
 }
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_pack<double, double>(const GridDesc&, const double*, long long, double*, int, cudaStream_t);
 template void launch_pack<double, float>(const GridDesc&, const double*, long long, float*, int, cudaStream_t);
 template void launch_unpack<double, double>(const GridDesc&, const double*, double*, long long, int, cudaStream_t);
@@ -978,14 +1070,14 @@ template void launch_pack<float, float>(const GridDesc&, const float*, long long
 template void launch_unpack<float, float>(const GridDesc&, const float*, float*, long long, int, cudaStream_t);
 #endif
 
-template <typename T, int DIM>
+template <typename T, int DIM, bool SYM = false>
 static void spmm_dim(const GridDesc& g, const T* st, const T* X, T* Y, int C, double* zaz, const DevState* state,
                      cudaStream_t s) {
   const dim3 grid(spmm_blocks<T>(g, C), g.nb);
 #define MPCG_SPMM_CASE(CC)                                                                      \
   case CC:                                                                                      \
-    if (zaz) k_spmm<T, DIM, CC, true><<<grid, kBlock, 0, s>>>(g, st, X, Y, zaz, state);         \
-    else k_spmm<T, DIM, CC, false><<<grid, kBlock, 0, s>>>(g, st, X, Y, zaz, state);           \
+    if (zaz) k_spmm<T, DIM, CC, true, SYM><<<grid, kBlock, 0, s>>>(g, st, X, Y, zaz, state);    \
+    else k_spmm<T, DIM, CC, false, SYM><<<grid, kBlock, 0, s>>>(g, st, X, Y, zaz, state);      \
     break;
   switch (C) {
     MPCG_SPMM_CASE(1) MPCG_SPMM_CASE(2) MPCG_SPMM_CASE(3) MPCG_SPMM_CASE(4) MPCG_SPMM_CASE(5)
@@ -1020,7 +1112,7 @@ void launch_spmm(const GridDesc& g, const T* st, const T* X, T* Y, int C, double
   else if (g.dim == 3) spmm_dim<T, 3>(g, st, X, Y, C, zaz, state, s);
   else spmm_dim<T, 2>(g, st, X, Y, C, zaz, state, s);
 }
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_spmm<double>(const GridDesc&, const double*, const double*, double*, int, double*,
                                   const DevState*, cudaStream_t);
 template void launch_spmm<float>(const GridDesc&, const float*, const float*, float*, int, double*,
@@ -1035,7 +1127,7 @@ void launch_residual(const GridDesc& g, const T* st, const T* b, const T* x, T* 
   else if (g.dim == 3) k_residual<T, 3><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part, xnz);
   else k_residual<T, 2><<<grid, kBlock, 0, s>>>(g, st, b, x, r, part, xnz);
 }
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_residual<double>(const GridDesc&, const double*, const double*, const double*, double*,
                                       double*, cudaStream_t, const int*);
 template void launch_residual<float>(const GridDesc&, const float*, const float*, const float*, float*, double*,
@@ -1049,17 +1141,16 @@ void launch_restrict(const GridDesc& gf, const GridDesc& gc, const T* rf, T* rc,
   if (gc.dim == 3) k_restrict<T, 3><<<grid, kBlock, 0, s>>>(gf, gc, rf, rc, state);
   else k_restrict<T, 2><<<grid, kBlock, 0, s>>>(gf, gc, rf, rc, state);
 }
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_restrict<double>(const GridDesc&, const GridDesc&, const double*, double*, const DevState*,
                                       cudaStream_t);
 template void launch_restrict<float>(const GridDesc&, const GridDesc&, const float*, float*, const DevState*,
                                      cudaStream_t);
 #endif
 
-template <typename T>
-void launch_jacobi(const GridDesc& g, const T* st, const T* dinv, const T* r, const T* sin, T* out, int mode,
-                   const DevState* state, cudaStream_t s) {
-  if (g.ncomp != 1) return;   // vector grids smooth with launch_vres / launch_vblock
+template <typename T, bool SYM = false>
+static void jacobi_impl(const GridDesc& g, const T* st, const T* dinv, const T* r, const T* sin, T* out, int mode,
+                        const DevState* state, cudaStream_t s) {
   // one point per thread where Vec<T>::W points per thread would leave fewer
   // than 4 warps per SM (the small coarse grids, latency-bound): more warps
   // in flight, same sums (measured: 33^3 and 17^3 launches 11.9 -> 7.2 us,
@@ -1070,13 +1161,20 @@ void launch_jacobi(const GridDesc& g, const T* st, const T* dinv, const T* r, co
   const bool narrow = mode != 2 && tune::lookup(tune::kJacobi, kind_of<T>(), g.npts, g.nb, 0, narrow_rule ? 1 : 0) != 0;
   if (narrow) {
     const dim3 grid(blocks_for(g.npts), g.nb);
-    if (g.dim == 3) k_jacobi<T, 3, 1><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
-    else k_jacobi<T, 2, 1><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
+    if (g.dim == 3) k_jacobi<T, 3, 1, SYM><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
+    else k_jacobi<T, 2, 1, SYM><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
     return;
   }
   const dim3 grid(blocks_for(g.npts / vw<T>()), g.nb);
-  if (g.dim == 3) k_jacobi<T, 3><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
-  else k_jacobi<T, 2><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
+  if (g.dim == 3) k_jacobi<T, 3, Vec<T>::W, SYM><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
+  else k_jacobi<T, 2, Vec<T>::W, SYM><<<grid, kBlock, 0, s>>>(g, st, dinv, r, sin, out, mode, state);
+}
+
+template <typename T>
+void launch_jacobi(const GridDesc& g, const T* st, const T* dinv, const T* r, const T* sin, T* out, int mode,
+                   const DevState* state, cudaStream_t s) {
+  if (g.ncomp != 1) return;   // vector grids smooth with launch_vres / launch_vblock
+  jacobi_impl<T>(g, st, dinv, r, sin, out, mode, state, s);
 }
 template <typename T>
 void launch_vres(const GridDesc& g, const T* st, const T* r, const T* x, T* t, const DevState* state,
@@ -1084,7 +1182,7 @@ void launch_vres(const GridDesc& g, const T* st, const T* r, const T* x, T* t, c
   k_vres<T, false><<<dim3(blocks_for(3 * (g.cstride / vw<T>())), g.nb), kBlock, 0, s>>>(g, st, r, x, t, nullptr,
                                                                                         state, nullptr);
 }
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_vres<double>(const GridDesc&, const double*, const double*, const double*, double*,
                                   const DevState*, cudaStream_t);
 template void launch_vres<float>(const GridDesc&, const float*, const float*, const float*, float*,
@@ -1096,7 +1194,7 @@ void launch_vres_block(const GridDesc& g, const T* st, const T* r, const T* x, c
                        const DevState* state, cudaStream_t s) {
   k_vres_block<T><<<dim3(blocks_for(g.cstride / vw<T>()), g.nb), kBlock, 0, s>>>(g, st, r, x, dinv, out, state);
 }
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_vres_block<double>(const GridDesc&, const double*, const double*, const double*,
                                         const double*, double*, const DevState*, cudaStream_t);
 template void launch_vres_block<float>(const GridDesc&, const float*, const float*, const float*, const float*,
@@ -1108,14 +1206,14 @@ void launch_vblock(const GridDesc& g, const T* dinv, const T* t, const T* sin, T
                    cudaStream_t s) {
   k_vblock<T><<<dim3(blocks_for(g.cstride / vw<T>()), g.nb), kBlock, 0, s>>>(g, dinv, t, sin, out, state);
 }
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_vblock<double>(const GridDesc&, const double*, const double*, const double*, double*,
                                     const DevState*, cudaStream_t);
 template void launch_vblock<float>(const GridDesc&, const float*, const float*, const float*, float*,
                                    const DevState*, cudaStream_t);
 #endif
 
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_jacobi<double>(const GridDesc&, const double*, const double*, const double*, const double*,
                                     double*, int, const DevState*, cudaStream_t);
 template void launch_jacobi<float>(const GridDesc&, const float*, const float*, const float*, const float*, float*,
@@ -1143,7 +1241,7 @@ template <typename T>
 void launch_sum_columns(const GridDesc& g, const T* Zc, int ncols, T* out, const DevState* state, cudaStream_t s) {
   k_sum_columns<T><<<dim3(stream_blocks(g), g.nb), kBlock, 0, s>>>(g, Zc, ncols, out, state);
 }
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_sum_columns<double>(const GridDesc&, const double*, int, double*, const DevState*, cudaStream_t);
 template void launch_sum_columns<float>(const GridDesc&, const float*, int, float*, const DevState*, cudaStream_t);
 #endif
@@ -1167,7 +1265,7 @@ void launch_coarse_tail(int jt, const GridDesc* g, const T* const* st, const T* 
   if (g[0].dim == 3) k_coarse_tail<T, 3><<<grid, 1024, smem, s>>>(a, state);
   else k_coarse_tail<T, 2><<<grid, 1024, smem, s>>>(a, state);
 }
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_coarse_tail<double>(int, const GridDesc*, const double* const*, const double* const*,
                                          double* const*, double* const*, const double*, const double*,
                                          const DevState*, cudaStream_t);
@@ -1183,7 +1281,7 @@ void launch_gs_colour(const GridDesc& g, const T* st, const T* b, T* x, int colo
   if (g.dim == 3) k_gs_colour<T, 3><<<grid, kBlock, 0, s>>>(g, st, b, x, colour, (T)omega, state);
   else k_gs_colour<T, 2><<<grid, kBlock, 0, s>>>(g, st, b, x, colour, (T)omega, state);
 }
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_gs_colour<double>(const GridDesc&, const double*, const double*, double*, int, double,
                                        const DevState*, cudaStream_t);
 template void launch_gs_colour<float>(const GridDesc&, const float*, const float*, float*, int, double,
@@ -1197,7 +1295,7 @@ void launch_defect(const GridDesc& g, const T* st, const T* b, const T* x, T* d,
   if (g.dim == 3) k_defect<T, 3><<<grid, kBlock, 0, s>>>(g, st, b, x, d, state);
   else k_defect<T, 2><<<grid, kBlock, 0, s>>>(g, st, b, x, d, state);
 }
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_defect<double>(const GridDesc&, const double*, const double*, const double*, double*,
                                     const DevState*, cudaStream_t);
 template void launch_defect<float>(const GridDesc&, const float*, const float*, const float*, float*,
@@ -1211,7 +1309,7 @@ void launch_prolong_add(const GridDesc& gc, const GridDesc& gf, const T* coarse,
   if (gf.dim == 3) k_prolong_add<T, 3><<<grid, kBlock, 0, s>>>(gc, gf, coarse, fine, state);
   else k_prolong_add<T, 2><<<grid, kBlock, 0, s>>>(gc, gf, coarse, fine, state);
 }
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_prolong_add<double>(const GridDesc&, const GridDesc&, const double*, double*, const DevState*,
                                          cudaStream_t);
 template void launch_prolong_add<float>(const GridDesc&, const GridDesc&, const float*, float*, const DevState*,
@@ -1222,7 +1320,7 @@ template <typename T>
 void launch_add_to(const GridDesc& g, const T* src, T* dst, const DevState* state, cudaStream_t s) {
   k_add_to<T><<<dim3(blocks_for(g.npts), g.nb), kBlock, 0, s>>>(g, src, dst, state);
 }
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_add_to<double>(const GridDesc&, const double*, double*, const DevState*, cudaStream_t);
 template void launch_add_to<float>(const GridDesc&, const float*, float*, const DevState*, cudaStream_t);
 #endif
@@ -1250,14 +1348,14 @@ void launch_prolong_all(const GridDesc& gf, const T* const* coarse, const GridDe
   }
 #undef MPCG_PROLONG_CASE
 }
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_prolong_all<double>(const GridDesc&, const double* const*, const GridDesc*, int, double*,
                                          const DevState*, cudaStream_t);
 template void launch_prolong_all<float>(const GridDesc&, const float* const*, const GridDesc*, int, float*,
                                         const DevState*, cudaStream_t);
 #endif
 
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 void launch_galerkin(const GridDesc& gf, const GridDesc& gc, const double* stf, double* stc, cudaStream_t s) {
   const dim3 grid(blocks_for(gc.npts), gc.nb);
   if (gc.dim == 3) k_galerkin<3><<<grid, kBlock, 0, s>>>(gf, gc, stf, stc);
@@ -1269,20 +1367,20 @@ template <typename T>
 void launch_dinv(const GridDesc& g, const double* st, T* dinv, double omega, cudaStream_t s) {
   k_dinv<T><<<dim3(blocks_for(g.npts), g.nb), kBlock, 0, s>>>(g, st, dinv, omega);
 }
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_dinv<double>(const GridDesc&, const double*, double*, double, cudaStream_t);
 template void launch_dinv<float>(const GridDesc&, const double*, float*, double, cudaStream_t);
 #endif
 
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 void launch_convert_f32(const double* src, float* dst, long long count, cudaStream_t s) {
   k_convert_f32<<<grid_for(count, 4096), kBlock, 0, s>>>(src, dst, count);
 }
 #endif
 
-#ifndef MPCG_STENCIL_DW
+#if MPCG_STENCIL_PLAIN
 template void launch_pack_flag<double>(const GridDesc&, const double*, double*, int*, cudaStream_t);
-#else
+#elif defined(MPCG_STENCIL_DW)
 // The double-word instances (FP64 data, double-FP32 arithmetic), compiled in
 // their own translation unit (stencil_dw.cu) to keep the build parallel.
 template void launch_pack<double, dw>(const GridDesc&, const double*, long long, dw*, int, cudaStream_t);
@@ -1325,6 +1423,30 @@ __global__ void k_convert_dw(const double* __restrict__ src, dw* __restrict__ ds
 
 void launch_convert_dw(const double* src, dw* dst, long long count, cudaStream_t s) {
   k_convert_dw<<<grid_for(count, 4096), kBlock, 0, s>>>(src, dst, count);
+}
+#endif
+
+#ifdef MPCG_STENCIL_SYM
+// FP32 kernels on the symmetric half of a scalar stencil, compiled in their
+// own translation unit (stencil_sym.cu).
+int sym_planes(int dim) { return dim == 3 ? 14 : 5; }
+
+void launch_sym_half(const GridDesc& g, const double* st, float* half, cudaStream_t s) {
+  if (g.dim == 3) k_sym_half<3><<<grid_for(g.cp, 4096), kBlock, 0, s>>>(g, st, half);
+  else k_sym_half<2><<<grid_for(g.cp, 4096), kBlock, 0, s>>>(g, st, half);
+}
+
+void launch_spmm_sym(const GridDesc& g, const float* half, const float* X, float* Y, int C, double* zaz,
+                     const DevState* state, cudaStream_t s) {
+  if (g.ncomp != 1) return;
+  if (g.dim == 3) spmm_dim<float, 3, true>(g, half, X, Y, C, zaz, state, s);
+  else spmm_dim<float, 2, true>(g, half, X, Y, C, zaz, state, s);
+}
+
+void launch_jacobi_sym(const GridDesc& g, const float* half, const float* dinv, const float* r, const float* sin,
+                       float* out, int mode, const DevState* state, cudaStream_t s) {
+  if (g.ncomp != 1) return;
+  jacobi_impl<float, true>(g, half, dinv, r, sin, out, mode, state, s);
 }
 #endif
 

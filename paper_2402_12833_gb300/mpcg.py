@@ -84,6 +84,8 @@ _SIGS = {
     "mg_level_size": (C.c_longlong, [C.c_void_p, C.c_int]),
     "mg_apply_operator": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
     "mg_corrections": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mg_apply_operator_f32": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    "mg_corrections_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "mg_get_operator": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "mg_hierarchy_destroy": (None, [C.c_void_p]),
     "mpcg_last_error": (C.c_char_p, []),
@@ -274,6 +276,16 @@ def mg_apply_operator(h: int, level: int, X_dev, Y_dev, ncols: int) -> None:
 
 def mg_corrections(h: int, r_dev, Z_dev) -> None:
     _check(load().mg_corrections(h, _ptr(r_dev), _ptr(Z_dev)))
+
+
+def mg_apply_operator_f32(h: int, level: int, X_dev, Y_dev, ncols: int) -> None:
+    """mg_apply_operator in the FP32 arithmetic of the mixed inner solves."""
+    _check(load().mg_apply_operator_f32(h, level, _ptr(X_dev), _ptr(Y_dev), ncols))
+
+
+def mg_corrections_f32(h: int, r_dev, Z_dev) -> None:
+    """mg_corrections in the FP32 arithmetic of the mixed inner solves."""
+    _check(load().mg_corrections_f32(h, _ptr(r_dev), _ptr(Z_dev)))
 
 
 def mg_get_operator(h: int, level: int, planes_dev) -> None:
