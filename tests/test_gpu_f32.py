@@ -8,7 +8,8 @@ the neighbour's entry).  Covered: 2D and 3D, every grid of the hierarchy
 (the narrow one-point-per-thread smoothing of the small grids included),
 all-Dirichlet grids with power-of-two pitches, a grid whose pitch exceeds its
 extent by more than one (Example 1: 159 unknowns per side, pitch 160), free
-(natural) faces, and ragged column counts.
+(natural) faces, ragged column counts, and grids of pitch 4 to 160 (rows
+that fill part of a warp, several rows per warp, or more than a warp).
 
 Bars.  SpMM: an output is a sum of at most 27 products of FP32-rounded
 operands accumulated in FP32, so |y32 - A x| <= gamma_29 (|A| |x|)
@@ -50,6 +51,8 @@ PROBS = {
     "poisson3d_17": lambda: pb.poisson_random(3, 17, 2),
     "kappa3d_33": lambda: pb.diffusion_macro(3, 33, 4, rhs="normal", rhs_seed=6),
     "diff3d_17_free": lambda: pb.diffusion_faces(3, 17, 0x2A, rhs_seed=4, kappa_seed=8),
+    "kappa3d_65": lambda: pb.diffusion_macro(3, 65, 5, rhs="normal", rhs_seed=7),
+    "diff3d_65_free": lambda: pb.diffusion_faces(3, 65, 0x2A, rhs_seed=8, kappa_seed=10),
 }
 
 
@@ -104,3 +107,38 @@ def test_f32_calls_need_a_mixed_stencil_hierarchy(M):
         M.mg_apply_operator_f32(H.h, prob.levels - 1, X, X.clone(), 1)
     with pytest.raises(M.MpcgError):
         M.mg_corrections_f32(H.h, X, torch.zeros((prob.levels, prob.n), dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("name", ["kappa3d_33", "kappa3d_65", "diff3d_65_free"])
+def test_f32_spmm_columns_are_independent(M, name):
+    """A column's product does not depend on the other columns: the 1-, 5-
+    and 6-column products (separate kernel instances) equal the first columns
+    of the 12-column product bit for bit."""
+    prob = PROBS[name]()
+    H = _hier(M, prob)
+    for j in range(prob.levels):
+        n = M.mg_level_size(H.h, j)
+        X = torch.from_numpy(pb.normal(500 + j, 12 * n).reshape(12, n)).cuda()
+        Y12 = torch.zeros_like(X)
+        M.mg_apply_operator_f32(H.h, j, X, Y12, 12)
+        for c in (1, 5, 6):
+            Yc = torch.zeros_like(X[:c])
+            M.mg_apply_operator_f32(H.h, j, X[:c].contiguous(), Yc, c)
+            assert torch.equal(Yc, Y12[:c]), (j, c)
+
+
+@pytest.mark.parametrize("name", ["kappa3d_65", "diff3d_65_free"])
+def test_f32_mixed_solve_reaches_fp64_tolerance(M, name):
+    """A mixed solve on a 65^3 grid (fine-grid SpMM with the z^T A z
+    partials): the true FP64 residual of its solution, taken with the
+    oracle's operator, meets the tolerance."""
+    prob = PROBS[name]()
+    H = _hier(M, prob)
+    O = _oracle(prob)
+    b = torch.from_numpy(prob.b).cuda()
+    x = torch.zeros_like(b)
+    st, k, rh, ah = H.solve(b, x, rtol=1e-8, maxit=2000)
+    assert st == M.MPCG_OK
+    xg = x.cpu().numpy()
+    tr = np.linalg.norm(prob.b - O.A[-1] @ xg) / np.linalg.norm(prob.b)
+    assert tr <= 1e-8
