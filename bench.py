@@ -497,6 +497,24 @@ def bench_ours(args):
                     "launches_per_step": launches, "true_rel_residual": true_res,
                     "x": x.detach().clone() if key in ("fp64", "fp64_dw") else None}
 
+    # the same mixed solve with the FP32 kernels on the full 27-plane stencil
+    # (half_stencil = 0) instead of its symmetric half, same launch-shape table
+    # and timing: the in-run comparison for the half-stencil layout
+    full = None
+    if args.only is None:
+        Hf = M.Hierarchy(st, DIM, NODES, prob.levels, m=M_WINDOW, precision=M.MPCG_MIXED, stream=sptr,
+                         use_graph=ug, half_stencil=0)
+        kf = {}
+
+        def full_step():
+            x.zero_()
+            _, kf["k"], _, _ = Hf.solve(b, x, rtol=RTOL, maxit=MAXIT, histories=False)
+
+        full_ms = max_over_ranks(_timed(full_step, args.steps, args.warmup, stream))
+        full = {"value": world * n / (full_ms * 1e-3), "ms_per_step": full_ms, "iterations": int(kf["k"]),
+                "stencil_words_per_unknown": 27, "note": "FP32 SpMM and Jacobi on the full stencil (half_stencil=0)"}
+        Hf.close()
+
     if args.only is not None:
         r = res[args.only]
         if rank == 0:
@@ -609,6 +627,7 @@ def bench_ours(args):
                                         "SpMM and Jacobi kernels; stored stencils elsewhere"},
             "roofline": prof["mixed"]["roofline"],
             "per_iteration": piter["mixed"],
+            "full_stencil": full,
             "autotune": None if args.no_autotune else {
                 "candidates_timed": tuned, "fixed_rules_ms_per_step": fixed_ms,
                 "note": "every leg timed with the autotuner's launch shapes; the fixed rules' times beside"},
@@ -1326,10 +1345,12 @@ def bench_learned(args):
     kap = torch.from_numpy(np.ascontiguousarray(prob.kappa).reshape(-1)).cuda()
     legs = {"plain": M.MPCG_MIXED, "learned": M.MPCG_MIXED, "plain_matrix_free": M.MPCG_MIXED,
             "learned_matrix_free": M.MPCG_MIXED, "plain_fp64": M.MPCG_FP64, "plain_fp64_dw": M.MPCG_FP64_DW,
-            "learned_fp64_dw": M.MPCG_FP64_DW}
+            "learned_fp64_dw": M.MPCG_FP64_DW, "plain_full_stencil": M.MPCG_MIXED}
     for key, prec in legs.items():
         print(f"learned workload: leg {key}", file=sys.stderr, flush=True)
-        H = M.Hierarchy(st, 2, 1025, prob.levels, m=M_WINDOW, precision=prec)
+        # plain_full_stencil: the FP32 kernels on the full 9-plane stencil instead of its symmetric half
+        H = M.Hierarchy(st, 2, 1025, prob.levels, m=M_WINDOW, precision=prec,
+                        half_stencil=0 if key == "plain_full_stencil" else 1)
         if key.startswith("learned"):
             M.mg_learned_attach(H.h, params)
         if key.endswith("matrix_free"):   # fine operator rebuilt from the element coefficients
@@ -1364,7 +1385,7 @@ def bench_learned(args):
         "plain": out["plain"], "learned": out["learned"],
         "plain_matrix_free": out["plain_matrix_free"], "learned_matrix_free": out["learned_matrix_free"],
         "plain_fp64": out["plain_fp64"], "plain_fp64_dw": out["plain_fp64_dw"],
-        "learned_fp64_dw": out["learned_fp64_dw"],
+        "learned_fp64_dw": out["learned_fp64_dw"], "plain_full_stencil": out["plain_full_stencil"],
         # wall time of the plain FP64 solve over that of mixed precision + the learned column
         "speedup_learned_mixed_vs_plain_fp64": out["plain_fp64"]["ms_per_solve"] / out["learned"]["ms_per_solve"],
         "speedup_learned_mixed_vs_plain_mixed": out["plain"]["ms_per_solve"] / out["learned"]["ms_per_solve"],

@@ -117,7 +117,7 @@ typedef struct {
  * pinv_tau = 1e-12, drop_delta = 1e-10, precision MPCG_FP64,
  * inner_rtol = 3e-3, inner pinv_tau = 1e-6, inner drop_delta = 1e-5,
  * use_graph = 1, sum_columns = 0, smoother = MPCG_SMOOTHER_JACOBI,
- * ssor_omega = 1, vcycle = 0.  The FP32
+ * ssor_omega = 1, vcycle = 0, half_stencil = 1.  The FP32
  * inner solves converge in fewer total iterations when restarted often (the
  * FP64 refinement renews the residual and the search space), hence the
  * loose inner tolerance. */
@@ -149,6 +149,14 @@ typedef struct {
                             smoother (nu SSOR steps, or nu damped-Jacobi sweeps, the
                             post-smoothing continuing from the corrected iterate);
                             scalar problems; not with sum_columns */
+  int half_stencil;      /* MPCG_MIXED, scalar stencil grids: 1 the FP32 SpMM and
+                            smoothing read the stencil's symmetric half (the diagonal
+                            and the couplings to the later neighbours, 14 of 27 planes
+                            in 3D, 5 of 9 in 2D; a coupling to an earlier neighbour is
+                            read as A(i, i - s) = A(i - s, i)); 0 the full stencil.
+                            The sums agree where the stored operator is exactly
+                            symmetric and differ by rounding where it is not (Galerkin
+                            products summed in another order) */
   void* stream;          /* cudaStream_t */
 } mpcg_options;
 

@@ -961,7 +961,7 @@ mpcg_status build_f32(mg_hierarchy* h) {
     CKS(h->mem.get(&L.dinv32, (size_t)L.ndinv * L.g.cp, s));
     launch_convert_f32(L.st64, L.st32, (long long)L.nplanes * L.g.cp, s);
     launch_convert_f32(L.dinv64, L.dinv32, (long long)L.ndinv * L.g.cp, s);
-    if (L.g.ncomp == 1) {   // the FP32 SpMM and Jacobi stream the symmetric half: 14 of 27 (5 of 9) planes
+    if (L.g.ncomp == 1 && h->opt.half_stencil) {   // the FP32 SpMM and Jacobi stream the symmetric half
       CKS(h->mem.get(&L.sth32, (size_t)sym_planes(L.g.dim) * L.g.cp, s));
       launch_sym_half(L.g, L.st64, L.sth32, s);
     }
@@ -1040,9 +1040,9 @@ mpcg_status check_options(const mpcg_options& opt) {
       (opt.sum_columns != 0 && opt.sum_columns != 1) || (opt.vcycle != 0 && opt.vcycle != 1) ||
       (opt.sum_columns && opt.vcycle) ||
       (opt.smoother != MPCG_SMOOTHER_JACOBI && opt.smoother != MPCG_SMOOTHER_SSOR) ||
-      !(opt.ssor_omega > 0.0 && opt.ssor_omega < 2.0)) {
+      !(opt.ssor_omega > 0.0 && opt.ssor_omega < 2.0) || (opt.half_stencil != 0 && opt.half_stencil != 1)) {
     set_err("invalid options (m in 1..%d, nu >= 1, omega > 0, tau/delta >= 0, max_outer >= 1, sum_columns 0/1, "
-            "vcycle 0/1 and not with sum_columns, smoother JACOBI/SSOR, 0 < ssor_omega < 2)",
+            "vcycle 0/1 and not with sum_columns, smoother JACOBI/SSOR, 0 < ssor_omega < 2, half_stencil 0/1)",
             MPCG_MAX_WINDOW);
     return MPCG_ERR_ARG;
   }
@@ -1117,6 +1117,7 @@ mpcg_status mpcg_default_options(mpcg_options* opt) {
   opt->smoother = MPCG_SMOOTHER_JACOBI;
   opt->ssor_omega = 1.0;
   opt->vcycle = 0;
+  opt->half_stencil = 1;
   opt->stream = nullptr;
   return MPCG_OK;
 }

@@ -55,7 +55,7 @@ class mpcg_options(C.Structure):
                 ("drop_delta", C.c_double), ("precision", C.c_int), ("inner_rtol", C.c_double),
                 ("inner_pinv_tau", C.c_double), ("inner_drop_delta", C.c_double), ("max_outer", C.c_int),
                 ("use_graph", C.c_int), ("sum_columns", C.c_int), ("smoother", C.c_int), ("ssor_omega", C.c_double),
-                ("vcycle", C.c_int), ("stream", C.c_void_p)]
+                ("vcycle", C.c_int), ("half_stencil", C.c_int), ("stream", C.c_void_p)]
 
 
 class mg_csr(C.Structure):

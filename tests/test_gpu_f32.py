@@ -142,3 +142,28 @@ def test_f32_mixed_solve_reaches_fp64_tolerance(M, name):
     xg = x.cpu().numpy()
     tr = np.linalg.norm(prob.b - O.A[-1] @ xg) / np.linalg.norm(prob.b)
     assert tr <= 1e-8
+
+
+@pytest.mark.parametrize("name", ["poisson2d_65", "kappa3d_33", "diff3d_17_free"])
+def test_f32_full_stencil_option(M, name):
+    """half_stencil = 0: the FP32 kernels read the full stored stencil; the
+    products meet the same bar against the oracle on every grid, and the
+    mixed solve still reaches the FP64 tolerance."""
+    prob = PROBS[name]()
+    H = _hier(M, prob, half_stencil=0)
+    O = _oracle(prob)
+    for j in range(prob.levels):
+        n = O.A[j].shape[0]
+        X = pb.normal(700 + j, 6 * n).reshape(6, n)
+        Yd = torch.zeros((6, n), dtype=torch.float64, device="cuda")
+        M.mg_apply_operator_f32(H.h, j, torch.from_numpy(X).cuda(), Yd, 6)
+        ref = (O.A[j] @ X.T).T
+        bound = (abs(O.A[j]) @ np.abs(X).T).T
+        assert np.all(np.abs(Yd.cpu().numpy() - ref) <= 64 * U * bound), j
+    b = torch.from_numpy(prob.b).cuda()
+    x = torch.zeros_like(b)
+    st, k, _, _ = H.solve(b, x, rtol=1e-8, maxit=2000)
+    assert st == M.MPCG_OK
+    assert np.linalg.norm(prob.b - O.A[-1] @ x.cpu().numpy()) <= 1e-8 * np.linalg.norm(prob.b)
+    with pytest.raises(M.MpcgError):
+        _hier(M, prob, half_stencil=2)
