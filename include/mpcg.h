@@ -377,9 +377,13 @@ mpcg_status mg_corrections(mg_hierarchy* h, const double* r_dev, double* Z_dev);
  * FP32 on entry and the FP32 kernels of the inner iterations (on scalar
  * grids, the stored stencil's symmetric half: the diagonal and the couplings
  * to the lexicographically later neighbours, the others read transposed as
- * A(i, i - s) = A(i - s, i)).  Same arguments and layouts as the FP64 calls;
- * results are returned as doubles.  MPCG_ERR_ARG unless h is a single
- * stencil hierarchy built with precision MPCG_MIXED.
+ * A(i, i - s) = A(i - s, i), unless the options set half_stencil = 0).
+ * mg_apply_operator_f32 applies the stored stencil even where a matrix-free
+ * fine operator is attached (mg_attach_q1_kappa); mg_corrections_f32 smooths
+ * as the inner solve does, with that operator on the fine grid when it is
+ * attached.  Same arguments and layouts as the
+ * FP64 calls; results are returned as doubles.  MPCG_ERR_ARG unless h is a
+ * single stencil hierarchy built with precision MPCG_MIXED.
  */
 mpcg_status mg_apply_operator_f32(mg_hierarchy* h, int level, const double* X_dev,
                                   double* Y_dev, int ncols);
