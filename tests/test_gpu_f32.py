@@ -20,6 +20,8 @@ size of |a||x| and fails it.  MG columns: two damped-Jacobi sweeps, the
 transfers and the coarse solve in FP32 data; the bar is 2e-5 of each
 column's largest entry (the observed error is a few 1e-7).
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -167,3 +169,42 @@ def test_f32_full_stencil_option(M, name):
     assert np.linalg.norm(prob.b - O.A[-1] @ x.cpu().numpy()) <= 1e-8 * np.linalg.norm(prob.b)
     with pytest.raises(M.MpcgError):
         _hier(M, prob, half_stencil=2)
+
+
+@functools.lru_cache(maxsize=1)
+def _full_size():
+    prob = pb.poisson_random(3, 129, 2)
+    return prob, _oracle(prob)
+
+
+def test_f32_full_size_spmm_columns_and_solve(M):
+    """The benchmark's workload at full size (3D Poisson 129^3, 2,048,383
+    unknowns, 6 grids): the fine-grid SpMM of the FP32 inner iterations with
+    its 6 columns, entrywise within 64 u of |A||x| of the oracle's product;
+    the 6 FP32 MG columns within 2e-5 of the oracle's; and the mixed solve's
+    true FP64 residual, taken with the oracle's operator, below 1e-8."""
+    prob, O = _full_size()
+    H = _hier(M, prob)
+    j = prob.levels - 1
+    X = pb.normal(900, 6 * prob.n).reshape(6, prob.n)
+    Yd = torch.zeros((6, prob.n), dtype=torch.float64, device="cuda")
+    M.mg_apply_operator_f32(H.h, j, torch.from_numpy(X).cuda(), Yd, 6)
+    Y = Yd.cpu().numpy()
+    del Yd
+    for c in range(6):
+        ref = O.A[j] @ X[c]
+        bound = abs(O.A[j]) @ np.abs(X[c])
+        assert np.all(np.abs(Y[c] - ref) <= 64 * U * bound), c
+    r = pb.normal(901, prob.n)
+    Zd = torch.zeros((prob.levels, prob.n), dtype=torch.float64, device="cuda")
+    M.mg_corrections_f32(H.h, torch.from_numpy(r).cuda(), Zd)
+    Z = Zd.cpu().numpy().T
+    del Zd
+    ref = O.mg_columns(r)
+    for l in range(prob.levels):
+        assert np.abs(Z[:, l] - ref[:, l]).max() <= 2e-5 * np.abs(ref[:, l]).max(), l
+    b = torch.from_numpy(prob.b).cuda()
+    x = torch.zeros_like(b)
+    st, k, _, _ = H.solve(b, x, rtol=1e-8, maxit=200, histories=False)
+    assert st == M.MPCG_OK
+    assert np.linalg.norm(prob.b - O.A[-1] @ x.cpu().numpy()) <= 1e-8 * np.linalg.norm(prob.b)
